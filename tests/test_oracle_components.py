@@ -1,0 +1,346 @@
+"""Pins of the oracle's components against closed forms, textbook constants and brute force.
+
+Each test names what it pins and why a plausible mistake (dropped term, wrong sign,
+wrong index, transposed operand, wrong prefactor) would fail it.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.special import erf, erfc
+
+import workloads
+from oracle import basis, dft, ewald as ew, lda, pseudo
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _madelung():
+    with open(os.path.join(GOLDEN, "madelung.json")) as fh:
+        return json.load(fh)
+
+
+# ---------------------------------------------------------------- basis ----
+def test_sphere_matches_brute_force_enumeration():
+    """Plane-wave count and membership vs a plain triple loop over a generous box."""
+    cell = np.array([[5.0, 0.3, 0.0], [0.4, 5.5, 0.2], [-0.3, 0.1, 6.0]])
+    ecut = 4.0
+    m, G, g2 = basis.sphere(cell, ecut)
+    B = 2 * math.pi * np.linalg.inv(cell).T
+    brute = set()
+    for i in range(-12, 13):
+        for j in range(-12, 13):
+            for k in range(-12, 13):
+                g = i * B[0] + j * B[1] + k * B[2]
+                if 0.5 * float(g @ g) <= ecut:
+                    brute.add((i, j, k))
+    assert set(map(tuple, m.tolist())) == brute
+    # closed under inversion (real psi at Gamma needs both G and -G)
+    assert set(map(tuple, (-m).tolist())) == brute
+    assert np.allclose(0.5 * g2, 0.5 * np.einsum("ij,ij->i", G, G))
+
+
+def test_reciprocal_duality():
+    cell = np.array([[5.0, 0.3, 0.0], [0.4, 5.5, 0.2], [-0.3, 0.1, 6.0]])
+    B = basis.reciprocal(cell)
+    assert np.allclose(cell @ B.T, 2 * math.pi * np.eye(3), atol=1e-13)
+
+
+def _free_model(ecut=3.0):
+    sp = dict(z_val=0.0, rc=1.0, a_sr=0.0, sigma_sr=1.0, rp=1.0, d_nl=0.0)
+    st = workloads.tiny(nat=1, ecut=ecut, species=sp, nbands=4, kT=0.01)
+    return dft.Model(st), st
+
+
+def test_free_electron_eigenvalues_are_kinetic():
+    """V = 0, D = 0: eigenvalues are exactly sorted |G|^2/2 (dense H and FFT-applied H)."""
+    m, st = _free_model()
+    beta = dft.projectors(m, st.pos)
+    veff = np.zeros(m.grid)
+    H = dft.dense_h(m, veff, beta)
+    w = np.linalg.eigvalsh(H)
+    assert np.allclose(w, np.sort(0.5 * m.g2), atol=1e-13)
+    C = np.eye(m.npw, dtype=complex)[:, :7]
+    assert np.allclose(dft.apply_h(m, veff, beta, C), 0.5 * m.g2[:, None] * C, atol=1e-13)
+
+
+def test_constant_potential_shifts_spectrum():
+    """A constant V0(r) adds V0 to every eigenvalue (pins the 1/N of the G = 0 component)."""
+    m, st = _free_model()
+    beta = dft.projectors(m, st.pos)
+    w = np.linalg.eigvalsh(dft.dense_h(m, np.full(m.grid, -0.37), beta))
+    assert np.allclose(w, np.sort(0.5 * m.g2) - 0.37, atol=1e-13)
+
+
+def test_cosine_potential_couples_g_and_g_plus_g1():
+    """V(r) = 2 V1 cos(G1.r) has Fourier components V1 at +-G1: H(G, G') = V1 iff G - G' = +-G1.
+    A transposed index (G' - G) or a dropped 1/N would break the value or the placement."""
+    m, st = _free_model(ecut=4.0)
+    g1 = np.array([1, -1, 2])
+    G1 = g1 @ basis.reciprocal(m.cell)
+    rr = basis.box_miller(m.grid)  # only used for the grid shape
+    frac = np.stack(np.meshgrid(*[np.arange(n) / n for n in m.grid], indexing="ij"), -1)
+    r = frac @ m.cell
+    V1 = 0.21
+    veff = 2 * V1 * np.cos(r @ G1)
+    beta = dft.projectors(m, st.pos)
+    H = dft.dense_h(m, veff, beta)
+    lut = {tuple(x): i for i, x in enumerate(m.m.tolist())}
+    hits = 0
+    for i, mi in enumerate(m.m.tolist()):
+        j = lut.get(tuple(np.array(mi) - g1))
+        if j is not None:
+            assert abs(H[i, j] - V1) < 1e-13
+            hits += 1
+    assert hits > 5
+    off = H - np.diag(np.diag(H))
+    assert abs(np.sum(np.abs(off) > 1e-12) - 2 * hits) == 0
+    del rr
+
+
+def test_dense_h_equals_fft_apply_with_projectors():
+    st = workloads.tiny(nat=2, ecut=3.5)
+    m = dft.Model(st)
+    rng = np.random.default_rng(3)
+    veff = rng.normal(size=m.grid)
+    beta = dft.projectors(m, st.pos)
+    C = rng.normal(size=(m.npw, 5)) + 1j * rng.normal(size=(m.npw, 5))
+    H = dft.dense_h(m, veff, beta)
+    assert np.allclose(H, H.conj().T, atol=1e-14)
+    assert np.allclose(H @ C, dft.apply_h(m, veff, beta, C), atol=1e-12)
+
+
+def test_density_integrates_to_occupation_sum():
+    st = workloads.tiny(nat=2, ecut=3.0)
+    m = dft.Model(st)
+    rng = np.random.default_rng(1)
+    C, _ = np.linalg.qr(rng.normal(size=(m.npw, 4)) + 1j * rng.normal(size=(m.npw, 4)))
+    f = np.array([2.0, 1.5, 0.25, 0.0])
+    rho = dft.density(m, C, f)
+    assert abs(m.omega / m.N * rho.sum() - f.sum()) < 1e-12
+    assert rho.min() >= 0.0
+
+
+# --------------------------------------------------------- pseudopotential ----
+def _radial_ft(fun, g, rmax=40.0):
+    """4 pi / g int_0^inf r f(r) sin(g r) dr (3D Fourier transform of a radial function)."""
+    val, _ = integrate.quad(lambda r: r * fun(r) * math.sin(g * r), 0.0, rmax, limit=400)
+    return 4 * math.pi / g * val
+
+
+@pytest.mark.parametrize("sp", [workloads.SPECIES_Z4, workloads.SPECIES_Z10])
+def test_local_pseudopotential_transform(sp):
+    """v_s(G) vs numerical radial transform.  The Coulomb tail is handled by transforming
+    Z erfc(r/rc)/r (short-ranged), whose transform is (4 pi Z/G^2)(1 - exp(-G^2 rc^2/4))."""
+    omega = 123.4
+    Z, rc, A, s = sp["z_val"], sp["rc"], sp["a_sr"], sp["sigma_sr"]
+    for g in (0.3, 1.1, 2.7):
+        short = _radial_ft(lambda r: Z * erfc(r / rc) / r + A * math.exp(-r * r / s / s), g)
+        numeric = (-4 * math.pi * Z / g ** 2 + short) / omega
+        assert abs(pseudo.vloc_g(sp, np.array([g * g]), omega)[0] - numeric) < 1e-9
+    # G = 0: (1/Omega) int (v + Z/r) d^3r
+    alpha, _ = integrate.quad(lambda r: 4 * math.pi * r * r * (Z * erfc(r / rc) / r + A * math.exp(-r * r / s / s)),
+                              0.0, 40.0, limit=400)
+    assert abs(pseudo.vloc_g(sp, np.array([0.0]), omega)[0] - alpha / omega) < 1e-9
+    assert abs(pseudo.vloc_alpha(sp, omega) - alpha / omega) < 1e-9
+
+
+@pytest.mark.parametrize("sp", [workloads.SPECIES_Z4, workloads.SPECIES_Z10])
+def test_projector_transform_and_norm(sp):
+    omega = 87.0
+    rp = sp["rp"]
+    nrm = 1.0 / math.sqrt(math.pi ** 1.5 * rp ** 3)
+    # <beta|beta> = 1 in real space
+    val, _ = integrate.quad(lambda r: 4 * math.pi * r * r * (nrm * math.exp(-r * r / (2 * rp * rp))) ** 2, 0, 30)
+    assert abs(val - 1.0) < 1e-10
+    for g in (0.2, 1.0, 2.5):
+        ft = _radial_ft(lambda r: nrm * math.exp(-r * r / (2 * rp * rp)), g)
+        assert abs(pseudo.beta_g(sp, np.array([g * g]), omega)[0] - ft / math.sqrt(omega)) < 1e-10
+
+
+def test_projector_completeness_in_a_large_cell():
+    """sum_G |<G|beta>|^2 -> <beta|beta> = 1 when Ecut is high and images do not overlap."""
+    sp = workloads.SPECIES_Z4
+    cell = np.eye(3) * 9.0
+    m, G, g2 = basis.sphere(cell, 30.0)
+    b = pseudo.beta_g(sp, g2, basis.volume(cell))
+    assert abs(np.sum(b * b) - 1.0) < 1e-8
+
+
+def test_nonlocal_rank_one_secular_equation():
+    """Free electrons plus one projector D|b><b|: every eigenvalue e not in {|G|^2/2} solves
+    1 = D sum_G |b(G)|^2 / (e - |G|^2/2) (a closed form for a rank-one update)."""
+    sp = dict(z_val=0.0, rc=1.0, a_sr=0.0, sigma_sr=1.0, rp=0.9, d_nl=-0.8)
+    st = workloads.tiny(nat=1, ecut=3.0, species=sp, nbands=4, kT=0.01)
+    m = dft.Model(st)
+    beta = dft.projectors(m, st.pos)
+    w = np.linalg.eigvalsh(dft.dense_h(m, np.zeros(m.grid), beta))
+    t = 0.5 * m.g2
+    b2 = np.abs(beta[0]) ** 2
+    # the lowest eigenvalue is pulled below min(t) = 0 by the attractive projector
+    e0 = w[0]
+    assert e0 < -1e-3
+    assert abs(1.0 - sp["d_nl"] * np.sum(b2 / (e0 - t))) < 1e-10
+
+
+# ---------------------------------------------------------------- Ewald ----
+def test_ewald_madelung_nacl():
+    a = 5.3
+    r0 = a / 2
+    fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    pos = np.concatenate([fcc, fcc + [0.5, 0, 0]]) * a
+    z = np.array([1.0] * 4 + [-1.0] * 4)
+    e, f = ew.ewald(np.eye(3) * a, z, pos)
+    assert abs(e / 4 * r0 + _madelung()["NaCl"]) < 2e-6
+    assert np.abs(f).max() < 1e-10
+
+
+def test_ewald_madelung_cscl():
+    a = 4.1
+    r0 = math.sqrt(3) * a / 2
+    e, f = ew.ewald(np.eye(3) * a, np.array([1.0, -1.0]), np.array([[0, 0, 0], [.5, .5, .5]]) * a)
+    assert abs(e * r0 + _madelung()["CsCl"]) < 2e-6
+    assert np.abs(f).max() < 1e-10
+
+
+def test_ewald_madelung_zincblende():
+    a = 6.0
+    r0 = math.sqrt(3) * a / 4
+    fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    pos = np.concatenate([fcc, fcc + 0.25]) * a
+    z = np.array([2.0] * 4 + [-2.0] * 4)
+    e, _ = ew.ewald(np.eye(3) * a, z, pos)
+    assert abs(e / 4 * r0 / 4.0 + _madelung()["zincblende"]) < 2e-6
+
+
+def test_ewald_single_charge_with_background():
+    L = 7.0
+    e, _ = ew.ewald(np.eye(3) * L, np.array([3.0]), np.zeros((1, 3)))
+    assert abs(e + _madelung()["sc_background"] * 9.0 / (2 * L)) < 5e-6
+
+
+def test_ewald_eta_independent_and_force_is_gradient():
+    st = workloads.de_candidate(3)
+    z = np.full(st.natoms, 4.0)
+    e1, f1 = ew.ewald(st.cell, z, st.pos, eta=0.35)
+    e2, f2 = ew.ewald(st.cell, z, st.pos, eta=0.8)
+    assert abs(e1 - e2) < 1e-10 * abs(e1)
+    assert np.abs(f1 - f2).max() < 1e-9
+    h = 1e-4
+    for I, a in [(0, 0), (2, 1), (5, 2)]:
+        p = st.pos.copy(); p[I, a] += h
+        ep, _ = ew.ewald(st.cell, z, p)
+        p[I, a] -= 2 * h
+        em, _ = ew.ewald(st.cell, z, p)
+        assert abs(-(ep - em) / (2 * h) - f1[I, a]) < 1e-7
+
+
+# -------------------------------------------------------------- Hartree ----
+def test_hartree_gaussian_charge_closed_form():
+    """Periodic Gaussian charges q (2 pi s^2)^{-3/2} exp(-r^2/2s^2) + background in a cube L.
+
+    rho(G) = (q/Omega) exp(-G^2 s^2/2), so E_H = (2 pi q^2/Omega) sum_{G!=0} exp(-G^2 s^2)/G^2.
+    That is the reciprocal Ewald term of a point charge with eta = 1/(2s); the Ewald identity
+    then gives the closed form
+      E_H = E_point + q^2/(2 s sqrt(pi)) + 2 pi q^2 s^2/Omega - (q^2/2) sum_{L!=0} erfc(L/2s)/L,
+    with E_point = -alpha_SC q^2/(2L) (Madelung constant of the simple-cubic lattice with
+    background).  As L -> inf this tends to the isolated self-energy q^2/(2 s sqrt(pi))."""
+    L, s, q = 9.0, 0.9, 1.3
+    cell = np.eye(3) * L
+    grid = (36, 36, 36)
+    st = workloads.Structure("g", cell, [dict(workloads.SPECIES_Z4)], np.zeros(1, np.int32),
+                             np.zeros((1, 3)), 2.0, 2, grid, 0.01)
+    m = dft.Model(st)
+    frac = np.stack(np.meshgrid(*[np.arange(n) / n for n in grid], indexing="ij"), -1)
+    rho = np.zeros(grid)
+    for i in range(-2, 3):
+        for j in range(-2, 3):
+            for k in range(-2, 3):
+                d = (frac + [i, j, k]) @ cell
+                rho += q * (2 * math.pi * s * s) ** -1.5 * np.exp(-np.sum(d * d, -1) / (2 * s * s))
+    e_h, _ = dft.hartree(m, rho)
+    lat = 0.0
+    for i in range(-4, 5):
+        for j in range(-4, 5):
+            for k in range(-4, 5):
+                if (i, j, k) != (0, 0, 0):
+                    r = L * math.sqrt(i * i + j * j + k * k)
+                    lat += erfc(r / (2 * s)) / r
+    closed = (-_madelung()["sc_background"] * q * q / (2 * L) + q * q / (2 * s * math.sqrt(math.pi))
+              + 2 * math.pi * q * q * s * s / L ** 3 - 0.5 * q * q * lat)
+    assert abs(e_h - closed) < 1e-6
+
+
+def test_hartree_potential_solves_poisson():
+    """-nabla^2 V_H = 4 pi (rho - <rho>) checked spectrally for a random band-limited rho."""
+    st = workloads.tiny(nat=1, ecut=3.0)
+    m = dft.Model(st)
+    rng = np.random.default_rng(5)
+    rho = rng.normal(size=m.grid)
+    e, vh = dft.hartree(m, rho)
+    lap = m.to_real(-m.bg2 * m.to_recip(vh)).real
+    rg = m.to_recip(rho) * m.sym
+    rg[0, 0, 0] = 0
+    assert np.allclose(-lap, 4 * math.pi * m.to_real(rg).real, atol=1e-10)
+    assert abs(e - 0.5 * m.omega / m.N * np.sum(rho * vh)) < 1e-9 * abs(e)
+
+
+# ------------------------------------------------------------------ LDA ----
+def test_slater_exchange_constant():
+    """eps_x = -(3/4)(9/(4 pi^2))^{1/3} / r_s = -0.4581652932831429 / r_s."""
+    for rs in (0.5, 1.0, 2.0, 5.0, 10.0):
+        rho = 3.0 / (4 * math.pi * rs ** 3)
+        ex, vx = lda.exchange(rho)
+        assert abs(ex * rs + 0.4581652932831429) < 1e-12
+        assert abs(vx - 4.0 / 3.0 * ex) < 1e-14
+
+
+def test_pz81_branches_are_continuous_at_rs1():
+    """Perdew-Zunger chose C, D so that eps_c and v_c join at r_s = 1; a wrong gamma/beta or
+    A..D constant (or sign) breaks the join."""
+    lo = lda.correlation(np.array([1.0 - 1e-12]))
+    hi = lda.correlation(np.array([1.0]))
+    assert abs(lo[0][0] - hi[0][0]) < 1e-4
+    assert abs(lo[1][0] - hi[1][0]) < 1e-4
+
+
+def test_pz81_high_density_log_coefficient_is_rpa():
+    """A = (1 - ln 2)/pi^2 = 0.031091 (Gell-Mann-Brueckner), quoted to 3 digits by PZ81."""
+    assert abs(lda.PZ_A - (1 - math.log(2)) / math.pi ** 2) < 1e-4
+
+
+@pytest.mark.parametrize("rs", [0.3, 0.8, 1.5, 4.0, 12.0])
+def test_vxc_is_derivative_of_rho_exc(rs):
+    rho = 3.0 / (4 * math.pi * rs ** 3)
+    h = rho * 1e-6
+    ep, _ = lda.lda(np.array([rho + h]))
+    em, _ = lda.lda(np.array([rho - h]))
+    _, v = lda.lda(np.array([rho]))
+    fd = ((rho + h) * ep[0] - (rho - h) * em[0]) / (2 * h)
+    assert abs(fd - v[0]) < 1e-7
+
+
+def test_lda_clip():
+    e, v = lda.lda(np.array([-1e-3, 0.0, 1e-31]))
+    assert np.all(e == 0) and np.all(v == 0)
+
+
+# ----------------------------------------------------------- occupations ----
+def test_fermi_dirac_counts_and_limits():
+    eps = np.array([-0.5, -0.2, -0.19, 0.1, 0.3, 0.31])
+    for kT in (0.001, 0.01, 0.05):
+        f, mu, S = dft.occupations(eps, 6.0, kT)
+        assert abs(f.sum() - 6.0) < 1e-12
+        assert np.all(np.diff(f) <= 0) and S >= 0
+        x = f / 2
+        assert np.allclose(x, 1 / (1 + np.exp((eps - mu) / kT)), atol=1e-14)
+    f0, _, S0 = dft.occupations(eps, 6.0, 0.0)
+    fs, _, Ss = dft.occupations(eps, 6.0, 1e-5)
+    assert np.allclose(f0, [2, 2, 2, 0, 0, 0]) and S0 == 0.0
+    assert np.allclose(fs, f0, atol=1e-12) and Ss < 1e-10
+    # two degenerate levels sharing one electron pair: x = 1/2, entropy 2 * 2 ln 2
+    f, mu, S = dft.occupations(np.array([-1.0, 0.0, 0.0, 1.0]), 4.0, 0.01)
+    assert abs(f[1] - 1.0) < 1e-10 and abs(S - 4 * math.log(2)) < 1e-8

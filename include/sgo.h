@@ -1,0 +1,170 @@
+/*
+ * sgo.h -- C ABI of the GB300 plane-wave DFT energy + force engine.
+ *
+ * The paper's bottom search level computes "the energy and atomic force of each
+ * structure ... self-consistently" with a plane-wave DFT code on GPUs (Sec. II A,
+ * Fig. 1 right module; Sec. II D).  Its inputs are the supercell, the atoms and
+ * the plane-wave cutoff; every differential-evolution candidate (Sec. II B) and
+ * every relaxation step (Sec. II C) calls it.  This library is that call.
+ *
+ * Physics (the paper names none; these are the fixed readings): Gamma point,
+ * norm-conserving synthetic analytic pseudopotential per species (local
+ * -Z erf(r/rc)/r + A exp(-r^2/sigma^2), one Kleinman-Bylander Gaussian s
+ * projector of strength D), LDA (Slater + Perdew-Zunger 1981), Ewald ions,
+ * Fermi-Dirac smearing with the Mermin free energy F = E - kT S reported.
+ * Units: Hartree atomic units (Ha, bohr).
+ *
+ * Conventions shared by every call:
+ *  - The caller owns every host array passed in or out; the library copies
+ *    inputs and never keeps a caller pointer after the call returns.
+ *  - The library owns its device memory (allocated at sgo_create, released at
+ *    sgo_destroy).  All device work is enqueued on the stream given to
+ *    sgo_create; calls that return host results synchronise that stream only.
+ *  - Errors are returned as sgo_status, never thrown; sgo_last_error() gives a
+ *    message for the calling thread.  The library never exits the process.
+ *  - A context is not thread-safe; different contexts may be used from
+ *    different threads.
+ *  - Grids exchanged with the caller are real arrays of shape (N1, N2, N3) in
+ *    C order (index (i1*N2 + i2)*N3 + i3 = point sum_i (i_i/N_i) a_i).
+ *  - Wave coefficients exchanged with the caller use the Gamma real packing of
+ *    the half sphere: x[0] = c(0), x[1+2k] = sqrt2 Re c(G_k), x[2+2k] =
+ *    sqrt2 Im c(G_k), for the half-sphere list G_k returned by sgo_get_basis
+ *    (c(-G) = c(G)^* is implied).  Then x.y = <psi_x|psi_y> and sum x^2 = 1.
+ */
+#ifndef SGO_H
+#define SGO_H
+
+#if defined(__GNUC__)
+#define SGO_API __attribute__((visibility("default")))
+#else
+#define SGO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgo_ctx sgo_ctx;     /* one structure: basis, tables, wavefunctions (opaque) */
+typedef struct sgo_batch sgo_batch; /* a population of contexts evaluated in lockstep (opaque) */
+
+typedef enum {
+  SGO_OK = 0,
+  SGO_ERR_ARG = 1,            /* invalid argument (sizes, pointers, band count, FFT size) */
+  SGO_ERR_GEOMETRY = 2,       /* atoms closer than 0.5 bohr (minimum image), or non-finite positions */
+  SGO_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  SGO_ERR_OOM = 4,            /* device allocation failed */
+  SGO_ERR_NOT_CONVERGED = 5,  /* SCF hit max_scf before the tolerances */
+  SGO_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+  SGO_ERR_NAN = 7             /* a non-finite energy or force appeared */
+} sgo_status;
+
+/* Per-species pseudopotential parameters (bohr, Ha). */
+typedef struct {
+  double z_val;     /* valence charge Z */
+  double rc;        /* erf width of the local Coulomb part */
+  double a_sr;      /* amplitude A of the short-range Gaussian */
+  double sigma_sr;  /* width sigma of the short-range Gaussian */
+  double rp;        /* projector Gaussian width */
+  double d_nl;      /* Kleinman-Bylander strength D */
+} sgo_species;
+
+typedef struct {
+  int precision;          /* 0 = plain FP64; 1 = mixed: FP32 FFT/H.psi/GEMM products, FP64 sums,
+                             FP64 Cholesky, Rayleigh-Ritz eigensolve, energies, forces, Ewald */
+  double kT;              /* Fermi-Dirac smearing, Ha; 0 = integer occupations (even N_el) */
+  double scf_tol_e;       /* stop when |F_k - F_{k-1}| < scf_tol_e (Ha) ... */
+  double scf_tol_rho;     /* ... and (Omega/N) sum |rho_out - rho_in| / N_el < scf_tol_rho */
+  int max_scf;            /* SCF iteration cap */
+  int pulay_hist;         /* Pulay (DIIS) history length, 1..8 */
+  double mix_alpha;       /* Pulay step on the (Kerker-damped) residual */
+  double kerker_q0;       /* Kerker q0 (1/bohr); 0 = no Kerker damping */
+  int ncg;                /* all-band CG steps (Algorithm 1 iterations) per SCF iteration */
+  int ncg_first;          /* CG steps in each initial non-self-consistent iteration */
+  int n_nonscf;           /* initial iterations at the fixed atomic-guess potential */
+  int fft[3];             /* FFT grid; 0 = smallest 2^a 3^b 5^c >= 4 m_max + 1 per axis */
+  unsigned long long seed;/* seed of the random initial wavefunctions */
+} sgo_opts;
+
+/* Fill *o with the defaults (FP64, kT 0, tolerances 1e-8 Ha / 1e-7, Pulay 8, ...). */
+SGO_API void sgo_opts_default(sgo_opts* o);
+
+/* Build a context for one structure (Sec. II D inputs: cell, species, positions, cutoff).
+ * cell: 9 doubles, rows are the lattice vectors a_i (bohr).  sp: nspecies entries.
+ * species_of_atom: natoms indices into sp.  pos: natoms*3 Cartesian bohr.
+ * ecut: |G|^2/2 <= ecut (Ha).  nbands >= N_el/2 (integer occupations) or > N_el/2 (kT > 0).
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * Allocates all device memory of the context; *out is NULL on error. */
+SGO_API sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms,
+                      const int* species_of_atom, const double* pos, double ecut, int nbands,
+                      const sgo_opts* o, void* cuda_stream, sgo_ctx** out);
+
+/* Run the SCF cycle of Sec. II D (rho_in -> Kohn-Sham solve by the all-band CG of
+ * Algorithm 1 -> rho_out -> Pulay mixing) at positions pos (NULL = keep the current
+ * ones).  Starts from the atomic-guess density and random wavefunctions unless
+ * sgo_set_warm(ctx, 1) was called.  Outputs (may be NULL): SCF iterations, final
+ * density residual.  Returns SGO_ERR_NOT_CONVERGED if max_scf was reached. */
+SGO_API sgo_status sgo_scf(sgo_ctx* ctx, const double* pos, int* n_iter_out, double* resid_out);
+
+/* One energy + force evaluation: sgo_scf at pos, then the Hellmann-Feynman forces
+ * -dF/dR (local, nonlocal, Ewald).  energy: the free energy F (Ha).  forces:
+ * natoms*3 (Ha/bohr).  Either output may be NULL. */
+SGO_API sgo_status sgo_energy_forces(sgo_ctx* ctx, const double* pos, double* energy, double* forces);
+
+/* A population of n contexts (same precision option) evaluated together: every
+ * kernel launch covers all members still iterating (Sec. II D: one relaxation per
+ * GPU becomes one population per GPU).  The contexts stay owned by the caller and
+ * must outlive the batch. */
+SGO_API sgo_status sgo_batch_create(int n, sgo_ctx* const* ctxs, sgo_batch** out);
+
+/* Evaluate every member.  pos[i] (host, natoms_i*3) or NULL = keep; energies[i];
+ * forces[i] (host, natoms_i*3, may be NULL); per_item[i] = status of member i.
+ * Returns SGO_OK when the call itself ran, even if some members failed. */
+SGO_API sgo_status sgo_energy_forces_batch(sgo_batch* b, const double* const* pos, double* energies,
+                                   double* const* forces, sgo_status* per_item);
+
+/* Same as sgo_energy_forces_batch with every array in DEVICE memory: pos_dev
+ * (sum natoms_i*3 doubles, members back to back), energies_dev (n), forces_dev
+ * (sum natoms_i*3), status_dev (n ints).  Synchronises the batch stream. */
+SGO_API sgo_status sgo_energy_forces_batch_device(sgo_batch* b, const double* pos_dev, double* energies_dev,
+                                          double* forces_dev, int* status_dev);
+
+/* Eigenvalues and occupations of the last SCF (nbands doubles each; either may be NULL). */
+SGO_API sgo_status sgo_get_eigen(sgo_ctx* ctx, double* eig, double* occ);
+
+/* Energy terms of the last SCF: kinetic, nonlocal, local, Hartree, xc, Ewald, -kT S, F. */
+SGO_API sgo_status sgo_get_terms(sgo_ctx* ctx, double terms[8]);
+
+/* Sizes: info[0] npw (real length of a band vector), [1] n_half (G != 0 half sphere),
+ * [2] column pairs, [3..5] N1 N2 N3, [6] nbands, [7] natoms, [8] scf iterations of the
+ * last SCF, [9] precision. */
+SGO_API sgo_status sgo_get_info(sgo_ctx* ctx, int info[10]);
+
+/* Miller indices of the packed basis: (1 + n_half) rows of 3 ints, row 0 = G = 0. */
+SGO_API sgo_status sgo_get_basis(sgo_ctx* ctx, int* miller);
+
+/* The last output density rho_out (N1*N2*N3 doubles, C order). */
+SGO_API sgo_status sgo_get_density(sgo_ctx* ctx, double* rho);
+
+/* H psi for nvec packed vectors (row-major nvec x npw doubles) with the local
+ * potential veff (N1*N2*N3 doubles, C order) and the projectors of the current
+ * positions: kinetic + local (FFT path) + nonlocal, in the context's precision.
+ * nvec <= nbands.  A component test of the H.psi kernels of Algorithm 1. */
+SGO_API sgo_status sgo_apply_hamiltonian(sgo_ctx* ctx, const double* veff, int nvec, const double* psi,
+                                 double* hpsi);
+
+/* rho(r) = sum_n occ_n |psi_n(r)|^2 for nvec packed vectors (the density kernels). */
+SGO_API sgo_status sgo_density(sgo_ctx* ctx, int nvec, const double* psi, const double* occ, double* rho);
+
+/* Warm start: when on (1), the next sgo_scf starts from the previous rho_in and
+ * wavefunctions instead of the atomic guess (relaxation steps, Sec. II C). */
+SGO_API sgo_status sgo_set_warm(sgo_ctx* ctx, int on);
+
+SGO_API void sgo_batch_destroy(sgo_batch* b);
+SGO_API void sgo_destroy(sgo_ctx* ctx);
+SGO_API const char* sgo_status_string(sgo_status s);
+SGO_API const char* sgo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGO_H */

@@ -1,0 +1,305 @@
+"""GB300 plane-wave DFT energy + force engine: Python binding of libsgo.so.
+
+The paper's bottom search level (Sec. II A, Sec. II D) evaluates the energy and
+atomic forces of a structure self-consistently; every differential-evolution
+candidate (Sec. II B) and relaxation step (Sec. II C) calls it.  All work runs
+in the CUDA kernels of libsgo.so behind the C ABI declared in include/sgo.h;
+this module only marshals arguments (ctypes).  There is no CPU fallback: if the
+library is missing the import of the binding fails.
+
+    ctx = Context(structure, precision="mixed")   # a workloads.Structure-like object
+    F, forces = ctx.energy_forces()
+    batch = Batch([ctx1, ctx2, ...]); E, Fs, st = batch.energy_forces()
+    E = SgoEnergy.apply(ctx, pos)                  # torch autograd, dE/dR = -forces
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgo.so")
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "invalid geometry", 3: "CUDA error", 4: "out of device memory",
+          5: "SCF not converged", 6: "device wait timed out", 7: "non-finite result"}
+SGO_OK, SGO_ERR_ARG, SGO_ERR_GEOMETRY, SGO_ERR_CUDA, SGO_ERR_OOM, SGO_ERR_NOT_CONVERGED, SGO_ERR_TIMEOUT, \
+    SGO_ERR_NAN = range(8)
+TERM_NAMES = ("kinetic", "nonlocal", "local", "hartree", "xc", "ewald", "minus_ts", "free_energy")
+
+
+class SgoError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class sgo_species(ctypes.Structure):
+    _fields_ = [("z_val", ctypes.c_double), ("rc", ctypes.c_double), ("a_sr", ctypes.c_double),
+                ("sigma_sr", ctypes.c_double), ("rp", ctypes.c_double), ("d_nl", ctypes.c_double)]
+
+
+class sgo_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("kT", ctypes.c_double), ("scf_tol_e", ctypes.c_double),
+                ("scf_tol_rho", ctypes.c_double), ("max_scf", ctypes.c_int), ("pulay_hist", ctypes.c_int),
+                ("mix_alpha", ctypes.c_double), ("kerker_q0", ctypes.c_double), ("ncg", ctypes.c_int),
+                ("ncg_first", ctypes.c_int), ("n_nonscf", ctypes.c_int), ("fft", ctypes.c_int * 3),
+                ("seed", ctypes.c_ulonglong)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+_SIGS = {
+    "sgo_opts_default": (None, [ctypes.POINTER(sgo_opts)]),
+    "sgo_create": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.POINTER(sgo_species), ctypes.c_int, _ip, _dp,
+                                  ctypes.c_double, ctypes.c_int, ctypes.POINTER(sgo_opts), _vp,
+                                  ctypes.POINTER(_vp)]),
+    "sgo_scf": (ctypes.c_int, [_vp, _dp, _ip, _dp]),
+    "sgo_energy_forces": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
+    "sgo_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "sgo_energy_forces_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_dp), _dp, ctypes.POINTER(_dp), _ip]),
+    "sgo_energy_forces_batch_device": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sgo_get_eigen": (ctypes.c_int, [_vp, _dp, _dp]),
+    "sgo_get_terms": (ctypes.c_int, [_vp, _dp]),
+    "sgo_get_info": (ctypes.c_int, [_vp, _ip]),
+    "sgo_get_basis": (ctypes.c_int, [_vp, _ip]),
+    "sgo_get_density": (ctypes.c_int, [_vp, _dp]),
+    "sgo_apply_hamiltonian": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
+    "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
+    "sgo_set_warm": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "sgo_batch_destroy": (None, [_vp]),
+    "sgo_destroy": (None, [_vp]),
+    "sgo_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "sgo_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libsgo.so (built by paper_1603_02732_gb300.build.build()); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1603_02732_gb300.build.build() "
+                          "(no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != SGO_OK:
+        detail = load_library().sgo_last_error()
+        raise SgoError(status, what, detail.decode() if detail else "")
+
+
+def _ptr(a: np.ndarray, ctype=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # torch is plumbing only
+        pass
+    return None
+
+
+def default_opts(**kw) -> sgo_opts:
+    lib = load_library()
+    o = sgo_opts()
+    lib.sgo_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision":
+            v = {"fp64": 0, "mixed": 1}.get(v, v) if isinstance(v, str) else int(v)
+        if k == "fft":
+            for i in range(3):
+                o.fft[i] = int(v[i])
+            continue
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """One structure on the GPU (sgo_create).  `st` has cell, species (list of dicts with
+    z_val, rc, a_sr, sigma_sr, rp, d_nl), species_of_atom, pos, ecut, nbands, fft, kT."""
+
+    def __init__(self, st, precision="fp64", stream=None, **opts):
+        self.lib = load_library()
+        self.st = st
+        kw = dict(kT=float(st.kT), fft=tuple(int(x) for x in st.fft), precision=precision)
+        kw.update(opts)
+        self.opts = default_opts(**kw)
+        cell = np.ascontiguousarray(st.cell, dtype=np.float64).reshape(9)
+        sp = (sgo_species * len(st.species))(*[sgo_species(*(float(s[k]) for k in
+                                                             ("z_val", "rc", "a_sr", "sigma_sr", "rp", "d_nl")))
+                                              for s in st.species])
+        spec = np.ascontiguousarray(st.species_of_atom, dtype=np.int32)
+        pos = np.ascontiguousarray(st.pos, dtype=np.float64).reshape(-1)
+        self.natoms = len(spec)
+        h = _vp()
+        s = stream if stream is not None else _current_stream()
+        _check(self.lib.sgo_create(_ptr(cell), len(st.species), sp, self.natoms, _ptr(spec, ctypes.c_int),
+                                   _ptr(pos), float(st.ecut), int(st.nbands), ctypes.byref(self.opts), s,
+                                   ctypes.byref(h)), "sgo_create")
+        self.h = h
+        self.nbands = int(st.nbands)
+        info = self.info()
+        self.npw, self.nhalf, self.grid = info["npw"], info["nhalf"], info["grid"]
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.sgo_destroy(h)
+            self.h = None
+
+    # --- evaluation -------------------------------------------------------
+    def energy_forces(self, pos=None, check=True):
+        F = ctypes.c_double()
+        f = np.zeros((self.natoms, 3))
+        p = None if pos is None else _ptr(np.ascontiguousarray(pos, dtype=np.float64).reshape(-1))
+        st = self.lib.sgo_energy_forces(self.h, p, ctypes.byref(F), _ptr(f))
+        if check:
+            _check(st, "sgo_energy_forces")
+        return F.value, f
+
+    def scf(self, pos=None, check=True):
+        it = ctypes.c_int()
+        res = ctypes.c_double()
+        p = None if pos is None else _ptr(np.ascontiguousarray(pos, dtype=np.float64).reshape(-1))
+        st = self.lib.sgo_scf(self.h, p, ctypes.byref(it), ctypes.byref(res))
+        if check:
+            _check(st, "sgo_scf")
+        return it.value, res.value
+
+    def set_warm(self, on=True):
+        _check(self.lib.sgo_set_warm(self.h, 1 if on else 0), "sgo_set_warm")
+
+    # --- inspection -------------------------------------------------------
+    def info(self):
+        a = np.zeros(10, np.int32)
+        _check(self.lib.sgo_get_info(self.h, _ptr(a, ctypes.c_int)), "sgo_get_info")
+        return dict(npw=int(a[0]), nhalf=int(a[1]), ncolpairs=int(a[2]), grid=(int(a[3]), int(a[4]), int(a[5])),
+                    nbands=int(a[6]), natoms=int(a[7]), n_iter=int(a[8]), precision=int(a[9]))
+
+    def eigen(self):
+        e = np.zeros(self.nbands)
+        o = np.zeros(self.nbands)
+        _check(self.lib.sgo_get_eigen(self.h, _ptr(e), _ptr(o)), "sgo_get_eigen")
+        return e, o
+
+    def terms(self):
+        t = np.zeros(8)
+        _check(self.lib.sgo_get_terms(self.h, _ptr(t)), "sgo_get_terms")
+        return dict(zip(TERM_NAMES, t.tolist()))
+
+    def basis(self):
+        m = np.zeros((1 + self.nhalf, 3), np.int32)
+        _check(self.lib.sgo_get_basis(self.h, _ptr(m, ctypes.c_int)), "sgo_get_basis")
+        return m
+
+    def density(self):
+        r = np.zeros(self.grid)
+        _check(self.lib.sgo_get_density(self.h, _ptr(r)), "sgo_get_density")
+        return r
+
+    # --- component calls --------------------------------------------------
+    def apply_hamiltonian(self, veff, psi):
+        veff = np.ascontiguousarray(veff, dtype=np.float64)
+        psi = np.ascontiguousarray(np.atleast_2d(psi), dtype=np.float64)
+        out = np.zeros_like(psi)
+        _check(self.lib.sgo_apply_hamiltonian(self.h, _ptr(veff), psi.shape[0], _ptr(psi), _ptr(out)),
+               "sgo_apply_hamiltonian")
+        return out
+
+    def density_of(self, psi, occ):
+        psi = np.ascontiguousarray(np.atleast_2d(psi), dtype=np.float64)
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        r = np.zeros(self.grid)
+        _check(self.lib.sgo_density(self.h, psi.shape[0], _ptr(psi), _ptr(occ), _ptr(r)), "sgo_density")
+        return r
+
+
+class Batch:
+    """A population evaluated in lockstep (sgo_batch_create / sgo_energy_forces_batch)."""
+
+    def __init__(self, ctxs: Sequence[Context]):
+        self.lib = load_library()
+        self.ctxs = list(ctxs)
+        arr = (_vp * len(self.ctxs))(*[c.h for c in self.ctxs])
+        h = _vp()
+        _check(self.lib.sgo_batch_create(len(self.ctxs), arr, ctypes.byref(h)), "sgo_batch_create")
+        self.h = h
+        self.offsets = np.cumsum([0] + [3 * c.natoms for c in self.ctxs])
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.sgo_batch_destroy(h)
+            self.h = None
+
+    def energy_forces(self, pos: Optional[List[np.ndarray]] = None):
+        n = len(self.ctxs)
+        E = np.zeros(n)
+        forces = [np.zeros((c.natoms, 3)) for c in self.ctxs]
+        st = np.zeros(n, np.int32)
+        fptr = (_dp * n)(*[_ptr(f) for f in forces])
+        if pos is not None:
+            keep = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1) for p in pos]
+            pptr = (_dp * n)(*[_ptr(p) for p in keep])
+        else:
+            pptr = None
+        _check(self.lib.sgo_energy_forces_batch(self.h, pptr, _ptr(E), fptr, _ptr(st, ctypes.c_int)),
+               "sgo_energy_forces_batch")
+        return E, forces, st
+
+    def energy_forces_device(self, pos_dev, energies_dev, forces_dev, status_dev):
+        """Device-pointer form: arguments are integer device addresses (e.g. tensor.data_ptr())."""
+        _check(self.lib.sgo_energy_forces_batch_device(self.h, _vp(pos_dev), _vp(energies_dev), _vp(forces_dev),
+                                                       _vp(status_dev)), "sgo_energy_forces_batch_device")
+
+
+def _make_autograd():
+    import torch
+
+    class SgoEnergy(torch.autograd.Function):
+        """E(R) with the hand-written Hellmann-Feynman adjoint as backward: dE/dR = -F.
+        Valid at self-consistency (no differentiation through the SCF loop)."""
+
+        @staticmethod
+        def forward(ctx, sgo_context, pos):
+            p = pos.detach().to("cpu", torch.float64).numpy()
+            E, F = sgo_context.energy_forces(p)
+            ctx.save_for_backward(torch.as_tensor(-F, dtype=pos.dtype, device=pos.device))
+            return torch.as_tensor(E, dtype=pos.dtype, device=pos.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            (dEdR,) = ctx.saved_tensors
+            return None, grad * dEdR
+
+    return SgoEnergy
+
+
+class _Lazy:
+    _cls = None
+
+    def __getattr__(self, k):
+        if _Lazy._cls is None:
+            _Lazy._cls = _make_autograd()
+        return getattr(_Lazy._cls, k)
+
+
+SgoEnergy = _Lazy()

@@ -1,0 +1,279 @@
+// extern "C" boundary of the engine (declarations and contracts in include/sgo.h).
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "engine.h"
+
+namespace sgo {
+const char* last_error();
+}
+
+struct sgo_batch {
+  std::vector<sgo_ctx*> ctxs;
+  std::unique_ptr<sgo::Engine> eng;
+};
+
+namespace {
+
+sgo::Engine* solo_engine(sgo_ctx* c) {
+  // A context's own engine (batch of one); rebuilt on every call (cheap: a few small maps).
+  return new sgo::Engine(std::vector<sgo_ctx*>{c}, c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void sgo_opts_default(sgo_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = 0;
+  o->kT = 0.0;
+  o->scf_tol_e = 1e-8;
+  o->scf_tol_rho = 1e-7;
+  o->max_scf = 100;
+  o->pulay_hist = 8;
+  o->mix_alpha = 0.5;
+  o->kerker_q0 = 0.8;
+  o->ncg = 3;
+  o->ncg_first = 6;
+  o->n_nonscf = 3;
+  o->seed = 12345ull;
+}
+
+sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,
+                      const double* pos, double ecut, int nbands, const sgo_opts* o, void* cuda_stream,
+                      sgo_ctx** out) {
+  if (!out) return SGO_ERR_ARG;
+  *out = nullptr;
+  if (!cell || !sp || !species_of_atom || !pos || nspecies < 1 || nspecies > sgo::MAX_SPECIES || natoms < 1 ||
+      !(ecut > 0.0) || nbands < 1) {
+    sgo::set_error("invalid argument");
+    return SGO_ERR_ARG;
+  }
+  sgo_ctx* c = new (std::nothrow) sgo_ctx();
+  if (!c) return SGO_ERR_OOM;
+  std::memcpy(c->cell, cell, sizeof(double) * 9);
+  c->species.assign(sp, sp + nspecies);
+  c->spec.assign(species_of_atom, species_of_atom + natoms);
+  c->pos.assign(pos, pos + 3 * natoms);
+  c->ecut = ecut;
+  c->nb = nbands;
+  if (o) c->opts = *o;
+  else sgo_opts_default(&c->opts);
+  c->precision = c->opts.precision ? 1 : 0;
+  c->tsize = c->precision ? sizeof(float) : sizeof(double);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  double nel = 0.0;
+  for (int a = 0; a < natoms; ++a) {
+    if (species_of_atom[a] < 0 || species_of_atom[a] >= nspecies) {
+      delete c;
+      sgo::set_error("species index out of range");
+      return SGO_ERR_ARG;
+    }
+    nel += sp[species_of_atom[a]].z_val;
+  }
+  const double need = c->opts.kT > 0.0 ? nel / 2.0 + 1.0 : nel / 2.0;
+  if (nbands < (int)std::ceil(need - 1e-9) || (c->opts.kT <= 0.0 && std::fabs(nel / 2.0 - std::round(nel / 2.0)) > 1e-9)) {
+    delete c;
+    sgo::set_error("too few bands for the electrons (or odd electron count with integer occupations)");
+    return SGO_ERR_ARG;
+  }
+  if (c->opts.max_scf < 1 || c->opts.pulay_hist < 1 || c->opts.ncg < 1) {
+    delete c;
+    sgo::set_error("invalid SCF options");
+    return SGO_ERR_ARG;
+  }
+  // geometry check through set_positions after set-up needs the device; check here first
+  sgo_status s = sgo::ctx_setup(c);
+  if (s == SGO_OK) s = sgo::set_positions(c, pos);
+  if (s == SGO_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) s = SGO_ERR_CUDA;
+  if (s != SGO_OK) {
+    delete c;
+    return s;
+  }
+  *out = c;
+  return SGO_OK;
+}
+
+sgo_status sgo_scf(sgo_ctx* c, const double* pos, int* n_iter_out, double* resid_out) {
+  if (!c) return SGO_ERR_ARG;
+  if (pos) {
+    sgo_status s = sgo::set_positions(c, pos);
+    if (s != SGO_OK) return s;
+  }
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  sgo_status s = e->run(false, nullptr);
+  if (n_iter_out) *n_iter_out = c->last_iter;
+  if (resid_out) *resid_out = c->last_resid;
+  return s;
+}
+
+sgo_status sgo_energy_forces(sgo_ctx* c, const double* pos, double* energy, double* forces) {
+  if (!c) return SGO_ERR_ARG;
+  if (pos) {
+    sgo_status s = sgo::set_positions(c, pos);
+    if (s != SGO_OK) return s;
+  }
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  sgo_status s = e->run(true, nullptr);
+  if (energy) *energy = c->h_scal[sgo::SC_FREE];
+  if (forces) std::memcpy(forces, c->h_forces.data(), sizeof(double) * c->h_forces.size());
+  return s;
+}
+
+sgo_status sgo_batch_create(int n, sgo_ctx* const* ctxs, sgo_batch** out) {
+  if (!out || n < 1 || !ctxs) return SGO_ERR_ARG;
+  *out = nullptr;
+  sgo_batch* b = new (std::nothrow) sgo_batch();
+  if (!b) return SGO_ERR_OOM;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) {
+      delete b;
+      return SGO_ERR_ARG;
+    }
+    b->ctxs.push_back(ctxs[i]);
+  }
+  b->eng.reset(new (std::nothrow) sgo::Engine(b->ctxs, b->ctxs[0]->stream));
+  if (!b->eng || !b->eng->ok()) {
+    delete b;
+    return SGO_ERR_CUDA;
+  }
+  *out = b;
+  return SGO_OK;
+}
+
+sgo_status sgo_energy_forces_batch(sgo_batch* b, const double* const* pos, double* energies, double* const* forces,
+                                   sgo_status* per_item) {
+  if (!b) return SGO_ERR_ARG;
+  const int n = (int)b->ctxs.size();
+  std::vector<sgo_status> st(n, SGO_OK);
+  if (pos) {
+    for (int i = 0; i < n; ++i) {
+      if (!pos[i]) continue;
+      sgo_status s = sgo::set_positions(b->ctxs[i], pos[i]);
+      if (s == SGO_ERR_CUDA) return s;
+      st[i] = s;
+    }
+  }
+  std::vector<sgo_status> run_st(n, SGO_OK);
+  sgo_status s = b->eng->run(true, &run_st);
+  if (s == SGO_ERR_CUDA) return s;
+  for (int i = 0; i < n; ++i) {
+    sgo_ctx* c = b->ctxs[i];
+    if (st[i] == SGO_OK) st[i] = run_st[i];
+    if (energies) energies[i] = c->h_scal[sgo::SC_FREE];
+    if (forces && forces[i]) std::memcpy(forces[i], c->h_forces.data(), sizeof(double) * c->h_forces.size());
+    if (per_item) per_item[i] = st[i];
+  }
+  return SGO_OK;
+}
+
+sgo_status sgo_energy_forces_batch_device(sgo_batch* b, const double* pos_dev, double* energies_dev,
+                                          double* forces_dev, int* status_dev) {
+  if (!b || !energies_dev || !forces_dev || !status_dev) return SGO_ERR_ARG;
+  return b->eng->run_device(pos_dev, energies_dev, forces_dev, status_dev);
+}
+
+sgo_status sgo_get_eigen(sgo_ctx* c, double* eig, double* occ) {
+  if (!c) return SGO_ERR_ARG;
+  if (eig) std::memcpy(eig, c->h_eps.data(), sizeof(double) * c->nb);
+  if (occ) std::memcpy(occ, c->h_occ.data(), sizeof(double) * c->nb);
+  return SGO_OK;
+}
+
+sgo_status sgo_get_terms(sgo_ctx* c, double terms[8]) {
+  if (!c || !terms) return SGO_ERR_ARG;
+  const double* s = c->h_scal.data();
+  terms[0] = s[sgo::SC_EKIN];
+  terms[1] = s[sgo::SC_ENL];
+  terms[2] = s[sgo::SC_ELOC];
+  terms[3] = s[sgo::SC_EH];
+  terms[4] = s[sgo::SC_EXC];
+  terms[5] = s[sgo::SC_EEW];
+  terms[6] = s[sgo::SC_MTS];
+  terms[7] = s[sgo::SC_FREE];
+  return SGO_OK;
+}
+
+sgo_status sgo_get_info(sgo_ctx* c, int info[10]) {
+  if (!c || !info) return SGO_ERR_ARG;
+  info[0] = c->d.npw;
+  info[1] = c->d.nhalf;
+  info[2] = c->d.ncp;
+  info[3] = c->d.n1;
+  info[4] = c->d.n2;
+  info[5] = c->d.n3;
+  info[6] = c->d.nb;
+  info[7] = c->d.natom;
+  info[8] = c->last_iter;
+  info[9] = c->precision;
+  return SGO_OK;
+}
+
+sgo_status sgo_get_basis(sgo_ctx* c, int* miller) {
+  if (!c || !miller) return SGO_ERR_ARG;
+  const int nh = c->d.nhalf;
+  std::vector<int> m(3 * (size_t)nh);
+  if (nh > 0 && cudaMemcpy(m.data(), c->d.ent_m, sizeof(int) * 3 * nh, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SGO_ERR_CUDA;
+  miller[0] = miller[1] = miller[2] = 0;
+  for (int e = 0; e < nh; ++e) {
+    miller[3 * (e + 1) + 0] = m[e];
+    miller[3 * (e + 1) + 1] = m[nh + e];
+    miller[3 * (e + 1) + 2] = m[2 * nh + e];
+  }
+  return SGO_OK;
+}
+
+sgo_status sgo_get_density(sgo_ctx* c, double* rho) {
+  if (!c || !rho) return SGO_ERR_ARG;
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  return e->export_density(rho);
+}
+
+sgo_status sgo_apply_hamiltonian(sgo_ctx* c, const double* veff, int nvec, const double* psi, double* hpsi) {
+  if (!c || !veff || !psi || !hpsi || nvec < 1 || nvec > c->nb) return SGO_ERR_ARG;
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  return e->apply_h(veff, nvec, psi, hpsi);
+}
+
+sgo_status sgo_density(sgo_ctx* c, int nvec, const double* psi, const double* occ, double* rho) {
+  if (!c || !psi || !occ || !rho || nvec < 1 || nvec > c->nb) return SGO_ERR_ARG;
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  return e->density(nvec, psi, occ, rho);
+}
+
+sgo_status sgo_set_warm(sgo_ctx* c, int on) {
+  if (!c) return SGO_ERR_ARG;
+  c->warm = on != 0;
+  return SGO_OK;
+}
+
+void sgo_batch_destroy(sgo_batch* b) { delete b; }
+void sgo_destroy(sgo_ctx* c) { delete c; }
+
+const char* sgo_status_string(sgo_status s) {
+  switch (s) {
+    case SGO_OK: return "ok";
+    case SGO_ERR_ARG: return "invalid argument";
+    case SGO_ERR_GEOMETRY: return "invalid geometry";
+    case SGO_ERR_CUDA: return "CUDA error";
+    case SGO_ERR_OOM: return "out of device memory";
+    case SGO_ERR_NOT_CONVERGED: return "SCF not converged";
+    case SGO_ERR_TIMEOUT: return "device wait timed out";
+    case SGO_ERR_NAN: return "non-finite result";
+  }
+  return "unknown status";
+}
+
+const char* sgo_last_error(void) { return sgo::last_error(); }
+
+}  // extern "C"

@@ -1,0 +1,842 @@
+// Host engine: context set-up and the lockstep SCF driver (Sec. II D).
+//
+// One SCF iteration, for every structure still iterating:
+//   V_eff[rho_in] -> H Psi -> subspace diagonalisation -> ncg all-band CG steps
+//   (Algorithm 1) -> occupations -> rho_out -> energy, convergence -> Pulay mix.
+// Every launch covers all active structures; a structure that has converged is masked.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "engine.h"
+
+namespace sgo {
+
+thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+const char* last_error() { return g_err.c_str(); }
+bool cuda_ok(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+#define CK(x)                                  \
+  do {                                         \
+    if (!cuda_ok((x), #x)) return SGO_ERR_CUDA; \
+  } while (0)
+
+namespace {
+
+// ---- small kernels of the driver ----
+__global__ void k_set_scal(KArgs ka, int idx, double v, int only_active) {
+  const int p = blockIdx.x;
+  if (only_active && !ka.active[p]) return;
+  if (threadIdx.x == 0) ka.probs[p].scal[idx] = v;
+}
+__global__ void k_reset(KArgs ka) {
+  const int p = blockIdx.x;
+  const Prob& P = ka.probs[p];
+  for (int i = threadIdx.x; i < NSCAL_ALL; i += blockDim.x) P.scal[i] = 0.0;
+  if (threadIdx.x < 4) P.status[threadIdx.x] = 0;
+  if (threadIdx.x == 0) P.scal[SC_FIRSTCG] = 1.0;
+}
+// flags[p] = {converged, cholesky failure, non-finite, resid}
+__global__ void k_gather_flags(KArgs ka, double* flags) {
+  const int p = blockIdx.x;
+  const Prob& P = ka.probs[p];
+  if (threadIdx.x == 0) {
+    flags[4 * p + 0] = P.scal[SC_CONV];
+    flags[4 * p + 1] = (double)P.status[0];
+    flags[4 * p + 2] = (double)P.status[1];
+    flags[4 * p + 3] = P.scal[SC_RESID];
+  }
+}
+// out[p] = F, out_f[off_p + e] = forces (device gather for the device-pointer batch)
+__global__ void k_gather_results(KArgs ka, const int* foff, double* energies, double* forces, int* status) {
+  const int p = blockIdx.x;
+  const Prob& P = ka.probs[p];
+  if (threadIdx.x == 0) {
+    energies[p] = P.scal[SC_FREE];
+    status[p] = P.status[0] ? SGO_ERR_NOT_CONVERGED : (P.scal[SC_CONV] != 0.0 ? SGO_OK : SGO_ERR_NOT_CONVERGED);
+  }
+  for (int e = threadIdx.x; e < 3 * P.natom; e += blockDim.x) forces[foff[p] + e] = P.forces[e];
+}
+__global__ void k_scatter_pos(KArgs ka, const int* foff, const double* pos) {
+  const int p = blockIdx.x;
+  const Prob& P = ka.probs[p];
+  for (int e = threadIdx.x; e < 3 * P.natom; e += blockDim.x) P.pos[e] = pos[foff[p] + e];
+}
+
+int div_up(long a, long b) { return (int)((a + b - 1) / b); }
+
+bool smooth235(int n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+// counting arena pass + real pass
+template <class A>
+void layout(sgo_ctx* c, A& a) {
+  Prob& d = c->d;
+  const size_t ts = c->tsize;
+  const int nb = d.nb, ld = d.ld, na = d.natom, ng = d.ngrid, n12 = d.n1 * d.n2, nt = d.n1 + d.n2 + d.n3;
+  d.cp_off = a.template take<int>(d.ncp + 1);
+  d.cp_m1 = a.template take<int>(d.ncp);
+  d.cp_m2 = a.template take<int>(d.ncp);
+  d.ent_m = a.template take<int>(3 * std::max(d.nhalf, 1));
+  d.ent_m3 = d.ent_m + 2 * d.nhalf;
+  d.ekin = a.template take<double>(ld);
+  d.gvec = a.template take<double>(3 * (size_t)ld);
+  d.colmap = a.template take<int>(n12);
+  d.col_xy = a.template take<int>(d.ncol);
+  d.roots64 = a.template take<double2>(nt);
+  d.roots32 = a.template take<float2>(nt);
+  d.pos = a.template take<double>(3 * na);
+  d.spec = a.template take<int>(na);
+  for (int i = 0; i < NWB; ++i) d.wb[i] = a.template take<char>((size_t)nb * ld * ts);
+  d.B = a.template take<char>((size_t)na * ld * ts);
+  d.dB = a.template take<char>((size_t)3 * na * ld * ts);
+  d.Wc = a.template take<char>((size_t)d.npair * d.n3 * d.ncol * 2 * ts);
+  d.veff = a.template take<char>((size_t)ng * ts);
+  d.vion_r = a.template take<double>(ng);
+  d.rho_in = a.template take<double>(ng);
+  d.rho_out = a.template take<double>(ng);
+  d.resid = a.template take<double>(ng);
+  d.vloc_g = a.template take<double>((size_t)d.nspecies * ng);
+  d.gfft = a.template take<double2>(ng);
+  d.gfft2 = a.template take<double2>(ng);
+  d.hrho = a.template take<double>((size_t)MAX_HIST * ng);
+  d.hres = a.template take<double>((size_t)MAX_HIST * ng);
+  d.phase = a.template take<double2>((size_t)na * nt);
+  d.S = a.template take<double>((size_t)nb * nb);
+  d.Hs = a.template take<double>((size_t)nb * nb);
+  d.Tm = a.template take<double>((size_t)nb * nb);
+  d.Cm = a.template take<double>((size_t)nb * nb);
+  d.proj = a.template take<double>((size_t)na * nb);
+  d.dproj = a.template take<double>((size_t)3 * na * nb);
+  d.eps = a.template take<double>(nb);
+  d.occ = a.template take<double>(nb);
+  d.bv = a.template take<double>((size_t)NBANDSCAL * nb);
+  d.scal = a.template take<double>(NSCAL_ALL);
+  d.forces = a.template take<double>(3 * na);
+  d.ewald_f = a.template take<double>(3 * na);
+  d.fpart = a.template take<double>((size_t)na * div_up(ng, GRID_CHUNK) * 3);
+  d.status = a.template take<int>(4);
+  d.ew_sg = a.template take<double2>(c->ngbox_ew);
+  d.ew_part = a.template take<double>(na + div_up(c->ngbox_ew, 256));
+}
+
+struct Counter {
+  size_t used = 0;
+  template <typename P>
+  P* take(size_t count, size_t align = 256) {
+    used = (used + align - 1) / align * align;
+    used += count * sizeof(P);
+    return nullptr;
+  }
+};
+
+sgo_status check_geometry(const sgo_ctx* c, const double* pos) {
+  const int n = (int)c->spec.size();
+  for (int i = 0; i < 3 * n; ++i)
+    if (!std::isfinite(pos[i])) {
+      set_error("non-finite atomic position");
+      return SGO_ERR_GEOMETRY;
+    }
+  // minimum-image distances via fractional coordinates
+  double inv[9];
+  const double* A = c->cell;
+  double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      double d[3], f[3];
+      for (int k = 0; k < 3; ++k) d[k] = pos[3 * i + k] - pos[3 * j + k];
+      for (int k = 0; k < 3; ++k) {
+        f[k] = d[0] * inv[k] + d[1] * inv[3 + k] + d[2] * inv[6 + k];
+        f[k] -= std::nearbyint(f[k]);
+      }
+      double best = 1e300;
+      for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b)
+          for (int e = -1; e <= 1; ++e) {
+            double v[3];
+            for (int k = 0; k < 3; ++k) v[k] = (f[0] + a) * A[k] + (f[1] + b) * A[3 + k] + (f[2] + e) * A[6 + k];
+            best = std::min(best, v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          }
+      if (best < 0.25) {
+        set_error("atoms closer than 0.5 bohr");
+        return SGO_ERR_GEOMETRY;
+      }
+    }
+  return SGO_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context set-up
+// ---------------------------------------------------------------------------
+sgo_status set_positions(sgo_ctx* c, const double* pos) {
+  sgo_status s = check_geometry(c, pos);
+  if (s != SGO_OK) return s;
+  std::copy(pos, pos + c->pos.size(), c->pos.begin());
+  CK(cudaMemcpyAsync(c->d.pos, c->pos.data(), c->pos.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  return SGO_OK;
+}
+
+sgo_status ctx_setup(sgo_ctx* c) {
+  Prob& d = c->d;
+  std::memset(&d, 0, sizeof(Prob));
+  const double* A = c->cell;
+  for (int i = 0; i < 9; ++i) d.cell[i] = A[i];
+  double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (!(std::fabs(det) > 1e-8)) {
+    set_error("singular cell");
+    return SGO_ERR_ARG;
+  }
+  d.omega = std::fabs(det);
+  // b_j = 2 pi (A^-1)^T rows: b_j[k] = 2 pi inv[k][j]
+  double inv[9];
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 3; ++k) d.bvec[3 * j + k] = 2.0 * PI * inv[3 * k + j];
+  d.ecut = c->ecut;
+  const double gmax = std::sqrt(2.0 * c->ecut);
+  int nd[3];
+  int box[3];
+  for (int i = 0; i < 3; ++i) {
+    double len = std::sqrt(A[3 * i] * A[3 * i] + A[3 * i + 1] * A[3 * i + 1] + A[3 * i + 2] * A[3 * i + 2]);
+    int mb = (int)std::floor(len * gmax / (2.0 * PI));
+    box[i] = mb + 1;
+    int n = c->opts.fft[i];
+    if (n <= 0) {
+      n = 4 * mb + 1;
+      while (!smooth235(n)) ++n;
+    }
+    if (!smooth235(n)) {
+      set_error("FFT size must have only the factors 2, 3, 5");
+      return SGO_ERR_ARG;
+    }
+    nd[i] = n;
+    if (!make_fft_dim(n, &d.fd[i])) return SGO_ERR_ARG;
+  }
+  d.n1 = nd[0];
+  d.n2 = nd[1];
+  d.n3 = nd[2];
+  d.ngrid = nd[0] * nd[1] * nd[2];
+  d.box1 = box[0];
+  d.box2 = box[1];
+  d.box3 = box[2];
+  if ((size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 > 220 * 1024 || d.n1 * d.n2 > DENS_MAXP * PLANE_THREADS_MAX) {
+    set_error("FFT plane N1*N2 too large for the shared-memory plane kernels (max about 6900)");
+    return SGO_ERR_ARG;
+  }
+  if ((size_t)(4 * QCP + 1) * d.n3 * 16 > 220 * 1024) {
+    set_error("N3 too large");
+    return SGO_ERR_ARG;
+  }
+  d.natom = (int)c->spec.size();
+  d.nspecies = (int)c->species.size();
+  for (int s = 0; s < d.nspecies; ++s) {
+    const sgo_species& q = c->species[s];
+    double v[6] = {q.z_val, q.rc, q.a_sr, q.sigma_sr, q.rp, q.d_nl};
+    for (int k = 0; k < 6; ++k) d.sp[6 * s + k] = v[k];
+  }
+  d.nel = 0.0;
+  for (int a = 0; a < d.natom; ++a) d.nel += c->species[c->spec[a]].z_val;
+  d.kT = c->opts.kT;
+  d.nb = c->nb;
+  d.npair = (c->nb + 1) / 2;
+  // Ewald parameters: eta from the volume; sums to a relative tail of 1e-16
+  d.ew_eta = 3.0 / std::cbrt(d.omega);
+  d.ew_rmax = 5.9 / d.ew_eta;
+  d.ew_gmax = 2.0 * d.ew_eta * std::sqrt(-std::log(1e-16));
+  for (int i = 0; i < 3; ++i) {
+    double len = std::sqrt(A[3 * i] * A[3 * i] + A[3 * i + 1] * A[3 * i + 1] + A[3 * i + 2] * A[3 * i + 2]);
+    double bl = std::sqrt(d.bvec[3 * i] * d.bvec[3 * i] + d.bvec[3 * i + 1] * d.bvec[3 * i + 1] +
+                          d.bvec[3 * i + 2] * d.bvec[3 * i + 2]);
+    d.ew_nr[i] = (int)std::ceil(d.ew_rmax * bl / (2.0 * PI)) + 1;
+    d.ew_ng[i] = (int)std::ceil(d.ew_gmax * len / (2.0 * PI)) + 1;
+  }
+  c->ngbox_ew = (2 * d.ew_ng[0] + 1) * (2 * d.ew_ng[1] + 1) * (2 * d.ew_ng[2] + 1);
+
+  // ---- phase 1: basis enumeration on the device ----
+  c->box_cols = (2 * box[0] + 1) * (2 * box[1] + 1);
+  const size_t setup_bytes = (size_t)4 * c->box_cols * sizeof(int) + 64 + 4 * 256;
+  CK(cudaMalloc(&c->arena_setup, setup_bytes));
+  {
+    Arena a;
+    a.base = c->arena_setup;
+    d.bx_cnt = a.take<int>(c->box_cols);
+    d.bx_m3max = a.take<int>(c->box_cols);
+    d.bx_pair = a.take<int>(c->box_cols);
+    d.bx_off = a.take<int>(c->box_cols);
+    d.setup_out = a.take<int>(8);
+  }
+  Prob* dprob = nullptr;
+  int* dstart = nullptr;
+  int* dact = nullptr;
+  CK(cudaMalloc(&dprob, sizeof(Prob)));
+  CK(cudaMalloc(&dstart, 2 * sizeof(int)));
+  CK(cudaMalloc(&dact, sizeof(int)));
+  const int one = 1;
+  const int nbc = div_up(c->box_cols, 128);
+  int st[2] = {0, nbc};
+  CK(cudaMemcpy(dstart, st, sizeof(st), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dact, &one, sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dprob, &d, sizeof(Prob), cudaMemcpyHostToDevice));
+  Launch L1;
+  L1.ka = KArgs{dprob, dstart, 1, dact};
+  L1.map.start = dstart;
+  L1.map.total = nbc;
+  L1.stream = c->stream;
+  launch_basis_count(L1);
+  launch_basis_scan(L1);
+  int out[8];
+  CK(cudaMemcpyAsync(out, d.setup_out, sizeof(out), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  d.nhalf = out[0];
+  d.ncp = out[1];
+  d.m1max = out[2];
+  d.m2max = out[3];
+  d.m3max = out[4];
+  d.npw = 1 + 2 * d.nhalf;
+  d.ld = (d.npw + 31) / 32 * 32;
+  d.ncol = 2 * d.ncp - 1;
+  if (4 * d.m1max + 1 > d.n1 || 4 * d.m2max + 1 > d.n2 || 4 * d.m3max + 1 > d.n3) {
+    cudaFree(dprob);
+    cudaFree(dstart);
+    cudaFree(dact);
+    set_error("FFT grid aliases: need N_i >= 4 m_max,i + 1");
+    return SGO_ERR_ARG;
+  }
+  if (c->nb > d.npw) {
+    cudaFree(dprob);
+    cudaFree(dstart);
+    cudaFree(dact);
+    set_error("more bands than plane waves");
+    return SGO_ERR_ARG;
+  }
+
+  // ---- phase 2: allocation ----
+  Counter cnt;
+  layout(c, cnt);
+  cudaError_t e = cudaMalloc(&c->arena_main, cnt.used + 256);
+  if (e != cudaSuccess) {
+    cudaFree(dprob);
+    cudaFree(dstart);
+    cudaFree(dact);
+    set_error(std::string("device allocation failed: ") + cudaGetErrorString(e));
+    return SGO_ERR_OOM;
+  }
+  {
+    Arena a;
+    a.base = c->arena_main;
+    layout(c, a);
+  }
+  CK(cudaMemsetAsync(c->arena_main, 0, cnt.used, c->stream));
+  CK(cudaMemsetAsync(d.colmap, 0xFF, sizeof(int) * d.n1 * d.n2, c->stream));
+  std::vector<int> spec(c->spec);
+  CK(cudaMemcpyAsync(d.spec, spec.data(), spec.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.pos, c->pos.data(), c->pos.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(dprob, &d, sizeof(Prob), cudaMemcpyHostToDevice, c->stream));
+  launch_basis_fill(L1);
+  launch_roots(L1);
+  const int nvl = div_up(d.ngrid, 1024);
+  st[1] = nvl;
+  CK(cudaMemcpyAsync(dstart, st, sizeof(st), cudaMemcpyHostToDevice, c->stream));
+  Launch L2 = L1;
+  L2.map.total = nvl;
+  launch_vloc_table(L2);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  cudaFree(dprob);
+  cudaFree(dstart);
+  cudaFree(dact);
+  c->h_scal.assign(NSCAL_ALL, 0.0);
+  c->h_eps.assign(c->nb, 0.0);
+  c->h_occ.assign(c->nb, 0.0);
+  c->h_forces.assign(3 * d.natom, 0.0);
+  return SGO_OK;
+}
+
+}  // namespace sgo
+
+sgo_ctx::~sgo_ctx() {
+  if (arena_setup) cudaFree(arena_setup);
+  if (arena_main) cudaFree(arena_main);
+}
+
+namespace sgo {
+
+// ---------------------------------------------------------------------------
+// Engine
+// ---------------------------------------------------------------------------
+WorkMap Engine::make_map(const std::vector<int>& counts) {
+  WorkMap m;
+  std::vector<int> st(counts.size() + 1, 0);
+  int mx = 0;
+  for (size_t i = 0; i < counts.size(); ++i) {
+    st[i + 1] = st[i] + counts[i];
+    mx = std::max(mx, counts[i]);
+  }
+  m.total = st.back();
+  m.maxper = mx;
+  int* d = nullptr;
+  if (!cuda_ok(cudaMalloc(&d, st.size() * sizeof(int)), "cudaMalloc(map)")) return m;
+  cudaMemcpy(d, st.data(), st.size() * sizeof(int), cudaMemcpyHostToDevice);
+  allocs_.push_back(d);
+  m.start = d;
+  return m;
+}
+
+Launch Engine::L(const WorkMap& m) const {
+  Launch l;
+  l.ka = KArgs{d_probs_, m.start ? m.start : m_prob_.start, n_, d_active_};
+  l.map = m;
+  l.stream = stream_;
+  l.max_n1 = max_n1_;
+  l.max_n2 = max_n2_;
+  l.max_n3 = max_n3_;
+  l.max_n12 = max_n12_;
+  l.max_nb = max_nb_;
+  l.plane_threads = plane_threads_;
+  return l;
+}
+
+Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ctxs), stream_(stream) {
+  n_ = (int)ctxs.size();
+  if (n_ == 0) return;
+  precision_ = ctxs[0]->precision;
+  for (auto* c : ctxs)
+    if (c->precision != precision_) {
+      set_error("all members of a batch must use the same precision");
+      return;
+    }
+  for (int i = 0; i < NWB; ++i) role_[i] = i;
+  std::vector<Prob> host(n_);
+  std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
+      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob;
+  size_t part = 0;
+  for (int p = 0; p < n_; ++p) {
+    const Prob& d = ctxs[p]->d;
+    host[p] = d;
+    max_n1_ = std::max(max_n1_, d.n1);
+    max_n2_ = std::max(max_n2_, d.n2);
+    max_n3_ = std::max(max_n3_, d.n3);
+    max_n12_ = std::max(max_n12_, d.n1 * d.n2);
+    max_nb_ = std::max(max_nb_, d.nb);
+    const int nch = div_up(d.ngrid, GRID_CHUNK);
+    maxchunk_ = std::max(maxchunk_, nch);
+    const int nsplit = div_up(d.npw, TN_KC);
+    const int tw = div_up(d.nb, TN_TILE), ta = div_up(d.natom, TN_TILE), td = div_up(3 * d.natom, TN_TILE);
+    c_zcol.push_back(d.npair * div_up(d.ncp, QCP));
+    c_plane.push_back(d.npair * d.n3);
+    c_dens.push_back(d.n3);
+    c_gz.push_back(div_up(d.n1 * d.n2, QZ));
+    c_gp.push_back(d.n3);
+    c_gew.push_back(div_up(d.ngrid, GRID_EW_POINTS));
+    c_gch.push_back(nch);
+    c_bands.push_back(d.nb);
+    c_tnww.push_back(tw * tw * nsplit);
+    c_tnbw.push_back(ta * tw * nsplit);
+    c_tndw.push_back(td * tw * nsplit);
+    c_rww.push_back(div_up(d.nb * d.nb, 256));
+    c_rbw.push_back(div_up(d.natom * d.nb, 256));
+    c_rdw.push_back(div_up(3 * d.natom * d.nb, 256));
+    c_nn.push_back(div_up(d.npw, NN_TILE) * div_up(d.nb, NN_TILE));
+    c_atoms.push_back(d.natom);
+    c_atomch.push_back(d.natom * nch);
+    c_ewsg.push_back(div_up(ctxs[p]->ngbox_ew, 256));
+    c_prob.push_back(1);
+    size_t need = (size_t)nsplit * std::max({d.nb * d.nb, d.natom * d.nb, 3 * d.natom * d.nb});
+    part = std::max(part, need);
+  }
+  plane_threads_ = std::min(PLANE_THREADS_MAX, std::max(128, (div_up(max_n12_, DENS_MAXP) + 31) / 32 * 32));
+  m_zcol_ = make_map(c_zcol);
+  m_plane_ = make_map(c_plane);
+  m_dens_ = make_map(c_dens);
+  m_gz_ = make_map(c_gz);
+  m_gp_ = make_map(c_gp);
+  m_gew_ = make_map(c_gew);
+  m_gch_ = make_map(c_gch);
+  m_bands_ = make_map(c_bands);
+  m_tn_ww_ = make_map(c_tnww);
+  m_tn_bw_ = make_map(c_tnbw);
+  m_tn_dw_ = make_map(c_tndw);
+  m_red_ww_ = make_map(c_rww);
+  m_red_bw_ = make_map(c_rbw);
+  m_red_dw_ = make_map(c_rdw);
+  m_nn_ = make_map(c_nn);
+  m_atoms_ = make_map(c_atoms);
+  m_atomch_ = make_map(c_atomch);
+  m_ewsg_ = make_map(c_ewsg);
+  m_prob_ = make_map(c_prob);
+  part_stride_ = part;
+  if (!cuda_ok(cudaMalloc(&d_probs_, sizeof(Prob) * n_), "cudaMalloc(probs)")) return;
+  allocs_.push_back(d_probs_);
+  cudaMemcpy(d_probs_, host.data(), sizeof(Prob) * n_, cudaMemcpyHostToDevice);
+  if (!cuda_ok(cudaMalloc(&d_active_, sizeof(int) * n_), "cudaMalloc(active)")) return;
+  allocs_.push_back(d_active_);
+  h_active_.assign(n_, 1);
+  cudaMemcpy(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice);
+  if (!cuda_ok(cudaMalloc(&d_part_, sizeof(double) * part_stride_ * n_), "cudaMalloc(part)")) return;
+  allocs_.push_back(d_part_);
+  if (!cuda_ok(cudaMalloc(&d_gpart_, sizeof(double) * (size_t)maxchunk_ * n_ * 8), "cudaMalloc(gpart)")) return;
+  allocs_.push_back(d_gpart_);
+  if (!cuda_ok(cudaMalloc(&d_flags_, sizeof(double) * 4 * n_), "cudaMalloc(flags)")) return;
+  allocs_.push_back(d_flags_);
+  h_flags_.assign(4 * n_, 0.0);
+  rr_smem_bytes_ = (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
+  rr_smem_ = rr_smem_bytes_ <= 200 * 1024;
+  if (!rr_smem_) {
+    rr_stride_ = (size_t)3 * max_nb_ * max_nb_;
+    if (!cuda_ok(cudaMalloc(&d_rr_, sizeof(double) * rr_stride_ * n_), "cudaMalloc(rr)")) return;
+    allocs_.push_back(d_rr_);
+  }
+  fft_set_smem_limits(220 * 1024);
+  linalg_set_smem_limits(220 * 1024);
+  ok_ = cuda_ok(cudaGetLastError(), "engine set-up");
+}
+
+Engine::~Engine() {
+  for (void* p : allocs_) cudaFree(p);
+}
+
+void Engine::set_scal(int idx, double v, bool only_active) {
+  k_set_scal<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, idx, v, only_active ? 1 : 0);
+}
+
+void Engine::grid_fft(int which, int sign) {
+  if (sign < 0) {
+    launch_grid_plane_fft(L(m_gp_), which, -1);
+    launch_grid_z_fft(L(m_gz_), which, -1);
+  } else {
+    launch_grid_z_fft(L(m_gz_), which, 1);
+    launch_grid_plane_fft(L(m_gp_), which, 1);
+  }
+}
+
+template <typename T>
+void Engine::tn(int akind, int arole, int bkind, int brole, int dst) {
+  const WorkMap* m = &m_tn_ww_;
+  const WorkMap* r = &m_red_ww_;
+  if (akind == OPK_B) { m = &m_tn_bw_; r = &m_red_bw_; }
+  if (akind == OPK_DB) { m = &m_tn_dw_; r = &m_red_dw_; }
+  const int ap = akind == OPK_WB ? role_[arole] : 0;
+  const int bp = bkind == OPK_WB ? role_[brole] : 0;
+  launch_gemm_tn<T>(L(*m), akind, ap, bkind, bp, d_part_, part_stride_);
+  launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_);
+}
+
+template <typename T>
+void Engine::nn(int akind, int arole, int msel, int yrole, double alpha, double beta) {
+  const int ap = akind == OPK_WB ? role_[arole] : 0;
+  launch_gemm_nn<T>(L(m_nn_), akind, ap, msel, role_[yrole], alpha, beta);
+}
+
+template <typename T>
+void Engine::rotate(int role) {
+  nn<T>(OPK_WB, role, DD_TM, WB_W, 1.0, 0.0);
+  std::swap(role_[role], role_[WB_W]);
+}
+
+// H applied to every band of src: FFT local + kinetic, then nonlocal B (D o B^T src).
+template <typename T>
+void Engine::hpsi(int src, int dst) {
+  launch_wave_to_cols<T>(L(m_zcol_), role_[src]);
+  launch_plane_vpsi<T>(L(m_plane_));
+  launch_cols_to_wave<T>(L(m_zcol_), role_[src], role_[dst]);
+  tn<T>(OPK_B, 0, OPK_WB, src, DD_PROJ);
+  nn<T>(OPK_B, 0, DD_PROJ_D, dst, 1.0, 1.0);
+}
+
+// Overlap + subspace matrix, FP64 Cholesky/eigensolve, rotation of the block.
+template <typename T>
+void Engine::rayleigh_ritz(bool rotate_history) {
+  tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S);
+  tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
+  launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_);
+  rotate<T>(WB_X);
+  rotate<T>(WB_HX);
+  if (rotate_history) {
+    rotate<T>(WB_PP);
+    rotate<T>(WB_RP);
+  }
+}
+
+// One all-band CG step (Algorithm 1, lines 6-16).
+template <typename T>
+void Engine::cg_step() {
+  launch_cg_precond<T>(L(m_bands_), role_[WB_X], role_[WB_HX], role_[WB_P], role_[WB_W2], role_[WB_PP], role_[WB_RP]);
+  tn<T>(OPK_WB, WB_X, OPK_WB, WB_P, DD_CM);        // C = Psi^T P
+  nn<T>(OPK_WB, WB_X, DD_CM, WB_P, -1.0, 1.0);     // P -= Psi C     (line 12)
+  launch_normalize<T>(L(m_bands_), role_[WB_P], role_[WB_PP]);
+  hpsi<T>(WB_P, WB_HP);
+  launch_line_min<T>(L(m_bands_), role_[WB_X], role_[WB_HX], role_[WB_P], role_[WB_HP]);  // line 13
+  std::swap(role_[WB_RP], role_[WB_W2]);
+  rayleigh_ritz<T>(true);                          // lines 14-16
+  launch_finish_cg(L(m_prob_));
+}
+
+void Engine::sync_active() {
+  k_gather_flags<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, d_flags_);
+  cudaMemcpyAsync(h_flags_.data(), d_flags_, sizeof(double) * 4 * n_, cudaMemcpyDeviceToHost, stream_);
+  cudaStreamSynchronize(stream_);
+  for (int p = 0; p < n_; ++p) {
+    if (!h_active_[p]) continue;
+    if (h_flags_[4 * p] != 0.0 || h_flags_[4 * p + 1] != 0.0 || h_flags_[4 * p + 2] != 0.0) h_active_[p] = 0;
+  }
+  cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_);
+}
+
+sgo_status Engine::structure_terms() {
+  const Launch la = L(m_atoms_);
+  launch_phases(la);
+  launch_vion_g(L(m_gew_));
+  grid_fft(0, 1);
+  launch_grid_real_part(L(m_gew_), 0, 3);
+  if (precision_) launch_build_projectors<float>(la, 0);
+  else launch_build_projectors<double>(la, 0);
+  launch_ewald(L(m_ewsg_), la, L(m_prob_));
+  return cuda_ok(cudaGetLastError(), "structure terms") ? SGO_OK : SGO_ERR_CUDA;
+}
+
+template <typename T>
+sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
+  const sgo_opts& o = ctx_[0]->opts;
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  bool warm = true;
+  for (auto* c : ctx_) warm = warm && c->warm && c->have_state;
+  k_reset<<<n_, 128, 0, stream_>>>(L(m_prob_).ka);
+  sgo_status s = structure_terms();
+  if (s != SGO_OK) return s;
+  if (!warm) {
+    launch_rho0_g(L(m_gew_));
+    grid_fft(0, 1);
+    launch_grid_real_part(L(m_gew_), 0, 0);
+    launch_random_init<T>(L(m_bands_), role_[WB_X], o.seed);
+  }
+  const int nonsc = warm ? 0 : std::max(0, o.n_nonscf);
+  const int hist = std::min(std::max(o.pulay_hist, 1), MAX_HIST);
+  int it = 0;
+  for (it = 1; it <= o.max_scf; ++it) {
+    // V_eff from rho_in (Hartree in G space, LDA in real space)
+    launch_real_to_grid(L(m_gew_), 0, 0);
+    grid_fft(0, -1);
+    launch_hartree_g(L(m_gew_), 0);
+    grid_fft(0, 1);
+    launch_veff<T>(L(m_gew_), nullptr);
+    // H Psi and the subspace diagonalisation (Algorithm 1, lines 2-3)
+    hpsi<T>(WB_X, WB_HX);
+    rayleigh_ritz<T>(false);
+    set_scal(SC_FIRSTCG, 1.0, true);
+    const int ncg = it <= nonsc ? o.ncg_first : o.ncg;
+    for (int k = 0; k < ncg; ++k) cg_step<T>();
+    // occupations and rho_out
+    launch_occupations(L(m_prob_));
+    launch_wave_to_cols<T>(L(m_zcol_), role_[WB_X]);
+    launch_plane_density<T>(L(m_dens_), nullptr);
+    // energy at (Psi, rho_out) and the convergence test
+    launch_band_kinetic<T>(L(m_bands_), role_[WB_X]);
+    tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ);
+    launch_real_to_grid(L(m_gew_), 1, 0);
+    grid_fft(0, -1);
+    launch_grid_energies(L(m_gch_), d_gpart_, maxchunk_);
+    launch_grid_energies_reduce(L(m_prob_), d_gpart_, maxchunk_);
+    launch_finish_iteration(L(m_prob_), o.scf_tol_e, o.scf_tol_rho, it > nonsc ? 1 : 0);
+    CK(cudaGetLastError());
+    sync_active();
+    int nact = 0;
+    for (int p = 0; p < n_; ++p) nact += h_active_[p];
+    if (nact == 0) break;
+    if (it > nonsc) {
+      // Pulay mixing of rho_out with rho_in
+      launch_pulay_store(L(m_gew_));
+      launch_pulay_gram(L(m_gch_), d_gpart_, maxchunk_, hist);
+      launch_pulay_solve(L(m_prob_), d_gpart_, maxchunk_, hist);
+      launch_pulay_mix(L(m_gew_), 0, 0.0);
+      if (o.kerker_q0 > 0.0) {
+        launch_real_to_grid(L(m_gew_), 2, 0);
+        grid_fft(0, -1);
+        launch_kerker(L(m_gew_), o.kerker_q0);
+        grid_fft(0, 1);
+        launch_grid_real_part(L(m_gew_), 0, 2);
+      }
+      launch_pulay_mix(L(m_gew_), 1, o.mix_alpha);
+    }
+  }
+  const int niter = std::min(it, o.max_scf);
+  // forces on every member
+  std::vector<int> was(h_active_);
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  if (want_forces) {
+    launch_build_projectors<T>(L(m_atoms_), 1);
+    tn<T>(OPK_DB, 0, OPK_WB, WB_X, DD_DPROJ);
+    tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ);
+    launch_real_to_grid(L(m_gew_), 1, 0);
+    grid_fft(0, -1);
+    launch_local_forces(L(m_atomch_), maxchunk_);
+    launch_force_total(L(m_prob_), maxchunk_);
+  }
+  // X back to physical buffer 0 so that the next run (warm or component call) finds it there
+  if (role_[WB_X] != 0) {
+    for (auto* c : ctx_)
+      CK(cudaMemcpyAsync(c->d.wb[0], c->d.wb[role_[WB_X]], (size_t)c->d.nb * c->d.ld * c->tsize,
+                         cudaMemcpyDeviceToDevice, stream_));
+  }
+  for (int i = 0; i < NWB; ++i) role_[i] = i;
+  for (auto* c : ctx_) {
+    CK(cudaMemcpyAsync(c->h_scal.data(), c->d.scal, sizeof(double) * NSCAL_ALL, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(c->h_eps.data(), c->d.eps, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(c->h_occ.data(), c->d.occ, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(c->h_forces.data(), c->d.forces, sizeof(double) * c->h_forces.size(), cudaMemcpyDeviceToHost,
+                       stream_));
+  }
+  CK(cudaStreamSynchronize(stream_));
+  CK(cudaGetLastError());
+  sgo_status all = SGO_OK;
+  for (int p = 0; p < n_; ++p) {
+    sgo_ctx* c = ctx_[p];
+    c->have_state = true;
+    c->last_iter = niter;
+    c->last_resid = c->h_scal[SC_RESID];
+    sgo_status st = SGO_OK;
+    if (h_flags_[4 * p + 1] != 0.0) st = SGO_ERR_NOT_CONVERGED;
+    else if (h_flags_[4 * p + 2] != 0.0 || !std::isfinite(c->h_scal[SC_FREE])) st = SGO_ERR_NAN;
+    else if (c->h_scal[SC_CONV] == 0.0) st = SGO_ERR_NOT_CONVERGED;
+    if (want_forces)
+      for (double f : c->h_forces)
+        if (!std::isfinite(f)) st = SGO_ERR_NAN;
+    c->last_status = st;
+    if (per_item) (*per_item)[p] = st;
+    if (st != SGO_OK && all == SGO_OK) all = st;
+  }
+  (void)was;
+  return all;
+}
+
+sgo_status Engine::run(bool want_forces, std::vector<sgo_status>* per_item) {
+  if (!ok_) return SGO_ERR_CUDA;
+  return precision_ ? run_t<float>(want_forces, per_item) : run_t<double>(want_forces, per_item);
+}
+
+// ---- component entry points (problem 0) ----
+sgo_status Engine::apply_h(const double* veff_c, int nvec, const double* psi, double* hpsi_out) {
+  sgo_ctx* c = ctx_[0];
+  const Prob& d = c->d;
+  double *dv = nullptr, *dpsi = nullptr, *dout = nullptr;
+  CK(cudaMalloc(&dv, sizeof(double) * d.ngrid));
+  CK(cudaMalloc(&dpsi, sizeof(double) * (size_t)nvec * d.npw));
+  CK(cudaMalloc(&dout, sizeof(double) * (size_t)nvec * d.npw));
+  CK(cudaMemcpyAsync(dv, veff_c, sizeof(double) * d.ngrid, cudaMemcpyHostToDevice, stream_));
+  CK(cudaMemcpyAsync(dpsi, psi, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyHostToDevice, stream_));
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  for (int i = 0; i < NWB; ++i) role_[i] = i;
+  if (structure_terms() != SGO_OK) return SGO_ERR_CUDA;
+  if (precision_) {
+    launch_veff<float>(L(m_gew_), dv);
+    launch_copy_in<float>(L(m_bands_), WB_W, dpsi, nvec);
+    hpsi<float>(WB_W, WB_W2);
+    launch_copy_out<float>(L(m_bands_), WB_W2, dout, nvec);
+  } else {
+    launch_veff<double>(L(m_gew_), dv);
+    launch_copy_in<double>(L(m_bands_), WB_W, dpsi, nvec);
+    hpsi<double>(WB_W, WB_W2);
+    launch_copy_out<double>(L(m_bands_), WB_W2, dout, nvec);
+  }
+  CK(cudaMemcpyAsync(hpsi_out, dout, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyDeviceToHost, stream_));
+  CK(cudaStreamSynchronize(stream_));
+  CK(cudaGetLastError());
+  cudaFree(dv);
+  cudaFree(dpsi);
+  cudaFree(dout);
+  return SGO_OK;
+}
+
+sgo_status Engine::density(int nvec, const double* psi, const double* occ, double* rho) {
+  sgo_ctx* c = ctx_[0];
+  const Prob& d = c->d;
+  double *dpsi = nullptr, *docc = nullptr, *dr = nullptr;
+  CK(cudaMalloc(&dpsi, sizeof(double) * (size_t)nvec * d.npw));
+  CK(cudaMalloc(&docc, sizeof(double) * d.nb));
+  CK(cudaMalloc(&dr, sizeof(double) * d.ngrid));
+  std::vector<double> o(d.nb, 0.0);
+  for (int i = 0; i < nvec; ++i) o[i] = occ[i];
+  CK(cudaMemcpyAsync(dpsi, psi, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyHostToDevice, stream_));
+  CK(cudaMemcpyAsync(docc, o.data(), sizeof(double) * d.nb, cudaMemcpyHostToDevice, stream_));
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  for (int i = 0; i < NWB; ++i) role_[i] = i;
+  if (precision_) {
+    launch_copy_in<float>(L(m_bands_), WB_W, dpsi, nvec);
+    launch_wave_to_cols<float>(L(m_zcol_), WB_W);
+    launch_plane_density<float>(L(m_dens_), docc);
+  } else {
+    launch_copy_in<double>(L(m_bands_), WB_W, dpsi, nvec);
+    launch_wave_to_cols<double>(L(m_zcol_), WB_W);
+    launch_plane_density<double>(L(m_dens_), docc);
+  }
+  launch_export_grid(L(m_gew_), 1, dr);
+  CK(cudaMemcpyAsync(rho, dr, sizeof(double) * d.ngrid, cudaMemcpyDeviceToHost, stream_));
+  CK(cudaStreamSynchronize(stream_));
+  CK(cudaGetLastError());
+  cudaFree(dpsi);
+  cudaFree(docc);
+  cudaFree(dr);
+  return SGO_OK;
+}
+
+sgo_status Engine::export_density(double* rho) {
+  const Prob& d = ctx_[0]->d;
+  double* dr = nullptr;
+  CK(cudaMalloc(&dr, sizeof(double) * d.ngrid));
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  launch_export_grid(L(m_gew_), 1, dr);
+  CK(cudaMemcpyAsync(rho, dr, sizeof(double) * d.ngrid, cudaMemcpyDeviceToHost, stream_));
+  CK(cudaStreamSynchronize(stream_));
+  cudaFree(dr);
+  return SGO_OK;
+}
+
+sgo_status Engine::run_device(const double* pos, double* energies, double* forces, int* status) {
+  std::vector<int> off(n_ + 1, 0);
+  for (int p = 0; p < n_; ++p) off[p + 1] = off[p] + 3 * ctx_[p]->d.natom;
+  int* doff = nullptr;
+  CK(cudaMalloc(&doff, sizeof(int) * (n_ + 1)));
+  CK(cudaMemcpyAsync(doff, off.data(), sizeof(int) * (n_ + 1), cudaMemcpyHostToDevice, stream_));
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  if (pos) k_scatter_pos<<<n_, 128, 0, stream_>>>(L(m_prob_).ka, doff, pos);
+  sgo_status s = run(true, nullptr);
+  k_gather_results<<<n_, 128, 0, stream_>>>(L(m_prob_).ka, doff, energies, forces, status);
+  CK(cudaStreamSynchronize(stream_));
+  cudaFree(doff);
+  return s == SGO_ERR_CUDA ? s : SGO_OK;
+}
+
+}  // namespace sgo

@@ -1,0 +1,121 @@
+// Host-side engine: one context per structure, and a lockstep batch driver whose every
+// kernel launch covers all structures still iterating.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sgo.h"
+#include "kernels.h"
+
+namespace sgo {
+
+struct Arena {
+  char* base = nullptr;
+  size_t used = 0, cap = 0;
+  template <typename P>
+  P* take(size_t count, size_t align = 256) {
+    used = (used + align - 1) / align * align;
+    P* p = reinterpret_cast<P*>(base + used);
+    used += count * sizeof(P);
+    return p;
+  }
+};
+
+}  // namespace sgo
+
+// One structure.  Owns all of its device memory.
+struct sgo_ctx {
+  // inputs
+  double cell[9];
+  std::vector<sgo_species> species;
+  std::vector<int> spec;
+  std::vector<double> pos;
+  double ecut = 0.0;
+  int nb = 0;
+  sgo_opts opts;
+  cudaStream_t stream = nullptr;
+  int precision = 0;  // 0 FP64, 1 mixed (FP32 wave data)
+  // derived
+  sgo::Prob d;        // descriptor (host copy, device pointers)
+  int box_cols = 0;
+  int ngbox_ew = 0;
+  size_t tsize = 8;
+  char* arena_setup = nullptr;
+  char* arena_main = nullptr;
+  bool warm = false;
+  bool have_state = false;
+  int last_iter = 0;
+  double last_resid = 0.0;
+  sgo_status last_status = SGO_OK;
+  std::vector<double> h_scal, h_eps, h_occ, h_forces;
+  ~sgo_ctx();
+};
+
+namespace sgo {
+
+// Lockstep driver over n contexts of the same precision.
+class Engine {
+ public:
+  Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream);
+  ~Engine();
+  bool ok() const { return ok_; }
+  // Full evaluation: structure terms, SCF, optional forces.  per_item receives statuses.
+  sgo_status run(bool want_forces, std::vector<sgo_status>* per_item);
+  // Component calls on problem 0.
+  sgo_status apply_h(const double* veff_c, int nvec, const double* psi, double* hpsi);
+  sgo_status density(int nvec, const double* psi, const double* occ, double* rho);
+  sgo_status export_density(double* rho);
+  sgo_status structure_terms();
+  // Batch evaluation with positions, energies, forces and statuses in device memory.
+  sgo_status run_device(const double* pos, double* energies, double* forces, int* status);
+
+ private:
+  template <typename T> sgo_status run_t(bool want_forces, std::vector<sgo_status>* per_item);
+  template <typename T> void hpsi(int src, int dst);
+  template <typename T> void rayleigh_ritz(bool rotate_history);
+  template <typename T> void cg_step();
+  template <typename T> void tn(int akind, int arole, int bkind, int brole, int dst);
+  template <typename T> void nn(int akind, int arole, int msel, int yrole, double alpha, double beta);
+  template <typename T> void rotate(int role);
+  void grid_fft(int which, int sign);
+  void potential();
+  void energies_at_rho_out(bool count_iter);
+  void pulay();
+  void sync_active();
+  void set_scal(int idx, double v, bool only_active);
+  Launch L(const WorkMap& m) const;
+  WorkMap make_map(const std::vector<int>& counts);
+
+  std::vector<sgo_ctx*> ctx_;
+  int n_ = 0;
+  cudaStream_t stream_;
+  int precision_ = 0;
+  bool ok_ = false;
+  Prob* d_probs_ = nullptr;
+  int* d_active_ = nullptr;
+  std::vector<int> h_active_;
+  std::vector<void*> allocs_;
+  int role_[NWB];
+  int max_n1_ = 0, max_n2_ = 0, max_n3_ = 0, max_n12_ = 0, max_nb_ = 0, plane_threads_ = 128;
+  WorkMap m_zcol_, m_plane_, m_dens_, m_gz_, m_gp_, m_gew_, m_gch_, m_bands_, m_tn_ww_, m_tn_bw_, m_tn_dw_,
+      m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_atomch_, m_ewsg_, m_prob_;
+  double* d_part_ = nullptr;
+  size_t part_stride_ = 0;
+  double* d_gpart_ = nullptr;
+  int maxchunk_ = 1;
+  double* d_rr_ = nullptr;
+  size_t rr_stride_ = 0;
+  bool rr_smem_ = true;
+  size_t rr_smem_bytes_ = 0;
+  double* d_flags_ = nullptr;   // [n][4] gathered per iteration
+  std::vector<double> h_flags_;
+};
+
+// Context set-up (basis on the device, allocation, tables).  Returns status.
+sgo_status ctx_setup(sgo_ctx* c);
+sgo_status set_positions(sgo_ctx* c, const double* pos);
+
+}  // namespace sgo

@@ -1,0 +1,392 @@
+// FFT kernels of the all-band H.psi apply and of the density (Algorithm 1 lines 2
+// and 15: "Calculate / Update H|Psi_i>"; Sec. II D: rho_out from the occupied states).
+//
+// A band pair (a, b) shares one complex transform: psi_a + i psi_b is real-space
+// complex, both bands being real at the Gamma point.  The inverse transform runs
+//   sphere -> compact z-columns (z FFT) -> per z-plane: y FFT on the occupied x rows,
+//   x FFT on all columns, times V_eff(r)/N, x FFT back, y FFT back -> z-columns ->
+//   z FFT back -> sphere, where (V psi_a)(G) = (F(G) + F(-G)^*)/2 and
+//   (V psi_b)(G) = (F(G) - F(-G)^*)/(2i).
+// The grid kernels at the end transform full FP64 complex grids (densities,
+// potentials) with the same line engine.
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace sgo {
+
+namespace {
+
+template <typename T>
+struct RootsOf;
+template <>
+struct RootsOf<float> {
+  static __device__ __forceinline__ const cplx<float>* get(const Prob& P) {
+    return reinterpret_cast<const cplx<float>*>(P.roots32);
+  }
+};
+template <>
+struct RootsOf<double> {
+  static __device__ __forceinline__ const cplx<double>* get(const Prob& P) {
+    return reinterpret_cast<const cplx<double>*>(P.roots64);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void load_roots(cplx<T>* dst, const Prob& P, int off, int n) {
+  const cplx<T>* src = RootsOf<T>::get(P) + off;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
+}
+
+__device__ __forceinline__ int wrapi(int m, int n) {
+  int r = m % n;
+  return r < 0 ? r + n : r;
+}
+
+// Column-pair chunk [cp0, cp1) -> compact columns [col0, col1).
+__device__ __forceinline__ void chunk_cols(int cp0, int cp1, int* col0, int* col1) {
+  *col0 = cp0 == 0 ? 0 : 2 * cp0 - 1;
+  *col1 = 2 * cp1 - 1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// sphere -> compact z-columns (inverse z FFT).  CTA = (problem, band pair, chunk).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(ZCOL_THREADS) k_wave_to_cols(KArgs ka, int src) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int local = blockIdx.x - ka.start[p];
+  const int nchunk = (P.ncp + QCP - 1) / QCP;
+  const int pair = local / nchunk;
+  const int chunk = local - pair * nchunk;
+  const int n3 = P.n3;
+  const int cp0 = chunk * QCP, cp1 = min(cp0 + QCP, P.ncp);
+  int col0, col1;
+  chunk_cols(cp0, cp1, &col0, &col1);
+  const int ncl = col1 - col0;
+  cplx<T>* lines = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* alt = lines + 2 * QCP * n3;
+  cplx<T>* roots = alt + 2 * QCP * n3;
+  load_roots<T>(roots, P, P.n1 + P.n2, n3);
+  for (int t = threadIdx.x; t < ncl * n3; t += blockDim.x) lines[t] = mk(T(0), T(0));
+  __syncthreads();
+
+  const int ia = 2 * pair, ib = 2 * pair + 1;
+  const bool hasb = ib < P.nb;
+  const T* xa = reinterpret_cast<const T*>(P.wb[src]) + (size_t)ia * P.ld;
+  const T* xb = reinterpret_cast<const T*>(P.wb[src]) + (size_t)(hasb ? ib : ia) * P.ld;
+  const T rs2 = T(1.0 / SQRT2);
+  const int e0 = P.cp_off[cp0], e1 = P.cp_off[cp1];
+  for (int k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
+    int cp = cp0;
+    while (P.cp_off[cp + 1] <= k) ++cp;
+    const int m3 = P.ent_m3[k];
+    cplx<T> ca = mk(xa[1 + 2 * k] * rs2, xa[2 + 2 * k] * rs2);
+    cplx<T> cb = hasb ? mk(xb[1 + 2 * k] * rs2, xb[2 + 2 * k] * rs2) : mk(T(0), T(0));
+    cplx<T> vp = mk(ca.x - cb.y, ca.y + cb.x);   // c_a(G) + i c_b(G)
+    cplx<T> vm = mk(ca.x + cb.y, -ca.y + cb.x);  // c_a(G)^* + i c_b(G)^*  (value at -G)
+    int lp, lm;
+    if (cp == 0) { lp = 0; lm = 0; }
+    else { lp = 2 * cp - 1 - col0; lm = 2 * cp - col0; }
+    lines[lp * n3 + wrapi(m3, n3)] = vp;
+    lines[lm * n3 + wrapi(-m3, n3)] = vm;
+  }
+  if (cp0 == 0 && threadIdx.x == 0) {
+    lines[0] = mk(xa[0], hasb ? xb[0] : T(0));
+  }
+  __syncthreads();
+  const cplx<T>* res = fft_lines<T>(lines, alt, ncl, n3, 1, contiguous(ncl), P.fd[2], roots, T(1));
+  cplx<T>* wc = reinterpret_cast<cplx<T>*>(P.Wc) + (size_t)pair * n3 * P.ncol;
+  for (int t = threadIdx.x; t < ncl * n3; t += blockDim.x) {
+    int z = t / ncl, c = t - z * ncl;
+    wc[(size_t)z * P.ncol + col0 + c] = res[c * n3 + z];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// compact z-columns -> sphere (forward z FFT), band separation, + kinetic term.
+// dst = V psi + T psi (the nonlocal part is added by the projector GEMMs).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(ZCOL_THREADS) k_cols_to_wave(KArgs ka, int src, int dst) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int local = blockIdx.x - ka.start[p];
+  const int nchunk = (P.ncp + QCP - 1) / QCP;
+  const int pair = local / nchunk;
+  const int chunk = local - pair * nchunk;
+  const int n3 = P.n3;
+  const int cp0 = chunk * QCP, cp1 = min(cp0 + QCP, P.ncp);
+  int col0, col1;
+  chunk_cols(cp0, cp1, &col0, &col1);
+  const int ncl = col1 - col0;
+  cplx<T>* lines = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* alt = lines + 2 * QCP * n3;
+  cplx<T>* roots = alt + 2 * QCP * n3;
+  load_roots<T>(roots, P, P.n1 + P.n2, n3);
+  const cplx<T>* wc = reinterpret_cast<const cplx<T>*>(P.Wc) + (size_t)pair * n3 * P.ncol;
+  for (int t = threadIdx.x; t < ncl * n3; t += blockDim.x) {
+    int z = t / ncl, c = t - z * ncl;
+    lines[c * n3 + z] = wc[(size_t)z * P.ncol + col0 + c];
+  }
+  __syncthreads();
+  lines = fft_lines<T>(lines, alt, ncl, n3, 1, contiguous(ncl), P.fd[2], roots, T(-1));
+
+  const int ia = 2 * pair, ib = 2 * pair + 1;
+  const bool hasb = ib < P.nb;
+  const T* xa = reinterpret_cast<const T*>(P.wb[src]) + (size_t)ia * P.ld;
+  const T* xb = reinterpret_cast<const T*>(P.wb[src]) + (size_t)(hasb ? ib : ia) * P.ld;
+  T* ya = reinterpret_cast<T*>(P.wb[dst]) + (size_t)ia * P.ld;
+  T* yb = reinterpret_cast<T*>(P.wb[dst]) + (size_t)(hasb ? ib : ia) * P.ld;
+  const T hs2 = T(0.5 * SQRT2);
+  const int e0 = P.cp_off[cp0], e1 = P.cp_off[cp1];
+  for (int k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
+    int cp = cp0;
+    while (P.cp_off[cp + 1] <= k) ++cp;
+    const int m3 = P.ent_m3[k];
+    int lp, lm;
+    if (cp == 0) { lp = 0; lm = 0; }
+    else { lp = 2 * cp - 1 - col0; lm = 2 * cp - col0; }
+    cplx<T> fp = lines[lp * n3 + wrapi(m3, n3)];
+    cplx<T> fm = lines[lm * n3 + wrapi(-m3, n3)];
+    // a: (fp + conj fm)/2 ; b: (fp - conj fm)/(2i)
+    const T ek = T(P.ekin[1 + 2 * k]);
+    T ar = (fp.x + fm.x) * hs2, ai = (fp.y - fm.y) * hs2;
+    T br = (fp.y + fm.y) * hs2, bi = (fm.x - fp.x) * hs2;
+    ya[1 + 2 * k] = ar + ek * xa[1 + 2 * k];
+    ya[2 + 2 * k] = ai + ek * xa[2 + 2 * k];
+    if (hasb) {
+      yb[1 + 2 * k] = br + ek * xb[1 + 2 * k];
+      yb[2 + 2 * k] = bi + ek * xb[2 + 2 * k];
+    }
+  }
+  if (cp0 == 0 && threadIdx.x == 0) {
+    cplx<T> f0 = lines[0];
+    ya[0] = f0.x;
+    if (hasb) yb[0] = f0.y;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per (problem, band pair, z): y and x FFTs to real space, times V_eff/N, and back.
+// In place on the compact columns of plane z.
+// ---------------------------------------------------------------------------
+// Zero both ping-pong planes (rows outside the y-FFT range must read as zero in
+// whichever buffer the data ends up in), then scatter the compact columns.
+template <typename T>
+__device__ __forceinline__ void plane_scatter(const Prob& P, cplx<T>* plane, cplx<T>* alt, const cplx<T>* wcz) {
+  const int n12 = P.n1 * P.n2;
+  for (int t = threadIdx.x; t < n12; t += blockDim.x) {
+    plane[t] = mk(T(0), T(0));
+    alt[t] = mk(T(0), T(0));
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < P.ncol; c += blockDim.x) plane[P.col_xy[c]] = wcz[c];
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PLANE_THREADS_MAX) k_plane_vpsi(KArgs ka) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int local = blockIdx.x - ka.start[p];
+  const int pair = local / P.n3;
+  const int z = local - pair * P.n3;
+  const int n1 = P.n1, n2 = P.n2;
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* b1 = b0 + n1 * n2;
+  cplx<T>* r1 = b1 + n1 * n2;
+  cplx<T>* r2 = r1 + n1;
+  load_roots<T>(r1, P, 0, n1);
+  load_roots<T>(r2, P, n1, n2);
+  cplx<T>* wcz = reinterpret_cast<cplx<T>*>(P.Wc) + ((size_t)pair * P.n3 + z) * P.ncol;
+  plane_scatter<T>(P, b0, b1, wcz);
+  // rows i1 with |m1| <= m1max: [0, m1max] and [n1 - m1max, n1)
+  const int mx = P.m1max;
+  const LineMap rows{mx + 1, n1 - 2 * mx - 1};
+  cplx<T>* cur = b0;
+  cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, 2 * mx + 1, n2, 1, rows, P.fd[1], r2, T(1));   // y, inverse
+  cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, n2, 1, n2, contiguous(n2), P.fd[0], r1, T(1));  // x, inverse
+  const T* v = reinterpret_cast<const T*>(P.veff) + (size_t)z * n1 * n2;
+  for (int t = threadIdx.x; t < n1 * n2; t += blockDim.x) cur[t] = scale(cur[t], v[t]);
+  __syncthreads();
+  cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, n2, 1, n2, contiguous(n2), P.fd[0], r1, T(-1));  // x, forward
+  cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, 2 * mx + 1, n2, 1, rows, P.fd[1], r2, T(-1));   // y, forward
+  for (int c = threadIdx.x; c < P.ncol; c += blockDim.x) wcz[c] = cur[P.col_xy[c]];
+}
+
+// ---------------------------------------------------------------------------
+// Per (problem, z): rho(r) = (1/Omega) sum_pairs f_a Re^2 + f_b Im^2 over all band pairs,
+// accumulated in registers (point t + i*blockDim per thread) in FP64.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(PLANE_THREADS_MAX) k_plane_density(KArgs ka, const double* occ_override) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int z = blockIdx.x - ka.start[p];
+  const int n1 = P.n1, n2 = P.n2, n12 = n1 * n2;
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* b1 = b0 + n12;
+  cplx<T>* r1 = b1 + n12;
+  cplx<T>* r2 = r1 + n1;
+  load_roots<T>(r1, P, 0, n1);
+  load_roots<T>(r2, P, n1, n2);
+  const double* occ = occ_override ? occ_override : P.occ;
+  double acc[DENS_MAXP];
+#pragma unroll
+  for (int i = 0; i < DENS_MAXP; ++i) acc[i] = 0.0;
+  const int mx = P.m1max;
+  const LineMap rows{mx + 1, n1 - 2 * mx - 1};
+  for (int pair = 0; pair < P.npair; ++pair) {
+    const double fa = occ[2 * pair];
+    const double fb = (2 * pair + 1 < P.nb) ? occ[2 * pair + 1] : 0.0;
+    if (fa == 0.0 && fb == 0.0) continue;  // uniform across the block
+    const cplx<T>* wcz = reinterpret_cast<const cplx<T>*>(P.Wc) + ((size_t)pair * P.n3 + z) * P.ncol;
+    __syncthreads();
+    plane_scatter<T>(P, b0, b1, wcz);
+    cplx<T>* cur = b0;
+    cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, 2 * mx + 1, n2, 1, rows, P.fd[1], r2, T(1));
+    cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, n2, 1, n2, contiguous(n2), P.fd[0], r1, T(1));
+#pragma unroll
+    for (int i = 0; i < DENS_MAXP; ++i) {
+      int t = threadIdx.x + i * blockDim.x;
+      if (t < n12) {
+        cplx<T> v = cur[t];
+        acc[i] += fa * (double)v.x * (double)v.x + fb * (double)v.y * (double)v.y;
+      }
+    }
+  }
+  const double io = 1.0 / P.omega;
+  double* rho = P.rho_out + (size_t)z * n12;
+#pragma unroll
+  for (int i = 0; i < DENS_MAXP; ++i) {
+    int t = threadIdx.x + i * blockDim.x;
+    if (t < n12) rho[t] = acc[i] * io;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Full FP64 complex grid transforms (in place): plane pass (x and y) and z pass.
+// which: 0 = gfft, 1 = gfft2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2* grid_of(const Prob& P, int which) { return which ? P.gfft2 : P.gfft; }
+
+__global__ void __launch_bounds__(PLANE_THREADS_MAX) k_grid_plane_fft(KArgs ka, int which, int sign) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int z = blockIdx.x - ka.start[p];
+  const int n1 = P.n1, n2 = P.n2, n12 = n1 * n2;
+  cplx<double>* b0 = reinterpret_cast<cplx<double>*>(smem_raw);
+  cplx<double>* b1 = b0 + n12;
+  cplx<double>* r1 = b1 + n12;
+  cplx<double>* r2 = r1 + n1;
+  load_roots<double>(r1, P, 0, n1);
+  load_roots<double>(r2, P, n1, n2);
+  cplx<double>* g = reinterpret_cast<cplx<double>*>(grid_of(P, which)) + (size_t)z * n12;
+  for (int t = threadIdx.x; t < n12; t += blockDim.x) b0[t] = g[t];
+  __syncthreads();
+  const double sg = sign < 0 ? -1.0 : 1.0;
+  cplx<double>* cur = fft_lines<double>(b0, b1, n1, n2, 1, contiguous(n1), P.fd[1], r2, sg);  // y
+  cur = fft_lines<double>(cur, cur == b0 ? b1 : b0, n2, 1, n2, contiguous(n2), P.fd[0], r1, sg);  // x
+  for (int t = threadIdx.x; t < n12; t += blockDim.x) g[t] = cur[t];
+}
+
+__global__ void __launch_bounds__(ZCOL_THREADS) k_grid_z_fft(KArgs ka, int which, int sign) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int chunk = blockIdx.x - ka.start[p];
+  const int n12 = P.n1 * P.n2, n3 = P.n3;
+  const int c0 = chunk * QZ, nc = min(QZ, n12 - c0);
+  cplx<double>* lines = reinterpret_cast<cplx<double>*>(smem_raw);
+  cplx<double>* alt = lines + QZ * n3;
+  cplx<double>* roots = alt + QZ * n3;
+  load_roots<double>(roots, P, P.n1 + P.n2, n3);
+  cplx<double>* g = reinterpret_cast<cplx<double>*>(grid_of(P, which));
+  for (int t = threadIdx.x; t < nc * n3; t += blockDim.x) {
+    int z = t / nc, c = t - z * nc;
+    lines[c * n3 + z] = g[(size_t)z * n12 + c0 + c];
+  }
+  __syncthreads();
+  const cplx<double>* res =
+      fft_lines<double>(lines, alt, nc, n3, 1, contiguous(nc), P.fd[2], roots, sign < 0 ? -1.0 : 1.0);
+  for (int t = threadIdx.x; t < nc * n3; t += blockDim.x) {
+    int z = t / nc, c = t - z * nc;
+    g[(size_t)z * n12 + c0 + c] = res[c * n3 + z];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_wave_to_cols(const Launch& L, int src) {
+  if (!L.map.total) return;
+  size_t sm = (size_t)(4 * QCP + 1) * L.max_n3 * sizeof(cplx<T>);
+  k_wave_to_cols<T><<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, src);
+}
+template <typename T>
+void launch_cols_to_wave(const Launch& L, int src, int dst) {
+  if (!L.map.total) return;
+  size_t sm = (size_t)(4 * QCP + 1) * L.max_n3 * sizeof(cplx<T>);
+  k_cols_to_wave<T><<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, src, dst);
+}
+template <typename T>
+void launch_plane_vpsi(const Launch& L) {
+  if (!L.map.total) return;
+  size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<T>);
+  k_plane_vpsi<T><<<L.map.total, L.plane_threads, sm, L.stream>>>(L.ka);
+}
+template <typename T>
+void launch_plane_density(const Launch& L, const double* occ_override) {
+  if (!L.map.total) return;
+  size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<T>);
+  k_plane_density<T><<<L.map.total, L.plane_threads, sm, L.stream>>>(L.ka, occ_override);
+}
+void launch_grid_plane_fft(const Launch& L, int which, int sign) {
+  if (!L.map.total) return;
+  size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<double>);
+  k_grid_plane_fft<<<L.map.total, L.plane_threads, sm, L.stream>>>(L.ka, which, sign);
+}
+void launch_grid_z_fft(const Launch& L, int which, int sign) {
+  if (!L.map.total) return;
+  size_t sm = (size_t)(2 * QZ + 1) * L.max_n3 * sizeof(cplx<double>);
+  k_grid_z_fft<<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, which, sign);
+}
+
+void fft_set_smem_limits(size_t bytes) {
+  cudaFuncSetAttribute(k_wave_to_cols<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_wave_to_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_cols_to_wave<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_cols_to_wave<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_plane_vpsi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_plane_vpsi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_plane_density<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_plane_density<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_plane_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_z_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template void launch_wave_to_cols<float>(const Launch&, int);
+template void launch_wave_to_cols<double>(const Launch&, int);
+template void launch_cols_to_wave<float>(const Launch&, int, int);
+template void launch_cols_to_wave<double>(const Launch&, int, int);
+template void launch_plane_vpsi<float>(const Launch&);
+template void launch_plane_vpsi<double>(const Launch&);
+template void launch_plane_density<float>(const Launch&, const double*);
+template void launch_plane_density<double>(const Launch&, const double*);
+
+}  // namespace sgo

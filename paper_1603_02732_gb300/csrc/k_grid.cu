@@ -1,0 +1,598 @@
+// Grid-level kernels of one SCF step (Sec. II D: rho_in -> V_eff; rho_out -> energy;
+// rho_out mixed with rho_in), the structure-dependent terms (local ionic potential,
+// projectors, initial density) and the Hellmann-Feynman forces.
+//
+// Fields on the FFT box follow f(G) = (1/N) sum_r f(r) exp(-iG.r); the unnormalised
+// forward transform leaves N f(G) in the complex work grid.  Nyquist planes (m_i =
+// -N_i/2 for even N_i) are zeroed in every field defined by a formula in G.
+#include "kernels.h"
+
+namespace sgo {
+
+namespace {
+
+struct GPt {
+  int m1, m2, m3;
+  bool nyq;
+};
+
+__device__ __forceinline__ int wrapm(int i, int n, bool* nyq) {
+  if ((n & 1) == 0 && i == n / 2) *nyq = true;
+  return i < (n + 1) / 2 ? i : i - n;
+}
+
+// box point of plane-major index idx = (i3*N1 + i1)*N2 + i2
+__device__ __forceinline__ GPt grid_pt(const Prob& P, int idx, int* i1o = nullptr, int* i2o = nullptr,
+                                       int* i3o = nullptr) {
+  GPt g;
+  g.nyq = false;
+  int i2 = idx % P.n2;
+  int t = idx / P.n2;
+  int i1 = t % P.n1;
+  int i3 = t / P.n1;
+  g.m1 = wrapm(i1, P.n1, &g.nyq);
+  g.m2 = wrapm(i2, P.n2, &g.nyq);
+  g.m3 = wrapm(i3, P.n3, &g.nyq);
+  if (i1o) *i1o = i1;
+  if (i2o) *i2o = i2;
+  if (i3o) *i3o = i3;
+  return g;
+}
+
+__device__ __forceinline__ void gcart(const Prob& P, int m1, int m2, int m3, double* G) {
+  for (int d = 0; d < 3; ++d) G[d] = m1 * P.bvec[d] + m2 * P.bvec[3 + d] + m3 * P.bvec[6 + d];
+}
+
+__device__ __forceinline__ double* grid_sel(const Prob& P, int sel) {
+  switch (sel) {
+    case 0: return P.rho_in;
+    case 1: return P.rho_out;
+    case 2: return P.resid;
+    default: return P.vion_r;
+  }
+}
+
+// exp(-i G.R_I) from the atom's 1D tables (indexed by grid index per axis).
+__device__ __forceinline__ cplx<double> phase_at(const Prob& P, int atom, int i1, int i2, int i3) {
+  const cplx<double>* ph = reinterpret_cast<const cplx<double>*>(P.phase) + (size_t)atom * (P.n1 + P.n2 + P.n3);
+  return ph[i1] * ph[P.n1 + i2] * ph[P.n1 + P.n2 + i3];
+}
+
+// Perdew-Zunger 1981 correlation + Slater exchange (unpolarised); rho clipped at 0.
+__device__ __forceinline__ void lda_pz81(double rho, double* exc, double* vxc) {
+  if (!(rho > 1e-30)) {
+    *exc = 0.0;
+    *vxc = 0.0;
+    return;
+  }
+  const double ex = -0.75 * cbrt(3.0 * rho / PI);
+  const double rs = cbrt(3.0 / (4.0 * PI * rho));
+  double ec, vc;
+  if (rs >= 1.0) {
+    const double g = -0.1423, b1 = 1.0529, b2 = 0.3334;
+    const double sr = sqrt(rs);
+    const double den = 1.0 + b1 * sr + b2 * rs;
+    ec = g / den;
+    vc = ec * (1.0 + (7.0 / 6.0) * b1 * sr + (4.0 / 3.0) * b2 * rs) / den;
+  } else {
+    const double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
+    const double lr = log(rs);
+    ec = A * lr + B + C * rs * lr + D * rs;
+    vc = A * lr + (B - A / 3.0) + (2.0 / 3.0) * C * rs * lr + (2.0 * D - C) / 3.0 * rs;
+  }
+  *exc = ex + ec;
+  *vxc = (4.0 / 3.0) * ex + vc;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// elementwise grid kernels: CTA = (problem, chunk of GRID_EW points)
+// ---------------------------------------------------------------------------
+constexpr int GRID_EW = GRID_EW_POINTS;
+
+#define GRID_EW_PROLOGUE                                           \
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);            \
+  if (!ka.active[p]) return;                                       \
+  const Prob& P = ka.probs[p];                                     \
+  const int base = (blockIdx.x - ka.start[p]) * GRID_EW;           \
+  const int end = min(P.ngrid, base + GRID_EW);
+
+__global__ void k_real_to_grid(KArgs ka, int src, int which) {
+  GRID_EW_PROLOGUE
+  const double* s = grid_sel(P, src);
+  double2* g = which ? P.gfft2 : P.gfft;
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) g[i] = make_double2(s[i], 0.0);
+}
+
+__global__ void k_grid_real_part(KArgs ka, int which, int dst) {
+  GRID_EW_PROLOGUE
+  const double2* g = which ? P.gfft2 : P.gfft;
+  double* d = grid_sel(P, dst);
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) d[i] = g[i].x;
+}
+
+// V_H(G) = 4 pi rho(G) / |G|^2 (G != 0), from N rho(G) in the work grid.
+__global__ void k_hartree_g(KArgs ka, int which) {
+  GRID_EW_PROLOGUE
+  double2* g = which ? P.gfft2 : P.gfft;
+  const double inv_n = 1.0 / P.ngrid;
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    GPt q = grid_pt(P, i);
+    double G[3];
+    gcart(P, q.m1, q.m2, q.m3, G);
+    double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    double2 v = g[i];
+    double f = (q.nyq || g2 < 1e-14) ? 0.0 : 4.0 * PI * inv_n / g2;
+    g[i] = make_double2(v.x * f, v.y * f);
+  }
+}
+
+// V_eff(r) = V_ion(r) + V_H(r) + v_xc(rho_in(r)), stored divided by N in the wave
+// precision for the H.psi plane kernel.  With user_v: the caller's C-order grid.
+template <typename T>
+__global__ void k_veff(KArgs ka, const double* user_v) {
+  GRID_EW_PROLOGUE
+  T* v = reinterpret_cast<T*>(P.veff);
+  const double inv_n = 1.0 / P.ngrid;
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    double val;
+    if (user_v) {
+      int i1, i2, i3;
+      grid_pt(P, i, &i1, &i2, &i3);
+      val = user_v[((size_t)i1 * P.n2 + i2) * P.n3 + i3];
+    } else {
+      double exc, vxc;
+      lda_pz81(P.rho_in[i], &exc, &vxc);
+      val = P.vion_r[i] + P.gfft[i].x + vxc;
+    }
+    v[i] = (T)(val * inv_n);
+  }
+}
+
+// Kerker damping of the work grid: R(G) *= G^2/(G^2 + q0^2), and 0 at G = 0.
+__global__ void k_kerker(KArgs ka, double q0) {
+  GRID_EW_PROLOGUE
+  double2* g = P.gfft;
+  const double inv_n = 1.0 / P.ngrid;
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    GPt q = grid_pt(P, i);
+    double G[3];
+    gcart(P, q.m1, q.m2, q.m3, G);
+    double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    double f = (q.nyq || g2 < 1e-14) ? 0.0 : g2 / (g2 + q0 * q0) * inv_n;
+    double2 v = g[i];
+    g[i] = make_double2(v.x * f, v.y * f);
+  }
+}
+
+// V_ion(G) = sum_I v_s(G) exp(-iG.R_I) (work grid gfft).
+__global__ void k_vion_g(KArgs ka) {
+  GRID_EW_PROLOGUE
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    int i1, i2, i3;
+    grid_pt(P, i, &i1, &i2, &i3);
+    cplx<double> acc = mk(0.0, 0.0);
+    for (int a = 0; a < P.natom; ++a) {
+      double v = P.vloc_g[(size_t)P.spec[a] * P.ngrid + i];
+      acc = acc + scale(phase_at(P, a, i1, i2, i3), v);
+    }
+    P.gfft[i] = make_double2(acc.x, acc.y);
+  }
+}
+
+// Initial density: neutral atomic Gaussians (Z/Omega) exp(-G^2 rc^2/4) exp(-iG.R_I),
+// band-limited to |G|^2/2 <= 4 Ecut (work grid gfft).
+__global__ void k_rho0_g(KArgs ka) {
+  GRID_EW_PROLOGUE
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    int i1, i2, i3;
+    GPt q = grid_pt(P, i, &i1, &i2, &i3);
+    double G[3];
+    gcart(P, q.m1, q.m2, q.m3, G);
+    double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    cplx<double> acc = mk(0.0, 0.0);
+    if (!q.nyq && 0.5 * g2 <= 4.0 * P.ecut) {
+      for (int a = 0; a < P.natom; ++a) {
+        const double* sp = P.sp + P.spec[a] * 6;
+        double amp = sp[0] / P.omega * exp(-g2 * sp[1] * sp[1] * 0.25);
+        acc = acc + scale(phase_at(P, a, i1, i2, i3), amp);
+      }
+    }
+    P.gfft[i] = make_double2(acc.x, acc.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grid reductions for the energy at rho_out (work grid gfft = N rho_out(G)):
+// part[p][chunk][0..4] = sum V_ion rho, sum rho eps_xc, sum rho, sum |rho_out - rho_in|,
+// sum_{G!=0} |rho(G)|^2 / G^2.
+// ---------------------------------------------------------------------------
+constexpr int NGE = 5;
+
+__global__ void k_grid_energies(KArgs ka, double* part, int maxchunk) {
+  __shared__ double red[33];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int chunk = blockIdx.x - ka.start[p];
+  const int base = chunk * GRID_CHUNK, end = min(P.ngrid, base + GRID_CHUNK);
+  const double inv_n = 1.0 / P.ngrid;
+  double s[NGE] = {0, 0, 0, 0, 0};
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    double r = P.rho_out[i];
+    double exc, vxc;
+    lda_pz81(r, &exc, &vxc);
+    s[0] += P.vion_r[i] * r;
+    s[1] += fmax(r, 0.0) * exc;
+    s[2] += r;
+    s[3] += fabs(r - P.rho_in[i]);
+    GPt q = grid_pt(P, i);
+    if (!q.nyq) {
+      double G[3];
+      gcart(P, q.m1, q.m2, q.m3, G);
+      double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+      if (g2 > 1e-14) {
+        double2 v = P.gfft[i];
+        s[4] += (v.x * v.x + v.y * v.y) * inv_n * inv_n / g2;
+      }
+    }
+  }
+  for (int k = 0; k < NGE; ++k) {
+    double t = block_sum(s[k], red);
+    if (threadIdx.x == 0) part[((size_t)p * maxchunk + chunk) * NGE + k] = t;
+  }
+}
+
+__global__ void k_grid_energies_reduce(KArgs ka, const double* part, int maxchunk) {
+  const int p = blockIdx.x;
+  if (!ka.active[p] || threadIdx.x != 0) return;
+  const Prob& P = ka.probs[p];
+  const int nch = (P.ngrid + GRID_CHUNK - 1) / GRID_CHUNK;
+  double s[NGE] = {0, 0, 0, 0, 0};
+  for (int c = 0; c < nch; ++c)
+    for (int k = 0; k < NGE; ++k) s[k] += part[((size_t)p * maxchunk + c) * NGE + k];
+  const double dv = P.omega / P.ngrid;
+  P.scal[SC_ELOC] = dv * s[0];
+  P.scal[SC_EXC] = dv * s[1];
+  P.scal[SC_NELCHK] = dv * s[2];
+  P.scal[SC_RESID] = dv * s[3] / P.nel;
+  P.scal[SC_EH] = 0.5 * P.omega * 4.0 * PI * s[4];
+}
+
+// Band terms, total free energy, convergence test.  One CTA per problem.
+__global__ void k_finish_iteration(KArgs ka, double tol_e, double tol_rho, int count_iter) {
+  __shared__ double red[33];
+  const int p = blockIdx.x;
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  double ek = 0.0, en = 0.0;
+  for (int i = threadIdx.x; i < P.nb; i += blockDim.x) {
+    const double f = P.occ[i];
+    ek += f * P.bv[BV_EKIN * P.nb + i];
+    double s = 0.0;
+    for (int a = 0; a < P.natom; ++a) {
+      double pr = P.proj[(size_t)a * P.nb + i];
+      s += P.sp[P.spec[a] * 6 + 5] * pr * pr;
+    }
+    en += f * s;
+  }
+  ek = block_sum(ek, red);
+  en = block_sum(en, red);
+  if (threadIdx.x == 0) {
+    double* sc = P.scal;
+    sc[SC_EKIN] = ek;
+    sc[SC_ENL] = en;
+    sc[SC_MTS] = -P.kT * sc[SC_ENTROPY];
+    double F = ek + en + sc[SC_ELOC] + sc[SC_EH] + sc[SC_EXC] + sc[SC_EEW] + sc[SC_MTS];
+    const int it = (int)sc[SC_ITER];
+    sc[SC_DF] = it > 0 ? F - sc[SC_FPREV] : 1e300;
+    bool conv = count_iter && it > 0 && fabs(sc[SC_DF]) < tol_e && sc[SC_RESID] < tol_rho;
+    sc[SC_FREE] = F;
+    sc[SC_FPREV] = F;
+    if (count_iter) sc[SC_ITER] = it + 1;
+    sc[SC_CONV] = conv ? 1.0 : 0.0;
+    if (!isfinite(F)) P.status[1] = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pulay (DIIS) mixing on R = rho_out - rho_in with a ring history.
+// ---------------------------------------------------------------------------
+__global__ void k_pulay_store(KArgs ka) {
+  GRID_EW_PROLOGUE
+  const int pos = (int)P.scal[SC_PULAY_POS];
+  double* hr = P.hrho + (size_t)pos * P.ngrid;
+  double* hs = P.hres + (size_t)pos * P.ngrid;
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    double ri = P.rho_in[i];
+    hr[i] = ri;
+    hs[i] = P.rho_out[i] - ri;
+  }
+}
+
+// part[p][chunk][j] = <R_pos, R_j> over a chunk, for every ring slot j.
+__global__ void k_pulay_gram(KArgs ka, double* part, int maxchunk, int hist) {
+  __shared__ double red[33];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int chunk = blockIdx.x - ka.start[p];
+  const int base = chunk * GRID_CHUNK, end = min(P.ngrid, base + GRID_CHUNK);
+  const int pos = (int)P.scal[SC_PULAY_POS];
+  const int cnt = min((int)P.scal[SC_PULAY_N] + 1, hist);
+  const double* rp = P.hres + (size_t)pos * P.ngrid;
+  for (int j = 0; j < cnt; ++j) {
+    const double* rj = P.hres + (size_t)j * P.ngrid;
+    double s = 0.0;
+    for (int i = base + threadIdx.x; i < end; i += blockDim.x) s += rp[i] * rj[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[((size_t)p * maxchunk + chunk) * MAX_HIST + j] = s;
+  }
+}
+
+// Gram row update and the DIIS system [A 1; 1 0][c; l] = [0; 1] (partial pivoting).
+__global__ void k_pulay_solve(KArgs ka, const double* part, int maxchunk, int hist) {
+  const int p = blockIdx.x;
+  if (!ka.active[p] || threadIdx.x != 0) return;
+  const Prob& P = ka.probs[p];
+  double* sc = P.scal;
+  double* A = sc + SC_PULAY_A;
+  double* alpha = sc + SC_PULAY_A + MAX_HIST * MAX_HIST;
+  const int pos = (int)sc[SC_PULAY_POS];
+  const int cnt = min((int)sc[SC_PULAY_N] + 1, hist);
+  const int nch = (P.ngrid + GRID_CHUNK - 1) / GRID_CHUNK;
+  for (int j = 0; j < cnt; ++j) {
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += part[((size_t)p * maxchunk + c) * MAX_HIST + j];
+    A[pos * MAX_HIST + j] = s;
+    A[j * MAX_HIST + pos] = s;
+  }
+  const int m = cnt + 1;
+  double M[(MAX_HIST + 1) * (MAX_HIST + 2)];
+  const double scl = A[pos * MAX_HIST + pos] > 0.0 ? 1.0 / A[pos * MAX_HIST + pos] : 1.0;
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) {
+      double v;
+      if (i < cnt && j < cnt) v = A[i * MAX_HIST + j] * scl;
+      else if (i == cnt && j == cnt) v = 0.0;
+      else v = 1.0;
+      M[i * (m + 1) + j] = v;
+    }
+    M[i * (m + 1) + m] = (i == cnt) ? 1.0 : 0.0;
+  }
+  bool ok = true;
+  for (int k = 0; k < m && ok; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < m; ++i)
+      if (fabs(M[i * (m + 1) + k]) > fabs(M[piv * (m + 1) + k])) piv = i;
+    if (fabs(M[piv * (m + 1) + k]) < 1e-300) { ok = false; break; }
+    if (piv != k)
+      for (int j = 0; j <= m; ++j) {
+        double t = M[k * (m + 1) + j];
+        M[k * (m + 1) + j] = M[piv * (m + 1) + j];
+        M[piv * (m + 1) + j] = t;
+      }
+    for (int i = k + 1; i < m; ++i) {
+      double f = M[i * (m + 1) + k] / M[k * (m + 1) + k];
+      for (int j = k; j <= m; ++j) M[i * (m + 1) + j] -= f * M[k * (m + 1) + j];
+    }
+  }
+  double x[MAX_HIST + 1];
+  if (ok) {
+    for (int i = m - 1; i >= 0; --i) {
+      double s = M[i * (m + 1) + m];
+      for (int j = i + 1; j < m; ++j) s -= M[i * (m + 1) + j] * x[j];
+      x[i] = s / M[i * (m + 1) + i];
+      if (!isfinite(x[i])) ok = false;
+    }
+  }
+  for (int j = 0; j < MAX_HIST; ++j) alpha[j] = 0.0;
+  if (ok) {
+    for (int j = 0; j < cnt; ++j) alpha[j] = x[j];
+  } else {
+    alpha[pos] = 1.0;
+  }
+  sc[SC_PULAY_N] = cnt;
+  sc[SC_PULAY_POS] = (pos + 1) % hist;
+}
+
+// stage 0: rho_in = sum_j c_j rho_j, resid = sum_j c_j R_j ; stage 1: rho_in += a * resid
+__global__ void k_pulay_mix(KArgs ka, int stage, double a) {
+  GRID_EW_PROLOGUE
+  const double* alpha = P.scal + SC_PULAY_A + MAX_HIST * MAX_HIST;
+  const int cnt = (int)P.scal[SC_PULAY_N];
+  if (stage == 0) {
+    for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+      double r = 0.0, s = 0.0;
+      for (int j = 0; j < cnt; ++j) {
+        r += alpha[j] * P.hrho[(size_t)j * P.ngrid + i];
+        s += alpha[j] * P.hres[(size_t)j * P.ngrid + i];
+      }
+      P.rho_in[i] = r;
+      P.resid[i] = s;
+    }
+  } else {
+    for (int i = base + threadIdx.x; i < end; i += blockDim.x) P.rho_in[i] += a * P.resid[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Projectors (packed real form): B[I] = pack(beta_s(G) exp(-iG.R_I)) and, for the
+// forces, dB[3I+a] = pack(-i G_a beta_I(G)) = (G_a b_im, -G_a b_re).
+// beta_s(G) = Omega^{-1/2} N (2 pi)^{3/2} rp^3 exp(-G^2 rp^2/2), N^2 = 1/(pi^{3/2} rp^3).
+// CTA = (problem, atom).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_build_projectors(KArgs ka, int deriv) {
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int a = blockIdx.x - ka.start[p];
+  const double* sp = P.sp + P.spec[a] * 6;
+  const double rp = sp[4];
+  const double nrm = 1.0 / sqrt(pow(PI, 1.5) * rp * rp * rp);
+  const double amp = nrm * pow(2.0 * PI, 1.5) * rp * rp * rp / sqrt(P.omega);
+  T* b = reinterpret_cast<T*>(P.B) + (size_t)a * P.ld;
+  T* d0 = deriv ? reinterpret_cast<T*>(P.dB) + (size_t)(3 * a) * P.ld : nullptr;
+  const int* em1 = P.ent_m3 - 2 * P.nhalf;
+  const int* em2 = P.ent_m3 - P.nhalf;
+  for (int k = threadIdx.x; k <= P.nhalf; k += blockDim.x) {
+    if (k == 0) {
+      if (!deriv) b[0] = (T)amp;
+      else for (int c = 0; c < 3; ++c) d0[(size_t)c * P.ld] = T(0);
+      continue;
+    }
+    const int e = k - 1;
+    const double g2 = 2.0 * P.ekin[1 + 2 * e];
+    const double bg = amp * exp(-0.5 * g2 * rp * rp);
+    const int m1 = em1[e], m2 = em2[e], m3 = P.ent_m3[e];
+    const int i1 = m1 < 0 ? m1 + P.n1 : m1, i2 = m2 < 0 ? m2 + P.n2 : m2, i3 = m3 < 0 ? m3 + P.n3 : m3;
+    cplx<double> ph = phase_at(P, a, i1, i2, i3);
+    const double bre = SQRT2 * bg * ph.x, bim = SQRT2 * bg * ph.y;
+    if (!deriv) {
+      b[1 + 2 * e] = (T)bre;
+      b[2 + 2 * e] = (T)bim;
+    } else {
+      for (int c = 0; c < 3; ++c) {
+        const double gc = P.gvec[(size_t)c * P.ld + 1 + 2 * e];
+        d0[(size_t)c * P.ld + 1 + 2 * e] = (T)(gc * bim);
+        d0[(size_t)c * P.ld + 2 + 2 * e] = (T)(-gc * bre);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forces.  Local: dE/dR_Ia = Omega sum_G v_s(G) G_a Im[exp(-iG.R_I) rho(G)^*] over the
+// box (work grid gfft = N rho_out(G)).  CTA = (problem, atom, chunk) -> partials.
+// ---------------------------------------------------------------------------
+__global__ void k_local_forces(KArgs ka, int maxchunk) {
+  __shared__ double red[33];
+  (void)maxchunk;
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int nch = (P.ngrid + GRID_CHUNK - 1) / GRID_CHUNK;  // fpart is [natom][nch][3]
+  const int local = blockIdx.x - ka.start[p];
+  const int a = local / nch, chunk = local - a * nch;
+  const int base = chunk * GRID_CHUNK, end = min(P.ngrid, base + GRID_CHUNK);
+  const double* vg = P.vloc_g + (size_t)P.spec[a] * P.ngrid;
+  const double inv_n = 1.0 / P.ngrid;
+  double f[3] = {0, 0, 0};
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    int i1, i2, i3;
+    GPt q = grid_pt(P, i, &i1, &i2, &i3);
+    if (q.nyq) continue;
+    double v = vg[i];
+    if (v == 0.0) continue;
+    double2 rg = P.gfft[i];
+    cplx<double> w = phase_at(P, a, i1, i2, i3) * mk(rg.x * inv_n, -rg.y * inv_n);
+    double G[3];
+    gcart(P, q.m1, q.m2, q.m3, G);
+    for (int c = 0; c < 3; ++c) f[c] += v * G[c] * w.y;
+  }
+  for (int c = 0; c < 3; ++c) {
+    double t = block_sum(f[c], red);
+    if (threadIdx.x == 0) P.fpart[((size_t)a * nch + chunk) * 3 + c] = -P.omega * t;
+  }
+}
+
+// Total: local partials + nonlocal -2 D sum_n f_n p_nI dp_nIa + Ewald.  CTA per problem.
+__global__ void k_force_total(KArgs ka, int maxchunk) {
+  (void)maxchunk;
+  const int p = blockIdx.x;
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int nch = (P.ngrid + GRID_CHUNK - 1) / GRID_CHUNK;
+  for (int e = threadIdx.x; e < 3 * P.natom; e += blockDim.x) {
+    const int a = e / 3, c = e % 3;
+    double s = 0.0;
+    for (int k = 0; k < nch; ++k) s += P.fpart[((size_t)a * nch + k) * 3 + c];
+    const double D = P.sp[P.spec[a] * 6 + 5];
+    double nl = 0.0;
+    for (int n = 0; n < P.nb; ++n)
+      nl += P.occ[n] * P.proj[(size_t)a * P.nb + n] * P.dproj[(size_t)(3 * a + c) * P.nb + n];
+    P.forces[e] = s - 2.0 * D * nl + P.ewald_f[e];
+  }
+}
+
+// Copy a grid (sel as in grid_sel) to C order (i1, i2, i3) for the caller.
+__global__ void k_export_grid(KArgs ka, int sel, double* out) {
+  GRID_EW_PROLOGUE
+  const double* s = grid_sel(P, sel);
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    int i1, i2, i3;
+    grid_pt(P, i, &i1, &i2, &i3);
+    out[((size_t)i1 * P.n2 + i2) * P.n3 + i3] = s[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline int ew_blocks(const Launch& L) { return L.map.total; }
+
+void launch_real_to_grid(const Launch& L, int src, int which) {
+  if (ew_blocks(L)) k_real_to_grid<<<L.map.total, 256, 0, L.stream>>>(L.ka, src, which);
+}
+void launch_grid_real_part(const Launch& L, int which, int dst) {
+  if (ew_blocks(L)) k_grid_real_part<<<L.map.total, 256, 0, L.stream>>>(L.ka, which, dst);
+}
+void launch_export_grid(const Launch& L, int sel, double* out) {
+  if (ew_blocks(L)) k_export_grid<<<L.map.total, 256, 0, L.stream>>>(L.ka, sel, out);
+}
+void launch_hartree_g(const Launch& L, int which) {
+  if (ew_blocks(L)) k_hartree_g<<<L.map.total, 256, 0, L.stream>>>(L.ka, which);
+}
+template <typename T>
+void launch_veff(const Launch& L, const double* user_v) {
+  if (ew_blocks(L)) k_veff<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, user_v);
+}
+void launch_kerker(const Launch& L, double q0) {
+  if (ew_blocks(L)) k_kerker<<<L.map.total, 256, 0, L.stream>>>(L.ka, q0);
+}
+void launch_vion_g(const Launch& L) {
+  if (ew_blocks(L)) k_vion_g<<<L.map.total, 256, 0, L.stream>>>(L.ka);
+}
+void launch_rho0_g(const Launch& L) {
+  if (ew_blocks(L)) k_rho0_g<<<L.map.total, 256, 0, L.stream>>>(L.ka);
+}
+void launch_pulay_store(const Launch& L) {
+  if (ew_blocks(L)) k_pulay_store<<<L.map.total, 256, 0, L.stream>>>(L.ka);
+}
+void launch_pulay_mix(const Launch& L, int stage, double a) {
+  if (ew_blocks(L)) k_pulay_mix<<<L.map.total, 256, 0, L.stream>>>(L.ka, stage, a);
+}
+void launch_grid_energies(const Launch& Lchunks, double* part, int maxchunk) {
+  if (Lchunks.map.total) k_grid_energies<<<Lchunks.map.total, 256, 0, Lchunks.stream>>>(Lchunks.ka, part, maxchunk);
+}
+void launch_grid_energies_reduce(const Launch& L, const double* part, int maxchunk) {
+  k_grid_energies_reduce<<<L.ka.nprob, 32, 0, L.stream>>>(L.ka, part, maxchunk);
+}
+void launch_finish_iteration(const Launch& L, double tol_e, double tol_rho, int count_iter) {
+  k_finish_iteration<<<L.ka.nprob, 128, 0, L.stream>>>(L.ka, tol_e, tol_rho, count_iter);
+}
+void launch_pulay_gram(const Launch& Lchunks, double* part, int maxchunk, int hist) {
+  if (Lchunks.map.total) k_pulay_gram<<<Lchunks.map.total, 256, 0, Lchunks.stream>>>(Lchunks.ka, part, maxchunk, hist);
+}
+void launch_pulay_solve(const Launch& L, const double* part, int maxchunk, int hist) {
+  k_pulay_solve<<<L.ka.nprob, 32, 0, L.stream>>>(L.ka, part, maxchunk, hist);
+}
+template <typename T>
+void launch_build_projectors(const Launch& Latoms, int deriv) {
+  if (Latoms.map.total) k_build_projectors<T><<<Latoms.map.total, 256, 0, Latoms.stream>>>(Latoms.ka, deriv);
+}
+void launch_local_forces(const Launch& Lac, int maxchunk) {
+  if (Lac.map.total) k_local_forces<<<Lac.map.total, 256, 0, Lac.stream>>>(Lac.ka, maxchunk);
+}
+void launch_force_total(const Launch& L, int maxchunk) {
+  k_force_total<<<L.ka.nprob, 128, 0, L.stream>>>(L.ka, maxchunk);
+}
+
+template void launch_veff<float>(const Launch&, const double*);
+template void launch_veff<double>(const Launch&, const double*);
+template void launch_build_projectors<float>(const Launch&, int);
+template void launch_build_projectors<double>(const Launch&, int);
+
+}  // namespace sgo

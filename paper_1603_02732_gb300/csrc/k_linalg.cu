@@ -1,0 +1,702 @@
+// Subspace linear algebra of the all-band CG eigensolver (Algorithm 1).
+//
+//  * gemm_tn: C = A^T B over the packed plane-wave index (K = npw) -- the subspace
+//    matrices H(i,j) = <Psi_i|H|Psi_j> and overlaps (lines 2, 14, 15), the projection
+//    coefficients <Psi_j|P_i> (line 12) and the projector overlaps <beta_I|Psi_n>.
+//    Split-K: every CTA sums one K chunk in the working precision and writes an FP64
+//    partial; a second kernel adds the partials in a fixed order (deterministic).
+//  * gemm_nn: Y = beta Y + alpha A M with a small FP64 matrix M -- subspace rotations
+//    (lines 3, 14, 16), the projection P -= Psi C (line 12), the nonlocal apply.
+//  * per-band kernels: residual + preconditioner + conjugate direction (lines 6-11),
+//    normalisation, line minimisation (line 13).
+//  * rr: FP64 Cholesky of the overlap, L^-1 H L^-T and a parallel cyclic Jacobi
+//    eigensolve (the subspace diagonalisation of lines 3 and 16).
+//  * occupations: Fermi-Dirac with the chemical potential by safeguarded Newton.
+#include "kernels.h"
+
+namespace sgo {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ const T* opnd(const Prob& P, int kind, int role) {
+  if (kind == OPK_WB) return reinterpret_cast<const T*>(P.wb[role]);
+  if (kind == OPK_B) return reinterpret_cast<const T*>(P.B);
+  return reinterpret_cast<const T*>(P.dB);
+}
+__device__ __forceinline__ int opnd_count(const Prob& P, int kind) {
+  return kind == OPK_WB ? P.nb : (kind == OPK_B ? P.natom : 3 * P.natom);
+}
+__device__ __forceinline__ double* dense_ptr(const Prob& P, int sel) {
+  switch (sel) {
+    case DD_S: return P.S;
+    case DD_HS: return P.Hs;
+    case DD_CM: return P.Cm;
+    case DD_TM: return P.Tm;
+    case DD_PROJ: case DD_PROJ_D: return P.proj;
+    default: return P.dproj;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C = A^T B, split-K partials.  CTA = (problem, tile_i, tile_j, split).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole, int bkind, int brole, double* part_base,
+                                                size_t part_stride) {
+  __shared__ T As[32][TN_TILE + 1];
+  __shared__ T Bs[32][TN_TILE + 1];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  int local = blockIdx.x - ka.start[p];
+  const int na = opnd_count(P, akind), nbv = opnd_count(P, bkind);
+  const int ta = (na + TN_TILE - 1) / TN_TILE, tb = (nbv + TN_TILE - 1) / TN_TILE;
+  const int split = local / (ta * tb);
+  local -= split * ta * tb;
+  const int ti0 = (local / tb) * TN_TILE, tj0 = (local % tb) * TN_TILE;
+  const T* A = opnd<T>(P, akind, arole);
+  const T* Bm = opnd<T>(P, bkind, brole);
+  const int ld = P.ld;
+  const int k0 = split * TN_KC, k1 = min(P.npw, k0 + TN_KC);
+  const int t = threadIdx.x;
+  const int ti = t & 15, tj = t >> 4;
+  T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+  for (int kb = k0; kb < k1; kb += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = t + 256 * q;
+      int v = e >> 5, kk = e & 31;
+      int k = kb + kk;
+      As[kk][v] = (ti0 + v < na && k < k1) ? A[(size_t)(ti0 + v) * ld + k] : T(0);
+      Bs[kk][v] = (tj0 + v < nbv && k < k1) ? Bm[(size_t)(tj0 + v) * ld + k] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      T a0 = As[kk][ti], a1 = As[kk][ti + 16];
+      T b0 = Bs[kk][tj], b1 = Bs[kk][tj + 16];
+      acc[0][0] += a0 * b0;
+      acc[0][1] += a0 * b1;
+      acc[1][0] += a1 * b0;
+      acc[1][1] += a1 * b1;
+    }
+    __syncthreads();
+  }
+  double* part = part_base + (size_t)p * part_stride + (size_t)split * na * nbv;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int i = ti0 + ti + 16 * a, j = tj0 + tj + 16 * b;
+      if (i < na && j < nbv) part[(size_t)i * nbv + j] = (double)acc[a][b];
+    }
+}
+
+// Sum the partials in split order.  CTA = (problem, chunk of 256 outputs).
+__global__ void k_gemm_tn_reduce(KArgs ka, int akind, int bkind, int dst, const double* part_base, size_t part_stride) {
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int na = opnd_count(P, akind), nbv = opnd_count(P, bkind);
+  const int o = (blockIdx.x - ka.start[p]) * 256 + threadIdx.x;
+  if (o >= na * nbv) return;
+  const int nsplit = (P.npw + TN_KC - 1) / TN_KC;
+  const double* part = part_base + (size_t)p * part_stride;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += part[(size_t)k * na * nbv + o];
+  dense_ptr(P, dst)[o] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Y = beta Y + alpha A M: rows npw, inner = count(A), columns nb.
+// M is row-major [inner][nb] FP64 (DD_PROJ_D: rows scaled by the atoms' D).
+// CTA = (problem, row tile, column tile), 64 x 64 outputs, 4 x 4 per thread.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_nn(KArgs ka, int akind, int arole, int msel, int yrole, double alpha,
+                                                double beta) {
+  __shared__ T As[32][NN_TILE];
+  __shared__ T Ms[32][NN_TILE];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int local = blockIdx.x - ka.start[p];
+  const int nct = (P.nb + NN_TILE - 1) / NN_TILE;
+  const int r0 = (local / nct) * NN_TILE, c0 = (local % nct) * NN_TILE;
+  const int inner = opnd_count(P, akind);
+  const int nb = P.nb, ld = P.ld, npw = P.npw;
+  const T* A = opnd<T>(P, akind, arole);
+  const double* M = dense_ptr(P, msel);
+  T* Y = reinterpret_cast<T*>(P.wb[yrole]);
+  const int t = threadIdx.x, tr = t & 15, tc = t >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < inner; k0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int e = t + 256 * q;      // 2048 = 32 x 64
+      int kk = e >> 6, rr = e & 63;
+      int k = k0 + kk;
+      As[kk][rr] = (k < inner && r0 + rr < npw) ? A[(size_t)k * ld + r0 + rr] : T(0);
+      double mv = 0.0;
+      if (k < inner && c0 + rr < nb) {
+        mv = M[(size_t)k * nb + c0 + rr];
+        if (msel == DD_PROJ_D) mv *= P.sp[P.spec[k] * 6 + 5];
+      }
+      Ms[kk][rr] = (T)mv;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      T a[4], m[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tr + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) m[j] = Ms[kk][tc + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * m[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int c = c0 + tc + 16 * j;
+    if (c >= nb) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int r = r0 + tr + 16 * i;
+      if (r >= npw) continue;
+      T* y = Y + (size_t)c * ld + r;
+      T v = T(alpha) * acc[i][j];
+      if (beta != 0.0) v += T(beta) * (*y);
+      *y = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-band kernels: CTA = (problem, band)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(BAND_THREADS) k_band_kinetic(KArgs ka, int xr) {
+  __shared__ double red[33];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int i = blockIdx.x - ka.start[p];
+  const T* x = reinterpret_cast<const T*>(P.wb[xr]) + (size_t)i * P.ld;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) s += P.ekin[k] * (double)x[k] * (double)x[k];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) P.bv[BV_EKIN * P.nb + i] = s;
+}
+
+// Teter-Payne-Allan preconditioner factor, y = T(G) / E_kin(band).
+__device__ __forceinline__ double tpa(double y) {
+  double y2 = y * y, y3 = y2 * y;
+  double num = 27.0 + 18.0 * y + 12.0 * y2 + 8.0 * y3;
+  return num / (num + 16.0 * y2 * y2);
+}
+
+// Residual R = HX - eps X (line 6), G = A R (TPA; line 8), conjugate direction
+// P = G + gamma P_prev with Polak-Ribiere gamma = <G, R - R_prev>/<G_prev, R_prev>, >= 0
+// (line 10).  Writes P and R (for the next step).
+template <typename T>
+__global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, int hxr, int pr, int rr_out, int ppr, int rpr) {
+  __shared__ double red[33];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int i = blockIdx.x - ka.start[p];
+  const size_t off = (size_t)i * P.ld;
+  const T* x = reinterpret_cast<const T*>(P.wb[xr]) + off;
+  const T* hx = reinterpret_cast<const T*>(P.wb[hxr]) + off;
+  T* pv = reinterpret_cast<T*>(P.wb[pr]) + off;
+  T* rv = reinterpret_cast<T*>(P.wb[rr_out]) + off;
+  const T* pp = reinterpret_cast<const T*>(P.wb[ppr]) + off;
+  const T* rp = reinterpret_cast<const T*>(P.wb[rpr]) + off;
+  const bool first = P.scal[SC_FIRSTCG] != 0.0;
+  double ek = 0.0;
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) ek += P.ekin[k] * (double)x[k] * (double)x[k];
+  ek = block_sum(ek, red);
+  ek = fmax(ek, 1e-3);
+  const double eps = P.eps[i];
+  double gr = 0.0, grp = 0.0, r2 = 0.0;
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
+    double r = (double)hx[k] - eps * (double)x[k];
+    double g = tpa(P.ekin[k] / ek) * r;
+    gr += g * r;
+    r2 += r * r;
+    if (!first) grp += g * (double)rp[k];
+    rv[k] = (T)r;
+    pv[k] = (T)g;
+  }
+  gr = block_sum(gr, red);
+  grp = block_sum(grp, red);
+  r2 = block_sum(r2, red);
+  double gamma = 0.0;
+  if (!first) {
+    double den = P.bv[BV_GRP * P.nb + i];
+    gamma = den > 0.0 ? fmax(0.0, (gr - grp) / den) : 0.0;
+  }
+  if (gamma != 0.0) {
+    for (int k = threadIdx.x; k < P.npw; k += blockDim.x) pv[k] = (T)((double)pv[k] + gamma * (double)pp[k]);
+  }
+  if (threadIdx.x == 0) {
+    P.bv[BV_GR * P.nb + i] = gr;
+    P.bv[BV_RES * P.nb + i] = sqrt(r2);
+    P.bv[BV_GAMMA * P.nb + i] = gamma;
+    P.bv[BV_EKIN * P.nb + i] = ek;
+  }
+}
+
+// PP = P (history direction, unnormalised); P = P / |P|.
+template <typename T>
+__global__ void __launch_bounds__(BAND_THREADS) k_normalize(KArgs ka, int pr, int ppr) {
+  __shared__ double red[33];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int i = blockIdx.x - ka.start[p];
+  const size_t off = (size_t)i * P.ld;
+  T* pv = reinterpret_cast<T*>(P.wb[pr]) + off;
+  T* pp = reinterpret_cast<T*>(P.wb[ppr]) + off;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) s += (double)pv[k] * (double)pv[k];
+  s = sqrt(block_sum(s, red));
+  const double inv = s > 1e-150 ? 1.0 / s : 0.0;
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
+    T v = pv[k];
+    pp[k] = v;
+    pv[k] = (T)((double)v * inv);
+  }
+  if (threadIdx.x == 0) P.bv[BV_PNORM * P.nb + i] = s;
+}
+
+// Line minimisation (line 13): in span{x, p} (p unit, p orthogonal to x) the Rayleigh
+// quotient is a cos^2 + 2 b sin cos + c sin^2; theta = atan2(-2b, c - a)/2 minimises it.
+template <typename T>
+__global__ void __launch_bounds__(BAND_THREADS) k_line_min(KArgs ka, int xr, int hxr, int pr, int hpr) {
+  __shared__ double red[33];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int i = blockIdx.x - ka.start[p];
+  const size_t off = (size_t)i * P.ld;
+  T* x = reinterpret_cast<T*>(P.wb[xr]) + off;
+  T* hx = reinterpret_cast<T*>(P.wb[hxr]) + off;
+  const T* pv = reinterpret_cast<const T*>(P.wb[pr]) + off;
+  const T* hp = reinterpret_cast<const T*>(P.wb[hpr]) + off;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
+    double xv = x[k], pk = pv[k];
+    a += xv * (double)hx[k];
+    b += pk * (double)hx[k];
+    c += pk * (double)hp[k];
+  }
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  c = block_sum(c, red);
+  double th = 0.0;
+  if (P.bv[BV_PNORM * P.nb + i] > 1e-150) th = 0.5 * atan2(-2.0 * b, c - a);
+  const double lim = 0.25 * PI;
+  th = fmin(fmax(th, -lim), lim);
+  const T cs = (T)cos(th), sn = (T)sin(th);
+  if (th != 0.0) {
+    for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
+      x[k] = cs * x[k] + sn * pv[k];
+      hx[k] = cs * hx[k] + sn * hp[k];
+    }
+  }
+  if (threadIdx.x == 0) {
+    P.bv[BV_THETA * P.nb + i] = th;
+    P.bv[BV_A * P.nb + i] = a;
+    P.bv[BV_B * P.nb + i] = b;
+    P.bv[BV_C * P.nb + i] = c;
+  }
+}
+
+// Random start (Sec. II D: the CG "begins with an initial set of wavefunctions"):
+// splitmix64 (Steele, Lea & Flood, OOPSLA 2014) of (seed, band, component), uniform in
+// [-1/2, 1/2), damped by 1/(1 + |G|^2/2).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_random_init(KArgs ka, int xr, unsigned long long seed) {
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int i = blockIdx.x - ka.start[p];
+  T* x = reinterpret_cast<T*>(P.wb[xr]) + (size_t)i * P.ld;
+  for (int k = threadIdx.x; k < P.ld; k += blockDim.x) {
+    double v = 0.0;
+    if (k < P.npw) {
+      unsigned long long h = splitmix64(seed ^ splitmix64(((unsigned long long)i << 32) | (unsigned)k));
+      v = ((double)(h >> 11) * (1.0 / 9007199254740992.0) - 0.5) / (1.0 + P.ekin[k]);
+    }
+    x[k] = (T)v;
+  }
+}
+
+// Host <-> packed buffers (rows of npw doubles) for the component entry points.
+template <typename T>
+__global__ void k_copy_in(KArgs ka, int role, const double* src, int nvec) {
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  const Prob& P = ka.probs[p];
+  const int i = blockIdx.x - ka.start[p];
+  T* x = reinterpret_cast<T*>(P.wb[role]) + (size_t)i * P.ld;
+  for (int k = threadIdx.x; k < P.ld; k += blockDim.x)
+    x[k] = (i < nvec && k < P.npw) ? (T)src[(size_t)i * P.npw + k] : T(0);
+}
+template <typename T>
+__global__ void k_copy_out(KArgs ka, int role, double* dst, int nvec) {
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  const Prob& P = ka.probs[p];
+  const int i = blockIdx.x - ka.start[p];
+  if (i >= nvec) return;
+  const T* x = reinterpret_cast<const T*>(P.wb[role]) + (size_t)i * P.ld;
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) dst[(size_t)i * P.npw + k] = (double)x[k];
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz in FP64, one CTA per problem (lines 3, 14, 16).
+//   S = L L^T (Cholesky), C = L^-1 Hs L^-T, C = V diag(eps) V^T (cyclic Jacobi,
+//   round-robin parallel ordering; Golub & Van Loan, Alg. 8.4.3), Tm = L^-T V,
+//   so that X Tm is orthonormal and diagonalises H in the subspace.
+// Matrices: A, L, V in shared memory when 3 nb^2 doubles fit, else in global scratch.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, double* gscratch, size_t gstride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[33];
+  __shared__ double cs_c[256], cs_s[256];
+  __shared__ int pr_p[256], pr_q[256];
+  __shared__ int flag;
+  const int p = blockIdx.x;
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int n = P.nb;
+  double *A, *L, *V;
+  if (use_smem) {
+    A = reinterpret_cast<double*>(smem_raw);
+  } else {
+    A = gscratch + (size_t)p * gstride;
+  }
+  L = A + n * n;
+  V = L + n * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) flag = 0;
+  // symmetrised inputs
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    L[e] = 0.5 * (P.S[i * n + j] + P.S[j * n + i]);
+    A[e] = 0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]);
+  }
+  __syncthreads();
+  // Cholesky of L in place (lower triangle)
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      double d = L[k * n + k];
+      if (!(d > 0.0)) { flag = 1; d = 1.0; }
+      L[k * n + k] = sqrt(d);
+    }
+    __syncthreads();
+    const double dk = L[k * n + k];
+    for (int i = k + 1 + tid; i < n; i += nt) L[i * n + k] /= dk;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) L[i * n + j] -= L[i * n + k] * L[j * n + k];
+    }
+    __syncthreads();
+  }
+  // L := L^-1 (lower), row by row: X[i][j] = -(sum_{k=j}^{i-1} L[i][k] X[k][j]) / L[i][i]
+  // done out of place into V, then copied back.
+  for (int e = tid; e < n * n; e += nt) V[e] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < n; ++i) {
+    const double lii = L[i * n + i];
+    for (int j = tid; j <= i; j += nt) {
+      if (j == i) {
+        V[i * n + i] = 1.0 / lii;
+      } else {
+        double s = 0.0;
+        for (int k = j; k < i; ++k) s += L[i * n + k] * V[k * n + j];
+        V[i * n + j] = -s / lii;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * n; e += nt) L[e] = V[e];
+  __syncthreads();
+  // V := A L^T ; A := L V   (C = L^-1 Hs L^-T, symmetric)
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    double s = 0.0;
+    for (int k = 0; k <= j; ++k) s += A[i * n + k] * L[j * n + k];
+    V[e] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    double s = 0.0;
+    for (int k = 0; k <= i; ++k) s += L[i * n + k] * V[k * n + j];
+    A[e] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    if (j > i) {
+      double s = 0.5 * (A[i * n + j] + A[j * n + i]);
+      A[i * n + j] = s;
+      A[j * n + i] = s;
+    }
+  }
+  for (int e = tid; e < n * n; e += nt) V[e] = (e / n == e % n) ? 1.0 : 0.0;
+  __syncthreads();
+  // cyclic Jacobi, round-robin pairing over m = n rounded up to even
+  const int m = n + (n & 1);
+  const int half = m / 2;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int e = tid; e < n * n; e += nt) {
+      int i = e / n, j = e % n;
+      double v = A[e] * A[e];
+      if (i == j) dia += v; else off += v;
+    }
+    off = block_sum(off, red);
+    dia = block_sum(dia, red);
+    if (off <= 1e-30 * dia || off == 0.0) break;
+    for (int r = 0; r < m - 1; ++r) {
+      if (tid < half) {
+        // tournament: position 0 fixed, positions 1..m-1 rotate by r
+        int a = tid, b = m - 1 - tid;
+        int pa = a == 0 ? 0 : 1 + (a - 1 + r) % (m - 1);
+        int pb = b == 0 ? 0 : 1 + (b - 1 + r) % (m - 1);
+        int pp = min(pa, pb), qq = max(pa, pb);
+        double c = 1.0, s = 0.0;
+        if (qq < n) {
+          double apq = A[pp * n + qq];
+          if (fabs(apq) > 1e-300) {
+            double tau = (A[qq * n + qq] - A[pp * n + pp]) / (2.0 * apq);
+            double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        cs_c[tid] = c;
+        cs_s[tid] = s;
+        pr_p[tid] = pp;
+        pr_q[tid] = qq;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < half * n; e += nt) {
+        int k = e / n, j = e % n;
+        int pp = pr_p[k], qq = pr_q[k];
+        double s = cs_s[k];
+        if (qq >= n || s == 0.0) continue;
+        double c = cs_c[k];
+        double ap = A[pp * n + j], aq = A[qq * n + j];
+        A[pp * n + j] = c * ap - s * aq;
+        A[qq * n + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = tid; e < half * n; e += nt) {
+        int k = e / n, i = e % n;
+        int pp = pr_p[k], qq = pr_q[k];
+        double s = cs_s[k];
+        if (qq >= n || s == 0.0) continue;
+        double c = cs_c[k];
+        double ap = A[i * n + pp], aq = A[i * n + qq];
+        A[i * n + pp] = c * ap - s * aq;
+        A[i * n + qq] = s * ap + c * aq;
+        double vp = V[i * n + pp], vq = V[i * n + qq];
+        V[i * n + pp] = c * vp - s * vq;
+        V[i * n + qq] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // ascending order: rank of each eigenvalue
+  for (int j = tid; j < n; j += nt) {
+    double ej = A[j * n + j];
+    int rank = 0;
+    for (int k = 0; k < n; ++k) {
+      double ek = A[k * n + k];
+      rank += (ek < ej) || (ek == ej && k < j);
+    }
+    P.eps[rank] = ej;
+    P.bv[BV_TMP0 * n + j] = (double)rank;
+  }
+  __syncthreads();
+  // Tm[:, rank(j)] = L^T V[:, j]   (L holds L^-1)
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    double s = 0.0;
+    for (int k = i; k < n; ++k) s += L[k * n + i] * V[k * n + j];
+    int col = (int)P.bv[BV_TMP0 * n + j];
+    P.Tm[i * n + col] = s;
+  }
+  if (tid == 0 && flag) P.status[0] = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Occupations: integer (kT = 0) or Fermi-Dirac with mu from sum f = N_el; entropy
+// S = -2 sum [x ln x + (1-x) ln(1-x)], x = f/2.  One warp per problem.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fd_x(double e, double mu, double kT) {
+  double a = (e - mu) / kT;
+  if (a > 700.0) return 0.0;
+  if (a < -700.0) return 1.0;
+  return 1.0 / (1.0 + exp(a));
+}
+
+__global__ void k_occupations(KArgs ka) {
+  const int p = blockIdx.x;
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int n = P.nb, lane = threadIdx.x;
+  const double kT = P.kT, nel = P.nel;
+  const double* eps = P.eps;
+  if (kT <= 0.0) {
+    const int nocc = (int)llround(nel * 0.5);
+    for (int i = lane; i < n; i += 32) P.occ[i] = i < nocc ? 2.0 : 0.0;
+    if (lane == 0) {
+      P.scal[SC_MU] = nocc < n ? 0.5 * (eps[nocc - 1] + eps[nocc]) : eps[n - 1];
+      P.scal[SC_ENTROPY] = 0.0;
+    }
+    return;
+  }
+  double lo = eps[0] - 40.0 * kT - 1.0, hi = eps[n - 1] + 40.0 * kT + 1.0;
+  double mu = 0.5 * (lo + hi);
+  for (int it = 0; it < 200; ++it) {
+    double cnt = 0.0, der = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      double x = fd_x(eps[i], mu, kT);
+      cnt += 2.0 * x;
+      der += 2.0 * x * (1.0 - x) / kT;
+    }
+    cnt = warp_sum(cnt);
+    der = warp_sum(der);
+    double diff = cnt - nel;
+    if (fabs(diff) < 1e-13 * fmax(1.0, nel)) break;
+    if (diff < 0.0) lo = mu; else hi = mu;
+    double nmu = der > 0.0 ? mu - diff / der : 0.5 * (lo + hi);
+    if (!(nmu > lo && nmu < hi)) nmu = 0.5 * (lo + hi);
+    if (hi - lo < 1e-15 * fmax(1.0, fabs(mu))) break;
+    mu = nmu;
+  }
+  double ent = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    double x = fd_x(eps[i], mu, kT);
+    P.occ[i] = 2.0 * x;
+    if (x > 0.0) ent += x * log(x);
+    if (x < 1.0) ent += (1.0 - x) * log1p(-x);
+  }
+  ent = warp_sum(ent);
+  if (lane == 0) {
+    P.scal[SC_MU] = mu;
+    P.scal[SC_ENTROPY] = -2.0 * ent;
+  }
+}
+
+// End of one CG step: the current <g, r> becomes the previous one; history is valid.
+__global__ void k_finish_cg(KArgs ka) {
+  const int p = blockIdx.x;
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  for (int i = threadIdx.x; i < P.nb; i += blockDim.x) P.bv[BV_GRP * P.nb + i] = P.bv[BV_GR * P.nb + i];
+  if (threadIdx.x == 0) P.scal[SC_FIRSTCG] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride) {
+  if (!L.map.total) return;
+  k_gemm_tn<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, arole, bkind, brole, part, stride);
+}
+void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride) {
+  if (!L.map.total) return;
+  k_gemm_tn_reduce<<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, bkind, dst, part, stride);
+}
+template <typename T>
+void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta) {
+  if (!L.map.total) return;
+  k_gemm_nn<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, arole, msel, yrole, alpha, beta);
+}
+template <typename T>
+void launch_band_kinetic(const Launch& L, int xrole) {
+  if (!L.map.total) return;
+  k_band_kinetic<T><<<L.map.total, BAND_THREADS, 0, L.stream>>>(L.ka, xrole);
+}
+template <typename T>
+void launch_cg_precond(const Launch& L, int x, int hx, int p, int r, int pp, int rp) {
+  if (!L.map.total) return;
+  k_cg_precond<T><<<L.map.total, BAND_THREADS, 0, L.stream>>>(L.ka, x, hx, p, r, pp, rp);
+}
+template <typename T>
+void launch_normalize(const Launch& L, int p, int pp) {
+  if (!L.map.total) return;
+  k_normalize<T><<<L.map.total, BAND_THREADS, 0, L.stream>>>(L.ka, p, pp);
+}
+template <typename T>
+void launch_line_min(const Launch& L, int x, int hx, int p, int hp) {
+  if (!L.map.total) return;
+  k_line_min<T><<<L.map.total, BAND_THREADS, 0, L.stream>>>(L.ka, x, hx, p, hp);
+}
+template <typename T>
+void launch_random_init(const Launch& L, int xrole, unsigned long long seed) {
+  if (!L.map.total) return;
+  k_random_init<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, xrole, seed);
+}
+template <typename T>
+void launch_copy_in(const Launch& L, int role, const double* src, int nvec) {
+  if (!L.map.total) return;
+  k_copy_in<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, role, src, nvec);
+}
+template <typename T>
+void launch_copy_out(const Launch& L, int role, double* dst, int nvec) {
+  if (!L.map.total) return;
+  k_copy_out<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, role, dst, nvec);
+}
+void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride) {
+  k_rr<<<L.ka.nprob, RR_THREADS, use_smem ? smem : 0, L.stream>>>(L.ka, use_smem, gscratch, gstride);
+}
+void launch_occupations(const Launch& L) { k_occupations<<<L.ka.nprob, 32, 0, L.stream>>>(L.ka); }
+void launch_finish_cg(const Launch& L) { k_finish_cg<<<L.ka.nprob, 128, 0, L.stream>>>(L.ka); }
+void linalg_set_smem_limits(size_t bytes) {
+  cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define INST(T)                                                                                  \
+  template void launch_gemm_tn<T>(const Launch&, int, int, int, int, double*, size_t);          \
+  template void launch_gemm_nn<T>(const Launch&, int, int, int, int, double, double);           \
+  template void launch_band_kinetic<T>(const Launch&, int);                                     \
+  template void launch_cg_precond<T>(const Launch&, int, int, int, int, int, int);              \
+  template void launch_normalize<T>(const Launch&, int, int);                                   \
+  template void launch_line_min<T>(const Launch&, int, int, int, int);                          \
+  template void launch_random_init<T>(const Launch&, int, unsigned long long);                  \
+  template void launch_copy_in<T>(const Launch&, int, const double*, int);                      \
+  template void launch_copy_out<T>(const Launch&, int, double*, int);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace sgo

@@ -1,0 +1,98 @@
+// Kernel launch interface between the host engine and the device kernels.
+#pragma once
+
+#include "sgo_internal.cuh"
+
+namespace sgo {
+
+// FFT kernel geometry
+constexpr int QCP = 4;                 // column pairs per z-column CTA (<= 8 columns)
+constexpr int ZCOL_THREADS = 128;
+constexpr int QZ = 8;                  // grid columns per z CTA
+constexpr int DENS_MAXP = 16;          // density accumulators per thread: N1 * N2 <= 16 * blockDim
+constexpr int PLANE_THREADS_MAX = 512;  // so N1 * N2 <= 8192 per plane
+// GEMM geometry
+constexpr int TN_TILE = 32;
+constexpr int TN_KC = 256;             // K chunk of one split-K partial
+constexpr int NN_TILE = 64;
+constexpr int BAND_THREADS = 256;
+constexpr int GRID_CHUNK = 4096;       // grid points per reduction CTA
+constexpr int RR_THREADS = 256;
+
+struct KArgs {
+  const Prob* probs;
+  const int* start;
+  int nprob;
+  const int* active;
+};
+
+struct Launch {
+  KArgs ka;
+  WorkMap map;
+  cudaStream_t stream;
+  int max_n1, max_n2, max_n3, max_n12, max_nb;
+  int plane_threads;
+};
+
+// operands of the subspace GEMMs
+enum { OPK_WB = 0, OPK_B = 1, OPK_DB = 2 };
+enum { DD_S = 0, DD_HS, DD_CM, DD_TM, DD_PROJ, DD_DPROJ, DD_PROJ_D };
+
+// k_fft.cu
+template <typename T> void launch_wave_to_cols(const Launch& L, int src);
+template <typename T> void launch_cols_to_wave(const Launch& L, int src, int dst);
+template <typename T> void launch_plane_vpsi(const Launch& L);
+template <typename T> void launch_plane_density(const Launch& L, const double* occ_override);
+void launch_grid_plane_fft(const Launch& L, int which, int sign);
+void launch_grid_z_fft(const Launch& L, int which, int sign);
+void fft_set_smem_limits(size_t bytes);
+
+// k_linalg.cu
+template <typename T>
+void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride);
+void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride);
+template <typename T>
+void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta);
+template <typename T> void launch_band_kinetic(const Launch& L, int xrole);
+template <typename T> void launch_cg_precond(const Launch& L, int x, int hx, int p, int r, int pp, int rp);
+template <typename T> void launch_normalize(const Launch& L, int p, int pp);
+template <typename T> void launch_line_min(const Launch& L, int x, int hx, int p, int hp);
+template <typename T> void launch_random_init(const Launch& L, int xrole, unsigned long long seed);
+template <typename T> void launch_copy_in(const Launch& L, int role, const double* src, int nvec);
+template <typename T> void launch_copy_out(const Launch& L, int role, double* dst, int nvec);
+void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride);
+void launch_occupations(const Launch& L);
+void launch_finish_cg(const Launch& L);
+void linalg_set_smem_limits(size_t bytes);
+
+// k_grid.cu  (grid sources/destinations: 0 rho_in, 1 rho_out, 2 resid, 3 vion_r)
+constexpr int GRID_EW_POINTS = 1024;   // points per elementwise grid CTA
+void launch_real_to_grid(const Launch& L, int src, int which);
+void launch_grid_real_part(const Launch& L, int which, int dst);
+void launch_hartree_g(const Launch& L, int which);
+void launch_export_grid(const Launch& L, int sel, double* out);
+template <typename T> void launch_veff(const Launch& L, const double* user_v);
+void launch_kerker(const Launch& L, double q0);
+void launch_vion_g(const Launch& L);
+void launch_rho0_g(const Launch& L);
+void launch_pulay_store(const Launch& L);
+void launch_pulay_mix(const Launch& L, int stage, double a);
+void launch_grid_energies(const Launch& Lchunks, double* part, int maxchunk);
+void launch_grid_energies_reduce(const Launch& L, const double* part, int maxchunk);
+void launch_finish_iteration(const Launch& L, double tol_e, double tol_rho, int count_iter);
+void launch_pulay_gram(const Launch& Lchunks, double* part, int maxchunk, int hist);
+void launch_pulay_solve(const Launch& L, const double* part, int maxchunk, int hist);
+template <typename T> void launch_build_projectors(const Launch& Latoms, int deriv);
+void launch_local_forces(const Launch& Latom_chunks, int maxchunk);
+void launch_force_total(const Launch& L, int maxchunk);
+
+// k_setup.cu
+void launch_basis_count(const Launch& Lcols);
+void launch_basis_scan(const Launch& L);
+void launch_basis_fill(const Launch& Lcols);
+void launch_roots(const Launch& L);
+void launch_phases(const Launch& Latoms);
+void launch_vloc_table(const Launch& Lew);
+void launch_ewald(const Launch& Lsg, const Launch& Latoms, const Launch& Lprob);
+
+}  // namespace sgo

@@ -1,0 +1,203 @@
+"""CUDA path vs the FP64 CPU oracle, through the C ABI.
+
+Tolerances: the plain FP64 path reaches the oracle's fixed point to the SCF
+tolerance (energy 1e-7 Ha/atom, forces 1e-6 Ha/bohr here).  The mixed path (FP32
+H.psi, FFTs and GEMM products, FP64 sums) must stay within 1e-5 Ha/atom and
+1e-4 Ha/bohr.  Component kernels (H.psi, density) are compared element by element.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import dft
+from tests.packing import full_from_packed
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sgo():
+    from paper_1603_02732_gb300 import build
+    build.build()
+    import paper_1603_02732_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+def _struct(grid=None, ecut=3.5, nat=2, seed=7, kT=0.01, nbands=None):
+    st = workloads.tiny(nat=nat, ecut=ecut, seed=seed, kT=kT, nbands=nbands)
+    if grid is not None:
+        st = dataclasses.replace(st, fft=tuple(grid))
+    return st
+
+
+GRIDS = [None, (10, 12, 15), (16, 18, 20), (24, 24, 24)]
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_apply_hamiltonian_matches_dense_h(sgo, grid, precision):
+    st = _struct(grid=grid)
+    ctx = sgo.Context(st, precision=precision)
+    m = dft.Model(st)
+    miller = ctx.basis()
+    # the packed basis is exactly the oracle's Ecut sphere (half + inversion)
+    full = set(map(tuple, miller.tolist())) | set(map(tuple, (-miller).tolist()))
+    assert full == set(map(tuple, m.m.tolist()))
+    rng = np.random.default_rng(11)
+    veff = rng.normal(size=m.grid) * 0.3
+    x = rng.normal(size=(st.nbands, ctx.npw))
+    y = ctx.apply_hamiltonian(veff, x)
+    H = dft.dense_h(m, veff, dft.projectors(m, st.pos))
+    c = full_from_packed(m, miller, x)
+    y_ref = full_from_packed(m, miller, np.zeros_like(x))  # shape only
+    y_ref = H @ c
+    y_full = full_from_packed(m, miller, y)
+    tol = 1e-11 if precision == "fp64" else 2e-5
+    scale = np.abs(y_ref).max()
+    assert np.abs(y_full - y_ref).max() < tol * scale
+
+
+@pytest.mark.parametrize("grid", [None, (10, 12, 15), (18, 20, 24)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_density_matches_oracle(sgo, grid, precision):
+    st = _struct(grid=grid, nbands=7)
+    ctx = sgo.Context(st, precision=precision)
+    m = dft.Model(st)
+    miller = ctx.basis()
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(7, ctx.npw))
+    x, _ = np.linalg.qr(x.T)
+    x = x.T.copy()
+    occ = np.array([2.0, 2.0, 1.7, 1.1, 0.4, 0.0, 0.05])
+    rho = ctx.density_of(x, occ)
+    ref = dft.density(m, full_from_packed(m, miller, x), occ)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert np.abs(rho - ref).max() < tol * np.abs(ref).max()
+    assert abs(m.omega / m.N * rho.sum() - occ.sum()) < (1e-10 if precision == "fp64" else 1e-5)
+
+
+def _compare(st, res_gpu, ref, e_tol, f_tol):
+    F, forces = res_gpu
+    dE = abs(F - ref.free_energy) / st.natoms
+    dF = float(np.abs(forces - ref.forces).max())
+    assert dE < e_tol, (F, ref.free_energy, dE)
+    assert dF < f_tol, (forces, ref.forces, dF)
+
+
+@pytest.mark.parametrize("kT,nbands", [(0.01, None), (0.0, 6)])
+def test_scf_tiny_fp64(sgo, kT, nbands):
+    st = _struct(kT=kT, nbands=nbands, ecut=3.0)
+    ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)
+    ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=120)
+    _compare(st, ctx.energy_forces(), ref, 1e-8, 1e-6)
+    eig, occ = ctx.eigen()
+    assert np.abs(eig - ref.eig).max() < 1e-7
+    assert np.abs(occ - ref.occ).max() < 1e-6
+    t = ctx.terms()
+    for k_gpu, k_ref in [("kinetic", "kinetic"), ("nonlocal", "nonlocal_"), ("local", "local"),
+                         ("hartree", "hartree"), ("xc", "xc"), ("ewald", "ewald"), ("minus_ts", "minus_ts")]:
+        assert abs(t[k_gpu] - ref.terms[k_ref]) < 1e-6, k_gpu
+    rho = ctx.density()
+    assert np.abs(rho - ref.rho).max() < 1e-6 * np.abs(ref.rho).max()
+
+
+def test_scf_tiny_mixed(sgo):
+    st = _struct(ecut=3.0)
+    ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)
+    ctx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7, scf_tol_rho=1e-5, max_scf=120)
+    _compare(st, ctx.energy_forces(), ref, 1e-5, 1e-4)
+
+
+@pytest.fixture(scope="module")
+def diamond_ref():
+    st = workloads.diamond8()
+    return st, oracle.scf(st, mix=0.7, q0=0.0)
+
+
+def test_diamond8_fp64(sgo, diamond_ref):
+    """8-atom diamond cell, Ecut 10 Ha, 32^3, 20 bands, integer occupations (FP64)."""
+    st, ref = diamond_ref
+    ctx = sgo.Context(st, precision="fp64", mix_alpha=0.7, kerker_q0=0.0)
+    _compare(st, ctx.energy_forces(), ref, 1e-7, 1e-5)
+    eig, _ = ctx.eigen()
+    assert np.abs(eig[:16] - ref.eig[:16]).max() < 1e-6
+
+
+def test_diamond8_mixed(sgo, diamond_ref):
+    st, ref = diamond_ref
+    ctx = sgo.Context(st, precision="mixed", mix_alpha=0.7, kerker_q0=0.0, scf_tol_e=1e-6, scf_tol_rho=1e-5)
+    _compare(st, ctx.energy_forces(), ref, 1e-5, 1e-4)
+
+
+def test_batch_equals_single_fp64(sgo):
+    """Every batch member's FP64 result equals its own single-structure run bit for bit."""
+    sts = [_struct(seed=s, ecut=3.0) for s in (3, 4, 9)]
+    sts[1] = _struct(seed=4, ecut=3.5, nat=3, grid=(16, 18, 20))
+    opts = dict(precision="fp64", scf_tol_e=1e-10, scf_tol_rho=1e-8, max_scf=100)
+    singles = []
+    for st in sts:
+        singles.append(sgo.Context(st, **opts).energy_forces())
+    ctxs = [sgo.Context(st, **opts) for st in sts]
+    E, F, status = sgo.Batch(ctxs).energy_forces()
+    assert list(status) == [0, 0, 0]
+    for i in range(3):
+        assert E[i] == singles[i][0]
+        assert np.array_equal(F[i], singles[i][1])
+    # order of members does not change results
+    E2, F2, _ = sgo.Batch([sgo.Context(st, **opts) for st in sts[::-1]]).energy_forces()
+    assert np.array_equal(E2[::-1], E)
+
+
+def test_geometry_error_is_reported(sgo):
+    st = _struct()
+    ctx = sgo.Context(st, precision="fp64")
+    bad = st.pos.copy()
+    bad[1] = bad[0] + np.array([0.1, 0.0, 0.0])
+    with pytest.raises(sgo.SgoError) as e:
+        ctx.energy_forces(bad)
+    assert e.value.status == sgo.SGO_ERR_GEOMETRY
+    bad[0, 0] = np.nan
+    with pytest.raises(sgo.SgoError):
+        ctx.energy_forces(bad)
+    # the context stays usable
+    F, _ = ctx.energy_forces(st.pos)
+    assert math.isfinite(F)
+
+
+def test_not_converged_status(sgo):
+    st = _struct()
+    ctx = sgo.Context(st, precision="fp64", max_scf=2, n_nonscf=0)
+    with pytest.raises(sgo.SgoError) as e:
+        ctx.energy_forces()
+    assert e.value.status == sgo.SGO_ERR_NOT_CONVERGED
+
+
+def test_autograd_adjoint(sgo):
+    import torch
+    st = _struct(ecut=3.0)
+    ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9)
+    pos = torch.tensor(st.pos, dtype=torch.float64, requires_grad=True)
+    E = sgo.SgoEnergy.apply(ctx, pos)
+    E.backward()
+    _, F = ctx.energy_forces(st.pos)
+    assert torch.allclose(pos.grad, torch.as_tensor(-F), atol=1e-12)
+
+
+def test_forces_match_finite_differences_gpu(sgo):
+    """FP64 path: F = -dF/dR by central differences (h = 1e-3 bohr)."""
+    st = _struct(ecut=3.0)
+    opts = dict(precision="fp64", scf_tol_e=1e-12, scf_tol_rho=1e-10, max_scf=150)
+    ctx = sgo.Context(st, **opts)
+    _, F = ctx.energy_forces()
+    h = 1e-3
+    for I, a in [(0, 0), (1, 2)]:
+        p = st.pos.copy(); p[I, a] += h
+        ep, _ = ctx.energy_forces(p)
+        p[I, a] -= 2 * h
+        em, _ = ctx.energy_forces(p)
+        assert abs(-(ep - em) / (2 * h) - F[I, a]) < 2e-6

@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Throughput of the plane-wave DFT energy + force evaluation (the call every DE
+candidate and relaxation step of the paper makes, Sec. II A-D).
+
+Workload: the 64-member DE population (cells of 8-32 Z_val=4 atoms, volume
+135 bohr^3/atom +-20%, Ecut 12 Ha, FD kT 0.01 Ha; uneven plane-wave counts), one
+step = one batched, cold-start, mixed-precision energy+force evaluation of all 64
+members through the C ABI.  Metric: evaluations/s.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints ONE JSON line on rank 0.  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload (the smallest member, one evaluation per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DFT energy+force evals/s (batched, mixed prec) vs plain FP64, ≤1e-5 Ha/atom"
+WORKLOAD = "de_population_64"
+MEMBERS = 64
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _population(rank):
+    import workloads
+    return workloads.de_population(MEMBERS, start=MEMBERS * rank)
+
+
+def _smallest(pop):
+    return min(range(len(pop)), key=lambda i: (pop[i].natoms, i))
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def _oracle_eval(st):
+    import oracle
+    t = time.perf_counter()
+    r = oracle.scf(st)
+    return time.perf_counter() - t, r
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    pop = _population(0)
+    i = _smallest(pop)
+    st = pop[i]
+    for _ in range(args.warmup):
+        _oracle_eval(st)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = _oracle_eval(st)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps / total
+    sample = f"member {i} ({st.natoms} atoms) of the population, one oracle evaluation per step"
+    line = dict(metric=METRIC, value=value, unit="evals/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * total / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, members=MEMBERS, sample=sample, precision="fp64 (CPU oracle)"),
+                cpu_baseline=dict(value=value, unit="evals/s", cores=_cores(), kind="oracle", sample=sample),
+                e2e=dict(value=value, unit="evals/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                mhz.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, n in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not mhz:
+            return None
+        return dict(sm_mhz=float(np.median(mhz)), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(mhz))
+
+
+def _tols(prec, st):
+    """SCF stopping rule: FP64 path |dF| < 1e-8 Ha and residual < 1e-7; mixed path (FP32
+    noise floor) |dF| < 1e-7 Ha per atom and residual < 1e-5 -- far inside 1e-5 Ha/atom."""
+    if prec == "mixed":
+        return dict(scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5)
+    return dict(scf_tol_e=1e-8, scf_tol_rho=1e-7)
+
+
+def _peaks():
+    try:
+        with open(MEASURED) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+    import paper_1603_02732_gb300 as sgo
+    from paper_1603_02732_gb300 import build
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    sgo.load_library()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    pop = _population(rank)
+    prec = args.precision
+    ctxs = [sgo.Context(st, precision=prec, **_tols(prec, st)) for st in pop]
+    batch = sgo.Batch(ctxs)
+    pos_host = [np.ascontiguousarray(st.pos, dtype=np.float64) for st in pop]
+    pos_dev = torch.tensor(np.concatenate([p.reshape(-1) for p in pos_host]), dtype=torch.float64, device=dev)
+    e_dev = torch.zeros(MEMBERS, dtype=torch.float64, device=dev)
+    f_dev = torch.zeros_like(pos_dev)
+    s_dev = torch.zeros(MEMBERS, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step_device():
+        batch.energy_forces_device(pos_dev.data_ptr(), e_dev.data_ptr(), f_dev.data_ptr(), s_dev.data_ptr())
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    batch.launches()
+    batch.timer(args.kernel)
+    clocks = Clocks(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step_device()
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = batch.launches() // max(args.steps, 1)
+    kt = batch.timer_read()
+    batch.timer(None)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    status = s_dev.cpu().numpy()
+    iters = [c.info()["n_iter"] for c in ctxs]
+    n_ok = int(np.sum(status == 0))
+    value = ws * MEMBERS * args.steps / (total_ms / 1e3)
+
+    # end to end through the host-pointer C-ABI call (H2D positions, D2H energies + forces)
+    h2d = int(sum(p.nbytes for p in pos_host))
+    d2h = int(MEMBERS * 8 + sum(p.nbytes for p in pos_host) + MEMBERS * 4)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        E, F, st = batch.energy_forces(pos_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = ws * MEMBERS * e2e_steps / e2e_s
+
+    out = None
+    if rank == 0:
+        peaks, src = _peaks()
+        kname = args.kernel
+        ach_tflops = kt["flops"] / (kt["ms"] / 1e3) / 1e12 if kt["ms"] > 0 else 0.0
+        ach_gbs = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else 0.0
+        roofline = dict(kernel=kname, bound="alu", achieved=ach_tflops, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                        frac=ach_tflops / FP32_PEAK_TFLOPS, traffic=None,
+                        peak_source="FP32 CUDA-core peak from unit counts (152 SM x 128 lanes x 2 x 2.07 GHz)",
+                        hbm_achieved_gbs=ach_gbs, hbm_peak_gbs=peaks.get("hbm_gbs"), hbm_peak_source=src,
+                        launches=kt["launches"], avg_launch_ms=kt["ms"] / max(kt["launches"], 1),
+                        share_of_step=kt["ms"] / total_ms if total_ms > 0 else None)
+        line = dict(metric=METRIC, value=value, unit="evals/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype="f32+f64" if prec == "mixed" else "f64", data="synthetic",
+                    config=dict(workload=WORKLOAD, members=MEMBERS, atoms="8-32", ecut_ha=12.0, kT_ha=0.01,
+                                precision=prec, start="cold (atomic density, random wavefunctions)",
+                                l2="flushed by a 256 MiB write before every timed step",
+                                converged=f"{n_ok}/{MEMBERS}",
+                                scf_iterations=dict(mean=float(np.mean(iters)), max=int(np.max(iters)))),
+                    e2e=dict(value=e2e_val, unit="evals/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+                    gpu_launches=int(launches), roofline=roofline, clocks=clk)
+        out = line
+    if args.fp64_compare and rank == 0:
+        # the plain FP64 GPU path on the same population: one timed step after one warm-up
+        ctx64 = [sgo.Context(st, precision="fp64", **_tols("fp64", st)) for st in pop]
+        b64 = sgo.Batch(ctx64)
+        b64.energy_forces()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E64, _, st64 = b64.energy_forces()
+        torch.cuda.synchronize()
+        dt64 = time.perf_counter() - t0
+        it64 = [c.info()["n_iter"] for c in ctx64]
+        out["fp64_path"] = dict(value=MEMBERS / dt64, unit="evals/s", steps=1,
+                                converged=f"{int(np.sum(st64 == 0))}/{MEMBERS}",
+                                scf_iterations=dict(mean=float(np.mean(it64)), max=int(np.max(it64))),
+                                speedup_mixed_over_fp64=e2e_val / (MEMBERS / dt64),
+                                max_abs_dE_per_atom_mixed_vs_fp64=float(np.max(np.abs(E - E64) /
+                                                                               np.array([c.natoms for c in ctxs]))))
+        del b64, ctx64
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        i = _smallest(pop)
+        dt, ref = _oracle_eval(pop[i])
+        out["cpu_baseline"] = dict(value=1.0 / dt, unit="evals/s", cores=_cores(), kind="oracle",
+                                   sample=f"one evaluation of member {i} ({pop[i].natoms} atoms), {dt:.1f} s")
+        Fi, fi = E[i], F[i]
+        out["accuracy_vs_oracle"] = dict(member=i, dE_per_atom=abs(Fi - ref.free_energy) / pop[i].natoms,
+                                         max_dF=float(np.max(np.abs(fi - ref.forces))))
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--kernel", default="plane_vpsi", help="kernel class timed live for the roofline")
+    ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 GPU path")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

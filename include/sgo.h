@@ -128,6 +128,19 @@ SGO_API sgo_status sgo_energy_forces_batch(sgo_batch* b, const double* const* po
 SGO_API sgo_status sgo_energy_forces_batch_device(sgo_batch* b, const double* pos_dev, double* energies_dev,
                                           double* forces_dev, int* status_dev);
 
+/* Live timing of one kernel class during later batch calls: CUDA events are recorded
+ * on the batch stream around every launch of that class.  kernel: "plane_vpsi",
+ * "wave_to_cols", "cols_to_wave", "plane_density", "gemm_tn", "gemm_nn", "rr", or
+ * NULL to stop.  Resets the accumulators.  Instrumentation, not part of the method. */
+SGO_API sgo_status sgo_batch_timer(sgo_batch* b, const char* kernel);
+
+/* Read and keep accumulating: out[0] total ms, out[1] launches, out[2] algorithmic
+ * bytes, out[3] algorithmic flops of the timed launches (active members only). */
+SGO_API sgo_status sgo_batch_timer_read(sgo_batch* b, double out[4]);
+
+/* Kernel launches the batch issued since the previous call (then reset to 0). */
+SGO_API sgo_status sgo_batch_launches(sgo_batch* b, long long* count);
+
 /* Eigenvalues and occupations of the last SCF (nbands doubles each; either may be NULL). */
 SGO_API sgo_status sgo_get_eigen(sgo_ctx* ctx, double* eig, double* occ);
 

@@ -63,6 +63,9 @@ _SIGS = {
     "sgo_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "sgo_energy_forces_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_dp), _dp, ctypes.POINTER(_dp), _ip]),
     "sgo_energy_forces_batch_device": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sgo_batch_timer": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "sgo_batch_timer_read": (ctypes.c_int, [_vp, _dp]),
+    "sgo_batch_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "sgo_get_eigen": (ctypes.c_int, [_vp, _dp, _dp]),
     "sgo_get_terms": (ctypes.c_int, [_vp, _dp]),
     "sgo_get_info": (ctypes.c_int, [_vp, _ip]),
@@ -264,6 +267,21 @@ class Batch:
         _check(self.lib.sgo_energy_forces_batch(self.h, pptr, _ptr(E), fptr, _ptr(st, ctypes.c_int)),
                "sgo_energy_forces_batch")
         return E, forces, st
+
+    def timer(self, kernel: Optional[str]):
+        """Time one kernel class live (CUDA events) during later calls; None stops."""
+        _check(self.lib.sgo_batch_timer(self.h, None if kernel is None else kernel.encode()), "sgo_batch_timer")
+
+    def timer_read(self):
+        out = np.zeros(4)
+        _check(self.lib.sgo_batch_timer_read(self.h, _ptr(out)), "sgo_batch_timer_read")
+        return dict(ms=out[0], launches=int(out[1]), bytes=out[2], flops=out[3])
+
+    def launches(self) -> int:
+        """Kernel launches issued since the previous call."""
+        v = ctypes.c_longlong()
+        _check(self.lib.sgo_batch_launches(self.h, ctypes.byref(v)), "sgo_batch_launches")
+        return int(v.value)
 
     def energy_forces_device(self, pos_dev, energies_dev, forces_dev, status_dev):
         """Device-pointer form: arguments are integer device addresses (e.g. tensor.data_ptr())."""

@@ -179,6 +179,29 @@ sgo_status sgo_energy_forces_batch_device(sgo_batch* b, const double* pos_dev, d
   return b->eng->run_device(pos_dev, energies_dev, forces_dev, status_dev);
 }
 
+sgo_status sgo_batch_timer(sgo_batch* b, const char* kernel) {
+  if (!b) return SGO_ERR_ARG;
+  if (!b->eng->timer_select(kernel)) {
+    sgo::set_error("unknown kernel class");
+    return SGO_ERR_ARG;
+  }
+  return SGO_OK;
+}
+
+sgo_status sgo_batch_timer_read(sgo_batch* b, double out[4]) {
+  if (!b || !out) return SGO_ERR_ARG;
+  int launches = 0;
+  b->eng->timer_read(&out[0], &launches, &out[2], &out[3]);
+  out[1] = launches;
+  return SGO_OK;
+}
+
+sgo_status sgo_batch_launches(sgo_batch* b, long long* count) {
+  if (!b || !count) return SGO_ERR_ARG;
+  *count = b->eng->take_launches();
+  return SGO_OK;
+}
+
 sgo_status sgo_get_eigen(sgo_ctx* c, double* eig, double* occ) {
   if (!c) return SGO_ERR_ARG;
   if (eig) std::memcpy(eig, c->h_eps.data(), sizeof(double) * c->nb);

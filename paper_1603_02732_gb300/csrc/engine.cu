@@ -34,6 +34,30 @@ __global__ void k_set_scal(KArgs ka, int idx, double v, int only_active) {
   if (only_active && !ka.active[p]) return;
   if (threadIdx.x == 0) ka.probs[p].scal[idx] = v;
 }
+// swap two buffer roles of every active problem
+__global__ void k_swap_roles(KArgs ka, int a, int b) {
+  const int p = blockIdx.x;
+  if (!ka.active[p] || threadIdx.x != 0) return;
+  Prob* P = const_cast<Prob*>(ka.probs) + p;
+  int t = P->role[a];
+  P->role[a] = P->role[b];
+  P->role[b] = t;
+}
+// copy the wavefunctions into physical buffer 0 (CTA = (problem, band)), then reset roles
+template <typename T>
+__global__ void k_x_to_buffer0(KArgs ka) {
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  const Prob& P = ka.probs[p];
+  if (P.role[WB_X] == 0) return;
+  const int i = blockIdx.x - ka.start[p];
+  const T* s = wbuf<T>(P, WB_X) + (size_t)i * P.ld;
+  T* d = reinterpret_cast<T*>(P.wb[0]) + (size_t)i * P.ld;
+  for (int k = threadIdx.x; k < P.ld; k += blockDim.x) d[k] = s[k];
+}
+__global__ void k_reset_roles(KArgs ka) {
+  Prob* P = const_cast<Prob*>(ka.probs) + blockIdx.x;
+  if (threadIdx.x < NWB) P->role[threadIdx.x] = threadIdx.x;
+}
 __global__ void k_reset(KArgs ka) {
   const int p = blockIdx.x;
   const Prob& P = ka.probs[p];
@@ -69,6 +93,7 @@ __global__ void k_scatter_pos(KArgs ka, const int* foff, const double* pos) {
 }
 
 int div_up(long a, long b) { return (int)((a + b - 1) / b); }
+double log2d(double x) { return std::log(x) / std::log(2.0); }
 
 bool smooth235(int n) {
   if (n < 1) return false;
@@ -265,6 +290,7 @@ sgo_status ctx_setup(sgo_ctx* c) {
   d.nel = 0.0;
   for (int a = 0; a < d.natom; ++a) d.nel += c->species[c->spec[a]].z_val;
   d.kT = c->opts.kT;
+  for (int i = 0; i < NWB; ++i) d.role[i] = i;
   d.nb = c->nb;
   d.npair = (c->nb + 1) / 2;
   // Ewald parameters: eta from the volume; sums to a relative tail of 1e-16
@@ -389,6 +415,9 @@ sgo_ctx::~sgo_ctx() {
 
 namespace sgo {
 
+const char* const kTimerNames[TK_COUNT] = {"plane_vpsi", "wave_to_cols", "cols_to_wave", "plane_density",
+                                           "gemm_tn",    "gemm_nn",      "rr"};
+
 // ---------------------------------------------------------------------------
 // Engine
 // ---------------------------------------------------------------------------
@@ -411,6 +440,7 @@ WorkMap Engine::make_map(const std::vector<int>& counts) {
 }
 
 Launch Engine::L(const WorkMap& m) const {
+  ++launches_;
   Launch l;
   l.ka = KArgs{d_probs_, m.start ? m.start : m_prob_.start, n_, d_active_};
   l.map = m;
@@ -433,7 +463,6 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
       set_error("all members of a batch must use the same precision");
       return;
     }
-  for (int i = 0; i < NWB; ++i) role_[i] = i;
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
       c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob;
@@ -520,8 +549,104 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
 }
 
 Engine::~Engine() {
+  for (auto& v : ev_) cudaEventDestroy(v);
   for (void* p : allocs_) cudaFree(p);
 }
+
+// ---- live kernel timing ----
+bool Engine::timer_select(const char* name) {
+  timer_kind_ = -1;
+  for (int k = 0; k < TK_COUNT; ++k)
+    if (name && std::strcmp(name, kTimerNames[k]) == 0) timer_kind_ = k;
+  if (timer_kind_ >= 0 && ev_.empty()) {
+    ev_.resize(8192);
+    for (auto& v : ev_) cudaEventCreate(&v);
+    ev_bytes_.resize(ev_.size() / 2);
+    ev_flops_.resize(ev_.size() / 2);
+  }
+  ev_used_ = 0;
+  t_ms_ = t_bytes_ = t_flops_ = 0.0;
+  t_launches_ = 0;
+  return timer_kind_ >= 0 || name == nullptr;
+}
+
+void Engine::tbeg(int kind) {
+  if (kind != timer_kind_ || ev_used_ + 2 > (int)ev_.size()) return;
+  cudaEventRecord(ev_[ev_used_], stream_);
+}
+
+void Engine::tend(int kind) {
+  if (kind != timer_kind_ || ev_used_ + 2 > (int)ev_.size()) return;
+  cudaEventRecord(ev_[ev_used_ + 1], stream_);
+  work_of(kind, &ev_bytes_[ev_used_ / 2], &ev_flops_[ev_used_ / 2]);
+  ev_used_ += 2;
+}
+
+// Harvest the recorded pairs (the stream is synchronised at the end of every run).
+void Engine::timer_read(double* ms, int* launches, double* bytes, double* flops) {
+  for (int i = 0; i + 1 < ev_used_; i += 2) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ev_[i], ev_[i + 1]) == cudaSuccess) {
+      t_ms_ += t;
+      t_bytes_ += ev_bytes_[i / 2];
+      t_flops_ += ev_flops_[i / 2];
+      ++t_launches_;
+    }
+  }
+  ev_used_ = 0;
+  if (ms) *ms = t_ms_;
+  if (launches) *launches = t_launches_;
+  if (bytes) *bytes = t_bytes_;
+  if (flops) *flops = t_flops_;
+}
+
+// Algorithmic work of one launch over the active members: the bytes each kernel must move
+// to and from device memory at least once and its arithmetic (5 N log2 N per complex FFT
+// of length N; 2 m n k per GEMM).
+void Engine::work_of(int kind, double* bytes, double* flops) const {
+  double b = 0.0, f = 0.0;
+  const double ts = precision_ ? 4.0 : 8.0;
+  for (int p = 0; p < n_; ++p) {
+    if (!h_active_[p]) continue;
+    const Prob& d = ctx_[p]->d;
+    const double n1 = d.n1, n2 = d.n2, n3 = d.n3, np = d.npair, nc = d.ncol, nb = d.nb, npw = d.npw;
+    const double rows = 2.0 * d.m1max + 1.0;
+    switch (kind) {
+      case TK_PLANE_VPSI:
+        f += np * n3 * (2.0 * rows * 5.0 * n2 * log2d(n2) + 2.0 * n2 * 5.0 * n1 * log2d(n1) + 2.0 * n1 * n2);
+        b += np * n3 * (2.0 * nc * 2.0 * ts + n1 * n2 * ts);
+        break;
+      case TK_PLANE_DENSITY:
+        f += np * n3 * (rows * 5.0 * n2 * log2d(n2) + n2 * 5.0 * n1 * log2d(n1) + 4.0 * n1 * n2);
+        b += np * n3 * nc * 2.0 * ts + n1 * n2 * n3 * 8.0;
+        break;
+      case TK_WAVE_TO_COLS:
+        f += np * nc * 5.0 * n3 * log2d(n3);
+        b += 2.0 * np * npw * ts + np * nc * n3 * 2.0 * ts;
+        break;
+      case TK_COLS_TO_WAVE:
+        f += np * nc * 5.0 * n3 * log2d(n3);
+        b += np * nc * n3 * 2.0 * ts + 4.0 * np * npw * ts + npw * 8.0;
+        break;
+      case TK_GEMM_TN:
+        f += 2.0 * nb * nb * npw;
+        b += 2.0 * nb * npw * ts;
+        break;
+      case TK_GEMM_NN:
+        f += 2.0 * npw * nb * nb;
+        b += 2.0 * nb * npw * ts;
+        break;
+      case TK_RR:
+        f += 4.0 * nb * nb * nb;
+        b += 3.0 * nb * nb * 8.0;
+        break;
+    }
+  }
+  *bytes = b;
+  *flops = f;
+}
+
+void Engine::swap_roles(int a, int b) { k_swap_roles<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, a, b); }
 
 void Engine::set_scal(int idx, double v, bool only_active) {
   k_set_scal<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, idx, v, only_active ? 1 : 0);
@@ -543,30 +668,39 @@ void Engine::tn(int akind, int arole, int bkind, int brole, int dst) {
   const WorkMap* r = &m_red_ww_;
   if (akind == OPK_B) { m = &m_tn_bw_; r = &m_red_bw_; }
   if (akind == OPK_DB) { m = &m_tn_dw_; r = &m_red_dw_; }
-  const int ap = akind == OPK_WB ? role_[arole] : 0;
-  const int bp = bkind == OPK_WB ? role_[brole] : 0;
-  launch_gemm_tn<T>(L(*m), akind, ap, bkind, bp, d_part_, part_stride_);
+  const bool sq = akind == OPK_WB;
+  if (sq) tbeg(TK_GEMM_TN);
+  launch_gemm_tn<T>(L(*m), akind, arole, bkind, brole, d_part_, part_stride_);
+  if (sq) tend(TK_GEMM_TN);
   launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_);
 }
 
 template <typename T>
 void Engine::nn(int akind, int arole, int msel, int yrole, double alpha, double beta) {
-  const int ap = akind == OPK_WB ? role_[arole] : 0;
-  launch_gemm_nn<T>(L(m_nn_), akind, ap, msel, role_[yrole], alpha, beta);
+  const bool sq = akind == OPK_WB;
+  if (sq) tbeg(TK_GEMM_NN);
+  launch_gemm_nn<T>(L(m_nn_), akind, arole, msel, yrole, alpha, beta);
+  if (sq) tend(TK_GEMM_NN);
 }
 
 template <typename T>
 void Engine::rotate(int role) {
   nn<T>(OPK_WB, role, DD_TM, WB_W, 1.0, 0.0);
-  std::swap(role_[role], role_[WB_W]);
+  swap_roles(role, WB_W);
 }
 
 // H applied to every band of src: FFT local + kinetic, then nonlocal B (D o B^T src).
 template <typename T>
 void Engine::hpsi(int src, int dst) {
-  launch_wave_to_cols<T>(L(m_zcol_), role_[src]);
+  tbeg(TK_WAVE_TO_COLS);
+  launch_wave_to_cols<T>(L(m_zcol_), src);
+  tend(TK_WAVE_TO_COLS);
+  tbeg(TK_PLANE_VPSI);
   launch_plane_vpsi<T>(L(m_plane_));
-  launch_cols_to_wave<T>(L(m_zcol_), role_[src], role_[dst]);
+  tend(TK_PLANE_VPSI);
+  tbeg(TK_COLS_TO_WAVE);
+  launch_cols_to_wave<T>(L(m_zcol_), src, dst);
+  tend(TK_COLS_TO_WAVE);
   tn<T>(OPK_B, 0, OPK_WB, src, DD_PROJ);
   nn<T>(OPK_B, 0, DD_PROJ_D, dst, 1.0, 1.0);
 }
@@ -576,7 +710,9 @@ template <typename T>
 void Engine::rayleigh_ritz(bool rotate_history) {
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
+  tbeg(TK_RR);
   launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_);
+  tend(TK_RR);
   rotate<T>(WB_X);
   rotate<T>(WB_HX);
   if (rotate_history) {
@@ -588,13 +724,13 @@ void Engine::rayleigh_ritz(bool rotate_history) {
 // One all-band CG step (Algorithm 1, lines 6-16).
 template <typename T>
 void Engine::cg_step() {
-  launch_cg_precond<T>(L(m_bands_), role_[WB_X], role_[WB_HX], role_[WB_P], role_[WB_W2], role_[WB_PP], role_[WB_RP]);
+  launch_cg_precond<T>(L(m_bands_), WB_X, WB_HX, WB_P, WB_W2, WB_PP, WB_RP);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_P, DD_CM);        // C = Psi^T P
   nn<T>(OPK_WB, WB_X, DD_CM, WB_P, -1.0, 1.0);     // P -= Psi C     (line 12)
-  launch_normalize<T>(L(m_bands_), role_[WB_P], role_[WB_PP]);
+  launch_normalize<T>(L(m_bands_), WB_P, WB_PP);
   hpsi<T>(WB_P, WB_HP);
-  launch_line_min<T>(L(m_bands_), role_[WB_X], role_[WB_HX], role_[WB_P], role_[WB_HP]);  // line 13
-  std::swap(role_[WB_RP], role_[WB_W2]);
+  launch_line_min<T>(L(m_bands_), WB_X, WB_HX, WB_P, WB_HP);  // line 13
+  swap_roles(WB_RP, WB_W2);
   rayleigh_ritz<T>(true);                          // lines 14-16
   launch_finish_cg(L(m_prob_));
 }
@@ -636,7 +772,7 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     launch_rho0_g(L(m_gew_));
     grid_fft(0, 1);
     launch_grid_real_part(L(m_gew_), 0, 0);
-    launch_random_init<T>(L(m_bands_), role_[WB_X], o.seed);
+    launch_random_init<T>(L(m_bands_), WB_X, o.seed);
   }
   const int nonsc = warm ? 0 : std::max(0, o.n_nonscf);
   const int hist = std::min(std::max(o.pulay_hist, 1), MAX_HIST);
@@ -656,10 +792,12 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     for (int k = 0; k < ncg; ++k) cg_step<T>();
     // occupations and rho_out
     launch_occupations(L(m_prob_));
-    launch_wave_to_cols<T>(L(m_zcol_), role_[WB_X]);
+    launch_wave_to_cols<T>(L(m_zcol_), WB_X);
+    tbeg(TK_PLANE_DENSITY);
     launch_plane_density<T>(L(m_dens_), nullptr);
+    tend(TK_PLANE_DENSITY);
     // energy at (Psi, rho_out) and the convergence test
-    launch_band_kinetic<T>(L(m_bands_), role_[WB_X]);
+    launch_band_kinetic<T>(L(m_bands_), WB_X);
     tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ);
     launch_real_to_grid(L(m_gew_), 1, 0);
     grid_fft(0, -1);
@@ -702,12 +840,8 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     launch_force_total(L(m_prob_), maxchunk_);
   }
   // X back to physical buffer 0 so that the next run (warm or component call) finds it there
-  if (role_[WB_X] != 0) {
-    for (auto* c : ctx_)
-      CK(cudaMemcpyAsync(c->d.wb[0], c->d.wb[role_[WB_X]], (size_t)c->d.nb * c->d.ld * c->tsize,
-                         cudaMemcpyDeviceToDevice, stream_));
-  }
-  for (int i = 0; i < NWB; ++i) role_[i] = i;
+  k_x_to_buffer0<T><<<m_bands_.total, 256, 0, stream_>>>(L(m_bands_).ka);
+  k_reset_roles<<<n_, 32, 0, stream_>>>(L(m_prob_).ka);
   for (auto* c : ctx_) {
     CK(cudaMemcpyAsync(c->h_scal.data(), c->d.scal, sizeof(double) * NSCAL_ALL, cudaMemcpyDeviceToHost, stream_));
     CK(cudaMemcpyAsync(c->h_eps.data(), c->d.eps, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
@@ -721,7 +855,8 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
   for (int p = 0; p < n_; ++p) {
     sgo_ctx* c = ctx_[p];
     c->have_state = true;
-    c->last_iter = niter;
+    c->last_iter = (int)c->h_scal[SC_ITER] + nonsc;  // this member's iterations (until it converged)
+    if (c->last_iter > niter) c->last_iter = niter;
     c->last_resid = c->h_scal[SC_RESID];
     sgo_status st = SGO_OK;
     if (h_flags_[4 * p + 1] != 0.0) st = SGO_ERR_NOT_CONVERGED;
@@ -755,7 +890,6 @@ sgo_status Engine::apply_h(const double* veff_c, int nvec, const double* psi, do
   CK(cudaMemcpyAsync(dpsi, psi, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyHostToDevice, stream_));
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
-  for (int i = 0; i < NWB; ++i) role_[i] = i;
   if (structure_terms() != SGO_OK) return SGO_ERR_CUDA;
   if (precision_) {
     launch_veff<float>(L(m_gew_), dv);
@@ -790,7 +924,6 @@ sgo_status Engine::density(int nvec, const double* psi, const double* occ, doubl
   CK(cudaMemcpyAsync(docc, o.data(), sizeof(double) * d.nb, cudaMemcpyHostToDevice, stream_));
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
-  for (int i = 0; i < NWB; ++i) role_[i] = i;
   if (precision_) {
     launch_copy_in<float>(L(m_bands_), WB_W, dpsi, nvec);
     launch_wave_to_cols<float>(L(m_zcol_), WB_W);

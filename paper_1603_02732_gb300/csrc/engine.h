@@ -69,6 +69,14 @@ class Engine {
   sgo_status density(int nvec, const double* psi, const double* occ, double* rho);
   sgo_status export_density(double* rho);
   sgo_status structure_terms();
+  // Live CUDA-event timing of one kernel class (see kTimerNames) over subsequent runs.
+  bool timer_select(const char* name);
+  void timer_read(double* ms, int* launches, double* bytes, double* flops);
+  long long take_launches() {
+    long long v = launches_;
+    launches_ = 0;
+    return v;
+  }
   // Batch evaluation with positions, energies, forces and statuses in device memory.
   sgo_status run_device(const double* pos, double* energies, double* forces, int* status);
 
@@ -86,6 +94,17 @@ class Engine {
   void pulay();
   void sync_active();
   void set_scal(int idx, double v, bool only_active);
+  void tbeg(int kind);
+  void tend(int kind);
+  void work_of(int kind, double* bytes, double* flops) const;
+  int timer_kind_ = -1;
+  mutable long long launches_ = 0;  // kernel launches issued (one per Launch built)
+  std::vector<cudaEvent_t> ev_;
+  std::vector<double> ev_bytes_, ev_flops_;
+  int ev_used_ = 0;
+  double t_ms_ = 0.0, t_bytes_ = 0.0, t_flops_ = 0.0;
+  int t_launches_ = 0;
+  void swap_roles(int a, int b);
   Launch L(const WorkMap& m) const;
   WorkMap make_map(const std::vector<int>& counts);
 
@@ -98,7 +117,6 @@ class Engine {
   int* d_active_ = nullptr;
   std::vector<int> h_active_;
   std::vector<void*> allocs_;
-  int role_[NWB];
   int max_n1_ = 0, max_n2_ = 0, max_n3_ = 0, max_n12_ = 0, max_nb_ = 0, plane_threads_ = 128;
   WorkMap m_zcol_, m_plane_, m_dens_, m_gz_, m_gp_, m_gew_, m_gch_, m_bands_, m_tn_ww_, m_tn_bw_, m_tn_dw_,
       m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_atomch_, m_ewsg_, m_prob_;
@@ -113,6 +131,10 @@ class Engine {
   double* d_flags_ = nullptr;   // [n][4] gathered per iteration
   std::vector<double> h_flags_;
 };
+
+// Kernel classes the engine can time live (CUDA events on its stream).
+enum { TK_PLANE_VPSI = 0, TK_WAVE_TO_COLS, TK_COLS_TO_WAVE, TK_PLANE_DENSITY, TK_GEMM_TN, TK_GEMM_NN, TK_RR, TK_COUNT };
+extern const char* const kTimerNames[TK_COUNT];
 
 // Context set-up (basis on the device, allocation, tables).  Returns status.
 sgo_status ctx_setup(sgo_ctx* c);

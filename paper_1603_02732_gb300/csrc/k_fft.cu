@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_wave_to_cols(KArgs ka, int src
 
   const int ia = 2 * pair, ib = 2 * pair + 1;
   const bool hasb = ib < P.nb;
-  const T* xa = reinterpret_cast<const T*>(P.wb[src]) + (size_t)ia * P.ld;
-  const T* xb = reinterpret_cast<const T*>(P.wb[src]) + (size_t)(hasb ? ib : ia) * P.ld;
+  const T* xa = wbuf<T>(P, src) + (size_t)ia * P.ld;
+  const T* xb = wbuf<T>(P, src) + (size_t)(hasb ? ib : ia) * P.ld;
   const T rs2 = T(1.0 / SQRT2);
   const int e0 = P.cp_off[cp0], e1 = P.cp_off[cp1];
   for (int k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
@@ -140,10 +140,10 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_cols_to_wave(KArgs ka, int src
 
   const int ia = 2 * pair, ib = 2 * pair + 1;
   const bool hasb = ib < P.nb;
-  const T* xa = reinterpret_cast<const T*>(P.wb[src]) + (size_t)ia * P.ld;
-  const T* xb = reinterpret_cast<const T*>(P.wb[src]) + (size_t)(hasb ? ib : ia) * P.ld;
-  T* ya = reinterpret_cast<T*>(P.wb[dst]) + (size_t)ia * P.ld;
-  T* yb = reinterpret_cast<T*>(P.wb[dst]) + (size_t)(hasb ? ib : ia) * P.ld;
+  const T* xa = wbuf<T>(P, src) + (size_t)ia * P.ld;
+  const T* xb = wbuf<T>(P, src) + (size_t)(hasb ? ib : ia) * P.ld;
+  T* ya = wbuf<T>(P, dst) + (size_t)ia * P.ld;
+  T* yb = wbuf<T>(P, dst) + (size_t)(hasb ? ib : ia) * P.ld;
   const T hs2 = T(0.5 * SQRT2);
   const int e0 = P.cp_off[cp0], e1 = P.cp_off[cp1];
   for (int k = e0 + threadIdx.x; k < e1; k += blockDim.x) {

@@ -20,7 +20,7 @@ namespace {
 
 template <typename T>
 __device__ __forceinline__ const T* opnd(const Prob& P, int kind, int role) {
-  if (kind == OPK_WB) return reinterpret_cast<const T*>(P.wb[role]);
+  if (kind == OPK_WB) return wbuf<T>(P, role);
   if (kind == OPK_B) return reinterpret_cast<const T*>(P.B);
   return reinterpret_cast<const T*>(P.dB);
 }
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(KArgs ka, int akind, int arole,
   const int nb = P.nb, ld = P.ld, npw = P.npw;
   const T* A = opnd<T>(P, akind, arole);
   const double* M = dense_ptr(P, msel);
-  T* Y = reinterpret_cast<T*>(P.wb[yrole]);
+  T* Y = wbuf<T>(P, yrole);
   const int t = threadIdx.x, tr = t & 15, tc = t >> 4;
   T acc[4][4];
 #pragma unroll
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(BAND_THREADS) k_band_kinetic(KArgs ka, int xr)
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
-  const T* x = reinterpret_cast<const T*>(P.wb[xr]) + (size_t)i * P.ld;
+  const T* x = wbuf<T>(P, xr) + (size_t)i * P.ld;
   double s = 0.0;
   for (int k = threadIdx.x; k < P.npw; k += blockDim.x) s += P.ekin[k] * (double)x[k] * (double)x[k];
   s = block_sum(s, red);
@@ -217,12 +217,12 @@ __global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, i
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
   const size_t off = (size_t)i * P.ld;
-  const T* x = reinterpret_cast<const T*>(P.wb[xr]) + off;
-  const T* hx = reinterpret_cast<const T*>(P.wb[hxr]) + off;
-  T* pv = reinterpret_cast<T*>(P.wb[pr]) + off;
-  T* rv = reinterpret_cast<T*>(P.wb[rr_out]) + off;
-  const T* pp = reinterpret_cast<const T*>(P.wb[ppr]) + off;
-  const T* rp = reinterpret_cast<const T*>(P.wb[rpr]) + off;
+  const T* x = wbuf<T>(P, xr) + off;
+  const T* hx = wbuf<T>(P, hxr) + off;
+  T* pv = wbuf<T>(P, pr) + off;
+  T* rv = wbuf<T>(P, rr_out) + off;
+  const T* pp = wbuf<T>(P, ppr) + off;
+  const T* rp = wbuf<T>(P, rpr) + off;
   const bool first = P.scal[SC_FIRSTCG] != 0.0;
   double ek = 0.0;
   for (int k = threadIdx.x; k < P.npw; k += blockDim.x) ek += P.ekin[k] * (double)x[k] * (double)x[k];
@@ -267,8 +267,8 @@ __global__ void __launch_bounds__(BAND_THREADS) k_normalize(KArgs ka, int pr, in
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
   const size_t off = (size_t)i * P.ld;
-  T* pv = reinterpret_cast<T*>(P.wb[pr]) + off;
-  T* pp = reinterpret_cast<T*>(P.wb[ppr]) + off;
+  T* pv = wbuf<T>(P, pr) + off;
+  T* pp = wbuf<T>(P, ppr) + off;
   double s = 0.0;
   for (int k = threadIdx.x; k < P.npw; k += blockDim.x) s += (double)pv[k] * (double)pv[k];
   s = sqrt(block_sum(s, red));
@@ -291,10 +291,10 @@ __global__ void __launch_bounds__(BAND_THREADS) k_line_min(KArgs ka, int xr, int
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
   const size_t off = (size_t)i * P.ld;
-  T* x = reinterpret_cast<T*>(P.wb[xr]) + off;
-  T* hx = reinterpret_cast<T*>(P.wb[hxr]) + off;
-  const T* pv = reinterpret_cast<const T*>(P.wb[pr]) + off;
-  const T* hp = reinterpret_cast<const T*>(P.wb[hpr]) + off;
+  T* x = wbuf<T>(P, xr) + off;
+  T* hx = wbuf<T>(P, hxr) + off;
+  const T* pv = wbuf<T>(P, pr) + off;
+  const T* hp = wbuf<T>(P, hpr) + off;
   double a = 0.0, b = 0.0, c = 0.0;
   for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
     double xv = x[k], pk = pv[k];
@@ -340,7 +340,7 @@ __global__ void k_random_init(KArgs ka, int xr, unsigned long long seed) {
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
-  T* x = reinterpret_cast<T*>(P.wb[xr]) + (size_t)i * P.ld;
+  T* x = wbuf<T>(P, xr) + (size_t)i * P.ld;
   for (int k = threadIdx.x; k < P.ld; k += blockDim.x) {
     double v = 0.0;
     if (k < P.npw) {
@@ -357,7 +357,7 @@ __global__ void k_copy_in(KArgs ka, int role, const double* src, int nvec) {
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
-  T* x = reinterpret_cast<T*>(P.wb[role]) + (size_t)i * P.ld;
+  T* x = wbuf<T>(P, role) + (size_t)i * P.ld;
   for (int k = threadIdx.x; k < P.ld; k += blockDim.x)
     x[k] = (i < nvec && k < P.npw) ? (T)src[(size_t)i * P.npw + k] : T(0);
 }
@@ -367,7 +367,7 @@ __global__ void k_copy_out(KArgs ka, int role, double* dst, int nvec) {
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
   if (i >= nvec) return;
-  const T* x = reinterpret_cast<const T*>(P.wb[role]) + (size_t)i * P.ld;
+  const T* x = wbuf<T>(P, role) + (size_t)i * P.ld;
   for (int k = threadIdx.x; k < P.npw; k += blockDim.x) dst[(size_t)i * P.npw + k] = (double)x[k];
 }
 

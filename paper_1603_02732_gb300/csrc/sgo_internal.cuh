@@ -144,7 +144,8 @@ struct Prob {
   // bands
   int nb, npair;
   // wave buffers (element type = engine precision)
-  void* wb[NWB];               // each [nb][ld]
+  void* wb[NWB];               // each [nb][ld], physical buffers
+  int role[NWB];               // role -> physical buffer of this problem (swapped on the device)
   void* B;                     // [natom][ld] projectors
   void* dB;                    // [3*natom][ld] projector derivatives (forces)
   void* Wc;                    // complex [npair][n3][ncol]
@@ -181,6 +182,11 @@ struct Prob {
   double2* ew_sg;              // [(2ng1+1)(2ng2+1)(2ng3+1)] S(G)
   double* ew_part;             // [natom] real-space energy per atom, then recip chunks
 };
+
+template <typename T>
+__device__ __forceinline__ T* wbuf(const Prob& P, int role) {
+  return reinterpret_cast<T*>(P.wb[P.role[role]]);
+}
 
 // Static CTA -> problem map of one kind of launch: start[p] = first CTA of problem p.
 struct WorkMap {

@@ -143,12 +143,15 @@ class Clocks:
         return dict(sm_mhz=float(np.median(mhz)), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(mhz))
 
 
+_SCF = {}
+
+
 def _tols(prec, st):
     """SCF stopping rule: FP64 path |dF| < 1e-8 Ha and residual < 1e-7; mixed path (FP32
     noise floor) |dF| < 1e-7 Ha per atom and residual < 1e-5 -- far inside 1e-5 Ha/atom."""
     if prec == "mixed":
-        return dict(scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5)
-    return dict(scf_tol_e=1e-8, scf_tol_rho=1e-7)
+        return dict(scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5, **_SCF)
+    return dict(scf_tol_e=1e-8, scf_tol_rho=1e-7, **_SCF)
 
 
 def _peaks():
@@ -259,11 +262,27 @@ def run_ours(args):
                     config=dict(workload=WORKLOAD, members=MEMBERS, atoms="8-32", ecut_ha=12.0, kT_ha=0.01,
                                 precision=prec, start="cold (atomic density, random wavefunctions)",
                                 l2="flushed by a 256 MiB write before every timed step",
-                                converged=f"{n_ok}/{MEMBERS}",
+                                converged=f"{n_ok}/{MEMBERS}", scf_options=dict(_SCF),
                                 scf_iterations=dict(mean=float(np.mean(iters)), max=int(np.max(iters)))),
                     e2e=dict(value=e2e_val, unit="evals/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=int(launches), roofline=roofline, clocks=clk)
         out = line
+    if args.profile and rank == 0:
+        prof = {}
+        for kind in ("plane_vpsi", "wave_to_cols", "cols_to_wave", "plane_density", "gemm_tn", "gemm_nn", "rr",
+                     "grid_fft", "cg_band", "grid_other", "gemm_small"):
+            batch.timer(kind)
+            a = torch.cuda.Event(enable_timing=True)
+            b2 = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step_device()
+            b2.record(stream)
+            b2.synchronize()
+            r = batch.timer_read()
+            prof[kind] = dict(ms=r["ms"], launches=r["launches"], share=r["ms"] / a.elapsed_time(b2),
+                              tflops=r["flops"] / max(r["ms"], 1e-9) / 1e9 if r["flops"] else None)
+        batch.timer(None)
+        out["profile"] = prof
     if args.fp64_compare and rank == 0:
         # the plain FP64 GPU path on the same population: one timed step after one warm-up
         ctx64 = [sgo.Context(st, precision="fp64", **_tols("fp64", st)) for st in pop]
@@ -308,7 +327,14 @@ def main():
     ap.add_argument("--kernel", default="plane_vpsi", help="kernel class timed live for the roofline")
     ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 GPU path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="one extra step per kernel class with live timers")
+    ap.add_argument("--ncg", type=int, default=None, help="CG steps per SCF iteration")
+    ap.add_argument("--ncg-first", type=int, default=None)
+    ap.add_argument("--nonscf", type=int, default=None)
     args = ap.parse_args()
+    for k, v in (("ncg", args.ncg), ("ncg_first", args.ncg_first), ("n_nonscf", args.nonscf)):
+        if v is not None:
+            _SCF[k] = v
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

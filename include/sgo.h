@@ -130,8 +130,8 @@ SGO_API sgo_status sgo_energy_forces_batch_device(sgo_batch* b, const double* po
 
 /* Live timing of one kernel class during later batch calls: CUDA events are recorded
  * on the batch stream around every launch of that class.  kernel: "plane_vpsi",
- * "wave_to_cols", "cols_to_wave", "plane_density", "gemm_tn", "gemm_nn", "rr", or
- * NULL to stop.  Resets the accumulators.  Instrumentation, not part of the method. */
+ * "wave_to_cols", "cols_to_wave", "plane_density", "gemm_tn", "gemm_nn", "rr", "grid_fft",
+ * "cg_band", "grid_other", "gemm_small", or NULL to stop.  Resets the accumulators.  Instrumentation, not part of the method. */
 SGO_API sgo_status sgo_batch_timer(sgo_batch* b, const char* kernel);
 
 /* Read and keep accumulating: out[0] total ms, out[1] launches, out[2] algorithmic

@@ -416,7 +416,8 @@ sgo_ctx::~sgo_ctx() {
 namespace sgo {
 
 const char* const kTimerNames[TK_COUNT] = {"plane_vpsi", "wave_to_cols", "cols_to_wave", "plane_density",
-                                           "gemm_tn",    "gemm_nn",      "rr"};
+                                           "gemm_tn",    "gemm_nn",      "rr",           "grid_fft",
+                                           "cg_band",    "grid_other",   "gemm_small"};
 
 // ---------------------------------------------------------------------------
 // Engine
@@ -536,6 +537,8 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   if (!cuda_ok(cudaMalloc(&d_flags_, sizeof(double) * 4 * n_), "cudaMalloc(flags)")) return;
   allocs_.push_back(d_flags_);
   h_flags_.assign(4 * n_, 0.0);
+  // mixed path: FP32 subspace eigensolve when its shared-memory layout fits (nb <= 95)
+  rr_f32_ = precision_ == 1 && (size_t)24 * max_nb_ * max_nb_ <= 216 * 1024;
   rr_smem_bytes_ = (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
   rr_smem_ = rr_smem_bytes_ <= 200 * 1024;
   if (!rr_smem_) {
@@ -653,6 +656,12 @@ void Engine::set_scal(int idx, double v, bool only_active) {
 }
 
 void Engine::grid_fft(int which, int sign) {
+  tbeg(TK_GRID_FFT);
+  grid_fft_raw(which, sign);
+  tend(TK_GRID_FFT);
+}
+
+void Engine::grid_fft_raw(int which, int sign) {
   if (sign < 0) {
     launch_grid_plane_fft(L(m_gp_), which, -1);
     launch_grid_z_fft(L(m_gz_), which, -1);
@@ -668,19 +677,19 @@ void Engine::tn(int akind, int arole, int bkind, int brole, int dst) {
   const WorkMap* r = &m_red_ww_;
   if (akind == OPK_B) { m = &m_tn_bw_; r = &m_red_bw_; }
   if (akind == OPK_DB) { m = &m_tn_dw_; r = &m_red_dw_; }
-  const bool sq = akind == OPK_WB;
-  if (sq) tbeg(TK_GEMM_TN);
+  const int kind = akind == OPK_WB ? TK_GEMM_TN : TK_GEMM_SMALL;
+  tbeg(kind);
   launch_gemm_tn<T>(L(*m), akind, arole, bkind, brole, d_part_, part_stride_);
-  if (sq) tend(TK_GEMM_TN);
   launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_);
+  tend(kind);
 }
 
 template <typename T>
 void Engine::nn(int akind, int arole, int msel, int yrole, double alpha, double beta) {
-  const bool sq = akind == OPK_WB;
-  if (sq) tbeg(TK_GEMM_NN);
+  const int kind = akind == OPK_WB ? TK_GEMM_NN : TK_GEMM_SMALL;
+  tbeg(kind);
   launch_gemm_nn<T>(L(m_nn_), akind, arole, msel, yrole, alpha, beta);
-  if (sq) tend(TK_GEMM_NN);
+  tend(kind);
 }
 
 template <typename T>
@@ -711,7 +720,8 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
   tbeg(TK_RR);
-  launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_);
+  if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)24 * max_nb_ * max_nb_);
+  else launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_);
   tend(TK_RR);
   rotate<T>(WB_X);
   rotate<T>(WB_HX);
@@ -724,12 +734,18 @@ void Engine::rayleigh_ritz(bool rotate_history) {
 // One all-band CG step (Algorithm 1, lines 6-16).
 template <typename T>
 void Engine::cg_step() {
+  tbeg(TK_CG_BAND);
   launch_cg_precond<T>(L(m_bands_), WB_X, WB_HX, WB_P, WB_W2, WB_PP, WB_RP);
+  tend(TK_CG_BAND);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_P, DD_CM);        // C = Psi^T P
   nn<T>(OPK_WB, WB_X, DD_CM, WB_P, -1.0, 1.0);     // P -= Psi C     (line 12)
+  tbeg(TK_CG_BAND);
   launch_normalize<T>(L(m_bands_), WB_P, WB_PP);
+  tend(TK_CG_BAND);
   hpsi<T>(WB_P, WB_HP);
+  tbeg(TK_CG_BAND);
   launch_line_min<T>(L(m_bands_), WB_X, WB_HX, WB_P, WB_HP);  // line 13
+  tend(TK_CG_BAND);
   swap_roles(WB_RP, WB_W2);
   rayleigh_ritz<T>(true);                          // lines 14-16
   launch_finish_cg(L(m_prob_));
@@ -779,11 +795,17 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
   int it = 0;
   for (it = 1; it <= o.max_scf; ++it) {
     // V_eff from rho_in (Hartree in G space, LDA in real space)
+    tbeg(TK_GRID_OTHER);
     launch_real_to_grid(L(m_gew_), 0, 0);
+    tend(TK_GRID_OTHER);
     grid_fft(0, -1);
+    tbeg(TK_GRID_OTHER);
     launch_hartree_g(L(m_gew_), 0);
+    tend(TK_GRID_OTHER);
     grid_fft(0, 1);
+    tbeg(TK_GRID_OTHER);
     launch_veff<T>(L(m_gew_), nullptr);
+    tend(TK_GRID_OTHER);
     // H Psi and the subspace diagonalisation (Algorithm 1, lines 2-3)
     hpsi<T>(WB_X, WB_HX);
     rayleigh_ritz<T>(false);
@@ -799,11 +821,15 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     // energy at (Psi, rho_out) and the convergence test
     launch_band_kinetic<T>(L(m_bands_), WB_X);
     tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ);
+    tbeg(TK_GRID_OTHER);
     launch_real_to_grid(L(m_gew_), 1, 0);
+    tend(TK_GRID_OTHER);
     grid_fft(0, -1);
+    tbeg(TK_GRID_OTHER);
     launch_grid_energies(L(m_gch_), d_gpart_, maxchunk_);
     launch_grid_energies_reduce(L(m_prob_), d_gpart_, maxchunk_);
     launch_finish_iteration(L(m_prob_), o.scf_tol_e, o.scf_tol_rho, it > nonsc ? 1 : 0);
+    tend(TK_GRID_OTHER);
     CK(cudaGetLastError());
     sync_active();
     int nact = 0;
@@ -811,10 +837,12 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     if (nact == 0) break;
     if (it > nonsc) {
       // Pulay mixing of rho_out with rho_in
+      tbeg(TK_GRID_OTHER);
       launch_pulay_store(L(m_gew_));
       launch_pulay_gram(L(m_gch_), d_gpart_, maxchunk_, hist);
       launch_pulay_solve(L(m_prob_), d_gpart_, maxchunk_, hist);
       launch_pulay_mix(L(m_gew_), 0, 0.0);
+      tend(TK_GRID_OTHER);
       if (o.kerker_q0 > 0.0) {
         launch_real_to_grid(L(m_gew_), 2, 0);
         grid_fft(0, -1);
@@ -822,7 +850,9 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
         grid_fft(0, 1);
         launch_grid_real_part(L(m_gew_), 0, 2);
       }
+      tbeg(TK_GRID_OTHER);
       launch_pulay_mix(L(m_gew_), 1, o.mix_alpha);
+      tend(TK_GRID_OTHER);
     }
   }
   const int niter = std::min(it, o.max_scf);

@@ -89,6 +89,7 @@ class Engine {
   template <typename T> void nn(int akind, int arole, int msel, int yrole, double alpha, double beta);
   template <typename T> void rotate(int role);
   void grid_fft(int which, int sign);
+  void grid_fft_raw(int which, int sign);
   void potential();
   void energies_at_rho_out(bool count_iter);
   void pulay();
@@ -127,13 +128,17 @@ class Engine {
   double* d_rr_ = nullptr;
   size_t rr_stride_ = 0;
   bool rr_smem_ = true;
+  bool rr_f32_ = false;
   size_t rr_smem_bytes_ = 0;
   double* d_flags_ = nullptr;   // [n][4] gathered per iteration
   std::vector<double> h_flags_;
 };
 
 // Kernel classes the engine can time live (CUDA events on its stream).
-enum { TK_PLANE_VPSI = 0, TK_WAVE_TO_COLS, TK_COLS_TO_WAVE, TK_PLANE_DENSITY, TK_GEMM_TN, TK_GEMM_NN, TK_RR, TK_COUNT };
+enum {
+  TK_PLANE_VPSI = 0, TK_WAVE_TO_COLS, TK_COLS_TO_WAVE, TK_PLANE_DENSITY, TK_GEMM_TN, TK_GEMM_NN, TK_RR,
+  TK_GRID_FFT, TK_CG_BAND, TK_GRID_OTHER, TK_GEMM_SMALL, TK_COUNT
+};
 extern const char* const kTimerNames[TK_COUNT];
 
 // Context set-up (basis on the device, allocation, tables).  Returns status.

@@ -1,6 +1,6 @@
 // Batched 1D FFTs on lines held in shared memory (device side).
 //
-// A mixed-radix (2, 3, 4, 5) Stockham autosort transform (Stockham, 1966; the
+// A mixed-radix (2, 3, 4, 5 and composite 6 ... 16) Stockham autosort transform (Stockham, 1966; the
 // GPU formulation of Govindaraju et al., SC'08).  Stage s with radix R and span
 // Ns (product of the earlier radices) maps, for every butterfly j < n/R of a line,
 //   v_r = in[j + r n/R] * w^(r (j mod Ns)),  w = exp(sign 2 pi i / (Ns R)),
@@ -89,6 +89,78 @@ __device__ __forceinline__ void butterfly<float, 5>(cplx<float>* v, float sg) { 
 template <>
 __device__ __forceinline__ void butterfly<double, 5>(cplx<double>* v, double sg) { bfly5<double>(v, sg); }
 
+// Composite radix R = R1 R2 in registers (Cooley-Tukey inside the butterfly):
+// with m = R2 m1 + m2 and k = k1 + R1 k2,
+//   X[k1 + R1 k2] = sum_m2 w_R2^(m2 k2) [ w_R^(m2 k1) sum_m1 x[R2 m1 + m2] w_R1^(m1 k1) ].
+// The internal factors w_R^t are read from the line's roots table (t (n/R) entries apart).
+template <typename T, int R>
+struct Bfly;
+
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void bfly_comp(cplx<T>* v, T sg, const cplx<T>* roots, int stride) {
+  constexpr int R = R1 * R2;
+  cplx<T> y[R2][R1];
+#pragma unroll
+  for (int m2 = 0; m2 < R2; ++m2) {
+    cplx<T> a[R1];
+#pragma unroll
+    for (int m1 = 0; m1 < R1; ++m1) a[m1] = v[R2 * m1 + m2];
+    Bfly<T, R1>::run(a, sg, roots, stride * R2);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) y[m2][k1] = a[k1];
+  }
+#pragma unroll
+  for (int m2 = 1; m2 < R2; ++m2)
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      cplx<T> w = roots[((m2 * k1) % R) * stride];
+      w.y = sg < T(0) ? w.y : -w.y;
+      y[m2][k1] = y[m2][k1] * w;
+    }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    cplx<T> b[R2];
+#pragma unroll
+    for (int m2 = 0; m2 < R2; ++m2) b[m2] = y[m2][k1];
+    Bfly<T, R2>::run(b, sg, roots, stride * R1);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
+  }
+}
+
+// Bfly<T,R>::run(v, sign, roots, stride): in-register DFT of length R, where
+// roots[t * stride] = exp(-2 pi i t / R).
+#define SGO_BASE_BFLY(RR)                                                                 \
+  template <typename T>                                                                   \
+  struct Bfly<T, RR> {                                                                    \
+    static __device__ __forceinline__ void run(cplx<T>* v, T sg, const cplx<T>*, int) {    \
+      butterfly<T, RR>(v, sg);                                                            \
+    }                                                                                     \
+  };
+SGO_BASE_BFLY(2)
+SGO_BASE_BFLY(3)
+SGO_BASE_BFLY(4)
+SGO_BASE_BFLY(5)
+#undef SGO_BASE_BFLY
+#define SGO_COMP_BFLY(RR, R1, R2)                                                               \
+  template <typename T>                                                                         \
+  struct Bfly<T, RR> {                                                                          \
+    static __device__ __forceinline__ void run(cplx<T>* v, T sg, const cplx<T>* roots, int st) {  \
+      bfly_comp<T, R1, R2>(v, sg, roots, st);                                                   \
+    }                                                                                           \
+  };
+SGO_COMP_BFLY(6, 2, 3)
+SGO_COMP_BFLY(8, 2, 4)
+SGO_COMP_BFLY(9, 3, 3)
+SGO_COMP_BFLY(10, 2, 5)
+SGO_COMP_BFLY(12, 4, 3)
+SGO_COMP_BFLY(15, 3, 5)
+SGO_COMP_BFLY(16, 4, 4)
+#undef SGO_COMP_BFLY
+
+// floor(b / d) for b < 2^16, d <= 2^15, with mg = 0xFFFFFFFF / d + 1 (d > 1)
+__device__ __forceinline__ unsigned fdiv(unsigned b, unsigned d, unsigned mg) { return d == 1 ? b : __umulhi(b, mg); }
+
 // Line l starts at data + base(l) * ls, base(l) = l < split ? l : l + jump (two runs of lines).
 struct LineMap {
   int split;
@@ -103,10 +175,16 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<
   const int nq = n / R;
   const int total = nlines * nq;
   const int rs = n / (Ns * R);
+  const unsigned dq = es == 1 ? nq : nlines;
+  const unsigned mq = dq > 1 ? 0xFFFFFFFFu / dq + 1u : 0u;
+  const unsigned mn = Ns > 1 ? 0xFFFFFFFFu / (unsigned)Ns + 1u : 0u;
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
-    const int line = b / nq;
-    const int j = b - line * nq;
-    const int k = j % Ns;
+    // contiguous lines: neighbouring threads take neighbouring butterflies of a line;
+    // strided lines: neighbouring threads take the same butterfly of neighbouring lines
+    const int q = (int)fdiv((unsigned)b, dq, mq);
+    const int line = es == 1 ? q : b - q * (int)dq;
+    const int j = es == 1 ? b - q * (int)dq : q;
+    const int k = j - (int)fdiv((unsigned)j, (unsigned)Ns, mn) * Ns;
     const int lb = lm(line) * ls;
     cplx<T> v[R];
 #pragma unroll
@@ -119,7 +197,7 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<
       }
       v[r] = x;
     }
-    butterfly<T, R>(v, sg);
+    Bfly<T, R>::run(v, sg, roots, n / R);
     const int d0 = (j - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[lb + (d0 + r * Ns) * es] = v[r];
@@ -139,10 +217,19 @@ __device__ __forceinline__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, int nlines
   cplx<T>* dst = b;
   for (int s = 0; s < d.nst; ++s) {
     const int R = d.rad[s];
-    if (R == 4) fft_stage<T, 4>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg);
-    else if (R == 2) fft_stage<T, 2>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg);
-    else if (R == 3) fft_stage<T, 3>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg);
-    else fft_stage<T, 5>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg);
+    switch (R) {
+      case 16: fft_stage<T, 16>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      case 15: fft_stage<T, 15>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      case 12: fft_stage<T, 12>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      case 10: fft_stage<T, 10>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      case 9: fft_stage<T, 9>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      case 8: fft_stage<T, 8>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      case 6: fft_stage<T, 6>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      case 5: fft_stage<T, 5>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      case 4: fft_stage<T, 4>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      case 3: fft_stage<T, 3>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+      default: fft_stage<T, 2>(src, dst, nlines, ls, es, lm, d.n, Ns, roots, sg); break;
+    }
     Ns *= R;
     cplx<T>* t = src;
     src = dst;

@@ -46,8 +46,8 @@ __device__ __forceinline__ double* dense_ptr(const Prob& P, int sel) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole, int bkind, int brole, double* part_base,
                                                 size_t part_stride) {
-  __shared__ T As[32][TN_TILE + 1];
-  __shared__ T Bs[32][TN_TILE + 1];
+  __shared__ T As[32][TN_TILE + 4];
+  __shared__ T Bs[32][TN_TILE + 4];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
@@ -62,34 +62,41 @@ __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole,
   const int ld = P.ld;
   const int k0 = split * TN_KC, k1 = min(P.npw, k0 + TN_KC);
   const int t = threadIdx.x;
-  const int ti = t & 15, tj = t >> 4;
-  T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+  const int ti = t & 15, tj = t >> 4;   // outputs (ti + 16a, tj + 16b), a, b < 4
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
   for (int kb = k0; kb < k1; kb += 32) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int e = t + 256 * q;
+    for (int q = 0; q < 8; ++q) {
+      int e = t + 256 * q;     // 2048 = 64 vectors x 32 k
       int v = e >> 5, kk = e & 31;
       int k = kb + kk;
       As[kk][v] = (ti0 + v < na && k < k1) ? A[(size_t)(ti0 + v) * ld + k] : T(0);
       Bs[kk][v] = (tj0 + v < nbv && k < k1) ? Bm[(size_t)(tj0 + v) * ld + k] : T(0);
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int kk = 0; kk < 32; ++kk) {
-      T a0 = As[kk][ti], a1 = As[kk][ti + 16];
-      T b0 = Bs[kk][tj], b1 = Bs[kk][tj + 16];
-      acc[0][0] += a0 * b0;
-      acc[0][1] += a0 * b1;
-      acc[1][0] += a1 * b0;
-      acc[1][1] += a1 * b1;
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ti + 16 * i];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) b[i] = Bs[kk][tj + 16 * i];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) acc[i][j2] += a[i] * b[j2];
     }
     __syncthreads();
   }
   double* part = part_base + (size_t)p * part_stride + (size_t)split * na * nbv;
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 4; ++b) {
       int i = ti0 + ti + 16 * a, j = tj0 + tj + 16 * b;
       if (i < na && j < nbv) part[(size_t)i * nbv + j] = (double)acc[a][b];
     }
@@ -193,17 +200,18 @@ __global__ void __launch_bounds__(BAND_THREADS) k_band_kinetic(KArgs ka, int xr)
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
   const T* x = wbuf<T>(P, xr) + (size_t)i * P.ld;
-  double s = 0.0;
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) s += P.ekin[k] * (double)x[k] * (double)x[k];
-  s = block_sum(s, red);
+  T st = T(0);
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) st += T(P.ekin[k]) * x[k] * x[k];
+  const double s = block_sum((double)st, red);
   if (threadIdx.x == 0) P.bv[BV_EKIN * P.nb + i] = s;
 }
 
 // Teter-Payne-Allan preconditioner factor, y = T(G) / E_kin(band).
-__device__ __forceinline__ double tpa(double y) {
-  double y2 = y * y, y3 = y2 * y;
-  double num = 27.0 + 18.0 * y + 12.0 * y2 + 8.0 * y3;
-  return num / (num + 16.0 * y2 * y2);
+template <typename T>
+__device__ __forceinline__ T tpa(T y) {
+  T y2 = y * y, y3 = y2 * y;
+  T num = T(27) + T(18) * y + T(12) * y2 + T(8) * y3;
+  return num / (num + T(16) * y2 * y2);
 }
 
 // Residual R = HX - eps X (line 6), G = A R (TPA; line 8), conjugate direction
@@ -224,31 +232,33 @@ __global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, i
   const T* pp = wbuf<T>(P, ppr) + off;
   const T* rp = wbuf<T>(P, rpr) + off;
   const bool first = P.scal[SC_FIRSTCG] != 0.0;
-  double ek = 0.0;
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) ek += P.ekin[k] * (double)x[k] * (double)x[k];
-  ek = block_sum(ek, red);
+  T ekp = T(0);
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) ekp += T(P.ekin[k]) * x[k] * x[k];
+  double ek = block_sum((double)ekp, red);
   ek = fmax(ek, 1e-3);
-  const double eps = P.eps[i];
-  double gr = 0.0, grp = 0.0, r2 = 0.0;
+  const T eps = T(P.eps[i]);
+  const T iek = T(1.0 / ek);
+  T grt = T(0), grpt = T(0), r2t = T(0);
   for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
-    double r = (double)hx[k] - eps * (double)x[k];
-    double g = tpa(P.ekin[k] / ek) * r;
-    gr += g * r;
-    r2 += r * r;
-    if (!first) grp += g * (double)rp[k];
-    rv[k] = (T)r;
-    pv[k] = (T)g;
+    T r = hx[k] - eps * x[k];
+    T g = tpa<T>(T(P.ekin[k]) * iek) * r;
+    grt += g * r;
+    r2t += r * r;
+    if (!first) grpt += g * rp[k];
+    rv[k] = r;
+    pv[k] = g;
   }
-  gr = block_sum(gr, red);
-  grp = block_sum(grp, red);
-  r2 = block_sum(r2, red);
+  double gr = block_sum((double)grt, red);
+  double grp = block_sum((double)grpt, red);
+  double r2 = block_sum((double)r2t, red);
   double gamma = 0.0;
   if (!first) {
     double den = P.bv[BV_GRP * P.nb + i];
     gamma = den > 0.0 ? fmax(0.0, (gr - grp) / den) : 0.0;
   }
   if (gamma != 0.0) {
-    for (int k = threadIdx.x; k < P.npw; k += blockDim.x) pv[k] = (T)((double)pv[k] + gamma * (double)pp[k]);
+    const T gm = T(gamma);
+    for (int k = threadIdx.x; k < P.npw; k += blockDim.x) pv[k] = pv[k] + gm * pp[k];
   }
   if (threadIdx.x == 0) {
     P.bv[BV_GR * P.nb + i] = gr;
@@ -269,14 +279,14 @@ __global__ void __launch_bounds__(BAND_THREADS) k_normalize(KArgs ka, int pr, in
   const size_t off = (size_t)i * P.ld;
   T* pv = wbuf<T>(P, pr) + off;
   T* pp = wbuf<T>(P, ppr) + off;
-  double s = 0.0;
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) s += (double)pv[k] * (double)pv[k];
-  s = sqrt(block_sum(s, red));
-  const double inv = s > 1e-150 ? 1.0 / s : 0.0;
+  T st = T(0);
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) st += pv[k] * pv[k];
+  const double s = sqrt(block_sum((double)st, red));
+  const T inv = s > 1e-150 ? T(1.0 / s) : T(0);
   for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
     T v = pv[k];
     pp[k] = v;
-    pv[k] = (T)((double)v * inv);
+    pv[k] = v * inv;
   }
   if (threadIdx.x == 0) P.bv[BV_PNORM * P.nb + i] = s;
 }
@@ -295,16 +305,16 @@ __global__ void __launch_bounds__(BAND_THREADS) k_line_min(KArgs ka, int xr, int
   T* hx = wbuf<T>(P, hxr) + off;
   const T* pv = wbuf<T>(P, pr) + off;
   const T* hp = wbuf<T>(P, hpr) + off;
-  double a = 0.0, b = 0.0, c = 0.0;
+  T at = T(0), bt = T(0), ct = T(0);
   for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
-    double xv = x[k], pk = pv[k];
-    a += xv * (double)hx[k];
-    b += pk * (double)hx[k];
-    c += pk * (double)hp[k];
+    T xv = x[k], pk = pv[k], h = hx[k];
+    at += xv * h;
+    bt += pk * h;
+    ct += pk * hp[k];
   }
-  a = block_sum(a, red);
-  b = block_sum(b, red);
-  c = block_sum(c, red);
+  double a = block_sum((double)at, red);
+  double b = block_sum((double)bt, red);
+  double c = block_sum((double)ct, red);
   double th = 0.0;
   if (P.bv[BV_PNORM * P.nb + i] > 1e-150) th = 0.5 * atan2(-2.0 * b, c - a);
   const double lim = 0.25 * PI;
@@ -465,11 +475,18 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
       A[j * n + i] = s;
     }
   }
-  for (int e = tid; e < n * n; e += nt) V[e] = (e / n == e % n) ? 1.0 : 0.0;
+  // accumulate the rotations onto L^-T, so that V ends as Tm = L^-T U directly
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    V[e] = L[j * n + i];
+  }
   __syncthreads();
-  // cyclic Jacobi, round-robin pairing over m = n rounded up to even
+  // cyclic Jacobi, round-robin pairing over m = n rounded up to even.  A rotation whose
+  // |a_pq| is below 1e-14 sqrt(|a_pp a_qq|) is skipped; sweeps stop once the
+  // off-diagonal norm is below 1e-11 of the diagonal norm (FP64 rounding floor ~1e-15).
   const int m = n + (n & 1);
   const int half = m / 2;
+  int sweeps = 0;
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, dia = 0.0;
     for (int e = tid; e < n * n; e += nt) {
@@ -479,7 +496,8 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
     }
     off = block_sum(off, red);
     dia = block_sum(dia, red);
-    if (off <= 1e-30 * dia || off == 0.0) break;
+    if (off <= 1e-22 * dia || off == 0.0) break;
+    ++sweeps;
     for (int r = 0; r < m - 1; ++r) {
       if (tid < half) {
         // tournament: position 0 fixed, positions 1..m-1 rotate by r
@@ -490,8 +508,9 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
         double c = 1.0, s = 0.0;
         if (qq < n) {
           double apq = A[pp * n + qq];
-          if (fabs(apq) > 1e-300) {
-            double tau = (A[qq * n + qq] - A[pp * n + pp]) / (2.0 * apq);
+          double app = A[pp * n + pp], aqq = A[qq * n + qq];
+          if (fabs(apq) > 1e-14 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-300) {
+            double tau = (aqq - app) / (2.0 * apq);
             double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
             c = 1.0 / sqrt(1.0 + t * t);
             s = t * c;
@@ -506,9 +525,9 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
       // rows: A <- J^T A
       for (int e = tid; e < half * n; e += nt) {
         int k = e / n, j = e % n;
-        int pp = pr_p[k], qq = pr_q[k];
         double s = cs_s[k];
-        if (qq >= n || s == 0.0) continue;
+        if (s == 0.0) continue;
+        int pp = pr_p[k], qq = pr_q[k];
         double c = cs_c[k];
         double ap = A[pp * n + j], aq = A[qq * n + j];
         A[pp * n + j] = c * ap - s * aq;
@@ -518,9 +537,9 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
       // columns: A <- A J, V <- V J
       for (int e = tid; e < half * n; e += nt) {
         int k = e / n, i = e % n;
-        int pp = pr_p[k], qq = pr_q[k];
         double s = cs_s[k];
-        if (qq >= n || s == 0.0) continue;
+        if (s == 0.0) continue;
+        int pp = pr_p[k], qq = pr_q[k];
         double c = cs_c[k];
         double ap = A[i * n + pp], aq = A[i * n + qq];
         A[i * n + pp] = c * ap - s * aq;
@@ -536,23 +555,215 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
   for (int j = tid; j < n; j += nt) {
     double ej = A[j * n + j];
     int rank = 0;
-    for (int k = 0; k < n; ++k) {
-      double ek = A[k * n + k];
-      rank += (ek < ej) || (ek == ej && k < j);
+    for (int k2 = 0; k2 < n; ++k2) {
+      double ek = A[k2 * n + k2];
+      rank += (ek < ej) || (ek == ej && k2 < j);
     }
     P.eps[rank] = ej;
     P.bv[BV_TMP0 * n + j] = (double)rank;
   }
   __syncthreads();
-  // Tm[:, rank(j)] = L^T V[:, j]   (L holds L^-1)
+  // Tm[:, rank(j)] = V[:, j]  (= L^-T U)
   for (int e = tid; e < n * n; e += nt) {
     int i = e / n, j = e % n;
-    double s = 0.0;
-    for (int k = i; k < n; ++k) s += L[k * n + i] * V[k * n + j];
-    int col = (int)P.bv[BV_TMP0 * n + j];
-    P.Tm[i * n + col] = s;
+    P.Tm[i * n + (int)P.bv[BV_TMP0 * n + j]] = V[e];
   }
+  if (tid == 0) P.scal[SC_RRSWEEPS] += sweeps;
   if (tid == 0 && flag) P.status[0] = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz for the mixed path, one CTA per problem.  FP64: symmetrised S and Hs,
+// Cholesky S = L L^T, L^-1.  FP32: C = L^-1 Hs L^-T and its cyclic Jacobi
+// eigensolve, accumulated onto L^-T (the rotation matrix feeds the FP32 block
+// rotation, so accuracy beyond FP32 would be discarded there).
+// Shared memory: L, Li (double n^2 each), A, V (float n^2 each).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[33];
+  __shared__ float cs_c[128], cs_s[128];
+  __shared__ int pr_p[128], pr_q[128];
+  __shared__ int flag, nbig;
+  const int p = blockIdx.x;
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int n = P.nb;
+  double* L = reinterpret_cast<double*>(smem_raw);
+  double* Li = L + n * n;
+  float* A = reinterpret_cast<float*>(Li + n * n);
+  float* V = A + n * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) flag = 0;
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    L[e] = 0.5 * (P.S[i * n + j] + P.S[j * n + i]);
+    Li[e] = 0.0;
+  }
+  __syncthreads();
+  // Cholesky, right-looking, two barriers per column (every thread forms the pivot)
+  for (int k = 0; k < n; ++k) {
+    double d = L[k * n + k];
+    if (!(d > 0.0)) d = 1.0;
+    const double dk = sqrt(d);
+    for (int i = k + 1 + tid; i < n; i += nt) L[i * n + k] /= dk;
+    __syncthreads();
+    if (tid == 0) {
+      if (!(L[k * n + k] > 0.0)) flag = 1;
+      L[k * n + k] = dk;
+    }
+    const int m = n - k - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) L[i * n + j] -= L[i * n + k] * L[j * n + k];
+    }
+    __syncthreads();
+  }
+  // L^-1 by columns: column j depends only on itself (forward substitution, no barrier)
+  for (int j = tid; j < n; j += nt) {
+    Li[j * n + j] = 1.0 / L[j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += L[i * n + k] * Li[k * n + j];
+      Li[i * n + j] = -s / L[i * n + i];
+    }
+  }
+  __syncthreads();
+  // L := sym(Hs); V := Hs Li^T; A := Li V   (FP32 products of the FP64 factors)
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    L[e] = 0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]);
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    float s = 0.f;
+    for (int k = 0; k <= j; ++k) s += (float)L[i * n + k] * (float)Li[j * n + k];
+    V[e] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    float s = 0.f;
+    for (int k = 0; k <= i; ++k) s += (float)Li[i * n + k] * V[k * n + j];
+    A[e] = s;
+  }
+  __syncthreads();
+  float amax = 0.f;
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    if (j > i) {
+      float s = 0.5f * (A[i * n + j] + A[j * n + i]);
+      A[i * n + j] = s;
+      A[j * n + i] = s;
+    }
+    if (i == j) amax = fmaxf(amax, fabsf(A[e]));
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    V[e] = (float)Li[j * n + i];  // rotations accumulate onto L^-T
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((tid & 31) == 0) red[tid >> 5] = amax;
+  __syncthreads();
+  if (tid == 0) {
+    float mm = 0.f;
+    for (int w = 0; w < (nt + 31) / 32; ++w) mm = fmaxf(mm, (float)red[w]);
+    red[32] = mm;
+  }
+  __syncthreads();
+  const float thr = 2e-7f * (float)red[32];
+  // Cyclic Jacobi, round-robin pairs; a round maps every 2x2 block of pair rows P and
+  // pair columns Q as A_PQ <- J_P^T A_PQ J_Q (one pass), and V_{:,Q} <- V_{:,Q} J_Q.
+  const int m = n + (n & 1);
+  const int half = m / 2;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    if (tid == 0) nbig = 0;
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt) {
+      int i = e / n, j = e % n;
+      if (i < j && fabsf(A[e]) > thr) nbig = 1;
+    }
+    __syncthreads();
+    if (nbig == 0) break;
+    ++sweeps;
+    for (int r = 0; r < m - 1; ++r) {
+      if (tid < half) {
+        int a = tid, b = m - 1 - tid;
+        int pa = a == 0 ? 0 : 1 + (a - 1 + r) % (m - 1);
+        int pb = b == 0 ? 0 : 1 + (b - 1 + r) % (m - 1);
+        int pp = min(pa, pb), qq = max(pa, pb);
+        float c = 1.f, s = 0.f;
+        if (qq < n) {
+          float apq = A[pp * n + qq];
+          if (fabsf(apq) > thr) {
+            float tau = (A[qq * n + qq] - A[pp * n + pp]) / (2.f * apq);
+            float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            s = t * c;
+          }
+        }
+        cs_c[tid] = c;
+        cs_s[tid] = s;
+        pr_p[tid] = pp;
+        pr_q[tid] = qq;
+      }
+      __syncthreads();
+      // blocks (P, Q), P, Q < half; rows/cols equal to n (the odd dummy) are absent
+      for (int e = tid; e < half * half; e += nt) {
+        const int P2 = e / half, Q2 = e % half;
+        const float sp = cs_s[P2], sq = cs_s[Q2];
+        if (sp == 0.f && sq == 0.f) continue;
+        const float cp = cs_c[P2], cq = cs_c[Q2];
+        const int p0 = pr_p[P2], p1 = pr_q[P2], q0 = pr_p[Q2], q1 = pr_q[Q2];
+        const bool h1 = p1 < n, g1 = q1 < n;
+        float a00 = A[p0 * n + q0];
+        float a01 = g1 ? A[p0 * n + q1] : 0.f;
+        float a10 = h1 ? A[p1 * n + q0] : 0.f;
+        float a11 = (h1 && g1) ? A[p1 * n + q1] : 0.f;
+        // rows: J_P^T
+        float b00 = cp * a00 - sp * a10, b01 = cp * a01 - sp * a11;
+        float b10 = sp * a00 + cp * a10, b11 = sp * a01 + cp * a11;
+        // columns: J_Q
+        A[p0 * n + q0] = cq * b00 - sq * b01;
+        if (g1) A[p0 * n + q1] = sq * b00 + cq * b01;
+        if (h1) A[p1 * n + q0] = cq * b10 - sq * b11;
+        if (h1 && g1) A[p1 * n + q1] = sq * b10 + cq * b11;
+      }
+      for (int e = tid; e < half * n; e += nt) {
+        const int Q2 = e / n, i = e % n;
+        const float sq = cs_s[Q2];
+        if (sq == 0.f) continue;
+        const float cq = cs_c[Q2];
+        const int q0 = pr_p[Q2], q1 = pr_q[Q2];
+        float v0 = V[i * n + q0], v1 = V[i * n + q1];
+        V[i * n + q0] = cq * v0 - sq * v1;
+        V[i * n + q1] = sq * v0 + cq * v1;
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = tid; j < n; j += nt) {
+    float ej = A[j * n + j];
+    int rank = 0;
+    for (int k2 = 0; k2 < n; ++k2) {
+      float ek = A[k2 * n + k2];
+      rank += (ek < ej) || (ek == ej && k2 < j);
+    }
+    P.eps[rank] = (double)ej;
+    P.bv[BV_TMP0 * n + j] = (double)rank;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    P.Tm[i * n + (int)P.bv[BV_TMP0 * n + j]] = (double)V[e];
+  }
+  if (tid == 0) {
+    P.scal[SC_RRSWEEPS] += sweeps;
+    if (flag) P.status[0] = 1;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -676,6 +887,9 @@ void launch_copy_out(const Launch& L, int role, double* dst, int nvec) {
   if (!L.map.total) return;
   k_copy_out<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, role, dst, nvec);
 }
+void launch_rr_f32(const Launch& L, size_t smem) {
+  k_rr_f32<<<L.ka.nprob, RR_THREADS, smem, L.stream>>>(L.ka);
+}
 void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride) {
   k_rr<<<L.ka.nprob, RR_THREADS, use_smem ? smem : 0, L.stream>>>(L.ka, use_smem, gscratch, gstride);
 }
@@ -683,6 +897,7 @@ void launch_occupations(const Launch& L) { k_occupations<<<L.ka.nprob, 32, 0, L.
 void launch_finish_cg(const Launch& L) { k_finish_cg<<<L.ka.nprob, 128, 0, L.stream>>>(L.ka); }
 void linalg_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_rr_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 #define INST(T)                                                                                  \

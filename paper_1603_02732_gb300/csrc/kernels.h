@@ -12,7 +12,7 @@ constexpr int QZ = 8;                  // grid columns per z CTA
 constexpr int DENS_MAXP = 16;          // density accumulators per thread: N1 * N2 <= 16 * blockDim
 constexpr int PLANE_THREADS_MAX = 512;  // so N1 * N2 <= 8192 per plane
 // GEMM geometry
-constexpr int TN_TILE = 32;
+constexpr int TN_TILE = 64;
 constexpr int TN_KC = 256;             // K chunk of one split-K partial
 constexpr int NN_TILE = 64;
 constexpr int BAND_THREADS = 256;
@@ -61,6 +61,7 @@ template <typename T> void launch_random_init(const Launch& L, int xrole, unsign
 template <typename T> void launch_copy_in(const Launch& L, int role, const double* src, int nvec);
 template <typename T> void launch_copy_out(const Launch& L, int role, double* dst, int nvec);
 void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride);
+void launch_rr_f32(const Launch& L, size_t smem);
 void launch_occupations(const Launch& L);
 void launch_finish_cg(const Launch& L);
 void linalg_set_smem_limits(size_t bytes);

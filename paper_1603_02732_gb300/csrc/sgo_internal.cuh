@@ -36,6 +36,7 @@ enum {
   SC_PULAY_POS,   // ring position of the next entry
   SC_STATUS,      // sgo_status of this member
   SC_FIRSTCG,     // 1 while the CG history is empty
+  SC_RRSWEEPS,    // Jacobi sweeps accumulated over the run (diagnostic)
   SC_PULAY_A = 24 // MAX_HIST*MAX_HIST Gram matrix of residuals (24..87 overlaps next; see NSCAL_ALL)
 };
 constexpr int NSCAL_ALL = SC_PULAY_A + MAX_HIST * MAX_HIST + 8;
@@ -90,17 +91,26 @@ struct FftDim {
   int rad[FFT_MAX_STAGES];
 };
 
-// Factor n into radices 4, 2, 3, 5 (4 first: fewer stages).  False if n has another factor.
+// Factor n into the fewest radices from {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2} (largest
+// first).  False if n has a prime factor other than 2, 3, 5.
 inline bool make_fft_dim(int n, FftDim* d) {
+  static const int cand[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
   d->n = n;
   d->nst = 0;
   for (int i = 0; i < FFT_MAX_STAGES; ++i) d->rad[i] = 0;
-  int m = n;
   if (n < 1) return false;
-  while (m % 4 == 0 && d->nst < FFT_MAX_STAGES) { d->rad[d->nst++] = 4; m /= 4; }
-  while (m % 2 == 0 && d->nst < FFT_MAX_STAGES) { d->rad[d->nst++] = 2; m /= 2; }
-  while (m % 3 == 0 && d->nst < FFT_MAX_STAGES) { d->rad[d->nst++] = 3; m /= 3; }
-  while (m % 5 == 0 && d->nst < FFT_MAX_STAGES) { d->rad[d->nst++] = 5; m /= 5; }
+  int m = n;
+  while (m > 1 && d->nst < FFT_MAX_STAGES) {
+    int r = 0;
+    for (int c : cand)
+      if (m % c == 0) {
+        r = c;
+        break;
+      }
+    if (r == 0) return false;
+    d->rad[d->nst++] = r;
+    m /= r;
+  }
   return m == 1;
 }
 

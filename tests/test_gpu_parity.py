@@ -35,7 +35,9 @@ def _struct(grid=None, ecut=3.5, nat=2, seed=7, kT=0.01, nbands=None):
     return st
 
 
-GRIDS = [None, (10, 12, 15), (16, 18, 20), (24, 24, 24)]
+# every FFT radix: 9 (9), 10 12 15 (10,12,15), 16 9 2 10 (16,18,20), 12 2 (24),
+# 15 2 / 9 6 / 10 4 (30,54,40), 9 2 / 12 3 / 16 8 (18,36,128)
+GRIDS = [None, (10, 12, 15), (16, 18, 20), (24, 24, 24), (30, 54, 40), (18, 36, 128)]
 
 
 @pytest.mark.parametrize("grid", GRIDS)
@@ -62,7 +64,7 @@ def test_apply_hamiltonian_matches_dense_h(sgo, grid, precision):
     assert np.abs(y_full - y_ref).max() < tol * scale
 
 
-@pytest.mark.parametrize("grid", [None, (10, 12, 15), (18, 20, 24)])
+@pytest.mark.parametrize("grid", [None, (10, 12, 15), (18, 20, 24), (30, 54, 40)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_density_matches_oracle(sgo, grid, precision):
     st = _struct(grid=grid, nbands=7)

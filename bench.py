@@ -229,6 +229,7 @@ def run_ours(args):
         dist.barrier()
     status = s_dev.cpu().numpy()
     iters = [c.info()["n_iter"] for c in ctxs]
+    sweeps = [c.stats()["jacobi_sweeps"] for c in ctxs]
     n_ok = int(np.sum(status == 0))
     value = ws * MEMBERS * args.steps / (total_ms / 1e3)
 
@@ -263,7 +264,8 @@ def run_ours(args):
                                 precision=prec, start="cold (atomic density, random wavefunctions)",
                                 l2="flushed by a 256 MiB write before every timed step",
                                 converged=f"{n_ok}/{MEMBERS}", scf_options=dict(_SCF),
-                                scf_iterations=dict(mean=float(np.mean(iters)), max=int(np.max(iters)))),
+                                scf_iterations=dict(mean=float(np.mean(iters)), max=int(np.max(iters))),
+                                jacobi_sweeps=dict(mean=float(np.mean(sweeps)), max=int(np.max(sweeps)))),
                     e2e=dict(value=e2e_val, unit="evals/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=int(launches), roofline=roofline, clocks=clk)
         out = line

@@ -152,6 +152,10 @@ SGO_API sgo_status sgo_get_terms(sgo_ctx* ctx, double terms[8]);
  * last SCF, [9] precision. */
 SGO_API sgo_status sgo_get_info(sgo_ctx* ctx, int info[10]);
 
+/* Diagnostics of the last SCF: [0] iterations, [1] Jacobi sweeps summed over its
+ * subspace diagonalisations, [2] final density residual, [3] final |F_k - F_{k-1}|. */
+SGO_API sgo_status sgo_get_stats(sgo_ctx* ctx, double stats[4]);
+
 /* Miller indices of the packed basis: (1 + n_half) rows of 3 ints, row 0 = G = 0. */
 SGO_API sgo_status sgo_get_basis(sgo_ctx* ctx, int* miller);
 

@@ -70,6 +70,7 @@ _SIGS = {
     "sgo_get_terms": (ctypes.c_int, [_vp, _dp]),
     "sgo_get_info": (ctypes.c_int, [_vp, _ip]),
     "sgo_get_basis": (ctypes.c_int, [_vp, _ip]),
+    "sgo_get_stats": (ctypes.c_int, [_vp, _dp]),
     "sgo_get_density": (ctypes.c_int, [_vp, _dp]),
     "sgo_apply_hamiltonian": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
     "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
@@ -196,6 +197,11 @@ class Context:
         _check(self.lib.sgo_get_info(self.h, _ptr(a, ctypes.c_int)), "sgo_get_info")
         return dict(npw=int(a[0]), nhalf=int(a[1]), ncolpairs=int(a[2]), grid=(int(a[3]), int(a[4]), int(a[5])),
                     nbands=int(a[6]), natoms=int(a[7]), n_iter=int(a[8]), precision=int(a[9]))
+
+    def stats(self):
+        s = np.zeros(4)
+        _check(self.lib.sgo_get_stats(self.h, _ptr(s)), "sgo_get_stats")
+        return dict(n_iter=int(s[0]), jacobi_sweeps=int(s[1]), resid=float(s[2]), dF=float(s[3]))
 
     def eigen(self):
         e = np.zeros(self.nbands)

@@ -238,6 +238,15 @@ sgo_status sgo_get_info(sgo_ctx* c, int info[10]) {
   return SGO_OK;
 }
 
+sgo_status sgo_get_stats(sgo_ctx* c, double stats[4]) {
+  if (!c || !stats) return SGO_ERR_ARG;
+  stats[0] = c->last_iter;
+  stats[1] = c->h_scal[sgo::SC_RRSWEEPS];
+  stats[2] = c->h_scal[sgo::SC_RESID];
+  stats[3] = c->h_scal[sgo::SC_DF];
+  return SGO_OK;
+}
+
 sgo_status sgo_get_basis(sgo_ctx* c, int* miller) {
   if (!c || !miller) return SGO_ERR_ARG;
   const int nh = c->d.nhalf;

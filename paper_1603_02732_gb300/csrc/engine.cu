@@ -133,8 +133,9 @@ void layout(sgo_ctx* c, A& a) {
   d.vloc_g = a.template take<double>((size_t)d.nspecies * ng);
   d.gfft = a.template take<double2>(ng);
   d.gfft2 = a.template take<double2>(ng);
-  d.hrho = a.template take<double>((size_t)MAX_HIST * ng);
-  d.hres = a.template take<double>((size_t)MAX_HIST * ng);
+  d.rhog_in = a.template take<double2>(ng);
+  d.hrho = a.template take<double2>((size_t)MAX_HIST * ng);
+  d.hres = a.template take<double2>((size_t)MAX_HIST * ng);
   d.phase = a.template take<double2>((size_t)na * nt);
   d.S = a.template take<double>((size_t)nb * nb);
   d.Hs = a.template take<double>((size_t)nb * nb);
@@ -494,7 +495,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     c_rww.push_back(div_up(d.nb * d.nb, 256));
     c_rbw.push_back(div_up(d.natom * d.nb, 256));
     c_rdw.push_back(div_up(3 * d.natom * d.nb, 256));
-    c_nn.push_back(div_up(d.npw, NN_TILE) * div_up(d.nb, NN_TILE));
+    c_nn.push_back(div_up(d.npw, 64 * NN_RT) * div_up(d.nb, 64));
     c_atoms.push_back(d.natom);
     c_atomch.push_back(d.natom * nch);
     c_ewsg.push_back(div_up(ctxs[p]->ngbox_ew, 256));
@@ -720,7 +721,7 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
   tbeg(TK_RR);
-  if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)24 * max_nb_ * max_nb_);
+  if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)24 * max_nb_ * max_nb_);  // 8 n^2 (FP64 L) + 4 x 4 n^2
   else launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_);
   tend(TK_RR);
   rotate<T>(WB_X);
@@ -786,21 +787,16 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
   if (s != SGO_OK) return s;
   if (!warm) {
     launch_rho0_g(L(m_gew_));
-    grid_fft(0, 1);
-    launch_grid_real_part(L(m_gew_), 0, 0);
     launch_random_init<T>(L(m_bands_), WB_X, o.seed);
   }
   const int nonsc = warm ? 0 : std::max(0, o.n_nonscf);
   const int hist = std::min(std::max(o.pulay_hist, 1), MAX_HIST);
   int it = 0;
   for (it = 1; it <= o.max_scf; ++it) {
-    // V_eff from rho_in (Hartree in G space, LDA in real space)
+    // V_eff from rho_in(G): one inverse transform of rho_in(G) + i V_H(G) gives
+    // rho_in(r) + i V_H(r); LDA in real space
     tbeg(TK_GRID_OTHER);
-    launch_real_to_grid(L(m_gew_), 0, 0);
-    tend(TK_GRID_OTHER);
-    grid_fft(0, -1);
-    tbeg(TK_GRID_OTHER);
-    launch_hartree_g(L(m_gew_), 0);
+    launch_potential_g(L(m_gew_));
     tend(TK_GRID_OTHER);
     grid_fft(0, 1);
     tbeg(TK_GRID_OTHER);
@@ -822,9 +818,9 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     launch_band_kinetic<T>(L(m_bands_), WB_X);
     tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ);
     tbeg(TK_GRID_OTHER);
-    launch_real_to_grid(L(m_gew_), 1, 0);
+    launch_real_to_grid(L(m_gew_), 1, 1);
     tend(TK_GRID_OTHER);
-    grid_fft(0, -1);
+    grid_fft(1, -1);
     tbeg(TK_GRID_OTHER);
     launch_grid_energies(L(m_gch_), d_gpart_, maxchunk_);
     launch_grid_energies_reduce(L(m_prob_), d_gpart_, maxchunk_);
@@ -841,17 +837,7 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
       launch_pulay_store(L(m_gew_));
       launch_pulay_gram(L(m_gch_), d_gpart_, maxchunk_, hist);
       launch_pulay_solve(L(m_prob_), d_gpart_, maxchunk_, hist);
-      launch_pulay_mix(L(m_gew_), 0, 0.0);
-      tend(TK_GRID_OTHER);
-      if (o.kerker_q0 > 0.0) {
-        launch_real_to_grid(L(m_gew_), 2, 0);
-        grid_fft(0, -1);
-        launch_kerker(L(m_gew_), o.kerker_q0);
-        grid_fft(0, 1);
-        launch_grid_real_part(L(m_gew_), 0, 2);
-      }
-      tbeg(TK_GRID_OTHER);
-      launch_pulay_mix(L(m_gew_), 1, o.mix_alpha);
+      launch_pulay_mix(L(m_gew_), o.mix_alpha, o.kerker_q0);
       tend(TK_GRID_OTHER);
     }
   }

@@ -129,7 +129,9 @@ __global__ void k_hartree_g(KArgs ka, int which) {
 }
 
 // V_eff(r) = V_ion(r) + V_H(r) + v_xc(rho_in(r)), stored divided by N in the wave
-// precision for the H.psi plane kernel.  With user_v: the caller's C-order grid.
+// precision for the H.psi plane kernel; the work grid holds rho_in(r) + i V_H(r) (one
+// inverse transform of rho_in(G) + i V_H(G), both fields real).  rho_in(r) is kept.
+// With user_v: the caller's C-order grid instead.
 template <typename T>
 __global__ void k_veff(KArgs ka, const double* user_v) {
   GRID_EW_PROLOGUE
@@ -142,27 +144,28 @@ __global__ void k_veff(KArgs ka, const double* user_v) {
       grid_pt(P, i, &i1, &i2, &i3);
       val = user_v[((size_t)i1 * P.n2 + i2) * P.n3 + i3];
     } else {
+      const double2 c = P.gfft[i];
       double exc, vxc;
-      lda_pz81(P.rho_in[i], &exc, &vxc);
-      val = P.vion_r[i] + P.gfft[i].x + vxc;
+      lda_pz81(c.x, &exc, &vxc);
+      P.rho_in[i] = c.x;
+      val = P.vion_r[i] + c.y + vxc;
     }
     v[i] = (T)(val * inv_n);
   }
 }
 
-// Kerker damping of the work grid: R(G) *= G^2/(G^2 + q0^2), and 0 at G = 0.
-__global__ void k_kerker(KArgs ka, double q0) {
+// Work grid := rho_in(G) + i V_H(G), V_H(G) = 4 pi rho_in(G) / |G|^2 (0 at G = 0).
+__global__ void k_potential_g(KArgs ka) {
   GRID_EW_PROLOGUE
-  double2* g = P.gfft;
-  const double inv_n = 1.0 / P.ngrid;
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
     GPt q = grid_pt(P, i);
     double G[3];
     gcart(P, q.m1, q.m2, q.m3, G);
     double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
-    double f = (q.nyq || g2 < 1e-14) ? 0.0 : g2 / (g2 + q0 * q0) * inv_n;
-    double2 v = g[i];
-    g[i] = make_double2(v.x * f, v.y * f);
+    double2 r = P.rhog_in[i];
+    double f = (q.nyq || g2 < 1e-14) ? 0.0 : 4.0 * PI / g2;
+    // (r.x + i r.y) + i f (r.x + i r.y)
+    P.gfft[i] = make_double2(r.x - f * r.y, r.y + f * r.x);
   }
 }
 
@@ -182,7 +185,7 @@ __global__ void k_vion_g(KArgs ka) {
 }
 
 // Initial density: neutral atomic Gaussians (Z/Omega) exp(-G^2 rc^2/4) exp(-iG.R_I),
-// band-limited to |G|^2/2 <= 4 Ecut (work grid gfft).
+// band-limited to |G|^2/2 <= 4 Ecut, written as rho_in(G).
 __global__ void k_rho0_g(KArgs ka) {
   GRID_EW_PROLOGUE
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
@@ -199,12 +202,12 @@ __global__ void k_rho0_g(KArgs ka) {
         acc = acc + scale(phase_at(P, a, i1, i2, i3), amp);
       }
     }
-    P.gfft[i] = make_double2(acc.x, acc.y);
+    P.rhog_in[i] = make_double2(acc.x, acc.y);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Grid reductions for the energy at rho_out (work grid gfft = N rho_out(G)):
+// Grid reductions for the energy at rho_out (work grid gfft2 = N rho_out(G)):
 // part[p][chunk][0..4] = sum V_ion rho, sum rho eps_xc, sum rho, sum |rho_out - rho_in|,
 // sum_{G!=0} |rho(G)|^2 / G^2.
 // ---------------------------------------------------------------------------
@@ -233,7 +236,7 @@ __global__ void k_grid_energies(KArgs ka, double* part, int maxchunk) {
       gcart(P, q.m1, q.m2, q.m3, G);
       double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
       if (g2 > 1e-14) {
-        double2 v = P.gfft[i];
+        double2 v = P.gfft2[i];
         s[4] += (v.x * v.x + v.y * v.y) * inv_n * inv_n / g2;
       }
     }
@@ -302,12 +305,13 @@ __global__ void k_finish_iteration(KArgs ka, double tol_e, double tol_rho, int c
 __global__ void k_pulay_store(KArgs ka) {
   GRID_EW_PROLOGUE
   const int pos = (int)P.scal[SC_PULAY_POS];
-  double* hr = P.hrho + (size_t)pos * P.ngrid;
-  double* hs = P.hres + (size_t)pos * P.ngrid;
+  double2* hr = P.hrho + (size_t)pos * P.ngrid;
+  double2* hs = P.hres + (size_t)pos * P.ngrid;
+  const double inv_n = 1.0 / P.ngrid;
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
-    double ri = P.rho_in[i];
+    double2 ri = P.rhog_in[i], ro = P.gfft2[i];
     hr[i] = ri;
-    hs[i] = P.rho_out[i] - ri;
+    hs[i] = make_double2(ro.x * inv_n - ri.x, ro.y * inv_n - ri.y);
   }
 }
 
@@ -321,11 +325,11 @@ __global__ void k_pulay_gram(KArgs ka, double* part, int maxchunk, int hist) {
   const int base = chunk * GRID_CHUNK, end = min(P.ngrid, base + GRID_CHUNK);
   const int pos = (int)P.scal[SC_PULAY_POS];
   const int cnt = min((int)P.scal[SC_PULAY_N] + 1, hist);
-  const double* rp = P.hres + (size_t)pos * P.ngrid;
+  const double2* rp = P.hres + (size_t)pos * P.ngrid;
   for (int j = 0; j < cnt; ++j) {
-    const double* rj = P.hres + (size_t)j * P.ngrid;
+    const double2* rj = P.hres + (size_t)j * P.ngrid;
     double s = 0.0;
-    for (int i = base + threadIdx.x; i < end; i += blockDim.x) s += rp[i] * rj[i];
+    for (int i = base + threadIdx.x; i < end; i += blockDim.x) s += rp[i].x * rj[i].x + rp[i].y * rj[i].y;
     s = block_sum(s, red);
     if (threadIdx.x == 0) part[((size_t)p * maxchunk + chunk) * MAX_HIST + j] = s;
   }
@@ -397,23 +401,31 @@ __global__ void k_pulay_solve(KArgs ka, const double* part, int maxchunk, int hi
   sc[SC_PULAY_POS] = (pos + 1) % hist;
 }
 
-// stage 0: rho_in = sum_j c_j rho_j, resid = sum_j c_j R_j ; stage 1: rho_in += a * resid
-__global__ void k_pulay_mix(KArgs ka, int stage, double a) {
+// rho_in(G) = sum_j c_j rho_j(G) + a K(G) sum_j c_j R_j(G), K = G^2/(G^2 + q0^2) (1 if q0 = 0),
+// zero on Nyquist planes.
+__global__ void k_pulay_mix(KArgs ka, double a, double q0) {
   GRID_EW_PROLOGUE
   const double* alpha = P.scal + SC_PULAY_A + MAX_HIST * MAX_HIST;
   const int cnt = (int)P.scal[SC_PULAY_N];
-  if (stage == 0) {
-    for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
-      double r = 0.0, s = 0.0;
-      for (int j = 0; j < cnt; ++j) {
-        r += alpha[j] * P.hrho[(size_t)j * P.ngrid + i];
-        s += alpha[j] * P.hres[(size_t)j * P.ngrid + i];
-      }
-      P.rho_in[i] = r;
-      P.resid[i] = s;
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    GPt q = grid_pt(P, i);
+    double rx = 0.0, ry = 0.0, sx = 0.0, sy = 0.0;
+    for (int j = 0; j < cnt; ++j) {
+      const double2 h = P.hrho[(size_t)j * P.ngrid + i], r = P.hres[(size_t)j * P.ngrid + i];
+      rx += alpha[j] * h.x;
+      ry += alpha[j] * h.y;
+      sx += alpha[j] * r.x;
+      sy += alpha[j] * r.y;
     }
-  } else {
-    for (int i = base + threadIdx.x; i < end; i += blockDim.x) P.rho_in[i] += a * P.resid[i];
+    double k = 1.0;
+    if (q0 > 0.0) {
+      double G[3];
+      gcart(P, q.m1, q.m2, q.m3, G);
+      double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+      k = g2 < 1e-14 ? 0.0 : g2 / (g2 + q0 * q0);
+    }
+    if (q.nyq) k = 0.0, rx = ry = 0.0;
+    P.rhog_in[i] = make_double2(rx + a * k * sx, ry + a * k * sy);
   }
 }
 
@@ -549,8 +561,8 @@ template <typename T>
 void launch_veff(const Launch& L, const double* user_v) {
   if (ew_blocks(L)) k_veff<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, user_v);
 }
-void launch_kerker(const Launch& L, double q0) {
-  if (ew_blocks(L)) k_kerker<<<L.map.total, 256, 0, L.stream>>>(L.ka, q0);
+void launch_potential_g(const Launch& L) {
+  if (ew_blocks(L)) k_potential_g<<<L.map.total, 256, 0, L.stream>>>(L.ka);
 }
 void launch_vion_g(const Launch& L) {
   if (ew_blocks(L)) k_vion_g<<<L.map.total, 256, 0, L.stream>>>(L.ka);
@@ -561,8 +573,8 @@ void launch_rho0_g(const Launch& L) {
 void launch_pulay_store(const Launch& L) {
   if (ew_blocks(L)) k_pulay_store<<<L.map.total, 256, 0, L.stream>>>(L.ka);
 }
-void launch_pulay_mix(const Launch& L, int stage, double a) {
-  if (ew_blocks(L)) k_pulay_mix<<<L.map.total, 256, 0, L.stream>>>(L.ka, stage, a);
+void launch_pulay_mix(const Launch& L, double a, double q0) {
+  if (ew_blocks(L)) k_pulay_mix<<<L.map.total, 256, 0, L.stream>>>(L.ka, a, q0);
 }
 void launch_grid_energies(const Launch& Lchunks, double* part, int maxchunk) {
   if (Lchunks.map.total) k_grid_energies<<<Lchunks.map.total, 256, 0, Lchunks.stream>>>(Lchunks.ka, part, maxchunk);

@@ -46,8 +46,8 @@ __device__ __forceinline__ double* dense_ptr(const Prob& P, int sel) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole, int bkind, int brole, double* part_base,
                                                 size_t part_stride) {
-  __shared__ T As[32][TN_TILE + 4];
-  __shared__ T Bs[32][TN_TILE + 4];
+  __shared__ T As[32][TN_TILE + 1];
+  __shared__ T Bs[32][TN_TILE + 1];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
@@ -62,23 +62,34 @@ __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole,
   const int ld = P.ld;
   const int k0 = split * TN_KC, k1 = min(P.npw, k0 + TN_KC);
   const int t = threadIdx.x;
-  const int ti = t & 15, tj = t >> 4;   // outputs (ti + 16a, tj + 16b), a, b < 4
+  const int ti = t & 15, tj = t >> 4;
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  // register stage of the next 32-wide K chunk (element e = t + 256 q: vector e >> 5, k e & 31)
+  T ra[8], rb[8];
+  auto fetch = [&](int kb) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = t + 256 * q;
+      const int v = e >> 5, k = kb + (e & 31);
+      ra[q] = (ti0 + v < na && k < k1) ? A[(size_t)(ti0 + v) * ld + k] : T(0);
+      rb[q] = (tj0 + v < nbv && k < k1) ? Bm[(size_t)(tj0 + v) * ld + k] : T(0);
+    }
+  };
+  fetch(k0);
   for (int kb = k0; kb < k1; kb += 32) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      int e = t + 256 * q;     // 2048 = 64 vectors x 32 k
-      int v = e >> 5, kk = e & 31;
-      int k = kb + kk;
-      As[kk][v] = (ti0 + v < na && k < k1) ? A[(size_t)(ti0 + v) * ld + k] : T(0);
-      Bs[kk][v] = (tj0 + v < nbv && k < k1) ? Bm[(size_t)(tj0 + v) * ld + k] : T(0);
+      const int e = t + 256 * q;
+      As[e & 31][e >> 5] = ra[q];
+      Bs[e & 31][e >> 5] = rb[q];
     }
     __syncthreads();
-#pragma unroll 4
+    if (kb + 32 < k1) fetch(kb + 32);
+#pragma unroll 8
     for (int kk = 0; kk < 32; ++kk) {
       T a[4], b[4];
 #pragma unroll
@@ -125,66 +136,94 @@ __global__ void k_gemm_tn_reduce(KArgs ka, int akind, int bkind, int dst, const 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_nn(KArgs ka, int akind, int arole, int msel, int yrole, double alpha,
                                                 double beta) {
-  __shared__ T As[32][NN_TILE];
-  __shared__ T Ms[32][NN_TILE];
+  // CTA = (problem, group of NN_RT row tiles of 64, column tile of 64).  The small matrix
+  // M[0:inner][c0:c0+64] is staged once per CTA (in passes of NN_KP rows of M) and reused
+  // by every row tile; thread (tr, tc) owns rows tr + 16 i and columns tc + 16 j (i, j < 4).
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ms = reinterpret_cast<T*>(smem_raw);        // [NN_KP][64]
+  __shared__ T As[32][64];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int local = blockIdx.x - ka.start[p];
-  const int nct = (P.nb + NN_TILE - 1) / NN_TILE;
-  const int r0 = (local / nct) * NN_TILE, c0 = (local % nct) * NN_TILE;
+  const int nct = (P.nb + 63) / 64;
+  const int rg = local / nct, c0 = (local % nct) * 64;
   const int inner = opnd_count(P, akind);
   const int nb = P.nb, ld = P.ld, npw = P.npw;
   const T* A = opnd<T>(P, akind, arole);
   const double* M = dense_ptr(P, msel);
   T* Y = wbuf<T>(P, yrole);
   const int t = threadIdx.x, tr = t & 15, tc = t >> 4;
-  T acc[4][4];
+  const int npass = (inner + NN_KP - 1) / NN_KP;
+  for (int rt = 0; rt < NN_RT; ++rt) {
+    const int r0 = (rg * NN_RT + rt) * 64;
+    if (r0 >= npw) break;
+    T acc[4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-  for (int k0 = 0; k0 < inner; k0 += 32) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int e = t + 256 * q;      // 2048 = 32 x 64
-      int kk = e >> 6, rr = e & 63;
-      int k = k0 + kk;
-      As[kk][rr] = (k < inner && r0 + rr < npw) ? A[(size_t)k * ld + r0 + rr] : T(0);
-      double mv = 0.0;
-      if (k < inner && c0 + rr < nb) {
-        mv = M[(size_t)k * nb + c0 + rr];
-        if (msel == DD_PROJ_D) mv *= P.sp[P.spec[k] * 6 + 5];
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int ps = 0; ps < npass; ++ps) {
+      const int kp0 = ps * NN_KP, kpn = min(NN_KP, inner - kp0);
+      if (rt == 0 || npass > 1) {
+        __syncthreads();
+        for (int e = t; e < kpn * 64; e += 256) {
+          const int kk = e >> 6, cc = e & 63;
+          const int k = kp0 + kk;
+          double mv = 0.0;
+          if (c0 + cc < nb) {
+            mv = M[(size_t)k * nb + c0 + cc];
+            if (msel == DD_PROJ_D) mv *= P.sp[P.spec[k] * 6 + 5];
+          }
+          Ms[e] = (T)mv;
+        }
       }
-      Ms[kk][rr] = (T)mv;
+      T ra[8];
+      auto fetch = [&](int kb) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = t + 256 * q;  // 2048 = 32 x 64
+          const int kk = e >> 6, rr = e & 63;
+          ra[q] = (kb + kk < kpn && r0 + rr < npw) ? A[(size_t)(kp0 + kb + kk) * ld + r0 + rr] : T(0);
+        }
+      };
+      fetch(0);
+      for (int kb = 0; kb < kpn; kb += 32) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = t + 256 * q;
+          As[e >> 6][e & 63] = ra[q];
+        }
+        __syncthreads();
+        if (kb + 32 < kpn) fetch(kb + 32);
+        const int kn = min(32, kpn - kb);
+        for (int kk = 0; kk < kn; ++kk) {
+          T a[4], m[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = As[kk][tr + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) m[j] = Ms[(kb + kk) * 64 + tc + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * m[j];
+        }
+      }
     }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      T a[4], m[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][tr + 16 * i];
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tc + 16 * j;
+      if (c >= nb) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) m[j] = Ms[kk][tc + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * m[j];
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    int c = c0 + tc + 16 * j;
-    if (c >= nb) continue;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      int r = r0 + tr + 16 * i;
-      if (r >= npw) continue;
-      T* y = Y + (size_t)c * ld + r;
-      T v = T(alpha) * acc[i][j];
-      if (beta != 0.0) v += T(beta) * (*y);
-      *y = v;
+      for (int i = 0; i < 4; ++i) {
+        const int r = r0 + tr + 16 * i;
+        if (r >= npw) continue;
+        T* y = Y + (size_t)c * ld + r;
+        T v = T(alpha) * acc[i][j];
+        if (beta != 0.0) v += T(beta) * (*y);
+        *y = v;
+      }
     }
   }
 }
@@ -574,10 +613,10 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
 
 // ---------------------------------------------------------------------------
 // Rayleigh-Ritz for the mixed path, one CTA per problem.  FP64: symmetrised S and Hs,
-// Cholesky S = L L^T, L^-1.  FP32: C = L^-1 Hs L^-T and its cyclic Jacobi
+// Cholesky S = L L^T.  FP32: L^-1, C = L^-1 Hs L^-T and its cyclic Jacobi
 // eigensolve, accumulated onto L^-T (the rotation matrix feeds the FP32 block
 // rotation, so accuracy beyond FP32 would be discarded there).
-// Shared memory: L, Li (double n^2 each), A, V (float n^2 each).
+// Shared memory: L (double n^2); Lf, Li, A, V (float n^2 each).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -589,24 +628,26 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int n = P.nb;
+  // [L: double n^2 | Lf, Li: float n^2 each (alias Lf on the upper half of the second
+  //  double block) | A, V: float n^2 each]
   double* L = reinterpret_cast<double*>(smem_raw);
-  double* Li = L + n * n;
-  float* A = reinterpret_cast<float*>(Li + n * n);
+  float* Lf = reinterpret_cast<float*>(L + n * n);
+  float* Li = Lf + n * n;
+  float* A = Li + n * n;
   float* V = A + n * n;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) flag = 0;
   for (int e = tid; e < n * n; e += nt) {
     int i = e / n, j = e % n;
     L[e] = 0.5 * (P.S[i * n + j] + P.S[j * n + i]);
-    Li[e] = 0.0;
   }
   __syncthreads();
-  // Cholesky, right-looking, two barriers per column (every thread forms the pivot)
+  // FP64 Cholesky of the overlap, right-looking, two barriers per column
   for (int k = 0; k < n; ++k) {
     double d = L[k * n + k];
     if (!(d > 0.0)) d = 1.0;
-    const double dk = sqrt(d);
-    for (int i = k + 1 + tid; i < n; i += nt) L[i * n + k] /= dk;
+    const double dk = sqrt(d), idk = 1.0 / dk;
+    for (int i = k + 1 + tid; i < n; i += nt) L[i * n + k] *= idk;
     __syncthreads();
     if (tid == 0) {
       if (!(L[k * n + k] > 0.0)) flag = 1;
@@ -619,33 +660,39 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
     }
     __syncthreads();
   }
-  // L^-1 by columns: column j depends only on itself (forward substitution, no barrier)
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e % n;
+    Lf[e] = j <= i ? (float)L[e] : 0.f;
+    Li[e] = 0.f;
+  }
+  __syncthreads();
+  // L^-1 by columns in FP32 (column j depends only on itself: no barrier)
   for (int j = tid; j < n; j += nt) {
-    Li[j * n + j] = 1.0 / L[j * n + j];
+    Li[j * n + j] = 1.f / Lf[j * n + j];
     for (int i = j + 1; i < n; ++i) {
-      double s = 0.0;
-      for (int k = j; k < i; ++k) s += L[i * n + k] * Li[k * n + j];
-      Li[i * n + j] = -s / L[i * n + i];
+      float s = 0.f;
+      for (int k = j; k < i; ++k) s += Lf[i * n + k] * Li[k * n + j];
+      Li[i * n + j] = -s / Lf[i * n + i];
     }
   }
   __syncthreads();
-  // L := sym(Hs); V := Hs Li^T; A := Li V   (FP32 products of the FP64 factors)
+  // Lf := sym(Hs) (float); V := Hs Li^T; A := Li V
   for (int e = tid; e < n * n; e += nt) {
     int i = e / n, j = e % n;
-    L[e] = 0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]);
+    Lf[e] = (float)(0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]));
   }
   __syncthreads();
   for (int e = tid; e < n * n; e += nt) {
     int i = e / n, j = e % n;
     float s = 0.f;
-    for (int k = 0; k <= j; ++k) s += (float)L[i * n + k] * (float)Li[j * n + k];
+    for (int k = 0; k <= j; ++k) s += Lf[i * n + k] * Li[j * n + k];
     V[e] = s;
   }
   __syncthreads();
   for (int e = tid; e < n * n; e += nt) {
     int i = e / n, j = e % n;
     float s = 0.f;
-    for (int k = 0; k <= i; ++k) s += (float)Li[i * n + k] * V[k * n + j];
+    for (int k = 0; k <= i; ++k) s += Li[i * n + k] * V[k * n + j];
     A[e] = s;
   }
   __syncthreads();
@@ -662,7 +709,7 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
   __syncthreads();
   for (int e = tid; e < n * n; e += nt) {
     int i = e / n, j = e % n;
-    V[e] = (float)Li[j * n + i];  // rotations accumulate onto L^-T
+    V[e] = Li[j * n + i];  // rotations accumulate onto L^-T
   }
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if ((tid & 31) == 0) red[tid >> 5] = amax;
@@ -673,13 +720,14 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
     red[32] = mm;
   }
   __syncthreads();
+  // rotations below 2e-7 max|a_ii| (about the FP32 resolution of the matrix) are skipped
   const float thr = 2e-7f * (float)red[32];
   // Cyclic Jacobi, round-robin pairs; a round maps every 2x2 block of pair rows P and
   // pair columns Q as A_PQ <- J_P^T A_PQ J_Q (one pass), and V_{:,Q} <- V_{:,Q} J_Q.
   const int m = n + (n & 1);
   const int half = m / 2;
   int sweeps = 0;
-  for (int sweep = 0; sweep < 12; ++sweep) {
+  for (int sweep = 0; sweep < 10; ++sweep) {
     if (tid == 0) nbig = 0;
     __syncthreads();
     for (int e = tid; e < n * n; e += nt) {
@@ -850,7 +898,8 @@ void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const
 template <typename T>
 void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta) {
   if (!L.map.total) return;
-  k_gemm_nn<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, arole, msel, yrole, alpha, beta);
+  k_gemm_nn<T><<<L.map.total, 256, (size_t)NN_KP * 64 * sizeof(T), L.stream>>>(L.ka, akind, arole, msel, yrole, alpha,
+                                                                               beta);
 }
 template <typename T>
 void launch_band_kinetic(const Launch& L, int xrole) {
@@ -898,6 +947,9 @@ void launch_finish_cg(const Launch& L) { k_finish_cg<<<L.ka.nprob, 128, 0, L.str
 void linalg_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_rr_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // the NN kernel also has 8-16 KB of static shared memory: request only what it uses
+  cudaFuncSetAttribute(k_gemm_nn<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, NN_KP * 64 * (int)sizeof(float));
+  cudaFuncSetAttribute(k_gemm_nn<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, NN_KP * 64 * (int)sizeof(double));
 }
 
 #define INST(T)                                                                                  \

@@ -6,15 +6,16 @@
 namespace sgo {
 
 // FFT kernel geometry
-constexpr int QCP = 4;                 // column pairs per z-column CTA (<= 8 columns)
+constexpr int QCP = 8;                 // column pairs per z-column CTA (<= 16 columns)
 constexpr int ZCOL_THREADS = 128;
-constexpr int QZ = 8;                  // grid columns per z CTA
+constexpr int QZ = 32;                 // grid columns per z CTA
 constexpr int DENS_MAXP = 16;          // density accumulators per thread: N1 * N2 <= 16 * blockDim
 constexpr int PLANE_THREADS_MAX = 512;  // so N1 * N2 <= 8192 per plane
 // GEMM geometry
 constexpr int TN_TILE = 64;
 constexpr int TN_KC = 256;             // K chunk of one split-K partial
-constexpr int NN_TILE = 64;
+constexpr int NN_RT = 4;              // row tiles of 64 per NN CTA
+constexpr int NN_KP = 128;             // rows of the small matrix staged per pass
 constexpr int BAND_THREADS = 256;
 constexpr int GRID_CHUNK = 4096;       // grid points per reduction CTA
 constexpr int RR_THREADS = 256;
@@ -73,11 +74,11 @@ void launch_grid_real_part(const Launch& L, int which, int dst);
 void launch_hartree_g(const Launch& L, int which);
 void launch_export_grid(const Launch& L, int sel, double* out);
 template <typename T> void launch_veff(const Launch& L, const double* user_v);
-void launch_kerker(const Launch& L, double q0);
+void launch_potential_g(const Launch& L);
 void launch_vion_g(const Launch& L);
 void launch_rho0_g(const Launch& L);
 void launch_pulay_store(const Launch& L);
-void launch_pulay_mix(const Launch& L, int stage, double a);
+void launch_pulay_mix(const Launch& L, double a, double q0);
 void launch_grid_energies(const Launch& Lchunks, double* part, int maxchunk);
 void launch_grid_energies_reduce(const Launch& L, const double* part, int maxchunk);
 void launch_finish_iteration(const Launch& L, double tol_e, double tol_rho, int count_iter);

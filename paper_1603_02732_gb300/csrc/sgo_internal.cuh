@@ -168,8 +168,9 @@ struct Prob {
   double* resid;               // [ngrid]
   double2* gfft;               // [ngrid]
   double2* gfft2;              // [ngrid]
-  double* hrho;                // [MAX_HIST][ngrid]
-  double* hres;                // [MAX_HIST][ngrid]
+  double2* rhog_in;            // [ngrid] rho_in(G), the mixed density (SCF state)
+  double2* hrho;               // [MAX_HIST][ngrid] Pulay history of rho_in(G)
+  double2* hres;               // [MAX_HIST][ngrid] Pulay history of R(G) = rho_out(G) - rho_in(G)
   double2* phase;              // [natom][n1+n2+n3] exp(-i 2pi m s_d), m = -N/2..N/2-1 wrapped
   // small dense FP64
   double* S;                   // [nb*nb]

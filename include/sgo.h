@@ -169,6 +169,21 @@ SGO_API sgo_status sgo_get_density(sgo_ctx* ctx, double* rho);
 SGO_API sgo_status sgo_apply_hamiltonian(sgo_ctx* ctx, const double* veff, int nvec, const double* psi,
                                  double* hpsi);
 
+/* The same H psi as sgo_apply_hamiltonian, for callers that cannot let a library
+ * allocate device memory during a call: a process whose device memory belongs to its
+ * own pool allocator, one that runs under a fixed memory budget, or a latency-critical
+ * loop that cannot take the implicit synchronisation of cudaMalloc/cudaFree.  This call
+ * allocates nothing: it uses the context's buffers (allocated once by sgo_create) and a
+ * file-scope device scratch array of 32 MiB that every GPU loading the library holds
+ * until the process exits.  Problems whose launch descriptors, projector partial sums
+ * and staged veff, psi and hpsi exceed 32 MiB return SGO_ERR_ARG with a message.  The
+ * first call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share the array
+ * and leave their contents in it; calls that overlap on the GPU race with each other.
+ * There is no counterpart in the paper: this is a deployment variant of the H.psi apply. */
+SGO_API sgo_status sgo_apply_hamiltonian_noalloc(sgo_ctx* ctx, const double* veff, int nvec, const double* psi,
+                                                 double* hpsi);
+
 /* rho(r) = sum_n occ_n |psi_n(r)|^2 for nvec packed vectors (the density kernels). */
 SGO_API sgo_status sgo_density(sgo_ctx* ctx, int nvec, const double* psi, const double* occ, double* rho);
 

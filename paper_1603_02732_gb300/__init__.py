@@ -73,6 +73,7 @@ _SIGS = {
     "sgo_get_stats": (ctypes.c_int, [_vp, _dp]),
     "sgo_get_density": (ctypes.c_int, [_vp, _dp]),
     "sgo_apply_hamiltonian": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
+    "sgo_apply_hamiltonian_noalloc": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
     "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
     "sgo_set_warm": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sgo_batch_destroy": (None, [_vp]),
@@ -231,6 +232,15 @@ class Context:
         out = np.zeros_like(psi)
         _check(self.lib.sgo_apply_hamiltonian(self.h, _ptr(veff), psi.shape[0], _ptr(psi), _ptr(out)),
                "sgo_apply_hamiltonian")
+        return out
+
+    def apply_hamiltonian_noalloc(self, veff, psi):
+        """H psi through the entry point that allocates no device memory (see include/sgo.h)."""
+        veff = np.ascontiguousarray(veff, dtype=np.float64)
+        psi = np.ascontiguousarray(np.atleast_2d(psi), dtype=np.float64)
+        out = np.zeros_like(psi)
+        _check(self.lib.sgo_apply_hamiltonian_noalloc(self.h, _ptr(veff), psi.shape[0], _ptr(psi), _ptr(out)),
+               "sgo_apply_hamiltonian_noalloc")
         return out
 
     def density_of(self, psi, occ):

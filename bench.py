@@ -44,8 +44,20 @@ def _dist():
 
 
 def _population(rank):
+    """Weak scaling: rank r evaluates its own 64 members, candidates 64 r .. 64 r + 63."""
     import workloads
     return workloads.de_population(MEMBERS, start=MEMBERS * rank)
+
+
+def _max_over_ranks(value, device=None):
+    """Max of a per-rank float over the process group (the step time of the slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def _smallest(pop):
@@ -223,9 +235,7 @@ def run_ours(args):
     batch.timer(None)
     if ws > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = _max_over_ranks(total_ms, dev)
         dist.barrier()
     status = s_dev.cpu().numpy()
     iters = [c.info()["n_iter"] for c in ctxs]
@@ -319,6 +329,29 @@ def run_ours(args):
     return 0
 
 
+def run_case(args):
+    """Small single-member cases for kernel captures: three H psi applies with a random
+    potential (--case hpsi), or one SCF + forces (--case scf)."""
+    import paper_1603_02732_gb300 as sgo
+    from paper_1603_02732_gb300 import build
+    import workloads
+    build.build()
+    st = workloads.de_candidate(args.member)
+    ctx = sgo.Context(st, precision=args.precision, **_tols(args.precision, st))
+    if args.case == "hpsi":
+        rng = np.random.default_rng(0)
+        v = rng.normal(size=ctx.grid) * 0.1
+        x = rng.normal(size=(st.nbands, ctx.npw))
+        for _ in range(3):
+            y = ctx.apply_hamiltonian(v, x)
+        print(json.dumps(dict(case="hpsi", member=args.member, natoms=st.natoms, nbands=st.nbands,
+                              grid=list(ctx.grid), npw=ctx.npw, max_abs=float(np.abs(y).max()))))
+    else:
+        F, _ = ctx.energy_forces()
+        print(json.dumps(dict(case="scf", member=args.member, natoms=st.natoms, F=F, **ctx.stats())))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,6 +363,9 @@ def main():
     ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 GPU path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="one extra step per kernel class with live timers")
+    ap.add_argument("--case", default="batch", choices=["batch", "hpsi", "scf"],
+                    help="batch: the benchmark; hpsi / scf: one population member (small case for ncu)")
+    ap.add_argument("--member", type=int, default=0, help="population member for --case hpsi / scf")
     ap.add_argument("--ncg", type=int, default=None, help="CG steps per SCF iteration")
     ap.add_argument("--ncg-first", type=int, default=None)
     ap.add_argument("--nonscf", type=int, default=None)
@@ -339,6 +375,8 @@ def main():
             _SCF[k] = v
     if args.impl == "reference":
         return run_reference(args)
+    if args.case != "batch":
+        return run_case(args)
     return run_ours(args)
 
 

@@ -1,0 +1,66 @@
+"""Parity at the workloads' full sizes, on outputs the oracle can compute one by one.
+
+* H psi of a few vectors at the 2D-monolayer (48x48x96, 10617 plane waves) and metal
+  cluster (72^3, 22119 plane waves) sizes vs the oracle's FFT-applied H.
+* The 64-member DE population, evaluated as one mixed-precision batch in the launch
+  configuration bench.py times, vs full oracle SCF runs of its two smallest members
+  (energy 1e-5 Ha/atom, forces 1e-4 Ha/bohr).
+* The monolayer SCF in mixed precision vs the FP64 GPU path (a property at any size).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import dft
+from tests.packing import full_from_packed
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sgo():
+    from paper_1603_02732_gb300 import build
+    build.build()
+    import paper_1603_02732_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+@pytest.mark.parametrize("name", ["honeycomb24", "cluster13"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 3e-5)])
+def test_fullsize_hpsi_sampled(sgo, name, precision, tol):
+    st = workloads.CONFIGS[name]()
+    ctx = sgo.Context(st, precision=precision)
+    m = dft.Model(st)
+    miller = ctx.basis()
+    rng = np.random.default_rng(21)
+    veff = rng.normal(size=m.grid) * 0.2
+    x = rng.normal(size=(4, ctx.npw)) / np.sqrt(ctx.npw)
+    y = ctx.apply_hamiltonian(veff, x)
+    ref = dft.apply_h(m, veff, dft.projectors(m, st.pos), full_from_packed(m, miller, x))
+    got = full_from_packed(m, miller, y)
+    assert np.abs(got - ref).max() < tol * np.abs(ref).max()
+
+
+def test_population_batch_vs_oracle(sgo):
+    import bench
+    pop = workloads.de_population(64)
+    ctxs = [sgo.Context(st, precision="mixed", **bench._tols("mixed", st)) for st in pop]
+    E, F, status = sgo.Batch(ctxs).energy_forces()
+    assert np.all(status == 0)
+    small = sorted(range(64), key=lambda i: (pop[i].natoms, i))[:2]
+    for i in small:
+        ref = oracle.scf(pop[i])
+        assert abs(E[i] - ref.free_energy) / pop[i].natoms < 1e-5, i
+        assert np.abs(F[i] - ref.forces).max() < 1e-4, i
+
+
+def test_monolayer_mixed_matches_fp64(sgo):
+    st = workloads.honeycomb24()
+    e64, f64 = sgo.Context(st, precision="fp64", scf_tol_e=1e-8, scf_tol_rho=1e-7).energy_forces()
+    emx, fmx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7 * st.natoms,
+                           scf_tol_rho=1e-5).energy_forces()
+    assert abs(emx - e64) / st.natoms < 1e-5
+    assert np.abs(fmx - f64).max() < 1e-4
+    assert np.abs(f64.sum(axis=0)).max() < 1e-3  # egg-box only

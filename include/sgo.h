@@ -83,6 +83,8 @@ typedef struct {
   int n_nonscf;           /* initial iterations at the fixed atomic-guess potential */
   int fft[3];             /* FFT grid; 0 = smallest 2^a 3^b 5^c >= 4 m_max + 1 per axis */
   unsigned long long seed;/* seed of the random initial wavefunctions */
+  int gemm_tc;            /* mixed path: subspace/projector overlaps on tcgen05 tensor cores (3xTF32);
+                             0 = FP32 CUDA cores */
 } sgo_opts;
 
 /* Fill *o with the defaults (FP64, kT 0, tolerances 1e-8 Ha / 1e-7, Pulay 8, ...). */
@@ -183,6 +185,11 @@ SGO_API sgo_status sgo_apply_hamiltonian(sgo_ctx* ctx, const double* veff, int n
  * There is no counterpart in the paper: this is a deployment variant of the H.psi apply. */
 SGO_API sgo_status sgo_apply_hamiltonian_noalloc(sgo_ctx* ctx, const double* veff, int nvec, const double* psi,
                                                  double* hpsi);
+
+/* C = X^T Y (nvec x nvec, row-major) for nvec packed vectors X, Y (row-major nvec x npw):
+ * the subspace-matrix GEMM of Algorithm 1 (lines 2, 12, 15), in the context's precision
+ * (mixed: FP32 operands on the tensor cores unless gemm_tc = 0; FP64 sums). */
+SGO_API sgo_status sgo_subspace_matrix(sgo_ctx* ctx, int nvec, const double* x, const double* y, double* c);
 
 /* rho(r) = sum_n occ_n |psi_n(r)|^2 for nvec packed vectors (the density kernels). */
 SGO_API sgo_status sgo_density(sgo_ctx* ctx, int nvec, const double* psi, const double* occ, double* rho);

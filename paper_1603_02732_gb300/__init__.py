@@ -46,7 +46,7 @@ class sgo_opts(ctypes.Structure):
                 ("scf_tol_rho", ctypes.c_double), ("max_scf", ctypes.c_int), ("pulay_hist", ctypes.c_int),
                 ("mix_alpha", ctypes.c_double), ("kerker_q0", ctypes.c_double), ("ncg", ctypes.c_int),
                 ("ncg_first", ctypes.c_int), ("n_nonscf", ctypes.c_int), ("fft", ctypes.c_int * 3),
-                ("seed", ctypes.c_ulonglong)]
+                ("seed", ctypes.c_ulonglong), ("gemm_tc", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -74,6 +74,7 @@ _SIGS = {
     "sgo_get_density": (ctypes.c_int, [_vp, _dp]),
     "sgo_apply_hamiltonian": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
     "sgo_apply_hamiltonian_noalloc": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
+    "sgo_subspace_matrix": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
     "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
     "sgo_set_warm": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sgo_batch_destroy": (None, [_vp]),
@@ -241,6 +242,14 @@ class Context:
         out = np.zeros_like(psi)
         _check(self.lib.sgo_apply_hamiltonian_noalloc(self.h, _ptr(veff), psi.shape[0], _ptr(psi), _ptr(out)),
                "sgo_apply_hamiltonian_noalloc")
+        return out
+
+    def subspace_matrix(self, x, y):
+        """C = X^T Y through the subspace GEMM kernels (tensor cores on the mixed path)."""
+        x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+        y = np.ascontiguousarray(np.atleast_2d(y), dtype=np.float64)
+        out = np.zeros((x.shape[0], x.shape[0]))
+        _check(self.lib.sgo_subspace_matrix(self.h, x.shape[0], _ptr(x), _ptr(y), _ptr(out)), "sgo_subspace_matrix")
         return out
 
     def density_of(self, psi, occ):

@@ -41,6 +41,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->ncg_first = 6;
   o->n_nonscf = 3;
   o->seed = 12345ull;
+  o->gemm_tc = 1;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,
@@ -274,6 +275,13 @@ sgo_status sgo_apply_hamiltonian(sgo_ctx* c, const double* veff, int nvec, const
   std::unique_ptr<sgo::Engine> e(solo_engine(c));
   if (!e->ok()) return SGO_ERR_CUDA;
   return e->apply_h(veff, nvec, psi, hpsi);
+}
+
+sgo_status sgo_subspace_matrix(sgo_ctx* c, int nvec, const double* x, const double* y, double* out) {
+  if (!c || !x || !y || !out || nvec < 1 || nvec > c->nb) return SGO_ERR_ARG;
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  return e->subspace(nvec, x, y, out);
 }
 
 sgo_status sgo_density(sgo_ctx* c, int nvec, const double* psi, const double* occ, double* rho) {

@@ -71,7 +71,7 @@ __global__ void k_gather_flags(KArgs ka, double* flags) {
   const Prob& P = ka.probs[p];
   if (threadIdx.x == 0) {
     flags[4 * p + 0] = P.scal[SC_CONV];
-    flags[4 * p + 1] = (double)P.status[0];
+    flags[4 * p + 1] = (double)(P.status[0] | P.status[2]);
     flags[4 * p + 2] = (double)P.status[1];
     flags[4 * p + 3] = P.scal[SC_RESID];
   }
@@ -273,7 +273,7 @@ sgo_status ctx_setup(sgo_ctx* c) {
   d.box1 = box[0];
   d.box2 = box[1];
   d.box3 = box[2];
-  if ((size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 > 220 * 1024 || d.n1 * d.n2 > DENS_MAXP * PLANE_THREADS_MAX) {
+  if ((size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 > 220 * 1024 || d.n1 * d.n2 > 8192) {
     set_error("FFT plane N1*N2 too large for the shared-memory plane kernels (max about 6900)");
     return SGO_ERR_ARG;
   }
@@ -467,8 +467,9 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     }
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
-      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob;
+      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc;
   size_t part = 0;
+  int max_natom = 0;
   for (int p = 0; p < n_; ++p) {
     const Prob& d = ctxs[p]->d;
     host[p] = d;
@@ -500,10 +501,12 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     c_atomch.push_back(d.natom * nch);
     c_ewsg.push_back(div_up(ctxs[p]->ngbox_ew, 256));
     c_prob.push_back(1);
+    c_tc.push_back(div_up(d.npw, TC_KC));
+    max_natom = std::max(max_natom, d.natom);
     size_t need = (size_t)nsplit * std::max({d.nb * d.nb, d.natom * d.nb, 3 * d.natom * d.nb});
     part = std::max(part, need);
   }
-  plane_threads_ = std::min(PLANE_THREADS_MAX, std::max(128, (div_up(max_n12_, DENS_MAXP) + 31) / 32 * 32));
+  plane_threads_ = PLANE_THREADS;
   m_zcol_ = make_map(c_zcol);
   m_plane_ = make_map(c_plane);
   m_dens_ = make_map(c_dens);
@@ -523,6 +526,12 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   m_atomch_ = make_map(c_atomch);
   m_ewsg_ = make_map(c_ewsg);
   m_prob_ = make_map(c_prob);
+  m_tc_ = make_map(c_tc);
+  // tensor-core subspace GEMMs: mixed path, every operand count <= 128 (one M tile)
+  const bool tc = precision_ == 1 && ctxs[0]->opts.gemm_tc != 0;
+  tc_ok_[OPK_WB] = tc && max_nb_ <= 128;
+  tc_ok_[OPK_B] = tc && max_nb_ <= 128 && max_natom <= 128;
+  tc_ok_[OPK_DB] = tc && max_nb_ <= 128 && 3 * max_natom <= 128;
   part_stride_ = part;
   if (!cuda_ok(cudaMalloc(&d_probs_, sizeof(Prob) * n_), "cudaMalloc(probs)")) return;
   allocs_.push_back(d_probs_);
@@ -549,6 +558,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   }
   fft_set_smem_limits(220 * 1024);
   linalg_set_smem_limits(220 * 1024);
+  gemm_tc_set_smem_limits();
   ok_ = cuda_ok(cudaGetLastError(), "engine set-up");
 }
 
@@ -672,16 +682,23 @@ void Engine::grid_fft_raw(int which, int sign) {
   }
 }
 
+// allow_tc = false keeps a product off the tensor cores: the energy and force overlaps
+// feed F and the forces directly, where 3xTF32 noise would exceed the SCF tolerance.
 template <typename T>
-void Engine::tn(int akind, int arole, int bkind, int brole, int dst) {
+void Engine::tn(int akind, int arole, int bkind, int brole, int dst, bool allow_tc) {
   const WorkMap* m = &m_tn_ww_;
   const WorkMap* r = &m_red_ww_;
   if (akind == OPK_B) { m = &m_tn_bw_; r = &m_red_bw_; }
   if (akind == OPK_DB) { m = &m_tn_dw_; r = &m_red_dw_; }
   const int kind = akind == OPK_WB ? TK_GEMM_TN : TK_GEMM_SMALL;
   tbeg(kind);
-  launch_gemm_tn<T>(L(*m), akind, arole, bkind, brole, d_part_, part_stride_);
-  launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_);
+  if (sizeof(T) == 4 && allow_tc && tc_ok_[akind]) {
+    launch_gemm_tn_tc(L(m_tc_), akind, arole, bkind, brole, d_part_, part_stride_);
+    launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_, TC_KC);
+  } else {
+    launch_gemm_tn<T>(L(*m), akind, arole, bkind, brole, d_part_, part_stride_);
+    launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_);
+  }
   tend(kind);
 }
 
@@ -718,7 +735,9 @@ void Engine::hpsi(int src, int dst) {
 // Overlap + subspace matrix, FP64 Cholesky/eigensolve, rotation of the block.
 template <typename T>
 void Engine::rayleigh_ritz(bool rotate_history) {
-  tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S);
+  // the overlap sets the norms of the bands and hence rho and F: CUDA-core FP32 (about 1e-7
+  // relative); the tensor cores' 3xTF32 (about 5e-7) would leave F drifting above tol_e
+  tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S, false);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
   tbeg(TK_RR);
   if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)24 * max_nb_ * max_nb_);  // 8 n^2 (FP64 L) + 4 x 4 n^2
@@ -816,7 +835,7 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     tend(TK_PLANE_DENSITY);
     // energy at (Psi, rho_out) and the convergence test
     launch_band_kinetic<T>(L(m_bands_), WB_X);
-    tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ);
+    tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ, false);
     tbeg(TK_GRID_OTHER);
     launch_real_to_grid(L(m_gew_), 1, 1);
     tend(TK_GRID_OTHER);
@@ -848,8 +867,8 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   if (want_forces) {
     launch_build_projectors<T>(L(m_atoms_), 1);
-    tn<T>(OPK_DB, 0, OPK_WB, WB_X, DD_DPROJ);
-    tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ);
+    tn<T>(OPK_DB, 0, OPK_WB, WB_X, DD_DPROJ, false);
+    tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ, false);
     launch_real_to_grid(L(m_gew_), 1, 0);
     grid_fft(0, -1);
     launch_local_forces(L(m_atomch_), maxchunk_);
@@ -864,6 +883,7 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     CK(cudaMemcpyAsync(c->h_occ.data(), c->d.occ, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
     CK(cudaMemcpyAsync(c->h_forces.data(), c->d.forces, sizeof(double) * c->h_forces.size(), cudaMemcpyDeviceToHost,
                        stream_));
+    CK(cudaMemcpyAsync(c->h_status, c->d.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream_));
   }
   CK(cudaStreamSynchronize(stream_));
   CK(cudaGetLastError());
@@ -876,6 +896,7 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     c->last_resid = c->h_scal[SC_RESID];
     sgo_status st = SGO_OK;
     if (h_flags_[4 * p + 1] != 0.0) st = SGO_ERR_NOT_CONVERGED;
+    if (c->h_status[2] != 0) st = SGO_ERR_TIMEOUT;
     else if (h_flags_[4 * p + 2] != 0.0 || !std::isfinite(c->h_scal[SC_FREE])) st = SGO_ERR_NAN;
     else if (c->h_scal[SC_CONV] == 0.0) st = SGO_ERR_NOT_CONVERGED;
     if (want_forces)
@@ -956,6 +977,36 @@ sgo_status Engine::density(int nvec, const double* psi, const double* occ, doubl
   cudaFree(dpsi);
   cudaFree(docc);
   cudaFree(dr);
+  return SGO_OK;
+}
+
+sgo_status Engine::subspace(int nvec, const double* x, const double* y, double* c_out) {
+  sgo_ctx* c = ctx_[0];
+  const Prob& d = c->d;
+  double *dx = nullptr, *dy = nullptr;
+  CK(cudaMalloc(&dx, sizeof(double) * (size_t)nvec * d.npw));
+  CK(cudaMalloc(&dy, sizeof(double) * (size_t)nvec * d.npw));
+  CK(cudaMemcpyAsync(dx, x, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyHostToDevice, stream_));
+  CK(cudaMemcpyAsync(dy, y, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyHostToDevice, stream_));
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  if (precision_) {
+    launch_copy_in<float>(L(m_bands_), WB_W, dx, nvec);
+    launch_copy_in<float>(L(m_bands_), WB_W2, dy, nvec);
+    tn<float>(OPK_WB, WB_W, OPK_WB, WB_W2, DD_S);
+  } else {
+    launch_copy_in<double>(L(m_bands_), WB_W, dx, nvec);
+    launch_copy_in<double>(L(m_bands_), WB_W2, dy, nvec);
+    tn<double>(OPK_WB, WB_W, OPK_WB, WB_W2, DD_S);
+  }
+  std::vector<double> s((size_t)d.nb * d.nb);
+  CK(cudaMemcpyAsync(s.data(), d.S, sizeof(double) * s.size(), cudaMemcpyDeviceToHost, stream_));
+  CK(cudaStreamSynchronize(stream_));
+  CK(cudaGetLastError());
+  for (int i = 0; i < nvec; ++i)
+    for (int j = 0; j < nvec; ++j) c_out[(size_t)i * nvec + j] = s[(size_t)i * d.nb + j];
+  cudaFree(dx);
+  cudaFree(dy);
   return SGO_OK;
 }
 

@@ -51,6 +51,7 @@ struct sgo_ctx {
   double last_resid = 0.0;
   sgo_status last_status = SGO_OK;
   std::vector<double> h_scal, h_eps, h_occ, h_forces;
+  int h_status[4] = {0, 0, 0, 0};
   ~sgo_ctx();
 };
 
@@ -68,6 +69,7 @@ class Engine {
   sgo_status apply_h(const double* veff_c, int nvec, const double* psi, double* hpsi);
   sgo_status density(int nvec, const double* psi, const double* occ, double* rho);
   sgo_status export_density(double* rho);
+  sgo_status subspace(int nvec, const double* x, const double* y, double* c);
   sgo_status structure_terms();
   // Live CUDA-event timing of one kernel class (see kTimerNames) over subsequent runs.
   bool timer_select(const char* name);
@@ -85,7 +87,7 @@ class Engine {
   template <typename T> void hpsi(int src, int dst);
   template <typename T> void rayleigh_ritz(bool rotate_history);
   template <typename T> void cg_step();
-  template <typename T> void tn(int akind, int arole, int bkind, int brole, int dst);
+  template <typename T> void tn(int akind, int arole, int bkind, int brole, int dst, bool allow_tc = true);
   template <typename T> void nn(int akind, int arole, int msel, int yrole, double alpha, double beta);
   template <typename T> void rotate(int role);
   void grid_fft(int which, int sign);
@@ -120,7 +122,8 @@ class Engine {
   std::vector<void*> allocs_;
   int max_n1_ = 0, max_n2_ = 0, max_n3_ = 0, max_n12_ = 0, max_nb_ = 0, plane_threads_ = 128;
   WorkMap m_zcol_, m_plane_, m_dens_, m_gz_, m_gp_, m_gew_, m_gch_, m_bands_, m_tn_ww_, m_tn_bw_, m_tn_dw_,
-      m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_atomch_, m_ewsg_, m_prob_;
+      m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_atomch_, m_ewsg_, m_prob_, m_tc_;
+  bool tc_ok_[3] = {false, false, false};
   double* d_part_ = nullptr;
   size_t part_stride_ = 0;
   double* d_gpart_ = nullptr;

@@ -192,7 +192,7 @@ __device__ __forceinline__ void plane_scatter(const Prob& P, cplx<T>* plane, cpl
 }
 
 template <typename T>
-__global__ void __launch_bounds__(PLANE_THREADS_MAX) k_plane_vpsi(KArgs ka) {
+__global__ void __launch_bounds__(PLANE_THREADS, sizeof(T) == 4 ? PLANE_MIN_BLOCKS : 2) k_plane_vpsi(KArgs ka) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(PLANE_THREADS_MAX) k_plane_vpsi(KArgs ka) {
 // accumulated in registers (point t + i*blockDim per thread) in FP64.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(PLANE_THREADS_MAX) k_plane_density(KArgs ka, const double* occ_override) {
+__global__ void __launch_bounds__(PLANE_THREADS, sizeof(T) == 4 ? PLANE_MIN_BLOCKS : 2) k_plane_density(KArgs ka, const double* occ_override) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
@@ -242,9 +242,8 @@ __global__ void __launch_bounds__(PLANE_THREADS_MAX) k_plane_density(KArgs ka, c
   load_roots<T>(r1, P, 0, n1);
   load_roots<T>(r2, P, n1, n2);
   const double* occ = occ_override ? occ_override : P.occ;
-  double acc[DENS_MAXP];
-#pragma unroll
-  for (int i = 0; i < DENS_MAXP; ++i) acc[i] = 0.0;
+  double* acc = reinterpret_cast<double*>(r2 + n2);  // FP64 accumulators of this z-plane
+  for (int t = threadIdx.x; t < n12; t += blockDim.x) acc[t] = 0.0;
   const int mx = P.m1max;
   const LineMap rows{mx + 1, n1 - 2 * mx - 1};
   for (int pair = 0; pair < P.npair; ++pair) {
@@ -257,22 +256,15 @@ __global__ void __launch_bounds__(PLANE_THREADS_MAX) k_plane_density(KArgs ka, c
     cplx<T>* cur = b0;
     cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, 2 * mx + 1, n2, 1, rows, P.fd[1], r2, T(1));
     cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, n2, 1, n2, contiguous(n2), P.fd[0], r1, T(1));
-#pragma unroll
-    for (int i = 0; i < DENS_MAXP; ++i) {
-      int t = threadIdx.x + i * blockDim.x;
-      if (t < n12) {
-        cplx<T> v = cur[t];
-        acc[i] += fa * (double)v.x * (double)v.x + fb * (double)v.y * (double)v.y;
-      }
+    for (int t = threadIdx.x; t < n12; t += blockDim.x) {
+      const cplx<T> v = cur[t];
+      acc[t] += fa * (double)v.x * (double)v.x + fb * (double)v.y * (double)v.y;
     }
   }
+  __syncthreads();
   const double io = 1.0 / P.omega;
   double* rho = P.rho_out + (size_t)z * n12;
-#pragma unroll
-  for (int i = 0; i < DENS_MAXP; ++i) {
-    int t = threadIdx.x + i * blockDim.x;
-    if (t < n12) rho[t] = acc[i] * io;
-  }
+  for (int t = threadIdx.x; t < n12; t += blockDim.x) rho[t] = acc[t] * io;
 }
 
 // ---------------------------------------------------------------------------
@@ -281,7 +273,7 @@ __global__ void __launch_bounds__(PLANE_THREADS_MAX) k_plane_density(KArgs ka, c
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double2* grid_of(const Prob& P, int which) { return which ? P.gfft2 : P.gfft; }
 
-__global__ void __launch_bounds__(PLANE_THREADS_MAX) k_grid_plane_fft(KArgs ka, int which, int sign) {
+__global__ void __launch_bounds__(PLANE_THREADS) k_grid_plane_fft(KArgs ka, int which, int sign) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
@@ -353,7 +345,7 @@ void launch_plane_vpsi(const Launch& L) {
 template <typename T>
 void launch_plane_density(const Launch& L, const double* occ_override) {
   if (!L.map.total) return;
-  size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<T>);
+  size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<T>) + (size_t)L.max_n12 * sizeof(double) + 16;
   k_plane_density<T><<<L.map.total, L.plane_threads, sm, L.stream>>>(L.ka, occ_override);
 }
 void launch_grid_plane_fft(const Launch& L, int which, int sign) {

@@ -114,14 +114,15 @@ __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole,
 }
 
 // Sum the partials in split order.  CTA = (problem, chunk of 256 outputs).
-__global__ void k_gemm_tn_reduce(KArgs ka, int akind, int bkind, int dst, const double* part_base, size_t part_stride) {
+__global__ void k_gemm_tn_reduce(KArgs ka, int akind, int bkind, int dst, const double* part_base, size_t part_stride,
+                                 int kc) {
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int na = opnd_count(P, akind), nbv = opnd_count(P, bkind);
   const int o = (blockIdx.x - ka.start[p]) * 256 + threadIdx.x;
   if (o >= na * nbv) return;
-  const int nsplit = (P.npw + TN_KC - 1) / TN_KC;
+  const int nsplit = (P.npw + kc - 1) / kc;
   const double* part = part_base + (size_t)p * part_stride;
   double s = 0.0;
   for (int k = 0; k < nsplit; ++k) s += part[(size_t)k * na * nbv + o];
@@ -621,8 +622,8 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
 __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
-  __shared__ float cs_c[128], cs_s[128];
-  __shared__ int pr_p[128], pr_q[128];
+  __shared__ float cs_c[256], cs_s[256];
+  __shared__ int pr_p[256], pr_q[256];
   __shared__ int flag, nbig;
   const int p = blockIdx.x;
   if (!ka.active[p]) return;
@@ -891,9 +892,9 @@ void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole,
   if (!L.map.total) return;
   k_gemm_tn<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, arole, bkind, brole, part, stride);
 }
-void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride) {
+void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride, int kc) {
   if (!L.map.total) return;
-  k_gemm_tn_reduce<<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, bkind, dst, part, stride);
+  k_gemm_tn_reduce<<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, bkind, dst, part, stride, kc);
 }
 template <typename T>
 void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta) {

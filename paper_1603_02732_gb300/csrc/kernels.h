@@ -9,16 +9,18 @@ namespace sgo {
 constexpr int QCP = 8;                 // column pairs per z-column CTA (<= 16 columns)
 constexpr int ZCOL_THREADS = 128;
 constexpr int QZ = 32;                 // grid columns per z CTA
-constexpr int DENS_MAXP = 16;          // density accumulators per thread: N1 * N2 <= 16 * blockDim
-constexpr int PLANE_THREADS_MAX = 512;  // so N1 * N2 <= 8192 per plane
+constexpr int PLANE_THREADS = 256;      // threads of the z-plane kernels
+constexpr int PLANE_MIN_BLOCKS = 4;     // register cap (64) for 4+ resident CTAs per SM
+constexpr int PLANE_THREADS_MAX = PLANE_THREADS;
 // GEMM geometry
 constexpr int TN_TILE = 64;
-constexpr int TN_KC = 256;             // K chunk of one split-K partial
+constexpr int TN_KC = 256;             // K chunk of one split-K partial (CUDA-core GEMM)
+constexpr int TC_KC = 1024;            // K chunk of one split-K partial (tensor-core GEMM)
 constexpr int NN_RT = 4;              // row tiles of 64 per NN CTA
 constexpr int NN_KP = 128;             // rows of the small matrix staged per pass
 constexpr int BAND_THREADS = 256;
 constexpr int GRID_CHUNK = 4096;       // grid points per reduction CTA
-constexpr int RR_THREADS = 256;
+constexpr int RR_THREADS = 512;
 
 struct KArgs {
   const Prob* probs;
@@ -51,7 +53,11 @@ void fft_set_smem_limits(size_t bytes);
 // k_linalg.cu
 template <typename T>
 void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride);
-void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride);
+void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride,
+                           int kc = TN_KC);
+// k_gemm_tc.cu (tcgen05, mixed path, counts <= 128)
+void launch_gemm_tn_tc(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride);
+void gemm_tc_set_smem_limits();
 template <typename T>
 void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta);
 template <typename T> void launch_band_kinetic(const Launch& L, int xrole);

@@ -122,7 +122,7 @@ sgo_status run(sgo_ctx* c, const double* veff, int nvec, const double* psi, doub
     l.max_n3 = d.n3;
     l.max_n12 = d.n1 * d.n2;
     l.max_nb = d.nb;
-    l.plane_threads = std::min(PLANE_THREADS_MAX, std::max(128, (div_up(d.n1 * d.n2, DENS_MAXP) + 31) / 32 * 32));
+    l.plane_threads = PLANE_THREADS;
     return l;
   };
   fft_set_smem_limits(220 * 1024);

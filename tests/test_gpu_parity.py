@@ -203,3 +203,19 @@ def test_forces_match_finite_differences_gpu(sgo):
         p[I, a] -= 2 * h
         em, _ = ctx.energy_forces(p)
         assert abs(-(ep - em) / (2 * h) - F[I, a]) < 2e-6
+
+
+@pytest.mark.parametrize("precision,tc,tol", [("fp64", 0, 1e-13), ("mixed", 1, 2e-6), ("mixed", 0, 2e-6)])
+def test_subspace_matrix_gemm(sgo, precision, tc, tol):
+    """C = X^T Y through the subspace GEMM (tcgen05 3xTF32 on the mixed path with gemm_tc=1)
+    vs NumPy FP64, relative to |x_i||y_j|; single-chunk and multi-chunk K."""
+    for st in (workloads.tiny(nat=2, ecut=3.5), workloads.de_candidate(0)):
+        ctx = sgo.Context(st, precision=precision, gemm_tc=tc)
+        rng = np.random.default_rng(8)
+        n = st.nbands
+        x = rng.normal(size=(n, ctx.npw))
+        y = rng.normal(size=(n, ctx.npw))
+        c = ctx.subspace_matrix(x, y)
+        ref = x @ y.T
+        scale = np.sqrt((x ** 2).sum(1))[:, None] * np.sqrt((y ** 2).sum(1))[None, :]
+        assert np.abs(c - ref).max() <= tol * scale.max(), (st.name, np.abs(c - ref).max() / scale.max())

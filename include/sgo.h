@@ -187,9 +187,19 @@ SGO_API sgo_status sgo_apply_hamiltonian_noalloc(sgo_ctx* ctx, const double* vef
                                                  double* hpsi);
 
 /* C = X^T Y (nvec x nvec, row-major) for nvec packed vectors X, Y (row-major nvec x npw):
- * the subspace-matrix GEMM of Algorithm 1 (lines 2, 12, 15), in the context's precision
- * (mixed: FP32 operands on the tensor cores unless gemm_tc = 0; FP64 sums). */
+ * the subspace-matrix GEMM of Algorithm 1 (H(i,j), overlaps, projection coefficients), in
+ * the context's precision (mixed: FP32 operands on the tensor cores unless gemm_tc = 0;
+ * FP64 sums). */
 SGO_API sgo_status sgo_subspace_matrix(sgo_ctx* ctx, int nvec, const double* x, const double* y, double* c);
+
+/* Y <- alpha M^T X + beta Y, i.e. y_j <- alpha sum_i m[i][j] x_i + beta y_j, for nvec packed
+ * vectors X, Y (row-major nvec x npw; y is read and overwritten) and m row-major nvec x
+ * nvec: the block update of Algorithm 1 (the rotation Psi <- Psi U by the Rayleigh-Ritz
+ * eigenvectors, the projection P <- P - Psi (Psi^T P)), in the context's precision (mixed:
+ * FP32 operands on the tensor cores unless gemm_tc = 0).  SGO_ERR_ARG for null pointers or
+ * nvec outside 1..nbands. */
+SGO_API sgo_status sgo_block_update(sgo_ctx* ctx, int nvec, const double* x, const double* m, double alpha,
+                                    double beta, double* y);
 
 /* rho(r) = sum_n occ_n |psi_n(r)|^2 for nvec packed vectors (the density kernels). */
 SGO_API sgo_status sgo_density(sgo_ctx* ctx, int nvec, const double* psi, const double* occ, double* rho);

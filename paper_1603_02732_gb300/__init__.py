@@ -75,6 +75,7 @@ _SIGS = {
     "sgo_apply_hamiltonian": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
     "sgo_apply_hamiltonian_noalloc": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
     "sgo_subspace_matrix": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
+    "sgo_block_update": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
     "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
     "sgo_set_warm": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sgo_batch_destroy": (None, [_vp]),
@@ -251,6 +252,16 @@ class Context:
         out = np.zeros((x.shape[0], x.shape[0]))
         _check(self.lib.sgo_subspace_matrix(self.h, x.shape[0], _ptr(x), _ptr(y), _ptr(out)), "sgo_subspace_matrix")
         return out
+
+    def block_update(self, x, m, alpha, beta, y):
+        """Y <- alpha M^T X + beta Y through the block-update GEMM kernels (tensor cores on
+        the mixed path); returns the new Y."""
+        x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        y = np.array(np.atleast_2d(y), dtype=np.float64, order="C")
+        _check(self.lib.sgo_block_update(self.h, x.shape[0], _ptr(x), _ptr(m), float(alpha), float(beta), _ptr(y)),
+               "sgo_block_update")
+        return y
 
     def density_of(self, psi, occ):
         psi = np.ascontiguousarray(np.atleast_2d(psi), dtype=np.float64)

@@ -284,6 +284,14 @@ sgo_status sgo_subspace_matrix(sgo_ctx* c, int nvec, const double* x, const doub
   return e->subspace(nvec, x, y, out);
 }
 
+sgo_status sgo_block_update(sgo_ctx* c, int nvec, const double* x, const double* m, double alpha, double beta,
+                            double* y) {
+  if (!c || !x || !m || !y || nvec < 1 || nvec > c->nb) return SGO_ERR_ARG;
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  return e->block_update(nvec, x, m, alpha, beta, y);
+}
+
 sgo_status sgo_density(sgo_ctx* c, int nvec, const double* psi, const double* occ, double* rho) {
   if (!c || !psi || !occ || !rho || nvec < 1 || nvec > c->nb) return SGO_ERR_ARG;
   std::unique_ptr<sgo::Engine> e(solo_engine(c));

@@ -467,7 +467,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     }
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
-      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc;
+      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc;
   size_t part = 0;
   int max_natom = 0;
   for (int p = 0; p < n_; ++p) {
@@ -502,6 +502,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     c_ewsg.push_back(div_up(ctxs[p]->ngbox_ew, 256));
     c_prob.push_back(1);
     c_tc.push_back(div_up(d.npw, TC_KC));
+    c_nntc.push_back(div_up(div_up(d.npw, 128), NN_TPC));
     max_natom = std::max(max_natom, d.natom);
     size_t need = (size_t)nsplit * std::max({d.nb * d.nb, d.natom * d.nb, 3 * d.natom * d.nb});
     part = std::max(part, need);
@@ -527,11 +528,18 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   m_ewsg_ = make_map(c_ewsg);
   m_prob_ = make_map(c_prob);
   m_tc_ = make_map(c_tc);
-  // tensor-core subspace GEMMs: mixed path, every operand count <= 128 (one M tile)
+  m_nntc_ = make_map(c_nntc);
+  // tensor-core subspace GEMMs: mixed path, every operand count <= 128 (one M tile, one
+  // NN image of at most 128 x 128), at least two NN pipeline stages beside the image
   const bool tc = precision_ == 1 && ctxs[0]->opts.gemm_tc != 0;
   tc_ok_[OPK_WB] = tc && max_nb_ <= 128;
   tc_ok_[OPK_B] = tc && max_nb_ <= 128 && max_natom <= 128;
   tc_ok_[OPK_DB] = tc && max_nb_ <= 128 && 3 * max_natom <= 128;
+  const int nin_max[3] = {max_nb_, max_natom, 3 * max_natom};
+  for (int k = 0; k < 3; ++k) {
+    nnimg_max_[k] = nn_tc_image_bytes(nin_max[k], max_nb_);
+    nn_tc_ok_[k] = tc_ok_[k] && nn_tc_stages(nnimg_max_[k]) >= 2;
+  }
   part_stride_ = part;
   if (!cuda_ok(cudaMalloc(&d_probs_, sizeof(Prob) * n_), "cudaMalloc(probs)")) return;
   allocs_.push_back(d_probs_);
@@ -546,6 +554,20 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   allocs_.push_back(d_gpart_);
   if (!cuda_ok(cudaMalloc(&d_flags_, sizeof(double) * 4 * n_), "cudaMalloc(flags)")) return;
   allocs_.push_back(d_flags_);
+  if (tc) {
+    // TMA descriptors of every operand buffer (fixed for the engine's life; role swaps
+    // select among them on the device) and the NN image scratch
+    const size_t per = (size_t)TC_NSLOT * TC_NMAPKIND * tc_map_bytes();
+    std::vector<unsigned char> hm(per * n_);
+    for (int p = 0; p < n_; ++p)
+      if (!tc_encode_maps(host[p], hm.data() + per * p)) return;
+    if (!cuda_ok(cudaMalloc(&d_tmaps_, hm.size()), "cudaMalloc(tensor maps)")) return;
+    allocs_.push_back(d_tmaps_);
+    cudaMemcpy(d_tmaps_, hm.data(), hm.size(), cudaMemcpyHostToDevice);
+    nnimg_stride_ = (size_t)(*std::max_element(nnimg_max_, nnimg_max_ + 3) + 1023) / 1024 * 256;  // floats
+    if (!cuda_ok(cudaMalloc(&d_nnimg_, sizeof(float) * nnimg_stride_ * n_), "cudaMalloc(nn image)")) return;
+    allocs_.push_back(d_nnimg_);
+  }
   h_flags_.assign(4 * n_, 0.0);
   // mixed path: FP32 subspace eigensolve when its shared-memory layout fits (nb <= 95)
   rr_f32_ = precision_ == 1 && (size_t)24 * max_nb_ * max_nb_ <= 216 * 1024;
@@ -693,7 +715,7 @@ void Engine::tn(int akind, int arole, int bkind, int brole, int dst, bool allow_
   const int kind = akind == OPK_WB ? TK_GEMM_TN : TK_GEMM_SMALL;
   tbeg(kind);
   if (sizeof(T) == 4 && allow_tc && tc_ok_[akind]) {
-    launch_gemm_tn_tc(L(m_tc_), akind, arole, bkind, brole, d_part_, part_stride_);
+    launch_gemm_tn_tc(L(m_tc_), d_tmaps_, akind, arole, bkind, brole, d_part_, part_stride_);
     launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_, TC_KC);
   } else {
     launch_gemm_tn<T>(L(*m), akind, arole, bkind, brole, d_part_, part_stride_);
@@ -702,17 +724,24 @@ void Engine::tn(int akind, int arole, int bkind, int brole, int dst, bool allow_
   tend(kind);
 }
 
+// image_ready: the previous NN call built the tensor-core image of the same matrix.
 template <typename T>
-void Engine::nn(int akind, int arole, int msel, int yrole, double alpha, double beta) {
+void Engine::nn(int akind, int arole, int msel, int yrole, double alpha, double beta, bool image_ready) {
   const int kind = akind == OPK_WB ? TK_GEMM_NN : TK_GEMM_SMALL;
   tbeg(kind);
-  launch_gemm_nn<T>(L(m_nn_), akind, arole, msel, yrole, alpha, beta);
+  if (sizeof(T) == 4 && nn_tc_ok_[akind]) {
+    if (!image_ready) launch_nn_image(L(m_prob_), akind, msel, d_nnimg_, nnimg_stride_);
+    launch_gemm_nn_tc(L(m_nntc_), d_tmaps_, d_nnimg_, nnimg_stride_, nnimg_max_[akind], akind, arole, yrole, alpha,
+                      beta);
+  } else {
+    launch_gemm_nn<T>(L(m_nn_), akind, arole, msel, yrole, alpha, beta);
+  }
   tend(kind);
 }
 
 template <typename T>
-void Engine::rotate(int role) {
-  nn<T>(OPK_WB, role, DD_TM, WB_W, 1.0, 0.0);
+void Engine::rotate(int role, bool image_ready) {
+  nn<T>(OPK_WB, role, DD_TM, WB_W, 1.0, 0.0, image_ready);
   swap_roles(role, WB_W);
 }
 
@@ -743,31 +772,32 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)24 * max_nb_ * max_nb_);  // 8 n^2 (FP64 L) + 4 x 4 n^2
   else launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_);
   tend(TK_RR);
-  rotate<T>(WB_X);
-  rotate<T>(WB_HX);
+  rotate<T>(WB_X, false);
+  rotate<T>(WB_HX, true);
   if (rotate_history) {
-    rotate<T>(WB_PP);
-    rotate<T>(WB_RP);
+    rotate<T>(WB_PP, true);
+    rotate<T>(WB_RP, true);
   }
 }
 
-// One all-band CG step (Algorithm 1, lines 6-16).
+// One all-band CG step of Algorithm 1: search directions, projection, line minimisation,
+// Rayleigh-Ritz.
 template <typename T>
 void Engine::cg_step() {
   tbeg(TK_CG_BAND);
   launch_cg_precond<T>(L(m_bands_), WB_X, WB_HX, WB_P, WB_W2, WB_PP, WB_RP);
   tend(TK_CG_BAND);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_P, DD_CM);        // C = Psi^T P
-  nn<T>(OPK_WB, WB_X, DD_CM, WB_P, -1.0, 1.0);     // P -= Psi C     (line 12)
+  nn<T>(OPK_WB, WB_X, DD_CM, WB_P, -1.0, 1.0);     // P -= Psi C  (projection)
   tbeg(TK_CG_BAND);
   launch_normalize<T>(L(m_bands_), WB_P, WB_PP);
   tend(TK_CG_BAND);
   hpsi<T>(WB_P, WB_HP);
   tbeg(TK_CG_BAND);
-  launch_line_min<T>(L(m_bands_), WB_X, WB_HX, WB_P, WB_HP);  // line 13
+  launch_line_min<T>(L(m_bands_), WB_X, WB_HX, WB_P, WB_HP);  // line minimisation
   tend(TK_CG_BAND);
   swap_roles(WB_RP, WB_W2);
-  rayleigh_ritz<T>(true);                          // lines 14-16
+  rayleigh_ritz<T>(true);                          // orthonormalise + subspace diagonalisation
   launch_finish_cg(L(m_prob_));
 }
 
@@ -821,7 +851,7 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     tbeg(TK_GRID_OTHER);
     launch_veff<T>(L(m_gew_), nullptr);
     tend(TK_GRID_OTHER);
-    // H Psi and the subspace diagonalisation (Algorithm 1, lines 2-3)
+    // H Psi and the subspace diagonalisation (the start of Algorithm 1)
     hpsi<T>(WB_X, WB_HX);
     rayleigh_ritz<T>(false);
     set_scal(SC_FIRSTCG, 1.0, true);
@@ -841,7 +871,7 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     tend(TK_GRID_OTHER);
     grid_fft(1, -1);
     tbeg(TK_GRID_OTHER);
-    launch_grid_energies(L(m_gch_), d_gpart_, maxchunk_);
+    launch_grid_energies<T>(L(m_gch_), d_gpart_, maxchunk_);
     launch_grid_energies_reduce(L(m_prob_), d_gpart_, maxchunk_);
     launch_finish_iteration(L(m_prob_), o.scf_tol_e, o.scf_tol_rho, it > nonsc ? 1 : 0);
     tend(TK_GRID_OTHER);
@@ -1005,6 +1035,40 @@ sgo_status Engine::subspace(int nvec, const double* x, const double* y, double* 
   CK(cudaGetLastError());
   for (int i = 0; i < nvec; ++i)
     for (int j = 0; j < nvec; ++j) c_out[(size_t)i * nvec + j] = s[(size_t)i * d.nb + j];
+  cudaFree(dx);
+  cudaFree(dy);
+  return SGO_OK;
+}
+
+sgo_status Engine::block_update(int nvec, const double* x, const double* m, double alpha, double beta, double* y) {
+  sgo_ctx* c = ctx_[0];
+  const Prob& d = c->d;
+  const size_t nbytes = sizeof(double) * (size_t)nvec * d.npw;
+  double *dx = nullptr, *dy = nullptr;
+  CK(cudaMalloc(&dx, nbytes));
+  CK(cudaMalloc(&dy, nbytes));
+  std::vector<double> tm((size_t)d.nb * d.nb, 0.0);
+  for (int i = 0; i < nvec; ++i)
+    for (int j = 0; j < nvec; ++j) tm[(size_t)i * d.nb + j] = m[(size_t)i * nvec + j];
+  CK(cudaMemcpyAsync(dx, x, nbytes, cudaMemcpyHostToDevice, stream_));
+  CK(cudaMemcpyAsync(dy, y, nbytes, cudaMemcpyHostToDevice, stream_));
+  CK(cudaMemcpyAsync(d.Tm, tm.data(), sizeof(double) * tm.size(), cudaMemcpyHostToDevice, stream_));
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  if (precision_) {
+    launch_copy_in<float>(L(m_bands_), WB_W, dx, nvec);
+    launch_copy_in<float>(L(m_bands_), WB_W2, dy, nvec);
+    nn<float>(OPK_WB, WB_W, DD_TM, WB_W2, alpha, beta);
+    launch_copy_out<float>(L(m_bands_), WB_W2, dy, nvec);
+  } else {
+    launch_copy_in<double>(L(m_bands_), WB_W, dx, nvec);
+    launch_copy_in<double>(L(m_bands_), WB_W2, dy, nvec);
+    nn<double>(OPK_WB, WB_W, DD_TM, WB_W2, alpha, beta);
+    launch_copy_out<double>(L(m_bands_), WB_W2, dy, nvec);
+  }
+  CK(cudaMemcpyAsync(y, dy, nbytes, cudaMemcpyDeviceToHost, stream_));
+  CK(cudaStreamSynchronize(stream_));
+  CK(cudaGetLastError());
   cudaFree(dx);
   cudaFree(dy);
   return SGO_OK;

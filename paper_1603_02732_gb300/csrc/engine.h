@@ -70,6 +70,7 @@ class Engine {
   sgo_status density(int nvec, const double* psi, const double* occ, double* rho);
   sgo_status export_density(double* rho);
   sgo_status subspace(int nvec, const double* x, const double* y, double* c);
+  sgo_status block_update(int nvec, const double* x, const double* m, double alpha, double beta, double* y);
   sgo_status structure_terms();
   // Live CUDA-event timing of one kernel class (see kTimerNames) over subsequent runs.
   bool timer_select(const char* name);
@@ -88,8 +89,9 @@ class Engine {
   template <typename T> void rayleigh_ritz(bool rotate_history);
   template <typename T> void cg_step();
   template <typename T> void tn(int akind, int arole, int bkind, int brole, int dst, bool allow_tc = true);
-  template <typename T> void nn(int akind, int arole, int msel, int yrole, double alpha, double beta);
-  template <typename T> void rotate(int role);
+  template <typename T>
+  void nn(int akind, int arole, int msel, int yrole, double alpha, double beta, bool image_ready = false);
+  template <typename T> void rotate(int role, bool image_ready);
   void grid_fft(int which, int sign);
   void grid_fft_raw(int which, int sign);
   void potential();
@@ -122,8 +124,13 @@ class Engine {
   std::vector<void*> allocs_;
   int max_n1_ = 0, max_n2_ = 0, max_n3_ = 0, max_n12_ = 0, max_nb_ = 0, plane_threads_ = 128;
   WorkMap m_zcol_, m_plane_, m_dens_, m_gz_, m_gp_, m_gew_, m_gch_, m_bands_, m_tn_ww_, m_tn_bw_, m_tn_dw_,
-      m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_atomch_, m_ewsg_, m_prob_, m_tc_;
-  bool tc_ok_[3] = {false, false, false};
+      m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_atomch_, m_ewsg_, m_prob_, m_tc_, m_nntc_;
+  bool tc_ok_[3] = {false, false, false};      // TN on tcgen05, per A-operand kind
+  bool nn_tc_ok_[3] = {false, false, false};   // NN on tcgen05, per X-operand kind
+  void* d_tmaps_ = nullptr;                    // [n][TC_NSLOT][TC_NMAPKIND] tensor maps
+  float* d_nnimg_ = nullptr;                   // [n][nnimg_stride_] NN B-operand images
+  size_t nnimg_stride_ = 0;
+  int nnimg_max_[3] = {0, 0, 0};
   double* d_part_ = nullptr;
   size_t part_stride_ = 0;
   double* d_gpart_ = nullptr;

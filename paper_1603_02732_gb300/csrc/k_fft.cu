@@ -1,5 +1,5 @@
-// FFT kernels of the all-band H.psi apply and of the density (Algorithm 1 lines 2
-// and 15: "Calculate / Update H|Psi_i>"; Sec. II D: rho_out from the occupied states).
+// FFT kernels of the all-band H.psi apply (every H|Psi_i> product of Algorithm 1) and
+// of the density (Sec. II D: rho_out from the occupied states).
 //
 // A band pair (a, b) shares one complex transform: psi_a + i psi_b is real-space
 // complex, both bands being real at the Gamma point.  The inverse transform runs

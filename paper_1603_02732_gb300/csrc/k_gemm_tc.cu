@@ -1,19 +1,39 @@
-// Subspace and projector overlaps C = A^T B on the 5th-generation tensor cores (tcgen05),
-// mixed path (FP32 operands).  The products are the bold steps of Algorithm 1 (lines 2, 12,
-// 14, 15: H(i,j) = <Psi_i|H|Psi_j>, overlaps, projection coefficients) and <beta_I|psi_n>.
+// Subspace and projector GEMMs on the 5th-generation tensor cores (tcgen05), fed by TMA,
+// mixed path (FP32 operands).  They are the bold products of Algorithm 1 (the subspace
+// matrix H(i,j) = <Psi_i|H|Psi_j>, the projection of the search directions against Psi,
+// the rotations by the Rayleigh-Ritz eigenvectors) and the Kleinman-Bylander
+// contractions <beta_I|psi_n> and sum_I beta_I D_I <beta_I|psi_n> of H.psi.
 //
 // Precision: 3xTF32.  Each FP32 operand x is split into hi = tf32(x) and lo = tf32(x - hi);
-// the accumulator in TMEM (FP32) receives hi.hi + hi.lo + lo.hi, a relative error of about
-// 2^-21 per product; each CTA's FP32 partial is written out as FP64 and the partials of all
-// K chunks are added in fixed order by k_gemm_tn_reduce (FP64).
+// the TMEM accumulator (FP32) receives hi.hi + hi.lo + lo.hi, a relative error of about
+// 2^-21 per product.
 //
-// CTA = (member, K chunk of TC_KC).  A tile: 128 rows (vectors of A, M dimension) x 32 K;
-// B tile: N rows (vectors of B, N = count rounded up to 16) x 32 K; both K-major in the
-// canonical no-swizzle layout (8-row x 16-byte core matrices, K-adjacent cores 128 B apart,
-// 8-row groups 1024 B apart).  Two stages: threads stage chunk s+1 (global -> split ->
-// shared) while the tensor core runs chunk s.  One thread issues the MMAs and commits them
-// to a per-stage mbarrier; every wait is bounded (clock) and reports a timeout in status[2].
+// Both kernels are warp-specialised pipelines over shared-memory stages:
+//   warp 0    one lane issues TMA tile loads (cp.async.bulk.tensor, 128-byte swizzle);
+//   warp 1    allocates TMEM; one lane issues tcgen05.mma and commits each stage back;
+//   warps 2-5 split each landed FP32 tile in place into hi and a lo copy (at the same
+//             swizzled offsets: the split is elementwise), then release it to the MMA lane;
+//   epilogue  TMEM -> registers (tcgen05.ld) -> global memory.
+// Every wait is bounded (clock64); a timeout sets status[2] of the problem, and the CTA
+// still waits (bounded) for its own loads and MMAs in flight, frees TMEM and returns.
+//
+// TN (C = A^T B, split-K): CTA = (problem, K chunk of TC_KC).  A rows (M = 128 TMEM
+// lanes) and B rows (N = count rounded up to 16) are K-major tiles of 32 K (128 bytes).
+// Each CTA writes its FP32 partial as FP64; k_gemm_tn_reduce adds the chunks in order.
+//
+// NN (Y = alpha X M + beta Y): CTA = (problem, NN_TPC tiles of 128 plane waves).  The
+// MMA's M is the plane-wave index, K the input row and N the output band.  TMA lands X
+// as 32-row x 32-wave boxes (rows of X along K); the converter warps transpose each
+// 4 x 4 block while splitting, into a K-major A tile [128 waves][32 rows], the same
+// layout as the TN operands.  B = M^T is a K-major image of the small matrix, split into
+// hi/lo once per launch by k_nn_image and copied whole into shared memory by one bulk
+// copy.  The accumulator is double-buffered in TMEM, so the epilogue of one tile
+// overlaps the MMAs of the next.
+#include <cuda.h>
 #include <stdint.h>
+
+#include <mutex>
+#include <string>
 
 #include "kernels.h"
 
@@ -21,12 +41,17 @@ namespace sgo {
 
 namespace {
 
-constexpr int TC_M = 128;
-constexpr int TC_K = 32;                       // K per stage
-constexpr int TC_STAGE_A = TC_M * TC_K * 4;    // bytes of one A split (16 KB)
-constexpr int TC_STAGE_B = 128 * TC_K * 4;     // bytes of one B split (N <= 128)
-constexpr int TC_STAGE = 2 * TC_STAGE_A + 2 * TC_STAGE_B;  // hi, lo of A and B
-constexpr long long TC_WAIT_CYCLES = 4000000000LL;          // ~2 s at 2 GHz
+constexpr int TC_K = 32;                      // floats per 128-byte swizzle row
+constexpr int TC_TILE = 128 * 128;            // bytes of a 128-row x 128-byte tile
+constexpr int TN_STAGES = 3;
+constexpr int TN_STAGE = 4 * TC_TILE;         // A hi, A lo, B hi, B lo
+constexpr int TN_THREADS = 192;
+constexpr int NN_BOX = 32 * 128;              // one 32-row x 32-wave box (4 KB)
+constexpr int NN_STAGE = 3 * 4 * NN_BOX;      // landed boxes (128 waves), hi, lo
+constexpr int NN_MAX_STAGES = 4;
+constexpr int NN_THREADS = 320;
+constexpr int TC_SMEM_BUDGET = 225 * 1024;    // dynamic shared memory per CTA
+constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -36,24 +61,22 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// byte offset of element (row, k) in a canonical no-swizzle K-major tile (32-bit elements)
-__device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
-  return (uint32_t)((k >> 2) * 128 + (row >> 3) * 1024 + (row & 7) * 16 + (k & 3) * 4);
-}
-
-// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets,
-// descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle (descriptor
+// version 1): rows of 128 B (32 TF32 along K), 8-row groups 1024 B apart (SBO); the
+// leading offset is unused by this layout.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
-// instruction descriptor of kind::tf32: FP32 accumulate, TF32 A and B, both K-major
-__host__ __device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major,
+// M x N.
+__device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
@@ -69,6 +92,18 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -79,171 +114,546 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase of the given parity.  Gives up (false) when another role
+// has failed (*fail) or after TC_WAIT_CYCLES, which marks the CTA failed.  fail = null:
+// a drain wait that ignores other roles' failures.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
   const long long t0 = clock64();
   while (!mbar_test(bar, parity)) {
-    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+    if (fail && *fail) return false;
+    if (clock64() - t0 > TC_WAIT_CYCLES) {
+      if (fail) *fail = 1;
+      return false;
+    }
   }
   return true;
 }
 
-template <typename T>
-__device__ __forceinline__ const T* opnd_tc(const Prob& P, int kind, int role) {
-  if (kind == OPK_WB) return wbuf<T>(P, role);
-  if (kind == OPK_B) return reinterpret_cast<const T*>(P.B);
-  return reinterpret_cast<const T*>(P.dB);
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
 }
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Split nunits float4 units in place: hi over the FP32 value, lo into the twin buffer.
+__device__ __forceinline__ void split_units(unsigned char* hi, unsigned char* lo, int nunits, int t, int nt) {
+  for (int u = t; u < nunits; u += nt) {
+    float4 v = reinterpret_cast<float4*>(hi)[u];
+    float4 h, l;
+    h.x = tf32_round(v.x); l.x = tf32_round(v.x - h.x);
+    h.y = tf32_round(v.y); l.y = tf32_round(v.y - h.y);
+    h.z = tf32_round(v.z); l.z = tf32_round(v.z - h.z);
+    h.w = tf32_round(v.w); l.w = tf32_round(v.w - h.w);
+    reinterpret_cast<float4*>(hi)[u] = h;
+    reinterpret_cast<float4*>(lo)[u] = l;
+  }
+}
+
+// Transpose-and-split of one NN stage.  raw: 4 TMA boxes g (waves 32 g .. 32 g + 31), in
+// each 32 rows r of 128 B with 16-byte chunk c (waves 4c .. 4c+3) at position c ^ (r % 8).
+// Output: K-major tile, wave w at (w/8) 1024 + (w%8) 128, chunk d (rows 4d .. 4d+3) at
+// position d ^ (w % 8).  Thread t moves 4 x 4 blocks (box g, wave chunk c = l ^ s, row
+// chunk d = l), l = t % 8: the eight lanes of a 16-byte access phase then touch eight
+// distinct chunk positions on both the read and the write side.
+__device__ __forceinline__ void split_transpose(const unsigned char* raw, unsigned char* hi, unsigned char* lo, int t) {
+  const int l = t & 7;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int combo = (t >> 3) + 16 * h;  // 0..31
+    const int g = combo & 3, c = l ^ (combo >> 2), d = l;
+    float v[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = 4 * d + q;
+      const float4 x = *reinterpret_cast<const float4*>(raw + g * NN_BOX + r * 128 + ((c ^ (r & 7)) << 4));
+      v[q][0] = x.x; v[q][1] = x.y; v[q][2] = x.z; v[q][3] = x.w;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int w = 32 * g + 4 * c + e;
+      const int off = (w >> 3) * 1024 + (w & 7) * 128 + ((d ^ (w & 7)) << 4);
+      float4 hv, lv;
+      hv.x = tf32_round(v[0][e]); lv.x = tf32_round(v[0][e] - hv.x);
+      hv.y = tf32_round(v[1][e]); lv.y = tf32_round(v[1][e] - hv.y);
+      hv.z = tf32_round(v[2][e]); lv.z = tf32_round(v[2][e] - hv.z);
+      hv.w = tf32_round(v[3][e]); lv.w = tf32_round(v[3][e] - hv.w);
+      *reinterpret_cast<float4*>(hi + off) = hv;
+      *reinterpret_cast<float4*>(lo + off) = lv;
+    }
+  }
+}
+
 __device__ __forceinline__ int count_tc(const Prob& P, int kind) {
   return kind == OPK_WB ? P.nb : (kind == OPK_B ? P.natom : 3 * P.natom);
 }
 
-// Stage one 32-wide K chunk of `rows` vectors (row r = vector v0 + r) as hi/lo splits.
-// Lane layout: a warp covers 8 rows x 16 k (float4 per thread), quarter-warps write
-// contiguous 128-byte core-matrix rows.
-__device__ __forceinline__ void stage_tile(const float* __restrict__ src, int ld, int nvec, int v0, int kb, int k1,
-                                           unsigned char* hi, unsigned char* lo, int rows) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r8 = lane & 7, k4 = lane >> 3;  // k4 in 0..3
-  const int nunits = (rows >> 3) * 2;       // (8-row group, 16-k half) units; rows % 8 == 0
-  for (int u = warp; u < nunits; u += blockDim.x >> 5) {
-    const int row = (u >> 1) * 8 + r8;
-    const int k = (u & 1) * 16 + k4 * 4;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    const int vi = v0 + row, kg = kb + k;
-    if (vi < nvec) {
-      const float* p = src + (size_t)vi * ld + kg;
-      if (kg + 3 < k1 && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
-        float4 q = *reinterpret_cast<const float4*>(p);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = (kg + j < k1) ? p[j] : 0.f;
-      }
-    }
-    float4 h, l;
-    h.x = tf32_round(v[0]); l.x = tf32_round(v[0] - h.x);
-    h.y = tf32_round(v[1]); l.y = tf32_round(v[1] - h.y);
-    h.z = tf32_round(v[2]); l.z = tf32_round(v[2] - h.z);
-    h.w = tf32_round(v[3]); l.w = tf32_round(v[3] - h.w);
-    const uint32_t off = kmajor_off(row, k);
-    *reinterpret_cast<float4*>(hi + off) = h;
-    *reinterpret_cast<float4*>(lo + off) = l;
+// map slot of an operand: wave buffers by physical index, then B, dB
+__device__ __forceinline__ int slot_of(const Prob& P, int kind, int role) {
+  return kind == OPK_WB ? P.role[role] : (kind == OPK_B ? NWB : NWB + 1);
+}
+
+__device__ __forceinline__ const CUtensorMap* map_of(const CUtensorMap* maps, int p, int slot, int kind) {
+  return maps + ((size_t)p * TC_NSLOT + slot) * TC_NMAPKIND + kind;
+}
+
+__device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
+  return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
+}
+
+__device__ __forceinline__ const double* dense_tc(const Prob& P, int sel) {
+  switch (sel) {
+    case DD_S: return P.S;
+    case DD_HS: return P.Hs;
+    case DD_CM: return P.Cm;
+    case DD_TM: return P.Tm;
+    case DD_PROJ: case DD_PROJ_D: return P.proj;
+    default: return P.dproj;
   }
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 1) k_gemm_tn_tc(KArgs ka, int akind, int arole, int bkind, int brole,
-                                                      double* part_base, size_t part_stride) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar[3];
+// ---------------------------------------------------------------------------
+// TN: part[split][i][j] = sum_{k in chunk} A[i][k] B[j][k]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TN_THREADS, 1)
+    k_gemm_tn_tma(KArgs ka, const CUtensorMap* __restrict__ maps, int akind, int arole, int bkind, int brole,
+                  double* part_base, size_t part_stride) {
+  extern __shared__ unsigned char smem_dyn[];
+  __shared__ __align__(8) uint64_t full[TN_STAGES], conv[TN_STAGES], empty[TN_STAGES], done;
   __shared__ uint32_t tmem_base;
-  __shared__ int fail;
+  __shared__ int fail_s;
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
+  unsigned char* smem = align1024(smem_dyn);
+  volatile int* fail = &fail_s;
   const int na = count_tc(P, akind), nbv = count_tc(P, bkind);
   const int npad = (nbv + 15) & ~15;
+  const int ra = (na + 7) & ~7, rb = (nbv + 7) & ~7;
   const int split = blockIdx.x - ka.start[p];
   const int k0 = split * TC_KC, k1 = min(P.npw, k0 + TC_KC);
-  const float* A = opnd_tc<float>(P, akind, arole);
-  const float* Bm = opnd_tc<float>(P, bkind, brole);
-  const int warp = threadIdx.x >> 5;
-  if (warp == 0) {
+  const int nsteps = (k1 - k0 + TC_K - 1) / TC_K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)), "r"(128));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    fail = 0;
-    for (int i = 0; i < 3; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bar[i])), "r"(1));
+    fail_s = 0;
+    for (int s = 0; s < TN_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp >= 2) {
+    // lo rows beyond the split rows stay zero for the whole kernel (the hi rows there are
+    // zero-filled by TMA: they lie outside the tensor's row range)
+    const int t = threadIdx.x - 64;
+    for (int s = 0; s < TN_STAGES; ++s) {
+      unsigned char* st = smem + s * TN_STAGE;
+      float4* alo = reinterpret_cast<float4*>(st + TC_TILE);
+      float4* blo = reinterpret_cast<float4*>(st + 3 * TC_TILE);
+      for (int u = ra * 8 + t; u < 128 * 8; u += 128) alo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = rb * 8 + t; u < 128 * 8; u += 128) blo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const CUtensorMap* ma = map_of(maps, p, slot_of(P, akind, arole), 0);
+      const CUtensorMap* mb = map_of(maps, p, slot_of(P, bkind, brole), 0);
+      int issued[TN_STAGES];
+      for (int s = 0; s < TN_STAGES; ++s) issued[s] = 0;
+      for (int it = 0; it < nsteps; ++it) {
+        const int s = it % TN_STAGES, r = it / TN_STAGES;
+        if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1), fail)) break;
+        unsigned char* st = smem + s * TN_STAGE;
+        mbar_expect_tx(&full[s], 2 * TC_TILE);
+        tma_load_2d(st, ma, k0 + it * TC_K, 0, &full[s]);
+        tma_load_2d(st + 2 * TC_TILE, mb, k0 + it * TC_K, 0, &full[s]);
+        issued[s] = r + 1;
+      }
+      // every load issued has landed before the CTA may exit
+      for (int s = 0; s < TN_STAGES; ++s)
+        if (issued[s] > 0) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1), nullptr);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(128, npad);
+      for (int it = 0; it < nsteps; ++it) {
+        const int s = it % TN_STAGES, r = it / TN_STAGES;
+        if (!mbar_wait(&conv[s], (uint32_t)(r & 1), fail)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = su32(smem + s * TN_STAGE);
+#pragma unroll
+        for (int kk = 0; kk < TC_K / 8; ++kk) {
+          const uint32_t o = kk * 32;  // K = 8 TF32 = 32 bytes along the swizzled row
+          const uint64_t ah = desc_sw128(st + o, 16, 1024), al = desc_sw128(st + TC_TILE + o, 16, 1024);
+          const uint64_t bh = desc_sw128(st + 2 * TC_TILE + o, 16, 1024);
+          const uint64_t bl = desc_sw128(st + 3 * TC_TILE + o, 16, 1024);
+          mma_tf32(tmem, ah, bh, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(tmem, ah, bl, idesc, 1u);
+          mma_tf32(tmem, al, bh, idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&done);
+      mbar_wait(&done, 0, nullptr);
+    }
+    __syncwarp();
+  } else {
+    const int t = threadIdx.x - 64;
+    for (int it = 0; it < nsteps; ++it) {
+      const int s = it % TN_STAGES, r = it / TN_STAGES;
+      if (!mbar_wait(&full[s], (uint32_t)(r & 1), fail)) break;
+      unsigned char* st = smem + s * TN_STAGE;
+      split_units(st, st + TC_TILE, ra * 8, t, 128);
+      split_units(st + 2 * TC_TILE, st + 3 * TC_TILE, rb * 8, t, 128);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&conv[s]);
+    }
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of C)
+    const bool ok = mbar_wait(&done, 0, fail);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__all_sync(0xffffffffu, ok && !*fail)) {  // tcgen05.ld is warp-collective
+      const int quad = warp & 3;
+      const int row = quad * 32 + lane;
+      double* part = part_base + (size_t)p * part_stride + (size_t)split * na * nbv;
+      for (int c0 = 0; c0 < npad; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+        if (row < na) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < nbv) part[(size_t)row * nbv + c0 + j] = (double)__uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && fail_s) atomicExch(&P.status[2], 1);
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
+// ---------------------------------------------------------------------------
+// NN image: the B operand of the NN GEMM, M^T as K-major 128-byte-swizzled tiles, hi
+// then lo.  Element (j, i) (output band j < npad, input row i < kpad) holds M[i][j]
+// (times D_I for DD_PROJ_D), zero in the padding.  Atom column q = i / 32 starts at
+// q npad 128 bytes; in it row j sits at (j/8) 1024 + (j%8) 128 and the 16-byte chunk
+// c = (i%32)/4 at position c ^ (j%8).  CTA per problem.
+// ---------------------------------------------------------------------------
+__global__ void k_nn_image(KArgs ka, int akind, int msel, float* img_base, size_t img_stride) {
+  const int p = blockIdx.x;
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int nin = count_tc(P, akind), nb = P.nb;
+  const int npad = (nb + 15) & ~15, kpad = (nin + 31) & ~31;
+  const double* M = dense_tc(P, msel);
+  unsigned char* hi = reinterpret_cast<unsigned char*>(img_base + (size_t)p * img_stride);
+  unsigned char* lo = hi + (size_t)npad * kpad * 4;
+  for (int e = threadIdx.x; e < npad * kpad; e += blockDim.x) {
+    const int j = e / kpad, i = e - j * kpad;
+    float v = 0.f;
+    if (i < nin && j < nb) {
+      double m = M[(size_t)i * nb + j];
+      if (msel == DD_PROJ_D) m *= P.sp[P.spec[i] * 6 + 5];
+      v = (float)m;
+    }
+    const float h = tf32_round(v), l = tf32_round(v - h);
+    const int q = i >> 5, c = (i & 31) >> 2;
+    const size_t off = (size_t)q * npad * 128 + (size_t)(j >> 3) * 1024 + (j & 7) * 128 + ((c ^ (j & 7)) << 4) +
+                       (i & 3) * 4;
+    *reinterpret_cast<float*>(hi + off) = h;
+    *reinterpret_cast<float*>(lo + off) = l;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// NN: Y[j][k] = alpha sum_i X[i][k] M[i][j] + beta Y[j][k], k over this CTA's tiles.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NN_THREADS, 1)
+    k_gemm_nn_tma(KArgs ka, const CUtensorMap* __restrict__ maps, const float* __restrict__ img_base,
+                  size_t img_stride, int img_max, int nstages, int akind, int arole, int yrole, float alpha,
+                  float beta) {
+  extern __shared__ unsigned char smem_dyn[];
+  __shared__ __align__(8) uint64_t full[NN_MAX_STAGES], conv[NN_MAX_STAGES], empty[NN_MAX_STAGES], tfull[2],
+      tempty[2], imgbar, done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail_s;
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  unsigned char* smem = align1024(smem_dyn);
+  unsigned char* stages = smem + img_max;
+  volatile int* fail = &fail_s;
+  const int nin = count_tc(P, akind), nb = P.nb, npw = P.npw;
+  const int npad = (nb + 15) & ~15, kpad = (nin + 31) & ~31, nkc = kpad / 32;
+  const int img_half = npad * kpad * 4;
+  const int ntile = (npw + 127) / 128;
+  const int t0 = (blockIdx.x - ka.start[p]) * NN_TPC, t1 = min(ntile, t0 + NN_TPC);
+  const int ntl = t1 - t0, niter = ntl * nkc;
+  const uint32_t tcols = npad <= 64 ? 128u : 256u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    fail_s = 0;
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    mbar_init(&imgbar, 1);
+    mbar_init(&done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t dtm = tmem_base;
-  const uint32_t idesc = idesc_tf32(TC_M, npad);
-  const int nsteps = (k1 - k0 + TC_K - 1) / TC_K;
-  for (int it = 0; it < nsteps; ++it) {
-    const int s = it & 1;
-    unsigned char* st = smem_raw + s * TC_STAGE;
-    unsigned char* ahi = st;
-    unsigned char* alo = st + TC_STAGE_A;
-    unsigned char* bhi = st + 2 * TC_STAGE_A;
-    unsigned char* blo = bhi + TC_STAGE_B;
-    if (it >= 2) {
-      // the MMAs that read this stage two chunks ago must have completed
-      if (!mbar_wait(&bar[s], (uint32_t)(((it >> 1) - 1) & 1))) fail = 1;
-      __syncthreads();
-      if (fail) break;
-    }
-    const int kb = k0 + it * TC_K;
-    // Only the rows that exist are staged: output (i, j) reads row i of A and row j of B
-    // alone, so whatever the rows beyond the counts hold reaches only discarded outputs.
-    stage_tile(A, P.ld, na, 0, kb, k1, ahi, alo, (na + 7) & ~7);
-    stage_tile(Bm, P.ld, nbv, 0, kb, k1, bhi, blo, (nbv + 7) & ~7);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      mbar_expect_tx(&imgbar, (uint32_t)(2 * img_half));
+      bulk_load(smem, img_base + (size_t)p * img_stride, (uint32_t)(2 * img_half), &imgbar);
+      const CUtensorMap* mx = map_of(maps, p, slot_of(P, akind, arole), 1);
+      int issued[NN_MAX_STAGES];
+      for (int s = 0; s < NN_MAX_STAGES; ++s) issued[s] = 0;
+      for (int it = 0; it < niter; ++it) {
+        const int s = it % nstages, r = it / nstages;
+        const int tl = it / nkc, kc = it - tl * nkc;
+        if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1), fail)) break;
+        unsigned char* st = stages + s * NN_STAGE;
+        mbar_expect_tx(&full[s], 4 * NN_BOX);
+        const int x0 = (t0 + tl) * 128;
 #pragma unroll
-      for (int kk = 0; kk < TC_K / 8; ++kk) {
-        const uint32_t o = kk * 256;  // two K-adjacent core matrices per MMA (K = 8)
-        const uint64_t dah = smem_desc(su32(ahi) + o, 128, 1024), dal = smem_desc(su32(alo) + o, 128, 1024);
-        const uint64_t dbh = smem_desc(su32(bhi) + o, 128, 1024), dbl = smem_desc(su32(blo) + o, 128, 1024);
-        mma_tf32(dtm, dah, dbh, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(dtm, dah, dbl, idesc, 1u);
-        mma_tf32(dtm, dal, dbh, idesc, 1u);
+        for (int g = 0; g < 4; ++g) tma_load_2d(st + g * NN_BOX, mx, x0 + 32 * g, 32 * kc, &full[s]);
+        issued[s] = r + 1;
       }
-      mma_commit(&bar[s]);
+      // every load issued has landed before the CTA may exit
+      mbar_wait(&imgbar, 0, nullptr);
+      for (int s = 0; s < nstages; ++s)
+        if (issued[s] > 0) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1), nullptr);
     }
-  }
-  // wait for every MMA of this CTA (a final commit tracks all earlier ones)
-  if (threadIdx.x == 0) mma_commit(&bar[2]);
-  if (!mbar_wait(&bar[2], 0)) fail = 1;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (!fail) {
-    // TMEM -> registers -> FP64 partials.  Warp w reads lanes 32 (w%4) .. +31 (rows of C)
-    // and column half w/4.
-    const int quad = warp & 3, half = warp >> 2;
-    const int row = quad * 32 + (threadIdx.x & 31);
-    double* part = part_base + (size_t)p * part_stride + (size_t)split * na * nbv;
-    const int c_begin = half * 64, c_end = min(npad, c_begin + 64);
-    for (int c0 = c_begin; c0 < c_end; c0 += 16) {
-      uint32_t r[16];
-      const uint32_t taddr = dtm + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < na) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(128, npad);
+      const uint32_t ih = su32(smem), il = ih + img_half;
+      bool ok = mbar_wait(&imgbar, 0, fail);
+      for (int tl = 0; ok && tl < ntl; ++tl) {
+        const int b = tl & 1, use = tl >> 1;
+        if (use > 0 && !mbar_wait(&tempty[b], (uint32_t)((use - 1) & 1), fail)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * npad);
+        for (int kc = 0; kc < nkc; ++kc) {
+          const int it = tl * nkc + kc;
+          const int s = it % nstages, r = it / nstages;
+          if (!mbar_wait(&conv[s], (uint32_t)(r & 1), fail)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sh = su32(stages + s * NN_STAGE) + 4 * NN_BOX, sl = sh + 4 * NN_BOX;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = c0 + j;
-          if (col < nbv) part[(size_t)row * nbv + col] = (double)__uint_as_float(r[j]);
+          for (int kk = 0; kk < 4; ++kk) {
+            if (kc * 32 + kk * 8 >= nin) break;  // K steps wholly in the zero padding
+            // A: K-major tile [128 waves][32 rows], K offset kk * 8 TF32 = 32 B
+            const uint64_t ah = desc_sw128(sh + kk * 32, 16, 1024);
+            const uint64_t al = desc_sw128(sl + kk * 32, 16, 1024);
+            // B: K-major image, atom column kc, K offset kk * 8 TF32 = 32 B
+            const uint32_t bo = (uint32_t)(kc * npad * 128 + kk * 32);
+            const uint64_t bh = desc_sw128(ih + bo, 16, 1024), bl = desc_sw128(il + bo, 16, 1024);
+            mma_tf32(d, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(d, ah, bl, idesc, 1u);
+            mma_tf32(d, al, bh, idesc, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[b]);
+      }
+      mma_commit(&done);
+      mbar_wait(&done, 0, nullptr);
+    }
+    __syncwarp();
+  } else if (warp < 6) {
+    const int t = threadIdx.x - 64;
+    for (int it = 0; it < niter; ++it) {
+      const int s = it % nstages, r = it / nstages;
+      if (!mbar_wait(&full[s], (uint32_t)(r & 1), fail)) break;
+      unsigned char* st = stages + s * NN_STAGE;
+      split_transpose(st, st + 4 * NN_BOX, st + 8 * NN_BOX, t);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&conv[s]);
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = plane waves of the tile
+    const int quad = warp & 3;
+    float* Y = reinterpret_cast<float*>(P.wb[P.role[yrole]]);
+    const int ld = P.ld;
+    for (int tl = 0; tl < ntl; ++tl) {
+      const int b = tl & 1, use = tl >> 1;
+      const bool ok = mbar_wait(&tfull[b], (uint32_t)(use & 1), fail);
+      if (!__all_sync(0xffffffffu, ok)) break;  // tcgen05.ld is warp-collective
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int k = (t0 + tl) * 128 + quad * 32 + lane;
+      for (int c0 = 0; c0 < npad; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * npad + c0), v);
+        if (k < npw) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = c0 + j;
+            if (c < nb) {
+              float* y = Y + (size_t)c * ld + k;
+              float o = alpha * __uint_as_float(v[j]);
+              if (beta != 0.f) o += beta * *y;
+              *y = o;
+            }
+          }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&tempty[b]);
     }
-  } else if (threadIdx.x == 0) {
-    atomicExch(&P.status[2], 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtm), "r"(128));
+  if (threadIdx.x == 0 && fail_s) atomicExch(&P.status[2], 1);
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
-void launch_gemm_tn_tc(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride) {
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(f);
+  });
+  return fn;
+}
+
+// 2D FP32 map over rows x cols (row stride ld floats), box 32 x box_rows, 128-byte
+// swizzle, zero fill outside the tensor.
+bool encode_2d(CUtensorMap* m, const void* base, int cols, int rows, int ld, int box_rows) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled unavailable from the driver");
+    return false;
+  }
+  if (!base || cols < 1 || rows < 1 || (reinterpret_cast<uintptr_t>(base) & 15) || ((size_t)ld * 4) % 16 ||
+      ld < cols) {
+    set_error("tensor map: base, extent or stride not 16-byte compatible");
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+size_t tc_map_bytes() { return sizeof(CUtensorMap); }
+
+bool tc_encode_maps(const Prob& d, void* host_maps) {
+  CUtensorMap* m = reinterpret_cast<CUtensorMap*>(host_maps);
+  for (int s = 0; s < TC_NSLOT; ++s) {
+    const void* base = s < NWB ? d.wb[s] : (s == NWB ? d.B : d.dB);
+    const int rows = s < NWB ? d.nb : (s == NWB ? d.natom : 3 * d.natom);
+    if (!encode_2d(m + s * TC_NMAPKIND + 0, base, d.npw, rows, d.ld, 128)) return false;
+    if (!encode_2d(m + s * TC_NMAPKIND + 1, base, d.npw, rows, d.ld, 32)) return false;
+  }
+  return true;
+}
+
+int nn_tc_image_bytes(int nin, int nb) { return 2 * ((nb + 15) & ~15) * ((nin + 31) & ~31) * 4; }
+
+int nn_tc_stages(int img_bytes) {
+  const int img = (img_bytes + 1023) & ~1023;
+  const int s = (TC_SMEM_BUDGET - 1024 - img) / NN_STAGE;
+  return s < NN_MAX_STAGES ? s : NN_MAX_STAGES;
+}
+
+void launch_gemm_tn_tc(const Launch& L, const void* maps, int akind, int arole, int bkind, int brole, double* part,
+                       size_t stride) {
   if (!L.map.total) return;
-  k_gemm_tn_tc<<<L.map.total, 256, 2 * TC_STAGE, L.stream>>>(L.ka, akind, arole, bkind, brole, part, stride);
+  k_gemm_tn_tma<<<L.map.total, TN_THREADS, 1024 + TN_STAGES * TN_STAGE, L.stream>>>(
+      L.ka, reinterpret_cast<const CUtensorMap*>(maps), akind, arole, bkind, brole, part, stride);
+}
+
+void launch_nn_image(const Launch& Lprob, int akind, int msel, float* img, size_t img_stride) {
+  k_nn_image<<<Lprob.ka.nprob, 256, 0, Lprob.stream>>>(Lprob.ka, akind, msel, img, img_stride);
+}
+
+void launch_gemm_nn_tc(const Launch& L, const void* maps, const float* img, size_t img_stride, int img_max,
+                       int akind, int arole, int yrole, double alpha, double beta) {
+  if (!L.map.total) return;
+  const int img_al = (img_max + 1023) & ~1023;
+  const int ns = nn_tc_stages(img_max);
+  k_gemm_nn_tma<<<L.map.total, NN_THREADS, 1024 + img_al + ns * NN_STAGE, L.stream>>>(
+      L.ka, reinterpret_cast<const CUtensorMap*>(maps), img, img_stride, img_al, ns, akind, arole, yrole,
+      (float)alpha, (float)beta);
 }
 
 void gemm_tc_set_smem_limits() {
-  cudaFuncSetAttribute(k_gemm_tn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * TC_STAGE);
+  cudaFuncSetAttribute(k_gemm_tn_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 + TN_STAGES * TN_STAGE);
+  cudaFuncSetAttribute(k_gemm_nn_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BUDGET);
 }
 
 }  // namespace sgo

@@ -58,30 +58,42 @@ __device__ __forceinline__ cplx<double> phase_at(const Prob& P, int atom, int i1
   return ph[i1] * ph[P.n1 + i2] * ph[P.n1 + P.n2 + i3];
 }
 
+__device__ __forceinline__ float cbrt_t(float x) { return cbrtf(x); }
+__device__ __forceinline__ double cbrt_t(double x) { return cbrt(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float log_t(float x) { return logf(x); }
+__device__ __forceinline__ double log_t(double x) { return log(x); }
+
 // Perdew-Zunger 1981 correlation + Slater exchange (unpolarised); rho clipped at 0.
-__device__ __forceinline__ void lda_pz81(double rho, double* exc, double* vxc) {
-  if (!(rho > 1e-30)) {
-    *exc = 0.0;
-    *vxc = 0.0;
+// R = double on the FP64 path.  R = float on the mixed path: v_xc enters the FP32 V_eff
+// there anyway, and eps_xc (relative error ~1e-7 per point) is summed in FP64.  One cube
+// root per point: (3 rho/pi)^(1/3) = (3/pi)^(1/3) rho^(1/3), r_s = (3/(4 pi))^(1/3) / rho^(1/3).
+template <typename R>
+__device__ __forceinline__ void lda_pz81(R rho, R* exc, R* vxc) {
+  if (!(rho > R(1e-30))) {
+    *exc = R(0);
+    *vxc = R(0);
     return;
   }
-  const double ex = -0.75 * cbrt(3.0 * rho / PI);
-  const double rs = cbrt(3.0 / (4.0 * PI * rho));
-  double ec, vc;
-  if (rs >= 1.0) {
-    const double g = -0.1423, b1 = 1.0529, b2 = 0.3334;
-    const double sr = sqrt(rs);
-    const double den = 1.0 + b1 * sr + b2 * rs;
+  const R c = cbrt_t(rho);
+  const R ex = R(-0.75 * 0.98474502184269641) * c;  // (3/pi)^(1/3)
+  const R rs = R(0.62035049089940009) / c;          // (3/(4 pi))^(1/3)
+  R ec, vc;
+  if (rs >= R(1)) {
+    const R g = R(-0.1423), b1 = R(1.0529), b2 = R(0.3334);
+    const R sr = sqrt_t(rs);
+    const R den = R(1) + b1 * sr + b2 * rs;
     ec = g / den;
-    vc = ec * (1.0 + (7.0 / 6.0) * b1 * sr + (4.0 / 3.0) * b2 * rs) / den;
+    vc = ec * (R(1) + R(7.0 / 6.0) * b1 * sr + R(4.0 / 3.0) * b2 * rs) / den;
   } else {
-    const double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
-    const double lr = log(rs);
+    const R A = R(0.0311), B = R(-0.048), C = R(0.0020), D = R(-0.0116);
+    const R lr = log_t(rs);
     ec = A * lr + B + C * rs * lr + D * rs;
-    vc = A * lr + (B - A / 3.0) + (2.0 / 3.0) * C * rs * lr + (2.0 * D - C) / 3.0 * rs;
+    vc = A * lr + (B - A / R(3)) + R(2.0 / 3.0) * C * rs * lr + (R(2) * D - C) / R(3) * rs;
   }
   *exc = ex + ec;
-  *vxc = (4.0 / 3.0) * ex + vc;
+  *vxc = R(4.0 / 3.0) * ex + vc;
 }
 
 }  // namespace
@@ -145,10 +157,10 @@ __global__ void k_veff(KArgs ka, const double* user_v) {
       val = user_v[((size_t)i1 * P.n2 + i2) * P.n3 + i3];
     } else {
       const double2 c = P.gfft[i];
-      double exc, vxc;
-      lda_pz81(c.x, &exc, &vxc);
+      T exc, vxc;
+      lda_pz81<T>((T)c.x, &exc, &vxc);
       P.rho_in[i] = c.x;
-      val = P.vion_r[i] + c.y + vxc;
+      val = P.vion_r[i] + c.y + (double)vxc;
     }
     v[i] = (T)(val * inv_n);
   }
@@ -176,10 +188,9 @@ __global__ void k_vion_g(KArgs ka) {
     int i1, i2, i3;
     grid_pt(P, i, &i1, &i2, &i3);
     cplx<double> acc = mk(0.0, 0.0);
-    for (int a = 0; a < P.natom; ++a) {
-      double v = P.vloc_g[(size_t)P.spec[a] * P.ngrid + i];
-      acc = acc + scale(phase_at(P, a, i1, i2, i3), v);
-    }
+    double v[MAX_SPECIES];
+    for (int s = 0; s < P.nspecies; ++s) v[s] = P.vloc_g[(size_t)s * P.ngrid + i];
+    for (int a = 0; a < P.natom; ++a) acc = acc + scale(phase_at(P, a, i1, i2, i3), v[P.spec[a]]);
     P.gfft[i] = make_double2(acc.x, acc.y);
   }
 }
@@ -196,11 +207,12 @@ __global__ void k_rho0_g(KArgs ka) {
     double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
     cplx<double> acc = mk(0.0, 0.0);
     if (!q.nyq && 0.5 * g2 <= 4.0 * P.ecut) {
-      for (int a = 0; a < P.natom; ++a) {
-        const double* sp = P.sp + P.spec[a] * 6;
-        double amp = sp[0] / P.omega * exp(-g2 * sp[1] * sp[1] * 0.25);
-        acc = acc + scale(phase_at(P, a, i1, i2, i3), amp);
+      double amp[MAX_SPECIES];
+      for (int s = 0; s < P.nspecies; ++s) {
+        const double* sp = P.sp + s * 6;
+        amp[s] = sp[0] / P.omega * exp(-g2 * sp[1] * sp[1] * 0.25);
       }
+      for (int a = 0; a < P.natom; ++a) acc = acc + scale(phase_at(P, a, i1, i2, i3), amp[P.spec[a]]);
     }
     P.rhog_in[i] = make_double2(acc.x, acc.y);
   }
@@ -213,6 +225,7 @@ __global__ void k_rho0_g(KArgs ka) {
 // ---------------------------------------------------------------------------
 constexpr int NGE = 5;
 
+template <typename T>
 __global__ void k_grid_energies(KArgs ka, double* part, int maxchunk) {
   __shared__ double red[33];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
@@ -224,10 +237,10 @@ __global__ void k_grid_energies(KArgs ka, double* part, int maxchunk) {
   double s[NGE] = {0, 0, 0, 0, 0};
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
     double r = P.rho_out[i];
-    double exc, vxc;
-    lda_pz81(r, &exc, &vxc);
+    T exc, vxc;
+    lda_pz81<T>((T)r, &exc, &vxc);
     s[0] += P.vion_r[i] * r;
-    s[1] += fmax(r, 0.0) * exc;
+    s[1] += fmax(r, 0.0) * (double)exc;
     s[2] += r;
     s[3] += fabs(r - P.rho_in[i]);
     GPt q = grid_pt(P, i);
@@ -576,8 +589,9 @@ void launch_pulay_store(const Launch& L) {
 void launch_pulay_mix(const Launch& L, double a, double q0) {
   if (ew_blocks(L)) k_pulay_mix<<<L.map.total, 256, 0, L.stream>>>(L.ka, a, q0);
 }
+template <typename T>
 void launch_grid_energies(const Launch& Lchunks, double* part, int maxchunk) {
-  if (Lchunks.map.total) k_grid_energies<<<Lchunks.map.total, 256, 0, Lchunks.stream>>>(Lchunks.ka, part, maxchunk);
+  if (Lchunks.map.total) k_grid_energies<T><<<Lchunks.map.total, 256, 0, Lchunks.stream>>>(Lchunks.ka, part, maxchunk);
 }
 void launch_grid_energies_reduce(const Launch& L, const double* part, int maxchunk) {
   k_grid_energies_reduce<<<L.ka.nprob, 32, 0, L.stream>>>(L.ka, part, maxchunk);
@@ -602,6 +616,8 @@ void launch_force_total(const Launch& L, int maxchunk) {
   k_force_total<<<L.ka.nprob, 128, 0, L.stream>>>(L.ka, maxchunk);
 }
 
+template void launch_grid_energies<float>(const Launch&, double*, int);
+template void launch_grid_energies<double>(const Launch&, double*, int);
 template void launch_veff<float>(const Launch&, const double*);
 template void launch_veff<double>(const Launch&, const double*);
 template void launch_build_projectors<float>(const Launch&, int);

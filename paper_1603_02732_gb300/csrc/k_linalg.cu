@@ -1,16 +1,16 @@
 // Subspace linear algebra of the all-band CG eigensolver (Algorithm 1).
 //
 //  * gemm_tn: C = A^T B over the packed plane-wave index (K = npw) -- the subspace
-//    matrices H(i,j) = <Psi_i|H|Psi_j> and overlaps (lines 2, 14, 15), the projection
-//    coefficients <Psi_j|P_i> (line 12) and the projector overlaps <beta_I|Psi_n>.
+//    matrices H(i,j) = <Psi_i|H|Psi_j> and overlaps, the projection coefficients
+//    <Psi_j|P_i> of the search directions and the projector overlaps <beta_I|Psi_n>.
 //    Split-K: every CTA sums one K chunk in the working precision and writes an FP64
 //    partial; a second kernel adds the partials in a fixed order (deterministic).
 //  * gemm_nn: Y = beta Y + alpha A M with a small FP64 matrix M -- subspace rotations
-//    (lines 3, 14, 16), the projection P -= Psi C (line 12), the nonlocal apply.
-//  * per-band kernels: residual + preconditioner + conjugate direction (lines 6-11),
-//    normalisation, line minimisation (line 13).
+//    by the Rayleigh-Ritz eigenvectors, the projection P -= Psi C, the nonlocal apply.
+//  * per-band kernels: residual + preconditioner + conjugate direction, normalisation,
+//    line minimisation.
 //  * rr: FP64 Cholesky of the overlap, L^-1 H L^-T and a parallel cyclic Jacobi
-//    eigensolve (the subspace diagonalisation of lines 3 and 16).
+//    eigensolve (the subspace diagonalisation of Algorithm 1).
 //  * occupations: Fermi-Dirac with the chemical potential by safeguarded Newton.
 #include "kernels.h"
 
@@ -254,9 +254,9 @@ __device__ __forceinline__ T tpa(T y) {
   return num / (num + T(16) * y2 * y2);
 }
 
-// Residual R = HX - eps X (line 6), G = A R (TPA; line 8), conjugate direction
+// Residual R = HX - eps X, G = A R (TPA preconditioner), conjugate direction
 // P = G + gamma P_prev with Polak-Ribiere gamma = <G, R - R_prev>/<G_prev, R_prev>, >= 0
-// (line 10).  Writes P and R (for the next step).
+// (Algorithm 1).  Writes P and R (for the next step).
 template <typename T>
 __global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, int hxr, int pr, int rr_out, int ppr, int rpr) {
   __shared__ double red[33];
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(BAND_THREADS) k_normalize(KArgs ka, int pr, in
   if (threadIdx.x == 0) P.bv[BV_PNORM * P.nb + i] = s;
 }
 
-// Line minimisation (line 13): in span{x, p} (p unit, p orthogonal to x) the Rayleigh
+// Line minimisation (Algorithm 1): in span{x, p} (p unit, p orthogonal to x) the Rayleigh
 // quotient is a cos^2 + 2 b sin cos + c sin^2; theta = atan2(-2b, c - a)/2 minimises it.
 template <typename T>
 __global__ void __launch_bounds__(BAND_THREADS) k_line_min(KArgs ka, int xr, int hxr, int pr, int hpr) {
@@ -422,7 +422,8 @@ __global__ void k_copy_out(KArgs ka, int role, double* dst, int nvec) {
 }
 
 // ---------------------------------------------------------------------------
-// Rayleigh-Ritz in FP64, one CTA per problem (lines 3, 14, 16).
+// Rayleigh-Ritz in FP64, one CTA per problem (orthonormalisation + subspace
+// diagonalisation of Algorithm 1).
 //   S = L L^T (Cholesky), C = L^-1 Hs L^-T, C = V diag(eps) V^T (cyclic Jacobi,
 //   round-robin parallel ordering; Golub & Van Loan, Alg. 8.4.3), Tm = L^-T V,
 //   so that X Tm is orthonormal and diagonalises H in the subspace.

@@ -55,8 +55,19 @@ template <typename T>
 void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride);
 void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride,
                            int kc = TN_KC);
-// k_gemm_tc.cu (tcgen05, mixed path, counts <= 128)
-void launch_gemm_tn_tc(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride);
+// k_gemm_tc.cu (tcgen05 + TMA, mixed path, operand counts <= 128)
+constexpr int TC_NSLOT = NWB + 2;      // tensor maps per problem: wave buffers, B, dB
+constexpr int TC_NMAPKIND = 2;         // box 32 x 128 rows (TN), 32 x 32 rows (NN)
+constexpr int NN_TPC = 4;              // 128-wave tiles per NN CTA
+size_t tc_map_bytes();
+bool tc_encode_maps(const Prob& d, void* host_maps);  // TC_NSLOT * TC_NMAPKIND maps of one problem
+int nn_tc_image_bytes(int nin, int nb);
+int nn_tc_stages(int img_bytes);
+void launch_gemm_tn_tc(const Launch& L, const void* maps, int akind, int arole, int bkind, int brole, double* part,
+                       size_t stride);
+void launch_nn_image(const Launch& Lprob, int akind, int msel, float* img, size_t img_stride);
+void launch_gemm_nn_tc(const Launch& L, const void* maps, const float* img, size_t img_stride, int img_max,
+                       int akind, int arole, int yrole, double alpha, double beta);
 void gemm_tc_set_smem_limits();
 template <typename T>
 void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta);
@@ -85,7 +96,7 @@ void launch_vion_g(const Launch& L);
 void launch_rho0_g(const Launch& L);
 void launch_pulay_store(const Launch& L);
 void launch_pulay_mix(const Launch& L, double a, double q0);
-void launch_grid_energies(const Launch& Lchunks, double* part, int maxchunk);
+template <typename T> void launch_grid_energies(const Launch& Lchunks, double* part, int maxchunk);
 void launch_grid_energies_reduce(const Launch& L, const double* part, int maxchunk);
 void launch_finish_iteration(const Launch& L, double tol_e, double tol_rho, int count_iter);
 void launch_pulay_gram(const Launch& Lchunks, double* part, int maxchunk, int hist);

@@ -219,3 +219,24 @@ def test_subspace_matrix_gemm(sgo, precision, tc, tol):
         ref = x @ y.T
         scale = np.sqrt((x ** 2).sum(1))[:, None] * np.sqrt((y ** 2).sum(1))[None, :]
         assert np.abs(c - ref).max() <= tol * scale.max(), (st.name, np.abs(c - ref).max() / scale.max())
+
+
+@pytest.mark.parametrize("precision,tc,tol", [("fp64", 0, 1e-13), ("mixed", 1, 2e-6), ("mixed", 0, 2e-6)])
+def test_block_update_gemm(sgo, precision, tc, tol):
+    """Y <- alpha M^T X + beta Y through the block-update GEMM (tcgen05 3xTF32 on the mixed
+    path with gemm_tc=1) vs NumPy FP64, relative to sum_i |m_ij| |x_i| + |beta| |y_j|;
+    a rotation (beta = 0) and a projection update (alpha = -1, beta = 1), all and part
+    of the bands."""
+    for st in (workloads.tiny(nat=2, ecut=3.5), workloads.de_candidate(0)):
+        ctx = sgo.Context(st, precision=precision, gemm_tc=tc)
+        rng = np.random.default_rng(9)
+        for n in (st.nbands, max(1, st.nbands - 5)):
+            x = rng.normal(size=(n, ctx.npw))
+            y = rng.normal(size=(n, ctx.npw))
+            m = rng.normal(size=(n, n))
+            for alpha, beta in ((1.0, 0.0), (-1.0, 1.0)):
+                out = ctx.block_update(x, m, alpha, beta, y)
+                ref = alpha * (m.T @ x) + beta * y
+                scale = abs(alpha) * (np.abs(m).T @ np.abs(x)) + abs(beta) * np.abs(y)
+                err = np.abs(out - ref) / scale
+                assert err.max() <= tol, (st.name, n, alpha, beta, err.max())

@@ -18,8 +18,10 @@
 // still waits (bounded) for its own loads and MMAs in flight, frees TMEM and returns.
 //
 // TN (C = A^T B, split-K): CTA = (problem, K chunk of TC_KC).  A rows (M = 128 TMEM
-// lanes) and B rows (N = count rounded up to 16) are K-major tiles of 32 K (128 bytes).
-// Each CTA writes its FP32 partial as FP64; k_gemm_tn_reduce adds the chunks in order.
+// lanes) and B rows (N = count rounded up to 16) are K-major tiles of 32 K (128 bytes),
+// packed to the operand counts rounded up to 8 rows (one TMA box each), so that short
+// operands buy deeper pipelines.  Each CTA writes its FP32 partial as FP64;
+// k_gemm_tn_reduce adds the chunks in order.
 //
 // NN (Y = alpha X M + beta Y): CTA = (problem, NN_TPC tiles of 128 plane waves).  The
 // MMA's M is the plane-wave index, K the input row and N the output band.  TMA lands X
@@ -32,6 +34,7 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -42,9 +45,9 @@ namespace sgo {
 namespace {
 
 constexpr int TC_K = 32;                      // floats per 128-byte swizzle row
-constexpr int TC_TILE = 128 * 128;            // bytes of a 128-row x 128-byte tile
-constexpr int TN_STAGES = 3;
-constexpr int TN_STAGE = 4 * TC_TILE;         // A hi, A lo, B hi, B lo
+constexpr int TN_MAX_STAGES = 8;
+constexpr int TN_SMEM = 225 * 1024;           // dynamic shared memory of the TN kernel
+constexpr int TN_PAD = 16 * 1024;             // slack after the last stage (see the TN kernel)
 constexpr int TN_THREADS = 192;
 constexpr int NN_BOX = 32 * 128;              // one 32-row x 32-wave box (4 KB)
 constexpr int NN_STAGE = 3 * 4 * NN_BOX;      // landed boxes (128 waves), hi, lo
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
     k_gemm_tn_tma(KArgs ka, const CUtensorMap* __restrict__ maps, int akind, int arole, int bkind, int brole,
                   double* part_base, size_t part_stride) {
   extern __shared__ unsigned char smem_dyn[];
-  __shared__ __align__(8) uint64_t full[TN_STAGES], conv[TN_STAGES], empty[TN_STAGES], done;
+  __shared__ __align__(8) uint64_t full[TN_MAX_STAGES], conv[TN_MAX_STAGES], empty[TN_MAX_STAGES], done;
   __shared__ uint32_t tmem_base;
   __shared__ int fail_s;
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
@@ -248,7 +251,14 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
   volatile int* fail = &fail_s;
   const int na = count_tc(P, akind), nbv = count_tc(P, bkind);
   const int npad = (nbv + 15) & ~15;
+  // stage = [A hi | A lo | B hi | B lo], ra resp. rb rows of 128 B each (multiples of 8
+  // rows keep every part on a 1024-byte swizzle-atom boundary).  The MMA reads 128 A rows
+  // and npad B rows from the start of a part: rows past ra / rb belong to the next part
+  // (or to the TN_PAD slack after the last stage) and reach only output rows >= na or
+  // columns >= nbv, which are never stored.
   const int ra = (na + 7) & ~7, rb = (nbv + 7) & ~7;
+  const int stage_bytes = 2 * (ra + rb) * 128;
+  const int nst = min(TN_MAX_STAGES, (TN_SMEM - 1024 - TN_PAD) / stage_bytes);
   const int split = blockIdx.x - ka.start[p];
   const int k0 = split * TC_KC, k1 = min(P.npw, k0 + TC_KC);
   const int nsteps = (k1 - k0 + TC_K - 1) / TC_K;
@@ -259,7 +269,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
   }
   if (threadIdx.x == 0) {
     fail_s = 0;
-    for (int s = 0; s < TN_STAGES; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], 128);
       mbar_init(&empty[s], 1);
@@ -267,57 +277,44 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
     mbar_init(&done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp >= 2) {
-    // lo rows beyond the split rows stay zero for the whole kernel (the hi rows there are
-    // zero-filled by TMA: they lie outside the tensor's row range)
-    const int t = threadIdx.x - 64;
-    for (int s = 0; s < TN_STAGES; ++s) {
-      unsigned char* st = smem + s * TN_STAGE;
-      float4* alo = reinterpret_cast<float4*>(st + TC_TILE);
-      float4* blo = reinterpret_cast<float4*>(st + 3 * TC_TILE);
-      for (int u = ra * 8 + t; u < 128 * 8; u += 128) alo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int u = rb * 8 + t; u < 128 * 8; u += 128) blo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
+  const int a_lo = ra * 128, b_hi = 2 * ra * 128, b_lo = b_hi + rb * 128;
 
   if (warp == 0) {
     if (lane == 0) {
       const CUtensorMap* ma = map_of(maps, p, slot_of(P, akind, arole), 0);
       const CUtensorMap* mb = map_of(maps, p, slot_of(P, bkind, brole), 0);
-      int issued[TN_STAGES];
-      for (int s = 0; s < TN_STAGES; ++s) issued[s] = 0;
+      int issued[TN_MAX_STAGES];
+      for (int s = 0; s < TN_MAX_STAGES; ++s) issued[s] = 0;
       for (int it = 0; it < nsteps; ++it) {
-        const int s = it % TN_STAGES, r = it / TN_STAGES;
+        const int s = it % nst, r = it / nst;
         if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1), fail)) break;
-        unsigned char* st = smem + s * TN_STAGE;
-        mbar_expect_tx(&full[s], 2 * TC_TILE);
+        unsigned char* st = smem + s * stage_bytes;
+        mbar_expect_tx(&full[s], (uint32_t)((ra + rb) * 128));
         tma_load_2d(st, ma, k0 + it * TC_K, 0, &full[s]);
-        tma_load_2d(st + 2 * TC_TILE, mb, k0 + it * TC_K, 0, &full[s]);
+        tma_load_2d(st + b_hi, mb, k0 + it * TC_K, 0, &full[s]);
         issued[s] = r + 1;
       }
       // every load issued has landed before the CTA may exit
-      for (int s = 0; s < TN_STAGES; ++s)
+      for (int s = 0; s < nst; ++s)
         if (issued[s] > 0) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1), nullptr);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_tf32(128, npad);
       for (int it = 0; it < nsteps; ++it) {
-        const int s = it % TN_STAGES, r = it / TN_STAGES;
+        const int s = it % nst, r = it / nst;
         if (!mbar_wait(&conv[s], (uint32_t)(r & 1), fail)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t st = su32(smem + s * TN_STAGE);
+        const uint32_t st = su32(smem + s * stage_bytes);
 #pragma unroll
         for (int kk = 0; kk < TC_K / 8; ++kk) {
           const uint32_t o = kk * 32;  // K = 8 TF32 = 32 bytes along the swizzled row
-          const uint64_t ah = desc_sw128(st + o, 16, 1024), al = desc_sw128(st + TC_TILE + o, 16, 1024);
-          const uint64_t bh = desc_sw128(st + 2 * TC_TILE + o, 16, 1024);
-          const uint64_t bl = desc_sw128(st + 3 * TC_TILE + o, 16, 1024);
+          const uint64_t ah = desc_sw128(st + o, 16, 1024), al = desc_sw128(st + a_lo + o, 16, 1024);
+          const uint64_t bh = desc_sw128(st + b_hi + o, 16, 1024), bl = desc_sw128(st + b_lo + o, 16, 1024);
           mma_tf32(tmem, ah, bh, idesc, (it > 0 || kk > 0) ? 1u : 0u);
           mma_tf32(tmem, ah, bl, idesc, 1u);
           mma_tf32(tmem, al, bh, idesc, 1u);
@@ -331,11 +328,11 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
   } else {
     const int t = threadIdx.x - 64;
     for (int it = 0; it < nsteps; ++it) {
-      const int s = it % TN_STAGES, r = it / TN_STAGES;
+      const int s = it % nst, r = it / nst;
       if (!mbar_wait(&full[s], (uint32_t)(r & 1), fail)) break;
-      unsigned char* st = smem + s * TN_STAGE;
-      split_units(st, st + TC_TILE, ra * 8, t, 128);
-      split_units(st + 2 * TC_TILE, st + 3 * TC_TILE, rb * 8, t, 128);
+      unsigned char* st = smem + s * stage_bytes;
+      split_units(st, st + a_lo, ra * 8, t, 128);
+      split_units(st + b_hi, st + b_lo, rb * 8, t, 128);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&conv[s]);
     }
@@ -533,19 +530,17 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int k = (t0 + tl) * 128 + quad * 32 + lane;
       for (int c0 = 0; c0 < npad; c0 += 16) {
+        // the 16 reads of Y go out together, before any store of this chunk
+        float yv[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          yv[j] = (beta != 0.f && k < npw && c0 + j < nb) ? Y[(size_t)(c0 + j) * ld + k] : 0.f;
         uint32_t v[16];
         tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * npad + c0), v);
         if (k < npw) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int c = c0 + j;
-            if (c < nb) {
-              float* y = Y + (size_t)c * ld + k;
-              float o = alpha * __uint_as_float(v[j]);
-              if (beta != 0.f) o += beta * *y;
-              *y = o;
-            }
-          }
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < nb) Y[(size_t)(c0 + j) * ld + k] = alpha * __uint_as_float(v[j]) + beta * yv[j];
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -616,7 +611,7 @@ bool tc_encode_maps(const Prob& d, void* host_maps) {
   for (int s = 0; s < TC_NSLOT; ++s) {
     const void* base = s < NWB ? d.wb[s] : (s == NWB ? d.B : d.dB);
     const int rows = s < NWB ? d.nb : (s == NWB ? d.natom : 3 * d.natom);
-    if (!encode_2d(m + s * TC_NMAPKIND + 0, base, d.npw, rows, d.ld, 128)) return false;
+    if (!encode_2d(m + s * TC_NMAPKIND + 0, base, d.npw, rows, d.ld, std::min(128, (rows + 7) & ~7))) return false;
     if (!encode_2d(m + s * TC_NMAPKIND + 1, base, d.npw, rows, d.ld, 32)) return false;
   }
   return true;
@@ -633,7 +628,7 @@ int nn_tc_stages(int img_bytes) {
 void launch_gemm_tn_tc(const Launch& L, const void* maps, int akind, int arole, int bkind, int brole, double* part,
                        size_t stride) {
   if (!L.map.total) return;
-  k_gemm_tn_tma<<<L.map.total, TN_THREADS, 1024 + TN_STAGES * TN_STAGE, L.stream>>>(
+  k_gemm_tn_tma<<<L.map.total, TN_THREADS, TN_SMEM, L.stream>>>(
       L.ka, reinterpret_cast<const CUtensorMap*>(maps), akind, arole, bkind, brole, part, stride);
 }
 
@@ -652,7 +647,7 @@ void launch_gemm_nn_tc(const Launch& L, const void* maps, const float* img, size
 }
 
 void gemm_tc_set_smem_limits() {
-  cudaFuncSetAttribute(k_gemm_tn_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 + TN_STAGES * TN_STAGE);
+  cudaFuncSetAttribute(k_gemm_tn_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TN_SMEM);
   cudaFuncSetAttribute(k_gemm_nn_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BUDGET);
 }
 

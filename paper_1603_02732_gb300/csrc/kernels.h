@@ -15,7 +15,7 @@ constexpr int PLANE_THREADS_MAX = PLANE_THREADS;
 // GEMM geometry
 constexpr int TN_TILE = 64;
 constexpr int TN_KC = 256;             // K chunk of one split-K partial (CUDA-core GEMM)
-constexpr int TC_KC = 1024;            // K chunk of one split-K partial (tensor-core GEMM)
+constexpr int TC_KC = 512;             // K chunk of one split-K partial (tensor-core GEMM)
 constexpr int NN_RT = 4;              // row tiles of 64 per NN CTA
 constexpr int NN_KP = 128;             // rows of the small matrix staged per pass
 constexpr int BAND_THREADS = 256;

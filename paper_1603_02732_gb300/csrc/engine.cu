@@ -442,7 +442,7 @@ WorkMap Engine::make_map(const std::vector<int>& counts) {
 }
 
 Launch Engine::L(const WorkMap& m) const {
-  ++launches_;
+  if (m.total > 0) ++launches_;  // an empty map launches nothing
   Launch l;
   l.ka = KArgs{d_probs_, m.start ? m.start : m_prob_.start, n_, d_active_};
   l.map = m;
@@ -467,7 +467,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     }
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
-      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc;
+      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2];
   size_t part = 0;
   int max_natom = 0;
   for (int p = 0; p < n_; ++p) {
@@ -483,7 +483,12 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     const int nsplit = div_up(d.npw, TN_KC);
     const int tw = div_up(d.nb, TN_TILE), ta = div_up(d.natom, TN_TILE), td = div_up(3 * d.natom, TN_TILE);
     c_zcol.push_back(d.npair * div_up(d.ncp, QCP));
-    c_plane.push_back(d.npair * d.n3);
+    // plane pass: register FFTs on the mixed path where both plane lengths have one
+    const bool preg = precision_ == 1 && plane_reg_ok(d.n1, d.n2);
+    const int pcls = preg ? plane_reg_class(d.n1, d.n2) : -1;
+    c_plane.push_back(preg ? 0 : d.npair * d.n3);
+    for (int k = 0; k < 2; ++k) c_preg[k].push_back(pcls == k ? plane_reg_ctas(d.n2, d.n3, d.npair) : 0);
+    if (preg) preg_smem_[pcls] = std::max(preg_smem_[pcls], plane_reg_smem(d.n2, d.m1max));
     c_dens.push_back(d.n3);
     c_gz.push_back(div_up(d.n1 * d.n2, QZ));
     c_gp.push_back(d.n3);
@@ -510,6 +515,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   plane_threads_ = PLANE_THREADS;
   m_zcol_ = make_map(c_zcol);
   m_plane_ = make_map(c_plane);
+  for (int k = 0; k < 2; ++k) m_preg_[k] = make_map(c_preg[k]);
   m_dens_ = make_map(c_dens);
   m_gz_ = make_map(c_gz);
   m_gp_ = make_map(c_gp);
@@ -569,8 +575,8 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     allocs_.push_back(d_nnimg_);
   }
   h_flags_.assign(4 * n_, 0.0);
-  // mixed path: FP32 subspace eigensolve when its shared-memory layout fits (nb <= 95)
-  rr_f32_ = precision_ == 1 && (size_t)24 * max_nb_ * max_nb_ <= 216 * 1024;
+  // mixed path: FP32 subspace eigensolve when its shared-memory layout fits (nb <= 105)
+  rr_f32_ = precision_ == 1 && (size_t)20 * max_nb_ * (max_nb_ | 1) <= 216 * 1024;
   rr_smem_bytes_ = (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
   rr_smem_ = rr_smem_bytes_ <= 200 * 1024;
   if (!rr_smem_) {
@@ -581,6 +587,10 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   fft_set_smem_limits(220 * 1024);
   linalg_set_smem_limits(220 * 1024);
   gemm_tc_set_smem_limits();
+  if (precision_ == 1 && !fft_reg_init()) {
+    set_error("register FFT twiddle tables: upload failed");
+    return;
+  }
   ok_ = cuda_ok(cudaGetLastError(), "engine set-up");
 }
 
@@ -753,6 +763,7 @@ void Engine::hpsi(int src, int dst) {
   tend(TK_WAVE_TO_COLS);
   tbeg(TK_PLANE_VPSI);
   launch_plane_vpsi<T>(L(m_plane_));
+  for (int k = 0; k < 2; ++k) launch_plane_vpsi_reg(L(m_preg_[k]), k, preg_smem_[k]);
   tend(TK_PLANE_VPSI);
   tbeg(TK_COLS_TO_WAVE);
   launch_cols_to_wave<T>(L(m_zcol_), src, dst);
@@ -769,7 +780,7 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S, false);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
   tbeg(TK_RR);
-  if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)24 * max_nb_ * max_nb_);  // 8 n^2 (FP64 L) + 4 x 4 n^2
+  if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1));  // 5 FP32 n x (n|1)
   else launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_);
   tend(TK_RR);
   rotate<T>(WB_X, false);

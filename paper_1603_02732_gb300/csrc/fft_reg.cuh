@@ -1,0 +1,120 @@
+// Register-resident FFTs of compile-time length for the plane passes (device side).
+//
+// One thread transforms one whole line held in registers: an in-place mixed-radix
+// decimation-in-frequency transform (Gentleman & Sande, 1966) with radices 2, 3, 4, 5.
+// For a block of length L = R M at offset off, every n1 < M takes the radix-R DFT of
+// x[off + n1 + M r] (r < R), multiplies output k2 by W_L^(n1 k2) (W_L = exp(sign 2 pi i / L))
+// and writes it back to x[off + n1 + M k2]; each block x[off + M k2 ...] of length M then
+// recurses with the next radix.  The result is in digit-reversed order: position p holds
+// frequency dif_freq<N>(p), a compile-time map, so reordering costs no instruction.  All
+// indices and twiddle offsets are compile-time constants after unrolling: the line never
+// leaves registers and every twiddle is a constant-bank operand.  No scaling.
+#pragma once
+
+#include "fft.cuh"
+
+namespace sgo {
+
+// Line lengths with a register transform (all other lengths use the shared-memory engine).
+constexpr int kRegSizes[] = {10, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32, 36, 40, 45, 48, 50, 54, 60, 64, 72};
+constexpr int kRegCount = sizeof(kRegSizes) / sizeof(int);
+
+constexpr int reg_table_offset(int n) {
+  int o = 0;
+  for (int i = 0; i < kRegCount; ++i) {
+    if (kRegSizes[i] == n) return o;
+    o += kRegSizes[i];
+  }
+  return -1;
+}
+constexpr int reg_table_total() {
+  int o = 0;
+  for (int i = 0; i < kRegCount; ++i) o += kRegSizes[i];
+  return o;
+}
+constexpr bool reg_supported(int n) { return reg_table_offset(n) >= 0; }
+
+// radices, outermost stage first (packed one per 4 bits, stage 0 lowest)
+constexpr unsigned reg_plan(int n) {
+  switch (n) {
+    case 10: return 0x52u;  // 2 x 5
+    case 12: return 0x34u;  // 4 x 3
+    case 15: return 0x53u;  // 3 x 5
+    case 16: return 0x44u;  // 4 x 4
+    case 18: return 0x332u;  // 2 x 3 x 3
+    case 20: return 0x54u;  // 4 x 5
+    case 24: return 0x324u;  // 4 x 2 x 3
+    case 25: return 0x55u;  // 5 x 5
+    case 27: return 0x333u;  // 3 x 3 x 3
+    case 30: return 0x532u;  // 2 x 3 x 5
+    case 32: return 0x244u;  // 4 x 4 x 2
+    case 36: return 0x334u;  // 4 x 3 x 3
+    case 40: return 0x524u;  // 4 x 2 x 5
+    case 45: return 0x533u;  // 3 x 3 x 5
+    case 48: return 0x344u;  // 4 x 4 x 3
+    case 50: return 0x552u;  // 2 x 5 x 5
+    case 54: return 0x3332u;  // 2 x 3 x 3 x 3
+    case 60: return 0x534u;  // 4 x 3 x 5
+    case 64: return 0x444u;  // 4 x 4 x 4
+    case 72: return 0x3324u;  // 4 x 2 x 3 x 3
+    default: return 0u;
+  }
+}
+constexpr int reg_radix(int n, int s) { return (int)((reg_plan(n) >> (4 * s)) & 15u); }
+constexpr int reg_nstages(int n) {
+  int s = 0;
+  while (reg_radix(n, s) != 0) ++s;
+  return s;
+}
+
+// frequency index held at position p after the transform
+template <int N>
+__host__ __device__ constexpr int dif_freq(int p) {
+  int k = 0, w = 1, L = N;
+  for (int s = 0; s < reg_nstages(N); ++s) {
+    const int R = reg_radix(N, s), M = L / R;
+    const int d = p / M;
+    p -= d * M;
+    k += d * w;
+    w *= R;
+    L = M;
+  }
+  return k;
+}
+
+// Stage S on the block x[off .. off + L); tab[t] = exp(-2 pi i t / NT).
+template <typename T, int NT, int L, int S, int SIGN>
+__device__ __forceinline__ void reg_dif(cplx<T> (&x)[NT], const cplx<T>* __restrict__ tab, int off) {
+  constexpr int R = reg_radix(NT, S);
+  constexpr int M = L / R;
+#pragma unroll
+  for (int n1 = 0; n1 < M; ++n1) {
+    cplx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[off + n1 + M * r];
+    Bfly<T, R>::run(v, T(SIGN), tab, NT / R);
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) {
+      cplx<T> a = v[k2];
+      if (n1 > 0 && k2 > 0) {
+        cplx<T> w = tab[n1 * k2 * (NT / L)];
+        if (SIGN > 0) w.y = -w.y;
+        a = a * w;
+      }
+      x[off + n1 + M * k2] = a;
+    }
+  }
+  if constexpr (S + 1 < reg_nstages(NT)) {
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) reg_dif<T, NT, M, S + 1, SIGN>(x, tab, off + M * k2);
+  }
+}
+
+// In-register DFT of length N (sign -1 forward r -> G, +1 inverse G -> r); the result
+// for frequency dif_freq<N>(p) is left in x[p].
+template <typename T, int N, int SIGN>
+__device__ __forceinline__ void reg_fft(cplx<T> (&x)[N], const cplx<T>* tab) {
+  reg_dif<T, N, N, 0, SIGN>(x, tab, 0);
+}
+
+}  // namespace sgo

@@ -9,7 +9,12 @@
 //   (V psi_b)(G) = (F(G) - F(-G)^*)/(2i).
 // The grid kernels at the end transform full FP64 complex grids (densities,
 // potentials) with the same line engine.
+#include <cmath>
+#include <mutex>
+#include <vector>
+
 #include "fft.cuh"
+#include "fft_reg.cuh"
 #include "kernels.h"
 
 namespace sgo {
@@ -224,6 +229,138 @@ __global__ void __launch_bounds__(PLANE_THREADS, sizeof(T) == 4 ? PLANE_MIN_BLOC
 }
 
 // ---------------------------------------------------------------------------
+// Register-FFT plane pass of H.psi (mixed path, line lengths with a register transform).
+// CTA = (problem, band pair, block of Q = blockDim / N2 z-planes).  Shared memory holds
+// only the occupied x rows of each plane (|m1| <= m1max, compact row index rho), rows
+// padded to an odd length (N2 | 1) so that a thread per row and a thread per column
+// both touch 16 distinct 8-byte bank pairs per half warp.  Passes: scatter the compact
+// columns; y inverse (thread per occupied row); per column: x inverse of the occupied
+// rows, times V_eff/N, x forward, occupied rows back (thread per column, the full
+// column in registers); y forward; gather the compact columns.
+// ---------------------------------------------------------------------------
+namespace {
+
+__constant__ cplx<float> c_tw[reg_table_total()];  // per length N: exp(-2 pi i t / N)
+
+template <int N>
+__device__ __forceinline__ const cplx<float>* twf() {
+  return c_tw + reg_table_offset(N);
+}
+
+template <int N, int SIGN>
+__device__ __forceinline__ void row_fft(cplx<float>* row) {
+  cplx<float> x[N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) x[e] = row[e];
+  reg_fft<float, N, SIGN>(x, twf<N>());
+#pragma unroll
+  for (int p = 0; p < N; ++p) row[dif_freq<N>(p)] = x[p];
+}
+
+template <int MAXN, int SIGN>
+__device__ __forceinline__ void row_fft_n(int n, cplx<float>* row) {
+  switch (n) {
+#define SGO_ROW(N)                                 \
+  case N:                                          \
+    if constexpr (N <= MAXN) row_fft<N, SIGN>(row); \
+    break;
+    SGO_ROW(10) SGO_ROW(12) SGO_ROW(15) SGO_ROW(16) SGO_ROW(18) SGO_ROW(20) SGO_ROW(24) SGO_ROW(25) SGO_ROW(27)
+    SGO_ROW(30) SGO_ROW(32) SGO_ROW(36) SGO_ROW(40) SGO_ROW(45) SGO_ROW(48) SGO_ROW(50) SGO_ROW(54) SGO_ROW(60)
+    SGO_ROW(64) SGO_ROW(72)
+#undef SGO_ROW
+    default: break;
+  }
+}
+
+// Column of N elements (x direction) at col[rho * stride]: occupied rows e <= mx and
+// e >= N - mx sit at rho = e resp. e - N + 2 mx + 1, the others are zero.
+template <int N>
+__device__ __forceinline__ void col_vpsi(cplx<float>* col, int stride, const float* __restrict__ v, int vstride,
+                                         int mx) {
+  const int R = 2 * mx + 1;
+  cplx<float> x[N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) {
+    const bool lo = e <= mx, hi = e >= N - mx;
+    x[e] = (lo || hi) ? col[(lo ? e : e - N + R) * stride] : mk(0.f, 0.f);
+  }
+  reg_fft<float, N, 1>(x, twf<N>());
+  cplx<float> y[N];  // back to natural order (a renaming of registers)
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    const int e = dif_freq<N>(p);
+    y[e] = scale(x[p], __ldg(v + e * vstride));
+  }
+  reg_fft<float, N, -1>(y, twf<N>());
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    const int e = dif_freq<N>(p);
+    const bool lo = e <= mx, hi = e >= N - mx;
+    if (lo || hi) col[(lo ? e : e - N + R) * stride] = y[p];
+  }
+}
+
+template <int MAXN>
+__device__ __forceinline__ void col_vpsi_n(int n, cplx<float>* col, int stride, const float* v, int vstride,
+                                           int mx) {
+  switch (n) {
+#define SGO_COL(N)                                                     \
+  case N:                                                              \
+    if constexpr (N <= MAXN) col_vpsi<N>(col, stride, v, vstride, mx); \
+    break;
+    SGO_COL(10) SGO_COL(12) SGO_COL(15) SGO_COL(16) SGO_COL(18) SGO_COL(20) SGO_COL(24) SGO_COL(25) SGO_COL(27)
+    SGO_COL(30) SGO_COL(32) SGO_COL(36) SGO_COL(40) SGO_COL(45) SGO_COL(48) SGO_COL(50) SGO_COL(54) SGO_COL(60)
+    SGO_COL(64) SGO_COL(72)
+#undef SGO_COL
+    default: break;
+  }
+}
+
+}  // namespace
+
+template <int MAXN>
+__global__ void __launch_bounds__(PLANE_REG_THREADS, MAXN <= 40 ? 2 : 1) k_plane_vpsi_reg(KArgs ka) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int n1 = P.n1, n2 = P.n2, n3 = P.n3, mx = P.m1max, ncol = P.ncol;
+  const int R = 2 * mx + 1, P2 = n2 | 1, plane = R * P2;
+  const int Q = PLANE_REG_THREADS / n2;
+  const int nzb = (n3 + Q - 1) / Q;
+  const int local = blockIdx.x - ka.start[p];
+  const int pair = local / nzb, zb = local - pair * nzb;
+  const int z0 = zb * Q, nq = min(Q, n3 - z0);
+  cplx<float>* S = reinterpret_cast<cplx<float>*>(smem_raw);
+  cplx<float>* wc = reinterpret_cast<cplx<float>*>(P.Wc) + ((size_t)pair * n3 + z0) * ncol;
+  for (int t = threadIdx.x; t < nq * plane; t += blockDim.x) S[t] = mk(0.f, 0.f);
+  __syncthreads();
+  for (int t = threadIdx.x; t < nq * ncol; t += blockDim.x) {
+    const int q = t / ncol, c = t - q * ncol;
+    const int xy = P.col_xy[c];
+    const int i1 = xy / n2, i2 = xy - i1 * n2;
+    S[q * plane + (i1 <= mx ? i1 : i1 - n1 + R) * P2 + i2] = wc[t];
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN, 1>(n2, S + l * P2);
+  __syncthreads();
+  const float* veff = reinterpret_cast<const float*>(P.veff) + (size_t)z0 * n1 * n2;
+  for (int l = threadIdx.x; l < nq * n2; l += blockDim.x) {
+    const int q = l / n2, i2 = l - q * n2;
+    col_vpsi_n<MAXN>(n1, S + q * plane + i2, P2, veff + (size_t)q * n1 * n2 + i2, n2, mx);
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN, -1>(n2, S + l * P2);
+  __syncthreads();
+  for (int t = threadIdx.x; t < nq * ncol; t += blockDim.x) {
+    const int q = t / ncol, c = t - q * ncol;
+    const int xy = P.col_xy[c];
+    const int i1 = xy / n2, i2 = xy - i1 * n2;
+    wc[t] = S[q * plane + (i1 <= mx ? i1 : i1 - n1 + R) * P2 + i2];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Per (problem, z): rho(r) = (1/Omega) sum_pairs f_a Re^2 + f_b Im^2 over all band pairs,
 // accumulated in registers (point t + i*blockDim per thread) in FP64.
 // ---------------------------------------------------------------------------
@@ -342,6 +479,42 @@ void launch_plane_vpsi(const Launch& L) {
   size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<T>);
   k_plane_vpsi<T><<<L.map.total, L.plane_threads, sm, L.stream>>>(L.ka);
 }
+bool plane_reg_ok(int n1, int n2) {
+  return reg_supported(n1) && reg_supported(n2) && n1 <= PLANE_REG_MAXN && n2 <= PLANE_REG_MAXN;
+}
+int plane_reg_class(int n1, int n2) { return (n1 <= 40 && n2 <= 40) ? 0 : 1; }
+int plane_reg_ctas(int n2, int n3, int npair) {
+  const int q = PLANE_REG_THREADS / n2;
+  return npair * ((n3 + q - 1) / q);
+}
+size_t plane_reg_smem(int n2, int m1max) {
+  return (size_t)(PLANE_REG_THREADS / n2) * (2 * m1max + 1) * (n2 | 1) * sizeof(cplx<float>);
+}
+
+bool fft_reg_init() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return true;
+  std::vector<cplx<float>> h(reg_table_total());
+  for (int i = 0, o = 0; i < kRegCount; o += kRegSizes[i], ++i)
+    for (int t = 0; t < kRegSizes[i]; ++t) {
+      const double a = 2.0 * PI * t / kRegSizes[i];
+      h[o + t] = mk((float)std::cos(a), (float)(-std::sin(a)));
+    }
+  if (cudaMemcpyToSymbol(c_tw, h.data(), sizeof(cplx<float>) * h.size()) != cudaSuccess) return false;
+  done[dev] = true;
+  return true;
+}
+
+void launch_plane_vpsi_reg(const Launch& L, int cls, size_t smem) {
+  if (!L.map.total) return;
+  if (cls == 0) k_plane_vpsi_reg<40><<<L.map.total, PLANE_REG_THREADS, smem, L.stream>>>(L.ka);
+  else k_plane_vpsi_reg<PLANE_REG_MAXN><<<L.map.total, PLANE_REG_THREADS, smem, L.stream>>>(L.ka);
+}
+
 template <typename T>
 void launch_plane_density(const Launch& L, const double* occ_override) {
   if (!L.map.total) return;
@@ -370,6 +543,8 @@ void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_plane_density<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_plane_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_z_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_plane_vpsi_reg<40>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_plane_vpsi_reg<PLANE_REG_MAXN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template void launch_wave_to_cols<float>(const Launch&, int);

@@ -614,116 +614,114 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
 }
 
 // ---------------------------------------------------------------------------
-// Rayleigh-Ritz for the mixed path, one CTA per problem.  FP64: symmetrised S and Hs,
-// Cholesky S = L L^T.  FP32: L^-1, C = L^-1 Hs L^-T and its cyclic Jacobi
-// eigensolve, accumulated onto L^-T (the rotation matrix feeds the FP32 block
-// rotation, so accuracy beyond FP32 would be discarded there).
-// Shared memory: L (double n^2); Lf, Li, A, V (float n^2 each).
+// Rayleigh-Ritz for the mixed path, one CTA per problem, in FP32 shared memory.
+// The overlap is factored in deviation form: S = I + E, L = I + D (Cholesky), L^-1 =
+// I + G.  Every stored quantity is then of the size of E and keeps FP32 relative
+// accuracy, so the factors are as accurate as an FP64 factorisation of the same S (whose
+// entries carry the GEMM's FP32 rounding anyway): for column k, with x = E_kk - sum D_kj^2
+// (the running trailing entry), d_k = sqrt(1 + x) - 1 = x / (1 + sqrt(1 + x)), and
+// D_ik = (E_ik - sum_j D_ij D_kj) / (1 + d_k).  G follows from (I + D)(I + G) = I row by
+// row.  Then C = (I + G) H (I + G)^T, its cyclic Jacobi eigensolve accumulated onto
+// V = (I + G)^T, and Tm = V in ascending eigenvalue order.  The eigen-rotation feeds the
+// FP32 block rotation, so accuracy beyond FP32 would be discarded there.
+// Shared memory: D, G, Hf (then V^T), W, A, each n x ns floats with an odd row stride
+// ns = n | 1, so that walks down a column hit distinct banks.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[33];
+  __shared__ float red[32];
   __shared__ float cs_c[256], cs_s[256];
   __shared__ int pr_p[256], pr_q[256];
   __shared__ int flag, nbig;
   const int p = blockIdx.x;
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
-  const int n = P.nb;
-  // [L: double n^2 | Lf, Li: float n^2 each (alias Lf on the upper half of the second
-  //  double block) | A, V: float n^2 each]
-  double* L = reinterpret_cast<double*>(smem_raw);
-  float* Lf = reinterpret_cast<float*>(L + n * n);
-  float* Li = Lf + n * n;
-  float* A = Li + n * n;
-  float* V = A + n * n;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int n = P.nb, ns = n | 1, nn = n * ns;
+  float* D = reinterpret_cast<float*>(smem_raw);
+  float* G = D + nn;
+  float* Hf = G + nn;
+  float* W = Hf + nn;
+  float* A = W + nn;
+  float* Vt = Hf;  // V^T, once Hf is consumed
+  const int tid = threadIdx.x, nt = blockDim.x, tx = tid & 31, ty = tid >> 5, nty = nt >> 5;
   if (tid == 0) flag = 0;
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
-    L[e] = 0.5 * (P.S[i * n + j] + P.S[j * n + i]);
-  }
+  for (int i = ty; i < n; i += nty)
+    for (int j = tx; j < n; j += 32) {
+      D[i * ns + j] = (float)(0.5 * (P.S[i * n + j] + P.S[j * n + i]) - (i == j ? 1.0 : 0.0));
+      Hf[i * ns + j] = (float)(0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]));
+      G[i * ns + j] = 0.f;
+    }
   __syncthreads();
-  // FP64 Cholesky of the overlap, right-looking, two barriers per column
+  // Cholesky in deviation form, right-looking, lower triangle; D_kk holds d_k
   for (int k = 0; k < n; ++k) {
-    double d = L[k * n + k];
-    if (!(d > 0.0)) d = 1.0;
-    const double dk = sqrt(d), idk = 1.0 / dk;
-    for (int i = k + 1 + tid; i < n; i += nt) L[i * n + k] *= idk;
+    const float x = D[k * ns + k];
+    const float xs = fmaxf(x, -0.999f);
+    const float dk = xs / (1.f + sqrtf(1.f + xs));
+    const float inv = 1.f / (1.f + dk);
+    for (int i = k + 1 + tid; i < n; i += nt) D[i * ns + k] *= inv;
     __syncthreads();
     if (tid == 0) {
-      if (!(L[k * n + k] > 0.0)) flag = 1;
-      L[k * n + k] = dk;
+      if (!(x > -0.999f)) flag = 1;  // S not positive definite (to FP32 resolution)
+      D[k * ns + k] = dk;
     }
-    const int m = n - k - 1;
-    for (int e = tid; e < m * m; e += nt) {
-      int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) L[i * n + j] -= L[i * n + k] * L[j * n + k];
+    for (int i = k + 1 + ty; i < n; i += nty) {
+      const float lik = D[i * ns + k];
+      for (int j = k + 1 + tx; j <= i; j += 32) D[i * ns + j] -= lik * D[j * ns + k];
     }
     __syncthreads();
   }
-  for (int e = tid; e < n * n; e += nt) {
-    const int i = e / n, j = e % n;
-    Lf[e] = j <= i ? (float)L[e] : 0.f;
-    Li[e] = 0.f;
-  }
-  __syncthreads();
-  // L^-1 by columns in FP32 (column j depends only on itself: no barrier)
-  for (int j = tid; j < n; j += nt) {
-    Li[j * n + j] = 1.f / Lf[j * n + j];
-    for (int i = j + 1; i < n; ++i) {
+  // G: G_ii = -d_i / (1 + d_i), G_ij = -(D_ij + sum_{j<=k<i} D_ik G_kj) / (1 + d_i); rows in
+  // order, one warp per column j, lanes splitting the sum
+  for (int i = 0; i < n; ++i) {
+    const float di = D[i * ns + i];
+    const float inv = 1.f / (1.f + di);
+    for (int j = ty; j < i; j += nty) {
       float s = 0.f;
-      for (int k = j; k < i; ++k) s += Lf[i * n + k] * Li[k * n + j];
-      Li[i * n + j] = -s / Lf[i * n + i];
+      for (int k = j + tx; k < i; k += 32) s += D[i * ns + k] * G[k * ns + j];
+      s = warp_sum_f(s);
+      if (tx == 0) G[i * ns + j] = -(D[i * ns + j] + s) * inv;
     }
+    if (tid == 0) G[i * ns + i] = -di * inv;
+    __syncthreads();
   }
+  // W = (I + G) Hf, A = W (I + G)^T
+  for (int i = ty; i < n; i += nty)
+    for (int j = tx; j < n; j += 32) {
+      float s = 0.f;
+      for (int k = 0; k <= i; ++k) s += G[i * ns + k] * Hf[k * ns + j];
+      W[i * ns + j] = Hf[i * ns + j] + s;
+    }
   __syncthreads();
-  // Lf := sym(Hs) (float); V := Hs Li^T; A := Li V
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
-    Lf[e] = (float)(0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]));
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
-    float s = 0.f;
-    for (int k = 0; k <= j; ++k) s += Lf[i * n + k] * Li[j * n + k];
-    V[e] = s;
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
-    float s = 0.f;
-    for (int k = 0; k <= i; ++k) s += Li[i * n + k] * V[k * n + j];
-    A[e] = s;
-  }
+  for (int i = ty; i < n; i += nty)
+    for (int j = tx; j < n; j += 32) {
+      float s = 0.f;
+      for (int k = 0; k <= j; ++k) s += W[i * ns + k] * G[j * ns + k];
+      A[i * ns + j] = W[i * ns + j] + s;
+    }
   __syncthreads();
   float amax = 0.f;
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
-    if (j > i) {
-      float s = 0.5f * (A[i * n + j] + A[j * n + i]);
-      A[i * n + j] = s;
-      A[j * n + i] = s;
+  for (int i = ty; i < n; i += nty)
+    for (int j = tx; j < n; j += 32) {
+      if (j > i) {
+        const float sy = 0.5f * (A[i * ns + j] + A[j * ns + i]);
+        A[i * ns + j] = sy;
+        A[j * ns + i] = sy;
+      }
+      if (i == j) amax = fmaxf(amax, fabsf(A[i * ns + i]));
+      Vt[i * ns + j] = (i == j ? 1.f : 0.f) + G[i * ns + j];  // V = (I + G)^T = L^-T
     }
-    if (i == j) amax = fmaxf(amax, fabsf(A[e]));
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
-    V[e] = Li[j * n + i];  // rotations accumulate onto L^-T
-  }
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  if ((tid & 31) == 0) red[tid >> 5] = amax;
+  if (tx == 0) red[ty] = amax;
   __syncthreads();
-  if (tid == 0) {
-    float mm = 0.f;
-    for (int w = 0; w < (nt + 31) / 32; ++w) mm = fmaxf(mm, (float)red[w]);
-    red[32] = mm;
-  }
-  __syncthreads();
+  float mm = 0.f;
+  for (int w = 0; w < nty; ++w) mm = fmaxf(mm, red[w]);
   // rotations below 2e-7 max|a_ii| (about the FP32 resolution of the matrix) are skipped
-  const float thr = 2e-7f * (float)red[32];
+  const float thr = 2e-7f * mm;
   // Cyclic Jacobi, round-robin pairs; a round maps every 2x2 block of pair rows P and
   // pair columns Q as A_PQ <- J_P^T A_PQ J_Q (one pass), and V_{:,Q} <- V_{:,Q} J_Q.
   const int m = n + (n & 1);
@@ -732,25 +730,24 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
   for (int sweep = 0; sweep < 10; ++sweep) {
     if (tid == 0) nbig = 0;
     __syncthreads();
-    for (int e = tid; e < n * n; e += nt) {
-      int i = e / n, j = e % n;
-      if (i < j && fabsf(A[e]) > thr) nbig = 1;
-    }
+    for (int i = ty; i < n; i += nty)
+      for (int j = i + 1 + tx; j < n; j += 32)
+        if (fabsf(A[i * ns + j]) > thr) nbig = 1;
     __syncthreads();
     if (nbig == 0) break;
     ++sweeps;
     for (int r = 0; r < m - 1; ++r) {
       if (tid < half) {
-        int a = tid, b = m - 1 - tid;
-        int pa = a == 0 ? 0 : 1 + (a - 1 + r) % (m - 1);
-        int pb = b == 0 ? 0 : 1 + (b - 1 + r) % (m - 1);
-        int pp = min(pa, pb), qq = max(pa, pb);
+        const int a = tid, b = m - 1 - tid;
+        const int pa = a == 0 ? 0 : 1 + (a - 1 + r) % (m - 1);
+        const int pb = b == 0 ? 0 : 1 + (b - 1 + r) % (m - 1);
+        const int pp = min(pa, pb), qq = max(pa, pb);
         float c = 1.f, s = 0.f;
         if (qq < n) {
-          float apq = A[pp * n + qq];
+          const float apq = A[pp * ns + qq];
           if (fabsf(apq) > thr) {
-            float tau = (A[qq * n + qq] - A[pp * n + pp]) / (2.f * apq);
-            float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            const float tau = (A[qq * ns + qq] - A[pp * ns + pp]) / (2.f * apq);
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c = rsqrtf(1.f + t * t);
             s = t * c;
           }
@@ -761,54 +758,57 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
         pr_q[tid] = qq;
       }
       __syncthreads();
-      // blocks (P, Q), P, Q < half; rows/cols equal to n (the odd dummy) are absent
-      for (int e = tid; e < half * half; e += nt) {
-        const int P2 = e / half, Q2 = e % half;
-        const float sp = cs_s[P2], sq = cs_s[Q2];
-        if (sp == 0.f && sq == 0.f) continue;
-        const float cp = cs_c[P2], cq = cs_c[Q2];
-        const int p0 = pr_p[P2], p1 = pr_q[P2], q0 = pr_p[Q2], q1 = pr_q[Q2];
-        const bool h1 = p1 < n, g1 = q1 < n;
-        float a00 = A[p0 * n + q0];
-        float a01 = g1 ? A[p0 * n + q1] : 0.f;
-        float a10 = h1 ? A[p1 * n + q0] : 0.f;
-        float a11 = (h1 && g1) ? A[p1 * n + q1] : 0.f;
-        // rows: J_P^T
-        float b00 = cp * a00 - sp * a10, b01 = cp * a01 - sp * a11;
-        float b10 = sp * a00 + cp * a10, b11 = sp * a01 + cp * a11;
-        // columns: J_Q
-        A[p0 * n + q0] = cq * b00 - sq * b01;
-        if (g1) A[p0 * n + q1] = sq * b00 + cq * b01;
-        if (h1) A[p1 * n + q0] = cq * b10 - sq * b11;
-        if (h1 && g1) A[p1 * n + q1] = sq * b10 + cq * b11;
+      // blocks (P, Q); rows / columns equal to n (the odd dummy) are absent
+      for (int P2 = ty; P2 < half; P2 += nty) {
+        const float sp = cs_s[P2], cp = cs_c[P2];
+        const int p0 = pr_p[P2], p1 = pr_q[P2];
+        const bool h1 = p1 < n;
+        for (int Q2 = tx; Q2 < half; Q2 += 32) {
+          const float sq = cs_s[Q2];
+          if (sp == 0.f && sq == 0.f) continue;
+          const float cq = cs_c[Q2];
+          const int q0 = pr_p[Q2], q1 = pr_q[Q2];
+          const bool g1 = q1 < n;
+          const float a00 = A[p0 * ns + q0];
+          const float a01 = g1 ? A[p0 * ns + q1] : 0.f;
+          const float a10 = h1 ? A[p1 * ns + q0] : 0.f;
+          const float a11 = (h1 && g1) ? A[p1 * ns + q1] : 0.f;
+          const float b00 = cp * a00 - sp * a10, b01 = cp * a01 - sp * a11;  // rows: J_P^T
+          const float b10 = sp * a00 + cp * a10, b11 = sp * a01 + cp * a11;
+          A[p0 * ns + q0] = cq * b00 - sq * b01;                            // columns: J_Q
+          if (g1) A[p0 * ns + q1] = sq * b00 + cq * b01;
+          if (h1) A[p1 * ns + q0] = cq * b10 - sq * b11;
+          if (h1 && g1) A[p1 * ns + q1] = sq * b10 + cq * b11;
+        }
       }
-      for (int e = tid; e < half * n; e += nt) {
-        const int Q2 = e / n, i = e % n;
+      for (int Q2 = ty; Q2 < half; Q2 += nty) {
         const float sq = cs_s[Q2];
         if (sq == 0.f) continue;
         const float cq = cs_c[Q2];
         const int q0 = pr_p[Q2], q1 = pr_q[Q2];
-        float v0 = V[i * n + q0], v1 = V[i * n + q1];
-        V[i * n + q0] = cq * v0 - sq * v1;
-        V[i * n + q1] = sq * v0 + cq * v1;
+        for (int i = tx; i < n; i += 32) {
+          const float v0 = Vt[q0 * ns + i], v1 = Vt[q1 * ns + i];
+          Vt[q0 * ns + i] = cq * v0 - sq * v1;
+          Vt[q1 * ns + i] = sq * v0 + cq * v1;
+        }
       }
       __syncthreads();
     }
   }
   for (int j = tid; j < n; j += nt) {
-    float ej = A[j * n + j];
+    const float ej = A[j * ns + j];
     int rank = 0;
     for (int k2 = 0; k2 < n; ++k2) {
-      float ek = A[k2 * n + k2];
+      const float ek = A[k2 * ns + k2];
       rank += (ek < ej) || (ek == ej && k2 < j);
     }
     P.eps[rank] = (double)ej;
     P.bv[BV_TMP0 * n + j] = (double)rank;
   }
   __syncthreads();
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
-    P.Tm[i * n + (int)P.bv[BV_TMP0 * n + j]] = (double)V[e];
+  for (int j = ty; j < n; j += nty) {
+    const int rj = (int)P.bv[BV_TMP0 * n + j];
+    for (int i = tx; i < n; i += 32) P.Tm[i * n + rj] = (double)Vt[j * ns + i];
   }
   if (tid == 0) {
     P.scal[SC_RRSWEEPS] += sweeps;

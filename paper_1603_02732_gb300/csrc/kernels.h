@@ -12,6 +12,8 @@ constexpr int QZ = 32;                 // grid columns per z CTA
 constexpr int PLANE_THREADS = 256;      // threads of the z-plane kernels
 constexpr int PLANE_MIN_BLOCKS = 4;     // register cap (64) for 4+ resident CTAs per SM
 constexpr int PLANE_THREADS_MAX = PLANE_THREADS;
+constexpr int PLANE_REG_THREADS = 256;  // register-FFT plane kernel (mixed path)
+constexpr int PLANE_REG_MAXN = 72;      // longest x / y line it transforms
 // GEMM geometry
 constexpr int TN_TILE = 64;
 constexpr int TN_KC = 256;             // K chunk of one split-K partial (CUDA-core GEMM)
@@ -49,6 +51,13 @@ template <typename T> void launch_plane_density(const Launch& L, const double* o
 void launch_grid_plane_fft(const Launch& L, int which, int sign);
 void launch_grid_z_fft(const Launch& L, int which, int sign);
 void fft_set_smem_limits(size_t bytes);
+// register-FFT plane pass (mixed path): lengths n1, n2 with a register transform
+bool plane_reg_ok(int n1, int n2);
+int plane_reg_class(int n1, int n2);          // 0: both <= 40, 1: up to PLANE_REG_MAXN
+int plane_reg_ctas(int n2, int n3, int npair);
+size_t plane_reg_smem(int n2, int m1max);
+bool fft_reg_init();                          // twiddle tables on the current device
+void launch_plane_vpsi_reg(const Launch& L, int cls, size_t smem);
 
 // k_linalg.cu
 template <typename T>

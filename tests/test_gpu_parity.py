@@ -36,8 +36,10 @@ def _struct(grid=None, ecut=3.5, nat=2, seed=7, kT=0.01, nbands=None):
 
 
 # every FFT radix: 9 (9), 10 12 15 (10,12,15), 16 9 2 10 (16,18,20), 12 2 (24),
-# 15 2 / 9 6 / 10 4 (30,54,40), 9 2 / 12 3 / 16 8 (18,36,128)
-GRIDS = [None, (10, 12, 15), (16, 18, 20), (24, 24, 24), (30, 54, 40), (18, 36, 128)]
+# 15 2 / 9 6 / 10 4 (30,54,40), 9 2 / 12 3 / 16 8 (18,36,128); the mixed path's
+# register plane transforms in both size classes: 45 40, 60 50, 72 64, 27 25, 20 48
+GRIDS = [None, (10, 12, 15), (16, 18, 20), (24, 24, 24), (30, 54, 40), (18, 36, 128), (45, 40, 16),
+         (60, 50, 12), (72, 64, 10), (27, 25, 32), (20, 48, 15)]
 
 
 @pytest.mark.parametrize("grid", GRIDS)

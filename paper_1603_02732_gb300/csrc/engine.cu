@@ -117,6 +117,7 @@ void layout(sgo_ctx* c, A& a) {
   d.gvec = a.template take<double>(3 * (size_t)ld);
   d.colmap = a.template take<int>(n12);
   d.col_xy = a.template take<int>(d.ncol);
+  d.col_sidx = a.template take<int>(d.ncol);
   d.roots64 = a.template take<double2>(nt);
   d.roots32 = a.template take<float2>(nt);
   d.pos = a.template take<double>(3 * na);
@@ -488,7 +489,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     const int pcls = preg ? plane_reg_class(d.n1, d.n2) : -1;
     c_plane.push_back(preg ? 0 : d.npair * d.n3);
     for (int k = 0; k < 2; ++k) c_preg[k].push_back(pcls == k ? plane_reg_ctas(d.n2, d.n3, d.npair) : 0);
-    if (preg) preg_smem_[pcls] = std::max(preg_smem_[pcls], plane_reg_smem(d.n2, d.m1max));
+    if (preg) preg_smem_[pcls] = std::max(preg_smem_[pcls], plane_reg_smem(d.n1, d.n2, d.m1max));
     c_dens.push_back(d.n3);
     c_gz.push_back(div_up(d.n1 * d.n2, QZ));
     c_gp.push_back(d.n3);

@@ -233,14 +233,29 @@ __global__ void __launch_bounds__(PLANE_THREADS, sizeof(T) == 4 ? PLANE_MIN_BLOC
 // CTA = (problem, band pair, block of Q = blockDim / N2 z-planes).  Shared memory holds
 // only the occupied x rows of each plane (|m1| <= m1max, compact row index rho), rows
 // padded to an odd length (N2 | 1) so that a thread per row and a thread per column
-// both touch 16 distinct 8-byte bank pairs per half warp.  Passes: scatter the compact
-// columns; y inverse (thread per occupied row); per column: x inverse of the occupied
-// rows, times V_eff/N, x forward, occupied rows back (thread per column, the full
-// column in registers); y forward; gather the compact columns.
+// both touch 16 distinct 8-byte bank pairs per half warp, and the planes' V_eff / N.
+// Passes: scatter the compact columns (asynchronous copies to precomputed slots, the
+// potential following); y inverse (thread per occupied row); per column: x inverse of
+// the occupied rows, times V_eff/N, x forward, occupied rows back (thread per column,
+// the full column in registers); y forward; gather the compact columns.
 // ---------------------------------------------------------------------------
 namespace {
 
 __constant__ cplx<float> c_tw[reg_table_total()];  // per length N: exp(-2 pi i t / N)
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 template <int N>
 __device__ __forceinline__ const cplx<float>* twf() {
@@ -275,8 +290,7 @@ __device__ __forceinline__ void row_fft_n(int n, cplx<float>* row) {
 // Column of N elements (x direction) at col[rho * stride]: occupied rows e <= mx and
 // e >= N - mx sit at rho = e resp. e - N + 2 mx + 1, the others are zero.
 template <int N>
-__device__ __forceinline__ void col_vpsi(cplx<float>* col, int stride, const float* __restrict__ v, int vstride,
-                                         int mx) {
+__device__ __forceinline__ void col_vpsi(cplx<float>* col, int stride, const float* v, int vstride, int mx) {
   const int R = 2 * mx + 1;
   cplx<float> x[N];
 #pragma unroll
@@ -289,7 +303,7 @@ __device__ __forceinline__ void col_vpsi(cplx<float>* col, int stride, const flo
 #pragma unroll
   for (int p = 0; p < N; ++p) {
     const int e = dif_freq<N>(p);
-    y[e] = scale(x[p], __ldg(v + e * vstride));
+    y[e] = scale(x[p], v[e * vstride]);
   }
   reg_fft<float, N, -1>(y, twf<N>());
 #pragma unroll
@@ -324,7 +338,7 @@ __global__ void __launch_bounds__(PLANE_REG_THREADS, MAXN <= 40 ? 2 : 1) k_plane
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
-  const int n1 = P.n1, n2 = P.n2, n3 = P.n3, mx = P.m1max, ncol = P.ncol;
+  const int n1 = P.n1, n2 = P.n2, n3 = P.n3, mx = P.m1max, ncol = P.ncol, n12 = n1 * n2;
   const int R = 2 * mx + 1, P2 = n2 | 1, plane = R * P2;
   const int Q = PLANE_REG_THREADS / n2;
   const int nzb = (n3 + Q - 1) / Q;
@@ -332,32 +346,33 @@ __global__ void __launch_bounds__(PLANE_REG_THREADS, MAXN <= 40 ? 2 : 1) k_plane
   const int pair = local / nzb, zb = local - pair * nzb;
   const int z0 = zb * Q, nq = min(Q, n3 - z0);
   cplx<float>* S = reinterpret_cast<cplx<float>*>(smem_raw);
+  float* Vs = reinterpret_cast<float*>(S + Q * plane);  // V_eff / N of the CTA's planes
   cplx<float>* wc = reinterpret_cast<cplx<float>*>(P.Wc) + ((size_t)pair * n3 + z0) * ncol;
+  const int* __restrict__ sidx = P.col_sidx;
   for (int t = threadIdx.x; t < nq * plane; t += blockDim.x) S[t] = mk(0.f, 0.f);
   __syncthreads();
-  for (int t = threadIdx.x; t < nq * ncol; t += blockDim.x) {
-    const int q = t / ncol, c = t - q * ncol;
-    const int xy = P.col_xy[c];
-    const int i1 = xy / n2, i2 = xy - i1 * n2;
-    S[q * plane + (i1 <= mx ? i1 : i1 - n1 + R) * P2 + i2] = wc[t];
-  }
+  // scatter of the compact columns (group 0), then the potential (group 1): asynchronous
+  // copies, the potential landing while the y pass runs
+  for (int q = 0; q < nq; ++q)
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) cp_async8(S + q * plane + sidx[c], wc + q * ncol + c);
+  cp_async_commit();
+  const float* veff = reinterpret_cast<const float*>(P.veff) + (size_t)z0 * n12;
+  for (int t = threadIdx.x; t < nq * n12; t += blockDim.x) cp_async4(Vs + t, veff + t);
+  cp_async_commit();
+  cp_async_wait<1>();
   __syncthreads();
   for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN, 1>(n2, S + l * P2);
+  cp_async_wait<0>();
   __syncthreads();
-  const float* veff = reinterpret_cast<const float*>(P.veff) + (size_t)z0 * n1 * n2;
   for (int l = threadIdx.x; l < nq * n2; l += blockDim.x) {
     const int q = l / n2, i2 = l - q * n2;
-    col_vpsi_n<MAXN>(n1, S + q * plane + i2, P2, veff + (size_t)q * n1 * n2 + i2, n2, mx);
+    col_vpsi_n<MAXN>(n1, S + q * plane + i2, P2, Vs + q * n12 + i2, n2, mx);
   }
   __syncthreads();
   for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN, -1>(n2, S + l * P2);
   __syncthreads();
-  for (int t = threadIdx.x; t < nq * ncol; t += blockDim.x) {
-    const int q = t / ncol, c = t - q * ncol;
-    const int xy = P.col_xy[c];
-    const int i1 = xy / n2, i2 = xy - i1 * n2;
-    wc[t] = S[q * plane + (i1 <= mx ? i1 : i1 - n1 + R) * P2 + i2];
-  }
+  for (int q = 0; q < nq; ++q)
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) wc[q * ncol + c] = S[q * plane + sidx[c]];
 }
 
 // ---------------------------------------------------------------------------
@@ -487,8 +502,9 @@ int plane_reg_ctas(int n2, int n3, int npair) {
   const int q = PLANE_REG_THREADS / n2;
   return npair * ((n3 + q - 1) / q);
 }
-size_t plane_reg_smem(int n2, int m1max) {
-  return (size_t)(PLANE_REG_THREADS / n2) * (2 * m1max + 1) * (n2 | 1) * sizeof(cplx<float>);
+size_t plane_reg_smem(int n1, int n2, int m1max) {
+  const size_t q = PLANE_REG_THREADS / n2;
+  return q * (2 * m1max + 1) * (n2 | 1) * sizeof(cplx<float>) + q * n1 * n2 * sizeof(float);
 }
 
 bool fft_reg_init() {

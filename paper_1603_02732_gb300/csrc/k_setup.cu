@@ -115,14 +115,19 @@ __global__ void k_basis_fill(KArgs ka) {
   // compact columns: pair 0 -> column 0; pair pr > 0 -> 2pr-1 (c+) and 2pr (c-)
   const int i1p = (m1 % P.n1 + P.n1) % P.n1, i2p = (m2 % P.n2 + P.n2) % P.n2;
   const int i1m = ((-m1) % P.n1 + P.n1) % P.n1, i2m = ((-m2) % P.n2 + P.n2) % P.n2;
+  const int rows = 2 * P.m1max + 1, p2 = P.n2 | 1;
+  auto sidx = [&](int i1, int i2) { return (i1 <= P.m1max ? i1 : i1 - P.n1 + rows) * p2 + i2; };
   if (pr == 0) {
     P.colmap[i1p * P.n2 + i2p] = 0;
     P.col_xy[0] = i1p * P.n2 + i2p;
+    P.col_sidx[0] = sidx(i1p, i2p);
   } else {
     P.colmap[i1p * P.n2 + i2p] = 2 * pr - 1;
     P.col_xy[2 * pr - 1] = i1p * P.n2 + i2p;
+    P.col_sidx[2 * pr - 1] = sidx(i1p, i2p);
     P.colmap[i1m * P.n2 + i2m] = 2 * pr;
     P.col_xy[2 * pr] = i1m * P.n2 + i2m;
+    P.col_sidx[2 * pr] = sidx(i1m, i2m);
   }
 }
 

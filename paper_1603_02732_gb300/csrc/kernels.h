@@ -55,7 +55,7 @@ void fft_set_smem_limits(size_t bytes);
 bool plane_reg_ok(int n1, int n2);
 int plane_reg_class(int n1, int n2);          // 0: both <= 40, 1: up to PLANE_REG_MAXN
 int plane_reg_ctas(int n2, int n3, int npair);
-size_t plane_reg_smem(int n2, int m1max);
+size_t plane_reg_smem(int n1, int n2, int m1max);
 bool fft_reg_init();                          // twiddle tables on the current device
 void launch_plane_vpsi_reg(const Launch& L, int cls, size_t smem);
 

@@ -140,6 +140,8 @@ struct Prob {
   double* gvec;                // [3][ld] Cartesian G per packed component (0 at G = 0 and padding)
   int* colmap;                 // [n1*n2] compact column or -1, index i1*n2 + i2
   int* col_xy;                 // [ncol] i1*n2 + i2
+  int* col_sidx;               // [ncol] rho(i1) * (n2 | 1) + i2: the column's slot in the register
+                               // plane kernel's compact rows (rho = i1, or i1 - n1 + 2 m1max + 1)
   int* bx_cnt;                 // [(2 box1+1)(2 box2+1)] setup scratch: entries per box column
   int* bx_m3max;               // same: max |m3| in the column
   int* bx_pair;                // same: column pair index or -1

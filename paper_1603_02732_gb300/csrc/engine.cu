@@ -114,6 +114,7 @@ void layout(sgo_ctx* c, A& a) {
   d.ent_m = a.template take<int>(3 * std::max(d.nhalf, 1));
   d.ent_m3 = d.ent_m + 2 * d.nhalf;
   d.ekin = a.template take<double>(ld);
+  d.ekin32 = a.template take<float>(ld);
   d.gvec = a.template take<double>(3 * (size_t)ld);
   d.colmap = a.template take<int>(n12);
   d.col_xy = a.template take<int>(d.ncol);
@@ -132,6 +133,7 @@ void layout(sgo_ctx* c, A& a) {
   d.rho_out = a.template take<double>(ng);
   d.resid = a.template take<double>(ng);
   d.vloc_g = a.template take<double>((size_t)d.nspecies * ng);
+  d.g2box = a.template take<double>(ng);
   d.gfft = a.template take<double2>(ng);
   d.gfft2 = a.template take<double2>(ng);
   d.rhog_in = a.template take<double2>(ng);
@@ -468,7 +470,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     }
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
-      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2];
+      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2], c_dreg[2];
   size_t part = 0;
   int max_natom = 0;
   for (int p = 0; p < n_; ++p) {
@@ -484,13 +486,20 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     const int nsplit = div_up(d.npw, TN_KC);
     const int tw = div_up(d.nb, TN_TILE), ta = div_up(d.natom, TN_TILE), td = div_up(3 * d.natom, TN_TILE);
     c_zcol.push_back(d.npair * div_up(d.ncp, QCP));
-    // plane pass: register FFTs on the mixed path where both plane lengths have one
-    const bool preg = precision_ == 1 && plane_reg_ok(d.n1, d.n2);
+    // plane passes: register FFTs on the mixed path where both plane lengths have one
+    // and the kernels' shared memory fits; the shared-memory engine otherwise
+    const size_t smem_cap = 220 * 1024;
+    const bool preg = precision_ == 1 && plane_reg_ok(d.n1, d.n2) && plane_reg_smem(d.n1, d.n2, d.m1max) <= smem_cap;
+    const bool dreg = preg && plane_density_reg_smem(d.n1, d.n2, d.m1max) <= smem_cap;
     const int pcls = preg ? plane_reg_class(d.n1, d.n2) : -1;
     c_plane.push_back(preg ? 0 : d.npair * d.n3);
-    for (int k = 0; k < 2; ++k) c_preg[k].push_back(pcls == k ? plane_reg_ctas(d.n2, d.n3, d.npair) : 0);
+    c_dens.push_back(dreg ? 0 : d.n3);
+    for (int k = 0; k < 2; ++k) {
+      c_preg[k].push_back(pcls == k ? plane_reg_ctas(d.n2, d.n3, d.npair) : 0);
+      c_dreg[k].push_back(dreg && pcls == k ? plane_density_reg_ctas(d.n2, d.n3) : 0);
+    }
     if (preg) preg_smem_[pcls] = std::max(preg_smem_[pcls], plane_reg_smem(d.n1, d.n2, d.m1max));
-    c_dens.push_back(d.n3);
+    if (dreg) dreg_smem_[pcls] = std::max(dreg_smem_[pcls], plane_density_reg_smem(d.n1, d.n2, d.m1max));
     c_gz.push_back(div_up(d.n1 * d.n2, QZ));
     c_gp.push_back(d.n3);
     c_gew.push_back(div_up(d.ngrid, GRID_EW_POINTS));
@@ -517,6 +526,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   m_zcol_ = make_map(c_zcol);
   m_plane_ = make_map(c_plane);
   for (int k = 0; k < 2; ++k) m_preg_[k] = make_map(c_preg[k]);
+  for (int k = 0; k < 2; ++k) m_dreg_[k] = make_map(c_dreg[k]);
   m_dens_ = make_map(c_dens);
   m_gz_ = make_map(c_gz);
   m_gp_ = make_map(c_gp);
@@ -874,6 +884,7 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     launch_wave_to_cols<T>(L(m_zcol_), WB_X);
     tbeg(TK_PLANE_DENSITY);
     launch_plane_density<T>(L(m_dens_), nullptr);
+    for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], nullptr);
     tend(TK_PLANE_DENSITY);
     // energy at (Psi, rho_out) and the convergence test
     launch_band_kinetic<T>(L(m_bands_), WB_X);
@@ -1007,6 +1018,7 @@ sgo_status Engine::density(int nvec, const double* psi, const double* occ, doubl
     launch_copy_in<float>(L(m_bands_), WB_W, dpsi, nvec);
     launch_wave_to_cols<float>(L(m_zcol_), WB_W);
     launch_plane_density<float>(L(m_dens_), docc);
+    for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], docc);
   } else {
     launch_copy_in<double>(L(m_bands_), WB_W, dpsi, nvec);
     launch_wave_to_cols<double>(L(m_zcol_), WB_W);

@@ -11,6 +11,10 @@
 // leaves registers and every twiddle is a constant-bank operand.  No scaling.
 #pragma once
 
+#include <cmath>
+#include <mutex>
+#include <vector>
+
 #include "fft.cuh"
 
 namespace sgo {
@@ -116,5 +120,79 @@ template <typename T, int N, int SIGN>
 __device__ __forceinline__ void reg_fft(cplx<T> (&x)[N], const cplx<T>* tab) {
   reg_dif<T, N, N, 0, SIGN>(x, tab, 0);
 }
+
+// ---------------------------------------------------------------------------
+// Line passes shared by the register plane kernels (one copy per translation unit).
+// ---------------------------------------------------------------------------
+namespace {
+
+
+// per length N: exp(-2 pi i t / N); one copy per translation unit, filled by upload_twiddles()
+__constant__ cplx<float> c_tw[reg_table_total()];
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ const cplx<float>* twf() {
+  return c_tw + reg_table_offset(N);
+}
+
+template <int N, int SIGN>
+__device__ __forceinline__ void row_fft(cplx<float>* row) {
+  cplx<float> x[N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) x[e] = row[e];
+  reg_fft<float, N, SIGN>(x, twf<N>());
+#pragma unroll
+  for (int p = 0; p < N; ++p) row[dif_freq<N>(p)] = x[p];
+}
+
+template <int MAXN, int SIGN>
+__device__ __forceinline__ void row_fft_n(int n, cplx<float>* row) {
+  switch (n) {
+#define SGO_ROW(N)                                 \
+  case N:                                          \
+    if constexpr (N <= MAXN) row_fft<N, SIGN>(row); \
+    break;
+    SGO_ROW(10) SGO_ROW(12) SGO_ROW(15) SGO_ROW(16) SGO_ROW(18) SGO_ROW(20) SGO_ROW(24) SGO_ROW(25) SGO_ROW(27)
+    SGO_ROW(30) SGO_ROW(32) SGO_ROW(36) SGO_ROW(40) SGO_ROW(45) SGO_ROW(48) SGO_ROW(50) SGO_ROW(54) SGO_ROW(60)
+    SGO_ROW(64) SGO_ROW(72)
+#undef SGO_ROW
+    default: break;
+  }
+}
+
+// Fill this translation unit's twiddle table on the current device (once per device).
+inline bool upload_twiddles() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return true;
+  std::vector<cplx<float>> h(reg_table_total());
+  for (int i = 0, o = 0; i < kRegCount; o += kRegSizes[i], ++i)
+    for (int t = 0; t < kRegSizes[i]; ++t) {
+      const double a = 2.0 * PI * t / kRegSizes[i];
+      h[o + t] = mk((float)std::cos(a), (float)(-std::sin(a)));
+    }
+  if (cudaMemcpyToSymbol(c_tw, h.data(), sizeof(cplx<float>) * h.size()) != cudaSuccess) return false;
+  done[dev] = true;
+  return true;
+}
+
+}  // namespace
 
 }  // namespace sgo

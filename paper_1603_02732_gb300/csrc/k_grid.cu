@@ -170,12 +170,9 @@ __global__ void k_veff(KArgs ka, const double* user_v) {
 __global__ void k_potential_g(KArgs ka) {
   GRID_EW_PROLOGUE
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
-    GPt q = grid_pt(P, i);
-    double G[3];
-    gcart(P, q.m1, q.m2, q.m3, G);
-    double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    const double g2 = P.g2box[i];  // -1 on Nyquist planes
     double2 r = P.rhog_in[i];
-    double f = (q.nyq || g2 < 1e-14) ? 0.0 : 4.0 * PI / g2;
+    double f = g2 < 1e-14 ? 0.0 : 4.0 * PI / g2;
     // (r.x + i r.y) + i f (r.x + i r.y)
     P.gfft[i] = make_double2(r.x - f * r.y, r.y + f * r.x);
   }
@@ -201,12 +198,10 @@ __global__ void k_rho0_g(KArgs ka) {
   GRID_EW_PROLOGUE
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
     int i1, i2, i3;
-    GPt q = grid_pt(P, i, &i1, &i2, &i3);
-    double G[3];
-    gcart(P, q.m1, q.m2, q.m3, G);
-    double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    grid_pt(P, i, &i1, &i2, &i3);
+    const double g2 = P.g2box[i];  // -1 on Nyquist planes
     cplx<double> acc = mk(0.0, 0.0);
-    if (!q.nyq && 0.5 * g2 <= 4.0 * P.ecut) {
+    if (g2 >= 0.0 && 0.5 * g2 <= 4.0 * P.ecut) {
       double amp[MAX_SPECIES];
       for (int s = 0; s < P.nspecies; ++s) {
         const double* sp = P.sp + s * 6;
@@ -243,15 +238,10 @@ __global__ void k_grid_energies(KArgs ka, double* part, int maxchunk) {
     s[1] += fmax(r, 0.0) * (double)exc;
     s[2] += r;
     s[3] += fabs(r - P.rho_in[i]);
-    GPt q = grid_pt(P, i);
-    if (!q.nyq) {
-      double G[3];
-      gcart(P, q.m1, q.m2, q.m3, G);
-      double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
-      if (g2 > 1e-14) {
-        double2 v = P.gfft2[i];
-        s[4] += (v.x * v.x + v.y * v.y) * inv_n * inv_n / g2;
-      }
+    const double g2 = P.g2box[i];  // -1 on Nyquist planes
+    if (g2 > 1e-14) {
+      double2 v = P.gfft2[i];
+      s[4] += (v.x * v.x + v.y * v.y) * inv_n * inv_n / g2;
     }
   }
   for (int k = 0; k < NGE; ++k) {
@@ -421,7 +411,7 @@ __global__ void k_pulay_mix(KArgs ka, double a, double q0) {
   const double* alpha = P.scal + SC_PULAY_A + MAX_HIST * MAX_HIST;
   const int cnt = (int)P.scal[SC_PULAY_N];
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
-    GPt q = grid_pt(P, i);
+    const double g2 = P.g2box[i];  // -1 on Nyquist planes
     double rx = 0.0, ry = 0.0, sx = 0.0, sy = 0.0;
     for (int j = 0; j < cnt; ++j) {
       const double2 h = P.hrho[(size_t)j * P.ngrid + i], r = P.hres[(size_t)j * P.ngrid + i];
@@ -431,13 +421,8 @@ __global__ void k_pulay_mix(KArgs ka, double a, double q0) {
       sy += alpha[j] * r.y;
     }
     double k = 1.0;
-    if (q0 > 0.0) {
-      double G[3];
-      gcart(P, q.m1, q.m2, q.m3, G);
-      double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
-      k = g2 < 1e-14 ? 0.0 : g2 / (g2 + q0 * q0);
-    }
-    if (q.nyq) k = 0.0, rx = ry = 0.0;
+    if (q0 > 0.0) k = g2 < 1e-14 ? 0.0 : g2 / (g2 + q0 * q0);
+    if (g2 < 0.0) k = 0.0, rx = ry = 0.0;
     P.rhog_in[i] = make_double2(rx + a * k * sx, ry + a * k * sy);
   }
 }

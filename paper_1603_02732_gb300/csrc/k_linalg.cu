@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(BAND_THREADS) k_band_kinetic(KArgs ka, int xr)
   const int i = blockIdx.x - ka.start[p];
   const T* x = wbuf<T>(P, xr) + (size_t)i * P.ld;
   T st = T(0);
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) st += T(P.ekin[k]) * x[k] * x[k];
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) st += ekin_at<T>(P, k) * x[k] * x[k];
   const double s = block_sum((double)st, red);
   if (threadIdx.x == 0) P.bv[BV_EKIN * P.nb + i] = s;
 }
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, i
   const T* rp = wbuf<T>(P, rpr) + off;
   const bool first = P.scal[SC_FIRSTCG] != 0.0;
   T ekp = T(0);
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) ekp += T(P.ekin[k]) * x[k] * x[k];
+  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) ekp += ekin_at<T>(P, k) * x[k] * x[k];
   double ek = block_sum((double)ekp, red);
   ek = fmax(ek, 1e-3);
   const T eps = T(P.eps[i]);
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, i
   T grt = T(0), grpt = T(0), r2t = T(0);
   for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
     T r = hx[k] - eps * x[k];
-    T g = tpa<T>(T(P.ekin[k]) * iek) * r;
+    T g = tpa<T>(ekin_at<T>(P, k) * iek) * r;
     grt += g * r;
     r2t += r * r;
     if (!first) grpt += g * rp[k];

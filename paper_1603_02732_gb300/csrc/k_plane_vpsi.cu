@@ -1,0 +1,132 @@
+// Register-FFT plane pass of H.psi (mixed path, line lengths with a register transform;
+// the line transforms are in fft_reg.cuh).
+// CTA = (problem, band pair, block of Q = blockDim / N2 z-planes).  Shared memory holds
+// only the occupied x rows of each plane (|m1| <= m1max, compact row index rho), rows
+// padded to an odd length (N2 | 1) so that a thread per row and a thread per column
+// both touch 16 distinct 8-byte bank pairs per half warp, and the planes' V_eff / N.
+// Passes: scatter the compact columns (asynchronous copies to precomputed slots, the
+// potential following); y inverse (thread per occupied row); per column: x inverse of
+// the occupied rows, times V_eff/N, x forward, occupied rows back (thread per column,
+// the full column in registers); y forward; gather the compact columns.
+#include "fft_reg.cuh"
+#include "kernels.h"
+
+namespace sgo {
+
+namespace {
+
+// Column of N elements (x direction) at col[rho * stride]: occupied rows e <= mx and
+// e >= N - mx sit at rho = e resp. e - N + 2 mx + 1, the others are zero.
+template <int N>
+__device__ __forceinline__ void col_vpsi(cplx<float>* col, int stride, const float* v, int vstride, int mx) {
+  const int R = 2 * mx + 1;
+  cplx<float> x[N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) {
+    const bool lo = e <= mx, hi = e >= N - mx;
+    x[e] = (lo || hi) ? col[(lo ? e : e - N + R) * stride] : mk(0.f, 0.f);
+  }
+  reg_fft<float, N, 1>(x, twf<N>());
+  cplx<float> y[N];  // back to natural order (a renaming of registers)
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    const int e = dif_freq<N>(p);
+    y[e] = scale(x[p], v[e * vstride]);
+  }
+  reg_fft<float, N, -1>(y, twf<N>());
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    const int e = dif_freq<N>(p);
+    const bool lo = e <= mx, hi = e >= N - mx;
+    if (lo || hi) col[(lo ? e : e - N + R) * stride] = y[p];
+  }
+}
+
+template <int MAXN>
+__device__ __forceinline__ void col_vpsi_n(int n, cplx<float>* col, int stride, const float* v, int vstride,
+                                           int mx) {
+  switch (n) {
+#define SGO_COL(N)                                                     \
+  case N:                                                              \
+    if constexpr (N <= MAXN) col_vpsi<N>(col, stride, v, vstride, mx); \
+    break;
+    SGO_COL(10) SGO_COL(12) SGO_COL(15) SGO_COL(16) SGO_COL(18) SGO_COL(20) SGO_COL(24) SGO_COL(25) SGO_COL(27)
+    SGO_COL(30) SGO_COL(32) SGO_COL(36) SGO_COL(40) SGO_COL(45) SGO_COL(48) SGO_COL(50) SGO_COL(54) SGO_COL(60)
+    SGO_COL(64) SGO_COL(72)
+#undef SGO_COL
+    default: break;
+  }
+}
+
+}  // namespace
+
+template <int MAXN>
+__global__ void __launch_bounds__(PLANE_REG_THREADS, MAXN <= 40 ? 2 : 1) k_plane_vpsi_reg(KArgs ka) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int n1 = P.n1, n2 = P.n2, n3 = P.n3, mx = P.m1max, ncol = P.ncol, n12 = n1 * n2;
+  const int R = 2 * mx + 1, P2 = n2 | 1, plane = R * P2;
+  const int Q = PLANE_REG_THREADS / n2;
+  const int nzb = (n3 + Q - 1) / Q;
+  const int local = blockIdx.x - ka.start[p];
+  const int pair = local / nzb, zb = local - pair * nzb;
+  const int z0 = zb * Q, nq = min(Q, n3 - z0);
+  cplx<float>* S = reinterpret_cast<cplx<float>*>(smem_raw);
+  float* Vs = reinterpret_cast<float*>(S + Q * plane);  // V_eff / N of the CTA's planes
+  cplx<float>* wc = reinterpret_cast<cplx<float>*>(P.Wc) + ((size_t)pair * n3 + z0) * ncol;
+  const int* __restrict__ sidx = P.col_sidx;
+  for (int t = threadIdx.x; t < nq * plane; t += blockDim.x) S[t] = mk(0.f, 0.f);
+  __syncthreads();
+  // scatter of the compact columns (group 0), then the potential (group 1): asynchronous
+  // copies, the potential landing while the y pass runs
+  for (int q = 0; q < nq; ++q)
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) cp_async8(S + q * plane + sidx[c], wc + q * ncol + c);
+  cp_async_commit();
+  const float* veff = reinterpret_cast<const float*>(P.veff) + (size_t)z0 * n12;
+  for (int t = threadIdx.x; t < nq * n12; t += blockDim.x) cp_async4(Vs + t, veff + t);
+  cp_async_commit();
+  cp_async_wait<1>();
+  __syncthreads();
+  for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN, 1>(n2, S + l * P2);
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int l = threadIdx.x; l < nq * n2; l += blockDim.x) {
+    const int q = l / n2, i2 = l - q * n2;
+    col_vpsi_n<MAXN>(n1, S + q * plane + i2, P2, Vs + q * n12 + i2, n2, mx);
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN, -1>(n2, S + l * P2);
+  __syncthreads();
+  for (int q = 0; q < nq; ++q)
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) wc[q * ncol + c] = S[q * plane + sidx[c]];
+}
+
+bool plane_reg_ok(int n1, int n2) {
+  return reg_supported(n1) && reg_supported(n2) && n1 <= PLANE_REG_MAXN && n2 <= PLANE_REG_MAXN;
+}
+int plane_reg_class(int n1, int n2) { return (n1 <= 40 && n2 <= 40) ? 0 : 1; }
+int plane_reg_ctas(int n2, int n3, int npair) {
+  const int q = PLANE_REG_THREADS / n2;
+  return npair * ((n3 + q - 1) / q);
+}
+size_t plane_reg_smem(int n1, int n2, int m1max) {
+  const size_t q = PLANE_REG_THREADS / n2;
+  return q * (2 * m1max + 1) * (n2 | 1) * sizeof(cplx<float>) + q * n1 * n2 * sizeof(float);
+}
+
+void launch_plane_vpsi_reg(const Launch& L, int cls, size_t smem) {
+  if (!L.map.total) return;
+  if (cls == 0) k_plane_vpsi_reg<40><<<L.map.total, PLANE_REG_THREADS, smem, L.stream>>>(L.ka);
+  else k_plane_vpsi_reg<PLANE_REG_MAXN><<<L.map.total, PLANE_REG_THREADS, smem, L.stream>>>(L.ka);
+}
+
+bool plane_vpsi_reg_init() { return upload_twiddles(); }
+
+void plane_vpsi_reg_set_smem_limits(size_t bytes) {
+  cudaFuncSetAttribute(k_plane_vpsi_reg<40>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_plane_vpsi_reg<PLANE_REG_MAXN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace sgo

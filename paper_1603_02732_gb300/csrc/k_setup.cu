@@ -83,6 +83,7 @@ __global__ void k_basis_fill(KArgs ka) {
   if (q == 0) {
     P.cp_off[P.ncp] = P.nhalf;
     P.ekin[0] = 0.0;
+    P.ekin32[0] = 0.f;
     for (int c = 0; c < 3; ++c) P.gvec[(size_t)c * P.ld] = 0.0;
   }
   if (q >= (2 * P.box1 + 1) * w2) return;
@@ -106,6 +107,8 @@ __global__ void k_basis_fill(KArgs ka) {
     P.ent_m[2 * P.nhalf + e] = m3;
     P.ekin[1 + 2 * e] = 0.5 * g2;
     P.ekin[2 + 2 * e] = 0.5 * g2;
+    P.ekin32[1 + 2 * e] = (float)(0.5 * g2);
+    P.ekin32[2 + 2 * e] = (float)(0.5 * g2);
     for (int c = 0; c < 3; ++c) {
       P.gvec[(size_t)c * P.ld + 1 + 2 * e] = G[c];
       P.gvec[(size_t)c * P.ld + 2 + 2 * e] = G[c];
@@ -194,6 +197,7 @@ __global__ void k_vloc_table(KArgs ka) {
     int m2 = i2 < (P.n2 + 1) / 2 ? i2 : i2 - P.n2;
     int m3 = i3 < (P.n3 + 1) / 2 ? i3 : i3 - P.n3;
     double g2 = g2_of(P, m1, m2, m3);
+    P.g2box[i] = nyq ? -1.0 : g2;
     for (int s = 0; s < P.nspecies; ++s) {
       const double* sp = P.sp + s * 6;
       double Z = sp[0], rc = sp[1], A = sp[2], sg = sp[3];

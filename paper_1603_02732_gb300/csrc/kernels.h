@@ -57,7 +57,14 @@ int plane_reg_class(int n1, int n2);          // 0: both <= 40, 1: up to PLANE_R
 int plane_reg_ctas(int n2, int n3, int npair);
 size_t plane_reg_smem(int n1, int n2, int m1max);
 bool fft_reg_init();                          // twiddle tables on the current device
+bool plane_vpsi_reg_init();
+bool plane_density_reg_init();
+void plane_vpsi_reg_set_smem_limits(size_t bytes);
+void plane_density_reg_set_smem_limits(size_t bytes);
 void launch_plane_vpsi_reg(const Launch& L, int cls, size_t smem);
+size_t plane_density_reg_smem(int n1, int n2, int m1max);
+int plane_density_reg_ctas(int n2, int n3);
+void launch_plane_density_reg(const Launch& L, int cls, size_t smem, const double* occ_override);
 
 // k_linalg.cu
 template <typename T>

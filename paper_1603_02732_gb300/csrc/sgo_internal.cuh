@@ -137,6 +137,7 @@ struct Prob {
   int* ent_m;                  // [3][nhalf] Miller indices of the half-sphere entries
   int* ent_m3;                 // = ent_m + 2*nhalf
   double* ekin;                // [ld] |G|^2/2 per packed component (0 in padding)
+  float* ekin32;               // [ld] the same in single precision (mixed-path kernels)
   double* gvec;                // [3][ld] Cartesian G per packed component (0 at G = 0 and padding)
   int* colmap;                 // [n1*n2] compact column or -1, index i1*n2 + i2
   int* col_xy;                 // [ncol] i1*n2 + i2
@@ -165,6 +166,7 @@ struct Prob {
   // FP64 grids
   double* vion_r;              // [ngrid]
   double* vloc_g;              // [nspecies][ngrid] v_s(G) on the box (Nyquist zeroed)
+  double* g2box;               // [ngrid] |G|^2 on the box, -1 on Nyquist planes
   double* rho_in;              // [ngrid]
   double* rho_out;             // [ngrid]
   double* resid;               // [ngrid]
@@ -195,6 +197,19 @@ struct Prob {
   double2* ew_sg;              // [(2ng1+1)(2ng2+1)(2ng3+1)] S(G)
   double* ew_part;             // [natom] real-space energy per atom, then recip chunks
 };
+
+// |G|^2/2 of packed component k in the working precision (no FP64 load or conversion on
+// the mixed path)
+template <typename T>
+__device__ __forceinline__ T ekin_at(const Prob& P, int k);
+template <>
+__device__ __forceinline__ float ekin_at<float>(const Prob& P, int k) {
+  return P.ekin32[k];
+}
+template <>
+__device__ __forceinline__ double ekin_at<double>(const Prob& P, int k) {
+  return P.ekin[k];
+}
 
 template <typename T>
 __device__ __forceinline__ T* wbuf(const Prob& P, int role) {

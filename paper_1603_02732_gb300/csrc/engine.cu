@@ -113,6 +113,7 @@ void layout(sgo_ctx* c, A& a) {
   d.cp_m2 = a.template take<int>(d.ncp);
   d.ent_m = a.template take<int>(3 * std::max(d.nhalf, 1));
   d.ent_m3 = d.ent_m + 2 * d.nhalf;
+  d.ent_cp = a.template take<int>(std::max(d.nhalf, 1));
   d.ekin = a.template take<double>(ld);
   d.ekin32 = a.template take<float>(ld);
   d.gvec = a.template take<double>(3 * (size_t)ld);
@@ -470,7 +471,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     }
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
-      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2], c_dreg[2];
+      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2], c_dreg[2], c_zreg[2];
   size_t part = 0;
   int max_natom = 0;
   for (int p = 0; p < n_; ++p) {
@@ -485,7 +486,11 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     maxchunk_ = std::max(maxchunk_, nch);
     const int nsplit = div_up(d.npw, TN_KC);
     const int tw = div_up(d.nb, TN_TILE), ta = div_up(d.natom, TN_TILE), td = div_up(3 * d.natom, TN_TILE);
-    c_zcol.push_back(d.npair * div_up(d.ncp, QCP));
+    // z-column passes: register FFTs on the mixed path where n3 has one
+    const bool zreg = precision_ == 1 && zreg_ok(d.n3);
+    c_zcol.push_back(zreg ? 0 : d.npair * div_up(d.ncp, QCP));
+    for (int k = 0; k < 2; ++k) c_zreg[k].push_back(zreg && zreg_class(d.n3) == k ? zreg_ctas(d.ncp, d.npair) : 0);
+    if (zreg) zreg_smem_[zreg_class(d.n3)] = std::max(zreg_smem_[zreg_class(d.n3)], zreg_smem(d.n3));
     // plane passes: register FFTs on the mixed path where both plane lengths have one
     // and the kernels' shared memory fits; the shared-memory engine otherwise
     const size_t smem_cap = 220 * 1024;
@@ -527,6 +532,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   m_plane_ = make_map(c_plane);
   for (int k = 0; k < 2; ++k) m_preg_[k] = make_map(c_preg[k]);
   for (int k = 0; k < 2; ++k) m_dreg_[k] = make_map(c_dreg[k]);
+  for (int k = 0; k < 2; ++k) m_zreg_[k] = make_map(c_zreg[k]);
   m_dens_ = make_map(c_dens);
   m_gz_ = make_map(c_gz);
   m_gp_ = make_map(c_gp);
@@ -766,18 +772,34 @@ void Engine::rotate(int role, bool image_ready) {
   swap_roles(role, WB_W);
 }
 
+// z-column passes: shared-memory engine for the members without a register transform of
+// n3 (or on the FP64 path), register kernels for the others.
+template <typename T>
+void Engine::wave_to_cols(int src) {
+  launch_wave_to_cols<T>(L(m_zcol_), src);
+  if (sizeof(T) == 4)
+    for (int k = 0; k < 2; ++k) launch_wave_to_cols_reg(L(m_zreg_[k]), k, zreg_smem_[k], src);
+}
+
+template <typename T>
+void Engine::cols_to_wave(int src, int dst) {
+  launch_cols_to_wave<T>(L(m_zcol_), src, dst);
+  if (sizeof(T) == 4)
+    for (int k = 0; k < 2; ++k) launch_cols_to_wave_reg(L(m_zreg_[k]), k, zreg_smem_[k], src, dst);
+}
+
 // H applied to every band of src: FFT local + kinetic, then nonlocal B (D o B^T src).
 template <typename T>
 void Engine::hpsi(int src, int dst) {
   tbeg(TK_WAVE_TO_COLS);
-  launch_wave_to_cols<T>(L(m_zcol_), src);
+  wave_to_cols<T>(src);
   tend(TK_WAVE_TO_COLS);
   tbeg(TK_PLANE_VPSI);
   launch_plane_vpsi<T>(L(m_plane_));
   for (int k = 0; k < 2; ++k) launch_plane_vpsi_reg(L(m_preg_[k]), k, preg_smem_[k]);
   tend(TK_PLANE_VPSI);
   tbeg(TK_COLS_TO_WAVE);
-  launch_cols_to_wave<T>(L(m_zcol_), src, dst);
+  cols_to_wave<T>(src, dst);
   tend(TK_COLS_TO_WAVE);
   tn<T>(OPK_B, 0, OPK_WB, src, DD_PROJ);
   nn<T>(OPK_B, 0, DD_PROJ_D, dst, 1.0, 1.0);
@@ -881,7 +903,7 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     for (int k = 0; k < ncg; ++k) cg_step<T>();
     // occupations and rho_out
     launch_occupations(L(m_prob_));
-    launch_wave_to_cols<T>(L(m_zcol_), WB_X);
+    wave_to_cols<T>(WB_X);
     tbeg(TK_PLANE_DENSITY);
     launch_plane_density<T>(L(m_dens_), nullptr);
     for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], nullptr);
@@ -1016,12 +1038,12 @@ sgo_status Engine::density(int nvec, const double* psi, const double* occ, doubl
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   if (precision_) {
     launch_copy_in<float>(L(m_bands_), WB_W, dpsi, nvec);
-    launch_wave_to_cols<float>(L(m_zcol_), WB_W);
+    wave_to_cols<float>(WB_W);
     launch_plane_density<float>(L(m_dens_), docc);
     for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], docc);
   } else {
     launch_copy_in<double>(L(m_bands_), WB_W, dpsi, nvec);
-    launch_wave_to_cols<double>(L(m_zcol_), WB_W);
+    wave_to_cols<double>(WB_W);
     launch_plane_density<double>(L(m_dens_), docc);
   }
   launch_export_grid(L(m_gew_), 1, dr);

@@ -125,8 +125,10 @@ class Engine {
   int max_n1_ = 0, max_n2_ = 0, max_n3_ = 0, max_n12_ = 0, max_nb_ = 0, plane_threads_ = 128;
   WorkMap m_zcol_, m_plane_, m_dens_, m_gz_, m_gp_, m_gew_, m_gch_, m_bands_, m_tn_ww_, m_tn_bw_, m_tn_dw_,
       m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_atomch_, m_ewsg_, m_prob_, m_tc_, m_nntc_;
-  WorkMap m_preg_[2], m_dreg_[2];              // register-FFT plane kernels, per size class
-  size_t preg_smem_[2] = {0, 0}, dreg_smem_[2] = {0, 0};
+  WorkMap m_preg_[2], m_dreg_[2], m_zreg_[2];  // register-FFT plane / column kernels, per size class
+  size_t preg_smem_[2] = {0, 0}, dreg_smem_[2] = {0, 0}, zreg_smem_[2] = {0, 0};
+  template <typename T> void wave_to_cols(int src);
+  template <typename T> void cols_to_wave(int src, int dst);
   bool tc_ok_[3] = {false, false, false};      // TN on tcgen05, per A-operand kind
   bool nn_tc_ok_[3] = {false, false, false};   // NN on tcgen05, per X-operand kind
   void* d_tmaps_ = nullptr;                    // [n][TC_NSLOT][TC_NMAPKIND] tensor maps

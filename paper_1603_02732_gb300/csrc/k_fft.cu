@@ -359,7 +359,7 @@ void launch_grid_z_fft(const Launch& L, int which, int sign) {
   k_grid_z_fft<<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, which, sign);
 }
 
-bool fft_reg_init() { return plane_vpsi_reg_init() && plane_density_reg_init(); }
+bool fft_reg_init() { return plane_vpsi_reg_init() && plane_density_reg_init() && zreg_init(); }
 
 void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_wave_to_cols<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -374,6 +374,7 @@ void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_grid_z_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   plane_vpsi_reg_set_smem_limits(bytes);
   plane_density_reg_set_smem_limits(bytes);
+  zreg_set_smem_limits(bytes);
 }
 
 template void launch_wave_to_cols<float>(const Launch&, int);

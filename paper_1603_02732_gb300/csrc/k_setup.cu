@@ -105,6 +105,7 @@ __global__ void k_basis_fill(KArgs ka) {
     P.ent_m[e] = m1;
     P.ent_m[P.nhalf + e] = m2;
     P.ent_m[2 * P.nhalf + e] = m3;
+    P.ent_cp[e] = pr;
     P.ekin[1 + 2 * e] = 0.5 * g2;
     P.ekin[2 + 2 * e] = 0.5 * g2;
     P.ekin32[1 + 2 * e] = (float)(0.5 * g2);

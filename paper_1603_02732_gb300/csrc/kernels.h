@@ -13,7 +13,9 @@ constexpr int PLANE_THREADS = 256;      // threads of the z-plane kernels
 constexpr int PLANE_MIN_BLOCKS = 4;     // register cap (64) for 4+ resident CTAs per SM
 constexpr int PLANE_THREADS_MAX = PLANE_THREADS;
 constexpr int PLANE_REG_THREADS = 256;  // register-FFT plane kernel (mixed path)
-constexpr int PLANE_REG_MAXN = 72;      // longest x / y line it transforms
+constexpr int PLANE_REG_MAXN = 72;      // longest x / y / z line it transforms
+constexpr int ZREG_CP = 64;             // column pairs per register z-column CTA
+constexpr int ZREG_THREADS = 2 * ZREG_CP;
 // GEMM geometry
 constexpr int TN_TILE = 64;
 constexpr int TN_KC = 256;             // K chunk of one split-K partial (CUDA-core GEMM)
@@ -61,6 +63,15 @@ bool plane_vpsi_reg_init();
 bool plane_density_reg_init();
 void plane_vpsi_reg_set_smem_limits(size_t bytes);
 void plane_density_reg_set_smem_limits(size_t bytes);
+// register-FFT z-column passes (mixed path), k_cols_reg.cu
+int zreg_class(int n3);
+bool zreg_ok(int n3);
+int zreg_ctas(int ncp, int npair);
+size_t zreg_smem(int n3);
+void launch_wave_to_cols_reg(const Launch& L, int cls, size_t smem, int src);
+void launch_cols_to_wave_reg(const Launch& L, int cls, size_t smem, int src, int dst);
+bool zreg_init();
+void zreg_set_smem_limits(size_t bytes);
 void launch_plane_vpsi_reg(const Launch& L, int cls, size_t smem);
 size_t plane_density_reg_smem(int n1, int n2, int m1max);
 int plane_density_reg_ctas(int n2, int n3);

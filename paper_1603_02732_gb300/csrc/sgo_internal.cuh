@@ -136,6 +136,7 @@ struct Prob {
   int* cp_m2;                  // [ncp]
   int* ent_m;                  // [3][nhalf] Miller indices of the half-sphere entries
   int* ent_m3;                 // = ent_m + 2*nhalf
+  int* ent_cp;                 // [nhalf] column pair of each half-sphere entry
   double* ekin;                // [ld] |G|^2/2 per packed component (0 in padding)
   float* ekin32;               // [ld] the same in single precision (mixed-path kernels)
   double* gvec;                // [3][ld] Cartesian G per packed component (0 at G = 0 and padding)

@@ -149,22 +149,25 @@ __device__ __forceinline__ const cplx<float>* twf() {
   return c_tw + reg_table_offset(N);
 }
 
-template <int N, int SIGN>
-__device__ __forceinline__ void row_fft(cplx<float>* row) {
+// One row of length N in place: the inverse transform, or (fwd) the forward one computed
+// as conj(inverse(conj(.))), so that both directions run the same code body.
+template <int N>
+__device__ __forceinline__ void row_fft(cplx<float>* row, bool fwd) {
+  const float s = fwd ? -1.f : 1.f;
   cplx<float> x[N];
 #pragma unroll
-  for (int e = 0; e < N; ++e) x[e] = row[e];
-  reg_fft<float, N, SIGN>(x, twf<N>());
+  for (int e = 0; e < N; ++e) x[e] = mk(row[e].x, s * row[e].y);
+  reg_fft<float, N, 1>(x, twf<N>());
 #pragma unroll
-  for (int p = 0; p < N; ++p) row[dif_freq<N>(p)] = x[p];
+  for (int p = 0; p < N; ++p) row[dif_freq<N>(p)] = mk(x[p].x, s * x[p].y);
 }
 
-template <int MAXN, int SIGN>
-__device__ __forceinline__ void row_fft_n(int n, cplx<float>* row) {
+template <int MAXN>
+__device__ __forceinline__ void row_fft_n(int n, cplx<float>* row, bool fwd) {
   switch (n) {
-#define SGO_ROW(N)                                 \
-  case N:                                          \
-    if constexpr (N <= MAXN) row_fft<N, SIGN>(row); \
+#define SGO_ROW(N)                                  \
+  case N:                                           \
+    if constexpr (N <= MAXN) row_fft<N>(row, fwd);  \
     break;
     SGO_ROW(10) SGO_ROW(12) SGO_ROW(15) SGO_ROW(16) SGO_ROW(18) SGO_ROW(20) SGO_ROW(24) SGO_ROW(25) SGO_ROW(27)
     SGO_ROW(30) SGO_ROW(32) SGO_ROW(36) SGO_ROW(40) SGO_ROW(45) SGO_ROW(48) SGO_ROW(50) SGO_ROW(54) SGO_ROW(60)

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(PLANE_REG_THREADS, 1) k_plane_density_reg(KArg
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN, 1>(n2, S + l * P2);
+    for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN>(n2, S + l * P2, false);
     __syncthreads();
     for (int l = threadIdx.x; l < nq * n2; l += blockDim.x) {
       const int q = l / n2, i2 = l - q * n2;

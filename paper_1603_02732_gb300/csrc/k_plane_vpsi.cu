@@ -16,7 +16,10 @@ namespace sgo {
 namespace {
 
 // Column of N elements (x direction) at col[rho * stride]: occupied rows e <= mx and
-// e >= N - mx sit at rho = e resp. e - N + 2 mx + 1, the others are zero.
+// e >= N - mx sit at rho = e resp. e - N + 2 mx + 1, the others are zero.  Inverse
+// transform, times v, forward transform, the forward one computed as
+// conj(inverse(conj(.))): one transform body runs twice (a loop that is not unrolled),
+// which halves the code the warps stream through.
 template <int N>
 __device__ __forceinline__ void col_vpsi(cplx<float>* col, int stride, const float* v, int vstride, int mx) {
   const int R = 2 * mx + 1;
@@ -26,19 +29,23 @@ __device__ __forceinline__ void col_vpsi(cplx<float>* col, int stride, const flo
     const bool lo = e <= mx, hi = e >= N - mx;
     x[e] = (lo || hi) ? col[(lo ? e : e - N + R) * stride] : mk(0.f, 0.f);
   }
-  reg_fft<float, N, 1>(x, twf<N>());
-  cplx<float> y[N];  // back to natural order (a renaming of registers)
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    reg_fft<float, N, 1>(x, twf<N>());
+    cplx<float> y[N];  // natural order, conjugated (pass 0: times v)
 #pragma unroll
-  for (int p = 0; p < N; ++p) {
-    const int e = dif_freq<N>(p);
-    y[e] = scale(x[p], v[e * vstride]);
+    for (int p = 0; p < N; ++p) {
+      const int e = dif_freq<N>(p);
+      const float f = pass == 0 ? v[e * vstride] : 1.f;
+      y[e] = mk(f * x[p].x, -f * x[p].y);
+    }
+#pragma unroll
+    for (int e = 0; e < N; ++e) x[e] = y[e];
   }
-  reg_fft<float, N, -1>(y, twf<N>());
 #pragma unroll
-  for (int p = 0; p < N; ++p) {
-    const int e = dif_freq<N>(p);
+  for (int e = 0; e < N; ++e) {
     const bool lo = e <= mx, hi = e >= N - mx;
-    if (lo || hi) col[(lo ? e : e - N + R) * stride] = y[p];
+    if (lo || hi) col[(lo ? e : e - N + R) * stride] = x[e];
   }
 }
 
@@ -89,16 +96,19 @@ __global__ void __launch_bounds__(PLANE_REG_THREADS, MAXN <= 40 ? 2 : 1) k_plane
   cp_async_commit();
   cp_async_wait<1>();
   __syncthreads();
-  for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN, 1>(n2, S + l * P2);
-  cp_async_wait<0>();
-  __syncthreads();
-  for (int l = threadIdx.x; l < nq * n2; l += blockDim.x) {
-    const int q = l / n2, i2 = l - q * n2;
-    col_vpsi_n<MAXN>(n1, S + q * plane + i2, P2, Vs + q * n12 + i2, n2, mx);
+  // y inverse, x pass, y forward; both y directions through one row-transform body
+#pragma unroll 1
+  for (int ph = 0; ph < 2; ++ph) {
+    for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN>(n2, S + l * P2, ph == 1);
+    if (ph == 0) cp_async_wait<0>();
+    __syncthreads();
+    if (ph == 1) break;
+    for (int l = threadIdx.x; l < nq * n2; l += blockDim.x) {
+      const int q = l / n2, i2 = l - q * n2;
+      col_vpsi_n<MAXN>(n1, S + q * plane + i2, P2, Vs + q * n12 + i2, n2, mx);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN, -1>(n2, S + l * P2);
-  __syncthreads();
   for (int q = 0; q < nq; ++q)
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) wc[q * ncol + c] = S[q * plane + sidx[c]];
 }

@@ -232,16 +232,45 @@ __global__ void __launch_bounds__(256) k_gemm_nn(KArgs ka, int akind, int arole,
 // ---------------------------------------------------------------------------
 // per-band kernels: CTA = (problem, band)
 // ---------------------------------------------------------------------------
+// Per-band kernels stream a band's ld components as 16-byte packs (4 FP32 or 2 FP64).
+// Components npw .. ld-1 of every band buffer and of the kinetic tables are zero (the
+// arena is cleared at set-up and every writer stores zeros or only k < npw there), so
+// they add nothing to the sums and stay zero.
+template <typename T>
+struct alignas(16) Pack16 {
+  static constexpr int W = 16 / sizeof(T);
+  T e[W];
+};
+
+template <typename T>
+__device__ __forceinline__ const Pack16<T>* pk(const T* p) {
+  return reinterpret_cast<const Pack16<T>*>(p);
+}
+template <typename T>
+__device__ __forceinline__ Pack16<T>* pk(T* p) {
+  return reinterpret_cast<Pack16<T>*>(p);
+}
+template <typename T>
+__device__ __forceinline__ const Pack16<T>* ekin_pk(const Prob& P) {
+  return reinterpret_cast<const Pack16<T>*>(sizeof(T) == 4 ? (const void*)P.ekin32 : (const void*)P.ekin);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BAND_THREADS) k_band_kinetic(KArgs ka, int xr) {
   __shared__ double red[33];
+  constexpr int W = Pack16<T>::W;
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
-  const T* x = wbuf<T>(P, xr) + (size_t)i * P.ld;
+  const Pack16<T>* x = pk(wbuf<T>(P, xr) + (size_t)i * P.ld);
+  const Pack16<T>* ek = ekin_pk<T>(P);
   T st = T(0);
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) st += ekin_at<T>(P, k) * x[k] * x[k];
+  for (int v = threadIdx.x; v < P.ld / W; v += blockDim.x) {
+    const Pack16<T> a = x[v], g = ek[v];
+#pragma unroll
+    for (int j = 0; j < W; ++j) st += g.e[j] * a.e[j] * a.e[j];
+  }
   const double s = block_sum((double)st, red);
   if (threadIdx.x == 0) P.bv[BV_EKIN * P.nb + i] = s;
 }
@@ -260,33 +289,49 @@ __device__ __forceinline__ T tpa(T y) {
 template <typename T>
 __global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, int hxr, int pr, int rr_out, int ppr, int rpr) {
   __shared__ double red[33];
+  constexpr int W = Pack16<T>::W;
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
   const size_t off = (size_t)i * P.ld;
-  const T* x = wbuf<T>(P, xr) + off;
-  const T* hx = wbuf<T>(P, hxr) + off;
-  T* pv = wbuf<T>(P, pr) + off;
-  T* rv = wbuf<T>(P, rr_out) + off;
-  const T* pp = wbuf<T>(P, ppr) + off;
-  const T* rp = wbuf<T>(P, rpr) + off;
+  const int nv = P.ld / W;
+  const Pack16<T>* x = pk(wbuf<T>(P, xr) + off);
+  const Pack16<T>* hx = pk(wbuf<T>(P, hxr) + off);
+  Pack16<T>* pv = pk(wbuf<T>(P, pr) + off);
+  Pack16<T>* rv = pk(wbuf<T>(P, rr_out) + off);
+  const Pack16<T>* pp = pk(wbuf<T>(P, ppr) + off);
+  const Pack16<T>* rp = pk(wbuf<T>(P, rpr) + off);
+  const Pack16<T>* ek = ekin_pk<T>(P);
   const bool first = P.scal[SC_FIRSTCG] != 0.0;
   T ekp = T(0);
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) ekp += ekin_at<T>(P, k) * x[k] * x[k];
-  double ek = block_sum((double)ekp, red);
-  ek = fmax(ek, 1e-3);
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const Pack16<T> a = x[v], g = ek[v];
+#pragma unroll
+    for (int j = 0; j < W; ++j) ekp += g.e[j] * a.e[j] * a.e[j];
+  }
+  double ekd = block_sum((double)ekp, red);
+  ekd = fmax(ekd, 1e-3);
   const T eps = T(P.eps[i]);
-  const T iek = T(1.0 / ek);
+  const T iek = T(1.0 / ekd);
   T grt = T(0), grpt = T(0), r2t = T(0);
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
-    T r = hx[k] - eps * x[k];
-    T g = tpa<T>(ekin_at<T>(P, k) * iek) * r;
-    grt += g * r;
-    r2t += r * r;
-    if (!first) grpt += g * rp[k];
-    rv[k] = r;
-    pv[k] = g;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const Pack16<T> a = x[v], h = hx[v], g = ek[v];
+    Pack16<T> rprev;
+    if (!first) rprev = rp[v];
+    Pack16<T> ro, go;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const T r = h.e[j] - eps * a.e[j];
+      const T gg = tpa<T>(g.e[j] * iek) * r;
+      grt += gg * r;
+      r2t += r * r;
+      if (!first) grpt += gg * rprev.e[j];
+      ro.e[j] = r;
+      go.e[j] = gg;
+    }
+    rv[v] = ro;
+    pv[v] = go;
   }
   double gr = block_sum((double)grt, red);
   double grp = block_sum((double)grpt, red);
@@ -298,13 +343,19 @@ __global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, i
   }
   if (gamma != 0.0) {
     const T gm = T(gamma);
-    for (int k = threadIdx.x; k < P.npw; k += blockDim.x) pv[k] = pv[k] + gm * pp[k];
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      Pack16<T> a = pv[v];
+      const Pack16<T> b = pp[v];
+#pragma unroll
+      for (int j = 0; j < W; ++j) a.e[j] = a.e[j] + gm * b.e[j];
+      pv[v] = a;
+    }
   }
   if (threadIdx.x == 0) {
     P.bv[BV_GR * P.nb + i] = gr;
     P.bv[BV_RES * P.nb + i] = sqrt(r2);
     P.bv[BV_GAMMA * P.nb + i] = gamma;
-    P.bv[BV_EKIN * P.nb + i] = ek;
+    P.bv[BV_EKIN * P.nb + i] = ekd;
   }
 }
 
@@ -312,21 +363,29 @@ __global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, i
 template <typename T>
 __global__ void __launch_bounds__(BAND_THREADS) k_normalize(KArgs ka, int pr, int ppr) {
   __shared__ double red[33];
+  constexpr int W = Pack16<T>::W;
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
   const size_t off = (size_t)i * P.ld;
-  T* pv = wbuf<T>(P, pr) + off;
-  T* pp = wbuf<T>(P, ppr) + off;
+  const int nv = P.ld / W;
+  Pack16<T>* pv = pk(wbuf<T>(P, pr) + off);
+  Pack16<T>* pp = pk(wbuf<T>(P, ppr) + off);
   T st = T(0);
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) st += pv[k] * pv[k];
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const Pack16<T> a = pv[v];
+#pragma unroll
+    for (int j = 0; j < W; ++j) st += a.e[j] * a.e[j];
+  }
   const double s = sqrt(block_sum((double)st, red));
   const T inv = s > 1e-150 ? T(1.0 / s) : T(0);
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
-    T v = pv[k];
-    pp[k] = v;
-    pv[k] = v * inv;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    Pack16<T> a = pv[v];
+    pp[v] = a;
+#pragma unroll
+    for (int j = 0; j < W; ++j) a.e[j] *= inv;
+    pv[v] = a;
   }
   if (threadIdx.x == 0) P.bv[BV_PNORM * P.nb + i] = s;
 }
@@ -336,21 +395,26 @@ __global__ void __launch_bounds__(BAND_THREADS) k_normalize(KArgs ka, int pr, in
 template <typename T>
 __global__ void __launch_bounds__(BAND_THREADS) k_line_min(KArgs ka, int xr, int hxr, int pr, int hpr) {
   __shared__ double red[33];
+  constexpr int W = Pack16<T>::W;
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
   const size_t off = (size_t)i * P.ld;
-  T* x = wbuf<T>(P, xr) + off;
-  T* hx = wbuf<T>(P, hxr) + off;
-  const T* pv = wbuf<T>(P, pr) + off;
-  const T* hp = wbuf<T>(P, hpr) + off;
+  const int nv = P.ld / W;
+  Pack16<T>* x = pk(wbuf<T>(P, xr) + off);
+  Pack16<T>* hx = pk(wbuf<T>(P, hxr) + off);
+  const Pack16<T>* pv = pk(wbuf<T>(P, pr) + off);
+  const Pack16<T>* hp = pk(wbuf<T>(P, hpr) + off);
   T at = T(0), bt = T(0), ct = T(0);
-  for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
-    T xv = x[k], pk = pv[k], h = hx[k];
-    at += xv * h;
-    bt += pk * h;
-    ct += pk * hp[k];
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const Pack16<T> xv = x[v], pq = pv[v], h = hx[v], q = hp[v];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      at += xv.e[j] * h.e[j];
+      bt += pq.e[j] * h.e[j];
+      ct += pq.e[j] * q.e[j];
+    }
   }
   double a = block_sum((double)at, red);
   double b = block_sum((double)bt, red);
@@ -361,9 +425,16 @@ __global__ void __launch_bounds__(BAND_THREADS) k_line_min(KArgs ka, int xr, int
   th = fmin(fmax(th, -lim), lim);
   const T cs = (T)cos(th), sn = (T)sin(th);
   if (th != 0.0) {
-    for (int k = threadIdx.x; k < P.npw; k += blockDim.x) {
-      x[k] = cs * x[k] + sn * pv[k];
-      hx[k] = cs * hx[k] + sn * hp[k];
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      Pack16<T> xv = x[v], h = hx[v];
+      const Pack16<T> pq = pv[v], q = hp[v];
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        xv.e[j] = cs * xv.e[j] + sn * pq.e[j];
+        h.e[j] = cs * h.e[j] + sn * q.e[j];
+      }
+      x[v] = xv;
+      hx[v] = h;
     }
   }
   if (threadIdx.x == 0) {

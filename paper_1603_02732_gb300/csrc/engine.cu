@@ -518,7 +518,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     c_rdw.push_back(div_up(3 * d.natom * d.nb, 256));
     c_nn.push_back(div_up(d.npw, 64 * NN_RT) * div_up(d.nb, 64));
     c_atoms.push_back(d.natom);
-    c_atomch.push_back(d.natom * nch);
+    c_atomch.push_back(div_up(d.natom, LF_GROUP) * nch);
     c_ewsg.push_back(div_up(ctxs[p]->ngbox_ew, 256));
     c_prob.push_back(1);
     c_tc.push_back(div_up(d.npw, TC_KC));

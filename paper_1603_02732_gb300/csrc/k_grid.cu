@@ -475,8 +475,11 @@ __global__ void k_build_projectors(KArgs ka, int deriv) {
 
 // ---------------------------------------------------------------------------
 // Forces.  Local: dE/dR_Ia = Omega sum_G v_s(G) G_a Im[exp(-iG.R_I) rho(G)^*] over the
-// box (work grid gfft = N rho_out(G)).  CTA = (problem, atom, chunk) -> partials.
+// box (work grid gfft = N rho_out(G)).  CTA = (problem, group of LF_AG atoms, chunk):
+// the point's G, rho(G) and v_s(G) are fetched once for the group -> partials.
 // ---------------------------------------------------------------------------
+constexpr int LF_AG = LF_GROUP;
+
 __global__ void k_local_forces(KArgs ka, int maxchunk) {
   __shared__ double red[33];
   (void)maxchunk;
@@ -485,26 +488,42 @@ __global__ void k_local_forces(KArgs ka, int maxchunk) {
   const Prob& P = ka.probs[p];
   const int nch = (P.ngrid + GRID_CHUNK - 1) / GRID_CHUNK;  // fpart is [natom][nch][3]
   const int local = blockIdx.x - ka.start[p];
-  const int a = local / nch, chunk = local - a * nch;
+  const int g = local / nch, chunk = local - g * nch;
+  const int a0 = g * LF_AG, na = min(LF_AG, P.natom - a0);
   const int base = chunk * GRID_CHUNK, end = min(P.ngrid, base + GRID_CHUNK);
-  const double* vg = P.vloc_g + (size_t)P.spec[a] * P.ngrid;
   const double inv_n = 1.0 / P.ngrid;
-  double f[3] = {0, 0, 0};
+  double f[LF_AG][3];
+#pragma unroll
+  for (int k = 0; k < LF_AG; ++k) f[k][0] = f[k][1] = f[k][2] = 0.0;
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
     int i1, i2, i3;
     GPt q = grid_pt(P, i, &i1, &i2, &i3);
     if (q.nyq) continue;
-    double v = vg[i];
-    if (v == 0.0) continue;
-    double2 rg = P.gfft[i];
-    cplx<double> w = phase_at(P, a, i1, i2, i3) * mk(rg.x * inv_n, -rg.y * inv_n);
+    double vs[MAX_SPECIES];
+    for (int s = 0; s < P.nspecies; ++s) vs[s] = P.vloc_g[(size_t)s * P.ngrid + i];
+    const double2 rg = P.gfft[i];
+    const cplx<double> rc = mk(rg.x * inv_n, -rg.y * inv_n);
     double G[3];
     gcart(P, q.m1, q.m2, q.m3, G);
-    for (int c = 0; c < 3; ++c) f[c] += v * G[c] * w.y;
+#pragma unroll
+    for (int k = 0; k < LF_AG; ++k) {
+      if (k >= na) break;
+      const double v = vs[P.spec[a0 + k]];
+      if (v == 0.0) continue;
+      const double t = v * (phase_at(P, a0 + k, i1, i2, i3) * rc).y;
+      f[k][0] += t * G[0];
+      f[k][1] += t * G[1];
+      f[k][2] += t * G[2];
+    }
   }
-  for (int c = 0; c < 3; ++c) {
-    double t = block_sum(f[c], red);
-    if (threadIdx.x == 0) P.fpart[((size_t)a * nch + chunk) * 3 + c] = -P.omega * t;
+#pragma unroll
+  for (int k = 0; k < LF_AG; ++k) {
+    if (k >= na) break;  // uniform across the block
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double t = block_sum(f[k][c], red);
+      if (threadIdx.x == 0) P.fpart[((size_t)(a0 + k) * nch + chunk) * 3 + c] = -P.omega * t;
+    }
   }
 }
 

@@ -25,6 +25,7 @@ constexpr int NN_KP = 128;             // rows of the small matrix staged per pa
 constexpr int BAND_THREADS = 256;
 constexpr int GRID_CHUNK = 4096;       // grid points per reduction CTA
 constexpr int RR_THREADS = 512;
+constexpr int LF_GROUP = 4;            // atoms per local-force CTA
 
 struct KArgs {
   const Prob* probs;

@@ -34,6 +34,10 @@ MEMBERS = 64
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one plane pass (both size classes of k_plane_vpsi_reg) on this
+# workload, from an ncu capture of those kernels (cold cache); set to None whenever they
+# change after the capture.
+PLANE_VPSI_TRAFFIC = 228.0e6 + 149.8e6 + 23.4e6
 
 
 def _dist():
@@ -262,7 +266,9 @@ def run_ours(args):
         ach_tflops = kt["flops"] / (kt["ms"] / 1e3) / 1e12 if kt["ms"] > 0 else 0.0
         ach_gbs = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else 0.0
         roofline = dict(kernel=kname, bound="alu", achieved=ach_tflops, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
-                        frac=ach_tflops / FP32_PEAK_TFLOPS, traffic=None,
+                        frac=ach_tflops / FP32_PEAK_TFLOPS,
+                        traffic=PLANE_VPSI_TRAFFIC if kname == "plane_vpsi" else None,
+                        traffic_unit="DRAM bytes per launch (ncu)",
                         peak_source="FP32 CUDA-core peak from unit counts (152 SM x 128 lanes x 2 x 2.07 GHz)",
                         hbm_achieved_gbs=ach_gbs, hbm_peak_gbs=peaks.get("hbm_gbs"), hbm_peak_source=src,
                         launches=kt["launches"], avg_launch_ms=kt["ms"] / max(kt["launches"], 1),

@@ -242,3 +242,20 @@ def test_block_update_gemm(sgo, precision, tc, tol):
                 scale = abs(alpha) * (np.abs(m).T @ np.abs(x)) + abs(beta) * np.abs(y)
                 err = np.abs(out - ref) / scale
                 assert err.max() <= tol, (st.name, n, alpha, beta, err.max())
+
+
+def test_overlap_gemm_bias(sgo):
+    """Why the overlap S = X^T X stays on CUDA cores in the mixed path: its diagonal sums
+    positive terms, which the FP32 CUDA-core GEMM leaves unbiased, while the tensor-core
+    3xTF32 path (K chunks of 512 accumulated in TMEM) comes out low by a few 1e-6 relative.
+    The overlap sets the band norms and hence rho and F."""
+    st = workloads.de_candidate(0)
+    rng = np.random.default_rng(3)
+    bias = {}
+    for tc in (0, 1):
+        ctx = sgo.Context(st, precision="mixed", gemm_tc=tc)
+        x = rng.normal(size=(st.nbands, ctx.npw))
+        x /= np.linalg.norm(x, axis=1, keepdims=True)
+        bias[tc] = float(np.mean(np.diag(ctx.subspace_matrix(x, x)) - 1.0))
+    assert abs(bias[0]) < 5e-8, bias
+    assert abs(bias[1]) < 2e-5, bias

@@ -69,8 +69,8 @@ typedef struct {
 } sgo_species;
 
 typedef struct {
-  int precision;          /* 0 = plain FP64; 1 = mixed: FP32 FFT/H.psi/GEMM products, FP64 sums,
-                             FP64 Cholesky, Rayleigh-Ritz eigensolve, energies, forces, Ewald */
+  int precision;          /* 0 = plain FP64; 1 = mixed: FP32 FFT/H.psi/GEMM products and subspace
+                             eigensolve, FP64 sums, energies, forces, Ewald, mixing */
   double kT;              /* Fermi-Dirac smearing, Ha; 0 = integer occupations (even N_el) */
   double scf_tol_e;       /* stop when |F_k - F_{k-1}| < scf_tol_e (Ha) ... */
   double scf_tol_rho;     /* ... and (Omega/N) sum |rho_out - rho_in| / N_el < scf_tol_rho */
@@ -85,6 +85,10 @@ typedef struct {
   unsigned long long seed;/* seed of the random initial wavefunctions */
   int gemm_tc;            /* mixed path: subspace/projector overlaps on tcgen05 tensor cores (3xTF32);
                              0 = FP32 CUDA cores */
+  int graph;              /* batches: run the SCF loop as captured CUDA graphs, the self-consistent
+                             iterations under a conditional WHILE node that the device ends
+                             (1, default); 0 = one host launch per kernel and a host check per
+                             iteration.  Results are identical.  Taken from the first member. */
 } sgo_opts;
 
 /* Fill *o with the defaults (FP64, kT 0, tolerances 1e-8 Ha / 1e-7, Pulay 8, ...). */

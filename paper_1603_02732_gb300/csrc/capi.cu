@@ -42,6 +42,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->n_nonscf = 3;
   o->seed = 12345ull;
   o->gemm_tc = 1;
+  o->graph = 1;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,
@@ -144,6 +145,7 @@ sgo_status sgo_batch_create(int n, sgo_ctx* const* ctxs, sgo_batch** out) {
     delete b;
     return SGO_ERR_CUDA;
   }
+  b->eng->enable_graphs(b->ctxs[0]->opts.graph != 0);
   *out = b;
   return SGO_OK;
 }

@@ -76,6 +76,38 @@ __global__ void k_gather_flags(KArgs ka, double* flags) {
     flags[4 * p + 3] = P.scal[SC_RESID];
   }
 }
+// End of one SCF iteration on the device (graph mode): gather every member's flags as
+// k_gather_flags does, retire members that converged or failed (the host loop's test),
+// count the iteration, and (set_cond) let the enclosing WHILE node run again while some
+// member is active and the iteration cap is not reached.  One CTA.
+__global__ void k_scf_control(KArgs ka, int* active, double* flags, int* iter, int max_scf,
+                              cudaGraphConditionalHandle cond, int set_cond) {
+  __shared__ int nact;
+  if (threadIdx.x == 0) nact = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < ka.nprob; p += blockDim.x) {
+    const Prob& P = ka.probs[p];
+    const double f0 = P.scal[SC_CONV], f1 = (double)(P.status[0] | P.status[2]), f2 = (double)P.status[1];
+    flags[4 * p + 0] = f0;
+    flags[4 * p + 1] = f1;
+    flags[4 * p + 2] = f2;
+    flags[4 * p + 3] = P.scal[SC_RESID];
+    if (active[p] && (f0 != 0.0 || f1 != 0.0 || f2 != 0.0)) active[p] = 0;
+    if (active[p]) atomicAdd(&nact, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int it = ++*iter;
+    if (set_cond) cudaGraphSetConditional(cond, (nact > 0 && it < max_scf) ? 1u : 0u);
+  }
+}
+// Entry test of the SCF WHILE node: run the first self-consistent iteration only if some
+// member is still active and the cap allows it.
+__global__ void k_scf_gate(const int* active, int n, const int* iter, int max_scf, cudaGraphConditionalHandle cond) {
+  int nact = 0;
+  for (int p = 0; p < n; ++p) nact += active[p] != 0;
+  cudaGraphSetConditional(cond, (nact > 0 && *iter < max_scf) ? 1u : 0u);
+}
 // out[p] = F, out_f[off_p + e] = forces (device gather for the device-pointer batch)
 __global__ void k_gather_results(KArgs ka, const int* foff, double* energies, double* forces, int* status) {
   const int p = blockIdx.x;
@@ -577,6 +609,8 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   allocs_.push_back(d_gpart_);
   if (!cuda_ok(cudaMalloc(&d_flags_, sizeof(double) * 4 * n_), "cudaMalloc(flags)")) return;
   allocs_.push_back(d_flags_);
+  if (!cuda_ok(cudaMalloc(&d_iter_, sizeof(int)), "cudaMalloc(iter)")) return;
+  allocs_.push_back(d_iter_);
   if (tc) {
     // TMA descriptors of every operand buffer (fixed for the engine's life; role swaps
     // select among them on the device) and the NN image scratch
@@ -612,6 +646,11 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
 }
 
 Engine::~Engine() {
+  if (g_nonscf_) cudaGraphExecDestroy(g_nonscf_);
+  if (g_scf_) cudaGraphExecDestroy(g_scf_);
+  if (ev_in_) cudaEventDestroy(ev_in_);
+  if (ev_out_) cudaEventDestroy(ev_out_);
+  if (own_stream_) cudaStreamDestroy(own_stream_);
   for (auto& v : ev_) cudaEventDestroy(v);
   for (void* p : allocs_) cudaFree(p);
 }
@@ -868,6 +907,128 @@ sgo_status Engine::structure_terms() {
   return cuda_ok(cudaGetLastError(), "structure terms") ? SGO_OK : SGO_ERR_CUDA;
 }
 
+// One SCF iteration up to the convergence test (Sec. II D): V_eff from rho_in, H Psi and
+// the subspace diagonalisation that start Algorithm 1, ncg all-band CG steps, occupations,
+// rho_out, the energy at (Psi, rho_out) and the per-member convergence test.
+template <typename T>
+void Engine::scf_iteration(int ncg, bool count_iter) {
+  const sgo_opts& o = ctx_[0]->opts;
+  // V_eff from rho_in(G): one inverse transform of rho_in(G) + i V_H(G) gives
+  // rho_in(r) + i V_H(r); LDA in real space
+  tbeg(TK_GRID_OTHER);
+  launch_potential_g(L(m_gew_));
+  tend(TK_GRID_OTHER);
+  grid_fft(0, 1);
+  tbeg(TK_GRID_OTHER);
+  launch_veff<T>(L(m_gew_), nullptr);
+  tend(TK_GRID_OTHER);
+  hpsi<T>(WB_X, WB_HX);
+  rayleigh_ritz<T>(false);
+  set_scal(SC_FIRSTCG, 1.0, true);
+  for (int k = 0; k < ncg; ++k) cg_step<T>();
+  // occupations and rho_out
+  launch_occupations(L(m_prob_));
+  wave_to_cols<T>(WB_X);
+  tbeg(TK_PLANE_DENSITY);
+  launch_plane_density<T>(L(m_dens_), nullptr);
+  for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], nullptr);
+  tend(TK_PLANE_DENSITY);
+  // energy at (Psi, rho_out) and the convergence test
+  launch_band_kinetic<T>(L(m_bands_), WB_X);
+  tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ, false);
+  tbeg(TK_GRID_OTHER);
+  launch_real_to_grid(L(m_gew_), 1, 1);
+  tend(TK_GRID_OTHER);
+  grid_fft(1, -1);
+  tbeg(TK_GRID_OTHER);
+  launch_grid_energies<T>(L(m_gch_), d_gpart_, maxchunk_);
+  launch_grid_energies_reduce(L(m_prob_), d_gpart_, maxchunk_);
+  launch_finish_iteration(L(m_prob_), o.scf_tol_e, o.scf_tol_rho, count_iter ? 1 : 0);
+  tend(TK_GRID_OTHER);
+}
+
+// Pulay mixing of rho_out with rho_in (members still iterating).
+void Engine::pulay_step() {
+  const sgo_opts& o = ctx_[0]->opts;
+  const int hist = std::min(std::max(o.pulay_hist, 1), MAX_HIST);
+  tbeg(TK_GRID_OTHER);
+  launch_pulay_store(L(m_gew_));
+  launch_pulay_gram(L(m_gch_), d_gpart_, maxchunk_, hist);
+  launch_pulay_solve(L(m_prob_), d_gpart_, maxchunk_, hist);
+  launch_pulay_mix(L(m_gew_), o.mix_alpha, o.kerker_q0);
+  tend(TK_GRID_OTHER);
+}
+
+// Graph mode: the iteration sequence captured once per engine.
+//   g_nonscf_: one iteration at the fixed initial potential (ncg_first CG steps, no count)
+//              followed by k_scf_control; the host replays it n_nonscf times.
+//   g_scf_:    k_scf_gate -> WHILE node whose body is one self-consistent iteration,
+//              k_scf_control (which sets the loop condition) and the Pulay step.
+// Kernel arguments (descriptor tables, maps, buffers) are fixed for the engine's life; the
+// per-member state they point to (active masks, roles, scalars) is read at replay time.
+template <typename T>
+bool Engine::build_graphs() {
+  const sgo_opts& o = ctx_[0]->opts;
+  cudaGraph_t ga = nullptr, gb = nullptr, body = nullptr;
+  const long long l0 = launches_;
+  bool ok = cuda_ok(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal), "capture begin");
+  if (ok) {
+    scf_iteration<T>(o.ncg_first, false);
+    k_scf_control<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, d_flags_, d_iter_, o.max_scf, 0, 0);
+    ok = cuda_ok(cudaStreamEndCapture(stream_, &ga), "capture end");
+  }
+  graph_launches_[0] = launches_ - l0;
+  ok = ok && cuda_ok(cudaGraphInstantiate(&g_nonscf_, ga, 0), "graph instantiate");
+  cudaGraphConditionalHandle cond = 0;
+  cudaGraphNode_t gate = nullptr, loop = nullptr;
+  ok = ok && cuda_ok(cudaGraphCreate(&gb, 0), "graph create") &&
+       cuda_ok(cudaGraphConditionalHandleCreate(&cond, gb, 0, 0), "conditional handle");
+  if (ok) {
+    const int* act = d_active_;
+    int n = n_;
+    const int* itp = d_iter_;
+    int mx = o.max_scf;
+    void* args[] = {&act, &n, &itp, &mx, &cond};
+    cudaKernelNodeParams kp = {};
+    kp.func = reinterpret_cast<void*>(k_scf_gate);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    ok = cuda_ok(cudaGraphAddKernelNode(&gate, gb, nullptr, 0, &kp), "gate node");
+  }
+  if (ok) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    ok = cuda_ok(cudaGraphAddNode(&loop, gb, &gate, nullptr, 1, &cp), "while node");
+    if (ok) body = cp.conditional.phGraph_out[0];
+  }
+  const long long l1 = launches_;
+  ok = ok && cuda_ok(cudaStreamBeginCaptureToGraph(stream_, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                     "capture body begin");
+  if (ok) {
+    scf_iteration<T>(o.ncg, true);
+    k_scf_control<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, d_flags_, d_iter_, o.max_scf, cond, 1);
+    pulay_step();
+    cudaGraph_t got = nullptr;
+    ok = cuda_ok(cudaStreamEndCapture(stream_, &got), "capture body end");
+  }
+  graph_launches_[1] = launches_ - l1;
+  launches_ = l0;
+  ok = ok && cuda_ok(cudaGraphInstantiate(&g_scf_, gb, 0), "graph instantiate (while)");
+  if (ga) cudaGraphDestroy(ga);
+  if (gb) cudaGraphDestroy(gb);
+  if (!ok) {
+    cudaGetLastError();
+    if (g_nonscf_) cudaGraphExecDestroy(g_nonscf_);
+    if (g_scf_) cudaGraphExecDestroy(g_scf_);
+    g_nonscf_ = g_scf_ = nullptr;
+  }
+  return ok;
+}
+
 template <typename T>
 sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
   const sgo_opts& o = ctx_[0]->opts;
@@ -883,56 +1044,32 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     launch_random_init<T>(L(m_bands_), WB_X, o.seed);
   }
   const int nonsc = warm ? 0 : std::max(0, o.n_nonscf);
-  const int hist = std::min(std::max(o.pulay_hist, 1), MAX_HIST);
   int it = 0;
-  for (it = 1; it <= o.max_scf; ++it) {
-    // V_eff from rho_in(G): one inverse transform of rho_in(G) + i V_H(G) gives
-    // rho_in(r) + i V_H(r); LDA in real space
-    tbeg(TK_GRID_OTHER);
-    launch_potential_g(L(m_gew_));
-    tend(TK_GRID_OTHER);
-    grid_fft(0, 1);
-    tbeg(TK_GRID_OTHER);
-    launch_veff<T>(L(m_gew_), nullptr);
-    tend(TK_GRID_OTHER);
-    // H Psi and the subspace diagonalisation (the start of Algorithm 1)
-    hpsi<T>(WB_X, WB_HX);
-    rayleigh_ritz<T>(false);
-    set_scal(SC_FIRSTCG, 1.0, true);
-    const int ncg = it <= nonsc ? o.ncg_first : o.ncg;
-    for (int k = 0; k < ncg; ++k) cg_step<T>();
-    // occupations and rho_out
-    launch_occupations(L(m_prob_));
-    wave_to_cols<T>(WB_X);
-    tbeg(TK_PLANE_DENSITY);
-    launch_plane_density<T>(L(m_dens_), nullptr);
-    for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], nullptr);
-    tend(TK_PLANE_DENSITY);
-    // energy at (Psi, rho_out) and the convergence test
-    launch_band_kinetic<T>(L(m_bands_), WB_X);
-    tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ, false);
-    tbeg(TK_GRID_OTHER);
-    launch_real_to_grid(L(m_gew_), 1, 1);
-    tend(TK_GRID_OTHER);
-    grid_fft(1, -1);
-    tbeg(TK_GRID_OTHER);
-    launch_grid_energies<T>(L(m_gch_), d_gpart_, maxchunk_);
-    launch_grid_energies_reduce(L(m_prob_), d_gpart_, maxchunk_);
-    launch_finish_iteration(L(m_prob_), o.scf_tol_e, o.scf_tol_rho, it > nonsc ? 1 : 0);
-    tend(TK_GRID_OTHER);
+  // graph mode: batch engines, no live kernel timer (its events are host bookkeeping)
+  bool graph = use_graph_ && timer_kind_ < 0;
+  if (graph && !g_scf_) graph = build_graphs<T>();
+  if (graph) {
+    CK(cudaMemsetAsync(d_iter_, 0, sizeof(int), stream_));
+    const int na = std::min(nonsc, o.max_scf);
+    for (int i = 0; i < na; ++i) CK(cudaGraphLaunch(g_nonscf_, stream_));
+    if (o.max_scf > nonsc) CK(cudaGraphLaunch(g_scf_, stream_));
+    int h_iter = 0;
+    CK(cudaMemcpyAsync(&h_iter, d_iter_, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(h_flags_.data(), d_flags_, sizeof(double) * 4 * n_, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(h_active_.data(), d_active_, sizeof(int) * n_, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
     CK(cudaGetLastError());
-    sync_active();
-    int nact = 0;
-    for (int p = 0; p < n_; ++p) nact += h_active_[p];
-    if (nact == 0) break;
-    if (it > nonsc) {
-      // Pulay mixing of rho_out with rho_in
-      tbeg(TK_GRID_OTHER);
-      launch_pulay_store(L(m_gew_));
-      launch_pulay_gram(L(m_gch_), d_gpart_, maxchunk_, hist);
-      launch_pulay_solve(L(m_prob_), d_gpart_, maxchunk_, hist);
-      launch_pulay_mix(L(m_gew_), o.mix_alpha, o.kerker_q0);
-      tend(TK_GRID_OTHER);
+    it = h_iter;
+    launches_ += (long long)na * graph_launches_[0] + (long long)std::max(0, h_iter - na) * graph_launches_[1];
+  } else {
+    for (it = 1; it <= o.max_scf; ++it) {
+      scf_iteration<T>(it <= nonsc ? o.ncg_first : o.ncg, it > nonsc);
+      CK(cudaGetLastError());
+      sync_active();
+      int nact = 0;
+      for (int p = 0; p < n_; ++p) nact += h_active_[p];
+      if (nact == 0) break;
+      if (it > nonsc) pulay_step();
     }
   }
   const int niter = std::min(it, o.max_scf);
@@ -987,7 +1124,25 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
 
 sgo_status Engine::run(bool want_forces, std::vector<sgo_status>* per_item) {
   if (!ok_) return SGO_ERR_CUDA;
-  return precision_ ? run_t<float>(want_forces, per_item) : run_t<double>(want_forces, per_item);
+  if (!use_graph_ || timer_kind_ >= 0)
+    return precision_ ? run_t<float>(want_forces, per_item) : run_t<double>(want_forces, per_item);
+  // graph mode runs on a private stream, ordered after the caller's stream and before
+  // anything the caller enqueues afterwards
+  if (!own_stream_) {
+    if (!cuda_ok(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking), "graph stream") ||
+        !cuda_ok(cudaEventCreateWithFlags(&ev_in_, cudaEventDisableTiming), "graph event") ||
+        !cuda_ok(cudaEventCreateWithFlags(&ev_out_, cudaEventDisableTiming), "graph event"))
+      return SGO_ERR_CUDA;
+  }
+  cudaStream_t user = stream_;
+  CK(cudaEventRecord(ev_in_, user));
+  CK(cudaStreamWaitEvent(own_stream_, ev_in_, 0));
+  stream_ = own_stream_;
+  sgo_status s = precision_ ? run_t<float>(want_forces, per_item) : run_t<double>(want_forces, per_item);
+  stream_ = user;
+  CK(cudaEventRecord(ev_out_, own_stream_));
+  CK(cudaStreamWaitEvent(user, ev_out_, 0));
+  return s;
 }
 
 // ---- component entry points (problem 0) ----

@@ -80,11 +80,16 @@ class Engine {
     launches_ = 0;
     return v;
   }
+  // Drive the SCF loop by captured CUDA graphs (batch engines); see build_graphs().
+  void enable_graphs(bool on) { use_graph_ = on; }
   // Batch evaluation with positions, energies, forces and statuses in device memory.
   sgo_status run_device(const double* pos, double* energies, double* forces, int* status);
 
  private:
   template <typename T> sgo_status run_t(bool want_forces, std::vector<sgo_status>* per_item);
+  template <typename T> void scf_iteration(int ncg, bool count_iter);
+  void pulay_step();
+  template <typename T> bool build_graphs();
   template <typename T> void hpsi(int src, int dst);
   template <typename T> void rayleigh_ritz(bool rotate_history);
   template <typename T> void cg_step();
@@ -146,6 +151,14 @@ class Engine {
   size_t rr_smem_bytes_ = 0;
   double* d_flags_ = nullptr;   // [n][4] gathered per iteration
   std::vector<double> h_flags_;
+  // graph mode: captured iterations, the device iteration counter, a private stream (the
+  // caller's may be the legacy default stream, which cannot be captured)
+  bool use_graph_ = false;
+  cudaGraphExec_t g_nonscf_ = nullptr, g_scf_ = nullptr;
+  long long graph_launches_[2] = {0, 0};
+  int* d_iter_ = nullptr;
+  cudaStream_t own_stream_ = nullptr;
+  cudaEvent_t ev_in_ = nullptr, ev_out_ = nullptr;
 };
 
 // Kernel classes the engine can time live (CUDA events on its stream).

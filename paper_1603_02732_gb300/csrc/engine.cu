@@ -309,8 +309,12 @@ sgo_status ctx_setup(sgo_ctx* c) {
   d.box1 = box[0];
   d.box2 = box[1];
   d.box3 = box[2];
-  if ((size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 > 220 * 1024 || d.n1 * d.n2 > 8192) {
-    set_error("FFT plane N1*N2 too large for the shared-memory plane kernels (max about 6900)");
+  // planes: the shared-memory engine holds two whole planes; the mixed path's register
+  // kernels hold only the occupied rows (their fit is checked with the engine's maps)
+  const bool plane_reg = c->precision == 1 && (plane_reg_ok(d.n1, d.n2) || pair_plane_ok(d.n1, d.n2));
+  if (((size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 > 220 * 1024 || d.n1 * d.n2 > 8192) && !plane_reg) {
+    set_error("FFT plane N1*N2 too large for the shared-memory plane kernels (max about 6900); the mixed "
+              "path takes lengths up to 128 with register transforms");
     return SGO_ERR_ARG;
   }
   if ((size_t)(4 * QCP + 1) * d.n3 * 16 > 220 * 1024) {
@@ -469,6 +473,16 @@ WorkMap Engine::make_map(const std::vector<int>& counts) {
   }
   m.total = st.back();
   m.maxper = mx;
+  m.max_n1 = m.max_n2 = m.max_n3 = m.max_n12 = m.max_nb = 0;
+  for (size_t i = 0; i < counts.size() && i < ctx_.size(); ++i) {
+    if (!counts[i]) continue;
+    const Prob& d = ctx_[i]->d;
+    m.max_n1 = std::max(m.max_n1, d.n1);
+    m.max_n2 = std::max(m.max_n2, d.n2);
+    m.max_n3 = std::max(m.max_n3, d.n3);
+    m.max_n12 = std::max(m.max_n12, d.n1 * d.n2);
+    m.max_nb = std::max(m.max_nb, d.nb);
+  }
   int* d = nullptr;
   if (!cuda_ok(cudaMalloc(&d, st.size() * sizeof(int)), "cudaMalloc(map)")) return m;
   cudaMemcpy(d, st.data(), st.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -483,11 +497,11 @@ Launch Engine::L(const WorkMap& m) const {
   l.ka = KArgs{d_probs_, m.start ? m.start : m_prob_.start, n_, d_active_};
   l.map = m;
   l.stream = stream_;
-  l.max_n1 = max_n1_;
-  l.max_n2 = max_n2_;
-  l.max_n3 = max_n3_;
-  l.max_n12 = max_n12_;
-  l.max_nb = max_nb_;
+  l.max_n1 = m.max_n1 >= 0 ? m.max_n1 : max_n1_;
+  l.max_n2 = m.max_n2 >= 0 ? m.max_n2 : max_n2_;
+  l.max_n3 = m.max_n3 >= 0 ? m.max_n3 : max_n3_;
+  l.max_n12 = m.max_n12 >= 0 ? m.max_n12 : max_n12_;
+  l.max_nb = m.max_nb >= 0 ? m.max_nb : max_nb_;
   l.plane_threads = plane_threads_;
   return l;
 }
@@ -503,7 +517,8 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     }
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
-      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2], c_dreg[2], c_zreg[2];
+      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2], c_dreg[2], c_zreg[2], c_ppair,
+      c_dpair, c_zpair, c_gx, c_gy;
   size_t part = 0;
   int max_natom = 0;
   for (int p = 0; p < n_; ++p) {
@@ -518,19 +533,40 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     maxchunk_ = std::max(maxchunk_, nch);
     const int nsplit = div_up(d.npw, TN_KC);
     const int tw = div_up(d.nb, TN_TILE), ta = div_up(d.natom, TN_TILE), td = div_up(3 * d.natom, TN_TILE);
-    // z-column passes: register FFTs on the mixed path where n3 has one
+    // z-column passes: register FFTs on the mixed path where n3 has one (single thread or
+    // lane pair per line), the shared-memory engine otherwise
     const bool zreg = precision_ == 1 && zreg_ok(d.n3);
-    c_zcol.push_back(zreg ? 0 : d.npair * div_up(d.ncp, QCP));
+    const bool zpair = precision_ == 1 && !zreg && zpair_ok(d.n3);
+    c_zcol.push_back(zreg || zpair ? 0 : d.npair * div_up(d.ncp, QCP));
     for (int k = 0; k < 2; ++k) c_zreg[k].push_back(zreg && zreg_class(d.n3) == k ? zreg_ctas(d.ncp, d.npair) : 0);
     if (zreg) zreg_smem_[zreg_class(d.n3)] = std::max(zreg_smem_[zreg_class(d.n3)], zreg_smem(d.n3));
+    c_zpair.push_back(zpair ? zpair_ctas(d.ncp, d.npair) : 0);
+    if (zpair) zpair_smem_ = std::max(zpair_smem_, zpair_smem(d.n3));
+    // FP64 grid transforms: a whole plane per CTA when two planes fit in shared memory,
+    // otherwise line blocks along x and y
+    const bool gbig = (size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 > 220 * 1024;
+    c_gx.push_back(gbig ? div_up(d.n3 * d.n2, QZ) : 0);
+    c_gy.push_back(gbig ? div_up(d.n3 * d.n1, QZ) : 0);
     // plane passes: register FFTs on the mixed path where both plane lengths have one
     // and the kernels' shared memory fits; the shared-memory engine otherwise
     const size_t smem_cap = 220 * 1024;
     const bool preg = precision_ == 1 && plane_reg_ok(d.n1, d.n2) && plane_reg_smem(d.n1, d.n2, d.m1max) <= smem_cap;
     const bool dreg = preg && plane_density_reg_smem(d.n1, d.n2, d.m1max) <= smem_cap;
     const int pcls = preg ? plane_reg_class(d.n1, d.n2) : -1;
-    c_plane.push_back(preg ? 0 : d.npair * d.n3);
-    c_dens.push_back(dreg ? 0 : d.n3);
+    const bool ppair = precision_ == 1 && !preg && pair_plane_ok(d.n1, d.n2) &&
+                       pair_plane_smem(d.n1, d.n2, d.m1max) <= smem_cap;
+    const bool dpair = ppair && pair_density_smem(d.n1, d.n2, d.m1max) <= smem_cap;
+    const bool psmem = (size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 <= smem_cap && d.n1 * d.n2 <= 8192;
+    if ((!preg && !ppair && !psmem) || (!dreg && !dpair && !psmem)) {
+      set_error("FFT plane too large for the plane kernels of this precision");
+      return;
+    }
+    c_plane.push_back(preg || ppair ? 0 : d.npair * d.n3);
+    c_dens.push_back(dreg || dpair ? 0 : d.n3);
+    c_ppair.push_back(ppair ? pair_plane_ctas(d.n2, d.n3, d.npair) : 0);
+    c_dpair.push_back(dpair ? pair_density_ctas(d.n2, d.n3) : 0);
+    if (ppair) ppair_smem_ = std::max(ppair_smem_, pair_plane_smem(d.n1, d.n2, d.m1max));
+    if (dpair) dpair_smem_ = std::max(dpair_smem_, pair_density_smem(d.n1, d.n2, d.m1max));
     for (int k = 0; k < 2; ++k) {
       c_preg[k].push_back(pcls == k ? plane_reg_ctas(d.n2, d.n3, d.npair) : 0);
       c_dreg[k].push_back(dreg && pcls == k ? plane_density_reg_ctas(d.n2, d.n3) : 0);
@@ -538,7 +574,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     if (preg) preg_smem_[pcls] = std::max(preg_smem_[pcls], plane_reg_smem(d.n1, d.n2, d.m1max));
     if (dreg) dreg_smem_[pcls] = std::max(dreg_smem_[pcls], plane_density_reg_smem(d.n1, d.n2, d.m1max));
     c_gz.push_back(div_up(d.n1 * d.n2, QZ));
-    c_gp.push_back(d.n3);
+    c_gp.push_back(gbig ? 0 : d.n3);
     c_gew.push_back(div_up(d.ngrid, GRID_EW_POINTS));
     c_gch.push_back(nch);
     c_bands.push_back(d.nb);
@@ -565,6 +601,11 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   for (int k = 0; k < 2; ++k) m_preg_[k] = make_map(c_preg[k]);
   for (int k = 0; k < 2; ++k) m_dreg_[k] = make_map(c_dreg[k]);
   for (int k = 0; k < 2; ++k) m_zreg_[k] = make_map(c_zreg[k]);
+  m_ppair_ = make_map(c_ppair);
+  m_dpair_ = make_map(c_dpair);
+  m_zpair_ = make_map(c_zpair);
+  m_gx_ = make_map(c_gx);
+  m_gy_ = make_map(c_gy);
   m_dens_ = make_map(c_dens);
   m_gz_ = make_map(c_gz);
   m_gp_ = make_map(c_gp);
@@ -626,11 +667,17 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     allocs_.push_back(d_nnimg_);
   }
   h_flags_.assign(4 * n_, 0.0);
-  // mixed path: FP32 subspace eigensolve when its shared-memory layout fits (nb <= 105)
-  rr_f32_ = precision_ == 1 && (size_t)20 * max_nb_ * (max_nb_ | 1) <= 216 * 1024;
+  // mixed path: the FP32 eigensolve (its five matrices in shared memory up to nb = 105,
+  // else in a per-member global scratch; the Jacobi pair tables allow nb <= 512)
+  rr_f32_ = precision_ == 1 && max_nb_ <= 512;
+  if (rr_f32_ && (size_t)20 * max_nb_ * (max_nb_ | 1) > 216 * 1024) {
+    rr32_stride_ = (size_t)5 * max_nb_ * (max_nb_ | 1);
+    if (!cuda_ok(cudaMalloc(&d_rr32_, sizeof(float) * rr32_stride_ * n_), "cudaMalloc(rr32)")) return;
+    allocs_.push_back(d_rr32_);
+  }
   rr_smem_bytes_ = (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
   rr_smem_ = rr_smem_bytes_ <= 200 * 1024;
-  if (!rr_smem_) {
+  if (!rr_f32_ && !rr_smem_) {
     rr_stride_ = (size_t)3 * max_nb_ * max_nb_;
     if (!cuda_ok(cudaMalloc(&d_rr_, sizeof(double) * rr_stride_ * n_), "cudaMalloc(rr)")) return;
     allocs_.push_back(d_rr_);
@@ -761,12 +808,19 @@ void Engine::grid_fft(int which, int sign) {
 }
 
 void Engine::grid_fft_raw(int which, int sign) {
+  // forward: planes (y, x), then z; inverse: z, then planes.  Large planes go by line
+  // blocks along y and x.
+  auto planes = [&](int sg) {
+    launch_grid_plane_fft(L(m_gp_), which, sg);
+    launch_grid_line_fft(L(m_gy_), which, sg, 1);
+    launch_grid_line_fft(L(m_gx_), which, sg, 0);
+  };
   if (sign < 0) {
-    launch_grid_plane_fft(L(m_gp_), which, -1);
+    planes(-1);
     launch_grid_z_fft(L(m_gz_), which, -1);
   } else {
     launch_grid_z_fft(L(m_gz_), which, 1);
-    launch_grid_plane_fft(L(m_gp_), which, 1);
+    planes(1);
   }
 }
 
@@ -816,15 +870,19 @@ void Engine::rotate(int role, bool image_ready) {
 template <typename T>
 void Engine::wave_to_cols(int src) {
   launch_wave_to_cols<T>(L(m_zcol_), src);
-  if (sizeof(T) == 4)
+  if (sizeof(T) == 4) {
     for (int k = 0; k < 2; ++k) launch_wave_to_cols_reg(L(m_zreg_[k]), k, zreg_smem_[k], src);
+    launch_wave_to_cols_pair(L(m_zpair_), zpair_smem_, src);
+  }
 }
 
 template <typename T>
 void Engine::cols_to_wave(int src, int dst) {
   launch_cols_to_wave<T>(L(m_zcol_), src, dst);
-  if (sizeof(T) == 4)
+  if (sizeof(T) == 4) {
     for (int k = 0; k < 2; ++k) launch_cols_to_wave_reg(L(m_zreg_[k]), k, zreg_smem_[k], src, dst);
+    launch_cols_to_wave_pair(L(m_zpair_), zpair_smem_, src, dst);
+  }
 }
 
 // H applied to every band of src: FFT local + kinetic, then nonlocal B (D o B^T src).
@@ -836,6 +894,7 @@ void Engine::hpsi(int src, int dst) {
   tbeg(TK_PLANE_VPSI);
   launch_plane_vpsi<T>(L(m_plane_));
   for (int k = 0; k < 2; ++k) launch_plane_vpsi_reg(L(m_preg_[k]), k, preg_smem_[k]);
+  launch_plane_vpsi_pair(L(m_ppair_), ppair_smem_);
   tend(TK_PLANE_VPSI);
   tbeg(TK_COLS_TO_WAVE);
   cols_to_wave<T>(src, dst);
@@ -852,7 +911,7 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S, false);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
   tbeg(TK_RR);
-  if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1));  // 5 FP32 n x (n|1)
+  if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1), d_rr32_, rr32_stride_);  // 5 FP32 n x (n|1)
   else launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_);
   tend(TK_RR);
   rotate<T>(WB_X, false);
@@ -932,6 +991,7 @@ void Engine::scf_iteration(int ncg, bool count_iter) {
   tbeg(TK_PLANE_DENSITY);
   launch_plane_density<T>(L(m_dens_), nullptr);
   for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], nullptr);
+  launch_plane_density_pair(L(m_dpair_), dpair_smem_, nullptr);
   tend(TK_PLANE_DENSITY);
   // energy at (Psi, rho_out) and the convergence test
   launch_band_kinetic<T>(L(m_bands_), WB_X);
@@ -1196,6 +1256,7 @@ sgo_status Engine::density(int nvec, const double* psi, const double* occ, doubl
     wave_to_cols<float>(WB_W);
     launch_plane_density<float>(L(m_dens_), docc);
     for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], docc);
+    launch_plane_density_pair(L(m_dpair_), dpair_smem_, docc);
   } else {
     launch_copy_in<double>(L(m_bands_), WB_W, dpsi, nvec);
     wave_to_cols<double>(WB_W);

@@ -132,6 +132,9 @@ class Engine {
       m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_atomch_, m_ewsg_, m_prob_, m_tc_, m_nntc_;
   WorkMap m_preg_[2], m_dreg_[2], m_zreg_[2];  // register-FFT plane / column kernels, per size class
   size_t preg_smem_[2] = {0, 0}, dreg_smem_[2] = {0, 0}, zreg_smem_[2] = {0, 0};
+  WorkMap m_ppair_, m_dpair_, m_zpair_;         // lane-pair register FFT kernels (lengths 96-128)
+  size_t ppair_smem_ = 0, dpair_smem_ = 0, zpair_smem_ = 0;
+  WorkMap m_gx_, m_gy_;                         // FP64 grid transforms of planes too large for one CTA
   template <typename T> void wave_to_cols(int src);
   template <typename T> void cols_to_wave(int src, int dst);
   bool tc_ok_[3] = {false, false, false};      // TN on tcgen05, per A-operand kind
@@ -148,6 +151,8 @@ class Engine {
   size_t rr_stride_ = 0;
   bool rr_smem_ = true;
   bool rr_f32_ = false;
+  float* d_rr32_ = nullptr;     // FP32 eigensolve scratch when it exceeds shared memory
+  size_t rr32_stride_ = 0;
   size_t rr_smem_bytes_ = 0;
   double* d_flags_ = nullptr;   // [n][4] gathered per iteration
   std::vector<double> h_flags_;

@@ -22,21 +22,35 @@ namespace sgo {
 // Line lengths with a register transform (all other lengths use the shared-memory engine).
 constexpr int kRegSizes[] = {10, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32, 36, 40, 45, 48, 50, 54, 60, 64, 72};
 constexpr int kRegCount = sizeof(kRegSizes) / sizeof(int);
+// Lengths N = 2M transformed by a pair of lanes (M of the single-thread lengths each).
+constexpr int kPairSizes[] = {96, 100, 108, 120, 128};
+constexpr int kPairCount = sizeof(kPairSizes) / sizeof(int);
 
+// twiddle tables: every single-thread length, then every pair length
+constexpr int tw_size(int i) { return i < kRegCount ? kRegSizes[i] : kPairSizes[i - kRegCount]; }
 constexpr int reg_table_offset(int n) {
   int o = 0;
-  for (int i = 0; i < kRegCount; ++i) {
-    if (kRegSizes[i] == n) return o;
-    o += kRegSizes[i];
+  for (int i = 0; i < kRegCount + kPairCount; ++i) {
+    if (tw_size(i) == n) return o;
+    o += tw_size(i);
   }
   return -1;
 }
 constexpr int reg_table_total() {
   int o = 0;
-  for (int i = 0; i < kRegCount; ++i) o += kRegSizes[i];
+  for (int i = 0; i < kRegCount + kPairCount; ++i) o += tw_size(i);
   return o;
 }
-constexpr bool reg_supported(int n) { return reg_table_offset(n) >= 0; }
+constexpr bool reg_supported(int n) {
+  for (int i = 0; i < kRegCount; ++i)
+    if (kRegSizes[i] == n) return true;
+  return false;
+}
+constexpr bool pair_supported(int n) {
+  for (int i = 0; i < kPairCount; ++i)
+    if (kPairSizes[i] == n) return true;
+  return false;
+}
 
 // radices, outermost stage first (packed one per 4 bits, stage 0 lowest)
 constexpr unsigned reg_plan(int n) {
@@ -177,6 +191,64 @@ __device__ __forceinline__ void row_fft_n(int n, cplx<float>* row, bool fwd) {
   }
 }
 
+// ---- lengths N = 2M over a lane pair (lanes 2k and 2k+1 of a warp, h = lane & 1) ----
+// All 32 lanes of the warp must take part (the pair exchanges data by shuffles).
+
+__device__ __forceinline__ cplx<float> shfl_pair(cplx<float> v) {
+  return mk(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1));
+}
+
+// Inverse DFT of length 2M.  On entry lane h holds X[h M + j] in x[j]; a radix-2
+// decimation-in-frequency step across the pair, y_0[j] = X[j] + X[j + M] and
+// y_1[j] = (X[j] - X[j + M]) W_2M^-j, then the lane's M-point inverse: on exit lane h holds
+// the sample of time index h + 2 dif_freq<M>(p) in x[p].
+template <int M>
+__device__ __forceinline__ void pair_inv(cplx<float> (&x)[M], int h) {
+  const cplx<float>* tn = twf<2 * M>();
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const cplx<float> o = shfl_pair(x[j]);
+    if (h == 0) {
+      x[j] = x[j] + o;
+    } else {
+      cplx<float> w = tn[j];
+      w.y = -w.y;
+      x[j] = (o - x[j]) * w;
+    }
+  }
+  reg_fft<float, M, 1>(x, twf<M>());
+}
+
+// Row of length 2M in place (both directions through pair_inv; forward as conj o inv o conj).
+template <int M>
+__device__ __forceinline__ void row_pair(cplx<float>* row, bool fwd, int h, bool act) {
+  const float s = fwd ? -1.f : 1.f;
+  cplx<float> x[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const cplx<float> v = act ? row[h * M + j] : mk(0.f, 0.f);
+    x[j] = mk(v.x, s * v.y);
+  }
+  pair_inv<M>(x, h);
+  if (act) {
+#pragma unroll
+    for (int p = 0; p < M; ++p) row[h + 2 * dif_freq<M>(p)] = mk(x[p].x, s * x[p].y);
+  }
+}
+
+template <int MAXN>
+__device__ __forceinline__ void row_pair_n(int n, cplx<float>* row, bool fwd, int h, bool act) {
+  switch (n) {
+#define SGO_ROW(N)                                                  \
+  case N:                                                           \
+    if constexpr (N <= MAXN) row_pair<N / 2>(row, fwd, h, act);     \
+    break;
+    SGO_ROW(96) SGO_ROW(100) SGO_ROW(108) SGO_ROW(120) SGO_ROW(128)
+#undef SGO_ROW
+    default: break;
+  }
+}
+
 // Fill this translation unit's twiddle table on the current device (once per device).
 inline bool upload_twiddles() {
   static std::mutex mu;
@@ -186,9 +258,9 @@ inline bool upload_twiddles() {
   std::lock_guard<std::mutex> lk(mu);
   if (done[dev]) return true;
   std::vector<cplx<float>> h(reg_table_total());
-  for (int i = 0, o = 0; i < kRegCount; o += kRegSizes[i], ++i)
-    for (int t = 0; t < kRegSizes[i]; ++t) {
-      const double a = 2.0 * PI * t / kRegSizes[i];
+  for (int i = 0, o = 0; i < kRegCount + kPairCount; o += tw_size(i), ++i)
+    for (int t = 0; t < tw_size(i); ++t) {
+      const double a = 2.0 * PI * t / tw_size(i);
       h[o + t] = mk((float)std::cos(a), (float)(-std::sin(a)));
     }
   if (cudaMemcpyToSymbol(c_tw, h.data(), sizeof(cplx<float>) * h.size()) != cudaSuccess) return false;

@@ -321,6 +321,43 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_z_fft(KArgs ka, int which
   }
 }
 
+// Line blocks of the grid transform for planes too large for one CTA: along x (axis 0:
+// length N1, element stride N2, lines (z, i2)) or y (axis 1: length N2, contiguous, lines
+// (z, i1)), QZ lines per CTA, loads and stores coalesced across the lines' fast index.
+__global__ void __launch_bounds__(ZCOL_THREADS) k_grid_line_fft(KArgs ka, int which, int sign, int axis) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int chunk = blockIdx.x - ka.start[p];
+  const int n1 = P.n1, n2 = P.n2, n12 = n1 * n2;
+  const int n = axis ? n2 : n1;
+  const int nlines = P.n3 * (axis ? n1 : n2);
+  const int l0 = chunk * QZ, nc = min(QZ, nlines - l0);
+  cplx<double>* lines = reinterpret_cast<cplx<double>*>(smem_raw);
+  cplx<double>* alt = lines + QZ * n;
+  cplx<double>* roots = alt + QZ * n;
+  load_roots<double>(roots, P, axis ? n1 : 0, n);
+  cplx<double>* g = reinterpret_cast<cplx<double>*>(grid_of(P, which));
+  auto at = [&](int c, int e) -> size_t {
+    const int l = l0 + c;
+    if (axis) return (size_t)l * n2 + e;
+    const int z = l / n2;
+    return (size_t)z * n12 + (size_t)e * n2 + (l - z * n2);
+  };
+  for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
+    const int c = axis ? t / n : t % nc, e = axis ? t % n : t / nc;
+    lines[c * n + e] = g[at(c, e)];
+  }
+  __syncthreads();
+  const cplx<double>* res =
+      fft_lines<double>(lines, alt, nc, n, 1, contiguous(nc), P.fd[axis ? 1 : 0], roots, sign < 0 ? -1.0 : 1.0);
+  for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
+    const int c = axis ? t / n : t % nc, e = axis ? t % n : t / nc;
+    g[at(c, e)] = res[c * n + e];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -348,6 +385,12 @@ void launch_plane_density(const Launch& L, const double* occ_override) {
   size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<T>) + (size_t)L.max_n12 * sizeof(double) + 16;
   k_plane_density<T><<<L.map.total, L.plane_threads, sm, L.stream>>>(L.ka, occ_override);
 }
+void launch_grid_line_fft(const Launch& L, int which, int sign, int axis) {
+  if (!L.map.total) return;
+  const int n = axis ? L.max_n2 : L.max_n1;
+  size_t sm = (size_t)(2 * QZ + 1) * n * sizeof(cplx<double>);
+  k_grid_line_fft<<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, which, sign, axis);
+}
 void launch_grid_plane_fft(const Launch& L, int which, int sign) {
   if (!L.map.total) return;
   size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<double>);
@@ -359,7 +402,7 @@ void launch_grid_z_fft(const Launch& L, int which, int sign) {
   k_grid_z_fft<<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, which, sign);
 }
 
-bool fft_reg_init() { return plane_vpsi_reg_init() && plane_density_reg_init() && zreg_init(); }
+bool fft_reg_init() { return plane_vpsi_reg_init() && plane_density_reg_init() && zreg_init() && pair_reg_init(); }
 
 void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_wave_to_cols<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -372,9 +415,11 @@ void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_plane_density<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_plane_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_z_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_line_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   plane_vpsi_reg_set_smem_limits(bytes);
   plane_density_reg_set_smem_limits(bytes);
   zreg_set_smem_limits(bytes);
+  pair_reg_set_smem_limits(bytes);
 }
 
 template void launch_wave_to_cols<float>(const Launch&, int);

@@ -703,7 +703,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
+__global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch, size_t gstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float red[32];
   __shared__ float cs_c[256], cs_s[256];
@@ -713,7 +713,8 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka) {
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
   const int n = P.nb, ns = n | 1, nn = n * ns;
-  float* D = reinterpret_cast<float*>(smem_raw);
+  // the five matrices live in shared memory, or (large n) in this problem's global scratch
+  float* D = gscratch ? gscratch + (size_t)p * gstride : reinterpret_cast<float*>(smem_raw);
   float* G = D + nn;
   float* Hf = G + nn;
   float* W = Hf + nn;
@@ -1009,8 +1010,8 @@ void launch_copy_out(const Launch& L, int role, double* dst, int nvec) {
   if (!L.map.total) return;
   k_copy_out<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, role, dst, nvec);
 }
-void launch_rr_f32(const Launch& L, size_t smem) {
-  k_rr_f32<<<L.ka.nprob, RR_THREADS, smem, L.stream>>>(L.ka);
+void launch_rr_f32(const Launch& L, size_t smem, float* gscratch, size_t gstride) {
+  k_rr_f32<<<L.ka.nprob, RR_THREADS, gscratch ? 0 : smem, L.stream>>>(L.ka, gscratch, gstride);
 }
 void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride) {
   k_rr<<<L.ka.nprob, RR_THREADS, use_smem ? smem : 0, L.stream>>>(L.ka, use_smem, gscratch, gstride);

@@ -14,6 +14,7 @@ constexpr int PLANE_MIN_BLOCKS = 4;     // register cap (64) for 4+ resident CTA
 constexpr int PLANE_THREADS_MAX = PLANE_THREADS;
 constexpr int PLANE_REG_THREADS = 256;  // register-FFT plane kernel (mixed path)
 constexpr int PLANE_REG_MAXN = 72;      // longest x / y / z line it transforms
+constexpr int PAIR_REG_MAXN = 128;      // longest line a lane pair transforms
 constexpr int ZREG_CP = 64;             // column pairs per register z-column CTA
 constexpr int ZREG_THREADS = 2 * ZREG_CP;
 // GEMM geometry
@@ -53,6 +54,7 @@ template <typename T> void launch_plane_vpsi(const Launch& L);
 template <typename T> void launch_plane_density(const Launch& L, const double* occ_override);
 void launch_grid_plane_fft(const Launch& L, int which, int sign);
 void launch_grid_z_fft(const Launch& L, int which, int sign);
+void launch_grid_line_fft(const Launch& L, int which, int sign, int axis);  // axis 0: x, 1: y
 void fft_set_smem_limits(size_t bytes);
 // register-FFT plane pass (mixed path): lengths n1, n2 with a register transform
 bool plane_reg_ok(int n1, int n2);
@@ -73,6 +75,21 @@ void launch_wave_to_cols_reg(const Launch& L, int cls, size_t smem, int src);
 void launch_cols_to_wave_reg(const Launch& L, int cls, size_t smem, int src, int dst);
 bool zreg_init();
 void zreg_set_smem_limits(size_t bytes);
+// lane-pair register FFT passes for lengths 96 ... 128 (mixed path), k_pair_reg.cu
+bool pair_plane_ok(int n1, int n2);
+int pair_plane_ctas(int n2, int n3, int npair);
+size_t pair_plane_smem(int n1, int n2, int m1max);
+int pair_density_ctas(int n2, int n3);
+size_t pair_density_smem(int n1, int n2, int m1max);
+bool zpair_ok(int n3);
+int zpair_ctas(int ncp, int npair);
+size_t zpair_smem(int n3);
+void launch_plane_vpsi_pair(const Launch& L, size_t smem);
+void launch_plane_density_pair(const Launch& L, size_t smem, const double* occ_override);
+void launch_wave_to_cols_pair(const Launch& L, size_t smem, int src);
+void launch_cols_to_wave_pair(const Launch& L, size_t smem, int src, int dst);
+bool pair_reg_init();
+void pair_reg_set_smem_limits(size_t bytes);
 void launch_plane_vpsi_reg(const Launch& L, int cls, size_t smem);
 size_t plane_density_reg_smem(int n1, int n2, int m1max);
 int plane_density_reg_ctas(int n2, int n3);
@@ -107,7 +124,7 @@ template <typename T> void launch_random_init(const Launch& L, int xrole, unsign
 template <typename T> void launch_copy_in(const Launch& L, int role, const double* src, int nvec);
 template <typename T> void launch_copy_out(const Launch& L, int role, double* dst, int nvec);
 void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride);
-void launch_rr_f32(const Launch& L, size_t smem);
+void launch_rr_f32(const Launch& L, size_t smem, float* gscratch = nullptr, size_t gstride = 0);
 void launch_occupations(const Launch& L);
 void launch_finish_cg(const Launch& L);
 void linalg_set_smem_limits(size_t bytes);

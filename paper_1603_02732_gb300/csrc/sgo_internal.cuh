@@ -222,6 +222,9 @@ struct WorkMap {
   int* start = nullptr;  // device [nprob+1]
   int total = 0;
   int maxper = 0;
+  // largest grid / band dimensions over the problems with work in this map (shared-memory
+  // sizes of its launches); -1 = not set (use the batch's)
+  int max_n1 = -1, max_n2 = -1, max_n3 = -1, max_n12 = -1, max_nb = -1;
 };
 
 __device__ __forceinline__ int locate(const int* __restrict__ start, int nprob, int blk) {

@@ -1,7 +1,8 @@
 """Parity at the workloads' full sizes, on outputs the oracle can compute one by one.
 
-* H psi of a few vectors at the 2D-monolayer (48x48x96, 10617 plane waves) and metal
-  cluster (72^3, 22119 plane waves) sizes vs the oracle's FFT-applied H.
+* H psi of a few vectors at the 2D-monolayer (48x48x96, 10617 plane waves), metal cluster
+  (72^3, 22119 plane waves) and large cluster (128^3, 93885 plane waves, mixed path) sizes vs
+  the oracle's FFT-applied H.
 * The 64-member DE population, evaluated as one mixed-precision batch in the launch
   configuration bench.py times, vs full oracle SCF runs of its two smallest members
   (energy 1e-5 Ha/atom, forces 1e-4 Ha/bohr).
@@ -27,9 +28,11 @@ def sgo():
     return pkg
 
 
-@pytest.mark.parametrize("name", ["honeycomb24", "cluster13"])
+@pytest.mark.parametrize("name", ["honeycomb24", "cluster13", "cluster55"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 3e-5)])
 def test_fullsize_hpsi_sampled(sgo, name, precision, tol):
+    if name == "cluster55" and precision == "fp64":
+        pytest.skip("128 x 128 planes: the FP64 path's shared-memory plane kernels do not take them")
     st = workloads.CONFIGS[name]()
     ctx = sgo.Context(st, precision=precision)
     m = dft.Model(st)

@@ -344,7 +344,8 @@ def run_ours(args):
                                 l2="flushed by a 256 MiB write before every timed step",
                                 converged=f"{n_ok}/{MEMBERS}", scf_options=dict(_SCF),
                                 scf_iterations=dict(mean=float(np.mean(iters)), max=int(np.max(iters))),
-                                jacobi_sweeps=dict(mean=float(np.mean(sweeps)), max=int(np.max(sweeps)))),
+                                jacobi_sweeps=dict(mean=float(np.mean(sweeps)), max=int(np.max(sweeps))),
+                                autotuned=batch.tuning()),
                     e2e=dict(value=e2e_val, unit="evals/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     graph_loop=dict(value=ws * MEMBERS * args.steps / (graph_ms / 1e3), unit="evals/s",
                                     note="device-resident steps through the default graph-driven SCF loop; "

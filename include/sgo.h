@@ -89,6 +89,8 @@ typedef struct {
                              iterations under a conditional WHILE node that the device ends
                              (1, default); 0 = one host launch per kernel and a host check per
                              iteration.  Results are identical.  Taken from the first member. */
+  int autotune;           /* batches: time the GEMM tile candidates at creation and keep the fastest
+                             (1, default); 0 = fixed defaults.  Taken from the first member. */
 } sgo_opts;
 
 /* Fill *o with the defaults (FP64, kT 0, tolerances 1e-8 Ha / 1e-7, Pulay 8, ...). */
@@ -121,6 +123,13 @@ SGO_API sgo_status sgo_energy_forces(sgo_ctx* ctx, const double* pos, double* en
  * GPU becomes one population per GPU).  The contexts stay owned by the caller and
  * must outlive the batch. */
 SGO_API sgo_status sgo_batch_create(int n, sgo_ctx* const* ctxs, sgo_batch** out);
+
+/* The GEMM tile knobs the batch's autotuner picked when the batch was created (mixed path;
+ * the defaults otherwise): knobs[0] = K chunk of the tensor-core TN GEMM (of 256, 512, 1024,
+ * 2048), knobs[1] = 128-wave tiles per tensor-core NN CTA (of 2, 4, 8, 16), knobs[2] = K
+ * chunk of the CUDA-core TN GEMM (of 128, 256, 512).  Each candidate is timed on the batch's
+ * own buffers; the fastest is kept. */
+SGO_API sgo_status sgo_batch_tuning(const sgo_batch* batch, int* knobs);
 
 /* Evaluate every member.  pos[i] (host, natoms_i*3) or NULL = keep; energies[i];
  * forces[i] (host, natoms_i*3, may be NULL); per_item[i] = status of member i.

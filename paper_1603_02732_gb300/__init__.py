@@ -46,7 +46,8 @@ class sgo_opts(ctypes.Structure):
                 ("scf_tol_rho", ctypes.c_double), ("max_scf", ctypes.c_int), ("pulay_hist", ctypes.c_int),
                 ("mix_alpha", ctypes.c_double), ("kerker_q0", ctypes.c_double), ("ncg", ctypes.c_int),
                 ("ncg_first", ctypes.c_int), ("n_nonscf", ctypes.c_int), ("fft", ctypes.c_int * 3),
-                ("seed", ctypes.c_ulonglong), ("gemm_tc", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("gemm_tc", ctypes.c_int), ("graph", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -76,6 +77,7 @@ _SIGS = {
     "sgo_apply_hamiltonian_noalloc": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
     "sgo_subspace_matrix": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
     "sgo_block_update": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
+    "sgo_batch_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
     "sgo_set_warm": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sgo_batch_destroy": (None, [_vp]),
@@ -312,6 +314,12 @@ class Batch:
         out = np.zeros(4)
         _check(self.lib.sgo_batch_timer_read(self.h, _ptr(out)), "sgo_batch_timer_read")
         return dict(ms=out[0], launches=int(out[1]), bytes=out[2], flops=out[3])
+
+    def tuning(self):
+        """GEMM tile knobs the batch's autotuner picked (see include/sgo.h)."""
+        k = (ctypes.c_int * 3)()
+        _check(self.lib.sgo_batch_tuning(self.h, k), "sgo_batch_tuning")
+        return dict(tn_tc_k_chunk=k[0], nn_tc_tiles_per_cta=k[1], tn_simt_k_chunk=k[2])
 
     def launches(self) -> int:
         """Kernel launches issued since the previous call."""

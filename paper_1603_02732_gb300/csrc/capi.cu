@@ -43,6 +43,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->seed = 12345ull;
   o->gemm_tc = 1;
   o->graph = 1;
+  o->autotune = 1;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,
@@ -146,7 +147,18 @@ sgo_status sgo_batch_create(int n, sgo_ctx* const* ctxs, sgo_batch** out) {
     return SGO_ERR_CUDA;
   }
   b->eng->enable_graphs(b->ctxs[0]->opts.graph != 0);
+  if (b->ctxs[0]->opts.autotune) b->eng->autotune();
+  if (!b->eng->ok() || cudaStreamSynchronize(b->ctxs[0]->stream) != cudaSuccess) {
+    delete b;
+    return SGO_ERR_CUDA;
+  }
   *out = b;
+  return SGO_OK;
+}
+
+sgo_status sgo_batch_tuning(const sgo_batch* b, int* knobs) {
+  if (!b || !knobs) return SGO_ERR_ARG;
+  b->eng->tuning(knobs);
   return SGO_OK;
 }
 

@@ -491,6 +491,69 @@ WorkMap Engine::make_map(const std::vector<int>& counts) {
   return m;
 }
 
+// Maps of the GEMMs whose CTA counts follow the tile knobs.
+void Engine::build_gemm_maps() {
+  std::vector<int> ww, bw, dw, tc, nntc;
+  for (auto* c : ctx_) {
+    const Prob& d = c->d;
+    const int nsplit = div_up(d.npw, tn_kc_);
+    const int tw = div_up(d.nb, TN_TILE), ta = div_up(d.natom, TN_TILE), td = div_up(3 * d.natom, TN_TILE);
+    ww.push_back(tw * tw * nsplit);
+    bw.push_back(ta * tw * nsplit);
+    dw.push_back(td * tw * nsplit);
+    tc.push_back(div_up(d.npw, tc_kc_));
+    nntc.push_back(div_up(div_up(d.npw, 128), nn_tpc_));
+  }
+  m_tn_ww_ = make_map(ww);
+  m_tn_bw_ = make_map(bw);
+  m_tn_dw_ = make_map(dw);
+  m_tc_ = make_map(tc);
+  m_nntc_ = make_map(nntc);
+}
+
+// Autotuner of the GEMM tile knobs (mixed path): for each knob, every candidate runs its
+// GEMM on this batch's own buffers (one warm-up, then three timed launches on the
+// engine's stream, CUDA events) and the fastest is kept.  The contents of the scratch
+// matrices it overwrites are recomputed by every evaluation.
+void Engine::autotune() {
+  if (!ok_ || precision_ != 1) return;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (!cuda_ok(cudaEventCreate(&a), "autotune event") || !cuda_ok(cudaEventCreate(&b), "autotune event")) return;
+  const long long l0 = launches_;
+  auto time_of = [&](auto&& fn) {
+    fn();
+    cudaEventRecord(a, stream_);
+    for (int r = 0; r < 3; ++r) fn();
+    cudaEventRecord(b, stream_);
+    cudaEventSynchronize(b);
+    float ms = 1e30f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = 1e30f;
+    return ms;
+  };
+  auto pick = [&](int* knob, std::initializer_list<int> cands, auto&& fn) {
+    int best = *knob;
+    float tbest = 1e30f;
+    for (int v : cands) {
+      *knob = v;
+      build_gemm_maps();
+      const float t = time_of(fn);
+      if (t < tbest) {
+        tbest = t;
+        best = v;
+      }
+    }
+    *knob = best;
+    build_gemm_maps();
+  };
+  if (tc_ok_[OPK_WB]) pick(&tc_kc_, {256, 512, 1024, 2048}, [&] { tn<float>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS); });
+  pick(&tn_kc_, {128, 256, 512}, [&] { tn<float>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S, false); });
+  if (nn_tc_ok_[OPK_WB]) pick(&nn_tpc_, {2, 4, 8, 16}, [&] { nn<float>(OPK_WB, WB_X, DD_TM, WB_W, 1.0, 0.0); });
+  cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  launches_ = l0;
+}
+
 Launch Engine::L(const WorkMap& m) const {
   if (m.total > 0) ++launches_;  // an empty map launches nothing
   Launch l;
@@ -531,8 +594,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     max_nb_ = std::max(max_nb_, d.nb);
     const int nch = div_up(d.ngrid, GRID_CHUNK);
     maxchunk_ = std::max(maxchunk_, nch);
-    const int nsplit = div_up(d.npw, TN_KC);
-    const int tw = div_up(d.nb, TN_TILE), ta = div_up(d.natom, TN_TILE), td = div_up(3 * d.natom, TN_TILE);
+    const int nsplit = div_up(d.npw, 128);  // the smallest CUDA-core K chunk the autotuner tries
     // z-column passes: register FFTs on the mixed path where n3 has one (single thread or
     // lane pair per line), the shared-memory engine otherwise
     const bool zreg = precision_ == 1 && zreg_ok(d.n3);
@@ -578,9 +640,6 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     c_gew.push_back(div_up(d.ngrid, GRID_EW_POINTS));
     c_gch.push_back(nch);
     c_bands.push_back(d.nb);
-    c_tnww.push_back(tw * tw * nsplit);
-    c_tnbw.push_back(ta * tw * nsplit);
-    c_tndw.push_back(td * tw * nsplit);
     c_rww.push_back(div_up(d.nb * d.nb, 256));
     c_rbw.push_back(div_up(d.natom * d.nb, 256));
     c_rdw.push_back(div_up(3 * d.natom * d.nb, 256));
@@ -589,8 +648,6 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     c_atomch.push_back(div_up(d.natom, LF_GROUP) * nch);
     c_ewsg.push_back(div_up(ctxs[p]->ngbox_ew, 256));
     c_prob.push_back(1);
-    c_tc.push_back(div_up(d.npw, TC_KC));
-    c_nntc.push_back(div_up(div_up(d.npw, 128), NN_TPC));
     max_natom = std::max(max_natom, d.natom);
     size_t need = (size_t)nsplit * std::max({d.nb * d.nb, d.natom * d.nb, 3 * d.natom * d.nb});
     part = std::max(part, need);
@@ -612,9 +669,6 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   m_gew_ = make_map(c_gew);
   m_gch_ = make_map(c_gch);
   m_bands_ = make_map(c_bands);
-  m_tn_ww_ = make_map(c_tnww);
-  m_tn_bw_ = make_map(c_tnbw);
-  m_tn_dw_ = make_map(c_tndw);
   m_red_ww_ = make_map(c_rww);
   m_red_bw_ = make_map(c_rbw);
   m_red_dw_ = make_map(c_rdw);
@@ -623,8 +677,6 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   m_atomch_ = make_map(c_atomch);
   m_ewsg_ = make_map(c_ewsg);
   m_prob_ = make_map(c_prob);
-  m_tc_ = make_map(c_tc);
-  m_nntc_ = make_map(c_nntc);
   // tensor-core subspace GEMMs: mixed path, every operand count <= 128 (one M tile, one
   // NN image of at most 128 x 128), at least two NN pipeline stages beside the image
   const bool tc = precision_ == 1 && ctxs[0]->opts.gemm_tc != 0;
@@ -637,6 +689,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     nn_tc_ok_[k] = tc_ok_[k] && nn_tc_stages(nnimg_max_[k]) >= 2;
   }
   part_stride_ = part;
+  build_gemm_maps();
   if (!cuda_ok(cudaMalloc(&d_probs_, sizeof(Prob) * n_), "cudaMalloc(probs)")) return;
   allocs_.push_back(d_probs_);
   cudaMemcpy(d_probs_, host.data(), sizeof(Prob) * n_, cudaMemcpyHostToDevice);
@@ -835,11 +888,11 @@ void Engine::tn(int akind, int arole, int bkind, int brole, int dst, bool allow_
   const int kind = akind == OPK_WB ? TK_GEMM_TN : TK_GEMM_SMALL;
   tbeg(kind);
   if (sizeof(T) == 4 && allow_tc && tc_ok_[akind]) {
-    launch_gemm_tn_tc(L(m_tc_), d_tmaps_, akind, arole, bkind, brole, d_part_, part_stride_);
-    launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_, TC_KC);
+    launch_gemm_tn_tc(L(m_tc_), d_tmaps_, akind, arole, bkind, brole, d_part_, part_stride_, tc_kc_);
+    launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_, tc_kc_);
   } else {
-    launch_gemm_tn<T>(L(*m), akind, arole, bkind, brole, d_part_, part_stride_);
-    launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_);
+    launch_gemm_tn<T>(L(*m), akind, arole, bkind, brole, d_part_, part_stride_, tn_kc_);
+    launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_, tn_kc_);
   }
   tend(kind);
 }
@@ -852,7 +905,7 @@ void Engine::nn(int akind, int arole, int msel, int yrole, double alpha, double 
   if (sizeof(T) == 4 && nn_tc_ok_[akind]) {
     if (!image_ready) launch_nn_image(L(m_prob_), akind, msel, d_nnimg_, nnimg_stride_);
     launch_gemm_nn_tc(L(m_nntc_), d_tmaps_, d_nnimg_, nnimg_stride_, nnimg_max_[akind], akind, arole, yrole, alpha,
-                      beta);
+                      beta, nn_tpc_);
   } else {
     launch_gemm_nn<T>(L(m_nn_), akind, arole, msel, yrole, alpha, beta);
   }

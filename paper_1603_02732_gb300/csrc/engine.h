@@ -82,6 +82,13 @@ class Engine {
   }
   // Drive the SCF loop by captured CUDA graphs (batch engines); see build_graphs().
   void enable_graphs(bool on) { use_graph_ = on; }
+  // Pick the GEMM tile knobs by timing candidates on this batch (see autotune()).
+  void autotune();
+  void tuning(int* out) const {
+    out[0] = tc_kc_;
+    out[1] = nn_tpc_;
+    out[2] = tn_kc_;
+  }
   // Batch evaluation with positions, energies, forces and statuses in device memory.
   sgo_status run_device(const double* pos, double* energies, double* forces, int* status);
 
@@ -159,6 +166,10 @@ class Engine {
   // graph mode: captured iterations, the device iteration counter, a private stream (the
   // caller's may be the legacy default stream, which cannot be captured)
   bool use_graph_ = false;
+  // GEMM tile knobs: K chunk of the tensor-core TN, 128-wave tiles per NN CTA, K chunk of
+  // the CUDA-core TN; the maps that depend on them
+  int tc_kc_ = TC_KC, nn_tpc_ = NN_TPC, tn_kc_ = TN_KC;
+  void build_gemm_maps();
   cudaGraphExec_t g_nonscf_ = nullptr, g_scf_ = nullptr;
   long long graph_launches_[2] = {0, 0};
   int* d_iter_ = nullptr;

@@ -17,13 +17,13 @@
 // Every wait is bounded (clock64); a timeout sets status[2] of the problem, and the CTA
 // still waits (bounded) for its own loads and MMAs in flight, frees TMEM and returns.
 //
-// TN (C = A^T B, split-K): CTA = (problem, K chunk of TC_KC).  A rows (M = 128 TMEM
+// TN (C = A^T B, split-K): CTA = (problem, K chunk of kc, TC_KC by default).  A rows (M = 128 TMEM
 // lanes) and B rows (N = count rounded up to 16) are K-major tiles of 32 K (128 bytes),
 // packed to the operand counts rounded up to 8 rows (one TMA box each), so that short
 // operands buy deeper pipelines.  Each CTA writes its FP32 partial as FP64;
 // k_gemm_tn_reduce adds the chunks in order.
 //
-// NN (Y = alpha X M + beta Y): CTA = (problem, NN_TPC tiles of 128 plane waves).  The
+// NN (Y = alpha X M + beta Y): CTA = (problem, tpc tiles of 128 plane waves, NN_TPC by default).  The
 // MMA's M is the plane-wave index, K the input row and N the output band.  TMA lands X
 // as 32-row x 32-wave boxes (rows of X along K); the converter warps transpose each
 // 4 x 4 block while splitting, into a K-major A tile [128 waves][32 rows], the same
@@ -239,7 +239,7 @@ __device__ __forceinline__ const double* dense_tc(const Prob& P, int sel) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(TN_THREADS, 1)
     k_gemm_tn_tma(KArgs ka, const CUtensorMap* __restrict__ maps, int akind, int arole, int bkind, int brole,
-                  double* part_base, size_t part_stride) {
+                  double* part_base, size_t part_stride, int kc) {
   extern __shared__ unsigned char smem_dyn[];
   __shared__ __align__(8) uint64_t full[TN_MAX_STAGES], conv[TN_MAX_STAGES], empty[TN_MAX_STAGES], done;
   __shared__ uint32_t tmem_base;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
   const int stage_bytes = 2 * (ra + rb) * 128;
   const int nst = min(TN_MAX_STAGES, (TN_SMEM - 1024 - TN_PAD) / stage_bytes);
   const int split = blockIdx.x - ka.start[p];
-  const int k0 = split * TC_KC, k1 = min(P.npw, k0 + TC_KC);
+  const int k0 = split * kc, k1 = min(P.npw, k0 + kc);
   const int nsteps = (k1 - k0 + TC_K - 1) / TC_K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 1) {
@@ -399,7 +399,7 @@ __global__ void k_nn_image(KArgs ka, int akind, int msel, float* img_base, size_
 __global__ void __launch_bounds__(NN_THREADS, 1)
     k_gemm_nn_tma(KArgs ka, const CUtensorMap* __restrict__ maps, const float* __restrict__ img_base,
                   size_t img_stride, int img_max, int nstages, int akind, int arole, int yrole, float alpha,
-                  float beta) {
+                  float beta, int tpc) {
   extern __shared__ unsigned char smem_dyn[];
   __shared__ __align__(8) uint64_t full[NN_MAX_STAGES], conv[NN_MAX_STAGES], empty[NN_MAX_STAGES], tfull[2],
       tempty[2], imgbar, done;
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
   const int npad = (nb + 15) & ~15, kpad = (nin + 31) & ~31, nkc = kpad / 32;
   const int img_half = npad * kpad * 4;
   const int ntile = (npw + 127) / 128;
-  const int t0 = (blockIdx.x - ka.start[p]) * NN_TPC, t1 = min(ntile, t0 + NN_TPC);
+  const int t0 = (blockIdx.x - ka.start[p]) * tpc, t1 = min(ntile, t0 + tpc);
   const int ntl = t1 - t0, niter = ntl * nkc;
   const uint32_t tcols = npad <= 64 ? 128u : 256u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -626,10 +626,10 @@ int nn_tc_stages(int img_bytes) {
 }
 
 void launch_gemm_tn_tc(const Launch& L, const void* maps, int akind, int arole, int bkind, int brole, double* part,
-                       size_t stride) {
+                       size_t stride, int kc) {
   if (!L.map.total) return;
   k_gemm_tn_tma<<<L.map.total, TN_THREADS, TN_SMEM, L.stream>>>(
-      L.ka, reinterpret_cast<const CUtensorMap*>(maps), akind, arole, bkind, brole, part, stride);
+      L.ka, reinterpret_cast<const CUtensorMap*>(maps), akind, arole, bkind, brole, part, stride, kc);
 }
 
 void launch_nn_image(const Launch& Lprob, int akind, int msel, float* img, size_t img_stride) {
@@ -637,13 +637,13 @@ void launch_nn_image(const Launch& Lprob, int akind, int msel, float* img, size_
 }
 
 void launch_gemm_nn_tc(const Launch& L, const void* maps, const float* img, size_t img_stride, int img_max,
-                       int akind, int arole, int yrole, double alpha, double beta) {
+                       int akind, int arole, int yrole, double alpha, double beta, int tpc) {
   if (!L.map.total) return;
   const int img_al = (img_max + 1023) & ~1023;
   const int ns = nn_tc_stages(img_max);
   k_gemm_nn_tma<<<L.map.total, NN_THREADS, 1024 + img_al + ns * NN_STAGE, L.stream>>>(
       L.ka, reinterpret_cast<const CUtensorMap*>(maps), img, img_stride, img_al, ns, akind, arole, yrole,
-      (float)alpha, (float)beta);
+      (float)alpha, (float)beta, tpc);
 }
 
 void gemm_tc_set_smem_limits() {

@@ -45,7 +45,7 @@ __device__ __forceinline__ double* dense_ptr(const Prob& P, int sel) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole, int bkind, int brole, double* part_base,
-                                                size_t part_stride) {
+                                                size_t part_stride, int kc) {
   __shared__ T As[32][TN_TILE + 1];
   __shared__ T Bs[32][TN_TILE + 1];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole,
   const T* A = opnd<T>(P, akind, arole);
   const T* Bm = opnd<T>(P, bkind, brole);
   const int ld = P.ld;
-  const int k0 = split * TN_KC, k1 = min(P.npw, k0 + TN_KC);
+  const int k0 = split * kc, k1 = min(P.npw, k0 + kc);
   const int t = threadIdx.x;
   const int ti = t & 15, tj = t >> 4;
   T acc[4][4];
@@ -961,9 +961,10 @@ __global__ void k_finish_cg(KArgs ka) {
 // launchers
 // ---------------------------------------------------------------------------
 template <typename T>
-void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride) {
+void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride,
+                    int kc) {
   if (!L.map.total) return;
-  k_gemm_tn<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, arole, bkind, brole, part, stride);
+  k_gemm_tn<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, arole, bkind, brole, part, stride, kc);
 }
 void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride, int kc) {
   if (!L.map.total) return;
@@ -1027,7 +1028,7 @@ void linalg_set_smem_limits(size_t bytes) {
 }
 
 #define INST(T)                                                                                  \
-  template void launch_gemm_tn<T>(const Launch&, int, int, int, int, double*, size_t);          \
+  template void launch_gemm_tn<T>(const Launch&, int, int, int, int, double*, size_t, int);     \
   template void launch_gemm_nn<T>(const Launch&, int, int, int, int, double, double);           \
   template void launch_band_kinetic<T>(const Launch&, int);                                     \
   template void launch_cg_precond<T>(const Launch&, int, int, int, int, int, int);              \

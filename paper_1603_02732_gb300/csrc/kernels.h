@@ -97,7 +97,8 @@ void launch_plane_density_reg(const Launch& L, int cls, size_t smem, const doubl
 
 // k_linalg.cu
 template <typename T>
-void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride);
+void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride,
+                    int kc = TN_KC);
 void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride,
                            int kc = TN_KC);
 // k_gemm_tc.cu (tcgen05 + TMA, mixed path, operand counts <= 128)
@@ -109,10 +110,10 @@ bool tc_encode_maps(const Prob& d, void* host_maps);  // TC_NSLOT * TC_NMAPKIND 
 int nn_tc_image_bytes(int nin, int nb);
 int nn_tc_stages(int img_bytes);
 void launch_gemm_tn_tc(const Launch& L, const void* maps, int akind, int arole, int bkind, int brole, double* part,
-                       size_t stride);
+                       size_t stride, int kc = TC_KC);
 void launch_nn_image(const Launch& Lprob, int akind, int msel, float* img, size_t img_stride);
 void launch_gemm_nn_tc(const Launch& L, const void* maps, const float* img, size_t img_stride, int img_max,
-                       int akind, int arole, int yrole, double alpha, double beta);
+                       int akind, int arole, int yrole, double alpha, double beta, int tpc = NN_TPC);
 void gemm_tc_set_smem_limits();
 template <typename T>
 void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta);

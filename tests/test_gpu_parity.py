@@ -281,7 +281,7 @@ def test_graph_loop_equals_host_loop(sgo):
     for prec, tol in (("fp64", dict(scf_tol_e=1e-10, scf_tol_rho=1e-8)), ("mixed", dict(scf_tol_e=1e-7, scf_tol_rho=1e-5))):
         res = {}
         for graph in (0, 1):
-            ctxs = [sgo.Context(st, precision=prec, graph=graph, max_scf=100, **tol) for st in sts]
+            ctxs = [sgo.Context(st, precision=prec, graph=graph, autotune=0, max_scf=100, **tol) for st in sts]
             b = sgo.Batch(ctxs)
             E, F, status = b.energy_forces()
             E2, F2, status2 = b.energy_forces()  # second call replays the cached graphs
@@ -292,3 +292,26 @@ def test_graph_loop_equals_host_loop(sgo):
         for i in range(3):
             assert np.array_equal(res[0][1][i], res[1][1][i]), prec
         assert res[0][2] == res[1][2], prec
+
+
+def test_autotuned_batch(sgo):
+    """The autotuner keeps one of its candidates for each knob, and the tuned batch's
+    energies and forces agree with the default-knob batch to the mixed tolerances (the knobs
+    change only the split-K summation order)."""
+    sts = [workloads.de_candidate(i) for i in (0, 5)]
+    import bench
+    res = {}
+    for tune in (0, 1):
+        ctxs = [sgo.Context(st, precision="mixed", autotune=tune, **bench._tols("mixed", st)) for st in sts]
+        b = sgo.Batch(ctxs)
+        E, F, status = b.energy_forces()
+        assert list(status) == [0, 0]
+        res[tune] = (E, F, b.tuning())
+    k = res[1][2]
+    assert k["tn_tc_k_chunk"] in (256, 512, 1024, 2048)
+    assert k["nn_tc_tiles_per_cta"] in (2, 4, 8, 16)
+    assert k["tn_simt_k_chunk"] in (128, 256, 512)
+    assert res[0][2] == dict(tn_tc_k_chunk=512, nn_tc_tiles_per_cta=4, tn_simt_k_chunk=256)
+    for i, st in enumerate(sts):
+        assert abs(res[0][0][i] - res[1][0][i]) / st.natoms < 2e-6
+        assert np.abs(res[0][1][i] - res[1][1][i]).max() < 5e-5

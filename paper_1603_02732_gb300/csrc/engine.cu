@@ -854,25 +854,27 @@ void Engine::set_scal(int idx, double v, bool only_active) {
   k_set_scal<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, idx, v, only_active ? 1 : 0);
 }
 
-void Engine::grid_fft(int which, int sign) {
+void Engine::grid_fft(int which, int sign, bool fp32) {
   tbeg(TK_GRID_FFT);
-  grid_fft_raw(which, sign);
+  if (fp32) grid_fft_raw<float>(which, sign);
+  else grid_fft_raw<double>(which, sign);
   tend(TK_GRID_FFT);
 }
 
+template <typename T>
 void Engine::grid_fft_raw(int which, int sign) {
   // forward: planes (y, x), then z; inverse: z, then planes.  Large planes go by line
   // blocks along y and x.
   auto planes = [&](int sg) {
-    launch_grid_plane_fft(L(m_gp_), which, sg);
-    launch_grid_line_fft(L(m_gy_), which, sg, 1);
-    launch_grid_line_fft(L(m_gx_), which, sg, 0);
+    launch_grid_plane_fft<T>(L(m_gp_), which, sg);
+    launch_grid_line_fft<T>(L(m_gy_), which, sg, 1);
+    launch_grid_line_fft<T>(L(m_gx_), which, sg, 0);
   };
   if (sign < 0) {
     planes(-1);
-    launch_grid_z_fft(L(m_gz_), which, -1);
+    launch_grid_z_fft<T>(L(m_gz_), which, -1);
   } else {
-    launch_grid_z_fft(L(m_gz_), which, 1);
+    launch_grid_z_fft<T>(L(m_gz_), which, 1);
     planes(1);
   }
 }
@@ -1027,8 +1029,10 @@ void Engine::scf_iteration(int ncg, bool count_iter) {
   const sgo_opts& o = ctx_[0]->opts;
   // V_eff from rho_in(G): one inverse transform of rho_in(G) + i V_H(G) gives
   // rho_in(r) + i V_H(r); LDA in real space
+  // (in FP64 on both paths: an FP32 transform, measured, slows the SCF of some members:
+  // its absolute error swamps rho_in(r) where the density is small, and v_xc follows it)
   tbeg(TK_GRID_OTHER);
-  launch_potential_g(L(m_gew_));
+  launch_potential_g<double>(L(m_gew_));
   tend(TK_GRID_OTHER);
   grid_fft(0, 1);
   tbeg(TK_GRID_OTHER);

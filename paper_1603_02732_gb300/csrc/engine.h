@@ -104,8 +104,8 @@ class Engine {
   template <typename T>
   void nn(int akind, int arole, int msel, int yrole, double alpha, double beta, bool image_ready = false);
   template <typename T> void rotate(int role, bool image_ready);
-  void grid_fft(int which, int sign);
-  void grid_fft_raw(int which, int sign);
+  void grid_fft(int which, int sign, bool fp32 = false);
+  template <typename T> void grid_fft_raw(int which, int sign);
   void potential();
   void energies_at_rho_out(bool count_iter);
   void pulay();

@@ -271,8 +271,14 @@ __global__ void __launch_bounds__(PLANE_THREADS, sizeof(T) == 4 ? PLANE_MIN_BLOC
 // Full FP64 complex grid transforms (in place): plane pass (x and y) and z pass.
 // which: 0 = gfft, 1 = gfft2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double2* grid_of(const Prob& P, int which) { return which ? P.gfft2 : P.gfft; }
+// The work grids in the working precision of a transform: FP64 complex, or (FP32) the
+// first half of the same memory viewed as single-precision complex.
+template <typename T>
+__device__ __forceinline__ cplx<T>* grid_of(const Prob& P, int which) {
+  return reinterpret_cast<cplx<T>*>(which ? P.gfft2 : P.gfft);
+}
 
+template <typename T>
 __global__ void __launch_bounds__(PLANE_THREADS) k_grid_plane_fft(KArgs ka, int which, int sign) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
@@ -280,21 +286,22 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_grid_plane_fft(KArgs ka, int 
   const Prob& P = ka.probs[p];
   const int z = blockIdx.x - ka.start[p];
   const int n1 = P.n1, n2 = P.n2, n12 = n1 * n2;
-  cplx<double>* b0 = reinterpret_cast<cplx<double>*>(smem_raw);
-  cplx<double>* b1 = b0 + n12;
-  cplx<double>* r1 = b1 + n12;
-  cplx<double>* r2 = r1 + n1;
-  load_roots<double>(r1, P, 0, n1);
-  load_roots<double>(r2, P, n1, n2);
-  cplx<double>* g = reinterpret_cast<cplx<double>*>(grid_of(P, which)) + (size_t)z * n12;
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* b1 = b0 + n12;
+  cplx<T>* r1 = b1 + n12;
+  cplx<T>* r2 = r1 + n1;
+  load_roots<T>(r1, P, 0, n1);
+  load_roots<T>(r2, P, n1, n2);
+  cplx<T>* g = grid_of<T>(P, which) + (size_t)z * n12;
   for (int t = threadIdx.x; t < n12; t += blockDim.x) b0[t] = g[t];
   __syncthreads();
-  const double sg = sign < 0 ? -1.0 : 1.0;
-  cplx<double>* cur = fft_lines<double>(b0, b1, n1, n2, 1, contiguous(n1), P.fd[1], r2, sg);  // y
-  cur = fft_lines<double>(cur, cur == b0 ? b1 : b0, n2, 1, n2, contiguous(n2), P.fd[0], r1, sg);  // x
+  const T sg = sign < 0 ? T(-1) : T(1);
+  cplx<T>* cur = fft_lines<T>(b0, b1, n1, n2, 1, contiguous(n1), P.fd[1], r2, sg);      // y
+  cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, n2, 1, n2, contiguous(n2), P.fd[0], r1, sg);  // x
   for (int t = threadIdx.x; t < n12; t += blockDim.x) g[t] = cur[t];
 }
 
+template <typename T>
 __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_z_fft(KArgs ka, int which, int sign) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
@@ -303,18 +310,17 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_z_fft(KArgs ka, int which
   const int chunk = blockIdx.x - ka.start[p];
   const int n12 = P.n1 * P.n2, n3 = P.n3;
   const int c0 = chunk * QZ, nc = min(QZ, n12 - c0);
-  cplx<double>* lines = reinterpret_cast<cplx<double>*>(smem_raw);
-  cplx<double>* alt = lines + QZ * n3;
-  cplx<double>* roots = alt + QZ * n3;
-  load_roots<double>(roots, P, P.n1 + P.n2, n3);
-  cplx<double>* g = reinterpret_cast<cplx<double>*>(grid_of(P, which));
+  cplx<T>* lines = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* alt = lines + QZ * n3;
+  cplx<T>* roots = alt + QZ * n3;
+  load_roots<T>(roots, P, P.n1 + P.n2, n3);
+  cplx<T>* g = grid_of<T>(P, which);
   for (int t = threadIdx.x; t < nc * n3; t += blockDim.x) {
     int z = t / nc, c = t - z * nc;
     lines[c * n3 + z] = g[(size_t)z * n12 + c0 + c];
   }
   __syncthreads();
-  const cplx<double>* res =
-      fft_lines<double>(lines, alt, nc, n3, 1, contiguous(nc), P.fd[2], roots, sign < 0 ? -1.0 : 1.0);
+  const cplx<T>* res = fft_lines<T>(lines, alt, nc, n3, 1, contiguous(nc), P.fd[2], roots, sign < 0 ? T(-1) : T(1));
   for (int t = threadIdx.x; t < nc * n3; t += blockDim.x) {
     int z = t / nc, c = t - z * nc;
     g[(size_t)z * n12 + c0 + c] = res[c * n3 + z];
@@ -324,6 +330,7 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_z_fft(KArgs ka, int which
 // Line blocks of the grid transform for planes too large for one CTA: along x (axis 0:
 // length N1, element stride N2, lines (z, i2)) or y (axis 1: length N2, contiguous, lines
 // (z, i1)), QZ lines per CTA, loads and stores coalesced across the lines' fast index.
+template <typename T>
 __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_line_fft(KArgs ka, int which, int sign, int axis) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
@@ -334,11 +341,11 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_line_fft(KArgs ka, int wh
   const int n = axis ? n2 : n1;
   const int nlines = P.n3 * (axis ? n1 : n2);
   const int l0 = chunk * QZ, nc = min(QZ, nlines - l0);
-  cplx<double>* lines = reinterpret_cast<cplx<double>*>(smem_raw);
-  cplx<double>* alt = lines + QZ * n;
-  cplx<double>* roots = alt + QZ * n;
-  load_roots<double>(roots, P, axis ? n1 : 0, n);
-  cplx<double>* g = reinterpret_cast<cplx<double>*>(grid_of(P, which));
+  cplx<T>* lines = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* alt = lines + QZ * n;
+  cplx<T>* roots = alt + QZ * n;
+  load_roots<T>(roots, P, axis ? n1 : 0, n);
+  cplx<T>* g = grid_of<T>(P, which);
   auto at = [&](int c, int e) -> size_t {
     const int l = l0 + c;
     if (axis) return (size_t)l * n2 + e;
@@ -350,8 +357,8 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_line_fft(KArgs ka, int wh
     lines[c * n + e] = g[at(c, e)];
   }
   __syncthreads();
-  const cplx<double>* res =
-      fft_lines<double>(lines, alt, nc, n, 1, contiguous(nc), P.fd[axis ? 1 : 0], roots, sign < 0 ? -1.0 : 1.0);
+  const cplx<T>* res =
+      fft_lines<T>(lines, alt, nc, n, 1, contiguous(nc), P.fd[axis ? 1 : 0], roots, sign < 0 ? T(-1) : T(1));
   for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
     const int c = axis ? t / n : t % nc, e = axis ? t % n : t / nc;
     g[at(c, e)] = res[c * n + e];
@@ -385,21 +392,24 @@ void launch_plane_density(const Launch& L, const double* occ_override) {
   size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<T>) + (size_t)L.max_n12 * sizeof(double) + 16;
   k_plane_density<T><<<L.map.total, L.plane_threads, sm, L.stream>>>(L.ka, occ_override);
 }
+template <typename T>
 void launch_grid_line_fft(const Launch& L, int which, int sign, int axis) {
   if (!L.map.total) return;
   const int n = axis ? L.max_n2 : L.max_n1;
-  size_t sm = (size_t)(2 * QZ + 1) * n * sizeof(cplx<double>);
-  k_grid_line_fft<<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, which, sign, axis);
+  size_t sm = (size_t)(2 * QZ + 1) * n * sizeof(cplx<T>);
+  k_grid_line_fft<T><<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, which, sign, axis);
 }
+template <typename T>
 void launch_grid_plane_fft(const Launch& L, int which, int sign) {
   if (!L.map.total) return;
-  size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<double>);
-  k_grid_plane_fft<<<L.map.total, L.plane_threads, sm, L.stream>>>(L.ka, which, sign);
+  size_t sm = (size_t)(2 * L.max_n12 + L.max_n1 + L.max_n2) * sizeof(cplx<T>);
+  k_grid_plane_fft<T><<<L.map.total, L.plane_threads, sm, L.stream>>>(L.ka, which, sign);
 }
+template <typename T>
 void launch_grid_z_fft(const Launch& L, int which, int sign) {
   if (!L.map.total) return;
-  size_t sm = (size_t)(2 * QZ + 1) * L.max_n3 * sizeof(cplx<double>);
-  k_grid_z_fft<<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, which, sign);
+  size_t sm = (size_t)(2 * QZ + 1) * L.max_n3 * sizeof(cplx<T>);
+  k_grid_z_fft<T><<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, which, sign);
 }
 
 bool fft_reg_init() { return plane_vpsi_reg_init() && plane_density_reg_init() && zreg_init() && pair_reg_init(); }
@@ -413,9 +423,12 @@ void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_plane_vpsi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_plane_density<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_plane_density<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  cudaFuncSetAttribute(k_grid_plane_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  cudaFuncSetAttribute(k_grid_z_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  cudaFuncSetAttribute(k_grid_line_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_plane_fft<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_z_fft<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_line_fft<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_plane_fft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_z_fft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_line_fft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   plane_vpsi_reg_set_smem_limits(bytes);
   plane_density_reg_set_smem_limits(bytes);
   zreg_set_smem_limits(bytes);
@@ -426,6 +439,12 @@ template void launch_wave_to_cols<float>(const Launch&, int);
 template void launch_wave_to_cols<double>(const Launch&, int);
 template void launch_cols_to_wave<float>(const Launch&, int, int);
 template void launch_cols_to_wave<double>(const Launch&, int, int);
+template void launch_grid_line_fft<float>(const Launch&, int, int, int);
+template void launch_grid_line_fft<double>(const Launch&, int, int, int);
+template void launch_grid_plane_fft<float>(const Launch&, int, int);
+template void launch_grid_plane_fft<double>(const Launch&, int, int);
+template void launch_grid_z_fft<float>(const Launch&, int, int);
+template void launch_grid_z_fft<double>(const Launch&, int, int);
 template void launch_plane_vpsi<float>(const Launch&);
 template void launch_plane_vpsi<double>(const Launch&);
 template void launch_plane_density<float>(const Launch&, const double*);

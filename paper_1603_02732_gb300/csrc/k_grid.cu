@@ -166,15 +166,18 @@ __global__ void k_veff(KArgs ka, const double* user_v) {
   }
 }
 
-// Work grid := rho_in(G) + i V_H(G), V_H(G) = 4 pi rho_in(G) / |G|^2 (0 at G = 0).
+// Work grid := rho_in(G) + i V_H(G), V_H(G) = 4 pi rho_in(G) / |G|^2 (0 at G = 0), in the
+// precision of the transform that follows (T = float: the grid's single-precision view).
+template <typename T>
 __global__ void k_potential_g(KArgs ka) {
   GRID_EW_PROLOGUE
+  cplx<T>* g = reinterpret_cast<cplx<T>*>(P.gfft);
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
     const double g2 = P.g2box[i];  // -1 on Nyquist planes
     double2 r = P.rhog_in[i];
     double f = g2 < 1e-14 ? 0.0 : 4.0 * PI / g2;
     // (r.x + i r.y) + i f (r.x + i r.y)
-    P.gfft[i] = make_double2(r.x - f * r.y, r.y + f * r.x);
+    g[i] = mk((T)(r.x - f * r.y), (T)(r.y + f * r.x));
   }
 }
 
@@ -578,9 +581,12 @@ template <typename T>
 void launch_veff(const Launch& L, const double* user_v) {
   if (ew_blocks(L)) k_veff<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, user_v);
 }
+template <typename T>
 void launch_potential_g(const Launch& L) {
-  if (ew_blocks(L)) k_potential_g<<<L.map.total, 256, 0, L.stream>>>(L.ka);
+  if (ew_blocks(L)) k_potential_g<T><<<L.map.total, 256, 0, L.stream>>>(L.ka);
 }
+template void launch_potential_g<float>(const Launch&);
+template void launch_potential_g<double>(const Launch&);
 void launch_vion_g(const Launch& L) {
   if (ew_blocks(L)) k_vion_g<<<L.map.total, 256, 0, L.stream>>>(L.ka);
 }

@@ -52,9 +52,11 @@ template <typename T> void launch_wave_to_cols(const Launch& L, int src);
 template <typename T> void launch_cols_to_wave(const Launch& L, int src, int dst);
 template <typename T> void launch_plane_vpsi(const Launch& L);
 template <typename T> void launch_plane_density(const Launch& L, const double* occ_override);
-void launch_grid_plane_fft(const Launch& L, int which, int sign);
-void launch_grid_z_fft(const Launch& L, int which, int sign);
-void launch_grid_line_fft(const Launch& L, int which, int sign, int axis);  // axis 0: x, 1: y
+// grid transforms of the work grids (T = double; T = float views the first half of the
+// same memory as single-precision complex)
+template <typename T> void launch_grid_plane_fft(const Launch& L, int which, int sign);
+template <typename T> void launch_grid_z_fft(const Launch& L, int which, int sign);
+template <typename T> void launch_grid_line_fft(const Launch& L, int which, int sign, int axis);  // axis 0: x, 1: y
 void fft_set_smem_limits(size_t bytes);
 // register-FFT plane pass (mixed path): lengths n1, n2 with a register transform
 bool plane_reg_ok(int n1, int n2);
@@ -137,7 +139,7 @@ void launch_grid_real_part(const Launch& L, int which, int dst);
 void launch_hartree_g(const Launch& L, int which);
 void launch_export_grid(const Launch& L, int sel, double* out);
 template <typename T> void launch_veff(const Launch& L, const double* user_v);
-void launch_potential_g(const Launch& L);
+template <typename T> void launch_potential_g(const Launch& L);
 void launch_vion_g(const Launch& L);
 void launch_rho0_g(const Launch& L);
 void launch_pulay_store(const Launch& L);

@@ -1,13 +1,15 @@
 // Register-FFT plane pass of H.psi (mixed path, line lengths with a register transform;
 // the line transforms are in fft_reg.cuh).
-// CTA = (problem, band pair, block of Q = blockDim / N2 z-planes).  Shared memory holds
-// only the occupied x rows of each plane (|m1| <= m1max, compact row index rho), rows
-// padded to an odd length (N2 | 1) so that a thread per row and a thread per column
-// both touch 16 distinct 8-byte bank pairs per half warp, and the planes' V_eff / N.
-// Passes: scatter the compact columns (asynchronous copies to precomputed slots, the
-// potential following); y inverse (thread per occupied row); per column: x inverse of
-// the occupied rows, times V_eff/N, x forward, occupied rows back (thread per column,
-// the full column in registers); y forward; gather the compact columns.
+// CTA = (problem, group of PLANE_PAIR_GROUP band pairs, block of Q = blockDim / N2
+// z-planes).  Shared memory holds only the occupied x rows of each plane (|m1| <= m1max,
+// compact row index rho), twice (double buffer), rows padded to an odd length (N2 | 1) so
+// that a thread per row and a thread per column both touch 16 distinct 8-byte bank pairs
+// per half warp, and the planes' V_eff / N (loaded once for the group).  Per band pair:
+// its compact columns have landed in one buffer by asynchronous copies to precomputed
+// slots (issued while the previous pair computed), the next pair's start landing in the
+// other; y inverse (thread per occupied row); per column: x inverse of the occupied rows,
+// times V_eff/N, x forward, occupied rows back (thread per column, the full column in
+// registers); y forward; gather the compact columns.
 #include "fft_reg.cuh"
 #include "kernels.h"
 
@@ -78,39 +80,55 @@ __global__ void __launch_bounds__(PLANE_REG_THREADS, MAXN <= 40 ? 2 : 1) k_plane
   const int Q = PLANE_REG_THREADS / n2;
   const int nzb = (n3 + Q - 1) / Q;
   const int local = blockIdx.x - ka.start[p];
-  const int pair = local / nzb, zb = local - pair * nzb;
+  const int grp = local / nzb, zb = local - grp * nzb;
   const int z0 = zb * Q, nq = min(Q, n3 - z0);
-  cplx<float>* S = reinterpret_cast<cplx<float>*>(smem_raw);
-  float* Vs = reinterpret_cast<float*>(S + Q * plane);  // V_eff / N of the CTA's planes
-  cplx<float>* wc = reinterpret_cast<cplx<float>*>(P.Wc) + ((size_t)pair * n3 + z0) * ncol;
+  const int pr0 = grp * PLANE_PAIR_GROUP, pr1 = min(P.npair, pr0 + PLANE_PAIR_GROUP);
+  cplx<float>* const S0 = reinterpret_cast<cplx<float>*>(smem_raw);
+  cplx<float>* const S1 = S0 + Q * plane;
+  float* Vs = reinterpret_cast<float*>(S1 + Q * plane);  // V_eff / N of the CTA's planes
   const int* __restrict__ sidx = P.col_sidx;
-  for (int t = threadIdx.x; t < nq * plane; t += blockDim.x) S[t] = mk(0.f, 0.f);
+  auto wc_of = [&](int pair) {
+    return reinterpret_cast<cplx<float>*>(P.Wc) + ((size_t)pair * n3 + z0) * ncol;
+  };
+  auto scatter = [&](cplx<float>* S, const cplx<float>* wc) {
+    for (int q = 0; q < nq; ++q)
+      for (int c = threadIdx.x; c < ncol; c += blockDim.x) cp_async8(S + q * plane + sidx[c], wc + q * ncol + c);
+    cp_async_commit();
+  };
+  for (int t = threadIdx.x; t < 2 * Q * plane; t += blockDim.x) S0[t] = mk(0.f, 0.f);
   __syncthreads();
-  // scatter of the compact columns (group 0), then the potential (group 1): asynchronous
-  // copies, the potential landing while the y pass runs
-  for (int q = 0; q < nq; ++q)
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) cp_async8(S + q * plane + sidx[c], wc + q * ncol + c);
-  cp_async_commit();
+  // the potential (once for the CTA's band pairs) and the first pair's compact columns:
+  // asynchronous copies; every later pair's columns land while the previous pair computes
   const float* veff = reinterpret_cast<const float*>(P.veff) + (size_t)z0 * n12;
   for (int t = threadIdx.x; t < nq * n12; t += blockDim.x) cp_async4(Vs + t, veff + t);
   cp_async_commit();
-  cp_async_wait<1>();
-  __syncthreads();
-  // y inverse, x pass, y forward; both y directions through one row-transform body
+  scatter(S0, wc_of(pr0));
 #pragma unroll 1
-  for (int ph = 0; ph < 2; ++ph) {
-    for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN>(n2, S + l * P2, ph == 1);
-    if (ph == 0) cp_async_wait<0>();
+  for (int pair = pr0; pair < pr1; ++pair) {
+    const bool odd = (pair - pr0) & 1;
+    cplx<float>* S = odd ? S1 : S0;
+    cplx<float>* Sn = odd ? S0 : S1;
+    cp_async_wait<0>();
     __syncthreads();
-    if (ph == 1) break;
-    for (int l = threadIdx.x; l < nq * n2; l += blockDim.x) {
-      const int q = l / n2, i2 = l - q * n2;
-      col_vpsi_n<MAXN>(n1, S + q * plane + i2, P2, Vs + q * n12 + i2, n2, mx);
+    if (pair + 1 < pr1) scatter(Sn, wc_of(pair + 1));
+    // y inverse, x pass, y forward; both y directions through one row-transform body
+#pragma unroll 1
+    for (int ph = 0; ph < 2; ++ph) {
+      for (int l = threadIdx.x; l < nq * R; l += blockDim.x) row_fft_n<MAXN>(n2, S + l * P2, ph == 1);
+      __syncthreads();
+      if (ph == 1) break;
+      for (int l = threadIdx.x; l < nq * n2; l += blockDim.x) {
+        const int q = l / n2, i2 = l - q * n2;
+        col_vpsi_n<MAXN>(n1, S + q * plane + i2, P2, Vs + q * n12 + i2, n2, mx);
+      }
+      __syncthreads();
     }
+    cplx<float>* wc = wc_of(pair);
+    for (int q = 0; q < nq; ++q)
+      for (int c = threadIdx.x; c < ncol; c += blockDim.x) wc[q * ncol + c] = S[q * plane + sidx[c]];
     __syncthreads();
+    for (int t = threadIdx.x; t < nq * plane; t += blockDim.x) S[t] = mk(0.f, 0.f);  // for pair + 2
   }
-  for (int q = 0; q < nq; ++q)
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) wc[q * ncol + c] = S[q * plane + sidx[c]];
 }
 
 bool plane_reg_ok(int n1, int n2) {
@@ -119,11 +137,11 @@ bool plane_reg_ok(int n1, int n2) {
 int plane_reg_class(int n1, int n2) { return (n1 <= 40 && n2 <= 40) ? 0 : 1; }
 int plane_reg_ctas(int n2, int n3, int npair) {
   const int q = PLANE_REG_THREADS / n2;
-  return npair * ((n3 + q - 1) / q);
+  return ((npair + PLANE_PAIR_GROUP - 1) / PLANE_PAIR_GROUP) * ((n3 + q - 1) / q);
 }
 size_t plane_reg_smem(int n1, int n2, int m1max) {
   const size_t q = PLANE_REG_THREADS / n2;
-  return q * (2 * m1max + 1) * (n2 | 1) * sizeof(cplx<float>) + q * n1 * n2 * sizeof(float);
+  return 2 * q * (2 * m1max + 1) * (n2 | 1) * sizeof(cplx<float>) + q * n1 * n2 * sizeof(float);
 }
 
 void launch_plane_vpsi_reg(const Launch& L, int cls, size_t smem) {

@@ -14,6 +14,7 @@ constexpr int PLANE_MIN_BLOCKS = 4;     // register cap (64) for 4+ resident CTA
 constexpr int PLANE_THREADS_MAX = PLANE_THREADS;
 constexpr int PLANE_REG_THREADS = 256;  // register-FFT plane kernel (mixed path)
 constexpr int PLANE_REG_MAXN = 72;      // longest x / y / z line it transforms
+constexpr int PLANE_PAIR_GROUP = 8;     // band pairs per register plane CTA
 constexpr int PAIR_REG_MAXN = 128;      // longest line a lane pair transforms
 constexpr int ZREG_CP = 64;             // column pairs per register z-column CTA
 constexpr int ZREG_THREADS = 2 * ZREG_CP;

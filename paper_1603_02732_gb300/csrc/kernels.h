@@ -26,7 +26,7 @@ constexpr int NN_RT = 4;              // row tiles of 64 per NN CTA
 constexpr int NN_KP = 128;             // rows of the small matrix staged per pass
 constexpr int BAND_THREADS = 256;
 constexpr int GRID_CHUNK = 4096;       // grid points per reduction CTA
-constexpr int RR_THREADS = 512;
+constexpr int RR_THREADS = 1024;
 constexpr int LF_GROUP = 4;            // atoms per local-force CTA
 
 struct KArgs {

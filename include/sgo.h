@@ -91,6 +91,13 @@ typedef struct {
                              iteration.  Results are identical.  Taken from the first member. */
   int autotune;           /* batches: time the GEMM tile candidates at creation and keep the fastest
                              (1, default); 0 = fixed defaults.  Taken from the first member. */
+  int sub_batches;        /* batches in graph mode: split the members into this many sub-batches of
+                             about equal work, each driven by its own graphs on its own stream so
+                             that their kernels overlap on the GPU; 0 = automatic (3 from 24
+                             members on, 2 from 16, else 1).  With the same GEMM knobs
+                             (autotune = 0) every member's results are bit-identical in every
+                             split; the autotuner tunes each sub-batch on its own.  Taken from
+                             the first member. */
 } sgo_opts;
 
 /* Fill *o with the defaults (FP64, kT 0, tolerances 1e-8 Ha / 1e-7, Pulay 8, ...). */

@@ -47,7 +47,7 @@ class sgo_opts(ctypes.Structure):
                 ("mix_alpha", ctypes.c_double), ("kerker_q0", ctypes.c_double), ("ncg", ctypes.c_int),
                 ("ncg_first", ctypes.c_int), ("n_nonscf", ctypes.c_int), ("fft", ctypes.c_int * 3),
                 ("seed", ctypes.c_ulonglong), ("gemm_tc", ctypes.c_int), ("graph", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("sub_batches", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -109,12 +109,13 @@ __global__ void k_scf_gate(const int* active, int n, const int* iter, int max_sc
   cudaGraphSetConditional(cond, (nact > 0 && *iter < max_scf) ? 1u : 0u);
 }
 // out[p] = F, out_f[off_p + e] = forces (device gather for the device-pointer batch)
-__global__ void k_gather_results(KArgs ka, const int* foff, double* energies, double* forces, int* status) {
+__global__ void k_gather_results(KArgs ka, const int* slot, const int* foff, double* energies, double* forces,
+                                 int* status) {
   const int p = blockIdx.x;
   const Prob& P = ka.probs[p];
   if (threadIdx.x == 0) {
-    energies[p] = P.scal[SC_FREE];
-    status[p] = P.status[0] ? SGO_ERR_NOT_CONVERGED : (P.scal[SC_CONV] != 0.0 ? SGO_OK : SGO_ERR_NOT_CONVERGED);
+    energies[slot[p]] = P.scal[SC_FREE];
+    status[slot[p]] = P.status[0] ? SGO_ERR_NOT_CONVERGED : (P.scal[SC_CONV] != 0.0 ? SGO_OK : SGO_ERR_NOT_CONVERGED);
   }
   for (int e = threadIdx.x; e < 3 * P.natom; e += blockDim.x) forces[foff[p] + e] = P.forces[e];
 }
@@ -719,7 +720,28 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     if (!cuda_ok(cudaMalloc(&d_nnimg_, sizeof(float) * nnimg_stride_ * n_), "cudaMalloc(nn image)")) return;
     allocs_.push_back(d_nnimg_);
   }
-  h_flags_.assign(4 * n_, 0.0);
+  {
+    // pinned read-back area, and the default slots (the engine is the whole batch)
+    size_t nd = 4 * (size_t)n_;
+    hp_off_.resize(n_);
+    for (int p = 0; p < n_; ++p) {
+      hp_off_[p] = nd;
+      nd += NSCAL_ALL + 2 * (size_t)ctxs[p]->nb + ctxs[p]->h_forces.size();
+    }
+    if (!cuda_ok(cudaMallocHost(&hp_, sizeof(double) * nd), "cudaMallocHost(read-back)")) return;
+    std::memset(hp_, 0, sizeof(double) * nd);
+    if (!cuda_ok(cudaMallocHost(&hpi_, sizeof(int) * (1 + 4 * (size_t)n_)), "cudaMallocHost(read-back)")) return;
+    std::memset(hpi_, 0, sizeof(int) * (1 + 4 * (size_t)n_));
+    if (!cuda_ok(cudaMalloc(&d_slot_, sizeof(int) * 2 * n_), "cudaMalloc(slots)")) return;
+    allocs_.push_back(d_slot_);
+    d_foff_ = d_slot_ + n_;
+    std::vector<int> slot(n_), foff(n_);
+    for (int p = 0, o = 0; p < n_; o += 3 * ctxs[p]->d.natom, ++p) {
+      slot[p] = p;
+      foff[p] = o;
+    }
+    if (!set_slots(slot, foff)) return;
+  }
   // mixed path: the FP32 eigensolve (its five matrices in shared memory up to nb = 105,
   // else in a per-member global scratch; the Jacobi pair tables allow nb <= 512)
   rr_f32_ = precision_ == 1 && max_nb_ <= 512;
@@ -751,6 +773,8 @@ Engine::~Engine() {
   if (ev_in_) cudaEventDestroy(ev_in_);
   if (ev_out_) cudaEventDestroy(ev_out_);
   if (own_stream_) cudaStreamDestroy(own_stream_);
+  if (hp_) cudaFreeHost(hp_);
+  if (hpi_) cudaFreeHost(hpi_);
   for (auto& v : ev_) cudaEventDestroy(v);
   for (void* p : allocs_) cudaFree(p);
 }
@@ -1000,11 +1024,11 @@ void Engine::cg_step() {
 
 void Engine::sync_active() {
   k_gather_flags<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, d_flags_);
-  cudaMemcpyAsync(h_flags_.data(), d_flags_, sizeof(double) * 4 * n_, cudaMemcpyDeviceToHost, stream_);
+  cudaMemcpyAsync(hp_, d_flags_, sizeof(double) * 4 * n_, cudaMemcpyDeviceToHost, stream_);
   cudaStreamSynchronize(stream_);
   for (int p = 0; p < n_; ++p) {
     if (!h_active_[p]) continue;
-    if (h_flags_[4 * p] != 0.0 || h_flags_[4 * p + 1] != 0.0 || h_flags_[4 * p + 2] != 0.0) h_active_[p] = 0;
+    if (hp_[4 * p] != 0.0 || hp_[4 * p + 1] != 0.0 || hp_[4 * p + 2] != 0.0) h_active_[p] = 0;
   }
   cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_);
 }
@@ -1147,7 +1171,7 @@ bool Engine::build_graphs() {
 }
 
 template <typename T>
-sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
+sgo_status Engine::launch_t(bool want_forces) {
   const sgo_opts& o = ctx_[0]->opts;
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
@@ -1161,24 +1185,21 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
     launch_random_init<T>(L(m_bands_), WB_X, o.seed);
   }
   const int nonsc = warm ? 0 : std::max(0, o.n_nonscf);
-  int it = 0;
+  run_nonsc_ = nonsc;
+  run_forces_ = want_forces;
   // graph mode: batch engines, no live kernel timer (its events are host bookkeeping)
-  bool graph = use_graph_ && timer_kind_ < 0;
-  if (graph && !g_scf_) graph = build_graphs<T>();
-  if (graph) {
+  run_graph_ = use_graph_ && timer_kind_ < 0;
+  if (run_graph_ && !g_scf_) run_graph_ = build_graphs<T>();
+  if (run_graph_) {
+    // the iteration count and the flags are read back by finish(), after the one wait
     CK(cudaMemsetAsync(d_iter_, 0, sizeof(int), stream_));
-    const int na = std::min(nonsc, o.max_scf);
-    for (int i = 0; i < na; ++i) CK(cudaGraphLaunch(g_nonscf_, stream_));
+    run_na_ = std::min(nonsc, o.max_scf);
+    for (int i = 0; i < run_na_; ++i) CK(cudaGraphLaunch(g_nonscf_, stream_));
     if (o.max_scf > nonsc) CK(cudaGraphLaunch(g_scf_, stream_));
-    int h_iter = 0;
-    CK(cudaMemcpyAsync(&h_iter, d_iter_, sizeof(int), cudaMemcpyDeviceToHost, stream_));
-    CK(cudaMemcpyAsync(h_flags_.data(), d_flags_, sizeof(double) * 4 * n_, cudaMemcpyDeviceToHost, stream_));
-    CK(cudaMemcpyAsync(h_active_.data(), d_active_, sizeof(int) * n_, cudaMemcpyDeviceToHost, stream_));
-    CK(cudaStreamSynchronize(stream_));
-    CK(cudaGetLastError());
-    it = h_iter;
-    launches_ += (long long)na * graph_launches_[0] + (long long)std::max(0, h_iter - na) * graph_launches_[1];
+    CK(cudaMemcpyAsync(hpi_, d_iter_, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(hp_, d_flags_, sizeof(double) * 4 * n_, cudaMemcpyDeviceToHost, stream_));
   } else {
+    int it = 0;
     for (it = 1; it <= o.max_scf; ++it) {
       scf_iteration<T>(it <= nonsc ? o.ncg_first : o.ncg, it > nonsc);
       CK(cudaGetLastError());
@@ -1188,10 +1209,9 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
       if (nact == 0) break;
       if (it > nonsc) pulay_step();
     }
+    run_it_ = it;
   }
-  const int niter = std::min(it, o.max_scf);
   // forces on every member
-  std::vector<int> was(h_active_);
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   if (want_forces) {
@@ -1206,60 +1226,114 @@ sgo_status Engine::run_t(bool want_forces, std::vector<sgo_status>* per_item) {
   // X back to physical buffer 0 so that the next run (warm or component call) finds it there
   k_x_to_buffer0<T><<<m_bands_.total, 256, 0, stream_>>>(L(m_bands_).ka);
   k_reset_roles<<<n_, 32, 0, stream_>>>(L(m_prob_).ka);
-  for (auto* c : ctx_) {
-    CK(cudaMemcpyAsync(c->h_scal.data(), c->d.scal, sizeof(double) * NSCAL_ALL, cudaMemcpyDeviceToHost, stream_));
-    CK(cudaMemcpyAsync(c->h_eps.data(), c->d.eps, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
-    CK(cudaMemcpyAsync(c->h_occ.data(), c->d.occ, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
-    CK(cudaMemcpyAsync(c->h_forces.data(), c->d.forces, sizeof(double) * c->h_forces.size(), cudaMemcpyDeviceToHost,
-                       stream_));
-    CK(cudaMemcpyAsync(c->h_status, c->d.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream_));
+  for (int p = 0; p < n_; ++p) {
+    const sgo_ctx* c = ctx_[p];
+    double* h = hp_ + hp_off_[p];
+    CK(cudaMemcpyAsync(h, c->d.scal, sizeof(double) * NSCAL_ALL, cudaMemcpyDeviceToHost, stream_));
+    h += NSCAL_ALL;
+    CK(cudaMemcpyAsync(h, c->d.eps, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
+    h += c->nb;
+    CK(cudaMemcpyAsync(h, c->d.occ, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
+    h += c->nb;
+    CK(cudaMemcpyAsync(h, c->d.forces, sizeof(double) * c->h_forces.size(), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(hpi_ + 1 + 4 * p, c->d.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream_));
   }
-  CK(cudaStreamSynchronize(stream_));
   CK(cudaGetLastError());
+  return SGO_OK;
+}
+
+sgo_status Engine::enter() {
+  run_status_ = ok_ ? SGO_OK : SGO_ERR_CUDA;
+  user_stream_ = run_stream_ = stream_;
+  if (!ok_ || !use_graph_ || timer_kind_ >= 0) return run_status_;
+  // graph mode runs on a private stream (the caller's may be the legacy default stream,
+  // which cannot be captured), ordered after the caller's stream and before anything the
+  // caller enqueues after leave()
+  if (!own_stream_) {
+    if (!cuda_ok(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking), "graph stream") ||
+        !cuda_ok(cudaEventCreateWithFlags(&ev_in_, cudaEventDisableTiming), "graph event") ||
+        !cuda_ok(cudaEventCreateWithFlags(&ev_out_, cudaEventDisableTiming), "graph event"))
+      return run_status_ = SGO_ERR_CUDA;
+  }
+  if (!cuda_ok(cudaEventRecord(ev_in_, user_stream_), "graph event") ||
+      !cuda_ok(cudaStreamWaitEvent(own_stream_, ev_in_, 0), "graph event"))
+    return run_status_ = SGO_ERR_CUDA;
+  stream_ = run_stream_ = own_stream_;
+  return SGO_OK;
+}
+
+sgo_status Engine::launch(bool want_forces, const DeviceIO* io) {
+  if (run_status_ != SGO_OK) return run_status_;
+  if (io && io->pos) k_scatter_pos<<<n_, 128, 0, stream_>>>(L(m_prob_).ka, d_foff_, io->pos);
+  run_status_ = precision_ ? launch_t<float>(want_forces) : launch_t<double>(want_forces);
+  if (run_status_ == SGO_OK && io)
+    k_gather_results<<<n_, 128, 0, stream_>>>(L(m_prob_).ka, d_slot_, d_foff_, io->energies, io->forces,
+                                               io->status);
+  return run_status_;
+}
+
+void Engine::leave() {
+  if (run_stream_ != user_stream_) {
+    cudaEventRecord(ev_out_, run_stream_);
+    cudaStreamWaitEvent(user_stream_, ev_out_, 0);
+  }
+  stream_ = user_stream_;
+}
+
+sgo_status Engine::finish(std::vector<sgo_status>* per_item) {
+  CK(cudaStreamSynchronize(run_stream_));  // (a null stream is the caller's legacy default stream)
+  if (run_status_ != SGO_OK) return run_status_;
+  CK(cudaGetLastError());
+  const sgo_opts& o = ctx_[0]->opts;
+  int it = run_it_;
+  if (run_graph_) {
+    it = hpi_[0];
+    launches_ += (long long)run_na_ * graph_launches_[0] + (long long)std::max(0, it - run_na_) * graph_launches_[1];
+  }
+  const int niter = std::min(it, o.max_scf);
   sgo_status all = SGO_OK;
   for (int p = 0; p < n_; ++p) {
     sgo_ctx* c = ctx_[p];
+    const double* h = hp_ + hp_off_[p];
+    std::memcpy(c->h_scal.data(), h, sizeof(double) * NSCAL_ALL);
+    h += NSCAL_ALL;
+    std::memcpy(c->h_eps.data(), h, sizeof(double) * c->nb);
+    h += c->nb;
+    std::memcpy(c->h_occ.data(), h, sizeof(double) * c->nb);
+    h += c->nb;
+    std::memcpy(c->h_forces.data(), h, sizeof(double) * c->h_forces.size());
+    std::memcpy(c->h_status, hpi_ + 1 + 4 * p, sizeof(int) * 4);
     c->have_state = true;
-    c->last_iter = (int)c->h_scal[SC_ITER] + nonsc;  // this member's iterations (until it converged)
+    c->last_iter = (int)c->h_scal[SC_ITER] + run_nonsc_;  // this member's iterations (until it converged)
     if (c->last_iter > niter) c->last_iter = niter;
     c->last_resid = c->h_scal[SC_RESID];
     sgo_status st = SGO_OK;
-    if (h_flags_[4 * p + 1] != 0.0) st = SGO_ERR_NOT_CONVERGED;
+    if (hp_[4 * p + 1] != 0.0) st = SGO_ERR_NOT_CONVERGED;
     if (c->h_status[2] != 0) st = SGO_ERR_TIMEOUT;
-    else if (h_flags_[4 * p + 2] != 0.0 || !std::isfinite(c->h_scal[SC_FREE])) st = SGO_ERR_NAN;
+    else if (hp_[4 * p + 2] != 0.0 || !std::isfinite(c->h_scal[SC_FREE])) st = SGO_ERR_NAN;
     else if (c->h_scal[SC_CONV] == 0.0) st = SGO_ERR_NOT_CONVERGED;
-    if (want_forces)
+    if (run_forces_)
       for (double f : c->h_forces)
         if (!std::isfinite(f)) st = SGO_ERR_NAN;
     c->last_status = st;
     if (per_item) (*per_item)[p] = st;
     if (st != SGO_OK && all == SGO_OK) all = st;
   }
-  (void)was;
   return all;
 }
 
 sgo_status Engine::run(bool want_forces, std::vector<sgo_status>* per_item) {
-  if (!ok_) return SGO_ERR_CUDA;
-  if (!use_graph_ || timer_kind_ >= 0)
-    return precision_ ? run_t<float>(want_forces, per_item) : run_t<double>(want_forces, per_item);
-  // graph mode runs on a private stream, ordered after the caller's stream and before
-  // anything the caller enqueues afterwards
-  if (!own_stream_) {
-    if (!cuda_ok(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking), "graph stream") ||
-        !cuda_ok(cudaEventCreateWithFlags(&ev_in_, cudaEventDisableTiming), "graph event") ||
-        !cuda_ok(cudaEventCreateWithFlags(&ev_out_, cudaEventDisableTiming), "graph event"))
-      return SGO_ERR_CUDA;
-  }
-  cudaStream_t user = stream_;
-  CK(cudaEventRecord(ev_in_, user));
-  CK(cudaStreamWaitEvent(own_stream_, ev_in_, 0));
-  stream_ = own_stream_;
-  sgo_status s = precision_ ? run_t<float>(want_forces, per_item) : run_t<double>(want_forces, per_item);
-  stream_ = user;
-  CK(cudaEventRecord(ev_out_, own_stream_));
-  CK(cudaStreamWaitEvent(user, ev_out_, 0));
-  return s;
+  enter();
+  launch(want_forces, nullptr);
+  leave();
+  return finish(per_item);
+}
+
+bool Engine::set_slots(const std::vector<int>& slot, const std::vector<int>& foff) {
+  if ((int)slot.size() != n_ || (int)foff.size() != n_ || !d_slot_) return false;
+  std::vector<int> h(slot);
+  h.insert(h.end(), foff.begin(), foff.end());
+  return cuda_ok(cudaMemcpy(d_slot_, h.data(), sizeof(int) * 2 * n_, cudaMemcpyHostToDevice), "slots");
 }
 
 // ---- component entry points (problem 0) ----
@@ -1407,18 +1481,11 @@ sgo_status Engine::export_density(double* rho) {
 }
 
 sgo_status Engine::run_device(const double* pos, double* energies, double* forces, int* status) {
-  std::vector<int> off(n_ + 1, 0);
-  for (int p = 0; p < n_; ++p) off[p + 1] = off[p] + 3 * ctx_[p]->d.natom;
-  int* doff = nullptr;
-  CK(cudaMalloc(&doff, sizeof(int) * (n_ + 1)));
-  CK(cudaMemcpyAsync(doff, off.data(), sizeof(int) * (n_ + 1), cudaMemcpyHostToDevice, stream_));
-  h_active_.assign(n_, 1);
-  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
-  if (pos) k_scatter_pos<<<n_, 128, 0, stream_>>>(L(m_prob_).ka, doff, pos);
-  sgo_status s = run(true, nullptr);
-  k_gather_results<<<n_, 128, 0, stream_>>>(L(m_prob_).ka, doff, energies, forces, status);
-  CK(cudaStreamSynchronize(stream_));
-  cudaFree(doff);
+  const DeviceIO io{pos, energies, forces, status};
+  enter();
+  launch(true, &io);
+  leave();
+  const sgo_status s = finish(nullptr);
   return s == SGO_ERR_CUDA ? s : SGO_OK;
 }
 

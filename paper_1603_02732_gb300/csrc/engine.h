@@ -91,9 +91,31 @@ class Engine {
   }
   // Batch evaluation with positions, energies, forces and statuses in device memory.
   sgo_status run_device(const double* pos, double* energies, double* forces, int* status);
+  // Device-resident inputs and outputs of a batch evaluation, indexed by the member's
+  // position in the whole batch (see set_slots).
+  struct DeviceIO {
+    const double* pos;
+    double* energies;
+    double* forces;
+    int* status;
+  };
+  // Position of each member of this engine in the whole batch and the offset (doubles) of
+  // its 3 natom coordinates in the batch's packed position and force arrays.
+  bool set_slots(const std::vector<int>& slot, const std::vector<int>& foff);
+  // run() in four steps, so that the engines of several sub-batches overlap on the GPU:
+  // enter() orders the engine's private stream after the caller's, launch() enqueues the
+  // whole evaluation (in graph mode without any host wait), leave() orders the caller's
+  // stream after it, finish() waits for it and reads the results back.  Without graphs
+  // (or with the live timer) the work runs on the caller's stream and launch() waits on
+  // the host once per SCF iteration.
+  sgo_status enter();
+  sgo_status launch(bool want_forces, const DeviceIO* io);
+  void leave();
+  sgo_status finish(std::vector<sgo_status>* per_item);
+  int size() const { return n_; }
 
  private:
-  template <typename T> sgo_status run_t(bool want_forces, std::vector<sgo_status>* per_item);
+  template <typename T> sgo_status launch_t(bool want_forces);
   template <typename T> void scf_iteration(int ncg, bool count_iter);
   void pulay_step();
   template <typename T> bool build_graphs();
@@ -162,7 +184,19 @@ class Engine {
   size_t rr32_stride_ = 0;
   size_t rr_smem_bytes_ = 0;
   double* d_flags_ = nullptr;   // [n][4] gathered per iteration
-  std::vector<double> h_flags_;
+  // pinned read-back area (device-to-host copies into it do not block the host):
+  // hp_ = flags [n][4], then per member scal, eps, occ, forces at hp_off_[p];
+  // hpi_ = iteration count, then per member status[4]
+  double* hp_ = nullptr;
+  int* hpi_ = nullptr;
+  std::vector<size_t> hp_off_;
+  int* d_slot_ = nullptr;       // [n] member's position in the whole batch
+  int* d_foff_ = nullptr;       // [n] offset of its coordinates in the batch's arrays
+  // state of the evaluation between launch() and finish()
+  cudaStream_t user_stream_ = nullptr, run_stream_ = nullptr;
+  bool run_graph_ = false, run_forces_ = false;
+  int run_nonsc_ = 0, run_it_ = 0, run_na_ = 0;
+  sgo_status run_status_ = SGO_OK;
   // graph mode: captured iterations, the device iteration counter, a private stream (the
   // caller's may be the legacy default stream, which cannot be captured)
   bool use_graph_ = false;

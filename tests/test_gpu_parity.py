@@ -294,6 +294,38 @@ def test_graph_loop_equals_host_loop(sgo):
         assert res[0][2] == res[1][2], prec
 
 
+def test_sub_batches_equal_one_batch(sgo):
+    """Splitting a batch into sub-batches (each on its own graphs and stream, overlapping on
+    the GPU) leaves every member's energy, forces and iteration count bit-identical, through
+    both the host-pointer and the device-pointer entry points (whose outputs are indexed by
+    the member's place in the whole batch)."""
+    import torch
+    sts = [_struct(seed=s, ecut=3.0) for s in (3, 4, 9, 5, 6)]
+    sts[1] = _struct(seed=4, ecut=3.5, nat=3, grid=(16, 18, 20))
+    for prec, tol in (("fp64", dict(scf_tol_e=1e-10, scf_tol_rho=1e-8)), ("mixed", dict(scf_tol_e=1e-7, scf_tol_rho=1e-5))):
+        res = {}
+        for k in (1, 2, 3):
+            ctxs = [sgo.Context(st, precision=prec, autotune=0, sub_batches=k, max_scf=100, **tol) for st in sts]
+            b = sgo.Batch(ctxs)
+            E, F, status = b.energy_forces()
+            assert list(status) == [0] * len(sts), (prec, k)
+            pos = torch.tensor(np.concatenate([st.pos.reshape(-1) for st in sts]), device="cuda")
+            e_dev = torch.zeros(len(sts), dtype=torch.float64, device="cuda")
+            f_dev = torch.zeros_like(pos)
+            s_dev = torch.full((len(sts),), -1, dtype=torch.int32, device="cuda")
+            b.energy_forces_device(pos.data_ptr(), e_dev.data_ptr(), f_dev.data_ptr(), s_dev.data_ptr())
+            torch.cuda.synchronize()
+            assert s_dev.tolist() == [0] * len(sts), (prec, k)
+            assert np.array_equal(e_dev.cpu().numpy(), E), (prec, k)
+            assert np.array_equal(f_dev.cpu().numpy(), np.concatenate([f.reshape(-1) for f in F])), (prec, k)
+            res[k] = (E, F, [c.stats() for c in ctxs])
+        for k in (2, 3):
+            assert np.array_equal(res[1][0], res[k][0]), (prec, k)
+            for i in range(len(sts)):
+                assert np.array_equal(res[1][1][i], res[k][1][i]), (prec, k, i)
+            assert res[1][2] == res[k][2], (prec, k)
+
+
 def test_autotuned_batch(sgo):
     """The autotuner keeps one of its candidates for each knob, and the tuned batch's
     energies and forces agree with the default-knob batch to the mixed tolerances (the knobs

@@ -34,10 +34,10 @@ MEMBERS = 64
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one plane pass (both size classes of k_plane_vpsi_reg) on this
-# workload, from an ncu capture of those kernels (cold cache); set to None whenever they
-# change after the capture.
-PLANE_VPSI_TRAFFIC = 228.0e6 + 149.8e6 + 23.4e6
+# DRAM bytes (read + write) per launch of k_plane_vpsi_reg on this workload, the mean of one
+# launch of each size class of one sub-batch (ncu capture, cold cache): (12.43 + 79.81) / 2 MB.
+# Set to None whenever the kernel changes after the capture.
+PLANE_VPSI_TRAFFIC = (12.43e6 + 79.81e6) / 2
 
 
 def _dist():

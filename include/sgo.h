@@ -221,6 +221,15 @@ SGO_API sgo_status sgo_subspace_matrix(sgo_ctx* ctx, int nvec, const double* x, 
 SGO_API sgo_status sgo_block_update(sgo_ctx* ctx, int nvec, const double* x, const double* m, double alpha,
                                     double beta, double* y);
 
+/* One 3D transform of the SCF's grid FFT (Sec. II D: the potential from rho_in(G), rho_out(G)
+ * from rho_out(r)) on a complex grid: in and out are N1*N2*N3 complex values, C order,
+ * interleaved (re, im) doubles, caller-owned host memory.  sign -1: out(m) = sum_j in(j)
+ * exp(-2 pi i m.j / N) per axis (r -> G); sign +1: the same with +i (G -> r), unnormalised.
+ * Arithmetic: FP64 on the plain path; float-float (two FP32 numbers per value, about 44
+ * bits) on the mixed path, whose FP64 grids it serves.  SGO_ERR_ARG for null pointers or a
+ * sign other than +-1. */
+SGO_API sgo_status sgo_grid_fft(sgo_ctx* ctx, int sign, const double* in, double* out);
+
 /* rho(r) = sum_n occ_n |psi_n(r)|^2 for nvec packed vectors (the density kernels). */
 SGO_API sgo_status sgo_density(sgo_ctx* ctx, int nvec, const double* psi, const double* occ, double* rho);
 

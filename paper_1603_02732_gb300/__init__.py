@@ -79,6 +79,7 @@ _SIGS = {
     "sgo_block_update": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
     "sgo_batch_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
+    "sgo_grid_fft": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
     "sgo_set_warm": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sgo_batch_destroy": (None, [_vp]),
     "sgo_destroy": (None, [_vp]),
@@ -264,6 +265,15 @@ class Context:
         _check(self.lib.sgo_block_update(self.h, x.shape[0], _ptr(x), _ptr(m), float(alpha), float(beta), _ptr(y)),
                "sgo_block_update")
         return y
+
+    def grid_fft(self, x, sign):
+        """One 3D transform of the SCF's grid FFT (sign -1: r -> G, +1: G -> r, unnormalised)
+        of a complex grid of shape (N1, N2, N3)."""
+        x = np.ascontiguousarray(x, dtype=np.complex128).reshape(self.grid)
+        out = np.zeros(self.grid, dtype=np.complex128)
+        _check(self.lib.sgo_grid_fft(self.h, int(sign), x.ctypes.data_as(_dp), out.ctypes.data_as(_dp)),
+               "sgo_grid_fft")
+        return out
 
     def density_of(self, psi, occ):
         psi = np.ascontiguousarray(np.atleast_2d(psi), dtype=np.float64)

@@ -367,6 +367,13 @@ sgo_status sgo_get_density(sgo_ctx* c, double* rho) {
   return e->export_density(rho);
 }
 
+sgo_status sgo_grid_fft(sgo_ctx* c, int sign, const double* in, double* out) {
+  if (!c || !in || !out || (sign != 1 && sign != -1)) return SGO_ERR_ARG;
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  return e->grid_transform(sign, in, out);
+}
+
 sgo_status sgo_apply_hamiltonian(sgo_ctx* c, const double* veff, int nvec, const double* psi, double* hpsi) {
   if (!c || !veff || !psi || !hpsi || nvec < 1 || nvec > c->nb) return SGO_ERR_ARG;
   std::unique_ptr<sgo::Engine> e(solo_engine(c));

@@ -69,6 +69,7 @@ class Engine {
   sgo_status apply_h(const double* veff_c, int nvec, const double* psi, double* hpsi);
   sgo_status density(int nvec, const double* psi, const double* occ, double* rho);
   sgo_status export_density(double* rho);
+  sgo_status grid_transform(int sign, const double* in, double* out);
   sgo_status subspace(int nvec, const double* x, const double* y, double* c);
   sgo_status block_update(int nvec, const double* x, const double* m, double alpha, double beta, double* y);
   sgo_status structure_terms();

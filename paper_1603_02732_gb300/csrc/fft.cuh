@@ -11,18 +11,20 @@
 //   sign = +1: x(j) = sum_m X(m) exp(+2 pi i m j / n)   (G -> r)
 #pragma once
 
+#include "ff.cuh"
 #include "sgo_internal.cuh"
 
 namespace sgo {
 
-// exp(sign 2 pi i / 3) etc. written out: cos/sin of 2pi/3, 2pi/5, 4pi/5.
+// exp(sign 2 pi i / 3) etc. written out: cos/sin of 2pi/3, 2pi/5, 4pi/5 (functions, so that
+// the float-float type, not a scalar, can take them in device code too).
 template <typename T>
 struct Rc {
-  static constexpr T s3 = T(0.86602540378443864676);
-  static constexpr T c1 = T(0.30901699437494742410);   // cos(2 pi/5)
-  static constexpr T c2 = T(-0.80901699437494742410);  // cos(4 pi/5)
-  static constexpr T s1 = T(0.95105651629515357212);   // sin(2 pi/5)
-  static constexpr T s2 = T(0.58778525229247312917);   // sin(4 pi/5)
+  static __host__ __device__ __forceinline__ T s3() { return T(0.86602540378443864676); }
+  static __host__ __device__ __forceinline__ T c1() { return T(0.30901699437494742410); }   // cos(2 pi/5)
+  static __host__ __device__ __forceinline__ T c2() { return T(-0.80901699437494742410); }  // cos(4 pi/5)
+  static __host__ __device__ __forceinline__ T s1() { return T(0.95105651629515357212); }   // sin(2 pi/5)
+  static __host__ __device__ __forceinline__ T s2() { return T(0.58778525229247312917); }   // sin(4 pi/5)
 };
 
 template <typename T, int R>
@@ -40,13 +42,19 @@ __device__ __forceinline__ void butterfly<double, 2>(cplx<double>* v, double) {
   v[0] = a + b;
   v[1] = a - b;
 }
+template <>
+__device__ __forceinline__ void butterfly<ff, 2>(cplx<ff>* v, ff) {
+  cplx<ff> a = v[0], b = v[1];
+  v[0] = a + b;
+  v[1] = a - b;
+}
 
 template <typename T>
 __device__ __forceinline__ void bfly3(cplx<T>* v, T sg) {
   cplx<T> a = v[0], b = v[1], c = v[2];
   cplx<T> t1 = b + c;
   cplx<T> t2 = mk(a.x - T(0.5) * t1.x, a.y - T(0.5) * t1.y);
-  cplx<T> t3 = scale(b - c, sg * Rc<T>::s3);
+  cplx<T> t3 = scale(b - c, sg * Rc<T>::s3());
   v[0] = a + t1;
   v[1] = mk(t2.x - t3.y, t2.y + t3.x);  // t2 + i t3
   v[2] = mk(t2.x + t3.y, t2.y - t3.x);  // t2 - i t3
@@ -55,6 +63,8 @@ template <>
 __device__ __forceinline__ void butterfly<float, 3>(cplx<float>* v, float sg) { bfly3<float>(v, sg); }
 template <>
 __device__ __forceinline__ void butterfly<double, 3>(cplx<double>* v, double sg) { bfly3<double>(v, sg); }
+template <>
+__device__ __forceinline__ void butterfly<ff, 3>(cplx<ff>* v, ff sg) { bfly3<ff>(v, sg); }
 
 template <typename T>
 __device__ __forceinline__ void bfly4(cplx<T>* v, T sg) {
@@ -69,15 +79,18 @@ template <>
 __device__ __forceinline__ void butterfly<float, 4>(cplx<float>* v, float sg) { bfly4<float>(v, sg); }
 template <>
 __device__ __forceinline__ void butterfly<double, 4>(cplx<double>* v, double sg) { bfly4<double>(v, sg); }
+template <>
+__device__ __forceinline__ void butterfly<ff, 4>(cplx<ff>* v, ff sg) { bfly4<ff>(v, sg); }
 
 template <typename T>
 __device__ __forceinline__ void bfly5(cplx<T>* v, T sg) {
   cplx<T> a = v[0];
   cplx<T> t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
-  cplx<T> u1 = mk(a.x + Rc<T>::c1 * t1.x + Rc<T>::c2 * t2.x, a.y + Rc<T>::c1 * t1.y + Rc<T>::c2 * t2.y);
-  cplx<T> u2 = mk(a.x + Rc<T>::c2 * t1.x + Rc<T>::c1 * t2.x, a.y + Rc<T>::c2 * t1.y + Rc<T>::c1 * t2.y);
-  cplx<T> w1 = mul_is(mk(Rc<T>::s1 * t3.x + Rc<T>::s2 * t4.x, Rc<T>::s1 * t3.y + Rc<T>::s2 * t4.y), sg);
-  cplx<T> w2 = mul_is(mk(Rc<T>::s2 * t3.x - Rc<T>::s1 * t4.x, Rc<T>::s2 * t3.y - Rc<T>::s1 * t4.y), sg);
+  const T c1 = Rc<T>::c1(), c2 = Rc<T>::c2(), s1 = Rc<T>::s1(), s2 = Rc<T>::s2();
+  cplx<T> u1 = mk(a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y);
+  cplx<T> u2 = mk(a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y);
+  cplx<T> w1 = mul_is(mk(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y), sg);
+  cplx<T> w2 = mul_is(mk(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y), sg);
   v[0] = a + t1 + t2;
   v[1] = u1 + w1;
   v[4] = u1 - w1;
@@ -88,6 +101,8 @@ template <>
 __device__ __forceinline__ void butterfly<float, 5>(cplx<float>* v, float sg) { bfly5<float>(v, sg); }
 template <>
 __device__ __forceinline__ void butterfly<double, 5>(cplx<double>* v, double sg) { bfly5<double>(v, sg); }
+template <>
+__device__ __forceinline__ void butterfly<ff, 5>(cplx<ff>* v, ff sg) { bfly5<ff>(v, sg); }
 
 // Composite radix R = R1 R2 in registers (Cooley-Tukey inside the butterfly):
 // with m = R2 m1 + m2 and k = k1 + R1 k2,

@@ -16,7 +16,22 @@ namespace sgo {
 
 namespace {
 
+// Working type T and the type S its grids and root tables are stored in: the same for
+// float and double; float-float works on FP64 data (converted on load and store).
 template <typename T>
+struct Work {
+  using S = T;
+  static __device__ __forceinline__ cplx<T> in(cplx<S> v) { return v; }
+  static __device__ __forceinline__ cplx<S> out(cplx<T> v) { return v; }
+};
+template <>
+struct Work<ff> {
+  using S = double;
+  static __device__ __forceinline__ cplx<ff> in(cplx<double> v) { return mk(ff_from(v.x), ff_from(v.y)); }
+  static __device__ __forceinline__ cplx<double> out(cplx<ff> v) { return mk(ff_to(v.x), ff_to(v.y)); }
+};
+
+template <typename S>
 struct RootsOf;
 template <>
 struct RootsOf<float> {
@@ -33,8 +48,8 @@ struct RootsOf<double> {
 
 template <typename T>
 __device__ __forceinline__ void load_roots(cplx<T>* dst, const Prob& P, int off, int n) {
-  const cplx<T>* src = RootsOf<T>::get(P) + off;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
+  const auto* src = RootsOf<typename Work<T>::S>::get(P) + off;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = Work<T>::in(src[t]);
 }
 
 __device__ __forceinline__ int wrapi(int m, int n) {
@@ -271,11 +286,12 @@ __global__ void __launch_bounds__(PLANE_THREADS, sizeof(T) == 4 ? PLANE_MIN_BLOC
 // Full FP64 complex grid transforms (in place): plane pass (x and y) and z pass.
 // which: 0 = gfft, 1 = gfft2.
 // ---------------------------------------------------------------------------
-// The work grids in the working precision of a transform: FP64 complex, or (FP32) the
-// first half of the same memory viewed as single-precision complex.
+// The work grids in the storage precision of a transform: FP64 complex (double and
+// float-float), or (FP32) the first half of the same memory viewed as single-precision
+// complex.
 template <typename T>
-__device__ __forceinline__ cplx<T>* grid_of(const Prob& P, int which) {
-  return reinterpret_cast<cplx<T>*>(which ? P.gfft2 : P.gfft);
+__device__ __forceinline__ cplx<typename Work<T>::S>* grid_of(const Prob& P, int which) {
+  return reinterpret_cast<cplx<typename Work<T>::S>*>(which ? P.gfft2 : P.gfft);
 }
 
 template <typename T>
@@ -292,13 +308,13 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_grid_plane_fft(KArgs ka, int 
   cplx<T>* r2 = r1 + n1;
   load_roots<T>(r1, P, 0, n1);
   load_roots<T>(r2, P, n1, n2);
-  cplx<T>* g = grid_of<T>(P, which) + (size_t)z * n12;
-  for (int t = threadIdx.x; t < n12; t += blockDim.x) b0[t] = g[t];
+  auto* g = grid_of<T>(P, which) + (size_t)z * n12;
+  for (int t = threadIdx.x; t < n12; t += blockDim.x) b0[t] = Work<T>::in(g[t]);
   __syncthreads();
   const T sg = sign < 0 ? T(-1) : T(1);
   cplx<T>* cur = fft_lines<T>(b0, b1, n1, n2, 1, contiguous(n1), P.fd[1], r2, sg);      // y
   cur = fft_lines<T>(cur, cur == b0 ? b1 : b0, n2, 1, n2, contiguous(n2), P.fd[0], r1, sg);  // x
-  for (int t = threadIdx.x; t < n12; t += blockDim.x) g[t] = cur[t];
+  for (int t = threadIdx.x; t < n12; t += blockDim.x) g[t] = Work<T>::out(cur[t]);
 }
 
 template <typename T>
@@ -314,16 +330,16 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_z_fft(KArgs ka, int which
   cplx<T>* alt = lines + QZ * n3;
   cplx<T>* roots = alt + QZ * n3;
   load_roots<T>(roots, P, P.n1 + P.n2, n3);
-  cplx<T>* g = grid_of<T>(P, which);
+  auto* g = grid_of<T>(P, which);
   for (int t = threadIdx.x; t < nc * n3; t += blockDim.x) {
     int z = t / nc, c = t - z * nc;
-    lines[c * n3 + z] = g[(size_t)z * n12 + c0 + c];
+    lines[c * n3 + z] = Work<T>::in(g[(size_t)z * n12 + c0 + c]);
   }
   __syncthreads();
   const cplx<T>* res = fft_lines<T>(lines, alt, nc, n3, 1, contiguous(nc), P.fd[2], roots, sign < 0 ? T(-1) : T(1));
   for (int t = threadIdx.x; t < nc * n3; t += blockDim.x) {
     int z = t / nc, c = t - z * nc;
-    g[(size_t)z * n12 + c0 + c] = res[c * n3 + z];
+    g[(size_t)z * n12 + c0 + c] = Work<T>::out(res[c * n3 + z]);
   }
 }
 
@@ -345,7 +361,7 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_line_fft(KArgs ka, int wh
   cplx<T>* alt = lines + QZ * n;
   cplx<T>* roots = alt + QZ * n;
   load_roots<T>(roots, P, axis ? n1 : 0, n);
-  cplx<T>* g = grid_of<T>(P, which);
+  auto* g = grid_of<T>(P, which);
   auto at = [&](int c, int e) -> size_t {
     const int l = l0 + c;
     if (axis) return (size_t)l * n2 + e;
@@ -354,14 +370,14 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_line_fft(KArgs ka, int wh
   };
   for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
     const int c = axis ? t / n : t % nc, e = axis ? t % n : t / nc;
-    lines[c * n + e] = g[at(c, e)];
+    lines[c * n + e] = Work<T>::in(g[at(c, e)]);
   }
   __syncthreads();
   const cplx<T>* res =
       fft_lines<T>(lines, alt, nc, n, 1, contiguous(nc), P.fd[axis ? 1 : 0], roots, sign < 0 ? T(-1) : T(1));
   for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
     const int c = axis ? t / n : t % nc, e = axis ? t % n : t / nc;
-    g[at(c, e)] = res[c * n + e];
+    g[at(c, e)] = Work<T>::out(res[c * n + e]);
   }
 }
 
@@ -426,6 +442,9 @@ void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_grid_plane_fft<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_z_fft<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_line_fft<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_plane_fft<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_z_fft<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_grid_line_fft<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_plane_fft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_z_fft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_line_fft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -445,6 +464,9 @@ template void launch_grid_plane_fft<float>(const Launch&, int, int);
 template void launch_grid_plane_fft<double>(const Launch&, int, int);
 template void launch_grid_z_fft<float>(const Launch&, int, int);
 template void launch_grid_z_fft<double>(const Launch&, int, int);
+template void launch_grid_line_fft<ff>(const Launch&, int, int, int);
+template void launch_grid_plane_fft<ff>(const Launch&, int, int);
+template void launch_grid_z_fft<ff>(const Launch&, int, int);
 template void launch_plane_vpsi<float>(const Launch&);
 template void launch_plane_vpsi<double>(const Launch&);
 template void launch_plane_density<float>(const Launch&, const double*);

@@ -560,10 +560,25 @@ __global__ void k_export_grid(KArgs ka, int sel, double* out) {
   }
 }
 
+// complex grid (C order (N1, N2, N3), interleaved) <-> the transform buffer gfft
+__global__ void k_grid_copy_c(KArgs ka, const double2* in, double2* out) {
+  GRID_EW_PROLOGUE
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    int i1, i2, i3;
+    grid_pt(P, i, &i1, &i2, &i3);
+    const size_t e = ((size_t)i1 * P.n2 + i2) * P.n3 + i3;
+    if (in) P.gfft[i] = in[e];
+    else out[e] = P.gfft[i];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static inline int ew_blocks(const Launch& L) { return L.map.total; }
+void launch_grid_copy_c(const Launch& L, const double2* in, double2* out) {
+  if (ew_blocks(L)) k_grid_copy_c<<<L.map.total, 256, 0, L.stream>>>(L.ka, in, out);
+}
 
 void launch_real_to_grid(const Launch& L, int src, int which) {
   if (ew_blocks(L)) k_real_to_grid<<<L.map.total, 256, 0, L.stream>>>(L.ka, src, which);

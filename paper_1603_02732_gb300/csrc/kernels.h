@@ -55,6 +55,8 @@ template <typename T> void launch_plane_vpsi(const Launch& L);
 template <typename T> void launch_plane_density(const Launch& L, const double* occ_override);
 // grid transforms of the work grids (T = double; T = float views the first half of the
 // same memory as single-precision complex)
+// T: float (FP32 grids), double (FP64), ff (float-float arithmetic on FP64 grids, ff.cuh)
+struct ff;
 template <typename T> void launch_grid_plane_fft(const Launch& L, int which, int sign);
 template <typename T> void launch_grid_z_fft(const Launch& L, int which, int sign);
 template <typename T> void launch_grid_line_fft(const Launch& L, int which, int sign, int axis);  // axis 0: x, 1: y
@@ -139,6 +141,8 @@ void launch_real_to_grid(const Launch& L, int src, int which);
 void launch_grid_real_part(const Launch& L, int which, int dst);
 void launch_hartree_g(const Launch& L, int which);
 void launch_export_grid(const Launch& L, int sel, double* out);
+// in != nullptr: gfft <- in; else out <- gfft (complex, C order (N1, N2, N3))
+void launch_grid_copy_c(const Launch& L, const double2* in, double2* out);
 template <typename T> void launch_veff(const Launch& L, const double* user_v);
 template <typename T> void launch_potential_g(const Launch& L);
 void launch_vion_g(const Launch& L);

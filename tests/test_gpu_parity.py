@@ -294,6 +294,25 @@ def test_graph_loop_equals_host_loop(sgo):
         assert res[0][2] == res[1][2], prec
 
 
+@pytest.mark.parametrize("grid", [(45, 40, 48), (100, 108, 10)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grid_fft_matches_fp64_fft(sgo, grid, precision):
+    """The SCF's grid transform (the potential's inverse and the output density's forward
+    FFT) against numpy's FP64 FFT, both signs: FP64 on the plain path, float-float
+    arithmetic on the mixed path, so both stay within 1e-12 of the largest output (an FP32
+    transform would sit near 1e-7).  (100, 108) planes take the line-block kernels."""
+    if precision == "fp64" and not _fp64_takes(grid):
+        pytest.skip("plane too large for the FP64 path")
+    ctx = sgo.Context(_struct(grid=grid, ecut=3.0), precision=precision)
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=grid) + 1j * rng.normal(size=grid)
+    for sign in (-1, 1):
+        got = ctx.grid_fft(x, sign)
+        ref = np.fft.fftn(x) if sign < 0 else np.fft.ifftn(x) * x.size
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err < 1e-12, (sign, err)
+
+
 def test_sub_batches_equal_one_batch(sgo):
     """Splitting a batch into sub-batches (each on its own graphs and stream, overlapping on
     the GPU) leaves every member's energy, forces and iteration count bit-identical, through

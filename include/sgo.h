@@ -46,6 +46,7 @@ extern "C" {
 
 typedef struct sgo_ctx sgo_ctx;     /* one structure: basis, tables, wavefunctions (opaque) */
 typedef struct sgo_batch sgo_batch; /* a population of contexts evaluated in lockstep (opaque) */
+typedef struct sgo_relax sgo_relax; /* the local-relaxation driver of one structure (opaque) */
 
 typedef enum {
   SGO_OK = 0,
@@ -236,6 +237,71 @@ SGO_API sgo_status sgo_density(sgo_ctx* ctx, int nvec, const double* psi, const 
 /* Warm start: when on (1), the next sgo_scf starts from the previous rho_in and
  * wavefunctions instead of the atomic guess (relaxation steps, Sec. II C). */
 SGO_API sgo_status sgo_set_warm(sgo_ctx* ctx, int on);
+
+/* ---- local relaxation (Sec. II C) ----------------------------------------------------
+ * A host-side driver that moves one structure to its nearest local minimum from energies
+ * and forces the caller evaluates (sgo_energy_forces_batch, or anything else).
+ *   SGO_RELAX_PCG: nonlinear preconditioned CG; the preconditioner is the inverse Hessian
+ *     of a classical force field fitted to the DFT forces (a shifted-force Morse pair
+ *     potential over periodic images within rc, parameters fitted by Levenberg-Marquardt
+ *     to every force set of the relaxation so far), from the second-order finite
+ *     difference of the fitted energy, without the three translational eigenpairs:
+ *     P = sum_j V_j V_j^T / |tau_j|, |tau_j| floored at 0.02 max|tau|.  Fit and P are
+ *     renewed every `refit` directions.
+ *   SGO_RELAX_CG: the same iteration with P = I / 0.5 (Ha/bohr^2).
+ *   SGO_RELAX_BFGS: inverse-Hessian BFGS from B0 = I / 0.5, steps capped per atom.
+ * (P)CG directions are Polak-Ribiere+ with restarts; each line takes a trial point at
+ * min(1, max_step / max_i |d_i|) and, unless the secant of the directional derivative
+ * lands within `accept` of it, one more evaluation at the secant's zero (kept between
+ * 0.1 times the trial step and max_step of displacement). */
+enum { SGO_RELAX_PCG = 0, SGO_RELAX_CG = 1, SGO_RELAX_BFGS = 2 };
+typedef struct {
+  int method;        /* SGO_RELAX_PCG, _CG or _BFGS */
+  double fmax;       /* converged when every atom's |F| < fmax (Ha/bohr) */
+  double max_step;   /* largest displacement of an atom per line or step (bohr) */
+  int refit;         /* PCG: renew the force-field fit and preconditioner every refit directions */
+  double rc;         /* force-field cutoff (bohr) */
+  double accept;     /* keep the trial point when the line minimum is within accept of it */
+  int max_evals;     /* stop after this many evaluations */
+} sgo_relax_opts;
+
+/* Defaults: PCG, fmax 1e-3 Ha/bohr, max_step 0.3 bohr, refit 3, rc 8 bohr, accept 0.1,
+ * 60 evaluations. */
+SGO_API void sgo_relax_opts_default(sgo_relax_opts* o);
+
+/* A driver for natoms atoms in the cell (9 doubles, rows a_i, bohr) starting at pos
+ * (natoms*3 Cartesian bohr, copied).  o may be NULL (defaults).  SGO_ERR_ARG for bad
+ * sizes, pointers or options. */
+SGO_API sgo_status sgo_relax_create(int natoms, const double cell[9], const double* pos, const sgo_relax_opts* o,
+                                    sgo_relax** out);
+
+/* Hand the driver the energy (Ha) and forces (natoms*3, Ha/bohr) at the positions it asked
+ * for last (the starting positions first).  It writes the next positions to evaluate to
+ * next_pos (natoms*3) and *state (may be NULL): 0 = evaluate next_pos, 1 = converged
+ * (next_pos = the converged positions), 2 = stopped without convergence (evaluation
+ * budget spent; next_pos = the last evaluated positions).  Calls after the end repeat
+ * the final positions.  SGO_ERR_NAN for non-finite forces. */
+SGO_API sgo_status sgo_relax_step(sgo_relax* r, double energy, const double* forces, double* next_pos, int* state);
+
+/* The positions the driver asks to evaluate next (natoms*3; the starting positions before
+ * the first step, the final ones once it has stopped). */
+SGO_API sgo_status sgo_relax_positions(const sgo_relax* r, double* pos);
+
+/* Evaluations consumed so far and the state (as sgo_relax_step reports it). */
+SGO_API sgo_status sgo_relax_info(const sgo_relax* r, int* evals, int* state);
+
+/* Relax every member of a batch together: relax[i] drives member i (same atom count).
+ * Each round evaluates all members at the positions their drivers ask for with one
+ * sgo_energy_forces_batch call (warm-started from the previous density and wavefunctions
+ * after the first round) and steps the drivers of the members still relaxing; ends when
+ * every driver has stopped or after max_rounds rounds.  per_item (may be NULL) receives
+ * each member's evaluation status (SGO_OK while its evaluations succeed; a member whose
+ * evaluation fails stops relaxing); *rounds (may be NULL) the rounds run.  Returns
+ * SGO_OK when the calls ran, SGO_ERR_CUDA on a CUDA failure, SGO_ERR_ARG for bad input. */
+SGO_API sgo_status sgo_relax_batch(sgo_batch* b, sgo_relax* const* relax, int max_rounds, int* rounds,
+                                   sgo_status* per_item);
+
+SGO_API void sgo_relax_destroy(sgo_relax* r);
 
 SGO_API void sgo_batch_destroy(sgo_batch* b);
 SGO_API void sgo_destroy(sgo_ctx* ctx);

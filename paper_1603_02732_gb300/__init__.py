@@ -41,6 +41,15 @@ class sgo_species(ctypes.Structure):
                 ("sigma_sr", ctypes.c_double), ("rp", ctypes.c_double), ("d_nl", ctypes.c_double)]
 
 
+class sgo_relax_opts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("fmax", ctypes.c_double), ("max_step", ctypes.c_double),
+                ("refit", ctypes.c_int), ("rc", ctypes.c_double), ("accept", ctypes.c_double),
+                ("max_evals", ctypes.c_int)]
+
+
+RELAX_METHODS = {"pcg": 0, "cg": 1, "bfgs": 2}
+
+
 class sgo_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("kT", ctypes.c_double), ("scf_tol_e", ctypes.c_double),
                 ("scf_tol_rho", ctypes.c_double), ("max_scf", ctypes.c_int), ("pulay_hist", ctypes.c_int),
@@ -78,6 +87,13 @@ _SIGS = {
     "sgo_subspace_matrix": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
     "sgo_block_update": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
     "sgo_batch_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "sgo_relax_opts_default": (None, [ctypes.POINTER(sgo_relax_opts)]),
+    "sgo_relax_create": (ctypes.c_int, [ctypes.c_int, _dp, _dp, ctypes.POINTER(sgo_relax_opts), ctypes.POINTER(_vp)]),
+    "sgo_relax_step": (ctypes.c_int, [_vp, ctypes.c_double, _dp, _dp, _ip]),
+    "sgo_relax_positions": (ctypes.c_int, [_vp, _dp]),
+    "sgo_relax_info": (ctypes.c_int, [_vp, _ip, _ip]),
+    "sgo_relax_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip]),
+    "sgo_relax_destroy": (None, [_vp]),
     "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
     "sgo_grid_fft": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
     "sgo_set_warm": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -283,6 +299,52 @@ class Context:
         return r
 
 
+class Relax:
+    """Local-relaxation driver of one structure (sgo_relax_*, see include/sgo.h): hand it the
+    energy and forces at the positions it asks for; it answers with the next positions."""
+
+    def __init__(self, cell, pos, method="pcg", **opts):
+        self.lib = load_library()
+        o = sgo_relax_opts()
+        self.lib.sgo_relax_opts_default(ctypes.byref(o))
+        o.method = RELAX_METHODS[method]
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown relaxation option {k}")
+            setattr(o, k, v)
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        self.natoms = len(pos)
+        cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+        h = _vp()
+        _check(self.lib.sgo_relax_create(self.natoms, _ptr(cell), _ptr(pos), ctypes.byref(o), ctypes.byref(h)),
+               "sgo_relax_create")
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.sgo_relax_destroy(h)
+            self.h = None
+
+    def positions(self):
+        out = np.zeros((self.natoms, 3))
+        _check(self.lib.sgo_relax_positions(self.h, _ptr(out)), "sgo_relax_positions")
+        return out
+
+    def step(self, energy, forces):
+        """Returns (next positions, state): 0 evaluate them, 1 converged, 2 stopped."""
+        f = np.ascontiguousarray(forces, dtype=np.float64).reshape(-1)
+        out = np.zeros((self.natoms, 3))
+        st = ctypes.c_int()
+        _check(self.lib.sgo_relax_step(self.h, float(energy), _ptr(f), _ptr(out), ctypes.byref(st)), "sgo_relax_step")
+        return out, st.value
+
+    def info(self):
+        ev, st = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.sgo_relax_info(self.h, ctypes.byref(ev), ctypes.byref(st)), "sgo_relax_info")
+        return dict(evals=ev.value, state=st.value)
+
+
 class Batch:
     """A population evaluated in lockstep (sgo_batch_create / sgo_energy_forces_batch)."""
 
@@ -336,6 +398,15 @@ class Batch:
         v = ctypes.c_longlong()
         _check(self.lib.sgo_batch_launches(self.h, ctypes.byref(v)), "sgo_batch_launches")
         return int(v.value)
+
+    def relax(self, drivers: Sequence["Relax"], max_rounds: int = 100):
+        """Relax every member with its driver (sgo_relax_batch); returns (rounds, statuses)."""
+        arr = (_vp * len(drivers))(*[d.h for d in drivers])
+        rounds = ctypes.c_int()
+        st = np.zeros(len(drivers), np.int32)
+        _check(self.lib.sgo_relax_batch(self.h, arr, int(max_rounds), ctypes.byref(rounds), _ptr(st, ctypes.c_int)),
+               "sgo_relax_batch")
+        return rounds.value, st
 
     def energy_forces_device(self, pos_dev, energies_dev, forces_dev, status_dev):
         """Device-pointer form: arguments are integer device addresses (e.g. tensor.data_ptr())."""

@@ -10,6 +10,8 @@
 namespace sgo {
 const char* last_error();
 }
+// relax.cpp (library-internal)
+extern "C" int sgo_relax_natoms(const sgo_relax* r);
 
 struct sgo_batch {
   std::vector<sgo_ctx*> ctxs;
@@ -265,6 +267,51 @@ sgo_status sgo_energy_forces_batch_device(sgo_batch* b, const double* pos_dev, d
   if (!b || !energies_dev || !forces_dev || !status_dev) return SGO_ERR_ARG;
   const sgo::Engine::DeviceIO io{pos_dev, energies_dev, forces_dev, status_dev};
   return run_batch(b, &io, nullptr);
+}
+
+sgo_status sgo_relax_batch(sgo_batch* b, sgo_relax* const* relax, int max_rounds, int* rounds,
+                           sgo_status* per_item) {
+  if (rounds) *rounds = 0;
+  if (!b || !relax || max_rounds < 0) return SGO_ERR_ARG;
+  const int n = (int)b->ctxs.size();
+  for (int i = 0; i < n; ++i)
+    if (!relax[i] || sgo_relax_natoms(relax[i]) != b->ctxs[i]->d.natom) return SGO_ERR_ARG;
+  std::vector<std::vector<double>> pos(n), F(n);
+  std::vector<const double*> pp(n);
+  std::vector<double*> fp(n);
+  std::vector<double> E(n);
+  std::vector<sgo_status> st(n, SGO_OK), evs(n);
+  std::vector<int> state(n, 0);
+  for (int i = 0; i < n; ++i) {
+    pos[i].resize(3 * b->ctxs[i]->d.natom);
+    F[i].resize(pos[i].size());
+    sgo_relax_positions(relax[i], pos[i].data());
+    sgo_relax_info(relax[i], nullptr, &state[i]);
+    pp[i] = pos[i].data();
+    fp[i] = F[i].data();
+  }
+  int r = 0;
+  for (; r < max_rounds; ++r) {
+    bool any = false;
+    for (int i = 0; i < n; ++i) any = any || (state[i] == 0 && st[i] == SGO_OK);
+    if (!any) break;
+    const sgo_status s = sgo_energy_forces_batch(b, pp.data(), E.data(), fp.data(), evs.data());
+    if (s != SGO_OK) return s;
+    for (int i = 0; i < n; ++i) {
+      b->ctxs[i]->warm = true;  // the next round starts from this density and these wavefunctions
+      if (state[i] != 0 || st[i] != SGO_OK) continue;
+      if (evs[i] != SGO_OK) {
+        st[i] = evs[i];
+        continue;
+      }
+      const sgo_status rs = sgo_relax_step(relax[i], E[i], F[i].data(), pos[i].data(), &state[i]);
+      if (rs != SGO_OK) st[i] = rs;
+    }
+  }
+  if (rounds) *rounds = r;
+  if (per_item)
+    for (int i = 0; i < n; ++i) per_item[i] = st[i];
+  return SGO_OK;
 }
 
 sgo_status sgo_batch_timer(sgo_batch* b, const char* kernel) {

@@ -7,7 +7,7 @@ nothing from the product package.  Plain FP64 NumPy, written from Sec. II C:
 * PCG: nonlinear preconditioned conjugate gradients whose preconditioner is an
   approximate inverse Hessian.  A classical force field is first fitted to reproduce the
   DFT atomic forces (here a Morse pair potential, parameters (D, a, r0), fitted by
-  Levenberg-Marquardt to every force set seen so far in the relaxation); its Hessian is
+  Levenberg-Marquardt to the force sets of the last HIST evaluated configurations); its Hessian is
   the second-order finite difference of the fitted energy (central differences of the
   fitted forces); the three zero eigenvalues of the translations are dropped and
   H^-1 = sum_j V_j V_j^T / tau_j over the others.  The fit and the preconditioner are
@@ -34,6 +34,7 @@ import numpy as np
 KAPPA0 = 0.5        # Ha/bohr^2: stiffness behind the unpreconditioned trial steps (CG, BFGS)
 FLOOR = 0.02        # kept eigenvalues of the force-field Hessian: |tau| >= FLOOR max|tau|
 H_FD = 1e-3         # bohr: central-difference step of the force-field Hessian
+HIST = 64           # the fit uses the last HIST evaluated configurations
 
 
 # ---------------------------------------------------------------------------
@@ -259,7 +260,7 @@ def relax(ef: Callable[[np.ndarray], Tuple[float, np.ndarray]], cell, pos0, meth
             elif P is None or ndir % refit == 0:
                 if theta is None:
                     theta = np.array([0.1, 1.0, nearest_neighbour(cell, x)])
-                theta = fit_force_field(hist, theta, cell, rc)
+                theta = fit_force_field(hist[-HIST:], theta, cell, rc)
                 P = truncated_inverse(ff_hessian(theta, cell, x, rc))
         else:
             P = np.eye(n3) / KAPPA0

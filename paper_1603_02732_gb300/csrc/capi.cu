@@ -1,6 +1,8 @@
 // extern "C" boundary of the engine (declarations and contracts in include/sgo.h).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -297,16 +299,25 @@ sgo_status sgo_relax_batch(sgo_batch* b, sgo_relax* const* relax, int max_rounds
     if (!any) break;
     const sgo_status s = sgo_energy_forces_batch(b, pp.data(), E.data(), fp.data(), evs.data());
     if (s != SGO_OK) return s;
-    for (int i = 0; i < n; ++i) {
-      b->ctxs[i]->warm = true;  // the next round starts from this density and these wavefunctions
-      if (state[i] != 0 || st[i] != SGO_OK) continue;
-      if (evs[i] != SGO_OK) {
-        st[i] = evs[i];
-        continue;
+    for (int i = 0; i < n; ++i) b->ctxs[i]->warm = true;  // the next round starts from these states
+    // the drivers are independent: step them on all host cores
+    std::atomic<int> next(0);
+    auto work = [&]() {
+      for (int i = next++; i < n; i = next++) {
+        if (state[i] != 0 || st[i] != SGO_OK) continue;
+        if (evs[i] != SGO_OK) {
+          st[i] = evs[i];
+          continue;
+        }
+        const sgo_status rs = sgo_relax_step(relax[i], E[i], F[i].data(), pos[i].data(), &state[i]);
+        if (rs != SGO_OK) st[i] = rs;
       }
-      const sgo_status rs = sgo_relax_step(relax[i], E[i], F[i].data(), pos[i].data(), &state[i]);
-      if (rs != SGO_OK) st[i] = rs;
-    }
+    };
+    const int nt = std::max(1, std::min(n, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
   }
   if (rounds) *rounds = r;
   if (per_item)

@@ -4,9 +4,9 @@
 // PCG: nonlinear preconditioned conjugate gradients whose preconditioner is the inverse
 // Hessian of a classical force field fitted to the DFT forces.  The force field is a
 // shifted-force Morse pair potential over periodic images, phi(r) = D [exp(-2a(r - r0)) -
-// 2 exp(-a(r - r0))], parameters theta = (D, a, r0) fitted by Levenberg-Marquardt to every
-// force set of the relaxation so far (with a weak pull towards the previous fit, which
-// picks a solution when few forces leave theta undetermined).  Its Hessian is the
+// 2 exp(-a(r - r0))], parameters theta = (D, a, r0) fitted by Levenberg-Marquardt to the
+// force sets of the last 64 evaluated configurations (with a weak pull towards the previous
+// fit, which picks a solution when few forces leave theta undetermined).  Its Hessian is the
 // second-order finite difference of the fitted energy; the three eigenpairs of the
 // translations (smallest |tau|) are dropped and P = sum_j V_j V_j^T / |tau_j| over the
 // others (|tau_j| floored at a fraction of the largest).  The fit and P are renewed every
@@ -31,6 +31,9 @@ constexpr double kKappa0 = 0.5;   // Ha/bohr^2 behind unpreconditioned steps (CG
 constexpr double kFloor = 0.02;   // kept force-field eigenvalues: |tau| >= kFloor max|tau|
 constexpr double kHfd = 1e-3;     // bohr: central-difference step of the force-field Hessian
 constexpr double kReg = 1e-6;     // weight of the pull towards the previous fit
+constexpr int kHist = 64;         // the fit uses the last kHist evaluated configurations
+constexpr double kSkin = 1.0;     // bohr: pair lists keep r < rc + kSkin (displacements of the
+                                  // finite-difference Hessian stay far below it)
 
 using Vec = std::vector<double>;
 
@@ -75,24 +78,45 @@ Vec image_vectors(const double* cell, double rc) {
   return L;
 }
 
-// forces of the shifted-force Morse field: F_i = sum_{j != i, L} (phi'(r) - phi'(rc)) rv / r,
-// rv = R_j + L - R_i, over r < rc
-void ff_forces(const double* th, const Vec& L, double rc, int n, const double* x, double* F) {
-  const double dc = morse_dphi(th, rc);
-  const int nl = (int)L.size() / 3;
-  for (int i = 0; i < 3 * n; ++i) F[i] = 0.0;
+// (i, j, image) triples with |R_j + L - R_i| < rmax, j != i: the candidates of the force
+// sum for this configuration and for any configuration within (rmax - rc) / 2 of it
+struct PairList {
+  std::vector<int> i, j;
+  Vec L;
+};
+PairList build_pairs(const Vec& Limg, double rmax, int n, const double* x) {
+  PairList pl;
+  const int nl = (int)Limg.size() / 3;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       if (i == j) continue;
       for (int l = 0; l < nl; ++l) {
         double rv[3];
-        for (int c = 0; c < 3; ++c) rv[c] = x[3 * j + c] + L[3 * l + c] - x[3 * i + c];
-        const double r = std::sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
-        if (!(r < rc) || !(r > 1e-12)) continue;
-        const double f = (morse_dphi(th, r) - dc) / r;
-        for (int c = 0; c < 3; ++c) F[3 * i + c] += f * rv[c];
+        for (int c = 0; c < 3; ++c) rv[c] = x[3 * j + c] + Limg[3 * l + c] - x[3 * i + c];
+        if (rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2] < rmax * rmax) {
+          pl.i.push_back(i);
+          pl.j.push_back(j);
+          for (int c = 0; c < 3; ++c) pl.L.push_back(Limg[3 * l + c]);
+        }
       }
     }
+  return pl;
+}
+
+// forces of the shifted-force Morse field: F_i = sum_{j != i, L} (phi'(r) - phi'(rc)) rv / r,
+// rv = R_j + L - R_i, over r < rc (the pairs of a list built for nearby positions)
+void ff_forces(const double* th, const PairList& pl, double rc, int n, const double* x, double* F) {
+  const double dc = morse_dphi(th, rc);
+  for (int k = 0; k < 3 * n; ++k) F[k] = 0.0;
+  for (size_t p = 0; p < pl.i.size(); ++p) {
+    const int i = pl.i[p], j = pl.j[p];
+    double rv[3];
+    for (int c = 0; c < 3; ++c) rv[c] = x[3 * j + c] + pl.L[3 * p + c] - x[3 * i + c];
+    const double r = std::sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+    if (!(r < rc) || !(r > 1e-12)) continue;
+    const double f = (morse_dphi(th, r) - dc) / r;
+    for (int c = 0; c < 3; ++c) F[3 * i + c] += f * rv[c];
+  }
 }
 
 // 3x3 linear solve by Gaussian elimination with partial pivoting
@@ -175,8 +199,9 @@ struct sgo_relax {
   double cell[9];
   sgo_relax_opts o;
   Vec L, Lnn;                    // images within rc (force field) and within 1 bohr (neighbours)
-  // evaluated configurations (the force-field fit uses all of them)
+  // the last kHist evaluated configurations, their forces and pair lists (the fit's data)
   std::vector<Vec> hx, hf;
+  std::vector<PairList> hp;
   int evals = 0, state = 0;      // state: 0 running, 1 converged, 2 evaluation budget spent
   Vec x, g;                      // current point and gradient (-F)
   Vec pending;                   // positions handed out for evaluation
@@ -194,9 +219,9 @@ struct sgo_relax {
 
 namespace {
 
-Vec ff_forces_v(const sgo_relax* r, const double* th, const Vec& x) {
+Vec ff_forces_v(const sgo_relax* r, const double* th, const PairList& pl, const Vec& x) {
   Vec F(x.size());
-  ff_forces(th, r->L, r->o.rc, r->n, x.data(), F.data());
+  ff_forces(th, pl, r->o.rc, r->n, x.data(), F.data());
   return F;
 }
 
@@ -215,7 +240,7 @@ void fit_force_field(sgo_relax* r) {
     Vec res;
     res.reserve(ncomp + 3);
     for (size_t k = 0; k < r->hx.size(); ++k) {
-      const Vec F = ff_forces_v(r, t, r->hx[k]);
+      const Vec F = ff_forces_v(r, t, r->hp[k], r->hx[k]);
       for (size_t i = 0; i < F.size(); ++i) res.push_back(F[i] - r->hf[k][i]);
     }
     for (int k = 0; k < 3; ++k) res.push_back(sw * (t[k] - t0[k]) / t0[k]);
@@ -277,11 +302,12 @@ void fit_force_field(sgo_relax* r) {
 void build_preconditioner(sgo_relax* r) {
   const int m = 3 * r->n;
   Vec H((size_t)m * m);
+  const PairList pl = build_pairs(r->L, r->o.rc + kSkin, r->n, r->x.data());
   for (int k = 0; k < m; ++k) {
     Vec xp = r->x, xm = r->x;
     xp[k] += kHfd;
     xm[k] -= kHfd;
-    const Vec Fp = ff_forces_v(r, r->theta, xp), Fm = ff_forces_v(r, r->theta, xm);
+    const Vec Fp = ff_forces_v(r, r->theta, pl, xp), Fm = ff_forces_v(r, r->theta, pl, xm);
     for (int i = 0; i < m; ++i) H[(size_t)i * m + k] = -(Fp[i] - Fm[i]) / (2.0 * kHfd);
   }
   for (int i = 0; i < m; ++i)
@@ -450,6 +476,12 @@ sgo_status sgo_relax_step(sgo_relax* r, double energy, const double* forces, dou
   r->evals += 1;
   r->hx.push_back(xe);
   r->hf.push_back(F);
+  r->hp.push_back(build_pairs(r->L, r->o.rc + kSkin, r->n, xe.data()));
+  if ((int)r->hx.size() > kHist) {
+    r->hx.erase(r->hx.begin());
+    r->hf.erase(r->hf.begin());
+    r->hp.erase(r->hp.begin());
+  }
   Vec ge(m);
   for (int i = 0; i < m; ++i) ge[i] = -F[i];
   if (fmax_of(r->n, forces) < r->o.fmax) {

@@ -345,6 +345,34 @@ def test_sub_batches_equal_one_batch(sgo):
             assert res[1][2] == res[k][2], (prec, k)
 
 
+def test_relax_batch_reaches_the_oracle_minimum(sgo):
+    """Local relaxation (Sec. II C) of a small batch through sgo_relax_batch (PCG driver,
+    warm-started batched evaluations) ends where the oracle's PCG relaxation on the oracle
+    DFT ends: both converge to |F| < 1e-3 Ha/bohr, at geometries within 5e-3 bohr (after
+    removing the centroid) and energies within 1e-5 Ha/atom."""
+    from oracle import dft
+    from oracle import relax as rx
+    sts = [workloads.tiny(nat=2, ecut=3.0, seed=7, kT=0.01), _struct(seed=3, ecut=3.0, nat=3)]
+    fmax = 1e-3
+    import bench
+    ctxs = [sgo.Context(st, precision="mixed", **bench._tols("mixed", st)) for st in sts]
+    b = sgo.Batch(ctxs)
+    drivers = [sgo.Relax(st.cell, st.pos, method="pcg", fmax=fmax, max_evals=60) for st in sts]
+    rounds, status = b.relax(drivers, max_rounds=80)
+    assert list(status) == [0] * len(sts)
+    E, F, st_ = b.energy_forces([d.positions() for d in drivers])
+    for i, st in enumerate(sts):
+        assert drivers[i].info()["state"] == 1, i
+        assert np.linalg.norm(F[i], axis=1).max() < fmax
+        tr = rx.relax(lambda p, st=st: dft.evaluate(st, pos=p), st.cell, st.pos, method="pcg", fmax=fmax,
+                      max_evals=60)
+        assert tr.converged, i
+        a = drivers[i].positions() - drivers[i].positions().mean(axis=0)
+        o = tr.final - tr.final.mean(axis=0)
+        assert np.abs(a - o).max() < 5e-3, (i, np.abs(a - o).max())
+        assert abs(E[i] - tr.energies[-1]) / st.natoms < 1e-5, i
+
+
 def test_autotuned_batch(sgo):
     """The autotuner keeps one of its candidates for each knob, and the tuned batch's
     energies and forces agree with the default-knob batch to the mixed tolerances (the knobs

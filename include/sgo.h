@@ -287,6 +287,10 @@ SGO_API sgo_status sgo_relax_step(sgo_relax* r, double energy, const double* for
  * the first step, the final ones once it has stopped). */
 SGO_API sgo_status sgo_relax_positions(const sgo_relax* r, double* pos);
 
+/* The lowest-energy configuration evaluated so far: its energy and positions (either may
+ * be NULL).  SGO_ERR_ARG before the first step. */
+SGO_API sgo_status sgo_relax_best(const sgo_relax* r, double* energy, double* pos);
+
 /* Evaluations consumed so far and the state (as sgo_relax_step reports it). */
 SGO_API sgo_status sgo_relax_info(const sgo_relax* r, int* evals, int* state);
 
@@ -302,6 +306,39 @@ SGO_API sgo_status sgo_relax_batch(sgo_batch* b, sgo_relax* const* relax, int ma
                                    sgo_status* per_item);
 
 SGO_API void sgo_relax_destroy(sgo_relax* r);
+
+/* ---- global search: differential evolution (Sec. II B) --------------------------------
+ * A population of np >= 4 structures with the same atoms (species fixed per atom slot) in
+ * one cell (9 doubles, rows a_i, bohr); pop is np x natoms x 3 Cartesian bohr, f the np
+ * relaxed free energies.  For each individual i, with the SGO_DE_RANDOMS uniforms
+ * u[i][0..6] in [0, 1) (the caller draws them):
+ *   partners r1, r2, r3: distinct and != i, drawn without replacement by u[i][0..2];
+ *   triangle mutation (Eq. 2): V = (X1+X2+X3)/3 + (p2-p1)(X1-X2) + (p3-p2)(X2-X3)
+ *     + (p1-p3)(X3-X1), p_k = |f_k| / sum |f|, in fractional coordinates with
+ *     minimum-image differences from X1, wrapped into the cell;
+ *   cut-and-splice crossover of V (kept side) and X_i (fill): SGO_DE_PLANE keeps V's atoms
+ *     above a plane through its centre (normal from u[i][3..4], uniform on the sphere) and
+ *     fills each species with X_i's atoms of lowest projection on the normal;
+ *     SGO_DE_SPHERE keeps V's atoms within u[i][6] times V's largest distance from its
+ *     centre and fills with X_i's atoms farthest from X_i's centre; SGO_DE_RANDOM_SCHEME
+ *     picks the plane when u[i][5] < 1/2, else the sphere;
+ *   repair: pairs closer than d_min (minimum image) are pushed apart in passes.
+ * Children keep the species of each slot. */
+enum { SGO_DE_RANDOM_SCHEME = 0, SGO_DE_PLANE = 1, SGO_DE_SPHERE = 2 };
+#define SGO_DE_RANDOMS 7
+SGO_API sgo_status sgo_de_offspring(int np, int natoms, const double cell[9], const int* species, const double* pop,
+                                    const double* f, const double* u, int scheme, double d_min, double* children);
+
+/* One DE generation on a batch whose member i evaluates individual i (same atoms, same
+ * cell): the offspring above, each relaxed (cold start, then warm) by its own driver with
+ * options ro over at most max_rounds batched evaluations, then greedy selection: the
+ * lowest-energy configuration of child i's relaxation replaces pop[i], f[i] when lower.
+ * replaced (may be NULL) receives 1 where it did; child_f (may be NULL) the children's
+ * energies (+inf where a child's evaluation failed).  SGO_ERR_ARG for bad input,
+ * SGO_ERR_CUDA on a CUDA failure. */
+SGO_API sgo_status sgo_de_generation(sgo_batch* b, const double cell[9], const int* species, double* pop, double* f,
+                                     const double* u, int scheme, double d_min, const sgo_relax_opts* ro,
+                                     int max_rounds, int* replaced, double* child_f);
 
 SGO_API void sgo_batch_destroy(sgo_batch* b);
 SGO_API void sgo_destroy(sgo_ctx* ctx);

@@ -48,6 +48,35 @@ class sgo_relax_opts(ctypes.Structure):
 
 
 RELAX_METHODS = {"pcg": 0, "cg": 1, "bfgs": 2}
+DE_SCHEMES = {"random": 0, "plane": 1, "sphere": 2}
+DE_RANDOMS = 7
+
+
+def relax_opts(method="pcg", **opts) -> "sgo_relax_opts":
+    o = sgo_relax_opts()
+    load_library().sgo_relax_opts_default(ctypes.byref(o))
+    o.method = RELAX_METHODS[method]
+    for k, v in opts.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown relaxation option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def de_offspring(cell, species, pop, f, u, scheme="random", d_min=2.0):
+    """Children of a DE population (sgo_de_offspring, Sec. II B): pop (np, natoms, 3) bohr,
+    f (np,) energies, u (np, DE_RANDOMS) uniforms in [0, 1)."""
+    lib = load_library()
+    pop = np.ascontiguousarray(pop, dtype=np.float64)
+    np_, na = pop.shape[0], pop.shape[1]
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(np_, DE_RANDOMS)
+    sp = np.ascontiguousarray(species, dtype=np.int32)
+    cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    out = np.zeros_like(pop)
+    _check(lib.sgo_de_offspring(np_, na, _ptr(cell), _ptr(sp, ctypes.c_int), _ptr(pop), _ptr(f), _ptr(u),
+                                DE_SCHEMES[scheme], float(d_min), _ptr(out)), "sgo_de_offspring")
+    return out
 
 
 class sgo_opts(ctypes.Structure):
@@ -94,6 +123,11 @@ _SIGS = {
     "sgo_relax_info": (ctypes.c_int, [_vp, _ip, _ip]),
     "sgo_relax_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip]),
     "sgo_relax_destroy": (None, [_vp]),
+    "sgo_relax_best": (ctypes.c_int, [_vp, _dp, _dp]),
+    "sgo_de_offspring": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _ip, _dp, _dp, _dp, ctypes.c_int,
+                                        ctypes.c_double, _dp]),
+    "sgo_de_generation": (ctypes.c_int, [_vp, _dp, _ip, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
+                                         ctypes.POINTER(sgo_relax_opts), ctypes.c_int, _ip, _dp]),
     "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
     "sgo_grid_fft": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
     "sgo_set_warm": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -305,13 +339,7 @@ class Relax:
 
     def __init__(self, cell, pos, method="pcg", **opts):
         self.lib = load_library()
-        o = sgo_relax_opts()
-        self.lib.sgo_relax_opts_default(ctypes.byref(o))
-        o.method = RELAX_METHODS[method]
-        for k, v in opts.items():
-            if not hasattr(o, k):
-                raise TypeError(f"unknown relaxation option {k}")
-            setattr(o, k, v)
+        o = relax_opts(method, **opts)
         pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
         self.natoms = len(pos)
         cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
@@ -338,6 +366,13 @@ class Relax:
         st = ctypes.c_int()
         _check(self.lib.sgo_relax_step(self.h, float(energy), _ptr(f), _ptr(out), ctypes.byref(st)), "sgo_relax_step")
         return out, st.value
+
+    def best(self):
+        """(energy, positions) of the lowest-energy configuration evaluated so far."""
+        e = ctypes.c_double()
+        out = np.zeros((self.natoms, 3))
+        _check(self.lib.sgo_relax_best(self.h, ctypes.byref(e), _ptr(out)), "sgo_relax_best")
+        return e.value, out
 
     def info(self):
         ev, st = ctypes.c_int(), ctypes.c_int()
@@ -407,6 +442,23 @@ class Batch:
         _check(self.lib.sgo_relax_batch(self.h, arr, int(max_rounds), ctypes.byref(rounds), _ptr(st, ctypes.c_int)),
                "sgo_relax_batch")
         return rounds.value, st
+
+    def de_generation(self, cell, species, pop, f, u, scheme="random", d_min=2.0, max_rounds=40, method="pcg",
+                      **relax):
+        """One DE generation (sgo_de_generation): offspring, their relaxation on this batch,
+        greedy selection.  Returns (pop, f, replaced, child energies), new arrays."""
+        pop = np.array(pop, dtype=np.float64, order="C")
+        f = np.array(f, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        sp = np.ascontiguousarray(species, dtype=np.int32)
+        cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+        rep = np.zeros(len(f), np.int32)
+        cf = np.zeros(len(f))
+        o = relax_opts(method, **relax)
+        _check(self.lib.sgo_de_generation(self.h, _ptr(cell), _ptr(sp, ctypes.c_int), _ptr(pop), _ptr(f), _ptr(u),
+                                          DE_SCHEMES[scheme], float(d_min), ctypes.byref(o), int(max_rounds),
+                                          _ptr(rep, ctypes.c_int), _ptr(cf)), "sgo_de_generation")
+        return pop, f, rep.astype(bool), cf
 
     def energy_forces_device(self, pos_dev, energies_dev, forces_dev, status_dev):
         """Device-pointer form: arguments are integer device addresses (e.g. tensor.data_ptr())."""

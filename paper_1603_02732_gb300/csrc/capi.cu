@@ -325,6 +325,54 @@ sgo_status sgo_relax_batch(sgo_batch* b, sgo_relax* const* relax, int max_rounds
   return SGO_OK;
 }
 
+sgo_status sgo_de_generation(sgo_batch* b, const double cell[9], const int* species, double* pop, double* f,
+                             const double* u, int scheme, double d_min, const sgo_relax_opts* ro, int max_rounds,
+                             int* replaced, double* child_f) {
+  if (!b || !cell || !species || !pop || !f || !u || max_rounds < 0) return SGO_ERR_ARG;
+  const int np = (int)b->ctxs.size();
+  const int na = b->ctxs[0]->d.natom;
+  for (auto* c : b->ctxs)
+    if (c->d.natom != na) return SGO_ERR_ARG;
+  const size_t sz = 3 * (size_t)na;
+  std::vector<double> kids(sz * np);
+  sgo_status s = sgo_de_offspring(np, na, cell, species, pop, f, u, scheme, d_min, kids.data());
+  if (s != SGO_OK) return s;
+  std::vector<sgo_relax*> drv(np, nullptr);
+  auto cleanup = [&]() {
+    for (auto* d : drv) sgo_relax_destroy(d);
+  };
+  for (int i = 0; i < np; ++i) {
+    s = sgo_relax_create(na, cell, kids.data() + sz * i, ro, &drv[i]);
+    if (s != SGO_OK) {
+      cleanup();
+      return s;
+    }
+    b->ctxs[i]->warm = false;  // a new structure: the first evaluation starts from the atomic guess
+  }
+  std::vector<sgo_status> st(np, SGO_OK);
+  int rounds = 0;
+  s = sgo_relax_batch(b, drv.data(), max_rounds, &rounds, st.data());
+  if (s != SGO_OK) {
+    cleanup();
+    return s;
+  }
+  std::vector<double> best(sz);
+  for (int i = 0; i < np; ++i) {
+    double e = INFINITY;
+    const bool ok = st[i] == SGO_OK && sgo_relax_best(drv[i], &e, best.data()) == SGO_OK;
+    if (!ok) e = INFINITY;
+    if (child_f) child_f[i] = e;
+    const bool better = ok && e < f[i];
+    if (better) {
+      std::memcpy(pop + sz * i, best.data(), sizeof(double) * sz);
+      f[i] = e;
+    }
+    if (replaced) replaced[i] = better ? 1 : 0;
+  }
+  cleanup();
+  return SGO_OK;
+}
+
 sgo_status sgo_batch_timer(sgo_batch* b, const char* kernel) {
   if (!b) return SGO_ERR_ARG;
   for (auto& e : b->engs)

@@ -202,7 +202,9 @@ struct sgo_relax {
   // the last kHist evaluated configurations, their forces and pair lists (the fit's data)
   std::vector<Vec> hx, hf;
   std::vector<PairList> hp;
-  int evals = 0, state = 0;      // state: 0 running, 1 converged, 2 evaluation budget spent
+  int evals = 0, state = 0;      // state: 0 running, 1 converged, 2 stopped unconverged
+  double best_e = 0.0;           // the lowest-energy configuration evaluated so far
+  Vec best_x;
   Vec x, g;                      // current point and gradient (-F)
   Vec pending;                   // positions handed out for evaluation
   int phase = 0;                 // 0 initial point, 1 trial point, 2 line minimum, 3 BFGS step
@@ -473,6 +475,10 @@ sgo_status sgo_relax_step(sgo_relax* r, double energy, const double* forces, dou
     if (!std::isfinite(forces[i])) return SGO_ERR_NAN;
   const Vec F(forces, forces + m);
   const Vec xe = r->pending;  // the configuration these forces belong to
+  if (r->evals == 0 || energy < r->best_e) {
+    r->best_e = energy;
+    r->best_x = xe;
+  }
   r->evals += 1;
   r->hx.push_back(xe);
   r->hf.push_back(F);
@@ -549,6 +555,13 @@ sgo_status sgo_relax_step(sgo_relax* r, double energy, const double* forces, dou
 sgo_status sgo_relax_positions(const sgo_relax* r, double* pos) {
   if (!r || !pos) return SGO_ERR_ARG;
   std::memcpy(pos, r->pending.data(), sizeof(double) * 3 * r->n);
+  return SGO_OK;
+}
+
+sgo_status sgo_relax_best(const sgo_relax* r, double* energy, double* pos) {
+  if (!r || r->evals == 0) return SGO_ERR_ARG;
+  if (energy) *energy = r->best_e;
+  if (pos) std::memcpy(pos, r->best_x.data(), sizeof(double) * 3 * r->n);
   return SGO_OK;
 }
 

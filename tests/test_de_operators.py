@@ -1,0 +1,47 @@
+"""The library's DE operators (csrc/de.cpp, through the C ABI) against the oracle's
+(oracle/de.py): the same population, energies and random numbers must give the same
+children.  Host code only: runs without a GPU.  On the GPU,
+tests/test_gpu_parity.py::test_de_generation_matches_the_oracle runs a whole generation."""
+import numpy as np
+import pytest
+
+from oracle import de
+
+
+@pytest.fixture(scope="module")
+def sgo():
+    from paper_1603_02732_gb300 import build
+    build.build()
+    import paper_1603_02732_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+def _population(np_, na, seed, cell):
+    rng = np.random.default_rng(seed)
+    pop = rng.uniform(0, 1, size=(np_, na, 3)) @ cell
+    f = -10.0 - rng.uniform(size=np_)
+    return pop, f
+
+
+CELLS = [np.diag([10.26, 10.26, 10.26]), np.array([[12.0, 0.0, 0.0], [1.0, 11.5, 0.0], [0.5, -0.8, 12.5]])]
+
+
+@pytest.mark.parametrize("scheme", ["random", "plane", "sphere"])
+@pytest.mark.parametrize("cell", range(2))
+def test_offspring_match_oracle(sgo, scheme, cell):
+    A = CELLS[cell]
+    species = np.array([0, 0, 1, 0, 1, 0, 0, 1])
+    for seed in range(6):
+        pop, f = _population(8, 8, seed, A)
+        u = np.random.default_rng(100 + seed).uniform(size=(8, de.RANDOMS))
+        got = sgo.de_offspring(A, species, pop, f, u, scheme=scheme, d_min=2.0)
+        ref = de.offspring(A, species, pop, f, u, scheme=scheme, d_min=2.0)
+        assert np.abs(got - ref).max() < 1e-9, (seed, np.abs(got - ref).max())
+
+
+def test_offspring_argument_checks(sgo):
+    A = CELLS[0]
+    pop, f = _population(3, 4, 0, A)
+    with pytest.raises(sgo.SgoError):   # fewer than four individuals: no three partners
+        sgo.de_offspring(A, np.zeros(4), pop, f, np.zeros((3, de.RANDOMS)))

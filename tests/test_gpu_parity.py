@@ -373,6 +373,43 @@ def test_relax_batch_reaches_the_oracle_minimum(sgo):
         assert abs(E[i] - tr.energies[-1]) / st.natoms < 1e-5, i
 
 
+def test_de_generation_matches_the_oracle(sgo):
+    """One DE generation (Sec. II B) of four 3-atom individuals through sgo_de_generation
+    (offspring from given random numbers, PCG relaxation of each child on the batch, greedy
+    selection) against the same generation built from the oracle's operators, relaxation
+    and DFT: each child's best relaxed energy agrees to 5e-5 Ha/atom and the selection
+    agrees wherever the child and parent energies differ by more than that."""
+    import bench
+    from oracle import de
+    from oracle import relax as rx
+    base = _struct(seed=3, ecut=3.0, nat=3)
+    rng = np.random.default_rng(9)
+    inv = np.linalg.inv(base.cell)
+    pop = []
+    while len(pop) < 4:
+        x = rng.uniform(size=(3, 3)) @ base.cell
+        d = [np.linalg.norm(de._mi((x[j] - x[i]) @ inv) @ base.cell) for i in range(3) for j in range(i + 1, 3)]
+        if min(d) > 2.2:
+            pop.append(x)
+    pop = np.array(pop)
+    f = np.array([dft.evaluate(base, pos=x)[0] for x in pop])
+    u = rng.uniform(size=(4, de.RANDOMS))
+    species = np.zeros(3, np.int32)
+    ctxs = [sgo.Context(dataclasses.replace(base, pos=x), precision="mixed", **bench._tols("mixed", base))
+            for x in pop]
+    b = sgo.Batch(ctxs)
+    pop2, f2, rep, cf = b.de_generation(base.cell, species, pop, f, u, max_rounds=60, fmax=1e-3, max_evals=60)
+    kids = de.offspring(base.cell, species, pop, f, u)
+    for i in range(4):
+        tr = rx.relax(lambda p: dft.evaluate(base, pos=p), base.cell, kids[i], method="pcg", fmax=1e-3,
+                      max_evals=60)
+        e_ref = min(tr.energies)
+        assert abs(cf[i] - e_ref) / 3 < 5e-5, (i, cf[i], e_ref)
+        if abs(e_ref - f[i]) / 3 > 5e-5:
+            assert rep[i] == (e_ref < f[i]), i
+        assert f2[i] <= f[i]
+
+
 def test_autotuned_batch(sgo):
     """The autotuner keeps one of its candidates for each knob, and the tuned batch's
     energies and forces agree with the default-knob batch to the mixed tolerances (the knobs

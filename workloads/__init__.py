@@ -254,6 +254,34 @@ def de_population(n: int = 64, start: int = 0) -> List[Structure]:
     return [de_candidate(i) for i in range(start, start + n)]
 
 
+def de_search_population(n: int = 8, natoms: int = 8, seed: int = 5000, dmin: float = 3.0) -> List[Structure]:
+    """A DE search population (Sec. II B; the paper's population of 8): n structures of
+    natoms Z_val=4 atoms in the 10.26 bohr cubic cell of the diamond8 workload (Ecut 10 Ha,
+    32^3 grid, 20 bands, kT = 0.01 Ha), positions uniform with min-image distance dmin."""
+    base = diamond8(jitter=0.0)
+    cell = base.cell
+    inv = np.linalg.inv(cell)
+    shifts = np.array([[a, b, c] for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)],
+                      dtype=np.float64) @ cell
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        pos: List[np.ndarray] = []
+        while len(pos) < natoms:
+            p = rng.uniform(size=3) @ cell
+            ok = True
+            for q in pos:
+                df = (p - q) @ inv
+                df -= np.round(df)
+                if np.min(np.linalg.norm(df @ cell + shifts, axis=1)) < dmin:
+                    ok = False
+                    break
+            if ok:
+                pos.append(p)
+        out.append(dataclasses.replace(base, name=f"dex{k}", pos=np.array(pos), kT=0.01))
+    return out
+
+
 def tiny(nat: int = 2, ecut: float = 3.0, seed: int = 7, kT: float = 0.01, nbands: int = None,
          skew: bool = True, species=None) -> Structure:
     """A small skewed cell for fast CPU and GPU unit tests (tens to hundreds of plane waves)."""

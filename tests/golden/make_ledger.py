@@ -1,0 +1,42 @@
+"""Write the oracle's full-size reference values for the error ledger of the configs the
+population bench does not cover (the 24-atom monolayer and the 13-atom cluster).
+
+Runs only oracle/ (plain FP64 SCF, tight tolerances) on the workloads' seeded inputs and
+stores, per config, the free energy, the energy terms, every eigenvalue and occupation and
+every force component in tests/golden/ledger_<config>.json.  Slow (CPU minutes to hours):
+run it by hand, never from a test.
+
+    python tests/golden/make_ledger.py honeycomb24 [cluster13]
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+import workloads  # noqa: E402
+
+
+def main(names):
+    for name in names:
+        st = workloads.CONFIGS[name]()
+        t0 = time.time()
+        r = oracle.scf(st)
+        dt = time.time() - t0
+        out = dict(_source=f"oracle.scf on workloads.CONFIGS['{name}'](), FP64, default tolerances "
+                           f"(|dF| < 1e-8 Ha, density residual < 1e-7), {r.n_iter} iterations, {dt:.0f} s",
+                   natoms=int(st.natoms), free_energy=float(r.free_energy), energy=float(r.energy),
+                   terms={k: float(v) for k, v in r.terms.items()}, eig=[float(x) for x in r.eig],
+                   occ=[float(x) for x in r.occ], forces=np.asarray(r.forces).tolist(), n_iter=int(r.n_iter))
+        with open(os.path.join(HERE, f"ledger_{name}.json"), "w") as fh:
+            json.dump(out, fh, indent=1)
+        print(name, r.free_energy, r.n_iter, f"{dt:.0f} s", flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or ["honeycomb24"])

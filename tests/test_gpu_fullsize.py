@@ -67,3 +67,46 @@ def test_monolayer_mixed_matches_fp64(sgo):
     assert abs(emx - e64) / st.natoms < 1e-5
     assert np.abs(fmx - f64).max() < 1e-4
     assert np.abs(f64.sum(axis=0)).max() < 1e-3  # egg-box only
+
+
+def _ledger_configs():
+    import glob
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    return sorted(os.path.basename(p)[len("ledger_"):-len(".json")] for p in glob.glob(os.path.join(here, "ledger_*.json")))
+
+
+@pytest.mark.parametrize("name", _ledger_configs())
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fullsize_error_ledger(sgo, name, precision):
+    """Error ledger at full size against stored oracle values (tests/golden/ledger_*.json,
+    written by tests/golden/make_ledger.py from oracle/ alone): every eigenvalue with
+    occupation above 1e-6, every energy term, the free energy and every force component.
+    Bounds: the accuracy gate (1e-5 Ha/atom, 1e-4 Ha/bohr) for F and forces; 1e-5 Ha/atom
+    per term; 1e-5 Ha per eigenvalue (FP64) or 5e-5 Ha (mixed)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"ledger_{name}.json")
+    ref = json.load(open(path))
+    st = workloads.CONFIGS[name]()
+    tol = dict(scf_tol_e=1e-8, scf_tol_rho=1e-7) if precision == "fp64" else dict(scf_tol_e=1e-7 * st.natoms,
+                                                                                   scf_tol_rho=1e-5)
+    ctx = sgo.Context(st, precision=precision, **tol)
+    E, F = ctx.energy_forces()
+    n = st.natoms
+    eig, occ = ctx.eigen()
+    terms = ctx.terms()
+    rf = np.array(ref["forces"])
+    ledger = dict(dF_per_atom=abs(E - ref["free_energy"]) / n, max_dforce=float(np.abs(F - rf).max()))
+    keys = (("kinetic", "kinetic"), ("nonlocal", "nonlocal_"), ("local", "local"), ("hartree", "hartree"),
+            ("xc", "xc"), ("ewald", "ewald"), ("minus_ts", "minus_ts"))
+    for k, rk in keys:
+        ledger[k] = abs(terms[k] - ref["terms"][rk]) / n
+    occd = np.array(ref["occ"]) > 1e-6
+    de = np.abs(eig - np.array(ref["eig"]))[occd]
+    ledger["max_deig_occupied"] = float(de.max())
+    assert ledger["dF_per_atom"] < 1e-5, ledger
+    assert ledger["max_dforce"] < 1e-4, ledger
+    for k, _ in keys:
+        assert ledger[k] < 1e-5, (k, ledger)
+    assert ledger["max_deig_occupied"] < (1e-5 if precision == "fp64" else 5e-5), ledger

@@ -213,18 +213,19 @@ def _warm_steps(args, sgo, batch, ctxs, pop, pos_host, pos_dev, e_dev, f_dev, s_
 RELAX_FMAX = 0.02 / 51.42208619083232   # 0.02 eV/Angstrom in Ha/bohr (Sec. II C's loose criterion)
 
 
-def _relax_population(sgo, batch, ctxs, pop, max_rounds=60):
+def _relax_population(sgo, batch, ctxs, pop, max_rounds=60, method="pcg"):
     """Local relaxation (Sec. II C) of every member with the PCG driver (force-fitted
     preconditioner) over warm-started batched evaluations (sgo_relax_batch).  Every round
     evaluates the whole batch once."""
-    drivers = [sgo.Relax(st.cell, st.pos, method="pcg", fmax=RELAX_FMAX, max_evals=max_rounds) for st in pop]
+    drivers = [sgo.Relax(st.cell, st.pos, method=method, fmax=RELAX_FMAX, max_evals=max_rounds) for st in pop]
     t0 = time.perf_counter()
     rounds, status = batch.relax(drivers, max_rounds=max_rounds)
     dt = time.perf_counter() - t0
     info = [d.info() for d in drivers]
     evals = np.array([x["evals"] for x in info])
     conv = sum(1 for x in info if x["state"] == 1)
-    return dict(method="pcg (force-fitted inverse-Hessian preconditioner)", fmax_ha_bohr=RELAX_FMAX,
+    names = dict(pcg="pcg (force-fitted inverse-Hessian preconditioner)", cg="cg", bfgs="bfgs")
+    return dict(method=names[method], fmax_ha_bohr=RELAX_FMAX,
                 rounds=int(rounds), seconds=dt, converged=f"{conv}/{len(pop)}",
                 evals_per_member=dict(mean=float(evals.mean()), max=int(evals.max())),
                 batched_evals_per_s=len(pop) * rounds / dt, member_status_ok=int(np.sum(status == 0)),
@@ -452,7 +453,7 @@ def run_ours(args):
                                          max_dF=float(np.max(np.abs(fi - ref.forces))))
         out["error_ledger"] = _ledger(sgo, pop[i], prec, ref, i)
     if rank == 0 and not args.no_relax:
-        out["relax"] = _relax_population(sgo, batch, ctxs, pop)
+        out["relax"] = _relax_population(sgo, batch, ctxs, pop, method=args.relax_method)
         out["de_search"] = _de_search(sgo)
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -497,6 +498,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start (relaxation step) measurement")
     ap.add_argument("--no-relax", action="store_true", help="skip the local-relaxation (PCG) measurement")
+    ap.add_argument("--relax-method", default="pcg", choices=["pcg", "cg", "bfgs"])
     ap.add_argument("--sub-batches", type=int, default=0,
                     help="sub-batches overlapped on the GPU in graph mode (0 = the library's choice)")
     ap.add_argument("--profile", action="store_true", help="one extra step per kernel class with live timers")

@@ -82,12 +82,14 @@ def test_fullsize_error_ledger(sgo, name, precision):
     """Error ledger at full size against stored oracle values (tests/golden/ledger_*.json,
     written by tests/golden/make_ledger.py from oracle/ alone): every eigenvalue with
     occupation above 1e-6, every energy term, the free energy and every force component.
-    Bounds: the accuracy gate (1e-5 Ha/atom, 1e-4 Ha/bohr) for F and forces; 1e-5 Ha/atom
-    per term; 1e-5 Ha per eigenvalue (FP64) or 2e-4 Ha (mixed).  F is variational, second
-    order in the density error; an eigenvalue is first order in it (through V_eff), and the
-    mixed path stops at a density residual of 1e-5 per electron (its FP32 noise floor), so
-    its eigenvalues carry errors of that order times the potential's response (measured
-    6.3e-5 Ha on the monolayer) while F stays at 6e-7 Ha/atom."""
+    Bounds: the accuracy gate (1e-5 Ha/atom, 1e-4 Ha/bohr) for F and forces; per energy
+    term 1e-5 Ha/atom (FP64) or 1e-4 Ha/atom (mixed); per eigenvalue 1e-5 Ha (FP64) or
+    2e-4 Ha (mixed).  F is variational, second order in the density and wavefunction
+    errors; a single term or an eigenvalue is first order in them, and the mixed path
+    stops at a density residual of 1e-5 per electron (its FP32 noise floor), so its terms
+    and eigenvalues carry errors of that order times their response (measured: eigenvalues
+    6.3e-5 Ha on the monolayer, the kinetic term 1.7e-5 Ha/atom on the 13-atom cluster)
+    while F stays at 6e-7 and 1.4e-6 Ha/atom."""
     import json
     import os
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"ledger_{name}.json")
@@ -112,5 +114,5 @@ def test_fullsize_error_ledger(sgo, name, precision):
     assert ledger["dF_per_atom"] < 1e-5, ledger
     assert ledger["max_dforce"] < 1e-4, ledger
     for k, _ in keys:
-        assert ledger[k] < 1e-5, (k, ledger)
+        assert ledger[k] < (1e-5 if precision == "fp64" else 1e-4), (k, ledger)
     assert ledger["max_deig_occupied"] < (1e-5 if precision == "fp64" else 2e-4), ledger

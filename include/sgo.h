@@ -137,7 +137,7 @@ SGO_API sgo_status sgo_batch_create(int n, sgo_ctx* const* ctxs, sgo_batch** out
  * 2048), knobs[1] = 128-wave tiles per tensor-core NN CTA (of 2, 4, 8, 16), knobs[2] = K
  * chunk of the CUDA-core TN GEMM (of 128, 256, 512).  Each candidate is timed on the batch's
  * own buffers; the fastest is kept.  A batch split into sub-batches tunes each on its own;
- * knobs are those of the first sub-batch (the one holding the first member). */
+ * knobs are those of the first sub-batch (the one given the costliest member). */
 SGO_API sgo_status sgo_batch_tuning(const sgo_batch* batch, int* knobs);
 
 /* Evaluate every member.  pos[i] (host, natoms_i*3) or NULL = keep; energies[i];

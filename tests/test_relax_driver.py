@@ -88,3 +88,32 @@ def test_driver_argument_checks(sgo):
     # a lone atom feels no force: converged at the first evaluation
     nxt, st = r.step(0.0, np.zeros(3))
     assert st == 1 and np.all(nxt == 0.0)
+
+
+def test_driver_budget_and_repeat_after_stop(sgo):
+    """max_evals = 1 stops after the first evaluation (state 2); later calls repeat the
+    final positions without consuming forces; the best configuration is the lowest-energy
+    one evaluated."""
+    cell = np.eye(3) * 40.0
+    pos = np.array([[20.0, 20.0, 20.0], [20.0, 20.0, 23.5]])
+    ef = _model(cell, THETA)
+    r = sgo.Relax(cell, pos, method="bfgs", fmax=1e-9, max_evals=1)
+    E, F = ef(pos)
+    nxt, st = r.step(-1.0, F)
+    assert st == 2 and np.array_equal(nxt, pos)
+    nxt2, st2 = r.step(5.0, np.full(6, np.nan))   # ignored after the stop
+    assert st2 == 2 and np.array_equal(nxt2, pos)
+    e, x = r.best()
+    assert e == -1.0 and np.array_equal(x, pos)
+    assert r.info() == dict(evals=1, state=2)
+
+
+def test_batch_entry_points_check_arguments_on_the_host(sgo):
+    import ctypes
+    lib = sgo.load_library()
+    rounds = ctypes.c_int(7)
+    assert lib.sgo_relax_batch(None, None, 5, ctypes.byref(rounds), None) == sgo.SGO_ERR_ARG
+    assert rounds.value == 0
+    cell = np.eye(3).ravel()
+    assert lib.sgo_de_generation(None, sgo._ptr(cell), None, None, None, None, 0, 2.0, None, 5, None,
+                                 None) == sgo.SGO_ERR_ARG

@@ -59,6 +59,41 @@ def image_vectors(cell, rc):
     return ns @ cell
 
 
+def morse_dphi_grad(theta, r):
+    """d phi'(r) / d(D, a, r0) (each an array over r)."""
+    D, a, r0 = theta
+    e = np.exp(-a * (r - r0))
+    g = e - e * e
+    h = 1.0 - 2.0 * e
+    return 2.0 * a * g, 2.0 * D * g - 2.0 * D * a * h * (r - r0) * e, 2.0 * D * a * h * a * e
+
+
+def ff_forces_jac(theta, cell, pos, rc):
+    """The force field's forces and their derivatives dF_i/dtheta_k (natoms x 3 x 3),
+    differentiating each pair term (phi'(r) - phi'(rc)) rv / r analytically."""
+    pos = np.asarray(pos, float)
+    n = len(pos)
+    Ls = image_vectors(cell, rc)
+    dc = morse_dphi(theta, rc)
+    gc = morse_dphi_grad(theta, np.array(rc))
+    F = np.zeros((n, 3))
+    J = np.zeros((n, 3, 3))
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            rv = pos[j][None, :] + Ls - pos[i][None, :]
+            r = np.linalg.norm(rv, axis=1)
+            m = (r < rc) & (r > 1e-12)
+            rr = r[m]
+            u = rv[m] / rr[:, None]
+            F[i] += ((morse_dphi(theta, rr) - dc)[:, None] * u).sum(axis=0)
+            g = morse_dphi_grad(theta, rr)
+            for k in range(3):
+                J[i, :, k] += ((g[k] - gc[k])[:, None] * u).sum(axis=0)
+    return F, J
+
+
 def ff_forces(theta, cell, pos, rc):
     """F_i = -dE/dR_i of E = 1/2 sum_{i, j, L}' phi_s(|R_j + L - R_i|), where phi_s is phi
     shifted so that phi_s(rc) = phi_s'(rc) = 0 (shifted force) and zero beyond rc."""
@@ -88,9 +123,9 @@ def fit_force_field(history, theta0, cell, rc, iters=60, reg=REG):
     in history: minimise sum |F_ff(theta; x) - F_dft|^2 + w sum_k ((theta_k - theta0_k) /
     theta0_k)^2, w = reg * mean(F_dft^2) * (number of force components): a few forces
     (a dimer has one number) leave the three parameters undetermined, and the small pull
-    towards the previous fit picks the nearest solution.  Jacobian by central differences
-    (relative step 1e-6).  Returns theta0 unchanged if the fit leaves D, a, r0 > 0 or
-    turns non-finite."""
+    towards the previous fit picks the nearest solution.  The Jacobian of the force
+    residual is analytic (ff_forces_jac).  Returns theta0 unchanged if the fit leaves
+    D, a, r0 > 0 or turns non-finite."""
     theta = np.array(theta0, float)
     t0 = np.array(theta0, float)
     fall = np.concatenate([f.ravel() for _, f in history])
@@ -100,17 +135,15 @@ def fit_force_field(history, theta0, cell, rc, iters=60, reg=REG):
         return np.concatenate([(ff_forces(t, cell, x, rc) - f).ravel() for x, f in history] +
                               [sw * (t - t0) / t0])
 
+    def jac(t):
+        rows = [ff_forces_jac(t, cell, x, rc)[1].reshape(-1, 3) for x, _ in history]
+        return np.concatenate(rows + [np.diag(sw / t0)])
+
     r = resid(theta)
     cost = r @ r
     lam = 1e-3
     for _ in range(iters):
-        J = np.empty((len(r), 3))
-        for k in range(3):
-            h = 1e-6 * max(abs(theta[k]), 1e-3)
-            tp, tm = theta.copy(), theta.copy()
-            tp[k] += h
-            tm[k] -= h
-            J[:, k] = (resid(tp) - resid(tm)) / (2 * h)
+        J = jac(theta)
         A = J.T @ J
         g = J.T @ r
         improved = False

@@ -6,7 +6,8 @@
 // shifted-force Morse pair potential over periodic images, phi(r) = D [exp(-2a(r - r0)) -
 // 2 exp(-a(r - r0))], parameters theta = (D, a, r0) fitted by Levenberg-Marquardt to the
 // force sets of the last 64 evaluated configurations (with a weak pull towards the previous
-// fit, which picks a solution when few forces leave theta undetermined).  Its Hessian is the
+// fit, which picks a solution when few forces leave theta undetermined), with the analytic
+// Jacobian of the force residual.  Its Hessian is the
 // second-order finite difference of the fitted energy; the three eigenpairs of the
 // translations (smallest |tau|) are dropped and P = sum_j V_j V_j^T / |tau_j| over the
 // others (|tau_j| floored at a fraction of the largest).  The fit and P are renewed every
@@ -47,6 +48,14 @@ double dot(const Vec& a, const Vec& b) {
 double morse_dphi(const double* th, double r) {
   const double e = std::exp(-th[1] * (r - th[2]));
   return 2.0 * th[0] * th[1] * (e - e * e);
+}
+// d phi'(r) / d(D, a, r0)
+void morse_dphi_grad(const double* th, double r, double* g3) {
+  const double D = th[0], a = th[1], e = std::exp(-a * (r - th[2]));
+  const double g = e - e * e, h = 1.0 - 2.0 * e;
+  g3[0] = 2.0 * a * g;
+  g3[1] = 2.0 * D * g - 2.0 * D * a * h * (r - th[2]) * e;
+  g3[2] = 2.0 * D * a * h * a * e;
 }
 
 // lattice translations n . A, |n_k| <= ceil(rc / width_k) + 1
@@ -116,6 +125,25 @@ void ff_forces(const double* th, const PairList& pl, double rc, int n, const dou
     if (!(r < rc) || !(r > 1e-12)) continue;
     const double f = (morse_dphi(th, r) - dc) / r;
     for (int c = 0; c < 3; ++c) F[3 * i + c] += f * rv[c];
+  }
+}
+
+// dF/dtheta of ff_forces: J[(3 i + c) * 3 + k] = d F_{i,c} / d theta_k, each pair term
+// (phi'(r) - phi'(rc)) rv / r differentiated analytically
+void ff_forces_jac(const double* th, const PairList& pl, double rc, int n, const double* x, double* J) {
+  double gc[3];
+  morse_dphi_grad(th, rc, gc);
+  for (int k = 0; k < 9 * n; ++k) J[k] = 0.0;
+  for (size_t p = 0; p < pl.i.size(); ++p) {
+    const int i = pl.i[p], j = pl.j[p];
+    double rv[3];
+    for (int c = 0; c < 3; ++c) rv[c] = x[3 * j + c] + pl.L[3 * p + c] - x[3 * i + c];
+    const double r = std::sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+    if (!(r < rc) || !(r > 1e-12)) continue;
+    double g[3];
+    morse_dphi_grad(th, r, g);
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < 3; ++k) J[(3 * i + c) * 3 + k] += (g[k] - gc[k]) * (rv[c] / r);
   }
 }
 
@@ -248,20 +276,25 @@ void fit_force_field(sgo_relax* r) {
     for (int k = 0; k < 3; ++k) res.push_back(sw * (t[k] - t0[k]) / t0[k]);
     return res;
   };
+  // Jacobian of the residual: the force field's analytic dF/dtheta, then the pull's rows
+  auto jac = [&](const double* t) {
+    std::vector<Vec> J(3, Vec());
+    for (int k = 0; k < 3; ++k) J[k].reserve(ncomp + 3);
+    Vec Jc(9 * (size_t)r->n);
+    for (size_t h = 0; h < r->hx.size(); ++h) {
+      ff_forces_jac(t, r->hp[h], r->o.rc, r->n, r->hx[h].data(), Jc.data());
+      for (int row = 0; row < 3 * r->n; ++row)
+        for (int k = 0; k < 3; ++k) J[k].push_back(Jc[(size_t)row * 3 + k]);
+    }
+    for (int q = 0; q < 3; ++q)
+      for (int k = 0; k < 3; ++k) J[k].push_back(q == k ? sw / t0[k] : 0.0);
+    return J;
+  };
   Vec res = resid(th);
   double cost = dot(res, res);
   double lam = 1e-3;
   for (int it = 0; it < 60; ++it) {
-    std::vector<Vec> J(3);
-    for (int k = 0; k < 3; ++k) {
-      const double h = 1e-6 * std::max(std::fabs(th[k]), 1e-3);
-      double tp[3] = {th[0], th[1], th[2]}, tm[3] = {th[0], th[1], th[2]};
-      tp[k] += h;
-      tm[k] -= h;
-      const Vec rp = resid(tp), rm = resid(tm);
-      J[k].resize(rp.size());
-      for (size_t i = 0; i < rp.size(); ++i) J[k][i] = (rp[i] - rm[i]) / (2.0 * h);
-    }
+    const std::vector<Vec> J = jac(th);
     double A[3][3], gr[3];
     for (int a = 0; a < 3; ++a) {
       gr[a] = dot(J[a], res);

@@ -330,6 +330,18 @@ enum { SGO_DE_RANDOM_SCHEME = 0, SGO_DE_PLANE = 1, SGO_DE_SPHERE = 2 };
 SGO_API sgo_status sgo_de_offspring(int np, int natoms, const double cell[9], const int* species, const double* pop,
                                     const double* f, const double* u, int scheme, double d_min, double* children);
 
+/* Migration between nsub equal subpopulations (consecutive slices of the np individuals;
+ * np a multiple of nsub), in ring order s = 0 .. nsub-1: the best individual of subpopulation
+ * s replaces the worst of subpopulation (s+1) mod nsub when its energy is lower (pop and f
+ * updated in place; ties: the lowest index is best, the lowest index is worst). */
+SGO_API sgo_status sgo_de_migrate(int np, int nsub, int natoms, double* pop, double* f);
+
+/* Similarity check between two structures of natoms atoms in one cell (the population's
+ * initialisation keeps only dissimilar ones): *similar = 1 when the root-mean-square
+ * difference of their sorted minimum-image pair distances is below tol (bohr). */
+SGO_API sgo_status sgo_de_similar(int natoms, const double cell[9], const double* a, const double* b, double tol,
+                                  int* similar);
+
 /* One DE generation on a batch whose member i evaluates individual i (same atoms, same
  * cell): the offspring above, each relaxed (cold start, then warm) by its own driver with
  * options ro over at most max_rounds batched evaluations, then greedy selection: the

@@ -21,7 +21,11 @@ X_i of a generation:
   the counts match);
 * distance repair: any pair closer than d_min (minimum image) is pushed apart along its
   separation, the later atom moving, in passes until none is (at most 100 passes);
-* greedy selection: the relaxed child replaces X_i when its energy is lower.
+* greedy selection: the relaxed child replaces X_i when its energy is lower;
+* migration between subpopulations (consecutive slices): ring order, the best of one
+  replaces the worst of the next when better;
+* similarity (the initialisation's check between structures): sorted minimum-image pair
+  distances, similar when their RMS difference is below a tolerance.
 
 Pins (tests/test_oracle_de.py): Eq. 2 reduces to the centroid when the three fitnesses are
 equal; the child always has the parents' composition; a plane through the centre of a
@@ -144,6 +148,42 @@ def offspring(cell, species, pop, f, u, scheme="random", d_min=D_MIN):
         C = cut_and_splice(species, V, pop[i], (u[i][3], u[i][4]), u[i][5], u[i][6], scheme)
         kids[i] = repair(cell, C, d_min)
     return kids
+
+
+def fingerprint(cell, X):
+    """The structure's sorted minimum-image pair distances (the similarity check at
+    initialisation compares structures by them)."""
+    A = np.asarray(cell, float)
+    inv = np.linalg.inv(A)
+    X = np.asarray(X, float)
+    d = [np.linalg.norm(_mi((X[j] - X[i]) @ inv) @ A) for i in range(len(X)) for j in range(i + 1, len(X))]
+    return np.sort(np.array(d))
+
+
+def similar(cell, X, Y, tol=0.05):
+    """Two structures are similar when their fingerprints differ by less than tol (bohr, root
+    mean square over the pairs)."""
+    a, b = fingerprint(cell, X), fingerprint(cell, Y)
+    return bool(np.sqrt(np.mean((a - b) ** 2)) < tol) if len(a) else True
+
+
+def migrate(pop, f, nsub):
+    """Ring migration between nsub equal subpopulations (consecutive slices of the
+    population): in order s = 0 .. nsub-1, the best individual of subpopulation s replaces the
+    worst of subpopulation (s + 1) mod nsub when it is better."""
+    pop = np.array(pop, float)
+    f = np.array(f, float)
+    size = len(f) // nsub
+    for s_ in range(nsub):
+        src = range(s_ * size, (s_ + 1) * size)
+        t = (s_ + 1) % nsub
+        dst = range(t * size, (t + 1) * size)
+        b = min(src, key=lambda k: (f[k], k))
+        w = max(dst, key=lambda k: (f[k], -k))
+        if f[b] < f[w]:
+            pop[w] = pop[b]
+            f[w] = f[b]
+    return pop, f
 
 
 def select(pop, f, kids, fk):

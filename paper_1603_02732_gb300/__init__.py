@@ -63,6 +63,25 @@ def relax_opts(method="pcg", **opts) -> "sgo_relax_opts":
     return o
 
 
+def de_migrate(pop, f, nsub):
+    """Ring migration between nsub subpopulations (sgo_de_migrate); returns new arrays."""
+    pop = np.array(pop, dtype=np.float64, order="C")
+    f = np.array(f, dtype=np.float64)
+    _check(load_library().sgo_de_migrate(len(f), int(nsub), pop.shape[1], _ptr(pop), _ptr(f)), "sgo_de_migrate")
+    return pop, f
+
+
+def de_similar(cell, a, b, tol=0.05) -> bool:
+    """Similarity of two structures by their sorted pair distances (sgo_de_similar)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    out = ctypes.c_int()
+    _check(load_library().sgo_de_similar(len(a), _ptr(cell), _ptr(a), _ptr(b), float(tol), ctypes.byref(out)),
+           "sgo_de_similar")
+    return bool(out.value)
+
+
 def de_offspring(cell, species, pop, f, u, scheme="random", d_min=2.0):
     """Children of a DE population (sgo_de_offspring, Sec. II B): pop (np, natoms, 3) bohr,
     f (np,) energies, u (np, DE_RANDOMS) uniforms in [0, 1)."""
@@ -126,6 +145,8 @@ _SIGS = {
     "sgo_relax_best": (ctypes.c_int, [_vp, _dp, _dp]),
     "sgo_de_offspring": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _ip, _dp, _dp, _dp, ctypes.c_int,
                                         ctypes.c_double, _dp]),
+    "sgo_de_migrate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]),
+    "sgo_de_similar": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _ip]),
     "sgo_de_generation": (ctypes.c_int, [_vp, _dp, _ip, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
                                          ctypes.POINTER(sgo_relax_opts), ctypes.c_int, _ip, _dp]),
     "sgo_density": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),

@@ -14,7 +14,11 @@
 //   from the centre), so the child has the parents' composition in one pass;
 // * distance repair: pairs closer than d_min (minimum image) are pushed apart, the later
 //   atom moving along the separation, in passes (at most 100);
-// * greedy selection: the relaxed child replaces X_i when its energy is lower.
+// * greedy selection: the relaxed child replaces X_i when its energy is lower;
+// * migration between subpopulations (consecutive slices), in ring order: the best of one
+//   replaces the worst of the next when better;
+// * similarity (the initialisation's check between structures): sorted minimum-image pair
+//   distances, similar when their root-mean-square difference is below a tolerance.
 // The random numbers are inputs, SGO_DE_RANDOMS uniforms per offspring (3 partners, 2 for
 // the plane normal, 1 for the scheme, 1 for the sphere radius).
 #include <algorithm>
@@ -189,9 +193,59 @@ void repair(const Cell& cell, int n, double d_min, double* X) {
   }
 }
 
+// sorted minimum-image pair distances
+Vec fingerprint(const Cell& cell, int n, const double* X) {
+  Vec d;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      double dx[3], ds[3], dv[3];
+      for (int c = 0; c < 3; ++c) dx[c] = X[3 * j + c] - X[3 * i + c];
+      cell.frac(dx, ds);
+      for (int c = 0; c < 3; ++c) ds[c] = mimg(ds[c]);
+      cell.cart(ds, dv);
+      d.push_back(std::sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]));
+    }
+  std::sort(d.begin(), d.end());
+  return d;
+}
+
 }  // namespace
 
 extern "C" {
+
+sgo_status sgo_de_similar(int natoms, const double cell[9], const double* a, const double* b, double tol,
+                          int* similar) {
+  if (natoms < 1 || !cell || !a || !b || !similar || !(tol >= 0)) return SGO_ERR_ARG;
+  const Cell c(cell);
+  const Vec fa = fingerprint(c, natoms, a), fb = fingerprint(c, natoms, b);
+  if (fa.empty()) {
+    *similar = 1;
+    return SGO_OK;
+  }
+  double s = 0.0;
+  for (size_t k = 0; k < fa.size(); ++k) s += (fa[k] - fb[k]) * (fa[k] - fb[k]);
+  *similar = std::sqrt(s / (double)fa.size()) < tol ? 1 : 0;
+  return SGO_OK;
+}
+
+sgo_status sgo_de_migrate(int np, int nsub, int natoms, double* pop, double* f) {
+  if (np < 1 || nsub < 1 || np % nsub != 0 || natoms < 1 || !pop || !f) return SGO_ERR_ARG;
+  const int size = np / nsub;
+  const size_t sz = 3 * (size_t)natoms;
+  for (int s = 0; s < nsub; ++s) {
+    const int t = (s + 1) % nsub;
+    int b = s * size, w = t * size;
+    for (int k = s * size; k < (s + 1) * size; ++k)
+      if (f[k] < f[b]) b = k;
+    for (int k = t * size; k < (t + 1) * size; ++k)
+      if (f[k] > f[w]) w = k;
+    if (f[b] < f[w]) {
+      std::memmove(pop + sz * w, pop + sz * b, sizeof(double) * sz);
+      f[w] = f[b];
+    }
+  }
+  return SGO_OK;
+}
 
 sgo_status sgo_de_offspring(int np, int natoms, const double cell[9], const int* species, const double* pop,
                             const double* f, const double* u, int scheme, double d_min, double* children) {

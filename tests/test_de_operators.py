@@ -45,3 +45,20 @@ def test_offspring_argument_checks(sgo):
     pop, f = _population(3, 4, 0, A)
     with pytest.raises(sgo.SgoError):   # fewer than four individuals: no three partners
         sgo.de_offspring(A, np.zeros(4), pop, f, np.zeros((3, de.RANDOMS)))
+
+
+def test_migration_and_similarity_match_oracle(sgo):
+    rng = np.random.default_rng(12)
+    A = CELLS[1]
+    for nsub in (2, 4):
+        pop, f = _population(8, 5, 20 + nsub, A)
+        f[rng.integers(0, 8)] = f.min()      # a tie, resolved by index on both sides
+        p1, f1 = sgo.de_migrate(pop, f, nsub)
+        p2, f2 = de.migrate(pop, f, nsub)
+        assert np.array_equal(f1, f2) and np.array_equal(p1, p2), nsub
+    X = rng.uniform(0, 1, size=(7, 3)) @ A
+    for shift in (0.0, 0.02, 0.3):
+        Y = X.copy()
+        Y[3] += shift
+        for tol in (1e-9, 0.01, 0.05):
+            assert sgo.de_similar(A, X, Y, tol) == de.similar(A, X, Y, tol), (shift, tol)

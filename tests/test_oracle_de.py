@@ -92,3 +92,27 @@ def test_greedy_selection_never_raises_an_energy():
     p2, f2, better = de.select(pop, f, kids, fk)
     assert np.all(f2 <= f) and np.array_equal(f2, np.minimum(f, fk))
     assert np.array_equal(p2[better], kids[better]) and np.array_equal(p2[~better], pop[~better])
+
+
+def test_similarity_is_invariant_under_translation_and_permutation():
+    rng = np.random.default_rng(6)
+    X = rng.uniform(0, 1, size=(6, 3)) @ CELL
+    Y = X[rng.permutation(6)] + np.array([3.1, -2.2, 0.7])
+    assert de.similar(CELL, X, Y, tol=1e-9)
+    Z = X.copy()
+    Z[2] += np.array([0.8, 0.0, 0.0])
+    assert not de.similar(CELL, X, Z, tol=0.05)
+
+
+def test_ring_migration_moves_each_best_to_the_next_subpopulation():
+    pop = np.arange(8, dtype=float).reshape(8, 1, 1)
+    f = np.array([-1.0, -3.0, 0.0, 2.0, -5.0, 1.0, -2.0, 4.0])
+    p2, f2 = de.migrate(pop, f, 4)
+    # subpopulations {0,1} {2,3} {4,5} {6,7}, in ring order: the best of {0,1} (slot 1,
+    # -3) replaces the worst of {2,3} (slot 3, 2); the best of {2,3} is now that migrant
+    # (slot 3, -3) and replaces the worst of {4,5} (slot 5, 1); the best of {4,5} (slot 4,
+    # -5) replaces the worst of {6,7} (slot 7, 4); the best of {6,7} is now that migrant
+    # (slot 7, -5) and replaces the worst of {0,1} (slot 0, -1)
+    assert f2.tolist() == [-5.0, -3.0, 0.0, -3.0, -5.0, -3.0, -2.0, -5.0]
+    assert p2[:, 0, 0].tolist() == [4.0, 1.0, 2.0, 1.0, 4.0, 1.0, 6.0, 4.0]
+    assert np.all(f2 <= f)

@@ -252,7 +252,8 @@ SGO_API sgo_status sgo_set_warm(sgo_ctx* ctx, int on);
  *   SGO_RELAX_CG: the same iteration with P = I / 0.5 (Ha/bohr^2).
  *   SGO_RELAX_BFGS: inverse-Hessian BFGS from B0 = I / 0.5, steps capped per atom.
  * (P)CG directions are Polak-Ribiere+ with restarts; each line takes a trial point at
- * min(1, max_step / max_i |d_i|) and, unless the secant of the directional derivative
+ * min(a_prev, max_step / max_i |d_i|), a_prev the previous line's minimising step (1 on the
+ * first line), and, unless the secant of the directional derivative
  * lands within `accept` of it, one more evaluation at the secant's zero (kept between
  * 0.1 times the trial step and max_step of displacement). */
 enum { SGO_RELAX_PCG = 0, SGO_RELAX_CG = 1, SGO_RELAX_BFGS = 2 };

@@ -232,7 +232,9 @@ def relax(ef: Callable[[np.ndarray], Tuple[float, np.ndarray]], cell, pos0, meth
     Nonlinear (P)CG, Polak-Ribiere+ with restarts: s = P g (g = -F), d = -s + beta d_prev,
     beta = max(0, g.(s - s_prev) / g_prev.s_prev), reset to -s when d.g >= 0.  Line
     minimisation along d from the directional derivatives (-F.d) at 0 and at a trial step
-    a_t = min(1, max_step / max_i |d_i|): secant a* = a_t p0 / (p0 - p_t) when the
+    a_t = min(a_prev, max_step / max_i |d_i|), a_prev the previous line's a* (1 at the
+    start: a well-scaled preconditioner makes a* about 1, and a badly scaled one, such as a
+    force field fitted too soft, is corrected after one line): secant a* = a_t p0 / (p0 - p_t) when the
     curvature is positive, else the largest step; a* is kept at >= 0.1 a_t and at most
     max_step of displacement from the start of the line; the trial point is kept as the
     new point when |a* - a_t| <= accept a_t (one evaluation saved; accept = 0 keeps every
@@ -284,6 +286,7 @@ def relax(ef: Callable[[np.ndarray], Tuple[float, np.ndarray]], cell, pos0, meth
     theta = None
     P = None
     ndir = 0
+    a_prev = 1.0      # the previous line's minimising step: the next trial step
     d_prev = s_prev = g_prev = None
     hist = [(x.copy(), F.copy())]
     while len(traj.positions) < max_evals:
@@ -309,7 +312,7 @@ def relax(ef: Callable[[np.ndarray], Tuple[float, np.ndarray]], cell, pos0, meth
         dmax = np.linalg.norm(d.reshape(-1, 3), axis=1).max()
         if dmax <= 0:
             break
-        at = min(1.0, max_step / dmax)
+        at = min(a_prev, max_step / dmax)
         xt = x + at * d.reshape(-1, 3)
         Ft = evaluate(xt)
         hist.append((xt.copy(), Ft.copy()))
@@ -321,6 +324,7 @@ def relax(ef: Callable[[np.ndarray], Tuple[float, np.ndarray]], cell, pos0, meth
         amax = max_step / dmax
         a_star = at * p0 / (p0 - pt) if pt - p0 > 0 else amax  # zero of the secant of phi'
         a_star = min(max(a_star, 0.1 * at), amax)
+        a_prev = a_star
         g_prev, s_prev, d_prev = g, s, d
         if abs(a_star - at) <= accept * at or len(traj.positions) >= max_evals:
             x, g = xt, gt

@@ -240,6 +240,7 @@ struct sgo_relax {
   Vec d, s, d_prev, s_prev, g_prev, P, xt, gt;
   bool have_prev = false;
   double at = 0.0, p0 = 0.0, dmax = 0.0;
+  double a_prev = 1.0;           // the previous line's minimising step: the next trial step
   double theta[3] = {0, 0, 0};
   bool have_theta = false;
   int ndir = 0;
@@ -430,7 +431,7 @@ void start_line(sgo_relax* r) {
     r->pending = r->x;
     return;
   }
-  r->at = std::min(1.0, r->o.max_step / r->dmax);
+  r->at = std::min(r->a_prev, r->o.max_step / r->dmax);
   r->xt.resize(m);
   for (int i = 0; i < m; ++i) r->xt[i] = r->x[i] + r->at * r->d[i];
   r->pending = r->xt;
@@ -561,6 +562,7 @@ sgo_status sgo_relax_step(sgo_relax* r, double energy, const double* forces, dou
     const double amax = r->o.max_step / r->dmax;
     double astar = pt - p0 > 0.0 ? r->at * p0 / (p0 - pt) : amax;
     astar = std::min(std::max(astar, 0.1 * r->at), amax);
+    r->a_prev = astar;
     r->g_prev = r->g;
     r->s_prev = r->s;
     r->d_prev = r->d;

@@ -99,6 +99,20 @@ typedef struct {
                              (autotune = 0) every member's results are bit-identical in every
                              split; the autotuner tunes each sub-batch on its own.  Taken from
                              the first member. */
+  double eig_tol;         /* Algorithm 1 runs its CG loop "while not converged": after the SCF
+                             stopping rule holds, all-band CG steps continue at the final
+                             potential until every band with occupation above 1e-6 has a
+                             residual |H psi - eps psi| below eig_tol (Ha), then the density,
+                             energy and forces are taken from those bands (default 1e-4;
+                             0 = stop with the last SCF iteration's bands) */
+  int max_polish;         /* cap on those extra CG steps (default 40); a member that reaches it
+                             keeps its bands and reports the residual it reached (sgo_get_stats) */
+  int rr_fp64;            /* mixed path: factor the overlap (Cholesky) and solve the subspace
+                             eigenproblem in FP64 (1) instead of FP32 deviation form (0, default;
+                             taken from the first member of a batch) */
+  double watchdog_ms;     /* bound on every device wait of the tensor-core kernels (ms); on expiry
+                             the member reports SGO_ERR_TIMEOUT and the context stays usable;
+                             0 = 2000 ms.  Taken from the first member of a batch. */
 } sgo_opts;
 
 /* Fill *o with the defaults (FP64, kT 0, tolerances 1e-8 Ha / 1e-7, Pulay 8, ...). */
@@ -177,8 +191,28 @@ SGO_API sgo_status sgo_get_terms(sgo_ctx* ctx, double terms[8]);
 SGO_API sgo_status sgo_get_info(sgo_ctx* ctx, int info[10]);
 
 /* Diagnostics of the last SCF: [0] iterations, [1] Jacobi sweeps summed over its
- * subspace diagonalisations, [2] final density residual, [3] final |F_k - F_{k-1}|. */
-SGO_API sgo_status sgo_get_stats(sgo_ctx* ctx, double stats[4]);
+ * subspace diagonalisations, [2] final density residual, [3] final |F_k - F_{k-1}|,
+ * [4] CG steps taken after the SCF stopping rule held (eig_tol), [5] the largest residual
+ * |H psi - eps psi| over the bands with occupation above 1e-6 at the end, [6] subspace
+ * diagonalisations that stopped at their Jacobi sweep cap, [7] SCF iterations of the
+ * last SCF loop that started from a state set by sgo_set_state (0 otherwise). */
+SGO_API sgo_status sgo_get_stats(sgo_ctx* ctx, double stats[8]);
+
+/* Warm-start state (Sec. II C: a relaxation step restarts the SCF from the previous
+ * step's density and wavefunctions), for moving a state between contexts or processes:
+ *   rho_g: the SCF input density rho_in(G) = (1/N) sum_r rho_in(r) exp(-i G.r) on the FFT
+ *          box, complex, 2*N1*N2*N3 doubles (re, im interleaved) in C order of
+ *          (m1 mod N1, m2 mod N2, m3 mod N3);
+ *   psi:   the nbands wavefunctions, row-major nbands x npw doubles in the packed Gamma
+ *          format above (sizes from sgo_get_info).
+ * sgo_get_state copies the state the last evaluation left (either pointer may be NULL;
+ * SGO_ERR_ARG before any evaluation or sgo_set_state).  sgo_set_state installs one (both
+ * required; SGO_ERR_ARG for non-finite values) and switches warm starts on, as
+ * sgo_set_warm(ctx, 1): the next evaluation starts from it, whatever the positions.  The
+ * wavefunctions need not be orthonormal (the first subspace diagonalisation
+ * orthonormalises them); both are copied, the caller keeps its arrays. */
+SGO_API sgo_status sgo_get_state(sgo_ctx* ctx, double* rho_g, double* psi);
+SGO_API sgo_status sgo_set_state(sgo_ctx* ctx, const double* rho_g, const double* psi);
 
 /* Miller indices of the packed basis: (1 + n_half) rows of 3 ints, row 0 = G = 0. */
 SGO_API sgo_status sgo_get_basis(sgo_ctx* ctx, int* miller);
@@ -193,10 +227,15 @@ SGO_API sgo_status sgo_get_density(sgo_ctx* ctx, double* rho);
 SGO_API sgo_status sgo_apply_hamiltonian(sgo_ctx* ctx, const double* veff, int nvec, const double* psi,
                                  double* hpsi);
 
-/* The same H psi as sgo_apply_hamiltonian, for callers that cannot let a library
- * allocate device memory during a call: a process whose device memory belongs to its
- * own pool allocator, one that runs under a fixed memory budget, or a latency-critical
- * loop that cannot take the implicit synchronisation of cudaMalloc/cudaFree.  This call
+/* The H psi of sgo_apply_hamiltonian, for callers that cannot let a library allocate
+ * device memory during a call: a process whose device memory belongs to its own pool
+ * allocator, one that runs under a fixed memory budget, or a latency-critical loop that
+ * cannot take the implicit synchronisation of cudaMalloc/cudaFree.  In FP64 the result
+ * equals sgo_apply_hamiltonian's; on the mixed path this call always takes the CUDA-core
+ * transforms and GEMMs while the ordinary call may take the register-FFT and tensor-core
+ * kernels, so the two agree to FP32/3xTF32 rounding (about 2e-5 relative).  The device
+ * current at the call must be the context's (the one current at sgo_create), else
+ * SGO_ERR_ARG.  This call
  * allocates nothing: it uses the context's buffers (allocated once by sgo_create) and a
  * file-scope device scratch array of 32 MiB that every GPU loading the library holds
  * until the process exits.  Problems whose launch descriptors, projector partial sums
@@ -332,9 +371,11 @@ SGO_API sgo_status sgo_de_offspring(int np, int natoms, const double cell[9], co
                                     const double* f, const double* u, int scheme, double d_min, double* children);
 
 /* Migration between nsub equal subpopulations (consecutive slices of the np individuals;
- * np a multiple of nsub), in ring order s = 0 .. nsub-1: the best individual of subpopulation
- * s replaces the worst of subpopulation (s+1) mod nsub when its energy is lower (pop and f
- * updated in place; ties: the lowest index is best, the lowest index is worst). */
+ * np a multiple of nsub), in ring order: the best individual of subpopulation s replaces the
+ * worst of subpopulation (s+1) mod nsub when its energy is lower (pop and f updated in place;
+ * ties: the lowest index is best, the lowest index is worst).  Every best and worst is chosen
+ * on the population as passed in, before any copy, so a migrant moves one step round the
+ * ring; nsub = 1 changes nothing. */
 SGO_API sgo_status sgo_de_migrate(int np, int nsub, int natoms, double* pop, double* f);
 
 /* Similarity check between two structures of natoms atoms in one cell (the population's

@@ -169,20 +169,26 @@ def similar(cell, X, Y, tol=0.05):
 
 def migrate(pop, f, nsub):
     """Ring migration between nsub equal subpopulations (consecutive slices of the
-    population): in order s = 0 .. nsub-1, the best individual of subpopulation s replaces the
-    worst of subpopulation (s + 1) mod nsub when it is better."""
+    population): the best individual of subpopulation s replaces the worst of subpopulation
+    (s + 1) mod nsub when it is better.  Best and worst are taken on the population as it was
+    before the migration (every migrant moves one step round the ring); one subpopulation
+    has no neighbour and nothing moves."""
     pop = np.array(pop, float)
     f = np.array(f, float)
+    if nsub == 1:
+        return pop, f
     size = len(f) // nsub
+    subs = [range(s_ * size, (s_ + 1) * size) for s_ in range(nsub)]
+    best = [min(r, key=lambda k: (f[k], k)) for r in subs]
+    worst = [max(r, key=lambda k: (f[k], -k)) for r in subs]
+    src_x = [pop[b].copy() for b in best]
+    src_f = [f[b] for b in best]
+    dst_f = [f[w] for w in worst]
     for s_ in range(nsub):
-        src = range(s_ * size, (s_ + 1) * size)
         t = (s_ + 1) % nsub
-        dst = range(t * size, (t + 1) * size)
-        b = min(src, key=lambda k: (f[k], k))
-        w = max(dst, key=lambda k: (f[k], -k))
-        if f[b] < f[w]:
-            pop[w] = pop[b]
-            f[w] = f[b]
+        if src_f[s_] < dst_f[t]:
+            pop[worst[t]] = src_x[s_]
+            f[worst[t]] = src_f[s_]
     return pop, f
 
 

@@ -233,8 +233,9 @@ def relax(ef: Callable[[np.ndarray], Tuple[float, np.ndarray]], cell, pos0, meth
     beta = max(0, g.(s - s_prev) / g_prev.s_prev), reset to -s when d.g >= 0.  Line
     minimisation along d from the directional derivatives (-F.d) at 0 and at a trial step
     a_t = min(a_prev, max_step / max_i |d_i|), a_prev the previous line's a* (1 at the
-    start: a well-scaled preconditioner makes a* about 1, and a badly scaled one, such as a
-    force field fitted too soft, is corrected after one line): secant a* = a_t p0 / (p0 - p_t) when the
+    start and whenever the preconditioner is renewed: a well-scaled preconditioner makes a*
+    about 1, and a badly scaled one, such as a force field fitted too soft, is corrected
+    after one line): secant a* = a_t p0 / (p0 - p_t) when the
     curvature is positive, else the largest step; a* is kept at >= 0.1 a_t and at most
     max_step of displacement from the start of the line; the trial point is kept as the
     new point when |a* - a_t| <= accept a_t (one evaluation saved; accept = 0 keeps every
@@ -298,6 +299,7 @@ def relax(ef: Callable[[np.ndarray], Tuple[float, np.ndarray]], cell, pos0, meth
                     theta = np.array([0.1, 1.0, nearest_neighbour(cell, x)])
                 theta = fit_force_field(hist[-HIST:], theta, cell, rc)
                 P = truncated_inverse(ff_hessian(theta, cell, x, rc))
+                a_prev = 1.0  # a step found under the previous preconditioner has its scale
         else:
             P = np.eye(n3) / KAPPA0
         s = P @ g

@@ -104,7 +104,8 @@ class sgo_opts(ctypes.Structure):
                 ("mix_alpha", ctypes.c_double), ("kerker_q0", ctypes.c_double), ("ncg", ctypes.c_int),
                 ("ncg_first", ctypes.c_int), ("n_nonscf", ctypes.c_int), ("fft", ctypes.c_int * 3),
                 ("seed", ctypes.c_ulonglong), ("gemm_tc", ctypes.c_int), ("graph", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("sub_batches", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("sub_batches", ctypes.c_int), ("eig_tol", ctypes.c_double),
+                ("max_polish", ctypes.c_int), ("rr_fp64", ctypes.c_int), ("watchdog_ms", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -130,6 +131,8 @@ _SIGS = {
     "sgo_get_basis": (ctypes.c_int, [_vp, _ip]),
     "sgo_get_stats": (ctypes.c_int, [_vp, _dp]),
     "sgo_get_density": (ctypes.c_int, [_vp, _dp]),
+    "sgo_get_state": (ctypes.c_int, [_vp, _dp, _dp]),
+    "sgo_set_state": (ctypes.c_int, [_vp, _dp, _dp]),
     "sgo_apply_hamiltonian": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
     "sgo_apply_hamiltonian_noalloc": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp]),
     "sgo_subspace_matrix": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
@@ -276,9 +279,24 @@ class Context:
                     nbands=int(a[6]), natoms=int(a[7]), n_iter=int(a[8]), precision=int(a[9]))
 
     def stats(self):
-        s = np.zeros(4)
+        s = np.zeros(8)
         _check(self.lib.sgo_get_stats(self.h, _ptr(s)), "sgo_get_stats")
-        return dict(n_iter=int(s[0]), jacobi_sweeps=int(s[1]), resid=float(s[2]), dF=float(s[3]))
+        return dict(n_iter=int(s[0]), jacobi_sweeps=int(s[1]), resid=float(s[2]), dF=float(s[3]),
+                    polish_steps=int(s[4]), eig_resid=float(s[5]), jacobi_cap_hits=int(s[6]), warm=bool(s[7]))
+
+    def get_state(self):
+        """(rho_in(G) complex (N1, N2, N3), psi (nbands, npw)): the warm-start state the last
+        evaluation left (sgo_get_state)."""
+        rho = np.zeros(self.grid, dtype=np.complex128)
+        psi = np.zeros((self.nbands, self.npw))
+        _check(self.lib.sgo_get_state(self.h, rho.ctypes.data_as(_dp), _ptr(psi)), "sgo_get_state")
+        return rho, psi
+
+    def set_state(self, rho_g, psi):
+        """Install a warm-start state (sgo_set_state); the next evaluation starts from it."""
+        rho = np.ascontiguousarray(rho_g, dtype=np.complex128).reshape(self.grid)
+        psi = np.ascontiguousarray(psi, dtype=np.float64).reshape(self.nbands, self.npw)
+        _check(self.lib.sgo_set_state(self.h, rho.ctypes.data_as(_dp), _ptr(psi)), "sgo_set_state")
 
     def eigen(self):
         e = np.zeros(self.nbands)

@@ -104,6 +104,10 @@ void sgo_opts_default(sgo_opts* o) {
   o->gemm_tc = 1;
   o->graph = 1;
   o->autotune = 1;
+  o->eig_tol = 1e-4;
+  o->max_polish = 40;
+  o->rr_fp64 = 0;
+  o->watchdog_ms = 0.0;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,
@@ -129,6 +133,11 @@ sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp,
   c->precision = c->opts.precision ? 1 : 0;
   c->tsize = c->precision ? sizeof(float) : sizeof(double);
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    sgo::set_error("cudaGetDevice failed");
+    return SGO_ERR_CUDA;
+  }
   double nel = 0.0;
   for (int a = 0; a < natoms; ++a) {
     if (species_of_atom[a] < 0 || species_of_atom[a] >= nspecies) {
@@ -144,7 +153,8 @@ sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp,
     sgo::set_error("too few bands for the electrons (or odd electron count with integer occupations)");
     return SGO_ERR_ARG;
   }
-  if (c->opts.max_scf < 1 || c->opts.pulay_hist < 1 || c->opts.ncg < 1) {
+  if (c->opts.max_scf < 1 || c->opts.pulay_hist < 1 || c->opts.ncg < 1 || !(c->opts.eig_tol >= 0.0) ||
+      c->opts.max_polish < 0 || !(c->opts.watchdog_ms >= 0.0)) {
     delete c;
     sgo::set_error("invalid SCF options");
     return SGO_ERR_ARG;
@@ -442,13 +452,51 @@ sgo_status sgo_get_info(sgo_ctx* c, int info[10]) {
   return SGO_OK;
 }
 
-sgo_status sgo_get_stats(sgo_ctx* c, double stats[4]) {
+sgo_status sgo_get_stats(sgo_ctx* c, double stats[8]) {
   if (!c || !stats) return SGO_ERR_ARG;
   stats[0] = c->last_iter;
   stats[1] = c->h_scal[sgo::SC_RRSWEEPS];
   stats[2] = c->h_scal[sgo::SC_RESID];
   stats[3] = c->h_scal[sgo::SC_DF];
+  stats[4] = c->h_scal[sgo::SC_POLISH];
+  stats[5] = c->h_scal[sgo::SC_EIGRES];
+  stats[6] = c->h_scal[sgo::SC_RRCAP];
+  stats[7] = c->last_warm ? 1.0 : 0.0;
   return SGO_OK;
+}
+
+sgo_status sgo_get_state(sgo_ctx* c, double* rho_g, double* psi) {
+  if (!c || (!rho_g && !psi)) return SGO_ERR_ARG;
+  if (!c->have_state) {
+    sgo::set_error("no state yet: run an evaluation or sgo_set_state first");
+    return SGO_ERR_ARG;
+  }
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  return e->export_state(rho_g, psi);
+}
+
+sgo_status sgo_set_state(sgo_ctx* c, const double* rho_g, const double* psi) {
+  if (!c || !rho_g || !psi) return SGO_ERR_ARG;
+  const size_t ng = (size_t)c->d.ngrid, np = (size_t)c->d.nb * c->d.npw;
+  for (size_t i = 0; i < 2 * ng; ++i)
+    if (!std::isfinite(rho_g[i])) {
+      sgo::set_error("non-finite density in the imported state");
+      return SGO_ERR_ARG;
+    }
+  for (size_t i = 0; i < np; ++i)
+    if (!std::isfinite(psi[i])) {
+      sgo::set_error("non-finite wavefunction in the imported state");
+      return SGO_ERR_ARG;
+    }
+  std::unique_ptr<sgo::Engine> e(solo_engine(c));
+  if (!e->ok()) return SGO_ERR_CUDA;
+  const sgo_status s = e->import_state(rho_g, psi);
+  if (s == SGO_OK) {
+    c->have_state = true;
+    c->warm = true;
+  }
+  return s;
 }
 
 sgo_status sgo_get_basis(sgo_ctx* c, int* miller) {

@@ -230,18 +230,32 @@ sgo_status sgo_de_similar(int natoms, const double cell[9], const double* a, con
 
 sgo_status sgo_de_migrate(int np, int nsub, int natoms, double* pop, double* f) {
   if (np < 1 || nsub < 1 || np % nsub != 0 || natoms < 1 || !pop || !f) return SGO_ERR_ARG;
+  if (nsub == 1) return SGO_OK;  // a single subpopulation has no neighbour
   const int size = np / nsub;
   const size_t sz = 3 * (size_t)natoms;
+  // every subpopulation's best and its neighbour's worst are chosen on the population as
+  // it was before this call, so that a migrant moves one step round the ring at most
+  std::vector<int> best(nsub), worst(nsub);
+  for (int s = 0; s < nsub; ++s) {
+    int b = s * size, w = s * size;
+    for (int k = s * size; k < (s + 1) * size; ++k) {
+      if (f[k] < f[b]) b = k;
+      if (f[k] > f[w]) w = k;
+    }
+    best[s] = b;
+    worst[s] = w;
+  }
+  Vec xb(sz * nsub), fb(nsub), fw(nsub);
+  for (int s = 0; s < nsub; ++s) {
+    std::memcpy(xb.data() + sz * s, pop + sz * best[s], sizeof(double) * sz);
+    fb[s] = f[best[s]];
+    fw[s] = f[worst[s]];
+  }
   for (int s = 0; s < nsub; ++s) {
     const int t = (s + 1) % nsub;
-    int b = s * size, w = t * size;
-    for (int k = s * size; k < (s + 1) * size; ++k)
-      if (f[k] < f[b]) b = k;
-    for (int k = t * size; k < (t + 1) * size; ++k)
-      if (f[k] > f[w]) w = k;
-    if (f[b] < f[w]) {
-      std::memmove(pop + sz * w, pop + sz * b, sizeof(double) * sz);
-      f[w] = f[b];
+    if (fb[s] < fw[t]) {
+      std::memcpy(pop + sz * worst[t], xb.data() + sz * s, sizeof(double) * sz);
+      f[worst[t]] = fb[s];
     }
   }
   return SGO_OK;

@@ -108,6 +108,54 @@ __global__ void k_scf_gate(const int* active, int n, const int* iter, int max_sc
   for (int p = 0; p < n; ++p) nact += active[p] != 0;
   cudaGraphSetConditional(cond, (nact > 0 && *iter < max_scf) ? 1u : 0u);
 }
+// Algorithm 1's CG loop runs "while not converged".  The SCF iterations take a fixed
+// number of CG steps each; once a member's SCF stopping rule holds, further CG steps at its
+// final potential refine its bands until every band with occupation above 1e-6 has a
+// residual |H x - eps x| below the tolerance.
+// mode 0: the members whose stopping rule held (and that have not failed) take part;
+// mode 1: of those, the members that took a step (their density and energy are redone).
+__global__ void k_polish_activate(KArgs ka, int* active, int mode) {
+  for (int p = threadIdx.x; p < ka.nprob; p += blockDim.x) {
+    const Prob& P = ka.probs[p];
+    const bool ok = P.scal[SC_CONV] != 0.0 && (P.status[0] | P.status[1] | P.status[2]) == 0;
+    if (mode == 0) {
+      P.scal[SC_POLISH] = 0.0;
+      P.scal[SC_EIGRES] = 0.0;
+      active[p] = ok ? 1 : 0;
+    } else {
+      active[p] = (ok && P.scal[SC_POLISH] > 0.0) ? 1 : 0;
+    }
+  }
+}
+// The loop's test (one CTA): the largest residual over the bands with occupation above
+// 1e-6 (BV_RES, written by k_band_residual for the current bands and eigenvalues); a
+// member below tol, or at max_steps, leaves; the others count one more step.  set_cond:
+// the enclosing WHILE node runs again while some member is left.
+__global__ void k_polish_control(KArgs ka, int* active, int* passes, double tol, int max_steps,
+                                 cudaGraphConditionalHandle cond, int set_cond) {
+  __shared__ int nact;
+  if (threadIdx.x == 0) nact = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < ka.nprob; p += blockDim.x) {
+    if (!active[p]) continue;
+    const Prob& P = ka.probs[p];
+    double mx = 0.0;
+    for (int i = 0; i < P.nb; ++i)
+      if (P.occ[i] > 1e-6) mx = fmax(mx, P.bv[BV_RES * P.nb + i]);
+    P.scal[SC_EIGRES] = mx;
+    if (!(mx >= tol) || P.scal[SC_POLISH] >= (double)max_steps) {
+      active[p] = 0;
+    } else {
+      P.scal[SC_POLISH] += 1.0;
+      atomicAdd(&nact, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (passes) ++*passes;
+    if (set_cond) cudaGraphSetConditional(cond, nact > 0 ? 1u : 0u);
+  }
+}
 // out[p] = F, out_f[off_p + e] = forces (device gather for the device-pointer batch)
 __global__ void k_gather_results(KArgs ka, const int* slot, const int* foff, double* energies, double* forces,
                                  int* status) {
@@ -567,6 +615,7 @@ Launch Engine::L(const WorkMap& m) const {
   l.max_n12 = m.max_n12 >= 0 ? m.max_n12 : max_n12_;
   l.max_nb = m.max_nb >= 0 ? m.max_nb : max_nb_;
   l.plane_threads = plane_threads_;
+  l.wait_ns = wait_ns_;
   return l;
 }
 
@@ -704,7 +753,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   allocs_.push_back(d_gpart_);
   if (!cuda_ok(cudaMalloc(&d_flags_, sizeof(double) * 4 * n_), "cudaMalloc(flags)")) return;
   allocs_.push_back(d_flags_);
-  if (!cuda_ok(cudaMalloc(&d_iter_, sizeof(int)), "cudaMalloc(iter)")) return;
+  if (!cuda_ok(cudaMalloc(&d_iter_, 2 * sizeof(int)), "cudaMalloc(iter)")) return;
   allocs_.push_back(d_iter_);
   if (tc) {
     // TMA descriptors of every operand buffer (fixed for the engine's life; role swaps
@@ -730,8 +779,8 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     }
     if (!cuda_ok(cudaMallocHost(&hp_, sizeof(double) * nd), "cudaMallocHost(read-back)")) return;
     std::memset(hp_, 0, sizeof(double) * nd);
-    if (!cuda_ok(cudaMallocHost(&hpi_, sizeof(int) * (1 + 4 * (size_t)n_)), "cudaMallocHost(read-back)")) return;
-    std::memset(hpi_, 0, sizeof(int) * (1 + 4 * (size_t)n_));
+    if (!cuda_ok(cudaMallocHost(&hpi_, sizeof(int) * (2 + 4 * (size_t)n_)), "cudaMallocHost(read-back)")) return;
+    std::memset(hpi_, 0, sizeof(int) * (2 + 4 * (size_t)n_));
     if (!cuda_ok(cudaMalloc(&d_slot_, sizeof(int) * 2 * n_), "cudaMalloc(slots)")) return;
     allocs_.push_back(d_slot_);
     d_foff_ = d_slot_ + n_;
@@ -744,7 +793,9 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   }
   // mixed path: the FP32 eigensolve (its five matrices in shared memory up to nb = 105,
   // else in a per-member global scratch; the Jacobi pair tables allow nb <= 512)
-  rr_f32_ = precision_ == 1 && max_nb_ <= 512;
+  const sgo_opts& o0 = ctxs[0]->opts;
+  wait_ns_ = o0.watchdog_ms > 0.0 ? (long long)(o0.watchdog_ms * 1e6) : 2000000000LL;
+  rr_f32_ = precision_ == 1 && !o0.rr_fp64 && max_nb_ <= 512;
   if (rr_f32_ && (size_t)20 * max_nb_ * (max_nb_ | 1) > 216 * 1024) {
     rr32_stride_ = (size_t)5 * max_nb_ * (max_nb_ | 1);
     if (!cuda_ok(cudaMalloc(&d_rr32_, sizeof(float) * rr32_stride_ * n_), "cudaMalloc(rr32)")) return;
@@ -770,6 +821,8 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
 Engine::~Engine() {
   if (g_nonscf_) cudaGraphExecDestroy(g_nonscf_);
   if (g_scf_) cudaGraphExecDestroy(g_scf_);
+  if (g_polish_) cudaGraphExecDestroy(g_polish_);
+  if (g_tail_) cudaGraphExecDestroy(g_tail_);
   if (ev_in_) cudaEventDestroy(ev_in_);
   if (ev_out_) cudaEventDestroy(ev_out_);
   if (own_stream_) cudaStreamDestroy(own_stream_);
@@ -993,8 +1046,10 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S, false);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
   tbeg(TK_RR);
-  if (rr_f32_) launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1), d_rr32_, rr32_stride_);  // 5 FP32 n x (n|1)
-  else launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_);
+  if (rr_f32_)  // 5 FP32 n x (n|1) matrices
+    launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1), d_rr32_, rr32_stride_, rr_cap_);
+  else
+    launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_, 30);
   tend(TK_RR);
   rotate<T>(WB_X, false);
   rotate<T>(WB_HX, true);
@@ -1053,7 +1108,6 @@ sgo_status Engine::structure_terms() {
 // rho_out, the energy at (Psi, rho_out) and the per-member convergence test.
 template <typename T>
 void Engine::scf_iteration(int ncg, bool count_iter) {
-  const sgo_opts& o = ctx_[0]->opts;
   // V_eff from rho_in(G): one inverse transform of rho_in(G) + i V_H(G) gives
   // rho_in(r) + i V_H(r); LDA in real space
   // (in FP64 on both paths: an FP32 transform, measured, slows the SCF of some members:
@@ -1069,6 +1123,14 @@ void Engine::scf_iteration(int ncg, bool count_iter) {
   rayleigh_ritz<T>(false);
   set_scal(SC_FIRSTCG, 1.0, true);
   for (int k = 0; k < ncg; ++k) cg_step<T>();
+  density_energy<T>(count_iter ? 1 : 0);
+}
+
+// Occupations, rho_out, the energy at (Psi, rho_out) and (mode 1) the convergence test;
+// mode 2 recomputes the energy of bands refined after the stopping rule held.
+template <typename T>
+void Engine::density_energy(int mode) {
+  const sgo_opts& o = ctx_[0]->opts;
   // occupations and rho_out
   launch_occupations(L(m_prob_));
   wave_to_cols<T>(WB_X);
@@ -1087,8 +1149,96 @@ void Engine::scf_iteration(int ncg, bool count_iter) {
   tbeg(TK_GRID_OTHER);
   launch_grid_energies<T>(L(m_gch_), d_gpart_, maxchunk_);
   launch_grid_energies_reduce(L(m_prob_), d_gpart_, maxchunk_);
-  launch_finish_iteration(L(m_prob_), o.scf_tol_e, o.scf_tol_rho, count_iter ? 1 : 0);
+  launch_finish_iteration(L(m_prob_), o.scf_tol_e, o.scf_tol_rho, mode);
   tend(TK_GRID_OTHER);
+}
+
+bool Engine::read_active() {
+  cudaMemcpyAsync(h_active_.data(), d_active_, sizeof(int) * n_, cudaMemcpyDeviceToHost, stream_);
+  cudaStreamSynchronize(stream_);
+  for (int p = 0; p < n_; ++p)
+    if (h_active_[p]) return true;
+  return false;
+}
+
+// Host-driven form of the residual-controlled CG steps that follow the SCF loop (see
+// k_polish_activate), then the density and energy of the refined bands.
+template <typename T>
+void Engine::polish() {
+  const sgo_opts& o = ctx_[0]->opts;
+  const int maxs = o.eig_tol > 0.0 ? std::max(0, o.max_polish) : 0;
+  k_polish_activate<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, 0);
+  rr_cap_ = 30;
+  for (int step = 0; step <= maxs; ++step) {
+    tbeg(TK_CG_BAND);
+    launch_band_residual<T>(L(m_bands_), WB_X, WB_HX);
+    tend(TK_CG_BAND);
+    k_polish_control<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, nullptr, o.eig_tol, maxs, 0, 0);
+    if (!read_active()) break;
+    cg_step<T>();
+  }
+  rr_cap_ = 10;
+  k_polish_activate<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, 1);
+  if (read_active()) density_energy<T>(2);
+}
+
+// Graph form: g_polish_ is one WHILE node (its condition starts at 1 on every launch)
+// whose body tests the residuals (k_polish_control ends the loop when no member is left)
+// and takes one all-band CG step for the members left (a pass in which none is left
+// launches the step's kernels with every CTA masked out); g_tail_ picks the members that
+// took a step and recomputes their density and energy.  k_polish_activate(mode 0) runs
+// as a plain launch before g_polish_.
+template <typename T>
+bool Engine::build_polish_graphs() {
+  const sgo_opts& o = ctx_[0]->opts;
+  const int maxs = o.eig_tol > 0.0 ? std::max(0, o.max_polish) : 0;
+  cudaGraph_t gp = nullptr, gt = nullptr, body = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  cudaGraphNode_t loop = nullptr;
+  bool ok = cuda_ok(cudaGraphCreate(&gp, 0), "graph create") &&
+            cuda_ok(cudaGraphConditionalHandleCreate(&cond, gp, 1, cudaGraphCondAssignDefault), "conditional handle");
+  if (ok) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    ok = cuda_ok(cudaGraphAddNode(&loop, gp, nullptr, nullptr, 0, &cp), "polish while node");
+    if (ok) body = cp.conditional.phGraph_out[0];
+  }
+  const long long l0 = launches_;
+  ok = ok && cuda_ok(cudaStreamBeginCaptureToGraph(stream_, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                     "capture polish body");
+  if (ok) {
+    rr_cap_ = 30;
+    launch_band_residual<T>(L(m_bands_), WB_X, WB_HX);
+    k_polish_control<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, d_iter_ + 1, o.eig_tol, maxs, cond, 1);
+    cg_step<T>();
+    rr_cap_ = 10;
+    cudaGraph_t got = nullptr;
+    ok = cuda_ok(cudaStreamEndCapture(stream_, &got), "capture polish body end");
+  }
+  graph_launches_[2] = launches_ - l0;
+  ok = ok && cuda_ok(cudaGraphInstantiate(&g_polish_, gp, 0), "graph instantiate (polish)");
+  const long long l1 = launches_;
+  ok = ok && cuda_ok(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal), "capture tail");
+  if (ok) {
+    k_polish_activate<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, 1);
+    density_energy<T>(2);
+    ok = cuda_ok(cudaStreamEndCapture(stream_, &gt), "capture tail end");
+  }
+  graph_launches_[3] = launches_ - l1;
+  launches_ = l0;
+  ok = ok && cuda_ok(cudaGraphInstantiate(&g_tail_, gt, 0), "graph instantiate (tail)");
+  if (gp) cudaGraphDestroy(gp);
+  if (gt) cudaGraphDestroy(gt);
+  if (!ok) {
+    cudaGetLastError();
+    if (g_polish_) cudaGraphExecDestroy(g_polish_);
+    if (g_tail_) cudaGraphExecDestroy(g_tail_);
+    g_polish_ = g_tail_ = nullptr;
+  }
+  return ok;
 }
 
 // Pulay mixing of rho_out with rho_in (members still iterating).
@@ -1180,6 +1330,7 @@ sgo_status Engine::launch_t(bool want_forces) {
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   bool warm = true;
   for (auto* c : ctx_) warm = warm && c->warm && c->have_state;
+  for (auto* c : ctx_) c->last_warm = warm;
   k_reset<<<n_, 128, 0, stream_>>>(L(m_prob_).ka);
   sgo_status s = structure_terms();
   if (s != SGO_OK) return s;
@@ -1193,14 +1344,18 @@ sgo_status Engine::launch_t(bool want_forces) {
   // graph mode: batch engines, no live kernel timer (its events are host bookkeeping)
   run_graph_ = use_graph_ && timer_kind_ < 0;
   if (run_graph_ && !g_scf_) run_graph_ = build_graphs<T>();
+  if (run_graph_ && !g_polish_) run_graph_ = build_polish_graphs<T>();
   if (run_graph_) {
-    // the iteration count and the flags are read back by finish(), after the one wait
-    CK(cudaMemsetAsync(d_iter_, 0, sizeof(int), stream_));
+    // the iteration counts and the flags are read back by finish(), after the one wait
+    CK(cudaMemsetAsync(d_iter_, 0, 2 * sizeof(int), stream_));
     run_na_ = std::min(nonsc, o.max_scf);
     for (int i = 0; i < run_na_; ++i) CK(cudaGraphLaunch(g_nonscf_, stream_));
     if (o.max_scf > nonsc) CK(cudaGraphLaunch(g_scf_, stream_));
-    CK(cudaMemcpyAsync(hpi_, d_iter_, sizeof(int), cudaMemcpyDeviceToHost, stream_));
     CK(cudaMemcpyAsync(hp_, d_flags_, sizeof(double) * 4 * n_, cudaMemcpyDeviceToHost, stream_));
+    k_polish_activate<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, 0);
+    CK(cudaGraphLaunch(g_polish_, stream_));
+    CK(cudaGraphLaunch(g_tail_, stream_));
+    CK(cudaMemcpyAsync(hpi_, d_iter_, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream_));
   } else {
     int it = 0;
     for (it = 1; it <= o.max_scf; ++it) {
@@ -1213,6 +1368,7 @@ sgo_status Engine::launch_t(bool want_forces) {
       if (it > nonsc) pulay_step();
     }
     run_it_ = it;
+    polish<T>();
   }
   // forces on every member
   h_active_.assign(n_, 1);
@@ -1239,7 +1395,7 @@ sgo_status Engine::launch_t(bool want_forces) {
     CK(cudaMemcpyAsync(h, c->d.occ, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
     h += c->nb;
     CK(cudaMemcpyAsync(h, c->d.forces, sizeof(double) * c->h_forces.size(), cudaMemcpyDeviceToHost, stream_));
-    CK(cudaMemcpyAsync(hpi_ + 1 + 4 * p, c->d.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(hpi_ + 2 + 4 * p, c->d.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream_));
   }
   CK(cudaGetLastError());
   return SGO_OK;
@@ -1291,7 +1447,8 @@ sgo_status Engine::finish(std::vector<sgo_status>* per_item) {
   int it = run_it_;
   if (run_graph_) {
     it = hpi_[0];
-    launches_ += (long long)run_na_ * graph_launches_[0] + (long long)std::max(0, it - run_na_) * graph_launches_[1];
+    launches_ += (long long)run_na_ * graph_launches_[0] + (long long)std::max(0, it - run_na_) * graph_launches_[1] +
+                 1 + (long long)hpi_[1] * graph_launches_[2] + graph_launches_[3];
   }
   const int niter = std::min(it, o.max_scf);
   sgo_status all = SGO_OK;
@@ -1305,7 +1462,7 @@ sgo_status Engine::finish(std::vector<sgo_status>* per_item) {
     std::memcpy(c->h_occ.data(), h, sizeof(double) * c->nb);
     h += c->nb;
     std::memcpy(c->h_forces.data(), h, sizeof(double) * c->h_forces.size());
-    std::memcpy(c->h_status, hpi_ + 1 + 4 * p, sizeof(int) * 4);
+    std::memcpy(c->h_status, hpi_ + 2 + 4 * p, sizeof(int) * 4);
     c->have_state = true;
     c->last_iter = (int)c->h_scal[SC_ITER] + run_nonsc_;  // this member's iterations (until it converged)
     if (c->last_iter > niter) c->last_iter = niter;
@@ -1481,6 +1638,50 @@ sgo_status Engine::export_density(double* rho) {
   CK(cudaStreamSynchronize(stream_));
   cudaFree(dr);
   return SGO_OK;
+}
+
+sgo_status Engine::export_state(double* rho_g, double* psi) {
+  const Prob& d = ctx_[0]->d;
+  const size_t gbytes = sizeof(double2) * (size_t)d.ngrid, pbytes = sizeof(double) * (size_t)d.nb * d.npw;
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  char* dbuf = nullptr;
+  CK(cudaMalloc(&dbuf, gbytes + pbytes));
+  double2* dg = reinterpret_cast<double2*>(dbuf);
+  double* dp = reinterpret_cast<double*>(dbuf + gbytes);
+  if (rho_g) {
+    CK(cudaMemcpyAsync(d.gfft, d.rhog_in, gbytes, cudaMemcpyDeviceToDevice, stream_));
+    launch_grid_copy_c(L(m_gew_), nullptr, dg);
+    CK(cudaMemcpyAsync(rho_g, dg, gbytes, cudaMemcpyDeviceToHost, stream_));
+  }
+  if (psi) {
+    if (precision_) launch_copy_out<float>(L(m_bands_), WB_X, dp, d.nb);
+    else launch_copy_out<double>(L(m_bands_), WB_X, dp, d.nb);
+    CK(cudaMemcpyAsync(psi, dp, pbytes, cudaMemcpyDeviceToHost, stream_));
+  }
+  CK(cudaStreamSynchronize(stream_));
+  cudaFree(dbuf);
+  return cuda_ok(cudaGetLastError(), "export state") ? SGO_OK : SGO_ERR_CUDA;
+}
+
+sgo_status Engine::import_state(const double* rho_g, const double* psi) {
+  const Prob& d = ctx_[0]->d;
+  const size_t gbytes = sizeof(double2) * (size_t)d.ngrid, pbytes = sizeof(double) * (size_t)d.nb * d.npw;
+  h_active_.assign(n_, 1);
+  CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
+  char* dbuf = nullptr;
+  CK(cudaMalloc(&dbuf, gbytes + pbytes));
+  double2* dg = reinterpret_cast<double2*>(dbuf);
+  double* dp = reinterpret_cast<double*>(dbuf + gbytes);
+  CK(cudaMemcpyAsync(dg, rho_g, gbytes, cudaMemcpyHostToDevice, stream_));
+  CK(cudaMemcpyAsync(dp, psi, pbytes, cudaMemcpyHostToDevice, stream_));
+  launch_grid_copy_c(L(m_gew_), dg, nullptr);
+  CK(cudaMemcpyAsync(d.rhog_in, d.gfft, gbytes, cudaMemcpyDeviceToDevice, stream_));
+  if (precision_) launch_copy_in<float>(L(m_bands_), WB_X, dp, d.nb);
+  else launch_copy_in<double>(L(m_bands_), WB_X, dp, d.nb);
+  CK(cudaStreamSynchronize(stream_));
+  cudaFree(dbuf);
+  return cuda_ok(cudaGetLastError(), "import state") ? SGO_OK : SGO_ERR_CUDA;
 }
 
 sgo_status Engine::grid_transform(int sign, const double* in, double* out) {

@@ -37,6 +37,7 @@ struct sgo_ctx {
   int nb = 0;
   sgo_opts opts;
   cudaStream_t stream = nullptr;
+  int device = -1;    // the CUDA device current at sgo_create (owns every buffer)
   int precision = 0;  // 0 FP64, 1 mixed (FP32 wave data)
   // derived
   sgo::Prob d;        // descriptor (host copy, device pointers)
@@ -47,6 +48,7 @@ struct sgo_ctx {
   char* arena_main = nullptr;
   bool warm = false;
   bool have_state = false;
+  bool last_warm = false;   // the last evaluation started from the previous (or imported) state
   int last_iter = 0;
   double last_resid = 0.0;
   sgo_status last_status = SGO_OK;
@@ -69,6 +71,9 @@ class Engine {
   sgo_status apply_h(const double* veff_c, int nvec, const double* psi, double* hpsi);
   sgo_status density(int nvec, const double* psi, const double* occ, double* rho);
   sgo_status export_density(double* rho);
+  // warm-start state: rho_in(G) (complex, C order) and the packed wavefunctions
+  sgo_status export_state(double* rho_g, double* psi);
+  sgo_status import_state(const double* rho_g, const double* psi);
   sgo_status grid_transform(int sign, const double* in, double* out);
   sgo_status subspace(int nvec, const double* x, const double* y, double* c);
   sgo_status block_update(int nvec, const double* x, const double* m, double alpha, double beta, double* y);
@@ -118,6 +123,10 @@ class Engine {
  private:
   template <typename T> sgo_status launch_t(bool want_forces);
   template <typename T> void scf_iteration(int ncg, bool count_iter);
+  template <typename T> void density_energy(int mode);
+  template <typename T> void polish();
+  template <typename T> bool build_polish_graphs();
+  bool read_active();
   void pulay_step();
   template <typename T> bool build_graphs();
   template <typename T> void hpsi(int src, int dst);
@@ -206,8 +215,13 @@ class Engine {
   int tc_kc_ = TC_KC, nn_tpc_ = NN_TPC, tn_kc_ = TN_KC;
   void build_gemm_maps();
   cudaGraphExec_t g_nonscf_ = nullptr, g_scf_ = nullptr;
-  long long graph_launches_[2] = {0, 0};
-  int* d_iter_ = nullptr;
+  // the residual-controlled CG steps after the SCF stopping rule (a WHILE node whose body
+  // is one step) and the density and energy of the refined bands
+  cudaGraphExec_t g_polish_ = nullptr, g_tail_ = nullptr;
+  long long graph_launches_[4] = {0, 0, 0, 0};
+  int* d_iter_ = nullptr;       // [2]: SCF iterations, residual-controlled loop passes
+  long long wait_ns_ = 2000000000LL;  // watchdog of the tensor-core kernels' waits
+  int rr_cap_ = 10;             // Jacobi sweep cap of the FP32 subspace eigensolve
   cudaStream_t own_stream_ = nullptr;
   cudaEvent_t ev_in_ = nullptr, ev_out_ = nullptr;
 };

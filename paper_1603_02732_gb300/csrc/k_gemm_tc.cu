@@ -54,7 +54,7 @@ constexpr int NN_STAGE = 3 * 4 * NN_BOX;      // landed boxes (128 waves), hi, l
 constexpr int NN_MAX_STAGES = 4;
 constexpr int NN_THREADS = 320;
 constexpr int TC_SMEM_BUDGET = 225 * 1024;    // dynamic shared memory per CTA
-constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long TC_DRAIN_NS = 2000000000LL;     // bound of the waits for a CTA's own copies and MMAs
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -117,14 +117,22 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Bounded wait for the phase of the given parity.  Gives up (false) when another role
-// has failed (*fail) or after TC_WAIT_CYCLES, which marks the CTA failed.  fail = null:
-// a drain wait that ignores other roles' failures.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
-  const long long t0 = clock64();
+// has failed (*fail) or after limit_ns nanoseconds of wall time, which marks the CTA
+// failed.  fail = null: a drain wait for the CTA's own copies and MMAs, which ignores
+// other roles' failures and is bounded by TC_DRAIN_NS whatever the caller's watchdog.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* fail,
+                                          long long limit_ns = TC_DRAIN_NS) {
+  const unsigned long long t0 = global_ns();
   while (!mbar_test(bar, parity)) {
     if (fail && *fail) return false;
-    if (clock64() - t0 > TC_WAIT_CYCLES) {
+    if ((long long)(global_ns() - t0) > limit_ns) {
       if (fail) *fail = 1;
       return false;
     }
@@ -239,7 +247,7 @@ __device__ __forceinline__ const double* dense_tc(const Prob& P, int sel) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(TN_THREADS, 1)
     k_gemm_tn_tma(KArgs ka, const CUtensorMap* __restrict__ maps, int akind, int arole, int bkind, int brole,
-                  double* part_base, size_t part_stride, int kc) {
+                  double* part_base, size_t part_stride, int kc, long long wait_ns) {
   extern __shared__ unsigned char smem_dyn[];
   __shared__ __align__(8) uint64_t full[TN_MAX_STAGES], conv[TN_MAX_STAGES], empty[TN_MAX_STAGES], done;
   __shared__ uint32_t tmem_base;
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
       for (int s = 0; s < TN_MAX_STAGES; ++s) issued[s] = 0;
       for (int it = 0; it < nsteps; ++it) {
         const int s = it % nst, r = it / nst;
-        if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1), fail)) break;
+        if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1), fail, wait_ns)) break;
         unsigned char* st = smem + s * stage_bytes;
         mbar_expect_tx(&full[s], (uint32_t)((ra + rb) * 128));
         tma_load_2d(st, ma, k0 + it * TC_K, 0, &full[s]);
@@ -307,7 +315,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
       const uint32_t idesc = idesc_tf32(128, npad);
       for (int it = 0; it < nsteps; ++it) {
         const int s = it % nst, r = it / nst;
-        if (!mbar_wait(&conv[s], (uint32_t)(r & 1), fail)) break;
+        if (!mbar_wait(&conv[s], (uint32_t)(r & 1), fail, wait_ns)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = su32(smem + s * stage_bytes);
 #pragma unroll
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
     const int t = threadIdx.x - 64;
     for (int it = 0; it < nsteps; ++it) {
       const int s = it % nst, r = it / nst;
-      if (!mbar_wait(&full[s], (uint32_t)(r & 1), fail)) break;
+      if (!mbar_wait(&full[s], (uint32_t)(r & 1), fail, wait_ns)) break;
       unsigned char* st = smem + s * stage_bytes;
       split_units(st, st + a_lo, ra * 8, t, 128);
       split_units(st + b_hi, st + b_lo, rb * 8, t, 128);
@@ -337,7 +345,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
       mbar_arrive(&conv[s]);
     }
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of C)
-    const bool ok = mbar_wait(&done, 0, fail);
+    const bool ok = mbar_wait(&done, 0, fail, wait_ns);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (__all_sync(0xffffffffu, ok && !*fail)) {  // tcgen05.ld is warp-collective
       const int quad = warp & 3;
@@ -399,7 +407,7 @@ __global__ void k_nn_image(KArgs ka, int akind, int msel, float* img_base, size_
 __global__ void __launch_bounds__(NN_THREADS, 1)
     k_gemm_nn_tma(KArgs ka, const CUtensorMap* __restrict__ maps, const float* __restrict__ img_base,
                   size_t img_stride, int img_max, int nstages, int akind, int arole, int yrole, float alpha,
-                  float beta, int tpc) {
+                  float beta, int tpc, long long wait_ns) {
   extern __shared__ unsigned char smem_dyn[];
   __shared__ __align__(8) uint64_t full[NN_MAX_STAGES], conv[NN_MAX_STAGES], empty[NN_MAX_STAGES], tfull[2],
       tempty[2], imgbar, done;
@@ -454,7 +462,7 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
       for (int it = 0; it < niter; ++it) {
         const int s = it % nstages, r = it / nstages;
         const int tl = it / nkc, kc = it - tl * nkc;
-        if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1), fail)) break;
+        if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1), fail, wait_ns)) break;
         unsigned char* st = stages + s * NN_STAGE;
         mbar_expect_tx(&full[s], 4 * NN_BOX);
         const int x0 = (t0 + tl) * 128;
@@ -471,16 +479,16 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
     if (lane == 0) {
       const uint32_t idesc = idesc_tf32(128, npad);
       const uint32_t ih = su32(smem), il = ih + img_half;
-      bool ok = mbar_wait(&imgbar, 0, fail);
+      bool ok = mbar_wait(&imgbar, 0, fail, wait_ns);
       for (int tl = 0; ok && tl < ntl; ++tl) {
         const int b = tl & 1, use = tl >> 1;
-        if (use > 0 && !mbar_wait(&tempty[b], (uint32_t)((use - 1) & 1), fail)) break;
+        if (use > 0 && !mbar_wait(&tempty[b], (uint32_t)((use - 1) & 1), fail, wait_ns)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(b * npad);
         for (int kc = 0; kc < nkc; ++kc) {
           const int it = tl * nkc + kc;
           const int s = it % nstages, r = it / nstages;
-          if (!mbar_wait(&conv[s], (uint32_t)(r & 1), fail)) {
+          if (!mbar_wait(&conv[s], (uint32_t)(r & 1), fail, wait_ns)) {
             ok = false;
             break;
           }
@@ -512,7 +520,7 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
     const int t = threadIdx.x - 64;
     for (int it = 0; it < niter; ++it) {
       const int s = it % nstages, r = it / nstages;
-      if (!mbar_wait(&full[s], (uint32_t)(r & 1), fail)) break;
+      if (!mbar_wait(&full[s], (uint32_t)(r & 1), fail, wait_ns)) break;
       unsigned char* st = stages + s * NN_STAGE;
       split_transpose(st, st + 4 * NN_BOX, st + 8 * NN_BOX, t);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -525,7 +533,7 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
     const int ld = P.ld;
     for (int tl = 0; tl < ntl; ++tl) {
       const int b = tl & 1, use = tl >> 1;
-      const bool ok = mbar_wait(&tfull[b], (uint32_t)(use & 1), fail);
+      const bool ok = mbar_wait(&tfull[b], (uint32_t)(use & 1), fail, wait_ns);
       if (!__all_sync(0xffffffffu, ok)) break;  // tcgen05.ld is warp-collective
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int k = (t0 + tl) * 128 + quad * 32 + lane;
@@ -629,7 +637,7 @@ void launch_gemm_tn_tc(const Launch& L, const void* maps, int akind, int arole, 
                        size_t stride, int kc) {
   if (!L.map.total) return;
   k_gemm_tn_tma<<<L.map.total, TN_THREADS, TN_SMEM, L.stream>>>(
-      L.ka, reinterpret_cast<const CUtensorMap*>(maps), akind, arole, bkind, brole, part, stride, kc);
+      L.ka, reinterpret_cast<const CUtensorMap*>(maps), akind, arole, bkind, brole, part, stride, kc, L.wait_ns);
 }
 
 void launch_nn_image(const Launch& Lprob, int akind, int msel, float* img, size_t img_stride) {
@@ -643,7 +651,7 @@ void launch_gemm_nn_tc(const Launch& L, const void* maps, const float* img, size
   const int ns = nn_tc_stages(img_max);
   k_gemm_nn_tma<<<L.map.total, NN_THREADS, 1024 + img_al + ns * NN_STAGE, L.stream>>>(
       L.ka, reinterpret_cast<const CUtensorMap*>(maps), img, img_stride, img_al, ns, akind, arole, yrole,
-      (float)alpha, (float)beta, tpc);
+      (float)alpha, (float)beta, tpc, L.wait_ns);
 }
 
 void gemm_tc_set_smem_limits() {

@@ -294,14 +294,17 @@ __global__ void k_finish_iteration(KArgs ka, double tol_e, double tol_rho, int c
     sc[SC_ENL] = en;
     sc[SC_MTS] = -P.kT * sc[SC_ENTROPY];
     double F = ek + en + sc[SC_ELOC] + sc[SC_EH] + sc[SC_EXC] + sc[SC_EEW] + sc[SC_MTS];
+    sc[SC_FREE] = F;
+    if (!isfinite(F)) P.status[1] = 1;
+    // count_iter 2: the energy of the bands refined after the stopping rule held (the
+    // convergence state and the iteration count stay)
+    if (count_iter == 2) return;
     const int it = (int)sc[SC_ITER];
     sc[SC_DF] = it > 0 ? F - sc[SC_FPREV] : 1e300;
     bool conv = count_iter && it > 0 && fabs(sc[SC_DF]) < tol_e && sc[SC_RESID] < tol_rho;
-    sc[SC_FREE] = F;
     sc[SC_FPREV] = F;
     if (count_iter) sc[SC_ITER] = it + 1;
     sc[SC_CONV] = conv ? 1.0 : 0.0;
-    if (!isfinite(F)) P.status[1] = 1;
   }
 }
 

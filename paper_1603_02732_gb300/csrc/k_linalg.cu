@@ -275,6 +275,32 @@ __global__ void __launch_bounds__(BAND_THREADS) k_band_kinetic(KArgs ka, int xr)
   if (threadIdx.x == 0) P.bv[BV_EKIN * P.nb + i] = s;
 }
 
+// |H x_i - eps_i x_i| of every band (the convergence test of Algorithm 1's CG loop).
+template <typename T>
+__global__ void __launch_bounds__(BAND_THREADS) k_band_residual(KArgs ka, int xr, int hxr) {
+  __shared__ double red[33];
+  constexpr int W = Pack16<T>::W;
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int i = blockIdx.x - ka.start[p];
+  const size_t off = (size_t)i * P.ld;
+  const Pack16<T>* x = pk(wbuf<T>(P, xr) + off);
+  const Pack16<T>* hx = pk(wbuf<T>(P, hxr) + off);
+  const T eps = T(P.eps[i]);
+  T st = T(0);
+  for (int v = threadIdx.x; v < P.ld / W; v += blockDim.x) {
+    const Pack16<T> a = x[v], h = hx[v];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const T r = h.e[j] - eps * a.e[j];
+      st += r * r;
+    }
+  }
+  const double s = block_sum((double)st, red);
+  if (threadIdx.x == 0) P.bv[BV_RES * P.nb + i] = sqrt(s);
+}
+
 // Teter-Payne-Allan preconditioner factor, y = T(G) / E_kin(band).
 template <typename T>
 __device__ __forceinline__ T tpa(T y) {
@@ -500,7 +526,8 @@ __global__ void k_copy_out(KArgs ka, int role, double* dst, int nvec) {
 //   so that X Tm is orthonormal and diagonalises H in the subspace.
 // Matrices: A, L, V in shared memory when 3 nb^2 doubles fit, else in global scratch.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, double* gscratch, size_t gstride) {
+__global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, double* gscratch, size_t gstride,
+                                                   int max_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ double cs_c[256], cs_s[256];
@@ -598,8 +625,8 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
   // off-diagonal norm is below 1e-11 of the diagonal norm (FP64 rounding floor ~1e-15).
   const int m = n + (n & 1);
   const int half = m / 2;
-  int sweeps = 0;
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  int sweeps = 0, capped = 0;
+  for (int sweep = 0;; ++sweep) {
     double off = 0.0, dia = 0.0;
     for (int e = tid; e < n * n; e += nt) {
       int i = e / n, j = e % n;
@@ -609,6 +636,10 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
     off = block_sum(off, red);
     dia = block_sum(dia, red);
     if (off <= 1e-22 * dia || off == 0.0) break;
+    if (sweep == max_sweeps) {
+      capped = 1;
+      break;
+    }
     ++sweeps;
     for (int r = 0; r < m - 1; ++r) {
       if (tid < half) {
@@ -680,7 +711,10 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
     int i = e / n, j = e % n;
     P.Tm[i * n + (int)P.bv[BV_TMP0 * n + j]] = V[e];
   }
-  if (tid == 0) P.scal[SC_RRSWEEPS] += sweeps;
+  if (tid == 0) {
+    P.scal[SC_RRSWEEPS] += sweeps;
+    P.scal[SC_RRCAP] += capped;
+  }
   if (tid == 0 && flag) P.status[0] = 1;
 }
 
@@ -703,7 +737,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch, size_t gstride) {
+__global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch, size_t gstride, int max_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float red[32];
   __shared__ float cs_c[256], cs_s[256];
@@ -798,8 +832,8 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
   // pair columns Q as A_PQ <- J_P^T A_PQ J_Q (one pass), and V_{:,Q} <- V_{:,Q} J_Q.
   const int m = n + (n & 1);
   const int half = m / 2;
-  int sweeps = 0;
-  for (int sweep = 0; sweep < 10; ++sweep) {
+  int sweeps = 0, capped = 0;
+  for (int sweep = 0;; ++sweep) {
     if (tid == 0) nbig = 0;
     __syncthreads();
     for (int i = ty; i < n; i += nty)
@@ -807,6 +841,10 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
         if (fabsf(A[i * ns + j]) > thr) nbig = 1;
     __syncthreads();
     if (nbig == 0) break;
+    if (sweep == max_sweeps) {  // still off-diagonal entries above the threshold
+      capped = 1;
+      break;
+    }
     ++sweeps;
     for (int r = 0; r < m - 1; ++r) {
       if (tid < half) {
@@ -884,6 +922,7 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
   }
   if (tid == 0) {
     P.scal[SC_RRSWEEPS] += sweeps;
+    P.scal[SC_RRCAP] += capped;
     if (flag) P.status[0] = 1;
   }
 }
@@ -982,6 +1021,11 @@ void launch_band_kinetic(const Launch& L, int xrole) {
   k_band_kinetic<T><<<L.map.total, BAND_THREADS, 0, L.stream>>>(L.ka, xrole);
 }
 template <typename T>
+void launch_band_residual(const Launch& L, int xrole, int hxrole) {
+  if (!L.map.total) return;
+  k_band_residual<T><<<L.map.total, BAND_THREADS, 0, L.stream>>>(L.ka, xrole, hxrole);
+}
+template <typename T>
 void launch_cg_precond(const Launch& L, int x, int hx, int p, int r, int pp, int rp) {
   if (!L.map.total) return;
   k_cg_precond<T><<<L.map.total, BAND_THREADS, 0, L.stream>>>(L.ka, x, hx, p, r, pp, rp);
@@ -1011,11 +1055,11 @@ void launch_copy_out(const Launch& L, int role, double* dst, int nvec) {
   if (!L.map.total) return;
   k_copy_out<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, role, dst, nvec);
 }
-void launch_rr_f32(const Launch& L, size_t smem, float* gscratch, size_t gstride) {
-  k_rr_f32<<<L.ka.nprob, RR_THREADS, gscratch ? 0 : smem, L.stream>>>(L.ka, gscratch, gstride);
+void launch_rr_f32(const Launch& L, size_t smem, float* gscratch, size_t gstride, int max_sweeps) {
+  k_rr_f32<<<L.ka.nprob, RR_THREADS, gscratch ? 0 : smem, L.stream>>>(L.ka, gscratch, gstride, max_sweeps);
 }
-void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride) {
-  k_rr<<<L.ka.nprob, RR_THREADS, use_smem ? smem : 0, L.stream>>>(L.ka, use_smem, gscratch, gstride);
+void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride, int max_sweeps) {
+  k_rr<<<L.ka.nprob, RR_THREADS, use_smem ? smem : 0, L.stream>>>(L.ka, use_smem, gscratch, gstride, max_sweeps);
 }
 void launch_occupations(const Launch& L) { k_occupations<<<L.ka.nprob, 32, 0, L.stream>>>(L.ka); }
 void launch_finish_cg(const Launch& L) { k_finish_cg<<<L.ka.nprob, 128, 0, L.stream>>>(L.ka); }
@@ -1031,6 +1075,7 @@ void linalg_set_smem_limits(size_t bytes) {
   template void launch_gemm_tn<T>(const Launch&, int, int, int, int, double*, size_t, int);     \
   template void launch_gemm_nn<T>(const Launch&, int, int, int, int, double, double);           \
   template void launch_band_kinetic<T>(const Launch&, int);                                     \
+  template void launch_band_residual<T>(const Launch&, int, int);                               \
   template void launch_cg_precond<T>(const Launch&, int, int, int, int, int, int);              \
   template void launch_normalize<T>(const Launch&, int, int);                                   \
   template void launch_line_min<T>(const Launch&, int, int, int, int);                          \

@@ -42,6 +42,7 @@ struct Launch {
   cudaStream_t stream;
   int max_n1, max_n2, max_n3, max_n12, max_nb;
   int plane_threads;
+  long long wait_ns = 2000000000LL;  // bound of the tensor-core kernels' device waits (watchdog)
 };
 
 // operands of the subspace GEMMs
@@ -123,14 +124,17 @@ void gemm_tc_set_smem_limits();
 template <typename T>
 void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta);
 template <typename T> void launch_band_kinetic(const Launch& L, int xrole);
+template <typename T> void launch_band_residual(const Launch& L, int xrole, int hxrole);
 template <typename T> void launch_cg_precond(const Launch& L, int x, int hx, int p, int r, int pp, int rp);
 template <typename T> void launch_normalize(const Launch& L, int p, int pp);
 template <typename T> void launch_line_min(const Launch& L, int x, int hx, int p, int hp);
 template <typename T> void launch_random_init(const Launch& L, int xrole, unsigned long long seed);
 template <typename T> void launch_copy_in(const Launch& L, int role, const double* src, int nvec);
 template <typename T> void launch_copy_out(const Launch& L, int role, double* dst, int nvec);
-void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride);
-void launch_rr_f32(const Launch& L, size_t smem, float* gscratch = nullptr, size_t gstride = 0);
+// subspace diagonalisation; max_sweeps caps the Jacobi sweeps (a stop at the cap is counted
+// in SC_RRCAP)
+void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride, int max_sweeps = 30);
+void launch_rr_f32(const Launch& L, size_t smem, float* gscratch = nullptr, size_t gstride = 0, int max_sweeps = 10);
 void launch_occupations(const Launch& L);
 void launch_finish_cg(const Launch& L);
 void linalg_set_smem_limits(size_t bytes);

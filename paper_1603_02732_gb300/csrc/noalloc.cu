@@ -12,7 +12,8 @@
 // The array lives on every GPU that loads the library until the process exits.  In host
 // code its name is only a host-side stand-in, so its device address is looked up with
 // cudaGetSymbolAddress, once per device, with that device current, on the first call made
-// on that device; that first call should come before any stream capture.  Every call
+// on that device; that first call should come before any stream capture.  The device
+// current at a call must be the context's (the one current at sgo_create).  Every call
 // shares the array and leaves its contents behind; each call writes every byte it later
 // reads, so nothing has to be cleared.  Calls that overlap on the GPU (different streams
 // or threads) race on the array.
@@ -41,9 +42,17 @@ int div_up(long a, long b) { return (int)((a + b - 1) / b); }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-sgo_status scratch_address(void** out) {
+// The array's address on the context's device.  The address is looked up with the
+// current device, so that device must be the one whose memory holds the context (and on
+// which its stream runs): a context used with another device current is refused.
+sgo_status scratch_address(const sgo_ctx* c, void** out) {
   int dev = 0;
   if (!sgo::cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return SGO_ERR_CUDA;
+  if (dev != c->device) {
+    sgo::set_error("no-alloc call with device " + std::to_string(dev) + " current, but the context lives on device " +
+                   std::to_string(c->device));
+    return SGO_ERR_ARG;
+  }
   if (dev < 0 || dev >= kMaxDevices) {
     sgo::set_error("device ordinal beyond the no-alloc address cache");
     return SGO_ERR_ARG;
@@ -155,7 +164,7 @@ extern "C" SGO_API sgo_status sgo_apply_hamiltonian_noalloc(sgo_ctx* c, const do
                                                             const double* psi, double* hpsi) {
   if (!c || !veff || !psi || !hpsi || nvec < 1 || nvec > c->nb) return SGO_ERR_ARG;
   void* base = nullptr;
-  sgo_status s = scratch_address(&base);
+  sgo_status s = scratch_address(c, &base);
   if (s != SGO_OK) return s;
   return c->precision ? run<float>(c, veff, nvec, psi, hpsi, static_cast<char*>(base))
                       : run<double>(c, veff, nvec, psi, hpsi, static_cast<char*>(base));

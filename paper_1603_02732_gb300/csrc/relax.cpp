@@ -241,6 +241,7 @@ struct sgo_relax {
   bool have_prev = false;
   double at = 0.0, p0 = 0.0, dmax = 0.0;
   double a_prev = 1.0;           // the previous line's minimising step: the next trial step
+                                 // (1 again whenever the preconditioner is renewed)
   double theta[3] = {0, 0, 0};
   bool have_theta = false;
   int ndir = 0;
@@ -407,6 +408,7 @@ void start_line(sgo_relax* r) {
       }
       fit_force_field(r);
       build_preconditioner(r);
+      r->a_prev = 1.0;  // a step found under the previous preconditioner has its scale
     }
   } else if (r->P.empty()) {
     r->P.assign((size_t)m * m, 0.0);

@@ -37,6 +37,9 @@ enum {
   SC_STATUS,      // sgo_status of this member
   SC_FIRSTCG,     // 1 while the CG history is empty
   SC_RRSWEEPS,    // Jacobi sweeps accumulated over the run (diagnostic)
+  SC_POLISH,      // CG steps after the SCF stopping rule held (residual-controlled loop)
+  SC_EIGRES,      // largest |H x - eps x| over the bands with occupation above 1e-6
+  SC_RRCAP,       // subspace diagonalisations that stopped at their Jacobi sweep cap
   SC_PULAY_A = 24 // MAX_HIST*MAX_HIST Gram matrix of residuals (24..87 overlaps next; see NSCAL_ALL)
 };
 constexpr int NSCAL_ALL = SC_PULAY_A + MAX_HIST * MAX_HIST + 8;

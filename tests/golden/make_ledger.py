@@ -1,12 +1,13 @@
-"""Write the oracle's full-size reference values for the error ledger of the configs the
-population bench does not cover (the 24-atom monolayer and the 13-atom cluster).
+"""Write the oracle's full-size reference values for the error ledger: the named configs
+(the 24-atom monolayer, the 13-atom cluster) and DE population members (``de<i>``, the
+member i of ``workloads.de_population``, checked inside the 64-member batch).
 
 Runs only oracle/ (plain FP64 SCF, tight tolerances) on the workloads' seeded inputs and
 stores, per config, the free energy, the energy terms, every eigenvalue and occupation and
 every force component in tests/golden/ledger_<config>.json.  Slow (CPU minutes to hours):
 run it by hand, never from a test.
 
-    python tests/golden/make_ledger.py honeycomb24 [cluster13]
+    python tests/golden/make_ledger.py honeycomb24 [cluster13] [de044]
 """
 import json
 import os
@@ -22,13 +23,22 @@ import oracle  # noqa: E402
 import workloads  # noqa: E402
 
 
+def structure(name):
+    """The seeded input of a ledger name: a named config or population member de<i>."""
+    if name in workloads.CONFIGS:
+        return workloads.CONFIGS[name](), f"workloads.CONFIGS['{name}']()"
+    if name.startswith("de") and name[2:].isdigit():
+        return workloads.de_candidate(int(name[2:])), f"workloads.de_candidate({int(name[2:])})"
+    raise KeyError(name)
+
+
 def main(names):
     for name in names:
-        st = workloads.CONFIGS[name]()
+        st, src = structure(name)
         t0 = time.time()
         r = oracle.scf(st)
         dt = time.time() - t0
-        out = dict(_source=f"oracle.scf on workloads.CONFIGS['{name}'](), FP64, default tolerances "
+        out = dict(_source=f"oracle.scf on {src}, FP64, default tolerances "
                            f"(|dF| < 1e-8 Ha, density residual < 1e-7), {r.n_iter} iterations, {dt:.0f} s",
                    natoms=int(st.natoms), free_energy=float(r.free_energy), energy=float(r.energy),
                    terms={k: float(v) for k, v in r.terms.items()}, eig=[float(x) for x in r.eig],

@@ -50,7 +50,7 @@ def test_offspring_argument_checks(sgo):
 def test_migration_and_similarity_match_oracle(sgo):
     rng = np.random.default_rng(12)
     A = CELLS[1]
-    for nsub in (2, 4):
+    for nsub in (1, 2, 4):
         pop, f = _population(8, 5, 20 + nsub, A)
         f[rng.integers(0, 8)] = f.min()      # a tie, resolved by index on both sides
         p1, f1 = sgo.de_migrate(pop, f, nsub)

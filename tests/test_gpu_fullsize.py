@@ -4,8 +4,9 @@
   (72^3, 22119 plane waves) and large cluster (128^3, 93885 plane waves, mixed path) sizes vs
   the oracle's FFT-applied H.
 * The 64-member DE population, evaluated as one mixed-precision batch in the launch
-  configuration bench.py times, vs full oracle SCF runs of its two smallest members
-  (energy 1e-5 Ha/atom, forces 1e-4 Ha/bohr).
+  configuration bench.py times, vs full oracle SCF runs of its two smallest members and
+  stored oracle ledgers of a mid-size and the largest member (energy 1e-5 Ha/atom, forces
+  1e-4 Ha/bohr, occupied eigenvalues 2e-4 Ha).
 * The monolayer SCF in mixed precision vs the FP64 GPU path (a property at any size).
 """
 import numpy as np
@@ -46,17 +47,41 @@ def test_fullsize_hpsi_sampled(sgo, name, precision, tol):
     assert np.abs(got - ref).max() < tol * np.abs(ref).max()
 
 
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"ledger_{name}.json")
+    return json.load(open(path)) if os.path.exists(path) else None
+
+
 def test_population_batch_vs_oracle(sgo):
+    """The 64-member population as one mixed-precision batch in bench.py's launch
+    configuration, against the oracle: its two smallest members (oracle SCF run here) and
+    the members with stored oracle ledgers (tests/golden/ledger_de<i>.json: a mid-size
+    member and the largest, 32 atoms, 80 bands), each on F (1e-5 Ha/atom), every force
+    component (1e-4 Ha/bohr) and every eigenvalue with occupation above 1e-6 (2e-4 Ha)."""
     import bench
     pop = workloads.de_population(64)
     ctxs = [sgo.Context(st, precision="mixed", **bench._tols("mixed", st)) for st in pop]
     E, F, status = sgo.Batch(ctxs).energy_forces()
     assert np.all(status == 0)
     small = sorted(range(64), key=lambda i: (pop[i].natoms, i))[:2]
-    for i in small:
-        ref = oracle.scf(pop[i])
-        assert abs(E[i] - ref.free_energy) / pop[i].natoms < 1e-5, i
-        assert np.abs(F[i] - ref.forces).max() < 1e-4, i
+    refs = {i: oracle.scf(pop[i]) for i in small}
+    for i, r in refs.items():
+        refs[i] = dict(free_energy=r.free_energy, forces=r.forces, eig=r.eig, occ=r.occ)
+    for i in range(64):
+        g = _golden(f"de{i:03d}")
+        if g is not None:
+            refs[i] = g
+    assert len(refs) >= 3
+    for i, ref in refs.items():
+        n = pop[i].natoms
+        assert abs(E[i] - ref["free_energy"]) / n < 1e-5, i
+        assert np.abs(F[i] - np.array(ref["forces"])).max() < 1e-4, i
+        eig, _ = ctxs[i].eigen()
+        occ = np.array(ref["occ"])
+        de = np.abs(eig - np.array(ref["eig"]))[occ > 1e-6]
+        assert de.max() < 2e-4, (i, float(de.max()), ctxs[i].stats())
 
 
 def test_monolayer_mixed_matches_fp64(sgo):
@@ -70,29 +95,33 @@ def test_monolayer_mixed_matches_fp64(sgo):
 
 
 def _ledger_configs():
+    """The named configs with stored oracle ledgers (population members, ledger_de<i>, are
+    checked inside the 64-member batch above)."""
     import glob
     import os
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-    return sorted(os.path.basename(p)[len("ledger_"):-len(".json")] for p in glob.glob(os.path.join(here, "ledger_*.json")))
+    names = (os.path.basename(p)[len("ledger_"):-len(".json")] for p in glob.glob(os.path.join(here, "ledger_*.json")))
+    return sorted(n for n in names if n in workloads.CONFIGS)
 
 
 @pytest.mark.parametrize("name", _ledger_configs())
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-rr64"])
 def test_fullsize_error_ledger(sgo, name, precision):
     """Error ledger at full size against stored oracle values (tests/golden/ledger_*.json,
     written by tests/golden/make_ledger.py from oracle/ alone): every eigenvalue with
     occupation above 1e-6, every energy term, the free energy and every force component.
     Bounds: the accuracy gate (1e-5 Ha/atom, 1e-4 Ha/bohr) for F and forces; per energy
     term 1e-5 Ha/atom (FP64) or 1e-4 Ha/atom (mixed); per eigenvalue with occupation above
-    1e-6, 1e-5 Ha (FP64), or (mixed) 2e-4 Ha weighted by the band's occupation f_n / 2:
-    Algorithm 1 converges the nearly empty bands at the top of the subspace last, and the
-    SCF stops on the energy and density (measured: 3.8e-3 Ha unweighted on the 13-atom
-    cluster, F within 1.4e-6 Ha/atom).  F is variational, second order in the density and wavefunction
-    errors; a single term or an eigenvalue is first order in them, and the mixed path
-    stops at a density residual of 1e-5 per electron (its FP32 noise floor), so its terms
-    and eigenvalues carry errors of that order times their response (measured: eigenvalues
-    6.3e-5 Ha on the monolayer, the kinetic term 1.7e-5 Ha/atom on the 13-atom cluster)
-    while F stays at 6e-7 and 1.4e-6 Ha/atom."""
+    1e-6, 1e-5 Ha (FP64) or 2e-4 Ha (mixed).  The reported bands satisfy Algorithm 1's
+    loop condition: after the SCF stopping rule, CG steps continue until every band with
+    occupation above 1e-6 has |H psi - eps psi| < eig_tol (1e-4 Ha), and the test checks
+    that it was reached.  F is variational, second order in the density and wavefunction
+    errors; a single term or an eigenvalue is first order in the density error, and the
+    mixed path stops at a density residual of 1e-5 per electron (its FP32 noise floor), so
+    its terms and eigenvalues carry errors of that order times their response (measured:
+    eigenvalues 6.3e-5 Ha on the monolayer, the kinetic term 1.7e-5 Ha/atom on the 13-atom
+    cluster) while F stays near 1e-6 Ha/atom.  mixed-rr64: the mixed path with the overlap
+    Cholesky and the subspace eigensolve in FP64 (the ablation of the FP32 eigensolve)."""
     import json
     import os
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"ledger_{name}.json")
@@ -100,7 +129,9 @@ def test_fullsize_error_ledger(sgo, name, precision):
     st = workloads.CONFIGS[name]()
     tol = dict(scf_tol_e=1e-8, scf_tol_rho=1e-7) if precision == "fp64" else dict(scf_tol_e=1e-7 * st.natoms,
                                                                                    scf_tol_rho=1e-5)
-    ctx = sgo.Context(st, precision=precision, **tol)
+    if precision == "mixed-rr64":
+        tol["rr_fp64"] = 1
+    ctx = sgo.Context(st, precision=precision.split("-")[0], **tol)
     E, F = ctx.energy_forces()
     n = st.natoms
     eig, occ = ctx.eigen()
@@ -115,12 +146,12 @@ def test_fullsize_error_ledger(sgo, name, precision):
     occd = occ_ref > 1e-6
     de = np.abs(eig - np.array(ref["eig"]))
     ledger["max_deig_occupied"] = float(de[occd].max())
-    ledger["max_weighted_deig"] = float((0.5 * occ_ref * de).max())
+    stats = ctx.stats()
+    ledger.update(stats)
+    print(name, precision, ledger)
+    assert stats["eig_resid"] < 1e-4, ledger
     assert ledger["dF_per_atom"] < 1e-5, ledger
     assert ledger["max_dforce"] < 1e-4, ledger
     for k, _ in keys:
         assert ledger[k] < (1e-5 if precision == "fp64" else 1e-4), (k, ledger)
-    if precision == "fp64":
-        assert ledger["max_deig_occupied"] < 1e-5, ledger
-    else:
-        assert ledger["max_weighted_deig"] < 2e-4, ledger
+    assert ledger["max_deig_occupied"] < (1e-5 if precision == "fp64" else 2e-4), ledger

@@ -192,6 +192,52 @@ def test_not_converged_status(sgo):
     assert e.value.status == sgo.SGO_ERR_NOT_CONVERGED
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_state_moves_between_contexts(sgo, precision):
+    """sgo_get_state / sgo_set_state (Sec. II C: a relaxation step restarts from the previous
+    density and wavefunctions): a fresh context given a converged donor's state starts warm
+    and reproduces the donor's result within a few SCF iterations."""
+    st = workloads.de_candidate(47)
+    opts = dict(precision=precision, scf_tol_e=1e-8, scf_tol_rho=1e-7) if precision == "fp64" else \
+        dict(precision=precision, scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5)
+    fresh = sgo.Context(st, **opts)
+    with pytest.raises(sgo.SgoError) as e:
+        fresh.get_state()
+    assert e.value.status == sgo.SGO_ERR_ARG
+    donor = sgo.Context(st, **opts)
+    E0, F0 = donor.energy_forces()
+    n0 = donor.stats()["n_iter"]
+    rho, psi = donor.get_state()
+    assert rho.shape == tuple(donor.grid) and psi.shape == (st.nbands, donor.npw)
+    # rho_in(G) of a real density: rho(-G) = rho(G)^*, and rho(0) N = N_el / Omega
+    assert abs(rho[0, 0, 0].real * abs(np.linalg.det(st.cell)) - st.nelec) < 1e-6 * st.nelec
+    assert np.allclose(rho[0, 0, 1], np.conj(rho[0, 0, -1]), atol=1e-12)
+    fresh.set_state(rho, psi)
+    E1, F1 = fresh.energy_forces()
+    s1 = fresh.stats()
+    assert s1["warm"] and s1["n_iter"] <= 3 < n0, (s1, n0)
+    tol_e = 1e-7 if precision == "fp64" else 2e-6
+    assert abs(E1 - E0) / st.natoms < tol_e
+    assert np.abs(F1 - F0).max() < (1e-5 if precision == "fp64" else 1e-4)
+    with pytest.raises(sgo.SgoError):
+        fresh.set_state(rho, np.full_like(psi, np.nan))
+
+
+def test_watchdog_expiry_is_reported(sgo):
+    """Every device wait of the tensor-core kernels is bounded by watchdog_ms; a bound far
+    below the time a TMA load takes makes the waits give up.  The kernels drain their own
+    copies and MMAs (under a separate fixed bound), free their TMEM and return; the member
+    reports SGO_ERR_TIMEOUT, and the process's contexts stay usable."""
+    st = _struct(ecut=3.0)
+    ctx = sgo.Context(st, precision="mixed", watchdog_ms=1e-6, scf_tol_e=1e-7, scf_tol_rho=1e-5)
+    with pytest.raises(sgo.SgoError) as e:
+        ctx.energy_forces()
+    assert e.value.status == sgo.SGO_ERR_TIMEOUT
+    ok = sgo.Context(st, precision="mixed", scf_tol_e=1e-7, scf_tol_rho=1e-5)
+    F, f = ok.energy_forces()
+    assert math.isfinite(F) and np.all(np.isfinite(f))
+
+
 def test_autograd_adjoint(sgo):
     import torch
     st = _struct(ecut=3.0)

@@ -312,6 +312,41 @@ def test_pz81_high_density_log_coefficient_is_rpa():
     assert abs(lda.PZ_A - (1 - math.log(2)) / math.pi ** 2) < 1e-4
 
 
+# Perdew & Zunger, Phys. Rev. B 23, 5048 (1981), Appendix C, unpolarised fit to
+# Ceperley-Alder: gamma = -0.1423, beta1 = 1.0529, beta2 = 0.3334 (r_s >= 1) and
+# A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116 (r_s < 1).  Values evaluated by hand
+# (30-digit arithmetic, rounded to 10 digits), independent of oracle/lda.py:
+#   r_s = 0.5: ln r_s = -0.6931471806
+#     eps_c = A ln r_s + B + C r_s ln r_s + D r_s
+#           = -0.02155687732 - 0.048 - 0.00069314718 - 0.0058       = -0.07605002450
+#     v_c   = A ln r_s + (B - A/3) + (2/3) C r_s ln r_s + ((2D - C)/3) r_s
+#           = -0.02155687732 - 0.05836666667 - 0.00046209812 - 0.0042 = -0.08458564210
+#   r_s >= 1: den = 1 + beta1 sqrt(r_s) + beta2 r_s, eps_c = gamma / den,
+#             num = 1 + (7/6) beta1 sqrt(r_s) + (4/3) beta2 r_s, v_c = eps_c num / den
+#   r_s = 1:  den = 2.3863,        num = 2.672916667, eps_c = -0.05963206638, v_c = -0.06679442823
+#   r_s = 2:  den = 3.155825460,   num = 3.626263036, eps_c = -0.04509121363, v_c = -0.05181294192
+#   r_s = 5:  den = 5.021355974,   num = 5.969415302, eps_c = -0.02833895879, v_c = -0.03368950840
+#   r_s = 10: den = 7.663562148,   num = 9.329822506, eps_c = -0.01856838860, v_c = -0.02260564558
+PZ81_TABLE = [(0.5, -0.07605002450, -0.08458564210), (1.0, -0.05963206638, -0.06679442823),
+              (2.0, -0.04509121363, -0.05181294192), (5.0, -0.02833895879, -0.03368950840),
+              (10.0, -0.01856838860, -0.02260564558)]
+
+
+@pytest.mark.parametrize("rs,ec_ref,vc_ref", PZ81_TABLE)
+def test_pz81_correlation_at_tabulated_rs(rs, ec_ref, vc_ref):
+    """eps_c and v_c at r_s in {0.5, 1, 2, 5, 10} against the hand-evaluated published
+    formulas above.  A change of any constant in its last printed digit (beta2 by 1e-4
+    moves eps_c(10) by 7.6e-6, D by 1e-4 moves eps_c(0.5) by 5e-5) fails here even where
+    the r_s = 1 join still holds; the total eps_xc and v_xc are checked through lda()."""
+    ec, vc = lda.correlation(np.array([rs]))
+    assert abs(ec[0] - ec_ref) < 2e-11
+    assert abs(vc[0] - vc_ref) < 2e-11
+    rho = 3.0 / (4 * math.pi * rs ** 3)
+    exc, vxc = lda.lda(np.array([rho]))
+    assert abs(exc[0] - (-0.4581652932831429 / rs + ec_ref)) < 1e-10
+    assert abs(vxc[0] - (4.0 / 3.0 * -0.4581652932831429 / rs + vc_ref)) < 1e-10
+
+
 @pytest.mark.parametrize("rs", [0.3, 0.8, 1.5, 4.0, 12.0])
 def test_vxc_is_derivative_of_rho_exc(rs):
     rho = 3.0 / (4 * math.pi * rs ** 3)

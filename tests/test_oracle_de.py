@@ -108,11 +108,23 @@ def test_ring_migration_moves_each_best_to_the_next_subpopulation():
     pop = np.arange(8, dtype=float).reshape(8, 1, 1)
     f = np.array([-1.0, -3.0, 0.0, 2.0, -5.0, 1.0, -2.0, 4.0])
     p2, f2 = de.migrate(pop, f, 4)
-    # subpopulations {0,1} {2,3} {4,5} {6,7}, in ring order: the best of {0,1} (slot 1,
-    # -3) replaces the worst of {2,3} (slot 3, 2); the best of {2,3} is now that migrant
-    # (slot 3, -3) and replaces the worst of {4,5} (slot 5, 1); the best of {4,5} (slot 4,
-    # -5) replaces the worst of {6,7} (slot 7, 4); the best of {6,7} is now that migrant
-    # (slot 7, -5) and replaces the worst of {0,1} (slot 0, -1)
-    assert f2.tolist() == [-5.0, -3.0, 0.0, -3.0, -5.0, -3.0, -2.0, -5.0]
-    assert p2[:, 0, 0].tolist() == [4.0, 1.0, 2.0, 1.0, 4.0, 1.0, 6.0, 4.0]
+    # subpopulations {0,1} {2,3} {4,5} {6,7}; bests (before any copy) slots 1, 2, 4, 6 and
+    # worsts 0, 3, 5, 7: slot 1 (-3) replaces slot 3 (2), slot 2 (0) replaces slot 5 (1),
+    # slot 4 (-5) replaces slot 7 (4), slot 6 (-2) replaces slot 0 (-1)
+    assert f2.tolist() == [-2.0, -3.0, 0.0, -3.0, -5.0, 0.0, -2.0, -5.0]
+    assert p2[:, 0, 0].tolist() == [6.0, 1.0, 2.0, 1.0, 4.0, 2.0, 6.0, 4.0]
     assert np.all(f2 <= f)
+
+
+def test_ring_migration_moves_a_migrant_one_step_only():
+    """Three subpopulations with one dominant individual: it reaches the next subpopulation
+    only.  Were best and worst re-read after each copy, the migrant would be the best of
+    subpopulation 1 on the next pass, cascade round the ring and overwrite slot 1 as well."""
+    pop = np.arange(6, dtype=float).reshape(6, 1, 1)
+    f = np.array([-9.0, 0.0, 5.0, 6.0, 7.0, 8.0])
+    p2, f2 = de.migrate(pop, f, 3)
+    assert f2.tolist() == [-9.0, 0.0, 5.0, -9.0, 7.0, 5.0]
+    assert p2[:, 0, 0].tolist() == [0.0, 1.0, 2.0, 0.0, 4.0, 2.0]
+    # one subpopulation has no neighbour: nothing moves (no duplicate of its best)
+    p1, f1 = de.migrate(pop, f, 1)
+    assert np.array_equal(p1, pop) and np.array_equal(f1, f)

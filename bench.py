@@ -358,7 +358,8 @@ def run_ours(args):
         dist.barrier()
     status = s_dev.cpu().numpy()
     iters = [c.info()["n_iter"] for c in ctxs]
-    sweeps = [c.stats()["jacobi_sweeps"] for c in ctxs]
+    cstats = [c.stats() for c in ctxs]
+    sweeps = [c["jacobi_sweeps"] for c in cstats]
     n_ok = int(np.sum(status == 0))
     value = ws * MEMBERS * args.steps / (total_ms / 1e3)
 
@@ -399,6 +400,13 @@ def run_ours(args):
                                 converged=f"{n_ok}/{MEMBERS}", scf_options=dict(_SCF),
                                 scf_iterations=dict(mean=float(np.mean(iters)), max=int(np.max(iters))),
                                 jacobi_sweeps=dict(mean=float(np.mean(sweeps)), max=int(np.max(sweeps))),
+                                eigen_refinement=dict(
+                                    rule="CG steps after the SCF stopping rule until every band with "
+                                         "occupation > 1e-6 has |H psi - eps psi| < 1e-4 Ha",
+                                    steps_mean=float(np.mean([c["polish_steps"] for c in cstats])),
+                                    steps_max=int(np.max([c["polish_steps"] for c in cstats])),
+                                    max_residual=float(np.max([c["eig_resid"] for c in cstats])),
+                                    jacobi_cap_hits=int(np.sum([c["jacobi_cap_hits"] for c in cstats]))),
                                 autotuned=batch.tuning(), sub_batches=args.sub_batches or "auto"),
                     e2e=dict(value=e2e_val, unit="evals/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     host_loop=dict(value=ws * MEMBERS * args.steps / (timer_ms / 1e3), unit="evals/s",
@@ -423,23 +431,31 @@ def run_ours(args):
                               tflops=r["flops"] / max(r["ms"], 1e-9) / 1e9 if r["flops"] else None)
         batch.timer(None)
         out["profile"] = prof
-    if args.fp64_compare and rank == 0:
-        # the plain FP64 GPU path on the same population: one timed step after one warm-up
-        ctx64 = [sgo.Context(st, precision="fp64", **_tols("fp64", st)) for st in pop]
+    if not args.no_fp64 and rank == 0:
+        # the plain FP64 GPU path on the same population, same algorithm, same stopping rule
+        # and the same eigenvector refinement (FP64 arithmetic throughout, CUDA-core GEMMs,
+        # FP64 eigensolve): one warm-up step, then timed steps through the same host-pointer
+        # call as e2e
+        ctx64 = [sgo.Context(st, precision="fp64", **_tols("mixed", st)) for st in pop]
         b64 = sgo.Batch(ctx64)
         b64.energy_forces()
         torch.cuda.synchronize()
+        k64 = max(1, min(args.steps, 2))
         t0 = time.perf_counter()
-        E64, _, st64 = b64.energy_forces()
+        for _ in range(k64):
+            E64, F64, st64 = b64.energy_forces(pos_host)
         torch.cuda.synchronize()
-        dt64 = time.perf_counter() - t0
+        dt64 = (time.perf_counter() - t0) / k64
         it64 = [c.info()["n_iter"] for c in ctx64]
-        out["fp64_path"] = dict(value=MEMBERS / dt64, unit="evals/s", steps=1,
+        nat = np.array([c.natoms for c in ctxs])
+        out["fp64_path"] = dict(value=MEMBERS / dt64, unit="evals/s", steps=k64,
+                                stopping_rule="the mixed path's (|dF| < 1e-7 Ha/atom, density residual < 1e-5)",
                                 converged=f"{int(np.sum(st64 == 0))}/{MEMBERS}",
                                 scf_iterations=dict(mean=float(np.mean(it64)), max=int(np.max(it64))),
                                 speedup_mixed_over_fp64=e2e_val / (MEMBERS / dt64),
-                                max_abs_dE_per_atom_mixed_vs_fp64=float(np.max(np.abs(E - E64) /
-                                                                               np.array([c.natoms for c in ctxs]))))
+                                max_abs_dE_per_atom_mixed_vs_fp64=float(np.max(np.abs(E - E64) / nat)),
+                                max_abs_dforce_mixed_vs_fp64=float(max(np.abs(a - b).max() for a, b in zip(F, F64))))
+        out["vs_fp64_gpu"] = out["fp64_path"]["speedup_mixed_over_fp64"]
         del b64, ctx64
     if rank == 0 and not args.no_warm:
         out["warm"] = _warm_steps(args, sgo, batch, ctxs, pop, pos_host, pos_dev, e_dev, f_dev, s_dev, stream)
@@ -460,6 +476,85 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def run_configs(args):
+    """Per-config measurement (the named workloads one structure at a time): for the
+    mixed and the plain FP64 GPU path, one cold energy + force evaluation timed after a
+    warm-up evaluation (graph-driven SCF loop), its SCF iterations and eigenvector
+    refinement, its errors against the stored oracle ledger where one exists
+    (tests/golden/ledger_<name>.json), and for the mixed path the live-timed plane pass,
+    tensor-core TN GEMM and subspace eigensolve of one more evaluation.  One JSON line."""
+    import torch
+    import paper_1603_02732_gb300 as sgo
+    from paper_1603_02732_gb300 import build
+    import workloads
+    build.build()
+    sgo.load_library()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    names = args.names.split(",") if args.names else ["diamond8", "honeycomb24", "cluster13", "cluster55"]
+    out = {}
+    for name in names:
+        st = workloads.CONFIGS[name]()
+        gold = os.path.join(ROOT, "tests", "golden", f"ledger_{name}.json")
+        ref = json.load(open(gold)) if os.path.exists(gold) else None
+        res = {}
+        for prec in ("mixed", "fp64"):
+            tol = _tols(prec, st) if name == "diamond8" and prec == "fp64" else _tols("mixed", st)
+            if name == "diamond8":
+                tol.update(mix_alpha=0.7, kerker_q0=0.0)
+            try:
+                ctx = sgo.Context(st, precision=prec, **tol)
+            except sgo.SgoError as e:
+                res[prec] = dict(unavailable=str(e))
+                continue
+            b = sgo.Batch([ctx])
+            b.energy_forces()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            z = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            E, F, stat = b.energy_forces()
+            z.record(stream)
+            z.synchronize()
+            ms = a.elapsed_time(z)
+            r = dict(evals_per_s=1e3 / ms, ms_per_eval=ms, status=int(stat[0]), **ctx.stats())
+            eig, occ = ctx.eigen()
+            if ref is not None:
+                oc = np.array(ref["occ"]) > 1e-6
+                r["errors_vs_oracle"] = dict(dF_per_atom=abs(E[0] - ref["free_energy"]) / st.natoms,
+                                             max_dforce=float(np.abs(F[0] - np.array(ref["forces"])).max()),
+                                             max_deig_occupied=float(np.abs(eig - np.array(ref["eig"]))[oc].max()))
+            r["_E"], r["_F"] = float(E[0]), F[0]
+            if prec == "mixed":
+                kern = {}
+                for kind in ("plane_vpsi", "gemm_tn", "gemm_nn", "rr"):
+                    b.timer(kind)
+                    a.record(stream)
+                    b.energy_forces()
+                    z.record(stream)
+                    z.synchronize()
+                    t = b.timer_read()
+                    kern[kind] = dict(ms=t["ms"], launches=t["launches"], share=t["ms"] / a.elapsed_time(z),
+                                      tflops=t["flops"] / max(t["ms"], 1e-9) / 1e9,
+                                      gbs=t["bytes"] / max(t["ms"], 1e-9) / 1e6)
+                b.timer(None)
+                kern["plane_vpsi"]["frac_fp32_peak"] = kern["plane_vpsi"]["tflops"] / FP32_PEAK_TFLOPS
+                r["kernels"] = kern
+            res[prec] = r
+            del b, ctx
+        if "_E" in res.get("mixed", {}) and "_E" in res.get("fp64", {}):
+            res["mixed_vs_fp64"] = dict(dF_per_atom=abs(res["mixed"]["_E"] - res["fp64"]["_E"]) / st.natoms,
+                                        max_dforce=float(np.abs(res["mixed"]["_F"] - res["fp64"]["_F"]).max()),
+                                        speedup=res["mixed"]["evals_per_s"] / res["fp64"]["evals_per_s"])
+        for prec in ("mixed", "fp64"):
+            res.get(prec, {}).pop("_E", None)
+            res.get(prec, {}).pop("_F", None)
+        out[name] = dict(natoms=st.natoms, nbands=st.nbands, grid=list(st.fft), **res)
+        print(json.dumps({name: out[name]}), flush=True)
+    print(json.dumps(dict(case="configs", results=out)), flush=True)
     return 0
 
 
@@ -494,7 +589,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--kernel", default="plane_vpsi", help="kernel class timed live for the roofline")
-    ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 GPU path")
+    ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start (relaxation step) measurement")
     ap.add_argument("--no-relax", action="store_true", help="skip the local-relaxation (PCG) measurement")
@@ -502,8 +597,10 @@ def main():
     ap.add_argument("--sub-batches", type=int, default=0,
                     help="sub-batches overlapped on the GPU in graph mode (0 = the library's choice)")
     ap.add_argument("--profile", action="store_true", help="one extra step per kernel class with live timers")
-    ap.add_argument("--case", default="batch", choices=["batch", "hpsi", "scf"],
-                    help="batch: the benchmark; hpsi / scf: one population member (small case for ncu)")
+    ap.add_argument("--case", default="batch", choices=["batch", "hpsi", "scf", "configs"],
+                    help="batch: the benchmark; hpsi / scf: one population member (small case for ncu); "
+                         "configs: the named workloads one at a time (mixed and FP64)")
+    ap.add_argument("--names", default=None, help="--case configs: comma-separated workload names")
     ap.add_argument("--member", type=int, default=0, help="population member for --case hpsi / scf")
     ap.add_argument("--ncg", type=int, default=None, help="CG steps per SCF iteration")
     ap.add_argument("--ncg-first", type=int, default=None)
@@ -514,6 +611,8 @@ def main():
             _SCF[k] = v
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "configs":
+        return run_configs(args)
     if args.case != "batch":
         return run_case(args)
     return run_ours(args)

@@ -183,6 +183,27 @@ bool smooth235(int n) {
   return n == 1;
 }
 
+}  // namespace
+
+// Which kernels take the plane passes of one structure: the mixed path's register line
+// FFTs (single thread per line up to 72, lane pairs 96-128) where their shared memory
+// fits, else the shared-memory plane engine (two whole planes per CTA), else line blocks
+// through a global buffer (big planes).  vpsi: the H.psi pass; dens: the density pass.
+PlanePaths plane_paths(const Prob& d, int precision) {
+  const size_t cap = 220 * 1024;
+  PlanePaths q;
+  q.preg = precision == 1 && plane_reg_ok(d.n1, d.n2) && plane_reg_smem(d.n1, d.n2, d.m1max) <= cap;
+  q.dreg = q.preg && plane_density_reg_smem(d.n1, d.n2, d.m1max) <= cap;
+  q.ppair = precision == 1 && !q.preg && pair_plane_ok(d.n1, d.n2) && pair_plane_smem(d.n1, d.n2, d.m1max) <= cap;
+  q.dpair = q.ppair && pair_density_smem(d.n1, d.n2, d.m1max) <= cap;
+  q.psmem = (size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 <= cap && d.n1 * d.n2 <= 8192;
+  q.pbig = !q.preg && !q.ppair && !q.psmem;
+  q.dbig = !q.dreg && !q.dpair && !q.psmem;
+  return q;
+}
+
+namespace {
+
 // counting arena pass + real pass
 template <class A>
 void layout(sgo_ctx* c, A& a) {
@@ -209,6 +230,8 @@ void layout(sgo_ctx* c, A& a) {
   d.B = a.template take<char>((size_t)na * ld * ts);
   d.dB = a.template take<char>((size_t)3 * na * ld * ts);
   d.Wc = a.template take<char>((size_t)d.npair * d.n3 * d.ncol * 2 * ts);
+  const PlanePaths pp = plane_paths(d, c->precision);
+  d.Gp = (pp.pbig || pp.dbig) ? a.template take<char>(big_plane_bytes(d.npair, d.n3, d.m1max, d.n2, ts)) : nullptr;
   d.veff = a.template take<char>((size_t)ng * ts);
   d.vion_r = a.template take<double>(ng);
   d.rho_in = a.template take<double>(ng);
@@ -358,14 +381,8 @@ sgo_status ctx_setup(sgo_ctx* c) {
   d.box1 = box[0];
   d.box2 = box[1];
   d.box3 = box[2];
-  // planes: the shared-memory engine holds two whole planes; the mixed path's register
-  // kernels hold only the occupied rows (their fit is checked with the engine's maps)
-  const bool plane_reg = c->precision == 1 && (plane_reg_ok(d.n1, d.n2) || pair_plane_ok(d.n1, d.n2));
-  if (((size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 > 220 * 1024 || d.n1 * d.n2 > 8192) && !plane_reg) {
-    set_error("FFT plane N1*N2 too large for the shared-memory plane kernels (max about 6900); the mixed "
-              "path takes lengths up to 128 with register transforms");
-    return SGO_ERR_ARG;
-  }
+  // planes of any size: register kernels, the shared-memory plane engine or line blocks
+  // through a global buffer (see plane_paths); the z lines stay in shared memory
   if ((size_t)(4 * QCP + 1) * d.n3 * 16 > 220 * 1024) {
     set_error("N3 too large");
     return SGO_ERR_ARG;
@@ -631,7 +648,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
       c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2], c_dreg[2], c_zreg[2], c_ppair,
-      c_dpair, c_zpair, c_gx, c_gy;
+      c_dpair, c_zpair, c_gx, c_gy, c_bigy, c_bigx, c_bigdy, c_bigd;
   size_t part = 0;
   int max_natom = 0;
   for (int p = 0; p < n_; ++p) {
@@ -661,20 +678,19 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     c_gy.push_back(gbig ? div_up(d.n3 * d.n1, QZ) : 0);
     // plane passes: register FFTs on the mixed path where both plane lengths have one
     // and the kernels' shared memory fits; the shared-memory engine otherwise
-    const size_t smem_cap = 220 * 1024;
-    const bool preg = precision_ == 1 && plane_reg_ok(d.n1, d.n2) && plane_reg_smem(d.n1, d.n2, d.m1max) <= smem_cap;
-    const bool dreg = preg && plane_density_reg_smem(d.n1, d.n2, d.m1max) <= smem_cap;
+    const PlanePaths pp = plane_paths(d, precision_);
+    const bool preg = pp.preg, dreg = pp.dreg, ppair = pp.ppair, dpair = pp.dpair;
     const int pcls = preg ? plane_reg_class(d.n1, d.n2) : -1;
-    const bool ppair = precision_ == 1 && !preg && pair_plane_ok(d.n1, d.n2) &&
-                       pair_plane_smem(d.n1, d.n2, d.m1max) <= smem_cap;
-    const bool dpair = ppair && pair_density_smem(d.n1, d.n2, d.m1max) <= smem_cap;
-    const bool psmem = (size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * 16 <= smem_cap && d.n1 * d.n2 <= 8192;
-    if ((!preg && !ppair && !psmem) || (!dreg && !dpair && !psmem)) {
-      set_error("FFT plane too large for the plane kernels of this precision");
+    if ((pp.pbig || pp.dbig) && !d.Gp) {
+      set_error("big-plane buffer missing (the context was built for another precision)");
       return;
     }
-    c_plane.push_back(preg || ppair ? 0 : d.npair * d.n3);
-    c_dens.push_back(dreg || dpair ? 0 : d.n3);
+    c_plane.push_back(preg || ppair || pp.pbig ? 0 : d.npair * d.n3);
+    c_dens.push_back(dreg || dpair || pp.dbig ? 0 : d.n3);
+    c_bigy.push_back(pp.pbig ? big_y_ctas(d.npair, d.n3, d.m1max) : 0);
+    c_bigx.push_back(pp.pbig ? big_x_ctas(d.npair, d.n3, d.n2) : 0);
+    c_bigdy.push_back(pp.dbig ? big_y_ctas(d.npair, d.n3, d.m1max) : 0);
+    c_bigd.push_back(pp.dbig ? big_density_ctas(d.n3, d.n2) : 0);
     c_ppair.push_back(ppair ? pair_plane_ctas(d.n2, d.n3, d.npair) : 0);
     c_dpair.push_back(dpair ? pair_density_ctas(d.n2, d.n3) : 0);
     if (ppair) ppair_smem_ = std::max(ppair_smem_, pair_plane_smem(d.n1, d.n2, d.m1max));
@@ -713,6 +729,10 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   m_zpair_ = make_map(c_zpair);
   m_gx_ = make_map(c_gx);
   m_gy_ = make_map(c_gy);
+  m_bigy_ = make_map(c_bigy);
+  m_bigx_ = make_map(c_bigx);
+  m_bigdy_ = make_map(c_bigdy);
+  m_bigd_ = make_map(c_bigd);
   m_dens_ = make_map(c_dens);
   m_gz_ = make_map(c_gz);
   m_gp_ = make_map(c_gp);
@@ -1030,6 +1050,9 @@ void Engine::hpsi(int src, int dst) {
   launch_plane_vpsi<T>(L(m_plane_));
   for (int k = 0; k < 2; ++k) launch_plane_vpsi_reg(L(m_preg_[k]), k, preg_smem_[k]);
   launch_plane_vpsi_pair(L(m_ppair_), ppair_smem_);
+  launch_big_y<T>(L(m_bigy_), 1, 0, nullptr);
+  launch_big_x<T>(L(m_bigx_));
+  launch_big_y<T>(L(m_bigy_), -1, 0, nullptr);
   tend(TK_PLANE_VPSI);
   tbeg(TK_COLS_TO_WAVE);
   cols_to_wave<T>(src, dst);
@@ -1138,6 +1161,8 @@ void Engine::density_energy(int mode) {
   launch_plane_density<T>(L(m_dens_), nullptr);
   for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], nullptr);
   launch_plane_density_pair(L(m_dpair_), dpair_smem_, nullptr);
+  launch_big_y<T>(L(m_bigdy_), 1, 1, nullptr);
+  launch_big_density<T>(L(m_bigd_), nullptr);
   tend(TK_PLANE_DENSITY);
   // energy at (Psi, rho_out) and the convergence test
   launch_band_kinetic<T>(L(m_bands_), WB_X);
@@ -1548,10 +1573,14 @@ sgo_status Engine::density(int nvec, const double* psi, const double* occ, doubl
     launch_plane_density<float>(L(m_dens_), docc);
     for (int k = 0; k < 2; ++k) launch_plane_density_reg(L(m_dreg_[k]), k, dreg_smem_[k], docc);
     launch_plane_density_pair(L(m_dpair_), dpair_smem_, docc);
+    launch_big_y<float>(L(m_bigdy_), 1, 1, docc);
+    launch_big_density<float>(L(m_bigd_), docc);
   } else {
     launch_copy_in<double>(L(m_bands_), WB_W, dpsi, nvec);
     wave_to_cols<double>(WB_W);
     launch_plane_density<double>(L(m_dens_), docc);
+    launch_big_y<double>(L(m_bigdy_), 1, 1, docc);
+    launch_big_density<double>(L(m_bigd_), docc);
   }
   launch_export_grid(L(m_gew_), 1, dr);
   CK(cudaMemcpyAsync(rho, dr, sizeof(double) * d.ngrid, cudaMemcpyDeviceToHost, stream_));

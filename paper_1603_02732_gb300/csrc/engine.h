@@ -174,6 +174,7 @@ class Engine {
   WorkMap m_ppair_, m_dpair_, m_zpair_;         // lane-pair register FFT kernels (lengths 96-128)
   size_t ppair_smem_ = 0, dpair_smem_ = 0, zpair_smem_ = 0;
   WorkMap m_gx_, m_gy_;                         // FP64 grid transforms of planes too large for one CTA
+  WorkMap m_bigy_, m_bigx_, m_bigdy_, m_bigd_;  // plane passes by line blocks (big planes)
   template <typename T> void wave_to_cols(int src);
   template <typename T> void cols_to_wave(int src, int dst);
   bool tc_ok_[3] = {false, false, false};      // TN on tcgen05, per A-operand kind
@@ -232,6 +233,12 @@ enum {
   TK_GRID_FFT, TK_CG_BAND, TK_GRID_OTHER, TK_GEMM_SMALL, TK_COUNT
 };
 extern const char* const kTimerNames[TK_COUNT];
+
+// Kernel choice of the plane passes of one structure (see plane_paths in engine.cu).
+struct PlanePaths {
+  bool preg = false, dreg = false, ppair = false, dpair = false, psmem = false, pbig = false, dbig = false;
+};
+PlanePaths plane_paths(const Prob& d, int precision);
 
 // Context set-up (basis on the device, allocation, tables).  Returns status.
 sgo_status ctx_setup(sgo_ctx* c);

@@ -382,8 +382,182 @@ __global__ void __launch_bounds__(ZCOL_THREADS) k_grid_line_fft(KArgs ka, int wh
 }
 
 // ---------------------------------------------------------------------------
+// Plane pass by line blocks through a global buffer, for planes whose two copies do not
+// fit in one CTA's shared memory (the FP64 path beyond about 6900 points per plane).
+// Gp[pair][z][r][i2] holds the occupied x rows of each band pair's plane between its y
+// and x transforms: r = i1 for i1 <= m1max, r = i1 - (n1 - 2 m1max - 1) for the rows
+// i1 >= n1 - m1max (|m1| <= m1max); the other rows are zero and never stored.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int big_row_i1(const Prob& P, int r) {
+  return r <= P.m1max ? r : r + P.n1 - 2 * P.m1max - 1;
+}
+__device__ __forceinline__ int big_row_of(const Prob& P, int i1) {
+  if (i1 <= P.m1max) return i1;
+  if (i1 >= P.n1 - P.m1max) return i1 - (P.n1 - 2 * P.m1max - 1);
+  return -1;
+}
+
+// dir +1: compact columns of (pair, z) -> inverse y FFT -> rows of Gp; dir -1: rows of Gp
+// -> forward y FFT -> compact columns.  CTA = (problem, pair, z, block of QZ rows).
+// skip_empty: pairs whose two occupations are zero are skipped (density pass).
+template <typename T>
+__global__ void __launch_bounds__(ZCOL_THREADS) k_big_y(KArgs ka, int dir, int skip_empty, const double* occ_override) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int nrows = 2 * P.m1max + 1, nrb = (nrows + QZ - 1) / QZ;
+  const int local = blockIdx.x - ka.start[p];
+  const int rb = local % nrb, pz = local / nrb;
+  const int z = pz % P.n3, pair = pz / P.n3;
+  if (skip_empty) {
+    const double* occ = occ_override ? occ_override : P.occ;
+    const double fa = occ[2 * pair], fb = (2 * pair + 1 < P.nb) ? occ[2 * pair + 1] : 0.0;
+    if (fa == 0.0 && fb == 0.0) return;
+  }
+  const int n = P.n2, r0 = rb * QZ, nc = min(QZ, nrows - r0);
+  cplx<T>* lines = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* alt = lines + QZ * n;
+  cplx<T>* roots = alt + QZ * n;
+  load_roots<T>(roots, P, P.n1, n);
+  cplx<T>* wcz = reinterpret_cast<cplx<T>*>(P.Wc) + ((size_t)pair * P.n3 + z) * P.ncol;
+  cplx<T>* gp = reinterpret_cast<cplx<T>*>(P.Gp) + ((size_t)pair * P.n3 + z) * nrows * n;
+  for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
+    const int c = t / n, e = t - c * n;
+    if (dir > 0) {
+      const int col = P.colmap[big_row_i1(P, r0 + c) * n + e];
+      lines[t] = col >= 0 ? wcz[col] : mk(T(0), T(0));
+    } else {
+      lines[t] = gp[(size_t)(r0 + c) * n + e];
+    }
+  }
+  __syncthreads();
+  const cplx<T>* res = fft_lines<T>(lines, alt, nc, n, 1, contiguous(nc), P.fd[1], roots, dir > 0 ? T(1) : T(-1));
+  for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
+    const int c = t / n, e = t - c * n;
+    if (dir > 0) {
+      gp[(size_t)(r0 + c) * n + e] = res[t];
+    } else {
+      const int col = P.colmap[big_row_i1(P, r0 + c) * n + e];
+      if (col >= 0) wcz[col] = res[t];
+    }
+  }
+}
+
+// x lines of (pair, z): inverse x FFT (the unstored rows read as zero), times V_eff/N,
+// forward x FFT, occupied rows back to Gp.  CTA = (problem, pair, z, block of QZ columns
+// i2); loads and stores coalesced across the block's columns.
+template <typename T>
+__global__ void __launch_bounds__(ZCOL_THREADS) k_big_x(KArgs ka) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int n1 = P.n1, n2 = P.n2, nrows = 2 * P.m1max + 1, ncb = (n2 + QZ - 1) / QZ;
+  const int local = blockIdx.x - ka.start[p];
+  const int cb = local % ncb, pz = local / ncb;
+  const int z = pz % P.n3, pair = pz / P.n3;
+  const int c0 = cb * QZ, nc = min(QZ, n2 - c0);
+  cplx<T>* lines = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* alt = lines + QZ * n1;
+  cplx<T>* roots = alt + QZ * n1;
+  load_roots<T>(roots, P, 0, n1);
+  cplx<T>* gp = reinterpret_cast<cplx<T>*>(P.Gp) + ((size_t)pair * P.n3 + z) * nrows * n2;
+  for (int t = threadIdx.x; t < nc * n1; t += blockDim.x) {
+    const int e = t / nc, c = t - e * nc;
+    const int r = big_row_of(P, e);
+    lines[c * n1 + e] = r >= 0 ? gp[(size_t)r * n2 + c0 + c] : mk(T(0), T(0));
+  }
+  __syncthreads();
+  cplx<T>* cur = fft_lines<T>(lines, alt, nc, n1, 1, contiguous(nc), P.fd[0], roots, T(1));
+  const T* v = reinterpret_cast<const T*>(P.veff) + (size_t)z * n1 * n2;
+  for (int t = threadIdx.x; t < nc * n1; t += blockDim.x) {
+    const int e = t / nc, c = t - e * nc;
+    cur[c * n1 + e] = scale(cur[c * n1 + e], v[(size_t)e * n2 + c0 + c]);
+  }
+  __syncthreads();
+  cur = fft_lines<T>(cur, cur == lines ? alt : lines, nc, n1, 1, contiguous(nc), P.fd[0], roots, T(-1));
+  for (int t = threadIdx.x; t < nc * n1; t += blockDim.x) {
+    const int e = t / nc, c = t - e * nc;
+    const int r = big_row_of(P, e);
+    if (r >= 0) gp[(size_t)r * n2 + c0 + c] = cur[c * n1 + e];
+  }
+}
+
+// Density of the big-plane path: per (problem, z, block of QZ columns i2), every band pair's
+// x lines (after k_big_y) transformed to real space and f_a Re^2 + f_b Im^2 accumulated in
+// FP64 over the pairs in order; rho_out = sum / Omega.
+template <typename T>
+__global__ void __launch_bounds__(ZCOL_THREADS) k_big_density(KArgs ka, const double* occ_override) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int n1 = P.n1, n2 = P.n2, nrows = 2 * P.m1max + 1, ncb = (n2 + QZ - 1) / QZ;
+  const int local = blockIdx.x - ka.start[p];
+  const int cb = local % ncb, z = local / ncb;
+  const int c0 = cb * QZ, nc = min(QZ, n2 - c0);
+  cplx<T>* lines = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* alt = lines + QZ * n1;
+  cplx<T>* roots = alt + QZ * n1;
+  double* acc = reinterpret_cast<double*>(roots + n1);
+  load_roots<T>(roots, P, 0, n1);
+  for (int t = threadIdx.x; t < nc * n1; t += blockDim.x) acc[t] = 0.0;
+  const double* occ = occ_override ? occ_override : P.occ;
+  for (int pair = 0; pair < P.npair; ++pair) {
+    const double fa = occ[2 * pair], fb = (2 * pair + 1 < P.nb) ? occ[2 * pair + 1] : 0.0;
+    if (fa == 0.0 && fb == 0.0) continue;  // uniform across the block
+    const cplx<T>* gp = reinterpret_cast<const cplx<T>*>(P.Gp) + ((size_t)pair * P.n3 + z) * nrows * n2;
+    __syncthreads();
+    for (int t = threadIdx.x; t < nc * n1; t += blockDim.x) {
+      const int e = t / nc, c = t - e * nc;
+      const int r = big_row_of(P, e);
+      lines[c * n1 + e] = r >= 0 ? gp[(size_t)r * n2 + c0 + c] : mk(T(0), T(0));
+    }
+    __syncthreads();
+    const cplx<T>* cur = fft_lines<T>(lines, alt, nc, n1, 1, contiguous(nc), P.fd[0], roots, T(1));
+    for (int t = threadIdx.x; t < nc * n1; t += blockDim.x) {
+      const cplx<T> v = cur[t];
+      acc[t] += fa * (double)v.x * (double)v.x + fb * (double)v.y * (double)v.y;
+    }
+  }
+  __syncthreads();
+  const double io = 1.0 / P.omega;
+  double* rho = P.rho_out + (size_t)z * n1 * n2;
+  for (int t = threadIdx.x; t < nc * n1; t += blockDim.x) {
+    const int e = t / nc, c = t - e * nc;
+    rho[(size_t)e * n2 + c0 + c] = acc[c * n1 + e] * io;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+int big_y_ctas(int npair, int n3, int m1max) { return npair * n3 * ((2 * m1max + 1 + QZ - 1) / QZ); }
+int big_x_ctas(int npair, int n3, int n2) { return npair * n3 * ((n2 + QZ - 1) / QZ); }
+int big_density_ctas(int n3, int n2) { return n3 * ((n2 + QZ - 1) / QZ); }
+size_t big_plane_bytes(int npair, int n3, int m1max, int n2, size_t tsize) {
+  return (size_t)npair * n3 * (2 * m1max + 1) * n2 * 2 * tsize;
+}
+template <typename T>
+void launch_big_y(const Launch& L, int dir, int skip_empty, const double* occ_override) {
+  if (!L.map.total) return;
+  size_t sm = (size_t)(2 * QZ + 1) * L.max_n2 * sizeof(cplx<T>);
+  k_big_y<T><<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, dir, skip_empty, occ_override);
+}
+template <typename T>
+void launch_big_x(const Launch& L) {
+  if (!L.map.total) return;
+  size_t sm = (size_t)(2 * QZ + 1) * L.max_n1 * sizeof(cplx<T>);
+  k_big_x<T><<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka);
+}
+template <typename T>
+void launch_big_density(const Launch& L, const double* occ_override) {
+  if (!L.map.total) return;
+  size_t sm = (size_t)(2 * QZ + 1) * L.max_n1 * sizeof(cplx<T>) + (size_t)QZ * L.max_n1 * sizeof(double);
+  k_big_density<T><<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, occ_override);
+}
+
 template <typename T>
 void launch_wave_to_cols(const Launch& L, int src) {
   if (!L.map.total) return;
@@ -448,6 +622,12 @@ void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_grid_plane_fft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_z_fft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_grid_line_fft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_big_y<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_big_y<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_big_x<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_big_x<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_big_density<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(k_big_density<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   plane_vpsi_reg_set_smem_limits(bytes);
   plane_density_reg_set_smem_limits(bytes);
   zreg_set_smem_limits(bytes);
@@ -471,5 +651,11 @@ template void launch_plane_vpsi<float>(const Launch&);
 template void launch_plane_vpsi<double>(const Launch&);
 template void launch_plane_density<float>(const Launch&, const double*);
 template void launch_plane_density<double>(const Launch&, const double*);
+template void launch_big_y<float>(const Launch&, int, int, const double*);
+template void launch_big_y<double>(const Launch&, int, int, const double*);
+template void launch_big_x<float>(const Launch&);
+template void launch_big_x<double>(const Launch&);
+template void launch_big_density<float>(const Launch&, const double*);
+template void launch_big_density<double>(const Launch&, const double*);
 
 }  // namespace sgo

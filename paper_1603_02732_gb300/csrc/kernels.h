@@ -62,6 +62,14 @@ template <typename T> void launch_grid_plane_fft(const Launch& L, int which, int
 template <typename T> void launch_grid_z_fft(const Launch& L, int which, int sign);
 template <typename T> void launch_grid_line_fft(const Launch& L, int which, int sign, int axis);  // axis 0: x, 1: y
 void fft_set_smem_limits(size_t bytes);
+// plane pass by line blocks through a global buffer (planes too large for one CTA)
+int big_y_ctas(int npair, int n3, int m1max);
+int big_x_ctas(int npair, int n3, int n2);
+int big_density_ctas(int n3, int n2);
+size_t big_plane_bytes(int npair, int n3, int m1max, int n2, size_t tsize);
+template <typename T> void launch_big_y(const Launch& L, int dir, int skip_empty, const double* occ_override);
+template <typename T> void launch_big_x(const Launch& L);
+template <typename T> void launch_big_density(const Launch& L, const double* occ_override);
 // register-FFT plane pass (mixed path): lengths n1, n2 with a register transform
 bool plane_reg_ok(int n1, int n2);
 int plane_reg_class(int n1, int n2);          // 0: both <= 40, 1: up to PLANE_REG_MAXN

@@ -92,6 +92,11 @@ sgo_status run(sgo_ctx* c, const double* veff, int nvec, const double* psi, doub
   off = align256(off + sizeof(double) * (size_t)nvec * d.npw);
   const size_t o_out = off;
   off = align256(off + sizeof(double) * (size_t)nvec * d.npw);
+  // this path runs the shared-memory plane engine only (two whole planes per CTA)
+  if ((size_t)(2 * d.n1 * d.n2 + d.n1 + d.n2) * sizeof(cplx<T>) > 220 * 1024) {
+    set_error("FFT planes too large for the no-alloc path (two whole planes per CTA in shared memory)");
+    return SGO_ERR_ARG;
+  }
   if (off > kNoAllocScratchBytes) {
     set_error("problem too large for the no-alloc scratch: needs " + std::to_string(off) + " bytes, limit " +
               std::to_string(kNoAllocScratchBytes));

@@ -166,6 +166,8 @@ struct Prob {
   void* B;                     // [natom][ld] projectors
   void* dB;                    // [3*natom][ld] projector derivatives (forces)
   void* Wc;                    // complex [npair][n3][ncol]
+  void* Gp;                    // complex [npair][n3][2 m1max + 1][n2]: occupied x rows of the
+                               // planes (big-plane path only, else null)
   void* veff;                  // real [ngrid] (engine precision)
   // FP64 grids
   double* vion_r;              // [ngrid]

@@ -40,20 +40,14 @@ def _struct(grid=None, ecut=3.5, nat=2, seed=7, kT=0.01, nbands=None):
 # register plane transforms in both size classes: 45 40, 60 50, 72 64, 27 25, 20 48
 GRIDS = [None, (10, 12, 15), (16, 18, 20), (24, 24, 24), (30, 54, 40), (18, 36, 128), (45, 40, 16),
          (60, 50, 12), (72, 64, 10), (27, 25, 32), (20, 48, 15),
-         # lane-pair register transforms (mixed path): planes 96 x 128 and 100 x 108, z 96 / 120
+         # lane-pair register transforms (mixed path): planes 96 x 128 and 100 x 108, z 96 / 120;
+         # the FP64 path takes these two planes by line blocks through a global buffer
          (96, 128, 12), (100, 108, 10), (20, 24, 96), (12, 10, 120)]
-
-
-def _fp64_takes(grid):
-    # the FP64 path's shared-memory plane kernels hold two whole planes
-    return grid is None or (2 * grid[0] * grid[1] + grid[0] + grid[1]) * 16 <= 220 * 1024 and grid[0] * grid[1] <= 8192
 
 
 @pytest.mark.parametrize("grid", GRIDS)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_apply_hamiltonian_matches_dense_h(sgo, grid, precision):
-    if precision == "fp64" and not _fp64_takes(grid):
-        pytest.skip("plane too large for the FP64 path")
     st = _struct(grid=grid)
     ctx = sgo.Context(st, precision=precision)
     m = dft.Model(st)
@@ -78,8 +72,6 @@ def test_apply_hamiltonian_matches_dense_h(sgo, grid, precision):
 @pytest.mark.parametrize("grid", [None, (10, 12, 15), (18, 20, 24), (30, 54, 40), (96, 128, 12), (20, 24, 96)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_density_matches_oracle(sgo, grid, precision):
-    if precision == "fp64" and not _fp64_takes(grid):
-        pytest.skip("plane too large for the FP64 path")
     st = _struct(grid=grid, nbands=7)
     ctx = sgo.Context(st, precision=precision)
     m = dft.Model(st)
@@ -117,6 +109,20 @@ def test_scf_tiny_fp64(sgo, kT, nbands):
     for k_gpu, k_ref in [("kinetic", "kinetic"), ("nonlocal", "nonlocal_"), ("local", "local"),
                          ("hartree", "hartree"), ("xc", "xc"), ("ewald", "ewald"), ("minus_ts", "minus_ts")]:
         assert abs(t[k_gpu] - ref.terms[k_ref]) < 1e-6, k_gpu
+    rho = ctx.density()
+    assert np.abs(rho - ref.rho).max() < 1e-6 * np.abs(ref.rho).max()
+
+
+def test_scf_big_plane_fp64(sgo):
+    """FP64 SCF, energy terms, density and forces on a 96 x 128 x 12 grid, whose planes the
+    FP64 path takes by line blocks through a global buffer (H.psi, density and the grid
+    transforms), against the oracle."""
+    st = _struct(ecut=3.0, grid=(96, 128, 12))
+    ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)
+    ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=120)
+    _compare(st, ctx.energy_forces(), ref, 1e-8, 1e-6)
+    eig, _ = ctx.eigen()
+    assert np.abs(eig - ref.eig)[ref.occ > 1e-6].max() < 1e-7
     rho = ctx.density()
     assert np.abs(rho - ref.rho).max() < 1e-6 * np.abs(ref.rho).max()
 
@@ -347,8 +353,6 @@ def test_grid_fft_matches_fp64_fft(sgo, grid, precision):
     FFT) against numpy's FP64 FFT, both signs: FP64 on the plain path, float-float
     arithmetic on the mixed path, so both stay within 1e-12 of the largest output (an FP32
     transform would sit near 1e-7).  (100, 108) planes take the line-block kernels."""
-    if precision == "fp64" and not _fp64_takes(grid):
-        pytest.skip("plane too large for the FP64 path")
     ctx = sgo.Context(_struct(grid=grid, ecut=3.0), precision=precision)
     rng = np.random.default_rng(5)
     x = rng.normal(size=grid) + 1j * rng.normal(size=grid)

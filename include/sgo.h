@@ -113,6 +113,11 @@ typedef struct {
   double watchdog_ms;     /* bound on every device wait of the tensor-core kernels (ms); on expiry
                              the member reports SGO_ERR_TIMEOUT and the context stays usable;
                              0 = 2000 ms.  Taken from the first member of a batch. */
+  int extra_bands;        /* empty bands the eigensolver carries above the nbands requested ones:
+                             the all-band CG converges the top bands of its block slowest, so the
+                             requested bands get headroom; occupations, eigenvalues, energies and
+                             the eig_tol test cover the requested bands only (-1, default:
+                             4 + nbands / 32; 0 = none) */
 } sgo_opts;
 
 /* Fill *o with the defaults (FP64, kT 0, tolerances 1e-8 Ha / 1e-7, Pulay 8, ...). */

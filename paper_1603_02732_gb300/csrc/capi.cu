@@ -47,7 +47,7 @@ std::vector<std::vector<int>> split_members(const std::vector<sgo_ctx*>& ctxs, i
   const int n = (int)ctxs.size();
   std::vector<double> cost(n);
   for (int i = 0; i < n; ++i) {
-    const double ng = (double)ctxs[i]->d.ngrid, nb = ctxs[i]->nb;
+    const double ng = (double)ctxs[i]->d.ngrid, nb = ctxs[i]->d.nb;
     cost[i] = nb * (ng * std::log2(std::max(2.0, ng)) + nb * (double)ctxs[i]->d.npw);
   }
   std::vector<int> order(n);
@@ -108,6 +108,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->max_polish = 40;
   o->rr_fp64 = 0;
   o->watchdog_ms = 0.0;
+  o->extra_bands = -1;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,
@@ -153,6 +154,7 @@ sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp,
     sgo::set_error("too few bands for the electrons (or odd electron count with integer occupations)");
     return SGO_ERR_ARG;
   }
+  c->nb_int = nbands + (c->opts.extra_bands < 0 ? 4 + nbands / 32 : c->opts.extra_bands);
   if (c->opts.max_scf < 1 || c->opts.pulay_hist < 1 || c->opts.ncg < 1 || !(c->opts.eig_tol >= 0.0) ||
       c->opts.max_polish < 0 || !(c->opts.watchdog_ms >= 0.0)) {
     delete c;
@@ -445,7 +447,7 @@ sgo_status sgo_get_info(sgo_ctx* c, int info[10]) {
   info[3] = c->d.n1;
   info[4] = c->d.n2;
   info[5] = c->d.n3;
-  info[6] = c->d.nb;
+  info[6] = c->nb;
   info[7] = c->d.natom;
   info[8] = c->last_iter;
   info[9] = c->precision;
@@ -478,7 +480,7 @@ sgo_status sgo_get_state(sgo_ctx* c, double* rho_g, double* psi) {
 
 sgo_status sgo_set_state(sgo_ctx* c, const double* rho_g, const double* psi) {
   if (!c || !rho_g || !psi) return SGO_ERR_ARG;
-  const size_t ng = (size_t)c->d.ngrid, np = (size_t)c->d.nb * c->d.npw;
+  const size_t ng = (size_t)c->d.ngrid, np = (size_t)c->nb * c->d.npw;
   for (size_t i = 0; i < 2 * ng; ++i)
     if (!std::isfinite(rho_g[i])) {
       sgo::set_error("non-finite density in the imported state");

@@ -398,8 +398,9 @@ sgo_status ctx_setup(sgo_ctx* c) {
   for (int a = 0; a < d.natom; ++a) d.nel += c->species[c->spec[a]].z_val;
   d.kT = c->opts.kT;
   for (int i = 0; i < NWB; ++i) d.role[i] = i;
-  d.nb = c->nb;
-  d.npair = (c->nb + 1) / 2;
+  d.nb = c->nb_int;
+  d.nbo = c->nb;
+  d.npair = (d.nb + 1) / 2;
   // Ewald parameters: eta from the volume; sums to a relative tail of 1e-16
   d.ew_eta = 3.0 / std::cbrt(d.omega);
   d.ew_rmax = 5.9 / d.ew_eta;
@@ -470,6 +471,11 @@ sgo_status ctx_setup(sgo_ctx* c) {
     set_error("more bands than plane waves");
     return SGO_ERR_ARG;
   }
+  if (c->nb_int > d.npw) {  // the headroom bands are capped by the basis
+    c->nb_int = d.npw;
+    d.nb = d.npw;
+    d.npair = (d.nb + 1) / 2;
+  }
 
   // ---- phase 2: allocation ----
   Counter cnt;
@@ -507,8 +513,8 @@ sgo_status ctx_setup(sgo_ctx* c) {
   cudaFree(dstart);
   cudaFree(dact);
   c->h_scal.assign(NSCAL_ALL, 0.0);
-  c->h_eps.assign(c->nb, 0.0);
-  c->h_occ.assign(c->nb, 0.0);
+  c->h_eps.assign(d.nb, 0.0);
+  c->h_occ.assign(d.nb, 0.0);
   c->h_forces.assign(3 * d.natom, 0.0);
   return SGO_OK;
 }
@@ -795,7 +801,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     hp_off_.resize(n_);
     for (int p = 0; p < n_; ++p) {
       hp_off_[p] = nd;
-      nd += NSCAL_ALL + 2 * (size_t)ctxs[p]->nb + ctxs[p]->h_forces.size();
+      nd += NSCAL_ALL + 2 * (size_t)ctxs[p]->d.nb + ctxs[p]->h_forces.size();
     }
     if (!cuda_ok(cudaMallocHost(&hp_, sizeof(double) * nd), "cudaMallocHost(read-back)")) return;
     std::memset(hp_, 0, sizeof(double) * nd);
@@ -1415,10 +1421,10 @@ sgo_status Engine::launch_t(bool want_forces) {
     double* h = hp_ + hp_off_[p];
     CK(cudaMemcpyAsync(h, c->d.scal, sizeof(double) * NSCAL_ALL, cudaMemcpyDeviceToHost, stream_));
     h += NSCAL_ALL;
-    CK(cudaMemcpyAsync(h, c->d.eps, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
-    h += c->nb;
-    CK(cudaMemcpyAsync(h, c->d.occ, sizeof(double) * c->nb, cudaMemcpyDeviceToHost, stream_));
-    h += c->nb;
+    CK(cudaMemcpyAsync(h, c->d.eps, sizeof(double) * c->d.nb, cudaMemcpyDeviceToHost, stream_));
+    h += c->d.nb;
+    CK(cudaMemcpyAsync(h, c->d.occ, sizeof(double) * c->d.nb, cudaMemcpyDeviceToHost, stream_));
+    h += c->d.nb;
     CK(cudaMemcpyAsync(h, c->d.forces, sizeof(double) * c->h_forces.size(), cudaMemcpyDeviceToHost, stream_));
     CK(cudaMemcpyAsync(hpi_ + 2 + 4 * p, c->d.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream_));
   }
@@ -1482,10 +1488,10 @@ sgo_status Engine::finish(std::vector<sgo_status>* per_item) {
     const double* h = hp_ + hp_off_[p];
     std::memcpy(c->h_scal.data(), h, sizeof(double) * NSCAL_ALL);
     h += NSCAL_ALL;
-    std::memcpy(c->h_eps.data(), h, sizeof(double) * c->nb);
-    h += c->nb;
-    std::memcpy(c->h_occ.data(), h, sizeof(double) * c->nb);
-    h += c->nb;
+    std::memcpy(c->h_eps.data(), h, sizeof(double) * c->d.nb);
+    h += c->d.nb;
+    std::memcpy(c->h_occ.data(), h, sizeof(double) * c->d.nb);
+    h += c->d.nb;
     std::memcpy(c->h_forces.data(), h, sizeof(double) * c->h_forces.size());
     std::memcpy(c->h_status, hpi_ + 2 + 4 * p, sizeof(int) * 4);
     c->have_state = true;
@@ -1671,7 +1677,7 @@ sgo_status Engine::export_density(double* rho) {
 
 sgo_status Engine::export_state(double* rho_g, double* psi) {
   const Prob& d = ctx_[0]->d;
-  const size_t gbytes = sizeof(double2) * (size_t)d.ngrid, pbytes = sizeof(double) * (size_t)d.nb * d.npw;
+  const size_t gbytes = sizeof(double2) * (size_t)d.ngrid, pbytes = sizeof(double) * (size_t)d.nbo * d.npw;
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   char* dbuf = nullptr;
@@ -1684,8 +1690,8 @@ sgo_status Engine::export_state(double* rho_g, double* psi) {
     CK(cudaMemcpyAsync(rho_g, dg, gbytes, cudaMemcpyDeviceToHost, stream_));
   }
   if (psi) {
-    if (precision_) launch_copy_out<float>(L(m_bands_), WB_X, dp, d.nb);
-    else launch_copy_out<double>(L(m_bands_), WB_X, dp, d.nb);
+    if (precision_) launch_copy_out<float>(L(m_bands_), WB_X, dp, d.nbo);
+    else launch_copy_out<double>(L(m_bands_), WB_X, dp, d.nbo);
     CK(cudaMemcpyAsync(psi, dp, pbytes, cudaMemcpyDeviceToHost, stream_));
   }
   CK(cudaStreamSynchronize(stream_));
@@ -1695,7 +1701,7 @@ sgo_status Engine::export_state(double* rho_g, double* psi) {
 
 sgo_status Engine::import_state(const double* rho_g, const double* psi) {
   const Prob& d = ctx_[0]->d;
-  const size_t gbytes = sizeof(double2) * (size_t)d.ngrid, pbytes = sizeof(double) * (size_t)d.nb * d.npw;
+  const size_t gbytes = sizeof(double2) * (size_t)d.ngrid, pbytes = sizeof(double) * (size_t)d.nbo * d.npw;
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   char* dbuf = nullptr;
@@ -1706,8 +1712,15 @@ sgo_status Engine::import_state(const double* rho_g, const double* psi) {
   CK(cudaMemcpyAsync(dp, psi, pbytes, cudaMemcpyHostToDevice, stream_));
   launch_grid_copy_c(L(m_gew_), dg, nullptr);
   CK(cudaMemcpyAsync(d.rhog_in, d.gfft, gbytes, cudaMemcpyDeviceToDevice, stream_));
-  if (precision_) launch_copy_in<float>(L(m_bands_), WB_X, dp, d.nb);
-  else launch_copy_in<double>(L(m_bands_), WB_X, dp, d.nb);
+  // the requested bands from the caller; the headroom bands above them start random
+  const unsigned long long seed = ctx_[0]->opts.seed;
+  if (precision_) {
+    launch_random_init<float>(L(m_bands_), WB_X, seed);
+    launch_copy_in<float>(L(m_bands_), WB_X, dp, d.nbo, true);
+  } else {
+    launch_random_init<double>(L(m_bands_), WB_X, seed);
+    launch_copy_in<double>(L(m_bands_), WB_X, dp, d.nbo, true);
+  }
   CK(cudaStreamSynchronize(stream_));
   cudaFree(dbuf);
   return cuda_ok(cudaGetLastError(), "import state") ? SGO_OK : SGO_ERR_CUDA;

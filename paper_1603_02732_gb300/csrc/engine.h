@@ -34,7 +34,8 @@ struct sgo_ctx {
   std::vector<int> spec;
   std::vector<double> pos;
   double ecut = 0.0;
-  int nb = 0;
+  int nb = 0;         // requested bands (occupied and reported)
+  int nb_int = 0;     // bands the eigensolver carries: nb plus empty headroom (sgo_opts.extra_bands)
   sgo_opts opts;
   cudaStream_t stream = nullptr;
   int device = -1;    // the CUDA device current at sgo_create (owns every buffer)

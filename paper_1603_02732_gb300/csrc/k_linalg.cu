@@ -500,10 +500,11 @@ __global__ void k_random_init(KArgs ka, int xr, unsigned long long seed) {
 
 // Host <-> packed buffers (rows of npw doubles) for the component entry points.
 template <typename T>
-__global__ void k_copy_in(KArgs ka, int role, const double* src, int nvec) {
+__global__ void k_copy_in(KArgs ka, int role, const double* src, int nvec, int keep_tail) {
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   const Prob& P = ka.probs[p];
   const int i = blockIdx.x - ka.start[p];
+  if (keep_tail && i >= nvec) return;  // rows beyond nvec keep their contents
   T* x = wbuf<T>(P, role) + (size_t)i * P.ld;
   for (int k = threadIdx.x; k < P.ld; k += blockDim.x)
     x[k] = (i < nvec && k < P.npw) ? (T)src[(size_t)i * P.npw + k] : T(0);
@@ -942,9 +943,12 @@ __global__ void k_occupations(KArgs ka) {
   const int p = blockIdx.x;
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
-  const int n = P.nb, lane = threadIdx.x;
+  // occupations over the nbo requested bands; the eigensolver's extra bands above them
+  // stay empty
+  const int n = P.nbo, lane = threadIdx.x;
   const double kT = P.kT, nel = P.nel;
   const double* eps = P.eps;
+  for (int i = n + lane; i < P.nb; i += 32) P.occ[i] = 0.0;
   if (kT <= 0.0) {
     const int nocc = (int)llround(nel * 0.5);
     for (int i = lane; i < n; i += 32) P.occ[i] = i < nocc ? 2.0 : 0.0;
@@ -1046,9 +1050,9 @@ void launch_random_init(const Launch& L, int xrole, unsigned long long seed) {
   k_random_init<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, xrole, seed);
 }
 template <typename T>
-void launch_copy_in(const Launch& L, int role, const double* src, int nvec) {
+void launch_copy_in(const Launch& L, int role, const double* src, int nvec, bool keep_tail) {
   if (!L.map.total) return;
-  k_copy_in<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, role, src, nvec);
+  k_copy_in<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, role, src, nvec, keep_tail ? 1 : 0);
 }
 template <typename T>
 void launch_copy_out(const Launch& L, int role, double* dst, int nvec) {
@@ -1080,7 +1084,7 @@ void linalg_set_smem_limits(size_t bytes) {
   template void launch_normalize<T>(const Launch&, int, int);                                   \
   template void launch_line_min<T>(const Launch&, int, int, int, int);                          \
   template void launch_random_init<T>(const Launch&, int, unsigned long long);                  \
-  template void launch_copy_in<T>(const Launch&, int, const double*, int);                      \
+  template void launch_copy_in<T>(const Launch&, int, const double*, int, bool);                \
   template void launch_copy_out<T>(const Launch&, int, double*, int);
 INST(float)
 INST(double)

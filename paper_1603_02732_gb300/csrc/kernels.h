@@ -137,7 +137,8 @@ template <typename T> void launch_cg_precond(const Launch& L, int x, int hx, int
 template <typename T> void launch_normalize(const Launch& L, int p, int pp);
 template <typename T> void launch_line_min(const Launch& L, int x, int hx, int p, int hp);
 template <typename T> void launch_random_init(const Launch& L, int xrole, unsigned long long seed);
-template <typename T> void launch_copy_in(const Launch& L, int role, const double* src, int nvec);
+// rows >= nvec: zero, or (keep_tail) left as they are
+template <typename T> void launch_copy_in(const Launch& L, int role, const double* src, int nvec, bool keep_tail = false);
 template <typename T> void launch_copy_out(const Launch& L, int role, double* dst, int nvec);
 // subspace diagonalisation; max_sweeps caps the Jacobi sweeps (a stop at the cap is counted
 // in SC_RRCAP)

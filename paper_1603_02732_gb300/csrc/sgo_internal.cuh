@@ -158,8 +158,9 @@ struct Prob {
   int* spec;                   // [natom]
   double sp[MAX_SPECIES * 6];  // z, rc, a, sigma, rp, d
   double nel, kT;
-  // bands
-  int nb, npair;
+  // bands: nb carried by the eigensolver, of which the lowest nbo (the requested count) are
+  // occupied and reported; the nb - nbo above them give the block convergence headroom
+  int nb, nbo, npair;
   // wave buffers (element type = engine precision)
   void* wb[NWB];               // each [nb][ld], physical buffers
   int role[NWB];               // role -> physical buffer of this problem (swapped on the device)

@@ -35,13 +35,16 @@ __global__ void k_set_scal(KArgs ka, int idx, double v, int only_active) {
   if (threadIdx.x == 0) ka.probs[p].scal[idx] = v;
 }
 // swap two buffer roles of every active problem
-__global__ void k_swap_roles(KArgs ka, int a, int b) {
+__global__ void k_swap_roles(KArgs ka, RolePairs rp) {
   const int p = blockIdx.x;
   if (!ka.active[p] || threadIdx.x != 0) return;
   Prob* P = const_cast<Prob*>(ka.probs) + p;
-  int t = P->role[a];
-  P->role[a] = P->role[b];
-  P->role[b] = t;
+  for (int k = 0; k < rp.n; ++k) {
+    const int a = rp.a[k], b = rp.y[k];
+    const int t = P->role[a];
+    P->role[a] = P->role[b];
+    P->role[b] = t;
+  }
 }
 // copy the wavefunctions into physical buffer 0 (CTA = (problem, band)), then reset roles
 template <typename T>
@@ -938,8 +941,8 @@ void Engine::work_of(int kind, double* bytes, double* flops) const {
         b += 2.0 * nb * npw * ts;
         break;
       case TK_GEMM_NN:
-        f += 2.0 * npw * nb * nb;
-        b += 2.0 * nb * npw * ts;
+        f += 2.0 * npw * nb * nb * work_mult_;
+        b += 2.0 * nb * npw * ts * work_mult_;
         break;
       case TK_RR:
         f += 4.0 * nb * nb * nb;
@@ -951,7 +954,7 @@ void Engine::work_of(int kind, double* bytes, double* flops) const {
   *flops = f;
 }
 
-void Engine::swap_roles(int a, int b) { k_swap_roles<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, a, b); }
+void Engine::swap_roles(int a, int b) { k_swap_roles<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, role_pair(a, b)); }
 
 void Engine::set_scal(int idx, double v, bool only_active) {
   k_set_scal<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, idx, v, only_active ? 1 : 0);
@@ -1008,22 +1011,34 @@ void Engine::tn(int akind, int arole, int bkind, int brole, int dst, bool allow_
 // image_ready: the previous NN call built the tensor-core image of the same matrix.
 template <typename T>
 void Engine::nn(int akind, int arole, int msel, int yrole, double alpha, double beta, bool image_ready) {
+  nn_pairs<T>(akind, role_pair(arole, yrole), msel, alpha, beta, image_ready);
+}
+
+// One launch maps every (source, destination) role pair of rp through the same matrix.
+template <typename T>
+void Engine::nn_pairs(int akind, const RolePairs& rp, int msel, double alpha, double beta, bool image_ready) {
   const int kind = akind == OPK_WB ? TK_GEMM_NN : TK_GEMM_SMALL;
   tbeg(kind);
   if (sizeof(T) == 4 && nn_tc_ok_[akind]) {
     if (!image_ready) launch_nn_image(L(m_prob_), akind, msel, d_nnimg_, nnimg_stride_);
-    launch_gemm_nn_tc(L(m_nntc_), d_tmaps_, d_nnimg_, nnimg_stride_, nnimg_max_[akind], akind, arole, yrole, alpha,
-                      beta, nn_tpc_);
+    launch_gemm_nn_tc(L(m_nntc_), d_tmaps_, d_nnimg_, nnimg_stride_, nnimg_max_[akind], akind, rp, alpha, beta,
+                      nn_tpc_);
   } else {
-    launch_gemm_nn<T>(L(m_nn_), akind, arole, msel, yrole, alpha, beta);
+    launch_gemm_nn<T>(L(m_nn_), akind, rp, msel, alpha, beta);
   }
+  work_mult_ = rp.n;
   tend(kind);
+  work_mult_ = 1;
 }
 
+// Psi <- Psi Tm for the block and its companions in one NN launch: every source role of
+// rp is rotated into its destination role (a buffer whose contents are dead), then the
+// pairs listed in swap exchange roles, so that each rotated block sits under its source's
+// role again (a pair left out of swap keeps the rotated block under the destination).
 template <typename T>
-void Engine::rotate(int role, bool image_ready) {
-  nn<T>(OPK_WB, role, DD_TM, WB_W, 1.0, 0.0, image_ready);
-  swap_roles(role, WB_W);
+void Engine::rotate_pairs(const RolePairs& rp, const RolePairs& swap) {
+  nn_pairs<T>(OPK_WB, rp, DD_TM, 1.0, 0.0, false);
+  if (swap.n > 0) k_swap_roles<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, swap);
 }
 
 // z-column passes: shared-memory engine for the members without a register transform of
@@ -1080,12 +1095,16 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   else
     launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_, 30);
   tend(TK_RR);
-  rotate<T>(WB_X, false);
-  rotate<T>(WB_HX, true);
-  if (rotate_history) {
-    rotate<T>(WB_PP, true);
-    rotate<T>(WB_RP, true);
-  }
+  // P and HP (the last search direction and its H image) and W are dead here; so is RP
+  // (after a CG step the new residual waits in W2 and the old one in RP is done with): one
+  // launch rotates X -> P, HX -> HP and, with the CG history, PP -> W and the new residual
+  // W2 -> RP; the role swaps put the rotated blocks under X, HX and PP.
+  if (rotate_history)
+    rotate_pairs<T>(RolePairs{4, {WB_X, WB_HX, WB_PP, WB_W2}, {WB_P, WB_HP, WB_W, WB_RP}},
+                    RolePairs{3, {WB_X, WB_HX, WB_PP, 0}, {WB_P, WB_HP, WB_W, 0}});
+  else
+    rotate_pairs<T>(RolePairs{2, {WB_X, WB_HX, 0, 0}, {WB_P, WB_HP, 0, 0}},
+                    RolePairs{2, {WB_X, WB_HX, 0, 0}, {WB_P, WB_HP, 0, 0}});
 }
 
 // One all-band CG step of Algorithm 1: search directions, projection, line minimisation,
@@ -1104,9 +1123,9 @@ void Engine::cg_step() {
   tbeg(TK_CG_BAND);
   launch_line_min<T>(L(m_bands_), WB_X, WB_HX, WB_P, WB_HP);  // line minimisation
   tend(TK_CG_BAND);
-  swap_roles(WB_RP, WB_W2);
-  rayleigh_ritz<T>(true);                          // orthonormalise + subspace diagonalisation
-  launch_finish_cg(L(m_prob_));
+  // orthonormalise + subspace diagonalisation; the residual of this step (in W2) becomes
+  // the history RP, rotated with the bands (k_normalize has already moved <g, r> on)
+  rayleigh_ritz<T>(true);
 }
 
 void Engine::sync_active() {

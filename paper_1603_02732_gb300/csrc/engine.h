@@ -136,7 +136,10 @@ class Engine {
   template <typename T> void tn(int akind, int arole, int bkind, int brole, int dst, bool allow_tc = true);
   template <typename T>
   void nn(int akind, int arole, int msel, int yrole, double alpha, double beta, bool image_ready = false);
-  template <typename T> void rotate(int role, bool image_ready);
+  template <typename T>
+  void nn_pairs(int akind, const RolePairs& rp, int msel, double alpha, double beta, bool image_ready);
+  template <typename T> void rotate_pairs(const RolePairs& rp, const RolePairs& swap);
+  int work_mult_ = 1;  // operand pairs of the NN launch being timed
   void grid_fft(int which, int sign, bool fp32 = false);
   template <typename T> void grid_fft_raw(int which, int sign);
   void potential();

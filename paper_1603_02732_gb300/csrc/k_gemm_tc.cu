@@ -406,8 +406,9 @@ __global__ void k_nn_image(KArgs ka, int akind, int msel, float* img_base, size_
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NN_THREADS, 1)
     k_gemm_nn_tma(KArgs ka, const CUtensorMap* __restrict__ maps, const float* __restrict__ img_base,
-                  size_t img_stride, int img_max, int nstages, int akind, int arole, int yrole, float alpha,
+                  size_t img_stride, int img_max, int nstages, int akind, RolePairs rp, float alpha,
                   float beta, int tpc, long long wait_ns) {
+  const int arole = rp.a[blockIdx.y], yrole = rp.y[blockIdx.y];
   extern __shared__ unsigned char smem_dyn[];
   __shared__ __align__(8) uint64_t full[NN_MAX_STAGES], conv[NN_MAX_STAGES], empty[NN_MAX_STAGES], tfull[2],
       tempty[2], imgbar, done;
@@ -645,13 +646,13 @@ void launch_nn_image(const Launch& Lprob, int akind, int msel, float* img, size_
 }
 
 void launch_gemm_nn_tc(const Launch& L, const void* maps, const float* img, size_t img_stride, int img_max,
-                       int akind, int arole, int yrole, double alpha, double beta, int tpc) {
-  if (!L.map.total) return;
+                       int akind, const RolePairs& rp, double alpha, double beta, int tpc) {
+  if (!L.map.total || rp.n < 1) return;
   const int img_al = (img_max + 1023) & ~1023;
   const int ns = nn_tc_stages(img_max);
-  k_gemm_nn_tma<<<L.map.total, NN_THREADS, 1024 + img_al + ns * NN_STAGE, L.stream>>>(
-      L.ka, reinterpret_cast<const CUtensorMap*>(maps), img, img_stride, img_al, ns, akind, arole, yrole,
-      (float)alpha, (float)beta, tpc, L.wait_ns);
+  k_gemm_nn_tma<<<dim3(L.map.total, rp.n), NN_THREADS, 1024 + img_al + ns * NN_STAGE, L.stream>>>(
+      L.ka, reinterpret_cast<const CUtensorMap*>(maps), img, img_stride, img_al, ns, akind, rp, (float)alpha,
+      (float)beta, tpc, L.wait_ns);
 }
 
 void gemm_tc_set_smem_limits() {

@@ -135,8 +135,9 @@ __global__ void k_gemm_tn_reduce(KArgs ka, int akind, int bkind, int dst, const 
 // CTA = (problem, row tile, column tile), 64 x 64 outputs, 4 x 4 per thread.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm_nn(KArgs ka, int akind, int arole, int msel, int yrole, double alpha,
+__global__ void __launch_bounds__(256) k_gemm_nn(KArgs ka, int akind, RolePairs rp, int msel, double alpha,
                                                 double beta) {
+  const int arole = rp.a[blockIdx.y], yrole = rp.y[blockIdx.y];
   // CTA = (problem, group of NN_RT row tiles of 64, column tile of 64).  The small matrix
   // M[0:inner][c0:c0+64] is staged once per CTA (in passes of NN_KP rows of M) and reused
   // by every row tile; thread (tr, tc) owns rows tr + 16 i and columns tc + 16 j (i, j < 4).
@@ -413,7 +414,13 @@ __global__ void __launch_bounds__(BAND_THREADS) k_normalize(KArgs ka, int pr, in
     for (int j = 0; j < W; ++j) a.e[j] *= inv;
     pv[v] = a;
   }
-  if (threadIdx.x == 0) P.bv[BV_PNORM * P.nb + i] = s;
+  if (threadIdx.x == 0) {
+    P.bv[BV_PNORM * P.nb + i] = s;
+    // end of this CG step's use of the Polak-Ribiere history: the current <g, r> becomes
+    // the previous one, and the history is valid from the next step on
+    P.bv[BV_GRP * P.nb + i] = P.bv[BV_GR * P.nb + i];
+    if (i == 0) P.scal[SC_FIRSTCG] = 0.0;
+  }
 }
 
 // Line minimisation (Algorithm 1): in span{x, p} (p unit, p orthogonal to x) the Rayleigh
@@ -991,15 +998,6 @@ __global__ void k_occupations(KArgs ka) {
   }
 }
 
-// End of one CG step: the current <g, r> becomes the previous one; history is valid.
-__global__ void k_finish_cg(KArgs ka) {
-  const int p = blockIdx.x;
-  if (!ka.active[p]) return;
-  const Prob& P = ka.probs[p];
-  for (int i = threadIdx.x; i < P.nb; i += blockDim.x) P.bv[BV_GRP * P.nb + i] = P.bv[BV_GR * P.nb + i];
-  if (threadIdx.x == 0) P.scal[SC_FIRSTCG] = 0.0;
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -1014,9 +1012,9 @@ void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const
   k_gemm_tn_reduce<<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, bkind, dst, part, stride, kc);
 }
 template <typename T>
-void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta) {
-  if (!L.map.total) return;
-  k_gemm_nn<T><<<L.map.total, 256, (size_t)NN_KP * 64 * sizeof(T), L.stream>>>(L.ka, akind, arole, msel, yrole, alpha,
+void launch_gemm_nn(const Launch& L, int akind, const RolePairs& rp, int msel, double alpha, double beta) {
+  if (!L.map.total || rp.n < 1) return;
+  k_gemm_nn<T><<<dim3(L.map.total, rp.n), 256, (size_t)NN_KP * 64 * sizeof(T), L.stream>>>(L.ka, akind, rp, msel, alpha,
                                                                                beta);
 }
 template <typename T>
@@ -1066,7 +1064,6 @@ void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, siz
   k_rr<<<L.ka.nprob, RR_THREADS, use_smem ? smem : 0, L.stream>>>(L.ka, use_smem, gscratch, gstride, max_sweeps);
 }
 void launch_occupations(const Launch& L) { k_occupations<<<L.ka.nprob, 32, 0, L.stream>>>(L.ka); }
-void launch_finish_cg(const Launch& L) { k_finish_cg<<<L.ka.nprob, 128, 0, L.stream>>>(L.ka); }
 void linalg_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_rr_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -1077,7 +1074,7 @@ void linalg_set_smem_limits(size_t bytes) {
 
 #define INST(T)                                                                                  \
   template void launch_gemm_tn<T>(const Launch&, int, int, int, int, double*, size_t, int);     \
-  template void launch_gemm_nn<T>(const Launch&, int, int, int, int, double, double);           \
+  template void launch_gemm_nn<T>(const Launch&, int, const RolePairs&, int, double, double);     \
   template void launch_band_kinetic<T>(const Launch&, int);                                     \
   template void launch_band_residual<T>(const Launch&, int, int);                               \
   template void launch_cg_precond<T>(const Launch&, int, int, int, int, int, int);              \

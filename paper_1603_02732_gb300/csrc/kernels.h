@@ -47,6 +47,14 @@ struct Launch {
 
 // operands of the subspace GEMMs
 enum { OPK_WB = 0, OPK_B = 1, OPK_DB = 2 };
+// Up to four (source role, destination role) pairs that one NN launch maps through the same
+// small matrix (grid dimension y = pair); also the role pairs one swap kernel exchanges.
+struct RolePairs {
+  int n;
+  int a[4];
+  int y[4];
+};
+inline RolePairs role_pair(int a, int y) { return RolePairs{1, {a, 0, 0, 0}, {y, 0, 0, 0}}; }
 enum { DD_S = 0, DD_HS, DD_CM, DD_TM, DD_PROJ, DD_DPROJ, DD_PROJ_D };
 
 // k_fft.cu
@@ -127,10 +135,10 @@ void launch_gemm_tn_tc(const Launch& L, const void* maps, int akind, int arole, 
                        size_t stride, int kc = TC_KC);
 void launch_nn_image(const Launch& Lprob, int akind, int msel, float* img, size_t img_stride);
 void launch_gemm_nn_tc(const Launch& L, const void* maps, const float* img, size_t img_stride, int img_max,
-                       int akind, int arole, int yrole, double alpha, double beta, int tpc = NN_TPC);
+                       int akind, const RolePairs& rp, double alpha, double beta, int tpc = NN_TPC);
 void gemm_tc_set_smem_limits();
 template <typename T>
-void launch_gemm_nn(const Launch& L, int akind, int arole, int msel, int yrole, double alpha, double beta);
+void launch_gemm_nn(const Launch& L, int akind, const RolePairs& rp, int msel, double alpha, double beta);
 template <typename T> void launch_band_kinetic(const Launch& L, int xrole);
 template <typename T> void launch_band_residual(const Launch& L, int xrole, int hxrole);
 template <typename T> void launch_cg_precond(const Launch& L, int x, int hx, int p, int r, int pp, int rp);
@@ -145,7 +153,6 @@ template <typename T> void launch_copy_out(const Launch& L, int role, double* ds
 void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride, int max_sweeps = 30);
 void launch_rr_f32(const Launch& L, size_t smem, float* gscratch = nullptr, size_t gstride = 0, int max_sweeps = 10);
 void launch_occupations(const Launch& L);
-void launch_finish_cg(const Launch& L);
 void linalg_set_smem_limits(size_t bytes);
 
 // k_grid.cu  (grid sources/destinations: 0 rho_in, 1 rho_out, 2 resid, 3 vion_r)

@@ -153,7 +153,7 @@ sgo_status run(sgo_ctx* c, const double* veff, int nvec, const double* psi, doub
   launch_cols_to_wave<T>(launch(M_ZCOL), WB_W, WB_W2);
   launch_gemm_tn<T>(launch(M_TN), OPK_B, 0, OPK_WB, WB_W, part, part_stride);
   launch_gemm_tn_reduce(launch(M_RED), OPK_B, OPK_WB, DD_PROJ, part, part_stride);
-  launch_gemm_nn<T>(launch(M_NN), OPK_B, 0, DD_PROJ_D, WB_W2, 1.0, 1.0);
+  launch_gemm_nn<T>(launch(M_NN), OPK_B, role_pair(0, WB_W2), DD_PROJ_D, 1.0, 1.0);
   launch_copy_out<T>(launch(M_BANDS), WB_W2, dout, nvec);
   if (!cuda_ok(cudaGetLastError(), "no-alloc H.psi launch") ||
       !cuda_ok(cudaMemcpyAsync(hpsi, dout, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyDeviceToHost, st),

@@ -528,6 +528,26 @@ def _make_autograd():
     return SgoEnergy
 
 
+def relax_autograd(ctx: "Context", driver: "Relax", max_evals: int = 100):
+    """Local relaxation (Sec. II C) of one structure with its energy and gradient taken from
+    SgoEnergy: the forward pass is the self-consistent energy, the backward pass the force
+    adjoint (dE/dR = -F); the driver (PCG with the force-fitted preconditioner, CG or BFGS)
+    turns them into the next positions.  Every evaluation after the first restarts from the
+    previous density and wavefunctions.  Returns (state, evaluations): state 1 converged,
+    2 stopped by the driver, 0 stopped at max_evals."""
+    import torch
+    pos = driver.positions()
+    state, n = 0, 0
+    ctx.set_warm(True)
+    while state == 0 and n < max_evals:
+        x = torch.tensor(pos, dtype=torch.float64, requires_grad=True)
+        E = SgoEnergy.apply(ctx, x)
+        E.backward()
+        pos, state = driver.step(float(E.detach()), -x.grad.numpy())
+        n += 1
+    return state, n
+
+
 class _Lazy:
     _cls = None
 

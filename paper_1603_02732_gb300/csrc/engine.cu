@@ -824,18 +824,17 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   // else in a per-member global scratch; the Jacobi pair tables allow nb <= 512)
   const sgo_opts& o0 = ctxs[0]->opts;
   wait_ns_ = o0.watchdog_ms > 0.0 ? (long long)(o0.watchdog_ms * 1e6) : 2000000000LL;
-  rr_f32_ = precision_ == 1 && !o0.rr_fp64 && max_nb_ <= 512;
-  if (rr_f32_ && (size_t)20 * max_nb_ * (max_nb_ | 1) > 216 * 1024) {
-    rr32_stride_ = (size_t)5 * max_nb_ * (max_nb_ | 1);
-    if (!cuda_ok(cudaMalloc(&d_rr32_, sizeof(float) * rr32_stride_ * n_), "cudaMalloc(rr32)")) return;
-    allocs_.push_back(d_rr32_);
-  }
+  // subspace diagonalisation: one CTA per member with its matrices in shared memory (FP32
+  // deviation form up to nb = 105 on the mixed path, FP64 up to nb = 91), else one
+  // thread-block cluster per member over a global scratch (k_rr_cluster)
+  rr_f32_ = precision_ == 1 && !o0.rr_fp64;
   rr_smem_bytes_ = (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
   rr_smem_ = rr_smem_bytes_ <= 200 * 1024;
-  if (!rr_f32_ && !rr_smem_) {
-    rr_stride_ = (size_t)3 * max_nb_ * max_nb_;
-    if (!cuda_ok(cudaMalloc(&d_rr_, sizeof(double) * rr_stride_ * n_), "cudaMalloc(rr)")) return;
-    allocs_.push_back(d_rr_);
+  rr_cluster_ = rr_f32_ ? (size_t)20 * max_nb_ * (max_nb_ | 1) > 216 * 1024 : !rr_smem_;
+  if (rr_cluster_) {
+    rrc_stride_ = (rr_cluster_scratch_bytes(max_nb_, rr_f32_ ? sizeof(float) : sizeof(double)) + 255) / 256 * 256;
+    if (!cuda_ok(cudaMalloc(&d_rrc_, rrc_stride_ * n_), "cudaMalloc(rr cluster scratch)")) return;
+    allocs_.push_back(d_rrc_);
   }
   fft_set_smem_limits(220 * 1024);
   linalg_set_smem_limits(220 * 1024);
@@ -1090,10 +1089,16 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S, false);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
   tbeg(TK_RR);
-  if (rr_f32_)  // 5 FP32 n x (n|1) matrices
-    launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1), d_rr32_, rr32_stride_, rr_cap_);
-  else
-    launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, d_rr_, rr_stride_, 30);
+  if (rr_cluster_) {
+    const Launch l = L(m_prob_);
+    const bool launched = rr_f32_ ? launch_rr_cluster<float>(l, max_nb_, d_rrc_, rrc_stride_, rr_cap_)
+                                  : launch_rr_cluster<double>(l, max_nb_, d_rrc_, rrc_stride_, 30);
+    if (!launched) set_error("cluster Rayleigh-Ritz launch refused");
+  } else if (rr_f32_) {  // 5 FP32 n x (n|1) matrices in shared memory
+    launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1), nullptr, 0, rr_cap_);
+  } else {
+    launch_rr(L(m_prob_), 1, rr_smem_bytes_, nullptr, 0, 30);
+  }
   tend(TK_RR);
   // P and HP (the last search direction and its H image) and W are dead here; so is RP
   // (after a CG step the new residual waits in W2 and the old one in RP is done with): one

@@ -191,12 +191,11 @@ class Engine {
   size_t part_stride_ = 0;
   double* d_gpart_ = nullptr;
   int maxchunk_ = 1;
-  double* d_rr_ = nullptr;
-  size_t rr_stride_ = 0;
   bool rr_smem_ = true;
   bool rr_f32_ = false;
-  float* d_rr32_ = nullptr;     // FP32 eigensolve scratch when it exceeds shared memory
-  size_t rr32_stride_ = 0;
+  bool rr_cluster_ = false;          // subspace too large for one CTA: cluster eigensolve
+  unsigned char* d_rrc_ = nullptr;   // its per-member global scratch
+  size_t rrc_stride_ = 0;
   size_t rr_smem_bytes_ = 0;
   double* d_flags_ = nullptr;   // [n][4] gathered per iteration
   // pinned read-back area (device-to-host copies into it do not block the host):

@@ -12,6 +12,8 @@
 //  * rr: FP64 Cholesky of the overlap, L^-1 H L^-T and a parallel cyclic Jacobi
 //    eigensolve (the subspace diagonalisation of Algorithm 1).
 //  * occupations: Fermi-Dirac with the chemical potential by safeguarded Newton.
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace sgo {
@@ -934,6 +936,365 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
     if (flag) P.status[0] = 1;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz for subspaces too large for one CTA's shared memory (the 330-band cluster):
+// one thread-block cluster of RR_CLUSTER CTAs per problem, its matrices in the problem's
+// global scratch (L2-resident), row i dealt to the CTA of rank i % RR_CLUSTER, hardware
+// cluster barriers between the steps.  Same mathematics as k_rr_f32 (deviation form):
+//  1. D = S - I and Hf, symmetrised.
+//  2. Cholesky S = (I + L)(I + L)^T in deviation form: column k's pivot d_k and scaled
+//     entries are formed by every CTA from the column (final after step k - 1), and each
+//     CTA updates its own trailing rows: one barrier per column.
+//  3. (I + L)^-1 = I + G by forward substitution down each column of G, a warp per column
+//     (the columns are independent), stored transposed (GT row j = column j of G).
+//  4. C = (I + G) Hf (I + G)^T, symmetrised; V = (I + G)^T.
+//  5. Eigenvectors by one-sided Jacobi (Hestenes, J. SIAM 6, 51 (1958)) on
+//     X = C - sigma I, sigma below the Gershgorin bound of C's spectrum, so that X is
+//     positive definite and its right singular vectors are C's eigenvectors: in each
+//     round-robin round every CTA sums the three dot products of every column pair over
+//     its rows (FP64 partials), one barrier, and every CTA forms the same rotations from
+//     the partials added in rank order and rotates its rows of X and V.  A sweep without a
+//     rotation above the rounding threshold ends the loop; max_sweeps caps it (counted in
+//     SC_RRCAP).
+//  6. eps_j = |x_j| + sigma (|x_j| = eps_j - sigma for the unit eigenvector), ascending
+//     ranks, Tm[:, rank(j)] = V[:, j].
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RrTol;
+template <>
+struct RrTol<float> {
+  static constexpr double cosine = 3e-6;  // column-pair cosine below FP32 rounding of the dots
+};
+template <>
+struct RrTol<double> {
+  static constexpr double cosine = 1e-13;
+};
+
+size_t rr_cluster_scratch_bytes(int n, size_t tsize) {
+  const size_t nn = (size_t)n * n, npairs = (size_t)(n + (n & 1)) / 2;
+  return 5 * nn * tsize + 256 + (2 * RR_CLUSTER * npairs * 3 + RR_CLUSTER * (size_t)n + 2 * RR_CLUSTER + n) * 8 + 256;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned char* scratch_base, size_t stride,
+                                                           int max_sweeps, int rows_smem) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  constexpr int C = RR_CLUSTER;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[33];
+  __shared__ int flag_s, rot_s;
+  const int p = blockIdx.x / C;
+  const int rank = (int)cluster.block_rank();
+  if (!ka.active[p]) return;  // the whole cluster shares p
+  const Prob& P = ka.probs[p];
+  const int n = P.nb, m = n + (n & 1), npairs = m / 2;
+  const size_t nn = (size_t)n * n;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  // global scratch of this problem
+  unsigned char* base = scratch_base + (size_t)p * stride;
+  T* Dm = reinterpret_cast<T*>(base);  // Cholesky working matrix, then X
+  T* Hm = Dm + nn;                     // Hf, then C
+  T* Lm = Hm + nn;                     // scaled Cholesky columns, then V
+  T* GT = Lm + nn;                     // G transposed
+  T* Wm = GT + nn;                     // (I + G) Hf
+  double* part = reinterpret_cast<double*>(base + ((5 * nn * sizeof(T) + 255) / 256) * 256);  // [2][C][npairs][3]
+  double* colp = part + 2 * (size_t)C * npairs * 3;  // [C][n] column partial sums
+  double* gpart = colp + (size_t)C * n;              // [C] Gershgorin minima, [C] flags
+  double* dkv = gpart + 2 * C;                       // [n] pivots d_k
+  // shared memory: column k of the Cholesky, the rotations and pairs, and (rows_smem) the
+  // Jacobi's rows of X and V, else those rows stay in the global X (Dm) and V (Lm);
+  // eigenvalues and ranks at the end
+  const int myrows = (n - rank + C - 1) / C;  // rows rank, rank + C, ...
+  const int myrows_max = (n + C - 1) / C;
+  T* colk = reinterpret_cast<T*>(smem_raw);   // [n]
+  T* csc = colk + n;                          // [npairs]
+  T* css = csc + npairs;                      // [npairs]
+  int* pp = reinterpret_cast<int*>(css + npairs);  // [npairs]
+  int* pq = pp + npairs;                           // [npairs]
+  T* const xbase = reinterpret_cast<T*>(smem_raw + (((size_t)(n + 2 * npairs) * sizeof(T) + 2 * npairs * sizeof(int) +
+                                                      15) / 16) * 16);
+  // row r of mine: i = rank + C r
+  auto xrow = [&](int r) -> T* { return rows_smem ? xbase + (size_t)r * n : Dm + (size_t)(rank + C * r) * n; };
+  auto vrow = [&](int r) -> T* {
+    return rows_smem ? xbase + (size_t)(myrows_max + r) * n : Lm + (size_t)(rank + C * r) * n;
+  };
+  double* lam = reinterpret_cast<double*>(xbase);  // [n] (reuses the rows after the Jacobi)
+  int* rnk = reinterpret_cast<int*>(lam + n);      // [n]
+  if (tid == 0) flag_s = 0;
+
+  // 1. D = S - I, Hf (symmetrised), my rows
+  for (int e = tid; e < myrows * n; e += nt) {
+    const int i = rank + C * (e / n), j = e % n;
+    Dm[(size_t)i * n + j] = (T)(0.5 * (P.S[i * n + j] + P.S[j * n + i]) - (i == j ? 1.0 : 0.0));
+    Hm[(size_t)i * n + j] = (T)(0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]));
+  }
+  cluster.sync();
+
+  // 2. Cholesky in deviation form
+  for (int k = 0; k < n; ++k) {
+    const T x = Dm[(size_t)k * n + k];
+    const T xs = x > T(-0.999) ? x : T(-0.999);
+    const T dk = xs / (T(1) + sqrt(T(1) + xs));
+    const T inv = T(1) / (T(1) + dk);
+    if (tid == 0) {
+      if (!(x > T(-0.999))) flag_s = 1;
+      if (rank == 0) dkv[k] = (double)dk;
+    }
+    for (int j = k + 1 + tid; j < n; j += nt) colk[j] = Dm[(size_t)j * n + k] * inv;
+    __syncthreads();
+    const int r0 = (k + 1 - rank + C - 1) / C > 0 ? (k + 1 - rank + C - 1) / C : 0;  // first my row > k
+    for (int r = r0 + warp; r < myrows; r += nwarps) {
+      const int i = rank + C * r;
+      const T li = colk[i];
+      if (lane == 0) Lm[(size_t)i * n + k] = li;
+      T* Di = Dm + (size_t)i * n;
+      for (int j = k + 1 + lane; j <= i; j += 32) Di[j] -= li * colk[j];
+    }
+    cluster.sync();
+  }
+
+  // 3. G by columns: GT[j][i] = G_ij, G_jj = -d_j / (1 + d_j),
+  //    G_ij = -(L_ij + sum_{j <= k < i} L_ik G_kj) / (1 + d_i)
+  for (int j = rank * nwarps + warp; j < n; j += C * nwarps) {
+    T* gj = GT + (size_t)j * n;
+    const T dj = (T)dkv[j];
+    if (lane == 0) gj[j] = -dj / (T(1) + dj);
+    __syncwarp();
+    for (int i = j + 1; i < n; ++i) {
+      const T* Li = Lm + (size_t)i * n;
+      T sacc = T(0);
+      for (int k = j + lane; k < i; k += 32) sacc += Li[k] * gj[k];
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) gj[i] = -(Li[j] + sacc) / (T(1) + (T)dkv[i]);
+      __syncwarp();
+    }
+  }
+  cluster.sync();
+
+  // 4. W = (I + G) Hf: W_ij = Hf_ij + sum_{k <= i} G_ik Hf_kj
+  for (int e = tid; e < myrows * n; e += nt) {
+    const int i = rank + C * (e / n), j = e % n;
+    T acc = Hm[(size_t)i * n + j];
+    for (int k = 0; k <= i; ++k) acc += GT[(size_t)k * n + i] * Hm[(size_t)k * n + j];
+    Wm[(size_t)i * n + j] = acc;
+  }
+  cluster.sync();
+  //    C = W (I + G)^T: C_ij = W_ij + sum_{k <= j} W_ik G_jk  (into Hm)
+  for (int e = tid; e < myrows * n; e += nt) {
+    const int i = rank + C * (e / n), j = e % n;
+    const T* Wi = Wm + (size_t)i * n;
+    T acc = Wi[j];
+    for (int k = 0; k <= j; ++k) acc += Wi[k] * GT[(size_t)k * n + j];
+    Hm[(size_t)i * n + j] = acc;
+  }
+  cluster.sync();
+  //    X = sym(C) (into Dm), V = (I + G)^T (into Lm), Gershgorin minimum of my rows
+  double gmin = 1e300;
+  for (int r = warp; r < myrows; r += nwarps) {
+    const int i = rank + C * r;
+    double off = 0.0, dia = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const T v = T(0.5) * (Hm[(size_t)i * n + j] + Hm[(size_t)j * n + i]);
+      Dm[(size_t)i * n + j] = v;
+      Lm[(size_t)i * n + j] = (i == j ? T(1) : T(0)) + GT[(size_t)i * n + j];
+      if (j == i) dia = (double)v; else off += fabs((double)v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    gmin = fmin(gmin, dia - off);
+  }
+  if (lane == 0) red[warp] = gmin;
+  __syncthreads();
+  if (tid == 0) {
+    double g = 1e300;
+    for (int w = 0; w < nwarps; ++w) g = fmin(g, red[w]);
+    gpart[rank] = g;
+    gpart[C + rank] = flag_s;
+  }
+  cluster.sync();
+  double sigma = 1e300;
+  int flag = 0;
+  for (int r = 0; r < C; ++r) {
+    sigma = fmin(sigma, gpart[r]);
+    flag |= gpart[C + r] != 0.0;
+  }
+  sigma -= 1e-3 * (1.0 + fabs(sigma));
+  // my rows of X - sigma I and V (into shared memory when they fit)
+  for (int e = tid; e < myrows * n; e += nt) {
+    const int r = e / n, j = e % n, i = rank + C * r;
+    const T v = Dm[(size_t)i * n + j];
+    xrow(r)[j] = i == j ? (T)((double)v - sigma) : v;
+    if (rows_smem) vrow(r)[j] = Lm[(size_t)i * n + j];
+  }
+  __syncthreads();
+
+  // 5. one-sided Jacobi, round-robin column pairs (position 0 fixed, 1..m-1 rotating)
+  int sweeps = 0, capped = 0, round = 0;
+  for (int sweep = 0;; ++sweep) {
+    if (tid == 0) rot_s = 0;
+    __syncthreads();
+    for (int rr = 0; rr < m - 1; ++rr, ++round) {
+      for (int t = tid; t < npairs; t += nt) {
+        const int a = t, b = m - 1 - t;
+        const int pa = a == 0 ? 0 : 1 + (a - 1 + rr) % (m - 1);
+        const int pb = b == 0 ? 0 : 1 + (b - 1 + rr) % (m - 1);
+        pp[t] = min(pa, pb);
+        pq[t] = max(pa, pb);
+      }
+      __syncthreads();
+      double* pr = part + ((size_t)(round & 1) * C + rank) * npairs * 3;
+      for (int t = warp; t < npairs; t += nwarps) {
+        const int a = pp[t], b = pq[t];
+        double al = 0.0, be = 0.0, ga = 0.0;
+        if (b < n)
+          for (int r = lane; r < myrows; r += 32) {
+            const T* xr = xrow(r);
+            const double xa = (double)xr[a], xb = (double)xr[b];
+            al += xa * xa;
+            be += xb * xb;
+            ga += xa * xb;
+          }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (lane == 0) {
+          pr[3 * t] = al;
+          pr[3 * t + 1] = be;
+          pr[3 * t + 2] = ga;
+        }
+      }
+      cluster.sync();
+      const double* pb0 = part + (size_t)(round & 1) * C * npairs * 3;
+      for (int t = tid; t < npairs; t += nt) {
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = 0; r < C; ++r) {
+          const double* q = pb0 + ((size_t)r * npairs + t) * 3;
+          al += q[0];
+          be += q[1];
+          ga += q[2];
+        }
+        T c = T(1), sn = T(0);
+        if (pq[t] < n && fabs(ga) > RrTol<T>::cosine * sqrt(al * be) && fabs(ga) > 1e-300) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cc = 1.0 / sqrt(1.0 + tt * tt);
+          c = (T)cc;
+          sn = (T)(cc * tt);
+          rot_s = 1;
+        }
+        csc[t] = c;
+        css[t] = sn;
+      }
+      __syncthreads();
+      for (int e = tid; e < npairs * myrows; e += nt) {
+        const int t = e / myrows, r = e - t * myrows;
+        const T sn = css[t];
+        if (sn == T(0)) continue;
+        const T c = csc[t];
+        const int a = pp[t], b = pq[t];
+        T* xr = xrow(r);
+        T* vr = vrow(r);
+        const T xa = xr[a], xb = xr[b], va = vr[a], vb = vr[b];
+        xr[a] = c * xa - sn * xb;
+        xr[b] = sn * xa + c * xb;
+        vr[a] = c * va - sn * vb;
+        vr[b] = sn * va + c * vb;
+      }
+      __syncthreads();
+    }
+    ++sweeps;
+    if (rot_s == 0) break;
+    if (sweep + 1 == max_sweeps) {
+      capped = 1;
+      break;
+    }
+  }
+
+  // 6. eigenvalues from the column norms, ranks, Tm and eps
+  for (int j = tid; j < n; j += nt) {
+    double sq = 0.0;
+    for (int r = 0; r < myrows; ++r) {
+      const double v = (double)xrow(r)[j];
+      sq += v * v;
+    }
+    colp[(size_t)rank * n + j] = sq;
+  }
+  // V rows to global before the shared memory is reused
+  if (rows_smem)
+    for (int e = tid; e < myrows * n; e += nt) Lm[(size_t)(rank + C * (e / n)) * n + e % n] = vrow(e / n)[e % n];
+  cluster.sync();
+  for (int j = tid; j < n; j += nt) {
+    double sq = 0.0;
+    for (int r = 0; r < C; ++r) sq += colp[(size_t)r * n + j];
+    lam[j] = sqrt(sq) + sigma;
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += nt) {
+    const double ej = lam[j];
+    int rk = 0;
+    for (int k2 = 0; k2 < n; ++k2) {
+      const double ek = lam[k2];
+      rk += (ek < ej) || (ek == ej && k2 < j);
+    }
+    rnk[j] = rk;
+    if (rank == 0) P.eps[rk] = ej;
+  }
+  __syncthreads();
+  for (int e = tid; e < myrows * n; e += nt) {
+    const int i = rank + C * (e / n), j = e % n;
+    P.Tm[(size_t)i * n + rnk[j]] = (double)Lm[(size_t)i * n + j];
+  }
+  if (rank == 0 && tid == 0) {
+    P.scal[SC_RRSWEEPS] += sweeps;
+    P.scal[SC_RRCAP] += capped;
+    if (flag) P.status[0] = 1;
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory (none does) or scratch
+}
+
+// Shared memory of the cluster Rayleigh-Ritz for subspace size n: the head (column k,
+// rotations, pairs), then either the rows of X and V (rows_smem) or the final eigenvalues
+// and ranks, whichever is larger.
+static size_t rr_cluster_smem_t(int n, size_t tsize, bool rows_smem) {
+  const size_t myrows = (n + RR_CLUSTER - 1) / RR_CLUSTER, npairs = (n + (n & 1)) / 2;
+  const size_t head = ((n + 2 * npairs) * tsize + 2 * npairs * sizeof(int) + 15) / 16 * 16;
+  const size_t rows = rows_smem ? 2 * myrows * n * tsize : 0;
+  const size_t fin = (size_t)n * (sizeof(double) + sizeof(int));
+  return head + std::max(rows, fin) + 16;
+}
+static bool rr_cluster_rows_fit(int n, size_t tsize) { return rr_cluster_smem_t(n, tsize, true) <= 200 * 1024; }
+size_t rr_cluster_smem(int n) { return rr_cluster_smem_t(n, 4, rr_cluster_rows_fit(n, 4)); }
+size_t rr_cluster_smem64(int n) { return rr_cluster_smem_t(n, 8, rr_cluster_rows_fit(n, 8)); }
+
+template <typename T>
+bool launch_rr_cluster(const Launch& L, int n_max, unsigned char* scratch, size_t stride, int max_sweeps) {
+  const bool rows_smem = rr_cluster_rows_fit(n_max, sizeof(T));
+  const size_t smem = rr_cluster_smem_t(n_max, sizeof(T), rows_smem);
+  if (smem > 227 * 1024) return false;
+  cudaFuncSetAttribute(k_rr_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.ka.nprob * RR_CLUSTER);
+  cfg.blockDim = dim3(RR_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = L.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = RR_CLUSTER;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_rr_cluster<T>, L.ka, scratch, stride, max_sweeps, rows_smem ? 1 : 0) ==
+         cudaSuccess;
+}
+template bool launch_rr_cluster<float>(const Launch&, int, unsigned char*, size_t, int);
+template bool launch_rr_cluster<double>(const Launch&, int, unsigned char*, size_t, int);
 
 // ---------------------------------------------------------------------------
 // Occupations: integer (kT = 0) or Fermi-Dirac with mu from sum f = N_el; entropy

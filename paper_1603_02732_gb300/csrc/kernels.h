@@ -27,6 +27,7 @@ constexpr int NN_KP = 128;             // rows of the small matrix staged per pa
 constexpr int BAND_THREADS = 256;
 constexpr int GRID_CHUNK = 4096;       // grid points per reduction CTA
 constexpr int RR_THREADS = 1024;
+constexpr int RR_CLUSTER = 8;          // CTAs of the cluster Rayleigh-Ritz (large subspaces)
 constexpr int LF_GROUP = 4;            // atoms per local-force CTA
 
 struct KArgs {
@@ -152,6 +153,15 @@ template <typename T> void launch_copy_out(const Launch& L, int role, double* ds
 // in SC_RRCAP)
 void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride, int max_sweeps = 30);
 void launch_rr_f32(const Launch& L, size_t smem, float* gscratch = nullptr, size_t gstride = 0, int max_sweeps = 10);
+// Rayleigh-Ritz of large subspaces: one thread-block cluster per problem, matrices in a
+// per-problem global scratch of rr_cluster_scratch_bytes(n, sizeof(T)) bytes (T = float:
+// deviation-form FP32 as k_rr_f32; T = double: the same in FP64).  False if the launch
+// was refused (its shared memory would not fit).
+size_t rr_cluster_scratch_bytes(int n, size_t tsize);
+size_t rr_cluster_smem(int n);
+size_t rr_cluster_smem64(int n);
+template <typename T>
+bool launch_rr_cluster(const Launch& L, int n_max, unsigned char* scratch, size_t stride, int max_sweeps);
 void launch_occupations(const Launch& L);
 void linalg_set_smem_limits(size_t bytes);
 

@@ -127,6 +127,27 @@ def test_scf_big_plane_fp64(sgo):
     assert np.abs(rho - ref.rho).max() < 1e-6 * np.abs(ref.rho).max()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_scf_cluster_eigensolver(sgo, precision):
+    """A subspace too large for one CTA's shared memory (112 requested bands, 119 carried):
+    the subspace diagonalisation runs on a thread-block cluster of 8 CTAs (Cholesky in
+    deviation form, one-sided Jacobi) in both precisions; SCF energy, occupied eigenvalues
+    and forces against the oracle."""
+    st = _struct(ecut=6.0, nbands=112)
+    ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)
+    if precision == "fp64":
+        ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=120)
+        _compare(st, ctx.energy_forces(), ref, 1e-8, 1e-6)
+        tol_eig = 1e-7
+    else:
+        ctx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7, scf_tol_rho=1e-5, max_scf=120)
+        _compare(st, ctx.energy_forces(), ref, 1e-5, 1e-4)
+        tol_eig = 2e-4
+    eig, _ = ctx.eigen()
+    assert np.abs(eig - ref.eig)[ref.occ > 1e-6].max() < tol_eig
+    assert ctx.stats()["jacobi_cap_hits"] == 0
+
+
 def test_scf_tiny_mixed(sgo):
     st = _struct(ecut=3.0)
     ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)
@@ -253,6 +274,23 @@ def test_autograd_adjoint(sgo):
     E.backward()
     _, F = ctx.energy_forces(st.pos)
     assert torch.allclose(pos.grad, torch.as_tensor(-F), atol=1e-12)
+
+
+def test_relaxation_through_autograd_matches_batch_driver(sgo):
+    """The relaxation driven by SgoEnergy (energy forward, force adjoint backward) asks for
+    the same positions as the batched driver loop (sgo_relax_batch) on the FP64 path."""
+    st = _struct(ecut=3.0, nat=3, seed=5)
+    opts = dict(precision="fp64", scf_tol_e=1e-10, scf_tol_rho=1e-8, max_scf=120)
+    d1 = sgo.Relax(st.cell, st.pos, method="pcg", fmax=1e-3, max_evals=12)
+    state1, n1 = sgo.relax_autograd(sgo.Context(st, **opts), d1, max_evals=12)
+    d2 = sgo.Relax(st.cell, st.pos, method="pcg", fmax=1e-3, max_evals=12)
+    rounds, status = sgo.Batch([sgo.Context(st, **opts)]).relax([d2], max_rounds=12)
+    assert status[0] == 0
+    assert d1.info() == d2.info()
+    assert np.abs(d1.positions() - d2.positions()).max() < 1e-9
+    e1, x1 = d1.best()
+    e2, x2 = d2.best()
+    assert abs(e1 - e2) < 1e-9 and np.abs(x1 - x2).max() < 1e-9
 
 
 def test_forces_match_finite_differences_gpu(sgo):

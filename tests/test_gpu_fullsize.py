@@ -160,8 +160,14 @@ def test_cluster13_forces_match_finite_differences(sgo):
     """The 13-atom cluster (72^3, 85 bands, kT 0.01 Ha) on the FP64 path: the force adjoint
     (local, nonlocal and Ewald terms of F = -dF/dR) against central differences of the
     GPU free energy, h = 1e-3 bohr, on three components; the displaced evaluations start
-    warm from the converged state.  The mixed path's forces at the same geometry are held
-    to the FP64 finite differences within the accuracy gate (1e-4 Ha/bohr)."""
+    warm from the converged state.  The Z = 10 valence density rises above r_s = 1 at
+    some grid points, where the published PZ81 constants leave the correlation energy a
+    step of 3.2066e-5 Ha per electron; a grid point crossing it moves F by the quantum
+    J = (Omega/N) rho_c 3.2066e-5 Ha (1.64e-7 Ha here, tests/test_oracle_scf.py pins the
+    oracle's steps), so the difference E(+h) - E(-h) is checked against -2 h F up to an
+    integer number of quanta.  The mixed path's forces at the same geometry are held to the
+    FP64 finite differences within the accuracy gate (1e-4 Ha/bohr)."""
+    from tests.test_oracle_scf import pz81_join_quantum
     st = workloads.cluster13()
     opts = dict(precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=150)
     ctx = sgo.Context(st, **opts)
@@ -175,8 +181,11 @@ def test_cluster13_forces_match_finite_differences(sgo):
         ep, _ = ctx.energy_forces(p)
         p[I, a] -= 2 * h
         em, _ = ctx.energy_forces(p)
-        fd = -(ep - em) / (2 * h)
-        assert abs(fd - F[I, a]) < 1e-5, (I, a, fd, F[I, a])
+        J = pz81_join_quantum(abs(np.linalg.det(st.cell)), np.prod(st.fft))
+        gap = (ep - em) + 2 * h * F[I, a]
+        k = round(gap / J)
+        assert abs(k) <= 3 and abs(gap - k * J) < 2 * h * 1e-5, (I, a, gap, J)
+        fd = -(ep - em - k * J) / (2 * h)
         assert abs(fd - Fm[I, a]) < 1e-4, (I, a, fd, Fm[I, a])
 
 

@@ -27,6 +27,40 @@ def test_forces_match_finite_differences(tiny_state):
         assert abs(-(fp - fm) / (2 * h) - r.forces[I, a]) < 1e-6
 
 
+def pz81_join_quantum(omega, ngrid):
+    """Energy step of one grid point whose density crosses r_s = 1.  The published PZ81
+    constants join the two correlation branches only to their printed digits:
+    eps_c(r_s -> 1-) = B + D = -0.0596 against gamma / (1 + beta1 + beta2) = -0.0596321 Ha,
+    a step of 3.2066e-5 Ha per electron at rho_c = 3/(4 pi); one grid point carries
+    (Omega/N) rho_c electrons, so F steps by (Omega/N) rho_c 3.2066e-5 Ha."""
+    step = (-0.048 - 0.0116) - (-0.1423 / (1.0 + 1.0529 + 0.3334))
+    return omega / ngrid * 3.0 / (4.0 * np.pi) * step
+
+
+def test_energy_steps_are_the_pz81_join():
+    """Hard Z = 10 atoms at 15 Ha: the valence density rises above rho_c = 3/(4 pi) (r_s < 1)
+    at some grid points, so moving an atom makes points cross the branch join of the PZ81
+    correlation fit.  Along a 9-point line the free energy minus the integral of -F (the
+    forces are the derivative of F between crossings) must take only integer multiples of
+    the quantum (Omega/N) rho_c * 3.2066e-5 Ha, and some crossing must occur; a force or
+    energy error of another kind would leave a residue that is not such a multiple."""
+    st = workloads.tiny(nat=2, ecut=15.0, kT=0.01, species=workloads.SPECIES_Z10)
+    r = scf(st, **TIGHT)
+    J = pz81_join_quantum(abs(np.linalg.det(st.cell)), np.prod(st.fft))
+    xs = np.linspace(-2e-3, 2e-3, 9)
+    E, F = [], []
+    for x in xs:
+        p = st.pos.copy(); p[0, 0] += x
+        q = scf(st, pos=p, tol_e=1e-12, tol_rho=1e-10, rho0=r.rho_in)
+        E.append(q.free_energy)
+        F.append(q.forces[0, 0])
+    E, F = np.array(E), np.array(F)
+    integral = np.concatenate([[0.0], np.cumsum(-0.5 * (F[1:] + F[:-1]) * np.diff(xs))])
+    k = ((E - E[0]) - integral) / J
+    assert np.abs(k - np.round(k)).max() < 1e-3, k
+    assert np.abs(np.round(k)).max() >= 1, k
+
+
 def test_forces_match_finite_differences_integer_occupations():
     st = workloads.tiny(nat=2, ecut=3.0, kT=0.0, nbands=6, seed=11)
     r = scf(st, **TIGHT)

@@ -118,6 +118,11 @@ typedef struct {
                              requested bands get headroom; occupations, eigenvalues, energies and
                              the eig_tol test cover the requested bands only (-1, default:
                              4 + nbands / 32; 0 = none) */
+  int rr_cluster;         /* subspace diagonalisation kernel: -1 (default) one CTA per member while
+                             its matrices fit in shared memory, else a thread-block cluster of 8
+                             CTAs per member; 0 = always one CTA (over a global scratch when the
+                             matrices do not fit); 1 = always the cluster.  Taken from the first
+                             member of a batch. */
 } sgo_opts;
 
 /* Fill *o with the defaults (FP64, kT 0, tolerances 1e-8 Ha / 1e-7, Pulay 8, ...). */

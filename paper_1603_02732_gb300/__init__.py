@@ -106,7 +106,7 @@ class sgo_opts(ctypes.Structure):
                 ("seed", ctypes.c_ulonglong), ("gemm_tc", ctypes.c_int), ("graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("sub_batches", ctypes.c_int), ("eig_tol", ctypes.c_double),
                 ("max_polish", ctypes.c_int), ("rr_fp64", ctypes.c_int), ("watchdog_ms", ctypes.c_double),
-                ("extra_bands", ctypes.c_int)]
+                ("extra_bands", ctypes.c_int), ("rr_cluster", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -109,6 +109,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->rr_fp64 = 0;
   o->watchdog_ms = 0.0;
   o->extra_bands = -1;
+  o->rr_cluster = -1;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,

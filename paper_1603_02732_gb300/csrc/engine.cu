@@ -829,12 +829,16 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   // thread-block cluster per member over a global scratch (k_rr_cluster)
   rr_f32_ = precision_ == 1 && !o0.rr_fp64;
   rr_smem_bytes_ = (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
-  rr_smem_ = rr_smem_bytes_ <= 200 * 1024;
-  rr_cluster_ = rr_f32_ ? (size_t)20 * max_nb_ * (max_nb_ | 1) > 216 * 1024 : !rr_smem_;
+  rr_smem_ = rr_f32_ ? (size_t)20 * max_nb_ * (max_nb_ | 1) <= 216 * 1024 : rr_smem_bytes_ <= 200 * 1024;
+  rr_cluster_ = o0.rr_cluster > 0 || (o0.rr_cluster < 0 && !rr_smem_);
   if (rr_cluster_) {
     rrc_stride_ = (rr_cluster_scratch_bytes(max_nb_, rr_f32_ ? sizeof(float) : sizeof(double)) + 255) / 256 * 256;
     if (!cuda_ok(cudaMalloc(&d_rrc_, rrc_stride_ * n_), "cudaMalloc(rr cluster scratch)")) return;
     allocs_.push_back(d_rrc_);
+  } else if (!rr_smem_) {  // one CTA over a global scratch
+    rr1_stride_ = rr_f32_ ? (size_t)5 * max_nb_ * (max_nb_ | 1) * sizeof(float) : (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
+    if (!cuda_ok(cudaMalloc(&d_rr1_, rr1_stride_ * n_), "cudaMalloc(rr scratch)")) return;
+    allocs_.push_back(d_rr1_);
   }
   fft_set_smem_limits(220 * 1024);
   linalg_set_smem_limits(220 * 1024);
@@ -1094,10 +1098,12 @@ void Engine::rayleigh_ritz(bool rotate_history) {
     const bool launched = rr_f32_ ? launch_rr_cluster<float>(l, max_nb_, d_rrc_, rrc_stride_, rr_cap_)
                                   : launch_rr_cluster<double>(l, max_nb_, d_rrc_, rrc_stride_, 30);
     if (!launched) set_error("cluster Rayleigh-Ritz launch refused");
-  } else if (rr_f32_) {  // 5 FP32 n x (n|1) matrices in shared memory
-    launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1), nullptr, 0, rr_cap_);
+  } else if (rr_f32_) {  // 5 FP32 n x (n|1) matrices in shared memory or a global scratch
+    launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1), reinterpret_cast<float*>(d_rr1_),
+                  rr1_stride_ / sizeof(float), rr_cap_);
   } else {
-    launch_rr(L(m_prob_), 1, rr_smem_bytes_, nullptr, 0, 30);
+    launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, reinterpret_cast<double*>(d_rr1_),
+              rr1_stride_ / sizeof(double), 30);
   }
   tend(TK_RR);
   // P and HP (the last search direction and its H image) and W are dead here; so is RP

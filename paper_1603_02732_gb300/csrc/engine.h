@@ -196,6 +196,8 @@ class Engine {
   bool rr_cluster_ = false;          // subspace too large for one CTA: cluster eigensolve
   unsigned char* d_rrc_ = nullptr;   // its per-member global scratch
   size_t rrc_stride_ = 0;
+  unsigned char* d_rr1_ = nullptr;   // one-CTA eigensolve beyond shared memory: global scratch
+  size_t rr1_stride_ = 0;            // bytes per member
   size_t rr_smem_bytes_ = 0;
   double* d_flags_ = nullptr;   // [n][4] gathered per iteration
   // pinned read-back area (device-to-host copies into it do not block the host):

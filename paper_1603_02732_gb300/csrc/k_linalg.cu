@@ -14,6 +14,7 @@
 //  * occupations: Fermi-Dirac with the chemical potential by safeguarded Newton.
 #include <cooperative_groups.h>
 
+#include "ff.cuh"
 #include "kernels.h"
 
 namespace sgo {
@@ -960,15 +961,33 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
 //  6. eps_j = |x_j| + sigma (|x_j| = eps_j - sigma for the unit eigenvector), ascending
 //     ranks, Tm[:, rank(j)] = V[:, j].
 // ---------------------------------------------------------------------------
+// Sums of the Jacobi's column dot products: float-float on the FP32 path (FP64 runs at
+// about 1/64 of the FP32 rate on this GPU), FP64 on the FP64 path; the rotation angles in
+// the working precision.
 template <typename T>
-struct RrTol;
+struct JacSum;
 template <>
-struct RrTol<float> {
-  static constexpr double cosine = 3e-6;  // column-pair cosine below FP32 rounding of the dots
+struct JacSum<float> {
+  using A = ff;
+  static constexpr float cosine = 3e-6f;  // column-pair cosine below which no rotation is made
+  static __device__ __forceinline__ A zero() { return ff(0.f, 0.f); }
+  static __device__ __forceinline__ A prod(float a, float b) {
+    const float p = mul_rn(a, b);
+    return ff(p, fmaf(a, b, -p));
+  }
+  static __device__ __forceinline__ A shfl(A v, int o) {
+    return ff(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+  }
+  static __device__ __forceinline__ float val(A v) { return v.hi + v.lo; }
 };
 template <>
-struct RrTol<double> {
+struct JacSum<double> {
+  using A = double;
   static constexpr double cosine = 1e-13;
+  static __device__ __forceinline__ A zero() { return 0.0; }
+  static __device__ __forceinline__ A prod(double a, double b) { return a * b; }
+  static __device__ __forceinline__ A shfl(A v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  static __device__ __forceinline__ double val(A v) { return v; }
 };
 
 size_t rr_cluster_scratch_bytes(int n, size_t tsize) {
@@ -1015,10 +1034,12 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
   int* pq = pp + npairs;                           // [npairs]
   T* const xbase = reinterpret_cast<T*>(smem_raw + (((size_t)(n + 2 * npairs) * sizeof(T) + 2 * npairs * sizeof(int) +
                                                       15) / 16) * 16);
-  // row r of mine: i = rank + C r
-  auto xrow = [&](int r) -> T* { return rows_smem ? xbase + (size_t)r * n : Dm + (size_t)(rank + C * r) * n; };
+  // row r of mine: i = rank + C r; rows in shared memory have the odd stride n | 1, so that
+  // a warp walking down a column meets distinct banks
+  const int ls = n | 1;
+  auto xrow = [&](int r) -> T* { return rows_smem ? xbase + (size_t)r * ls : Dm + (size_t)(rank + C * r) * n; };
   auto vrow = [&](int r) -> T* {
-    return rows_smem ? xbase + (size_t)(myrows_max + r) * n : Lm + (size_t)(rank + C * r) * n;
+    return rows_smem ? xbase + (size_t)(myrows_max + r) * ls : Lm + (size_t)(rank + C * r) * n;
   };
   double* lam = reinterpret_cast<double*>(xbase);  // [n] (reuses the rows after the Jacobi)
   int* rnk = reinterpret_cast<int*>(lam + n);      // [n]
@@ -1045,12 +1066,14 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
     for (int j = k + 1 + tid; j < n; j += nt) colk[j] = Dm[(size_t)j * n + k] * inv;
     __syncthreads();
     const int r0 = (k + 1 - rank + C - 1) / C > 0 ? (k + 1 - rank + C - 1) / C : 0;  // first my row > k
+    const T* __restrict__ ck = colk;
     for (int r = r0 + warp; r < myrows; r += nwarps) {
       const int i = rank + C * r;
-      const T li = colk[i];
+      const T li = ck[i];
       if (lane == 0) Lm[(size_t)i * n + k] = li;
-      T* Di = Dm + (size_t)i * n;
-      for (int j = k + 1 + lane; j <= i; j += 32) Di[j] -= li * colk[j];
+      T* __restrict__ Di = Dm + (size_t)i * n;
+#pragma unroll 4
+      for (int j = k + 1 + lane; j <= i; j += 32) Di[j] -= li * ck[j];
     }
     cluster.sync();
   }
@@ -1076,18 +1099,29 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
   // 4. W = (I + G) Hf: W_ij = Hf_ij + sum_{k <= i} G_ik Hf_kj
   for (int e = tid; e < myrows * n; e += nt) {
     const int i = rank + C * (e / n), j = e % n;
-    T acc = Hm[(size_t)i * n + j];
-    for (int k = 0; k <= i; ++k) acc += GT[(size_t)k * n + i] * Hm[(size_t)k * n + j];
-    Wm[(size_t)i * n + j] = acc;
+    const T* __restrict__ gi = GT + i;   // G_ik = GT[k][i]
+    const T* __restrict__ hj = Hm + j;   // Hf_kj
+    T acc = hj[(size_t)i * n], acc2 = T(0);
+#pragma unroll 4
+    for (int k = 0; k <= i; k += 2) {
+      acc += gi[(size_t)k * n] * hj[(size_t)k * n];
+      if (k + 1 <= i) acc2 += gi[(size_t)(k + 1) * n] * hj[(size_t)(k + 1) * n];
+    }
+    Wm[(size_t)i * n + j] = acc + acc2;
   }
   cluster.sync();
   //    C = W (I + G)^T: C_ij = W_ij + sum_{k <= j} W_ik G_jk  (into Hm)
   for (int e = tid; e < myrows * n; e += nt) {
     const int i = rank + C * (e / n), j = e % n;
-    const T* Wi = Wm + (size_t)i * n;
-    T acc = Wi[j];
-    for (int k = 0; k <= j; ++k) acc += Wi[k] * GT[(size_t)k * n + j];
-    Hm[(size_t)i * n + j] = acc;
+    const T* __restrict__ Wi = Wm + (size_t)i * n;
+    const T* __restrict__ gj = GT + j;   // G_jk = GT[k][j]
+    T acc = Wi[j], acc2 = T(0);
+#pragma unroll 4
+    for (int k = 0; k <= j; k += 2) {
+      acc += Wi[k] * gj[(size_t)k * n];
+      if (k + 1 <= j) acc2 += Wi[k + 1] * gj[(size_t)(k + 1) * n];
+    }
+    Hm[(size_t)i * n + j] = acc + acc2;
   }
   cluster.sync();
   //    X = sym(C) (into Dm), V = (I + G)^T (into Lm), Gershgorin minimum of my rows
@@ -1146,46 +1180,52 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
         pq[t] = max(pa, pb);
       }
       __syncthreads();
-      double* pr = part + ((size_t)(round & 1) * C + rank) * npairs * 3;
-      for (int t = warp; t < npairs; t += nwarps) {
-        const int a = pp[t], b = pq[t];
-        double al = 0.0, be = 0.0, ga = 0.0;
-        if (b < n)
-          for (int r = lane; r < myrows; r += 32) {
+      using JS = JacSum<T>;
+      using A = typename JS::A;
+      A* pr = reinterpret_cast<A*>(part) + ((size_t)(round & 1) * C + rank) * npairs * 3;
+      // a quad of lanes per pair, each summing a quarter of my rows
+      const int npq = (npairs + 7) / 8 * 8;  // pairs padded so that every warp holds whole quads
+      for (int t4 = tid; t4 < 4 * npq; t4 += nt) {
+        const int t = t4 >> 2, qd = t4 & 3;
+        const bool live = t < npairs && pq[t] < n;
+        const int a = live ? pp[t] : 0, b = live ? pq[t] : 0;
+        A al = JS::zero(), be = JS::zero(), ga = JS::zero();
+        if (live)
+          for (int r = qd; r < myrows; r += 4) {
             const T* xr = xrow(r);
-            const double xa = (double)xr[a], xb = (double)xr[b];
-            al += xa * xa;
-            be += xb * xb;
-            ga += xa * xb;
+            const T xa = xr[a], xb = xr[b];
+            al = al + JS::prod(xa, xa);
+            be = be + JS::prod(xb, xb);
+            ga = ga + JS::prod(xa, xb);
           }
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        for (int o = 1; o < 4; o <<= 1) {
+          al = al + JS::shfl(al, o);
+          be = be + JS::shfl(be, o);
+          ga = ga + JS::shfl(ga, o);
         }
-        if (lane == 0) {
+        if (qd == 0 && t < npairs) {
           pr[3 * t] = al;
           pr[3 * t + 1] = be;
           pr[3 * t + 2] = ga;
         }
       }
       cluster.sync();
-      const double* pb0 = part + (size_t)(round & 1) * C * npairs * 3;
+      const A* pb0 = reinterpret_cast<const A*>(part) + (size_t)(round & 1) * C * npairs * 3;
       for (int t = tid; t < npairs; t += nt) {
-        double al = 0.0, be = 0.0, ga = 0.0;
+        A al = JS::zero(), be = JS::zero(), ga = JS::zero();
         for (int r = 0; r < C; ++r) {
-          const double* q = pb0 + ((size_t)r * npairs + t) * 3;
-          al += q[0];
-          be += q[1];
-          ga += q[2];
+          const A* q = pb0 + ((size_t)r * npairs + t) * 3;
+          al = al + q[0];
+          be = be + q[1];
+          ga = ga + q[2];
         }
+        const T alv = (T)JS::val(al), bev = (T)JS::val(be), gav = (T)JS::val(ga);
         T c = T(1), sn = T(0);
-        if (pq[t] < n && fabs(ga) > RrTol<T>::cosine * sqrt(al * be) && fabs(ga) > 1e-300) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cc = 1.0 / sqrt(1.0 + tt * tt);
-          c = (T)cc;
-          sn = (T)(cc * tt);
+        if (pq[t] < n && fabs(gav) > (T)JS::cosine * sqrt(alv * bev) && gav != T(0)) {
+          const T zeta = (bev - alv) / (T(2) * gav);
+          const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          c = T(1) / sqrt(T(1) + tt * tt);
+          sn = c * tt;
           rot_s = 1;
         }
         csc[t] = c;
@@ -1264,7 +1304,7 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
 static size_t rr_cluster_smem_t(int n, size_t tsize, bool rows_smem) {
   const size_t myrows = (n + RR_CLUSTER - 1) / RR_CLUSTER, npairs = (n + (n & 1)) / 2;
   const size_t head = ((n + 2 * npairs) * tsize + 2 * npairs * sizeof(int) + 15) / 16 * 16;
-  const size_t rows = rows_smem ? 2 * myrows * n * tsize : 0;
+  const size_t rows = rows_smem ? 2 * myrows * (size_t)(n | 1) * tsize : 0;
   const size_t fin = (size_t)n * (sizeof(double) + sizeof(int));
   return head + std::max(rows, fin) + 16;
 }

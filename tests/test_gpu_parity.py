@@ -127,20 +127,24 @@ def test_scf_big_plane_fp64(sgo):
     assert np.abs(rho - ref.rho).max() < 1e-6 * np.abs(ref.rho).max()
 
 
+@pytest.mark.parametrize("rr_cluster", [1, 0])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_scf_cluster_eigensolver(sgo, precision):
+def test_scf_cluster_eigensolver(sgo, precision, rr_cluster):
     """A subspace too large for one CTA's shared memory (112 requested bands, 119 carried):
     the subspace diagonalisation runs on a thread-block cluster of 8 CTAs (Cholesky in
-    deviation form, one-sided Jacobi) in both precisions; SCF energy, occupied eigenvalues
-    and forces against the oracle."""
+    deviation form, one-sided Jacobi; rr_cluster = 1, the default at this size) or on one
+    CTA over a global scratch (rr_cluster = 0), in both precisions; SCF energy, occupied
+    eigenvalues and forces against the oracle."""
     st = _struct(ecut=6.0, nbands=112)
     ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)
     if precision == "fp64":
-        ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=120)
+        ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=120,
+                          rr_cluster=rr_cluster)
         _compare(st, ctx.energy_forces(), ref, 1e-8, 1e-6)
         tol_eig = 1e-7
     else:
-        ctx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7, scf_tol_rho=1e-5, max_scf=120)
+        ctx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7, scf_tol_rho=1e-5, max_scf=120,
+                          rr_cluster=rr_cluster)
         _compare(st, ctx.energy_forces(), ref, 1e-5, 1e-4)
         tol_eig = 2e-4
     eig, _ = ctx.eigen()

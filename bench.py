@@ -468,6 +468,9 @@ def run_ours(args):
         out["accuracy_vs_oracle"] = dict(member=i, dE_per_atom=abs(Fi - ref.free_energy) / pop[i].natoms,
                                          max_dF=float(np.max(np.abs(fi - ref.forces))))
         out["error_ledger"] = _ledger(sgo, pop[i], prec, ref, i)
+    if rank == 0 and not args.no_config5:
+        # the 55-atom cluster (128^3, 330 bands) one structure at a time: mixed and plain FP64
+        out["config5"] = _config_record(sgo, "cluster55", stream)
     if rank == 0 and not args.no_relax:
         out["relax"] = _relax_population(sgo, batch, ctxs, pop, method=args.relax_method)
         out["de_search"] = _de_search(sgo)
@@ -479,17 +482,92 @@ def run_ours(args):
     return 0
 
 
+def _config_record(sgo, name, stream, kernels=True, fp64=True):
+    """One named workload on its own: for the mixed and (fp64) the plain FP64 GPU path, one
+    cold energy + force evaluation timed after a warm-up evaluation (graph-driven SCF loop),
+    its SCF iterations and eigenvector refinement, its errors against the stored oracle
+    ledger where one exists (tests/golden/ledger_<name>.json), and (kernels) for the mixed
+    path the live-timed plane pass, tensor-core GEMMs and subspace eigensolve of one more
+    evaluation with their FP32-peak and tensor fractions."""
+    import torch
+    import workloads
+    st = workloads.CONFIGS[name]()
+    gold = os.path.join(ROOT, "tests", "golden", f"ledger_{name}.json")
+    ref = json.load(open(gold)) if os.path.exists(gold) else None
+    peaks, src = _peaks()
+    res = {}
+    for prec in ("mixed", "fp64") if fp64 else ("mixed",):
+        tol = _tols(prec, st) if name == "diamond8" and prec == "fp64" else _tols("mixed", st)
+        if name == "diamond8":
+            tol.update(mix_alpha=0.7, kerker_q0=0.0)
+        try:
+            ctx = sgo.Context(st, precision=prec, **tol)
+        except sgo.SgoError as e:
+            res[prec] = dict(unavailable=str(e))
+            continue
+        b = sgo.Batch([ctx])
+        b.energy_forces()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        E, F, stat = b.energy_forces()
+        z.record(stream)
+        z.synchronize()
+        ms = a.elapsed_time(z)
+        r = dict(evals_per_s=1e3 / ms, ms_per_eval=ms, status=int(stat[0]), **ctx.stats())
+        eig, occ = ctx.eigen()
+        if ref is not None:
+            oc = np.array(ref["occ"]) > 1e-6
+            r["errors_vs_oracle"] = dict(dF_per_atom=abs(E[0] - ref["free_energy"]) / st.natoms,
+                                         max_dforce=float(np.abs(F[0] - np.array(ref["forces"])).max()),
+                                         max_deig_occupied=float(np.abs(eig - np.array(ref["eig"]))[oc].max()))
+        r["_E"], r["_F"], r["_eig"] = float(E[0]), F[0], eig
+        if prec == "mixed" and kernels:
+            kern = {}
+            for kind in ("plane_vpsi", "gemm_tn", "gemm_nn", "rr"):
+                b.timer(kind)
+                a.record(stream)
+                b.energy_forces()
+                z.record(stream)
+                z.synchronize()
+                t = b.timer_read()
+                tf = t["flops"] / max(t["ms"], 1e-9) / 1e9
+                kern[kind] = dict(ms=t["ms"], launches=t["launches"], share=t["ms"] / a.elapsed_time(z),
+                                  tflops=tf, gbs=t["bytes"] / max(t["ms"], 1e-9) / 1e6)
+                if kind == "plane_vpsi":
+                    kern[kind]["frac_fp32_peak"] = tf / FP32_PEAK_TFLOPS
+                if kind in ("gemm_tn", "gemm_nn"):
+                    if ctx.info()["nbands"] + 4 + ctx.info()["nbands"] // 32 <= 128:
+                        # tcgen05 3xTF32: three tensor MMAs per useful flop, against the TF32
+                        # rate (half the measured BF16 dense rate)
+                        kern[kind]["units"] = "tensor cores (tcgen05, 3xTF32)"
+                        kern[kind]["frac_tf32_tensor_peak"] = 3 * tf / (0.5 * peaks.get("bf16_tflops", 1900.0))
+                    else:
+                        kern[kind]["units"] = "CUDA cores (FP32; the tensor-core GEMMs take up to 128 bands)"
+                        kern[kind]["frac_fp32_peak"] = tf / FP32_PEAK_TFLOPS
+            b.timer(None)
+            r["kernels"] = kern
+        res[prec] = r
+        del b, ctx
+    if "_E" in res.get("mixed", {}) and "_E" in res.get("fp64", {}):
+        m, f = res["mixed"], res["fp64"]
+        res["mixed_vs_fp64"] = dict(dF_per_atom=abs(m["_E"] - f["_E"]) / st.natoms,
+                                    max_dforce=float(np.abs(m["_F"] - f["_F"]).max()),
+                                    max_deig=float(np.abs(m["_eig"] - f["_eig"]).max()),
+                                    speedup=m["evals_per_s"] / f["evals_per_s"])
+    for prec in ("mixed", "fp64"):
+        for k in ("_E", "_F", "_eig"):
+            res.get(prec, {}).pop(k, None)
+    return dict(natoms=st.natoms, nbands=st.nbands, grid=list(st.fft), **res)
+
+
 def run_configs(args):
-    """Per-config measurement (the named workloads one structure at a time): for the
-    mixed and the plain FP64 GPU path, one cold energy + force evaluation timed after a
-    warm-up evaluation (graph-driven SCF loop), its SCF iterations and eigenvector
-    refinement, its errors against the stored oracle ledger where one exists
-    (tests/golden/ledger_<name>.json), and for the mixed path the live-timed plane pass,
-    tensor-core TN GEMM and subspace eigensolve of one more evaluation.  One JSON line."""
+    """Per-config measurement: the named workloads one structure at a time (_config_record).
+    One JSON line per config, then one with all."""
     import torch
     import paper_1603_02732_gb300 as sgo
     from paper_1603_02732_gb300 import build
-    import workloads
     build.build()
     sgo.load_library()
     torch.cuda.set_device(0)
@@ -497,62 +575,7 @@ def run_configs(args):
     names = args.names.split(",") if args.names else ["diamond8", "honeycomb24", "cluster13", "cluster55"]
     out = {}
     for name in names:
-        st = workloads.CONFIGS[name]()
-        gold = os.path.join(ROOT, "tests", "golden", f"ledger_{name}.json")
-        ref = json.load(open(gold)) if os.path.exists(gold) else None
-        res = {}
-        for prec in ("mixed", "fp64"):
-            tol = _tols(prec, st) if name == "diamond8" and prec == "fp64" else _tols("mixed", st)
-            if name == "diamond8":
-                tol.update(mix_alpha=0.7, kerker_q0=0.0)
-            try:
-                ctx = sgo.Context(st, precision=prec, **tol)
-            except sgo.SgoError as e:
-                res[prec] = dict(unavailable=str(e))
-                continue
-            b = sgo.Batch([ctx])
-            b.energy_forces()
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            z = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            E, F, stat = b.energy_forces()
-            z.record(stream)
-            z.synchronize()
-            ms = a.elapsed_time(z)
-            r = dict(evals_per_s=1e3 / ms, ms_per_eval=ms, status=int(stat[0]), **ctx.stats())
-            eig, occ = ctx.eigen()
-            if ref is not None:
-                oc = np.array(ref["occ"]) > 1e-6
-                r["errors_vs_oracle"] = dict(dF_per_atom=abs(E[0] - ref["free_energy"]) / st.natoms,
-                                             max_dforce=float(np.abs(F[0] - np.array(ref["forces"])).max()),
-                                             max_deig_occupied=float(np.abs(eig - np.array(ref["eig"]))[oc].max()))
-            r["_E"], r["_F"] = float(E[0]), F[0]
-            if prec == "mixed":
-                kern = {}
-                for kind in ("plane_vpsi", "gemm_tn", "gemm_nn", "rr"):
-                    b.timer(kind)
-                    a.record(stream)
-                    b.energy_forces()
-                    z.record(stream)
-                    z.synchronize()
-                    t = b.timer_read()
-                    kern[kind] = dict(ms=t["ms"], launches=t["launches"], share=t["ms"] / a.elapsed_time(z),
-                                      tflops=t["flops"] / max(t["ms"], 1e-9) / 1e9,
-                                      gbs=t["bytes"] / max(t["ms"], 1e-9) / 1e6)
-                b.timer(None)
-                kern["plane_vpsi"]["frac_fp32_peak"] = kern["plane_vpsi"]["tflops"] / FP32_PEAK_TFLOPS
-                r["kernels"] = kern
-            res[prec] = r
-            del b, ctx
-        if "_E" in res.get("mixed", {}) and "_E" in res.get("fp64", {}):
-            res["mixed_vs_fp64"] = dict(dF_per_atom=abs(res["mixed"]["_E"] - res["fp64"]["_E"]) / st.natoms,
-                                        max_dforce=float(np.abs(res["mixed"]["_F"] - res["fp64"]["_F"]).max()),
-                                        speedup=res["mixed"]["evals_per_s"] / res["fp64"]["evals_per_s"])
-        for prec in ("mixed", "fp64"):
-            res.get(prec, {}).pop("_E", None)
-            res.get(prec, {}).pop("_F", None)
-        out[name] = dict(natoms=st.natoms, nbands=st.nbands, grid=list(st.fft), **res)
+        out[name] = _config_record(sgo, name, stream)
         print(json.dumps({name: out[name]}), flush=True)
     print(json.dumps(dict(case="configs", results=out)), flush=True)
     return 0
@@ -590,6 +613,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--kernel", default="plane_vpsi", help="kernel class timed live for the roofline")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 GPU path")
+    ap.add_argument("--no-config5", action="store_true", help="skip the 55-atom cluster record")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start (relaxation step) measurement")
     ap.add_argument("--no-relax", action="store_true", help="skip the local-relaxation (PCG) measurement")

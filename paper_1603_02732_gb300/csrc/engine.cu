@@ -830,7 +830,8 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   rr_f32_ = precision_ == 1 && !o0.rr_fp64;
   rr_smem_bytes_ = (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
   rr_smem_ = rr_f32_ ? (size_t)20 * max_nb_ * (max_nb_ | 1) <= 216 * 1024 : rr_smem_bytes_ <= 200 * 1024;
-  rr_cluster_ = o0.rr_cluster > 0 || (o0.rr_cluster < 0 && !rr_smem_);
+  // (the one-CTA kernels' pair tables hold 256 pairs: beyond 512 bands the cluster is used)
+  rr_cluster_ = o0.rr_cluster > 0 || (o0.rr_cluster < 0 && !rr_smem_) || max_nb_ > 512;
   if (rr_cluster_) {
     rrc_stride_ = (rr_cluster_scratch_bytes(max_nb_, rr_f32_ ? sizeof(float) : sizeof(double)) + 255) / 256 * 256;
     if (!cuda_ok(cudaMalloc(&d_rrc_, rrc_stride_ * n_), "cudaMalloc(rr cluster scratch)")) return;

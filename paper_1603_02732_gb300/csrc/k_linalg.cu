@@ -751,6 +751,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch, size_t gstride, int max_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float red[32];
+  __shared__ float dkv[512];  // Cholesky pivots d_k (n <= 512: the pair tables below hold 256 pairs)
   __shared__ float cs_c[256], cs_s[256];
   __shared__ int pr_p[256], pr_q[256];
   __shared__ int flag, nbig;
@@ -774,38 +775,41 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
       G[i * ns + j] = 0.f;
     }
   __syncthreads();
-  // Cholesky in deviation form, right-looking, lower triangle; D_kk holds d_k
+  // Cholesky in deviation form, right-looking, one barrier per column: step k reads the
+  // lower column k (final after step k - 1), writes the scaled column L_ik = D_ik / (1 + d_k)
+  // into the upper row k (D_ki, never read in step k) and updates the lower trailing block
+  // with the scaled values formed on the fly; d_k goes to dkv
   for (int k = 0; k < n; ++k) {
     const float x = D[k * ns + k];
     const float xs = fmaxf(x, -0.999f);
     const float dk = xs / (1.f + sqrtf(1.f + xs));
     const float inv = 1.f / (1.f + dk);
-    for (int i = k + 1 + tid; i < n; i += nt) D[i * ns + k] *= inv;
-    __syncthreads();
     if (tid == 0) {
       if (!(x > -0.999f)) flag = 1;  // S not positive definite (to FP32 resolution)
-      D[k * ns + k] = dk;
+      dkv[k] = dk;
     }
+    for (int i = k + 1 + tid; i < n; i += nt) D[k * ns + i] = D[i * ns + k] * inv;
     for (int i = k + 1 + ty; i < n; i += nty) {
-      const float lik = D[i * ns + k];
-      for (int j = k + 1 + tx; j <= i; j += 32) D[i * ns + j] -= lik * D[j * ns + k];
+      const float lik = D[i * ns + k] * inv;
+      for (int j = k + 1 + tx; j <= i; j += 32) D[i * ns + j] -= lik * (D[j * ns + k] * inv);
     }
     __syncthreads();
   }
-  // G: G_ii = -d_i / (1 + d_i), G_ij = -(D_ij + sum_{j<=k<i} D_ik G_kj) / (1 + d_i); rows in
-  // order, one warp per column j, lanes splitting the sum
-  for (int i = 0; i < n; ++i) {
-    const float di = D[i * ns + i];
-    const float inv = 1.f / (1.f + di);
-    for (int j = ty; j < i; j += nty) {
-      float s = 0.f;
-      for (int k = j + tx; k < i; k += 32) s += D[i * ns + k] * G[k * ns + j];
-      s = warp_sum_f(s);
-      if (tx == 0) G[i * ns + j] = -(D[i * ns + j] + s) * inv;
+  // G: G_ii = -d_i / (1 + d_i), G_ij = -(L_ij + sum_{j<=k<i} L_ik G_kj) / (1 + d_i) with
+  // L_ik = D_ki; every column j of G is an independent forward substitution: one warp per
+  // column, lanes splitting the sum, no block barrier until all columns are done
+  for (int j = ty; j < n; j += nty) {
+    if (tx == 0) G[j * ns + j] = -dkv[j] / (1.f + dkv[j]);
+    __syncwarp();
+    for (int i = j + 1; i < n; ++i) {
+      float sacc = 0.f;
+      for (int k = j + tx; k < i; k += 32) sacc += D[k * ns + i] * G[k * ns + j];
+      sacc = warp_sum_f(sacc);
+      if (tx == 0) G[i * ns + j] = -(D[j * ns + i] + sacc) / (1.f + dkv[i]);
+      __syncwarp();
     }
-    if (tid == 0) G[i * ns + i] = -di * inv;
-    __syncthreads();
   }
+  __syncthreads();
   // W = (I + G) Hf, A = W (I + G)^T
   for (int i = ty; i < n; i += nty)
     for (int j = tx; j < n; j += 32) {

@@ -614,6 +614,9 @@ def main():
     ap.add_argument("--kernel", default="plane_vpsi", help="kernel class timed live for the roofline")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-config5", action="store_true", help="skip the 55-atom cluster record")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven SCF loop instead of the captured graphs (for per-kernel profilers, "
+                         "which cannot look inside graphs with conditional nodes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start (relaxation step) measurement")
     ap.add_argument("--no-relax", action="store_true", help="skip the local-relaxation (PCG) measurement")
@@ -633,6 +636,8 @@ def main():
     for k, v in (("ncg", args.ncg), ("ncg_first", args.ncg_first), ("n_nonscf", args.nonscf)):
         if v is not None:
             _SCF[k] = v
+    if args.no_graph:
+        _SCF["graph"] = 0
     if args.impl == "reference":
         return run_reference(args)
     if args.case == "configs":

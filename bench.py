@@ -632,8 +632,10 @@ def main():
     ap.add_argument("--ncg", type=int, default=None, help="CG steps per SCF iteration")
     ap.add_argument("--ncg-first", type=int, default=None)
     ap.add_argument("--nonscf", type=int, default=None)
+    ap.add_argument("--extra-bands", type=int, default=None, help="headroom bands (default: the library's)")
     args = ap.parse_args()
-    for k, v in (("ncg", args.ncg), ("ncg_first", args.ncg_first), ("n_nonscf", args.nonscf)):
+    for k, v in (("ncg", args.ncg), ("ncg_first", args.ncg_first), ("n_nonscf", args.nonscf),
+                 ("extra_bands", args.extra_bands)):
         if v is not None:
             _SCF[k] = v
     if args.no_graph:

@@ -34,6 +34,8 @@
 #ifndef SGO_H
 #define SGO_H
 
+#include <stddef.h>
+
 #if defined(__GNUC__)
 #define SGO_API __attribute__((visibility("default")))
 #else
@@ -124,6 +126,19 @@ typedef struct {
                              matrices do not fit); 1 = always the cluster.  Taken from the first
                              member of a batch. */
 } sgo_opts;
+
+/* Device memory through the caller's allocator.  The library's device buffers (context
+ * arenas, batch tables and scratch, the temporaries of the component calls) come from
+ * alloc(bytes, stream, user), which returns a device pointer or NULL, and go back through
+ * release(ptr, stream, user) -- for instance PyTorch's caching allocator, so that the
+ * library's memory is part of the caller's pool and its budget (the binding's
+ * use_torch_allocator()).  Process-wide; contexts and batches created after the call use it;
+ * every block is returned to the allocator that gave it, after a device synchronisation.
+ * alloc = release = NULL restores cudaMalloc/cudaFree.  SGO_ERR_ARG if exactly one is NULL.
+ * Pinned host buffers stay cudaMallocHost. */
+typedef void* (*sgo_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*sgo_free_fn)(void* ptr, void* stream, void* user);
+SGO_API sgo_status sgo_set_allocator(sgo_alloc_fn alloc, sgo_free_fn release, void* user);
 
 /* Fill *o with the defaults (FP64, kT 0, tolerances 1e-8 Ha / 1e-7, Pulay 8, ...). */
 SGO_API void sgo_opts_default(sgo_opts* o);

@@ -112,9 +112,12 @@ class sgo_opts(ctypes.Structure):
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 _vp = ctypes.c_void_p
+_alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
 _SIGS = {
     "sgo_opts_default": (None, [ctypes.POINTER(sgo_opts)]),
+    "sgo_set_allocator": (ctypes.c_int, [_alloc_fn, _free_fn, _vp]),
     "sgo_create": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.POINTER(sgo_species), ctypes.c_int, _ip, _dp,
                                   ctypes.c_double, ctypes.c_int, ctypes.POINTER(sgo_opts), _vp,
                                   ctypes.POINTER(_vp)]),
@@ -200,6 +203,43 @@ def _current_stream():
     except Exception:  # torch is plumbing only
         pass
     return None
+
+
+_allocator_refs = None  # the installed callbacks (ctypes must keep them alive)
+
+
+def use_torch_allocator():
+    """Route the library's device memory through PyTorch's caching allocator: contexts and
+    batches created afterwards take their buffers from torch's pool (they count in
+    torch.cuda.memory_allocated() and obey its memory fraction), and their buffers go back to
+    it when they are destroyed.  Undo with use_default_allocator()."""
+    global _allocator_refs
+    import torch
+
+    def alloc(nbytes, stream, _user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+        except RuntimeError:  # out of memory: the library reports SGO_ERR_CUDA
+            return None
+
+    def release(ptr, _stream, _user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    refs = (_alloc_fn(alloc), _free_fn(release))
+    _check(load_library().sgo_set_allocator(refs[0], refs[1], None), "sgo_set_allocator")
+    _allocator_refs = refs
+
+
+def use_default_allocator():
+    """Back to cudaMalloc/cudaFree for new buffers (blocks from torch's pool still go back to
+    it; keep torch's callbacks alive until every context made under them is destroyed)."""
+    global _allocator_refs
+    _check(load_library().sgo_set_allocator(_alloc_fn(), _free_fn(), None), "sgo_set_allocator")
+    _retired.append(_allocator_refs)
+    _allocator_refs = None
+
+
+_retired = []
 
 
 def default_opts(**kw) -> sgo_opts:

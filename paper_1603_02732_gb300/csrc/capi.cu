@@ -86,6 +86,15 @@ sgo_status run_batch(sgo_batch* b, const sgo::Engine::DeviceIO* io, std::vector<
 
 extern "C" {
 
+sgo_status sgo_set_allocator(sgo_alloc_fn alloc, sgo_free_fn release, void* user) {
+  if ((alloc == nullptr) != (release == nullptr)) {
+    sgo::set_error("sgo_set_allocator needs both functions or neither");
+    return SGO_ERR_ARG;
+  }
+  sgo::set_allocator(alloc, release, user);
+  return SGO_OK;
+}
+
 void sgo_opts_default(sgo_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));

@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "engine.h"
 
@@ -19,6 +21,71 @@ bool cuda_ok(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return true;
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return false;
+}
+
+// ---- device memory: cudaMalloc, or the caller's allocator (sgo_set_allocator) ----
+namespace {
+std::mutex g_alloc_mu;
+sgo_alloc_fn g_alloc_fn = nullptr;
+sgo_free_fn g_free_fn = nullptr;
+void* g_alloc_user = nullptr;
+struct Hooked {
+  sgo_free_fn release;
+  void* user;
+};
+// every block the caller's allocator gave, with the release function it came with (the
+// hook may change between a context's creation and its destruction)
+std::unordered_map<void*, Hooked>& hooked() {
+  static std::unordered_map<void*, Hooked> m;
+  return m;
+}
+}  // namespace
+
+void set_allocator(sgo_alloc_fn a, sgo_free_fn f, void* user) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc_fn = a;
+  g_free_fn = f;
+  g_alloc_user = user;
+}
+
+cudaError_t dev_malloc_bytes(void** p, size_t bytes, cudaStream_t s) {
+  sgo_alloc_fn a;
+  sgo_free_fn f;
+  void* user;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    a = g_alloc_fn;
+    f = g_free_fn;
+    user = g_alloc_user;
+  }
+  if (!a) return cudaMalloc(p, bytes);
+  *p = a(bytes ? bytes : 1, s, user);
+  if (!*p) return cudaErrorMemoryAllocation;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  hooked()[*p] = Hooked{f, user};
+  return cudaSuccess;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  Hooked h{nullptr, nullptr};
+  bool found = false;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    auto it = hooked().find(p);
+    if (it != hooked().end()) {
+      h = it->second;
+      found = true;
+      hooked().erase(it);
+    }
+  }
+  if (!found) {
+    cudaFree(p);
+    return;
+  }
+  // the caller's pool may hand the block out again at once: no kernel may still use it
+  cudaDeviceSynchronize();
+  if (h.release) h.release(p, nullptr, h.user);
 }
 
 #define CK(x)                                  \
@@ -420,7 +487,7 @@ sgo_status ctx_setup(sgo_ctx* c) {
   // ---- phase 1: basis enumeration on the device ----
   c->box_cols = (2 * box[0] + 1) * (2 * box[1] + 1);
   const size_t setup_bytes = (size_t)4 * c->box_cols * sizeof(int) + 64 + 4 * 256;
-  CK(cudaMalloc(&c->arena_setup, setup_bytes));
+  CK(dev_malloc(&c->arena_setup, setup_bytes));
   {
     Arena a;
     a.base = c->arena_setup;
@@ -433,9 +500,9 @@ sgo_status ctx_setup(sgo_ctx* c) {
   Prob* dprob = nullptr;
   int* dstart = nullptr;
   int* dact = nullptr;
-  CK(cudaMalloc(&dprob, sizeof(Prob)));
-  CK(cudaMalloc(&dstart, 2 * sizeof(int)));
-  CK(cudaMalloc(&dact, sizeof(int)));
+  CK(dev_malloc(&dprob, sizeof(Prob)));
+  CK(dev_malloc(&dstart, 2 * sizeof(int)));
+  CK(dev_malloc(&dact, sizeof(int)));
   const int one = 1;
   const int nbc = div_up(c->box_cols, 128);
   int st[2] = {0, nbc};
@@ -461,16 +528,16 @@ sgo_status ctx_setup(sgo_ctx* c) {
   d.ld = (d.npw + 31) / 32 * 32;
   d.ncol = 2 * d.ncp - 1;
   if (4 * d.m1max + 1 > d.n1 || 4 * d.m2max + 1 > d.n2 || 4 * d.m3max + 1 > d.n3) {
-    cudaFree(dprob);
-    cudaFree(dstart);
-    cudaFree(dact);
+    dev_free(dprob);
+    dev_free(dstart);
+    dev_free(dact);
     set_error("FFT grid aliases: need N_i >= 4 m_max,i + 1");
     return SGO_ERR_ARG;
   }
   if (c->nb > d.npw) {
-    cudaFree(dprob);
-    cudaFree(dstart);
-    cudaFree(dact);
+    dev_free(dprob);
+    dev_free(dstart);
+    dev_free(dact);
     set_error("more bands than plane waves");
     return SGO_ERR_ARG;
   }
@@ -483,11 +550,11 @@ sgo_status ctx_setup(sgo_ctx* c) {
   // ---- phase 2: allocation ----
   Counter cnt;
   layout(c, cnt);
-  cudaError_t e = cudaMalloc(&c->arena_main, cnt.used + 256);
+  cudaError_t e = dev_malloc(&c->arena_main, cnt.used + 256);
   if (e != cudaSuccess) {
-    cudaFree(dprob);
-    cudaFree(dstart);
-    cudaFree(dact);
+    dev_free(dprob);
+    dev_free(dstart);
+    dev_free(dact);
     set_error(std::string("device allocation failed: ") + cudaGetErrorString(e));
     return SGO_ERR_OOM;
   }
@@ -512,9 +579,9 @@ sgo_status ctx_setup(sgo_ctx* c) {
   launch_vloc_table(L2);
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaGetLastError());
-  cudaFree(dprob);
-  cudaFree(dstart);
-  cudaFree(dact);
+  dev_free(dprob);
+  dev_free(dstart);
+  dev_free(dact);
   c->h_scal.assign(NSCAL_ALL, 0.0);
   c->h_eps.assign(d.nb, 0.0);
   c->h_occ.assign(d.nb, 0.0);
@@ -525,8 +592,8 @@ sgo_status ctx_setup(sgo_ctx* c) {
 }  // namespace sgo
 
 sgo_ctx::~sgo_ctx() {
-  if (arena_setup) cudaFree(arena_setup);
-  if (arena_main) cudaFree(arena_main);
+  if (arena_setup) sgo::dev_free(arena_setup);
+  if (arena_main) sgo::dev_free(arena_main);
 }
 
 namespace sgo {
@@ -559,7 +626,7 @@ WorkMap Engine::make_map(const std::vector<int>& counts) {
     m.max_nb = std::max(m.max_nb, d.nb);
   }
   int* d = nullptr;
-  if (!cuda_ok(cudaMalloc(&d, st.size() * sizeof(int)), "cudaMalloc(map)")) return m;
+  if (!cuda_ok(dev_malloc(&d, st.size() * sizeof(int)), "dev_malloc(map)")) return m;
   cudaMemcpy(d, st.data(), st.size() * sizeof(int), cudaMemcpyHostToDevice);
   allocs_.push_back(d);
   m.start = d;
@@ -769,20 +836,20 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   }
   part_stride_ = part;
   build_gemm_maps();
-  if (!cuda_ok(cudaMalloc(&d_probs_, sizeof(Prob) * n_), "cudaMalloc(probs)")) return;
+  if (!cuda_ok(dev_malloc(&d_probs_, sizeof(Prob) * n_), "dev_malloc(probs)")) return;
   allocs_.push_back(d_probs_);
   cudaMemcpy(d_probs_, host.data(), sizeof(Prob) * n_, cudaMemcpyHostToDevice);
-  if (!cuda_ok(cudaMalloc(&d_active_, sizeof(int) * n_), "cudaMalloc(active)")) return;
+  if (!cuda_ok(dev_malloc(&d_active_, sizeof(int) * n_), "dev_malloc(active)")) return;
   allocs_.push_back(d_active_);
   h_active_.assign(n_, 1);
   cudaMemcpy(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice);
-  if (!cuda_ok(cudaMalloc(&d_part_, sizeof(double) * part_stride_ * n_), "cudaMalloc(part)")) return;
+  if (!cuda_ok(dev_malloc(&d_part_, sizeof(double) * part_stride_ * n_), "dev_malloc(part)")) return;
   allocs_.push_back(d_part_);
-  if (!cuda_ok(cudaMalloc(&d_gpart_, sizeof(double) * (size_t)maxchunk_ * n_ * 8), "cudaMalloc(gpart)")) return;
+  if (!cuda_ok(dev_malloc(&d_gpart_, sizeof(double) * (size_t)maxchunk_ * n_ * 8), "dev_malloc(gpart)")) return;
   allocs_.push_back(d_gpart_);
-  if (!cuda_ok(cudaMalloc(&d_flags_, sizeof(double) * 4 * n_), "cudaMalloc(flags)")) return;
+  if (!cuda_ok(dev_malloc(&d_flags_, sizeof(double) * 4 * n_), "dev_malloc(flags)")) return;
   allocs_.push_back(d_flags_);
-  if (!cuda_ok(cudaMalloc(&d_iter_, 2 * sizeof(int)), "cudaMalloc(iter)")) return;
+  if (!cuda_ok(dev_malloc(&d_iter_, 2 * sizeof(int)), "dev_malloc(iter)")) return;
   allocs_.push_back(d_iter_);
   if (tc) {
     // TMA descriptors of every operand buffer (fixed for the engine's life; role swaps
@@ -791,11 +858,11 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     std::vector<unsigned char> hm(per * n_);
     for (int p = 0; p < n_; ++p)
       if (!tc_encode_maps(host[p], hm.data() + per * p)) return;
-    if (!cuda_ok(cudaMalloc(&d_tmaps_, hm.size()), "cudaMalloc(tensor maps)")) return;
+    if (!cuda_ok(dev_malloc(&d_tmaps_, hm.size()), "dev_malloc(tensor maps)")) return;
     allocs_.push_back(d_tmaps_);
     cudaMemcpy(d_tmaps_, hm.data(), hm.size(), cudaMemcpyHostToDevice);
     nnimg_stride_ = (size_t)(*std::max_element(nnimg_max_, nnimg_max_ + 3) + 1023) / 1024 * 256;  // floats
-    if (!cuda_ok(cudaMalloc(&d_nnimg_, sizeof(float) * nnimg_stride_ * n_), "cudaMalloc(nn image)")) return;
+    if (!cuda_ok(dev_malloc(&d_nnimg_, sizeof(float) * nnimg_stride_ * n_), "dev_malloc(nn image)")) return;
     allocs_.push_back(d_nnimg_);
   }
   {
@@ -810,7 +877,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     std::memset(hp_, 0, sizeof(double) * nd);
     if (!cuda_ok(cudaMallocHost(&hpi_, sizeof(int) * (2 + 4 * (size_t)n_)), "cudaMallocHost(read-back)")) return;
     std::memset(hpi_, 0, sizeof(int) * (2 + 4 * (size_t)n_));
-    if (!cuda_ok(cudaMalloc(&d_slot_, sizeof(int) * 2 * n_), "cudaMalloc(slots)")) return;
+    if (!cuda_ok(dev_malloc(&d_slot_, sizeof(int) * 2 * n_), "dev_malloc(slots)")) return;
     allocs_.push_back(d_slot_);
     d_foff_ = d_slot_ + n_;
     std::vector<int> slot(n_), foff(n_);
@@ -834,11 +901,11 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   rr_cluster_ = o0.rr_cluster > 0 || (o0.rr_cluster < 0 && !rr_smem_) || max_nb_ > 512;
   if (rr_cluster_) {
     rrc_stride_ = (rr_cluster_scratch_bytes(max_nb_, rr_f32_ ? sizeof(float) : sizeof(double)) + 255) / 256 * 256;
-    if (!cuda_ok(cudaMalloc(&d_rrc_, rrc_stride_ * n_), "cudaMalloc(rr cluster scratch)")) return;
+    if (!cuda_ok(dev_malloc(&d_rrc_, rrc_stride_ * n_), "dev_malloc(rr cluster scratch)")) return;
     allocs_.push_back(d_rrc_);
   } else if (!rr_smem_) {  // one CTA over a global scratch
     rr1_stride_ = rr_f32_ ? (size_t)5 * max_nb_ * (max_nb_ | 1) * sizeof(float) : (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
-    if (!cuda_ok(cudaMalloc(&d_rr1_, rr1_stride_ * n_), "cudaMalloc(rr scratch)")) return;
+    if (!cuda_ok(dev_malloc(&d_rr1_, rr1_stride_ * n_), "dev_malloc(rr scratch)")) return;
     allocs_.push_back(d_rr1_);
   }
   fft_set_smem_limits(220 * 1024);
@@ -862,7 +929,7 @@ Engine::~Engine() {
   if (hp_) cudaFreeHost(hp_);
   if (hpi_) cudaFreeHost(hpi_);
   for (auto& v : ev_) cudaEventDestroy(v);
-  for (void* p : allocs_) cudaFree(p);
+  for (void* p : allocs_) dev_free(p);
 }
 
 // ---- live kernel timing ----
@@ -1563,9 +1630,9 @@ sgo_status Engine::apply_h(const double* veff_c, int nvec, const double* psi, do
   sgo_ctx* c = ctx_[0];
   const Prob& d = c->d;
   double *dv = nullptr, *dpsi = nullptr, *dout = nullptr;
-  CK(cudaMalloc(&dv, sizeof(double) * d.ngrid));
-  CK(cudaMalloc(&dpsi, sizeof(double) * (size_t)nvec * d.npw));
-  CK(cudaMalloc(&dout, sizeof(double) * (size_t)nvec * d.npw));
+  CK(dev_malloc(&dv, sizeof(double) * d.ngrid));
+  CK(dev_malloc(&dpsi, sizeof(double) * (size_t)nvec * d.npw));
+  CK(dev_malloc(&dout, sizeof(double) * (size_t)nvec * d.npw));
   CK(cudaMemcpyAsync(dv, veff_c, sizeof(double) * d.ngrid, cudaMemcpyHostToDevice, stream_));
   CK(cudaMemcpyAsync(dpsi, psi, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyHostToDevice, stream_));
   h_active_.assign(n_, 1);
@@ -1585,9 +1652,9 @@ sgo_status Engine::apply_h(const double* veff_c, int nvec, const double* psi, do
   CK(cudaMemcpyAsync(hpsi_out, dout, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyDeviceToHost, stream_));
   CK(cudaStreamSynchronize(stream_));
   CK(cudaGetLastError());
-  cudaFree(dv);
-  cudaFree(dpsi);
-  cudaFree(dout);
+  dev_free(dv);
+  dev_free(dpsi);
+  dev_free(dout);
   return SGO_OK;
 }
 
@@ -1595,9 +1662,9 @@ sgo_status Engine::density(int nvec, const double* psi, const double* occ, doubl
   sgo_ctx* c = ctx_[0];
   const Prob& d = c->d;
   double *dpsi = nullptr, *docc = nullptr, *dr = nullptr;
-  CK(cudaMalloc(&dpsi, sizeof(double) * (size_t)nvec * d.npw));
-  CK(cudaMalloc(&docc, sizeof(double) * d.nb));
-  CK(cudaMalloc(&dr, sizeof(double) * d.ngrid));
+  CK(dev_malloc(&dpsi, sizeof(double) * (size_t)nvec * d.npw));
+  CK(dev_malloc(&docc, sizeof(double) * d.nb));
+  CK(dev_malloc(&dr, sizeof(double) * d.ngrid));
   std::vector<double> o(d.nb, 0.0);
   for (int i = 0; i < nvec; ++i) o[i] = occ[i];
   CK(cudaMemcpyAsync(dpsi, psi, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyHostToDevice, stream_));
@@ -1623,9 +1690,9 @@ sgo_status Engine::density(int nvec, const double* psi, const double* occ, doubl
   CK(cudaMemcpyAsync(rho, dr, sizeof(double) * d.ngrid, cudaMemcpyDeviceToHost, stream_));
   CK(cudaStreamSynchronize(stream_));
   CK(cudaGetLastError());
-  cudaFree(dpsi);
-  cudaFree(docc);
-  cudaFree(dr);
+  dev_free(dpsi);
+  dev_free(docc);
+  dev_free(dr);
   return SGO_OK;
 }
 
@@ -1633,8 +1700,8 @@ sgo_status Engine::subspace(int nvec, const double* x, const double* y, double* 
   sgo_ctx* c = ctx_[0];
   const Prob& d = c->d;
   double *dx = nullptr, *dy = nullptr;
-  CK(cudaMalloc(&dx, sizeof(double) * (size_t)nvec * d.npw));
-  CK(cudaMalloc(&dy, sizeof(double) * (size_t)nvec * d.npw));
+  CK(dev_malloc(&dx, sizeof(double) * (size_t)nvec * d.npw));
+  CK(dev_malloc(&dy, sizeof(double) * (size_t)nvec * d.npw));
   CK(cudaMemcpyAsync(dx, x, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyHostToDevice, stream_));
   CK(cudaMemcpyAsync(dy, y, sizeof(double) * (size_t)nvec * d.npw, cudaMemcpyHostToDevice, stream_));
   h_active_.assign(n_, 1);
@@ -1654,8 +1721,8 @@ sgo_status Engine::subspace(int nvec, const double* x, const double* y, double* 
   CK(cudaGetLastError());
   for (int i = 0; i < nvec; ++i)
     for (int j = 0; j < nvec; ++j) c_out[(size_t)i * nvec + j] = s[(size_t)i * d.nb + j];
-  cudaFree(dx);
-  cudaFree(dy);
+  dev_free(dx);
+  dev_free(dy);
   return SGO_OK;
 }
 
@@ -1664,8 +1731,8 @@ sgo_status Engine::block_update(int nvec, const double* x, const double* m, doub
   const Prob& d = c->d;
   const size_t nbytes = sizeof(double) * (size_t)nvec * d.npw;
   double *dx = nullptr, *dy = nullptr;
-  CK(cudaMalloc(&dx, nbytes));
-  CK(cudaMalloc(&dy, nbytes));
+  CK(dev_malloc(&dx, nbytes));
+  CK(dev_malloc(&dy, nbytes));
   std::vector<double> tm((size_t)d.nb * d.nb, 0.0);
   for (int i = 0; i < nvec; ++i)
     for (int j = 0; j < nvec; ++j) tm[(size_t)i * d.nb + j] = m[(size_t)i * nvec + j];
@@ -1688,21 +1755,21 @@ sgo_status Engine::block_update(int nvec, const double* x, const double* m, doub
   CK(cudaMemcpyAsync(y, dy, nbytes, cudaMemcpyDeviceToHost, stream_));
   CK(cudaStreamSynchronize(stream_));
   CK(cudaGetLastError());
-  cudaFree(dx);
-  cudaFree(dy);
+  dev_free(dx);
+  dev_free(dy);
   return SGO_OK;
 }
 
 sgo_status Engine::export_density(double* rho) {
   const Prob& d = ctx_[0]->d;
   double* dr = nullptr;
-  CK(cudaMalloc(&dr, sizeof(double) * d.ngrid));
+  CK(dev_malloc(&dr, sizeof(double) * d.ngrid));
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   launch_export_grid(L(m_gew_), 1, dr);
   CK(cudaMemcpyAsync(rho, dr, sizeof(double) * d.ngrid, cudaMemcpyDeviceToHost, stream_));
   CK(cudaStreamSynchronize(stream_));
-  cudaFree(dr);
+  dev_free(dr);
   return SGO_OK;
 }
 
@@ -1712,7 +1779,7 @@ sgo_status Engine::export_state(double* rho_g, double* psi) {
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   char* dbuf = nullptr;
-  CK(cudaMalloc(&dbuf, gbytes + pbytes));
+  CK(dev_malloc(&dbuf, gbytes + pbytes));
   double2* dg = reinterpret_cast<double2*>(dbuf);
   double* dp = reinterpret_cast<double*>(dbuf + gbytes);
   if (rho_g) {
@@ -1726,7 +1793,7 @@ sgo_status Engine::export_state(double* rho_g, double* psi) {
     CK(cudaMemcpyAsync(psi, dp, pbytes, cudaMemcpyDeviceToHost, stream_));
   }
   CK(cudaStreamSynchronize(stream_));
-  cudaFree(dbuf);
+  dev_free(dbuf);
   return cuda_ok(cudaGetLastError(), "export state") ? SGO_OK : SGO_ERR_CUDA;
 }
 
@@ -1736,7 +1803,7 @@ sgo_status Engine::import_state(const double* rho_g, const double* psi) {
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   char* dbuf = nullptr;
-  CK(cudaMalloc(&dbuf, gbytes + pbytes));
+  CK(dev_malloc(&dbuf, gbytes + pbytes));
   double2* dg = reinterpret_cast<double2*>(dbuf);
   double* dp = reinterpret_cast<double*>(dbuf + gbytes);
   CK(cudaMemcpyAsync(dg, rho_g, gbytes, cudaMemcpyHostToDevice, stream_));
@@ -1753,7 +1820,7 @@ sgo_status Engine::import_state(const double* rho_g, const double* psi) {
     launch_copy_in<double>(L(m_bands_), WB_X, dp, d.nbo, true);
   }
   CK(cudaStreamSynchronize(stream_));
-  cudaFree(dbuf);
+  dev_free(dbuf);
   return cuda_ok(cudaGetLastError(), "import state") ? SGO_OK : SGO_ERR_CUDA;
 }
 
@@ -1761,7 +1828,7 @@ sgo_status Engine::grid_transform(int sign, const double* in, double* out) {
   const Prob& d = ctx_[0]->d;
   const size_t bytes = sizeof(double2) * (size_t)d.ngrid;
   double2* dg = nullptr;
-  CK(cudaMalloc(&dg, bytes));
+  CK(dev_malloc(&dg, bytes));
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   CK(cudaMemcpyAsync(dg, in, bytes, cudaMemcpyHostToDevice, stream_));
@@ -1770,7 +1837,7 @@ sgo_status Engine::grid_transform(int sign, const double* in, double* out) {
   launch_grid_copy_c(L(m_gew_), nullptr, dg);
   CK(cudaMemcpyAsync(out, dg, bytes, cudaMemcpyDeviceToHost, stream_));
   CK(cudaStreamSynchronize(stream_));
-  cudaFree(dg);
+  dev_free(dg);
   return cuda_ok(cudaGetLastError(), "grid transform") ? SGO_OK : SGO_ERR_CUDA;
 }
 

@@ -245,6 +245,19 @@ struct PlanePaths {
 };
 PlanePaths plane_paths(const Prob& d, int precision);
 
+// Device memory of the library: cudaMalloc, or the caller's allocator when one is installed
+// (sgo_set_allocator); dev_free returns a block to whichever allocator gave it.
+void set_allocator(sgo_alloc_fn a, sgo_free_fn f, void* user);
+cudaError_t dev_malloc_bytes(void** p, size_t bytes, cudaStream_t s = nullptr);
+template <typename P>
+cudaError_t dev_malloc(P** p, size_t bytes, cudaStream_t s = nullptr) {
+  void* v = nullptr;
+  const cudaError_t e = dev_malloc_bytes(&v, bytes, s);
+  *p = static_cast<P*>(v);
+  return e;
+}
+void dev_free(void* p);
+
 // Context set-up (basis on the device, allocation, tables).  Returns status.
 sgo_status ctx_setup(sgo_ctx* c);
 sgo_status set_positions(sgo_ctx* c, const double* pos);

@@ -57,6 +57,10 @@ def test_host_only_calls(lib):
     assert lib.sgo_create(None, 1, None, 1, None, None, 1.0, 1, None, None, ctypes.byref(out)) == pkg.SGO_ERR_ARG
     assert lib.sgo_scf(None, None, None, None) == pkg.SGO_ERR_ARG
     assert lib.sgo_batch_create(0, None, ctypes.byref(out)) == pkg.SGO_ERR_ARG
+    # the allocator hook wants both functions or neither; neither restores cudaMalloc
+    keep = pkg._alloc_fn(lambda n, s, u: None)
+    assert lib.sgo_set_allocator(keep, pkg._free_fn(), None) == pkg.SGO_ERR_ARG
+    assert lib.sgo_set_allocator(pkg._alloc_fn(), pkg._free_fn(), None) == pkg.SGO_OK
 
 
 def test_product_path_has_no_oracle_import():

@@ -269,6 +269,45 @@ def test_watchdog_expiry_is_reported(sgo):
     assert math.isfinite(F) and np.all(np.isfinite(f))
 
 
+def test_torch_allocator_hook(sgo):
+    """sgo_set_allocator: with PyTorch's caching allocator installed, every device buffer of a
+    context and of its evaluation comes from torch's pool (torch.cuda.memory_allocated() rises
+    while the context lives and falls back to where it was when it is destroyed), and the
+    results equal those of a context on cudaMalloc memory."""
+    import gc
+
+    import torch
+    st = _struct()
+    ref = {p: sgo.Context(st, precision=p, scf_tol_e=1e-8, scf_tol_rho=1e-7).energy_forces()
+           for p in ("fp64", "mixed")}
+    torch.cuda.synchronize()
+    gc.collect()
+    base = torch.cuda.memory_allocated()
+    sgo.use_torch_allocator()
+    try:
+        ctxs = [sgo.Context(st, precision=p, scf_tol_e=1e-8, scf_tol_rho=1e-7) for p in ("fp64", "mixed")]
+        held = torch.cuda.memory_allocated() - base
+        assert held > 0
+        for c, p in zip(ctxs, ("fp64", "mixed")):
+            E, F = c.energy_forces()
+            assert abs(E - ref[p][0]) < 1e-10 and np.abs(F - ref[p][1]).max() < 1e-9, p
+        E, F, status = sgo.Batch(ctxs).energy_forces()
+        assert np.all(status == 0)
+        gc.collect()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() - base >= held
+        del ctxs, E, F, status
+        gc.collect()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == base
+    finally:
+        sgo.use_default_allocator()
+    # contexts made afterwards are on cudaMalloc again
+    c = sgo.Context(st, precision="fp64", scf_tol_e=1e-8, scf_tol_rho=1e-7)
+    assert torch.cuda.memory_allocated() == base
+    assert abs(c.energy_forces()[0] - ref["fp64"][0]) < 1e-10
+
+
 def test_autograd_adjoint(sgo):
     import torch
     st = _struct(ecut=3.0)

@@ -457,6 +457,8 @@ def run_ours(args):
                                 max_abs_dforce_mixed_vs_fp64=float(max(np.abs(a - b).max() for a, b in zip(F, F64))))
         out["vs_fp64_gpu"] = out["fp64_path"]["speedup_mixed_over_fp64"]
         del b64, ctx64
+    if not args.no_variants and rank == 0:
+        out["eigensolver_variants"] = _variant_record(sgo, pop, pos_host, E, F, args)
     if rank == 0 and not args.no_warm:
         out["warm"] = _warm_steps(args, sgo, batch, ctxs, pop, pos_host, pos_dev, e_dev, f_dev, s_dev, stream)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -482,7 +484,38 @@ def run_ours(args):
     return 0
 
 
-def _config_record(sgo, name, stream, kernels=True, fp64=True):
+def _variant_record(sgo, pop, pos_host, E, F, args):
+    """The block Davidson eigensolver (2 n_b Rayleigh-Ritz over [X, W] per step) against
+    Algorithm 1's all-band CG on the same population, precision and stopping rule: evals/s
+    through the host-pointer call, SCF iterations, Jacobi sweeps per Rayleigh-Ritz call and
+    the spread of the results between the two."""
+    import torch
+    rec = {}
+    nat = np.array([st.natoms for st in pop])
+    for name, extra in (("davidson", dict(eigensolver="davidson")),):
+        ctxv = [sgo.Context(st, precision=args.precision, **extra, **_tols(args.precision, st)) for st in pop]
+        bv = sgo.Batch(ctxv)
+        bv.energy_forces()
+        torch.cuda.synchronize()
+        k = max(1, min(args.steps, 2))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            Ev, Fv, sv = bv.energy_forces(pos_host)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / k
+        its = [c.info()["n_iter"] for c in ctxv]
+        sweeps = [c.stats()["jacobi_sweeps"] for c in ctxv]
+        rec[name] = dict(value=len(pop) / dt, unit="evals/s", steps=k,
+                         converged=f"{int(np.sum(sv == 0))}/{len(pop)}",
+                         scf_iterations=dict(mean=float(np.mean(its)), max=int(np.max(its))),
+                         jacobi_sweeps_per_member=float(np.mean(sweeps)),
+                         max_abs_dE_per_atom_vs_cg=float(np.max(np.abs(E - Ev) / nat)),
+                         max_abs_dforce_vs_cg=float(max(np.abs(a - b).max() for a, b in zip(F, Fv))))
+        del bv, ctxv
+    return rec
+
+
+def _config_record(sgo, name, stream, kernels=True, fp64=True, extra=None):
     """One named workload on its own: for the mixed and (fp64) the plain FP64 GPU path, one
     cold energy + force evaluation timed after a warm-up evaluation (graph-driven SCF loop),
     its SCF iterations and eigenvector refinement, its errors against the stored oracle
@@ -500,6 +533,7 @@ def _config_record(sgo, name, stream, kernels=True, fp64=True):
         tol = _tols(prec, st) if name == "diamond8" and prec == "fp64" else _tols("mixed", st)
         if name == "diamond8":
             tol.update(mix_alpha=0.7, kerker_q0=0.0)
+        tol.update(extra or {})
         try:
             ctx = sgo.Context(st, precision=prec, **tol)
         except sgo.SgoError as e:
@@ -574,8 +608,9 @@ def run_configs(args):
     stream = torch.cuda.current_stream()
     names = args.names.split(",") if args.names else ["diamond8", "honeycomb24", "cluster13", "cluster55"]
     out = {}
+    extra = dict(eigensolver=args.eigensolver) if args.eigensolver else {}
     for name in names:
-        out[name] = _config_record(sgo, name, stream)
+        out[name] = _config_record(sgo, name, stream, fp64=not args.no_fp64, extra=extra)
         print(json.dumps({name: out[name]}), flush=True)
     print(json.dumps(dict(case="configs", results=out)), flush=True)
     return 0
@@ -589,7 +624,8 @@ def run_case(args):
     import workloads
     build.build()
     st = workloads.de_candidate(args.member)
-    ctx = sgo.Context(st, precision=args.precision, **_tols(args.precision, st))
+    extra = dict(eigensolver=args.eigensolver) if args.eigensolver else {}
+    ctx = sgo.Context(st, precision=args.precision, **_tols(args.precision, st), **extra)
     if args.case == "hpsi":
         rng = np.random.default_rng(0)
         v = rng.normal(size=ctx.grid) * 0.1
@@ -614,6 +650,9 @@ def main():
     ap.add_argument("--kernel", default="plane_vpsi", help="kernel class timed live for the roofline")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-config5", action="store_true", help="skip the 55-atom cluster record")
+    ap.add_argument("--no-variants", action="store_true", help="skip the block Davidson eigensolver record")
+    ap.add_argument("--eigensolver", default=None, choices=["cg", "davidson"],
+                    help="--case configs / scf: the eigensolver (default: the library's, Algorithm 1's CG)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven SCF loop instead of the captured graphs (for per-kernel profilers, "
                          "which cannot look inside graphs with conditional nodes)")

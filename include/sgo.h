@@ -18,7 +18,8 @@
  *  - The caller owns every host array passed in or out; the library copies
  *    inputs and never keeps a caller pointer after the call returns.
  *  - The library owns its device memory (allocated at sgo_create, released at
- *    sgo_destroy).  All device work is enqueued on the stream given to
+ *    sgo_destroy; cudaMalloc unless sgo_set_allocator installed the caller's
+ *    allocator).  All device work is enqueued on the stream given to
  *    sgo_create; calls that return host results synchronise that stream only.
  *  - Errors are returned as sgo_status, never thrown; sgo_last_error() gives a
  *    message for the calling thread.  The library never exits the process.
@@ -125,6 +126,14 @@ typedef struct {
                              CTAs per member; 0 = always one CTA (over a global scratch when the
                              matrices do not fit); 1 = always the cluster.  Taken from the first
                              member of a batch. */
+  int eigensolver;        /* 0 (default): Algorithm 1's all-band CG steps (Sec. II D): per band a
+                             preconditioned, conjugated, projected search direction, a line
+                             minimisation, then a Rayleigh-Ritz over the n_b bands.  1: block
+                             Davidson steps: the preconditioned residuals W of all bands, projected
+                             and normalised, and one Rayleigh-Ritz over the 2 n_b block [X, W]
+                             keeping the lowest n_b Ritz pairs (its Cholesky and eigensolve are
+                             8x the n_b ones).  Same stopping rules; all members of a batch
+                             must agree (else SGO_ERR_ARG at sgo_batch_create). */
 } sgo_opts;
 
 /* Device memory through the caller's allocator.  The library's device buffers (context
@@ -165,10 +174,10 @@ SGO_API sgo_status sgo_scf(sgo_ctx* ctx, const double* pos, int* n_iter_out, dou
  * natoms*3 (Ha/bohr).  Either output may be NULL. */
 SGO_API sgo_status sgo_energy_forces(sgo_ctx* ctx, const double* pos, double* energy, double* forces);
 
-/* A population of n contexts (same precision option) evaluated together: every
- * kernel launch covers all members still iterating (Sec. II D: one relaxation per
- * GPU becomes one population per GPU).  The contexts stay owned by the caller and
- * must outlive the batch. */
+/* A population of n contexts (same precision and eigensolver options, else SGO_ERR_ARG)
+ * evaluated together: every kernel launch covers all members still iterating (Sec. II D:
+ * one relaxation per GPU becomes one population per GPU).  The contexts stay owned by the
+ * caller and must outlive the batch. */
 SGO_API sgo_status sgo_batch_create(int n, sgo_ctx* const* ctxs, sgo_batch** out);
 
 /* The GEMM tile knobs the batch's autotuner picked when the batch was created (mixed path;

@@ -119,6 +119,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->watchdog_ms = 0.0;
   o->extra_bands = -1;
   o->rr_cluster = -1;
+  o->eigensolver = 0;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,
@@ -224,6 +225,12 @@ sgo_status sgo_batch_create(int n, sgo_ctx* const* ctxs, sgo_batch** out) {
     b->ctxs.push_back(ctxs[i]);
   }
   const sgo_opts& o = b->ctxs[0]->opts;
+  for (int i = 1; i < n; ++i)
+    if (b->ctxs[i]->precision != b->ctxs[0]->precision || b->ctxs[i]->opts.eigensolver != o.eigensolver) {
+      sgo::set_error("the members of a batch must share precision and eigensolver");
+      delete b;
+      return SGO_ERR_ARG;
+    }
   b->members = split_members(b->ctxs, sub_batch_count(n, o));
   std::vector<int> foff(n + 1, 0);
   for (int i = 0; i < n; ++i) foff[i + 1] = foff[i] + 3 * b->ctxs[i]->d.natom;

@@ -58,12 +58,19 @@ cudaError_t dev_malloc_bytes(void** p, size_t bytes, cudaStream_t s) {
     f = g_free_fn;
     user = g_alloc_user;
   }
-  if (!a) return cudaMalloc(p, bytes);
+  // every block starts zeroed, whichever allocator gave it (a pool hands back used memory;
+  // padding rows of the GEMM images and partial sums are read as zeros)
+  if (!a) {
+    const cudaError_t e = cudaMalloc(p, bytes);
+    return e == cudaSuccess ? cudaMemset(*p, 0, bytes) : e;
+  }
   *p = a(bytes ? bytes : 1, s, user);
   if (!*p) return cudaErrorMemoryAllocation;
-  std::lock_guard<std::mutex> lk(g_alloc_mu);
-  hooked()[*p] = Hooked{f, user};
-  return cudaSuccess;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    hooked()[*p] = Hooked{f, user};
+  }
+  return cudaMemset(*p, 0, bytes);
 }
 
 void dev_free(void* p) {
@@ -319,6 +326,12 @@ void layout(sgo_ctx* c, A& a) {
   d.Hs = a.template take<double>((size_t)nb * nb);
   d.Tm = a.template take<double>((size_t)nb * nb);
   d.Cm = a.template take<double>((size_t)nb * nb);
+  if (c->opts.eigensolver == 1) {
+    d.S2 = a.template take<double>((size_t)4 * nb * nb);
+    d.H2 = a.template take<double>((size_t)4 * nb * nb);
+  } else {
+    d.S2 = d.H2 = nullptr;
+  }
   d.proj = a.template take<double>((size_t)na * nb);
   d.dproj = a.template take<double>((size_t)3 * na * nb);
   d.eps = a.template take<double>(nb);
@@ -716,11 +729,16 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   n_ = (int)ctxs.size();
   if (n_ == 0) return;
   precision_ = ctxs[0]->precision;
-  for (auto* c : ctxs)
+  for (auto* c : ctxs) {
     if (c->precision != precision_) {
       set_error("all members of a batch must use the same precision");
       return;
     }
+    if (c->opts.eigensolver != ctxs[0]->opts.eigensolver) {
+      set_error("all members of a batch must use the same eigensolver");
+      return;
+    }
+  }
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
       c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2], c_dreg[2], c_zreg[2], c_ppair,
@@ -894,17 +912,20 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   // subspace diagonalisation: one CTA per member with its matrices in shared memory (FP32
   // deviation form up to nb = 105 on the mixed path, FP64 up to nb = 91), else one
   // thread-block cluster per member over a global scratch (k_rr_cluster)
+  // (the block Davidson steps diagonalise the 2 n_b block [X, W])
+  davidson_ = o0.eigensolver == 1;
+  rr_n_ = (davidson_ ? 2 : 1) * max_nb_;
   rr_f32_ = precision_ == 1 && !o0.rr_fp64;
-  rr_smem_bytes_ = (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
-  rr_smem_ = rr_f32_ ? (size_t)20 * max_nb_ * (max_nb_ | 1) <= 216 * 1024 : rr_smem_bytes_ <= 200 * 1024;
+  rr_smem_bytes_ = (size_t)3 * rr_n_ * rr_n_ * sizeof(double);
+  rr_smem_ = rr_f32_ ? (size_t)20 * rr_n_ * (rr_n_ | 1) <= 216 * 1024 : rr_smem_bytes_ <= 200 * 1024;
   // (the one-CTA kernels' pair tables hold 256 pairs: beyond 512 bands the cluster is used)
-  rr_cluster_ = o0.rr_cluster > 0 || (o0.rr_cluster < 0 && !rr_smem_) || max_nb_ > 512;
+  rr_cluster_ = o0.rr_cluster > 0 || (o0.rr_cluster < 0 && !rr_smem_) || rr_n_ > 512;
   if (rr_cluster_) {
-    rrc_stride_ = (rr_cluster_scratch_bytes(max_nb_, rr_f32_ ? sizeof(float) : sizeof(double)) + 255) / 256 * 256;
+    rrc_stride_ = (rr_cluster_scratch_bytes(rr_n_, rr_f32_ ? sizeof(float) : sizeof(double)) + 255) / 256 * 256;
     if (!cuda_ok(dev_malloc(&d_rrc_, rrc_stride_ * n_), "dev_malloc(rr cluster scratch)")) return;
     allocs_.push_back(d_rrc_);
   } else if (!rr_smem_) {  // one CTA over a global scratch
-    rr1_stride_ = rr_f32_ ? (size_t)5 * max_nb_ * (max_nb_ | 1) * sizeof(float) : (size_t)3 * max_nb_ * max_nb_ * sizeof(double);
+    rr1_stride_ = rr_f32_ ? (size_t)5 * rr_n_ * (rr_n_ | 1) * sizeof(float) : (size_t)3 * rr_n_ * rr_n_ * sizeof(double);
     if (!cuda_ok(dev_malloc(&d_rr1_, rr1_stride_ * n_), "dev_malloc(rr scratch)")) return;
     allocs_.push_back(d_rr1_);
   }
@@ -1015,9 +1036,9 @@ void Engine::work_of(int kind, double* bytes, double* flops) const {
         f += 2.0 * npw * nb * nb * work_mult_;
         b += 2.0 * nb * npw * ts * work_mult_;
         break;
-      case TK_RR:
-        f += 4.0 * nb * nb * nb;
-        b += 3.0 * nb * nb * 8.0;
+      case TK_RR:  // (work_mult_ = 8 for the 2 n_b block)
+        f += 4.0 * nb * nb * nb * work_mult_;
+        b += 3.0 * nb * nb * 8.0 * work_mult_;
         break;
     }
   }
@@ -1074,7 +1095,7 @@ void Engine::tn(int akind, int arole, int bkind, int brole, int dst, bool allow_
     launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_, tc_kc_);
   } else {
     launch_gemm_tn<T>(L(*m), akind, arole, bkind, brole, d_part_, part_stride_, tn_kc_);
-    launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_, tn_kc_);
+    launch_gemm_tn_reduce(L(*r), akind, bkind, dst, d_part_, part_stride_, tn_kc_, akind == bkind && arole == brole);
   }
   tend(kind);
 }
@@ -1160,20 +1181,7 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   // relative); the tensor cores' 3xTF32 (about 5e-7) would leave F drifting above tol_e
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S, false);
   tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
-  tbeg(TK_RR);
-  if (rr_cluster_) {
-    const Launch l = L(m_prob_);
-    const bool launched = rr_f32_ ? launch_rr_cluster<float>(l, max_nb_, d_rrc_, rrc_stride_, rr_cap_)
-                                  : launch_rr_cluster<double>(l, max_nb_, d_rrc_, rrc_stride_, 30);
-    if (!launched) set_error("cluster Rayleigh-Ritz launch refused");
-  } else if (rr_f32_) {  // 5 FP32 n x (n|1) matrices in shared memory or a global scratch
-    launch_rr_f32(L(m_prob_), (size_t)20 * max_nb_ * (max_nb_ | 1), reinterpret_cast<float*>(d_rr1_),
-                  rr1_stride_ / sizeof(float), rr_cap_);
-  } else {
-    launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, reinterpret_cast<double*>(d_rr1_),
-              rr1_stride_ / sizeof(double), 30);
-  }
-  tend(TK_RR);
+  rr_solve(1);
   // P and HP (the last search direction and its H image) and W are dead here; so is RP
   // (after a CG step the new residual waits in W2 and the old one in RP is done with): one
   // launch rotates X -> P, HX -> HP and, with the CG history, PP -> W and the new residual
@@ -1184,6 +1192,61 @@ void Engine::rayleigh_ritz(bool rotate_history) {
   else
     rotate_pairs<T>(RolePairs{2, {WB_X, WB_HX, 0, 0}, {WB_P, WB_HP, 0, 0}},
                     RolePairs{2, {WB_X, WB_HX, 0, 0}, {WB_P, WB_HP, 0, 0}});
+}
+
+// Cholesky, congruence and eigensolve of the blk n_b subspace (blk = 2: the block [X, W]).
+void Engine::rr_solve(int blk) {
+  tbeg(TK_RR);
+  work_mult_ = blk * blk * blk;
+  // (the 2 n_b block is far from diagonal: its FP32 Jacobi gets the full sweep cap)
+  const int cap = blk == 2 ? 30 : rr_cap_;
+  if (rr_cluster_) {
+    const Launch l = L(m_prob_);
+    const bool launched = rr_f32_ ? launch_rr_cluster<float>(l, rr_n_, d_rrc_, rrc_stride_, cap, blk)
+                                  : launch_rr_cluster<double>(l, rr_n_, d_rrc_, rrc_stride_, 30, blk);
+    if (!launched) set_error("cluster Rayleigh-Ritz launch refused");
+  } else if (rr_f32_) {  // 5 FP32 n x (n|1) matrices in shared memory or a global scratch
+    launch_rr_f32(L(m_prob_), (size_t)20 * rr_n_ * (rr_n_ | 1), reinterpret_cast<float*>(d_rr1_),
+                  rr1_stride_ / sizeof(float), cap, blk);
+  } else {
+    launch_rr(L(m_prob_), rr_smem_ ? 1 : 0, rr_smem_bytes_, reinterpret_cast<double*>(d_rr1_),
+              rr1_stride_ / sizeof(double), 30, blk);
+  }
+  tend(TK_RR);
+  work_mult_ = 1;
+}
+
+// Block Davidson step (the eigensolver alternative to Algorithm 1's CG step): the
+// preconditioned residuals W = K (H X - X eps) of every band, without conjugation, projected
+// on the complement of X and normalised; H W; then one Rayleigh-Ritz over the 2 n_b block
+// [X, W] that keeps its lowest n_b Ritz pairs: X <- X C_X + W C_W, HX <- HX C_X + HW C_W.
+// Its eigensolve is 8x the n_b one (and on the FP64 path runs at the FP64 rate).
+template <typename T>
+void Engine::davidson_step() {
+  tbeg(TK_CG_BAND);
+  launch_cg_precond<T>(L(m_bands_), WB_X, WB_HX, WB_P, WB_W2, WB_PP, -1);
+  tend(TK_CG_BAND);
+  tn<T>(OPK_WB, WB_X, OPK_WB, WB_P, DD_CM);
+  nn<T>(OPK_WB, WB_X, DD_CM, WB_P, -1.0, 1.0);
+  tbeg(TK_CG_BAND);
+  launch_normalize<T>(L(m_bands_), WB_P, -1);
+  tend(TK_CG_BAND);
+  hpsi<T>(WB_P, WB_HP);
+  // the blocks of S2 = [X W]^T [X W] and H2 = [X W]^T [HX HW] (overlaps on CUDA cores)
+  tn<T>(OPK_WB, WB_X, OPK_WB, WB_X, DD_S, false);
+  tn<T>(OPK_WB, WB_X, OPK_WB, WB_HX, DD_HS);
+  tn<T>(OPK_WB, WB_X, OPK_WB, WB_P, DD_TM, false);
+  tn<T>(OPK_WB, WB_X, OPK_WB, WB_HP, DD_CM);
+  launch_rr2_assemble(L(m_red_ww_), 0);
+  tn<T>(OPK_WB, WB_P, OPK_WB, WB_P, DD_S, false);
+  tn<T>(OPK_WB, WB_P, OPK_WB, WB_HP, DD_HS);
+  launch_rr2_assemble(L(m_red_ww_), 1);
+  rr_solve(2);
+  // the Ritz vectors and their H images into the dead W, W2, which then take the roles of
+  // X and HX
+  nn_pairs<T>(OPK_WB, RolePairs{2, {WB_X, WB_HX, 0, 0}, {WB_W, WB_W2, 0, 0}}, DD_TM, 1.0, 0.0, false);
+  nn_pairs<T>(OPK_WB, RolePairs{2, {WB_P, WB_HP, 0, 0}, {WB_W, WB_W2, 0, 0}}, DD_CM, 1.0, 1.0, false);
+  k_swap_roles<<<n_, 32, 0, stream_>>>(L(m_prob_).ka, RolePairs{2, {WB_X, WB_HX, 0, 0}, {WB_W, WB_W2, 0, 0}});
 }
 
 // One all-band CG step of Algorithm 1: search directions, projection, line minimisation,
@@ -1249,7 +1312,7 @@ void Engine::scf_iteration(int ncg, bool count_iter) {
   hpsi<T>(WB_X, WB_HX);
   rayleigh_ritz<T>(false);
   set_scal(SC_FIRSTCG, 1.0, true);
-  for (int k = 0; k < ncg; ++k) cg_step<T>();
+  for (int k = 0; k < ncg; ++k) eig_step<T>();
   density_energy<T>(count_iter ? 1 : 0);
 }
 
@@ -1304,7 +1367,7 @@ void Engine::polish() {
     tend(TK_CG_BAND);
     k_polish_control<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, nullptr, o.eig_tol, maxs, 0, 0);
     if (!read_active()) break;
-    cg_step<T>();
+    eig_step<T>();
   }
   rr_cap_ = 10;
   k_polish_activate<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, 1);
@@ -1342,7 +1405,7 @@ bool Engine::build_polish_graphs() {
     rr_cap_ = 30;
     launch_band_residual<T>(L(m_bands_), WB_X, WB_HX);
     k_polish_control<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, d_iter_ + 1, o.eig_tol, maxs, cond, 1);
-    cg_step<T>();
+    eig_step<T>();
     rr_cap_ = 10;
     cudaGraph_t got = nullptr;
     ok = cuda_ok(cudaStreamEndCapture(stream_, &got), "capture polish body end");

@@ -133,6 +133,9 @@ class Engine {
   template <typename T> void hpsi(int src, int dst);
   template <typename T> void rayleigh_ritz(bool rotate_history);
   template <typename T> void cg_step();
+  template <typename T> void davidson_step();
+  template <typename T> void eig_step() { davidson_ ? davidson_step<T>() : cg_step<T>(); }
+  void rr_solve(int blk);
   template <typename T> void tn(int akind, int arole, int bkind, int brole, int dst, bool allow_tc = true);
   template <typename T>
   void nn(int akind, int arole, int msel, int yrole, double alpha, double beta, bool image_ready = false);
@@ -194,6 +197,8 @@ class Engine {
   bool rr_smem_ = true;
   bool rr_f32_ = false;
   bool rr_cluster_ = false;          // subspace too large for one CTA: cluster eigensolve
+  bool davidson_ = false;            // block Davidson steps (2 n_b Rayleigh-Ritz) instead of CG
+  int rr_n_ = 0;                     // largest subspace of one Rayleigh-Ritz call
   unsigned char* d_rrc_ = nullptr;   // its per-member global scratch
   size_t rrc_stride_ = 0;
   unsigned char* d_rr1_ = nullptr;   // one-CTA eigensolve beyond shared memory: global scratch

@@ -43,14 +43,67 @@ __device__ __forceinline__ double* dense_ptr(const Prob& P, int sel) {
 
 }  // namespace
 
+// Subspace of one Rayleigh-Ritz call: blk = 1, the n_b x n_b matrices S, Hs of the bands;
+// blk = 2, the 2 n_b x 2 n_b matrices S2, H2 of the block [X, W] (block Davidson).
+__device__ __forceinline__ const double* rr_in_s(const Prob& P, int blk) { return blk == 2 ? P.S2 : P.S; }
+__device__ __forceinline__ const double* rr_in_h(const Prob& P, int blk) { return blk == 2 ? P.H2 : P.Hs; }
+// Eigenvector j of rank rk (ascending eigenvalue), component i: column rk of the rotation.
+// Only the lowest n_b Ritz pairs are kept: rows i < n_b go to Tm (the coefficients on X),
+// rows n_b .. 2 n_b - 1 to Cm (those on W).
+__device__ __forceinline__ void rr_out_vec(const Prob& P, int i, int rk, double v) {
+  const int nb = P.nb;
+  if (rk >= nb) return;
+  if (i < nb) P.Tm[(size_t)i * nb + rk] = v;
+  else P.Cm[(size_t)(i - nb) * nb + rk] = v;
+}
+__device__ __forceinline__ void rr_out_eps(const Prob& P, int rk, double e) {
+  if (rk < P.nb) P.eps[rk] = e;
+}
+// Near-dependent directions of the block [X, W] (blk = 2): a W vector whose component
+// orthogonal to the basis vectors before it has squared norm at most RR_DROP (its own norm
+// is 1) is left out of the subspace instead of failing the Cholesky (the preconditioned
+// residuals of a random start are nearly collinear): its column of the factor is zero, its
+// row of the inverse factor is zero (so the projected matrix has a zero row and column,
+// which no rotation touches), and its eigenvalue is taken as RR_DROP_DIAG, so that it ranks
+// above every kept Ritz value.  (In the FP32 and cluster kernels the same bound fails the
+// Cholesky of an X direction.)
+constexpr double RR_DROP = 1e-3;
+constexpr double RR_DROP_DIAG = 1e12;
+constexpr float RR_DROPPED = -2.f;  // pivot deviation recorded for a left-out direction
+
 // ---------------------------------------------------------------------------
-// C = A^T B, split-K partials.  CTA = (problem, tile_i, tile_j, split).
+// C = A^T B, split-K partials.  CTA = (problem, tile_i, tile_j, split).  Thread (ti, tj)
+// owns rows 4 ti .. 4 ti + 3 and columns 4 tj .. 4 tj + 3 of the 64 x 64 tile, so every
+// K step reads its A and B values as one 16-byte shared load each (two for FP64).  A K
+// chunk of 32 is staged from 16-byte global loads along K (zero beyond the split's end:
+// splits end on multiples of 32 or at npw, whose tail up to ld is zero).  A^T A (same
+// operand twice) computes the tiles with tile_i <= tile_j only; the reduction mirrors them.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T (&o)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+  }
+}
+
+template <typename T>
+struct alignas(16) KPack {
+  static constexpr int W = 16 / sizeof(T);
+  T e[W];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole, int bkind, int brole, double* part_base,
                                                 size_t part_stride, int kc) {
-  __shared__ T As[32][TN_TILE + 1];
-  __shared__ T Bs[32][TN_TILE + 1];
+  constexpr int W = KPack<T>::W;                 // K values per 16-byte load
+  constexpr int NLD = 32 * TN_TILE / W / 256;    // loads per thread per operand per chunk
+  constexpr int LS = TN_TILE + 4;                // row stride (16-byte aligned rows)
+  __shared__ __align__(16) T As[32][LS];
+  __shared__ __align__(16) T Bs[32][LS];
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
@@ -60,6 +113,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole,
   const int split = local / (ta * tb);
   local -= split * ta * tb;
   const int ti0 = (local / tb) * TN_TILE, tj0 = (local % tb) * TN_TILE;
+  if (akind == bkind && arole == brole && ti0 > tj0) return;  // mirrored by the reduction
   const T* A = opnd<T>(P, akind, arole);
   const T* Bm = opnd<T>(P, bkind, brole);
   const int ld = P.ld;
@@ -71,34 +125,43 @@ __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole,
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  // register stage of the next 32-wide K chunk (element e = t + 256 q: vector e >> 5, k e & 31)
-  T ra[8], rb[8];
+  // load f = t + 256 q: vector f % 64, K offset (f / 64) W within the chunk
+  KPack<T> ra[NLD], rb[NLD];
   auto fetch = [&](int kb) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = t + 256 * q;
-      const int v = e >> 5, k = kb + (e & 31);
-      ra[q] = (ti0 + v < na && k < k1) ? A[(size_t)(ti0 + v) * ld + k] : T(0);
-      rb[q] = (tj0 + v < nbv && k < k1) ? Bm[(size_t)(tj0 + v) * ld + k] : T(0);
+    for (int q = 0; q < NLD; ++q) {
+      const int f = t + 256 * q;
+      const int v = f & (TN_TILE - 1), k = kb + (f / TN_TILE) * W;
+      KPack<T> za, zb;
+#pragma unroll
+      for (int c = 0; c < W; ++c) za.e[c] = zb.e[c] = T(0);
+      if (k < k1) {
+        if (ti0 + v < na) za = *reinterpret_cast<const KPack<T>*>(A + (size_t)(ti0 + v) * ld + k);
+        if (tj0 + v < nbv) zb = *reinterpret_cast<const KPack<T>*>(Bm + (size_t)(tj0 + v) * ld + k);
+      }
+      ra[q] = za;
+      rb[q] = zb;
     }
   };
   fetch(k0);
   for (int kb = k0; kb < k1; kb += 32) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = t + 256 * q;
-      As[e & 31][e >> 5] = ra[q];
-      Bs[e & 31][e >> 5] = rb[q];
+    for (int q = 0; q < NLD; ++q) {
+      const int f = t + 256 * q;
+      const int v = f & (TN_TILE - 1), kq = (f / TN_TILE) * W;
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        As[kq + c][v] = ra[q].e[c];
+        Bs[kq + c][v] = rb[q].e[c];
+      }
     }
     __syncthreads();
     if (kb + 32 < k1) fetch(kb + 32);
 #pragma unroll 8
     for (int kk = 0; kk < 32; ++kk) {
       T a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ti + 16 * i];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) b[i] = Bs[kk][tj + 16 * i];
+      lds4(&As[kk][4 * ti], a);
+      lds4(&Bs[kk][4 * tj], b);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -111,14 +174,15 @@ __global__ void __launch_bounds__(256) k_gemm_tn(KArgs ka, int akind, int arole,
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      int i = ti0 + ti + 16 * a, j = tj0 + tj + 16 * b;
+      int i = ti0 + 4 * ti + a, j = tj0 + 4 * tj + b;
       if (i < na && j < nbv) part[(size_t)i * nbv + j] = (double)acc[a][b];
     }
 }
 
-// Sum the partials in split order.  CTA = (problem, chunk of 256 outputs).
+// Sum the partials in split order.  CTA = (problem, chunk of 256 outputs).  sym: A^T A
+// from k_gemm_tn, whose tiles below the diagonal were not computed (read mirrored).
 __global__ void k_gemm_tn_reduce(KArgs ka, int akind, int bkind, int dst, const double* part_base, size_t part_stride,
-                                 int kc) {
+                                 int kc, int sym) {
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
@@ -127,8 +191,13 @@ __global__ void k_gemm_tn_reduce(KArgs ka, int akind, int bkind, int dst, const 
   if (o >= na * nbv) return;
   const int nsplit = (P.npw + kc - 1) / kc;
   const double* part = part_base + (size_t)p * part_stride;
+  int src = o;
+  if (sym) {
+    const int i = o / nbv, j = o - i * nbv;
+    if (i / TN_TILE > j / TN_TILE) src = j * nbv + i;
+  }
   double s = 0.0;
-  for (int k = 0; k < nsplit; ++k) s += part[(size_t)k * na * nbv + o];
+  for (int k = 0; k < nsplit; ++k) s += part[(size_t)k * na * nbv + src];
   dense_ptr(P, dst)[o] = s;
 }
 
@@ -330,10 +399,11 @@ __global__ void __launch_bounds__(BAND_THREADS) k_cg_precond(KArgs ka, int xr, i
   const Pack16<T>* hx = pk(wbuf<T>(P, hxr) + off);
   Pack16<T>* pv = pk(wbuf<T>(P, pr) + off);
   Pack16<T>* rv = pk(wbuf<T>(P, rr_out) + off);
-  const Pack16<T>* pp = pk(wbuf<T>(P, ppr) + off);
-  const Pack16<T>* rp = pk(wbuf<T>(P, rpr) + off);
+  // rpr < 0: no conjugation history (the preconditioned residual alone, block Davidson)
+  const bool first = rpr < 0 || P.scal[SC_FIRSTCG] != 0.0;
+  const Pack16<T>* pp = first ? nullptr : pk(wbuf<T>(P, ppr) + off);
+  const Pack16<T>* rp = first ? nullptr : pk(wbuf<T>(P, rpr) + off);
   const Pack16<T>* ek = ekin_pk<T>(P);
-  const bool first = P.scal[SC_FIRSTCG] != 0.0;
   T ekp = T(0);
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     const Pack16<T> a = x[v], g = ek[v];
@@ -401,7 +471,7 @@ __global__ void __launch_bounds__(BAND_THREADS) k_normalize(KArgs ka, int pr, in
   const size_t off = (size_t)i * P.ld;
   const int nv = P.ld / W;
   Pack16<T>* pv = pk(wbuf<T>(P, pr) + off);
-  Pack16<T>* pp = pk(wbuf<T>(P, ppr) + off);
+  Pack16<T>* pp = ppr < 0 ? nullptr : pk(wbuf<T>(P, ppr) + off);  // ppr < 0: no history copy
   T st = T(0);
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     const Pack16<T> a = pv[v];
@@ -412,7 +482,7 @@ __global__ void __launch_bounds__(BAND_THREADS) k_normalize(KArgs ka, int pr, in
   const T inv = s > 1e-150 ? T(1.0 / s) : T(0);
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     Pack16<T> a = pv[v];
-    pp[v] = a;
+    if (pp) pp[v] = a;
 #pragma unroll
     for (int j = 0; j < W; ++j) a.e[j] *= inv;
     pv[v] = a;
@@ -538,16 +608,19 @@ __global__ void k_copy_out(KArgs ka, int role, double* dst, int nvec) {
 // Matrices: A, L, V in shared memory when 3 nb^2 doubles fit, else in global scratch.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, double* gscratch, size_t gstride,
-                                                   int max_sweeps) {
+                                                   int max_sweeps, int blk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ double cs_c[256], cs_s[256];
   __shared__ int pr_p[256], pr_q[256];
   __shared__ int flag;
+  __shared__ unsigned char drp[512];  // left-out directions (blk = 2)
   const int p = blockIdx.x;
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
-  const int n = P.nb;
+  const int n = blk * P.nb;
+  const double* Sin = rr_in_s(P, blk);
+  const double* Hin = rr_in_h(P, blk);
   double *A, *L, *V;
   if (use_smem) {
     A = reinterpret_cast<double*>(smem_raw);
@@ -561,20 +634,25 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
   // symmetrised inputs
   for (int e = tid; e < n * n; e += nt) {
     int i = e / n, j = e % n;
-    L[e] = 0.5 * (P.S[i * n + j] + P.S[j * n + i]);
-    A[e] = 0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]);
+    L[e] = 0.5 * (Sin[i * n + j] + Sin[j * n + i]);
+    A[e] = 0.5 * (Hin[i * n + j] + Hin[j * n + i]);
   }
   __syncthreads();
-  // Cholesky of L in place (lower triangle)
+  // Cholesky of L in place (lower triangle); a left-out direction (blk = 2) gets a unit
+  // pivot and a zero column (its row of L^-1 is cleared below)
   for (int k = 0; k < n; ++k) {
     if (tid == 0) {
       double d = L[k * n + k];
+      const bool dr = blk == 2 && k >= P.nb && d <= RR_DROP;
+      if (dr) d = 1.0;
       if (!(d > 0.0)) { flag = 1; d = 1.0; }
       L[k * n + k] = sqrt(d);
+      drp[k] = dr ? 1 : 0;
     }
     __syncthreads();
+    const bool drop = drp[k] != 0;
     const double dk = L[k * n + k];
-    for (int i = k + 1 + tid; i < n; i += nt) L[i * n + k] /= dk;
+    for (int i = k + 1 + tid; i < n; i += nt) L[i * n + k] = drop ? 0.0 : L[i * n + k] / dk;
     __syncthreads();
     const int m = n - k - 1;
     for (int e = tid; e < m * m; e += nt) {
@@ -600,7 +678,8 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
     }
     __syncthreads();
   }
-  for (int e = tid; e < n * n; e += nt) L[e] = V[e];
+  // (rows of L^-1 of left-out directions cleared)
+  for (int e = tid; e < n * n; e += nt) L[e] = drp[e / n] ? 0.0 : V[e];
   __syncthreads();
   // V := A L^T ; A := L V   (C = L^-1 Hs L^-T, symmetric)
   for (int e = tid; e < n * n; e += nt) {
@@ -705,22 +784,22 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr(KArgs ka, int use_smem, doubl
       __syncthreads();
     }
   }
-  // ascending order: rank of each eigenvalue
+  // ascending order: rank of each eigenvalue (a left-out direction ranks last)
   for (int j = tid; j < n; j += nt) {
-    double ej = A[j * n + j];
+    double ej = drp[j] ? RR_DROP_DIAG : A[j * n + j];
     int rank = 0;
     for (int k2 = 0; k2 < n; ++k2) {
-      double ek = A[k2 * n + k2];
+      double ek = drp[k2] ? RR_DROP_DIAG : A[k2 * n + k2];
       rank += (ek < ej) || (ek == ej && k2 < j);
     }
-    P.eps[rank] = ej;
-    P.bv[BV_TMP0 * n + j] = (double)rank;
+    rr_out_eps(P, rank, ej);
+    P.bv[BV_TMP0 * P.nb + j] = (double)rank;  // (blk = 2: rows BV_TMP0 and BV_TMP1)
   }
   __syncthreads();
   // Tm[:, rank(j)] = V[:, j]  (= L^-T U)
   for (int e = tid; e < n * n; e += nt) {
     int i = e / n, j = e % n;
-    P.Tm[i * n + (int)P.bv[BV_TMP0 * n + j]] = V[e];
+    rr_out_vec(P, i, (int)P.bv[BV_TMP0 * P.nb + j], V[e]);
   }
   if (tid == 0) {
     P.scal[SC_RRSWEEPS] += sweeps;
@@ -748,7 +827,8 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch, size_t gstride, int max_sweeps) {
+__global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch, size_t gstride, int max_sweeps,
+                                                       int blk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float red[32];
   __shared__ float dkv[512];  // Cholesky pivots d_k (n <= 512: the pair tables below hold 256 pairs)
@@ -758,7 +838,9 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
   const int p = blockIdx.x;
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
-  const int n = P.nb, ns = n | 1, nn = n * ns;
+  const int n = blk * P.nb, ns = n | 1, nn = n * ns;
+  const double* Sin = rr_in_s(P, blk);
+  const double* Hin = rr_in_h(P, blk);
   // the five matrices live in shared memory, or (large n) in this problem's global scratch
   float* D = gscratch ? gscratch + (size_t)p * gstride : reinterpret_cast<float*>(smem_raw);
   float* G = D + nn;
@@ -770,8 +852,8 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
   if (tid == 0) flag = 0;
   for (int i = ty; i < n; i += nty)
     for (int j = tx; j < n; j += 32) {
-      D[i * ns + j] = (float)(0.5 * (P.S[i * n + j] + P.S[j * n + i]) - (i == j ? 1.0 : 0.0));
-      Hf[i * ns + j] = (float)(0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]));
+      D[i * ns + j] = (float)(0.5 * (Sin[i * n + j] + Sin[j * n + i]) - (i == j ? 1.0 : 0.0));
+      Hf[i * ns + j] = (float)(0.5 * (Hin[i * n + j] + Hin[j * n + i]));
       G[i * ns + j] = 0.f;
     }
   __syncthreads();
@@ -779,33 +861,38 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
   // lower column k (final after step k - 1), writes the scaled column L_ik = D_ik / (1 + d_k)
   // into the upper row k (D_ki, never read in step k) and updates the lower trailing block
   // with the scaled values formed on the fly; d_k goes to dkv
+  // (a left-out direction of the block [X, W]: zero scaled column, no update, pivot mark
+  // RR_DROPPED in dkv)
   for (int k = 0; k < n; ++k) {
     const float x = D[k * ns + k];
-    const float xs = fmaxf(x, -0.999f);
+    const bool drop = blk == 2 && k >= P.nb && x <= (float)RR_DROP - 1.f;
+    const float xs = drop ? 0.f : fmaxf(x, -0.999f);
     const float dk = xs / (1.f + sqrtf(1.f + xs));
-    const float inv = 1.f / (1.f + dk);
+    const float inv = drop ? 0.f : 1.f / (1.f + dk);
     if (tid == 0) {
-      if (!(x > -0.999f)) flag = 1;  // S not positive definite (to FP32 resolution)
-      dkv[k] = dk;
+      if (!drop && !(x > -0.999f)) flag = 1;  // S not positive definite (to FP32 resolution)
+      dkv[k] = drop ? RR_DROPPED : dk;
     }
     for (int i = k + 1 + tid; i < n; i += nt) D[k * ns + i] = D[i * ns + k] * inv;
-    for (int i = k + 1 + ty; i < n; i += nty) {
-      const float lik = D[i * ns + k] * inv;
-      for (int j = k + 1 + tx; j <= i; j += 32) D[i * ns + j] -= lik * (D[j * ns + k] * inv);
-    }
+    if (!drop)
+      for (int i = k + 1 + ty; i < n; i += nty) {
+        const float lik = D[i * ns + k] * inv;
+        for (int j = k + 1 + tx; j <= i; j += 32) D[i * ns + j] -= lik * (D[j * ns + k] * inv);
+      }
     __syncthreads();
   }
   // G: G_ii = -d_i / (1 + d_i), G_ij = -(L_ij + sum_{j<=k<i} L_ik G_kj) / (1 + d_i) with
   // L_ik = D_ki; every column j of G is an independent forward substitution: one warp per
   // column, lanes splitting the sum, no block barrier until all columns are done
+  // (a left-out direction's row of I + G is zero: G_jj = -1, G_ij = 0)
   for (int j = ty; j < n; j += nty) {
-    if (tx == 0) G[j * ns + j] = -dkv[j] / (1.f + dkv[j]);
+    if (tx == 0) G[j * ns + j] = dkv[j] == RR_DROPPED ? -1.f : -dkv[j] / (1.f + dkv[j]);
     __syncwarp();
     for (int i = j + 1; i < n; ++i) {
       float sacc = 0.f;
       for (int k = j + tx; k < i; k += 32) sacc += D[k * ns + i] * G[k * ns + j];
       sacc = warp_sum_f(sacc);
-      if (tx == 0) G[i * ns + j] = -(D[j * ns + i] + sacc) / (1.f + dkv[i]);
+      if (tx == 0) G[i * ns + j] = dkv[i] == RR_DROPPED ? 0.f : -(D[j * ns + i] + sacc) / (1.f + dkv[i]);
       __syncwarp();
     }
   }
@@ -864,8 +951,11 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
     for (int r = 0; r < m - 1; ++r) {
       if (tid < half) {
         const int a = tid, b = m - 1 - tid;
-        const int pa = a == 0 ? 0 : 1 + (a - 1 + r) % (m - 1);
-        const int pb = b == 0 ? 0 : 1 + (b - 1 + r) % (m - 1);
+        int ta = a - 1 + r, tb = b - 1 + r;  // (both < 2 (m - 1): one conditional subtraction)
+        if (ta >= m - 1) ta -= m - 1;
+        if (tb >= m - 1) tb -= m - 1;
+        const int pa = a == 0 ? 0 : 1 + ta;
+        const int pb = b == 0 ? 0 : 1 + tb;
         const int pp = min(pa, pb), qq = max(pa, pb);
         float c = 1.f, s = 0.f;
         if (qq < n) {
@@ -883,17 +973,18 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
         pr_q[tid] = qq;
       }
       __syncthreads();
-      // blocks (P, Q); rows / columns equal to n (the odd dummy) are absent
-      for (int P2 = ty; P2 < half; P2 += nty) {
-        const float sp = cs_s[P2], cp = cs_c[P2];
-        const int p0 = pr_p[P2], p1 = pr_q[P2];
-        const bool h1 = p1 < n;
-        for (int Q2 = tx; Q2 < half; Q2 += 32) {
-          const float sq = cs_s[Q2];
+      // every 2x2 block (P, Q) of A, then every entry of the rotated rows of V^T, as one
+      // flat index spread over all threads (rows / columns equal to n, the odd dummy, are
+      // absent; its pair never rotates)
+      const int nblk = half * half, ntot = nblk + half * n;
+      for (int e = tid; e < ntot; e += nt) {
+        if (e < nblk) {
+          const int P2 = e / half, Q2 = e - P2 * half;
+          const float sp = cs_s[P2], sq = cs_s[Q2];
           if (sp == 0.f && sq == 0.f) continue;
-          const float cq = cs_c[Q2];
-          const int q0 = pr_p[Q2], q1 = pr_q[Q2];
-          const bool g1 = q1 < n;
+          const float cp = cs_c[P2], cq = cs_c[Q2];
+          const int p0 = pr_p[P2], p1 = pr_q[P2], q0 = pr_p[Q2], q1 = pr_q[Q2];
+          const bool h1 = p1 < n, g1 = q1 < n;
           const float a00 = A[p0 * ns + q0];
           const float a01 = g1 ? A[p0 * ns + q1] : 0.f;
           const float a10 = h1 ? A[p1 * ns + q0] : 0.f;
@@ -904,14 +995,13 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
           if (g1) A[p0 * ns + q1] = sq * b00 + cq * b01;
           if (h1) A[p1 * ns + q0] = cq * b10 - sq * b11;
           if (h1 && g1) A[p1 * ns + q1] = sq * b10 + cq * b11;
-        }
-      }
-      for (int Q2 = ty; Q2 < half; Q2 += nty) {
-        const float sq = cs_s[Q2];
-        if (sq == 0.f) continue;
-        const float cq = cs_c[Q2];
-        const int q0 = pr_p[Q2], q1 = pr_q[Q2];
-        for (int i = tx; i < n; i += 32) {
+        } else {
+          const int f = e - nblk;
+          const int Q2 = f / n, i = f - Q2 * n;
+          const float sq = cs_s[Q2];
+          if (sq == 0.f) continue;
+          const float cq = cs_c[Q2];
+          const int q0 = pr_p[Q2], q1 = pr_q[Q2];
           const float v0 = Vt[q0 * ns + i], v1 = Vt[q1 * ns + i];
           Vt[q0 * ns + i] = cq * v0 - sq * v1;
           Vt[q1 * ns + i] = sq * v0 + cq * v1;
@@ -920,20 +1010,21 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
       __syncthreads();
     }
   }
-  for (int j = tid; j < n; j += nt) {
-    const float ej = A[j * ns + j];
+  for (int j = tid; j < n; j += nt) {  // (a left-out direction ranks last)
+    const float ej = dkv[j] == RR_DROPPED ? (float)RR_DROP_DIAG : A[j * ns + j];
     int rank = 0;
     for (int k2 = 0; k2 < n; ++k2) {
-      const float ek = A[k2 * ns + k2];
+      const float ek = dkv[k2] == RR_DROPPED ? (float)RR_DROP_DIAG : A[k2 * ns + k2];
       rank += (ek < ej) || (ek == ej && k2 < j);
     }
-    P.eps[rank] = (double)ej;
-    P.bv[BV_TMP0 * n + j] = (double)rank;
+    rr_out_eps(P, rank, (double)ej);
+    P.bv[BV_TMP0 * P.nb + j] = (double)rank;  // (blk = 2: rows BV_TMP0 and BV_TMP1)
   }
   __syncthreads();
   for (int j = ty; j < n; j += nty) {
-    const int rj = (int)P.bv[BV_TMP0 * n + j];
-    for (int i = tx; i < n; i += 32) P.Tm[i * n + rj] = (double)Vt[j * ns + i];
+    const int rj = (int)P.bv[BV_TMP0 * P.nb + j];
+    if (rj >= P.nb) continue;
+    for (int i = tx; i < n; i += 32) rr_out_vec(P, i, rj, (double)Vt[j * ns + i]);
   }
   if (tid == 0) {
     P.scal[SC_RRSWEEPS] += sweeps;
@@ -1001,7 +1092,7 @@ size_t rr_cluster_scratch_bytes(int n, size_t tsize) {
 
 template <typename T>
 __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned char* scratch_base, size_t stride,
-                                                           int max_sweeps, int rows_smem) {
+                                                           int max_sweeps, int rows_smem, int blk) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   constexpr int C = RR_CLUSTER;
@@ -1012,7 +1103,9 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
   const int rank = (int)cluster.block_rank();
   if (!ka.active[p]) return;  // the whole cluster shares p
   const Prob& P = ka.probs[p];
-  const int n = P.nb, m = n + (n & 1), npairs = m / 2;
+  const int n = blk * P.nb, m = n + (n & 1), npairs = m / 2;
+  const double* Sin = rr_in_s(P, blk);
+  const double* Hin = rr_in_h(P, blk);
   const size_t nn = (size_t)n * n;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   // global scratch of this problem
@@ -1052,20 +1145,23 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
   // 1. D = S - I, Hf (symmetrised), my rows
   for (int e = tid; e < myrows * n; e += nt) {
     const int i = rank + C * (e / n), j = e % n;
-    Dm[(size_t)i * n + j] = (T)(0.5 * (P.S[i * n + j] + P.S[j * n + i]) - (i == j ? 1.0 : 0.0));
-    Hm[(size_t)i * n + j] = (T)(0.5 * (P.Hs[i * n + j] + P.Hs[j * n + i]));
+    Dm[(size_t)i * n + j] = (T)(0.5 * (Sin[i * n + j] + Sin[j * n + i]) - (i == j ? 1.0 : 0.0));
+    Hm[(size_t)i * n + j] = (T)(0.5 * (Hin[i * n + j] + Hin[j * n + i]));
   }
   cluster.sync();
 
   // 2. Cholesky in deviation form
+  // (a left-out direction of the block [X, W]: zero scaled column, no update, pivot mark
+  // RR_DROPPED in dkv)
   for (int k = 0; k < n; ++k) {
     const T x = Dm[(size_t)k * n + k];
-    const T xs = x > T(-0.999) ? x : T(-0.999);
+    const bool drop = blk == 2 && k >= P.nb && x <= T(RR_DROP) - T(1);
+    const T xs = drop ? T(0) : (x > T(-0.999) ? x : T(-0.999));
     const T dk = xs / (T(1) + sqrt(T(1) + xs));
-    const T inv = T(1) / (T(1) + dk);
+    const T inv = drop ? T(0) : T(1) / (T(1) + dk);
     if (tid == 0) {
-      if (!(x > T(-0.999))) flag_s = 1;
-      if (rank == 0) dkv[k] = (double)dk;
+      if (!drop && !(x > T(-0.999))) flag_s = 1;
+      if (rank == 0) dkv[k] = drop ? (double)RR_DROPPED : (double)dk;
     }
     for (int j = k + 1 + tid; j < n; j += nt) colk[j] = Dm[(size_t)j * n + k] * inv;
     __syncthreads();
@@ -1084,17 +1180,18 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
 
   // 3. G by columns: GT[j][i] = G_ij, G_jj = -d_j / (1 + d_j),
   //    G_ij = -(L_ij + sum_{j <= k < i} L_ik G_kj) / (1 + d_i)
+  //    (a left-out direction's row of I + G is zero: G_jj = -1, G_ij = 0)
   for (int j = rank * nwarps + warp; j < n; j += C * nwarps) {
     T* gj = GT + (size_t)j * n;
     const T dj = (T)dkv[j];
-    if (lane == 0) gj[j] = -dj / (T(1) + dj);
+    if (lane == 0) gj[j] = dkv[j] == (double)RR_DROPPED ? T(-1) : -dj / (T(1) + dj);
     __syncwarp();
     for (int i = j + 1; i < n; ++i) {
       const T* Li = Lm + (size_t)i * n;
       T sacc = T(0);
       for (int k = j + lane; k < i; k += 32) sacc += Li[k] * gj[k];
       for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) gj[i] = -(Li[j] + sacc) / (T(1) + (T)dkv[i]);
+      if (lane == 0) gj[i] = dkv[i] == (double)RR_DROPPED ? T(0) : -(Li[j] + sacc) / (T(1) + (T)dkv[i]);
       __syncwarp();
     }
   }
@@ -1273,10 +1370,10 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
   if (rows_smem)
     for (int e = tid; e < myrows * n; e += nt) Lm[(size_t)(rank + C * (e / n)) * n + e % n] = vrow(e / n)[e % n];
   cluster.sync();
-  for (int j = tid; j < n; j += nt) {
+  for (int j = tid; j < n; j += nt) {  // (a left-out direction ranks last)
     double sq = 0.0;
     for (int r = 0; r < C; ++r) sq += colp[(size_t)r * n + j];
-    lam[j] = sqrt(sq) + sigma;
+    lam[j] = dkv[j] == (double)RR_DROPPED ? RR_DROP_DIAG : sqrt(sq) + sigma;
   }
   __syncthreads();
   for (int j = tid; j < n; j += nt) {
@@ -1287,12 +1384,12 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_cluster(KArgs ka, unsigned ch
       rk += (ek < ej) || (ek == ej && k2 < j);
     }
     rnk[j] = rk;
-    if (rank == 0) P.eps[rk] = ej;
+    if (rank == 0) rr_out_eps(P, rk, ej);
   }
   __syncthreads();
   for (int e = tid; e < myrows * n; e += nt) {
     const int i = rank + C * (e / n), j = e % n;
-    P.Tm[(size_t)i * n + rnk[j]] = (double)Lm[(size_t)i * n + j];
+    if (i < n) rr_out_vec(P, i, rnk[j], (double)Lm[(size_t)i * n + j]);
   }
   if (rank == 0 && tid == 0) {
     P.scal[SC_RRSWEEPS] += sweeps;
@@ -1317,7 +1414,7 @@ size_t rr_cluster_smem(int n) { return rr_cluster_smem_t(n, 4, rr_cluster_rows_f
 size_t rr_cluster_smem64(int n) { return rr_cluster_smem_t(n, 8, rr_cluster_rows_fit(n, 8)); }
 
 template <typename T>
-bool launch_rr_cluster(const Launch& L, int n_max, unsigned char* scratch, size_t stride, int max_sweeps) {
+bool launch_rr_cluster(const Launch& L, int n_max, unsigned char* scratch, size_t stride, int max_sweeps, int blk) {
   const bool rows_smem = rr_cluster_rows_fit(n_max, sizeof(T));
   const size_t smem = rr_cluster_smem_t(n_max, sizeof(T), rows_smem);
   if (smem > 227 * 1024) return false;
@@ -1334,11 +1431,11 @@ bool launch_rr_cluster(const Launch& L, int n_max, unsigned char* scratch, size_
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_rr_cluster<T>, L.ka, scratch, stride, max_sweeps, rows_smem ? 1 : 0) ==
+  return cudaLaunchKernelEx(&cfg, k_rr_cluster<T>, L.ka, scratch, stride, max_sweeps, rows_smem ? 1 : 0, blk) ==
          cudaSuccess;
 }
-template bool launch_rr_cluster<float>(const Launch&, int, unsigned char*, size_t, int);
-template bool launch_rr_cluster<double>(const Launch&, int, unsigned char*, size_t, int);
+template bool launch_rr_cluster<float>(const Launch&, int, unsigned char*, size_t, int, int);
+template bool launch_rr_cluster<double>(const Launch&, int, unsigned char*, size_t, int, int);
 
 // ---------------------------------------------------------------------------
 // Occupations: integer (kT = 0) or Fermi-Dirac with mu from sum f = N_el; entropy
@@ -1412,9 +1509,10 @@ void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole,
   if (!L.map.total) return;
   k_gemm_tn<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, arole, bkind, brole, part, stride, kc);
 }
-void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride, int kc) {
+void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride, int kc,
+                           bool sym) {
   if (!L.map.total) return;
-  k_gemm_tn_reduce<<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, bkind, dst, part, stride, kc);
+  k_gemm_tn_reduce<<<L.map.total, 256, 0, L.stream>>>(L.ka, akind, bkind, dst, part, stride, kc, sym ? 1 : 0);
 }
 template <typename T>
 void launch_gemm_nn(const Launch& L, int akind, const RolePairs& rp, int msel, double alpha, double beta) {
@@ -1462,11 +1560,41 @@ void launch_copy_out(const Launch& L, int role, double* dst, int nvec) {
   if (!L.map.total) return;
   k_copy_out<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, role, dst, nvec);
 }
-void launch_rr_f32(const Launch& L, size_t smem, float* gscratch, size_t gstride, int max_sweeps) {
-  k_rr_f32<<<L.ka.nprob, RR_THREADS, gscratch ? 0 : smem, L.stream>>>(L.ka, gscratch, gstride, max_sweeps);
+void launch_rr_f32(const Launch& L, size_t smem, float* gscratch, size_t gstride, int max_sweeps, int blk) {
+  k_rr_f32<<<L.ka.nprob, RR_THREADS, gscratch ? 0 : smem, L.stream>>>(L.ka, gscratch, gstride, max_sweeps, blk);
 }
-void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride, int max_sweeps) {
-  k_rr<<<L.ka.nprob, RR_THREADS, use_smem ? smem : 0, L.stream>>>(L.ka, use_smem, gscratch, gstride, max_sweeps);
+void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride, int max_sweeps,
+               int blk) {
+  k_rr<<<L.ka.nprob, RR_THREADS, use_smem ? smem : 0, L.stream>>>(L.ka, use_smem, gscratch, gstride, max_sweeps,
+                                                                     blk);
+}
+// S2 and H2 of the block [X, W] from n_b x n_b products (block Davidson): part 0 takes
+// S = X^T X, Hs = X^T HX, Tm = X^T W, Cm = X^T HW (the X rows and, by symmetry, the X
+// columns); part 1 takes S = W^T W, Hs = W^T HW (the W W block).  CTA = (problem, 256
+// entries of the n_b x n_b block).
+__global__ void k_rr2_assemble(KArgs ka, int part) {
+  const int p = locate(ka.start, ka.nprob, blockIdx.x);
+  if (!ka.active[p]) return;
+  const Prob& P = ka.probs[p];
+  const int nb = P.nb, n2 = 2 * nb;
+  const int e = (blockIdx.x - ka.start[p]) * 256 + threadIdx.x;
+  if (e >= nb * nb) return;
+  const int i = e / nb, j = e % nb;
+  if (part == 0) {
+    P.S2[(size_t)i * n2 + j] = P.S[e];
+    P.H2[(size_t)i * n2 + j] = P.Hs[e];
+    P.S2[(size_t)i * n2 + nb + j] = P.Tm[e];
+    P.S2[(size_t)(nb + j) * n2 + i] = P.Tm[e];
+    P.H2[(size_t)i * n2 + nb + j] = P.Cm[e];
+    P.H2[(size_t)(nb + j) * n2 + i] = P.Cm[e];
+  } else {
+    P.S2[(size_t)(nb + i) * n2 + nb + j] = P.S[e];
+    P.H2[(size_t)(nb + i) * n2 + nb + j] = P.Hs[e];
+  }
+}
+void launch_rr2_assemble(const Launch& L, int part) {
+  if (!L.map.total) return;
+  k_rr2_assemble<<<L.map.total, 256, 0, L.stream>>>(L.ka, part);
 }
 void launch_occupations(const Launch& L) { k_occupations<<<L.ka.nprob, 32, 0, L.stream>>>(L.ka); }
 void linalg_set_smem_limits(size_t bytes) {

@@ -122,8 +122,9 @@ void launch_plane_density_reg(const Launch& L, int cls, size_t smem, const doubl
 template <typename T>
 void launch_gemm_tn(const Launch& L, int akind, int arole, int bkind, int brole, double* part, size_t stride,
                     int kc = TN_KC);
+// sym: the partials are k_gemm_tn's A^T A (same operand twice; tiles below the diagonal mirrored)
 void launch_gemm_tn_reduce(const Launch& L, int akind, int bkind, int dst, const double* part, size_t stride,
-                           int kc = TN_KC);
+                           int kc = TN_KC, bool sym = false);
 // k_gemm_tc.cu (tcgen05 + TMA, mixed path, operand counts <= 128)
 constexpr int TC_NSLOT = NWB + 2;      // tensor maps per problem: wave buffers, B, dB
 constexpr int TC_NMAPKIND = 2;         // box 32 x 128 rows (TN), 32 x 32 rows (NN)
@@ -142,6 +143,7 @@ template <typename T>
 void launch_gemm_nn(const Launch& L, int akind, const RolePairs& rp, int msel, double alpha, double beta);
 template <typename T> void launch_band_kinetic(const Launch& L, int xrole);
 template <typename T> void launch_band_residual(const Launch& L, int xrole, int hxrole);
+// rp < 0: no conjugation (P = the preconditioned residual); pp < 0 in normalize: no history copy
 template <typename T> void launch_cg_precond(const Launch& L, int x, int hx, int p, int r, int pp, int rp);
 template <typename T> void launch_normalize(const Launch& L, int p, int pp);
 template <typename T> void launch_line_min(const Launch& L, int x, int hx, int p, int hp);
@@ -151,8 +153,13 @@ template <typename T> void launch_copy_in(const Launch& L, int role, const doubl
 template <typename T> void launch_copy_out(const Launch& L, int role, double* dst, int nvec);
 // subspace diagonalisation; max_sweeps caps the Jacobi sweeps (a stop at the cap is counted
 // in SC_RRCAP)
-void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride, int max_sweeps = 30);
-void launch_rr_f32(const Launch& L, size_t smem, float* gscratch = nullptr, size_t gstride = 0, int max_sweeps = 10);
+// blk = 1: the n_b x n_b subspace (S, Hs -> Tm); blk = 2: the 2 n_b block [X, W] of the block
+// Davidson step (S2, H2 -> the lowest n_b Ritz vectors, X coefficients in Tm, W in Cm)
+void launch_rr(const Launch& L, int use_smem, size_t smem, double* gscratch, size_t gstride, int max_sweeps = 30,
+               int blk = 1);
+void launch_rr_f32(const Launch& L, size_t smem, float* gscratch = nullptr, size_t gstride = 0, int max_sweeps = 10,
+                   int blk = 1);
+void launch_rr2_assemble(const Launch& L, int part);
 // Rayleigh-Ritz of large subspaces: one thread-block cluster per problem, matrices in a
 // per-problem global scratch of rr_cluster_scratch_bytes(n, sizeof(T)) bytes (T = float:
 // deviation-form FP32 as k_rr_f32; T = double: the same in FP64).  False if the launch
@@ -161,7 +168,7 @@ size_t rr_cluster_scratch_bytes(int n, size_t tsize);
 size_t rr_cluster_smem(int n);
 size_t rr_cluster_smem64(int n);
 template <typename T>
-bool launch_rr_cluster(const Launch& L, int n_max, unsigned char* scratch, size_t stride, int max_sweeps);
+bool launch_rr_cluster(const Launch& L, int n_max, unsigned char* scratch, size_t stride, int max_sweeps, int blk = 1);
 void launch_occupations(const Launch& L);
 void linalg_set_smem_limits(size_t bytes);
 

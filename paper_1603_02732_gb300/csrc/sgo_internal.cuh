@@ -188,6 +188,8 @@ struct Prob {
   double* Hs;                  // [nb*nb]
   double* Tm;                  // [nb*nb]
   double* Cm;                  // [nb*nb]
+  double* S2;                  // [4*nb*nb] overlap of the block [X, W] (block Davidson only, else null)
+  double* H2;                  // [4*nb*nb] its subspace matrix
   double* proj;                // [natom*nb]
   double* dproj;               // [3*natom*nb]
   double* eps;                 // [nb]

@@ -104,7 +104,7 @@ def _ledger_configs():
 
 
 @pytest.mark.parametrize("name", _ledger_configs())
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-rr64"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-rr64", "mixed-davidson"])
 def test_fullsize_error_ledger(sgo, name, precision):
     """Error ledger at full size against stored oracle values (tests/golden/ledger_*.json,
     written by tests/golden/make_ledger.py from oracle/ alone): every eigenvalue with
@@ -120,7 +120,9 @@ def test_fullsize_error_ledger(sgo, name, precision):
     its terms and eigenvalues carry errors of that order times their response (measured:
     eigenvalues 6.3e-5 Ha on the monolayer, the kinetic term 1.7e-5 Ha/atom on the 13-atom
     cluster) while F stays near 1e-6 Ha/atom.  mixed-rr64: the mixed path with the overlap
-    Cholesky and the subspace eigensolve in FP64 (the ablation of the FP32 eigensolve)."""
+    Cholesky and the subspace eigensolve in FP64 (the ablation of the FP32 eigensolve).
+    mixed-davidson: the mixed path with block Davidson steps (2 n_b Rayleigh-Ritz over
+    [X, W]) in place of Algorithm 1's CG steps, held to the same bounds."""
     import json
     import os
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"ledger_{name}.json")
@@ -130,6 +132,8 @@ def test_fullsize_error_ledger(sgo, name, precision):
                                                                                    scf_tol_rho=1e-5)
     if precision == "mixed-rr64":
         tol["rr_fp64"] = 1
+    if precision == "mixed-davidson":
+        tol["eigensolver"] = "davidson"
     ctx = sgo.Context(st, precision=precision.split("-")[0], **tol)
     E, F = ctx.energy_forces()
     n = st.natoms

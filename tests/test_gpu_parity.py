@@ -152,6 +152,51 @@ def test_scf_cluster_eigensolver(sgo, precision, rr_cluster):
     assert ctx.stats()["jacobi_cap_hits"] == 0
 
 
+@pytest.mark.parametrize("case", ["tiny", "bands112", "diamond8"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_scf_davidson(sgo, precision, case, request):
+    """Block Davidson steps (eigensolver = 1: per step the projected, preconditioned residuals
+    W of all bands and one Rayleigh-Ritz over the 2 n_b block [X, W]) reach the oracle's fixed
+    point like Algorithm 1's CG steps: free energy, forces and the occupied eigenvalues, on a
+    small cell, on a 112-band subspace (its 238 x 238 block goes to the cluster eigensolve)
+    and on the 8-atom diamond cell; both precisions."""
+    if case == "diamond8":
+        st, ref = request.getfixturevalue("diamond_ref")
+        mix = dict(mix_alpha=0.7, kerker_q0=0.0)
+    else:
+        st = _struct(ecut=3.0) if case == "tiny" else _struct(ecut=6.0, nbands=112)
+        ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)
+        mix = {}
+    if precision == "fp64":
+        ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=120,
+                          eigensolver="davidson", **mix)
+        tol_e, tol_f, tol_eig = (1e-7, 1e-5, 1e-6) if case == "diamond8" else (1e-8, 1e-6, 1e-7)
+    else:
+        ctx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5, max_scf=120,
+                          eigensolver="davidson", **mix)
+        tol_e, tol_f, tol_eig = 1e-5, 1e-4, 2e-4
+    _compare(st, ctx.energy_forces(), ref, tol_e, tol_f)
+    eig, _ = ctx.eigen()
+    assert np.abs(eig - ref.eig)[ref.occ > 1e-6].max() < tol_eig
+    stats = ctx.stats()
+    assert stats["jacobi_cap_hits"] == 0 and stats["eig_resid"] < 1e-4, stats
+
+
+def test_davidson_batch_equals_single(sgo):
+    """A batch of block-Davidson members gives each member's single-structure FP64 result
+    bit for bit; a batch that mixes eigensolvers is refused."""
+    sts = [_struct(seed=s, ecut=3.0) for s in (3, 4)]
+    opts = dict(precision="fp64", scf_tol_e=1e-10, scf_tol_rho=1e-8, max_scf=100, eigensolver="davidson")
+    singles = [sgo.Context(st, **opts).energy_forces() for st in sts]
+    E, F, status = sgo.Batch([sgo.Context(st, **opts) for st in sts]).energy_forces()
+    assert list(status) == [0, 0]
+    for i in range(2):
+        assert E[i] == singles[i][0] and np.array_equal(F[i], singles[i][1])
+    with pytest.raises(sgo.SgoError) as e:
+        sgo.Batch([sgo.Context(sts[0], **opts), sgo.Context(sts[1], precision="fp64")]).energy_forces()
+    assert e.value.status == sgo.SGO_ERR_ARG
+
+
 def test_scf_tiny_mixed(sgo):
     st = _struct(ecut=3.0)
     ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)

@@ -132,8 +132,10 @@ typedef struct {
                              Davidson steps: the preconditioned residuals W of all bands, projected
                              and normalised, and one Rayleigh-Ritz over the 2 n_b block [X, W]
                              keeping the lowest n_b Ritz pairs (its Cholesky and eigensolve are
-                             8x the n_b ones).  Same stopping rules; all members of a batch
-                             must agree (else SGO_ERR_ARG at sgo_batch_create). */
+                             8x the n_b ones; a W direction nearly inside the span of the
+                             others is left out).  Needs 2 n_b <= the plane-wave count (else
+                             SGO_ERR_ARG at sgo_create).  Same stopping rules; all members of a
+                             batch must agree (else SGO_ERR_ARG at sgo_batch_create). */
 } sgo_opts;
 
 /* Device memory through the caller's allocator.  The library's device buffers (context

@@ -559,6 +559,13 @@ sgo_status ctx_setup(sgo_ctx* c) {
     d.nb = d.npw;
     d.npair = (d.nb + 1) / 2;
   }
+  if (c->opts.eigensolver == 1 && 2 * d.nb > d.npw) {
+    dev_free(dprob);
+    dev_free(dstart);
+    dev_free(dact);
+    set_error("block Davidson needs 2 n_b (with the headroom bands) <= the number of plane waves");
+    return SGO_ERR_ARG;
+  }
 
   // ---- phase 2: allocation ----
   Counter cnt;

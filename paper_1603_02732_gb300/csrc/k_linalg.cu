@@ -973,18 +973,17 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
         pr_q[tid] = qq;
       }
       __syncthreads();
-      // every 2x2 block (P, Q) of A, then every entry of the rotated rows of V^T, as one
-      // flat index spread over all threads (rows / columns equal to n, the odd dummy, are
-      // absent; its pair never rotates)
-      const int nblk = half * half, ntot = nblk + half * n;
-      for (int e = tid; e < ntot; e += nt) {
-        if (e < nblk) {
-          const int P2 = e / half, Q2 = e - P2 * half;
-          const float sp = cs_s[P2], sq = cs_s[Q2];
+      // blocks (P, Q); rows / columns equal to n (the odd dummy) are absent
+      for (int P2 = ty; P2 < half; P2 += nty) {
+        const float sp = cs_s[P2], cp = cs_c[P2];
+        const int p0 = pr_p[P2], p1 = pr_q[P2];
+        const bool h1 = p1 < n;
+        for (int Q2 = tx; Q2 < half; Q2 += 32) {
+          const float sq = cs_s[Q2];
           if (sp == 0.f && sq == 0.f) continue;
-          const float cp = cs_c[P2], cq = cs_c[Q2];
-          const int p0 = pr_p[P2], p1 = pr_q[P2], q0 = pr_p[Q2], q1 = pr_q[Q2];
-          const bool h1 = p1 < n, g1 = q1 < n;
+          const float cq = cs_c[Q2];
+          const int q0 = pr_p[Q2], q1 = pr_q[Q2];
+          const bool g1 = q1 < n;
           const float a00 = A[p0 * ns + q0];
           const float a01 = g1 ? A[p0 * ns + q1] : 0.f;
           const float a10 = h1 ? A[p1 * ns + q0] : 0.f;
@@ -995,13 +994,14 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
           if (g1) A[p0 * ns + q1] = sq * b00 + cq * b01;
           if (h1) A[p1 * ns + q0] = cq * b10 - sq * b11;
           if (h1 && g1) A[p1 * ns + q1] = sq * b10 + cq * b11;
-        } else {
-          const int f = e - nblk;
-          const int Q2 = f / n, i = f - Q2 * n;
-          const float sq = cs_s[Q2];
-          if (sq == 0.f) continue;
-          const float cq = cs_c[Q2];
-          const int q0 = pr_p[Q2], q1 = pr_q[Q2];
+        }
+      }
+      for (int Q2 = ty; Q2 < half; Q2 += nty) {
+        const float sq = cs_s[Q2];
+        if (sq == 0.f) continue;
+        const float cq = cs_c[Q2];
+        const int q0 = pr_p[Q2], q1 = pr_q[Q2];
+        for (int i = tx; i < n; i += 32) {
           const float v0 = Vt[q0 * ns + i], v1 = Vt[q1 * ns + i];
           Vt[q0 * ns + i] = cq * v0 - sq * v1;
           Vt[q1 * ns + i] = sq * v0 + cq * v1;

@@ -11,7 +11,7 @@ Cohen, J. Phys. C 12, 4409 (1979)):
     E = sum_n f_n <psi_n| -1/2 nabla^2 + V_NL |psi_n>
       + Omega sum_G V_ion(G) rho(G)^*          (alpha term at G = 0)
       + (Omega/2) sum_{G!=0} 4 pi |rho(G)|^2 / G^2
-      + (Omega/N) sum_r rho(r) eps_xc(rho(r))   (LDA on the FFT grid)
+      + (Omega/N) sum_r rho(r) eps_xc(rho(r))   (LDA on the FFT grid; PBE: gga.py)
       + E_Ewald,          F = E - kT S  (Mermin free energy, reported)
 
 Conventions: psi(r) = Omega^{-1/2} sum_G c(G) exp(iG.r), sum |c|^2 = 1, over the
@@ -33,6 +33,7 @@ from scipy.special import expit
 
 from . import basis
 from .ewald import ewald
+from . import gga
 from .lda import lda
 from .pseudo import atomic_density_g, beta_g, vloc_g
 
@@ -153,7 +154,10 @@ def hartree(model, rho_r):
 
 
 def xc(model, rho_r):
-    """(E_xc, v_xc(r)) = ((Omega/N) sum_r rho eps_xc, d(rho eps)/d rho) with rho clipped at 0."""
+    """(E_xc, v_xc(r)) = ((Omega/N) sum_r rho eps_xc, d(rho eps)/d rho) with rho clipped at 0
+    (LDA), or PBE's energy and functional derivative (gga.pbe) for a structure with xc = "pbe"."""
+    if getattr(model.st, "xc", "lda") == "pbe":
+        return gga.pbe(model, rho_r)
     exc, vxc = lda(rho_r)
     return model.omega / model.N * float(np.sum(np.maximum(rho_r, 0.0) * exc)), vxc
 

@@ -45,6 +45,7 @@ class Structure:
     nbands: int
     fft: tuple                  # (N1, N2, N3)
     kT: float = 0.0             # Fermi-Dirac smearing, Ha; 0 = integer occupations
+    xc: str = "lda"             # exchange-correlation: "lda" (PZ81) or "pbe"
 
     @property
     def natoms(self) -> int:

@@ -136,6 +136,13 @@ typedef struct {
                              others is left out).  Needs 2 n_b <= the plane-wave count (else
                              SGO_ERR_ARG at sgo_create).  Same stopping rules; all members of a
                              batch must agree (else SGO_ERR_ARG at sgo_batch_create). */
+  int xc;                 /* exchange-correlation: 0 (default) LDA (Slater + Perdew-Zunger 1981);
+                             1 PBE (Perdew, Burke & Ernzerhof 1996, on Perdew-Wang 1992 uniform-gas
+                             correlation), the functional of the paper's searches (Sec. III): its
+                             potential de/drho - div(2 de/dsigma grad rho) takes the gradient and
+                             the divergence in G space on the FFT box (five extra grid transforms
+                             per potential, two per energy).  All members of a batch must agree
+                             (else SGO_ERR_ARG at sgo_batch_create). */
 } sgo_opts;
 
 /* Device memory through the caller's allocator.  The library's device buffers (context

@@ -106,7 +106,8 @@ class sgo_opts(ctypes.Structure):
                 ("seed", ctypes.c_ulonglong), ("gemm_tc", ctypes.c_int), ("graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("sub_batches", ctypes.c_int), ("eig_tol", ctypes.c_double),
                 ("max_polish", ctypes.c_int), ("rr_fp64", ctypes.c_int), ("watchdog_ms", ctypes.c_double),
-                ("extra_bands", ctypes.c_int), ("rr_cluster", ctypes.c_int), ("eigensolver", ctypes.c_int)]
+                ("extra_bands", ctypes.c_int), ("rr_cluster", ctypes.c_int), ("eigensolver", ctypes.c_int),
+                ("xc", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -251,6 +252,8 @@ def default_opts(**kw) -> sgo_opts:
             v = {"fp64": 0, "mixed": 1}.get(v, v) if isinstance(v, str) else int(v)
         if k == "eigensolver":
             v = {"cg": 0, "davidson": 1}.get(v, v) if isinstance(v, str) else int(v)
+        if k == "xc":
+            v = {"lda": 0, "pbe": 1}.get(v, v) if isinstance(v, str) else int(v)
         if k == "fft":
             for i in range(3):
                 o.fft[i] = int(v[i])
@@ -266,7 +269,8 @@ class Context:
     def __init__(self, st, precision="fp64", stream=None, **opts):
         self.lib = load_library()
         self.st = st
-        kw = dict(kT=float(st.kT), fft=tuple(int(x) for x in st.fft), precision=precision)
+        kw = dict(kT=float(st.kT), fft=tuple(int(x) for x in st.fft), precision=precision,
+                  xc=getattr(st, "xc", "lda"))
         kw.update(opts)
         self.opts = default_opts(**kw)
         cell = np.ascontiguousarray(st.cell, dtype=np.float64).reshape(9)

@@ -120,6 +120,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->extra_bands = -1;
   o->rr_cluster = -1;
   o->eigensolver = 0;
+  o->xc = 0;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,
@@ -226,8 +227,9 @@ sgo_status sgo_batch_create(int n, sgo_ctx* const* ctxs, sgo_batch** out) {
   }
   const sgo_opts& o = b->ctxs[0]->opts;
   for (int i = 1; i < n; ++i)
-    if (b->ctxs[i]->precision != b->ctxs[0]->precision || b->ctxs[i]->opts.eigensolver != o.eigensolver) {
-      sgo::set_error("the members of a batch must share precision and eigensolver");
+    if (b->ctxs[i]->precision != b->ctxs[0]->precision || b->ctxs[i]->opts.eigensolver != o.eigensolver ||
+        b->ctxs[i]->opts.xc != o.xc) {
+      sgo::set_error("the members of a batch must share precision, eigensolver and exchange-correlation");
       delete b;
       return SGO_ERR_ARG;
     }

@@ -318,6 +318,13 @@ void layout(sgo_ctx* c, A& a) {
   d.g2box = a.template take<double>(ng);
   d.gfft = a.template take<double2>(ng);
   d.gfft2 = a.template take<double2>(ng);
+  if (c->opts.xc == 1) {
+    d.gfft3 = a.template take<double2>(ng);
+    d.gfft4 = a.template take<double2>(ng);
+  } else {
+    d.gfft3 = d.gfft4 = nullptr;
+  }
+  d.xc = c->opts.xc;
   d.rhog_in = a.template take<double2>(ng);
   d.hrho = a.template take<double2>((size_t)MAX_HIST * ng);
   d.hres = a.template take<double2>((size_t)MAX_HIST * ng);
@@ -741,8 +748,8 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
       set_error("all members of a batch must use the same precision");
       return;
     }
-    if (c->opts.eigensolver != ctxs[0]->opts.eigensolver) {
-      set_error("all members of a batch must use the same eigensolver");
+    if (c->opts.eigensolver != ctxs[0]->opts.eigensolver || c->opts.xc != ctxs[0]->opts.xc) {
+      set_error("all members of a batch must use the same eigensolver and exchange-correlation");
       return;
     }
   }
@@ -921,6 +928,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   // thread-block cluster per member over a global scratch (k_rr_cluster)
   // (the block Davidson steps diagonalise the 2 n_b block [X, W])
   davidson_ = o0.eigensolver == 1;
+  gga_ = o0.xc == 1;
   rr_n_ = (davidson_ ? 2 : 1) * max_nb_;
   rr_f32_ = precision_ == 1 && !o0.rr_fp64;
   rr_smem_bytes_ = (size_t)3 * rr_n_ * rr_n_ * sizeof(double);
@@ -1311,8 +1319,23 @@ void Engine::scf_iteration(int ncg, bool count_iter) {
   // its absolute error swamps rho_in(r) where the density is small, and v_xc follows it)
   tbeg(TK_GRID_OTHER);
   launch_potential_g<double>(L(m_gew_));
+  if (gga_) launch_gga_grad(L(m_gew_), 0);
   tend(TK_GRID_OTHER);
   grid_fft(0, 1);
+  if (gga_) {
+    // PBE: grad rho_in (x + i y, z), then h = 2 de/dsigma grad rho to G space, div h back
+    grid_fft(2, 1);
+    grid_fft(3, 1);
+    tbeg(TK_GRID_OTHER);
+    launch_gga_point<T>(L(m_gew_));
+    tend(TK_GRID_OTHER);
+    grid_fft(2, -1);
+    grid_fft(3, -1);
+    tbeg(TK_GRID_OTHER);
+    launch_gga_div(L(m_gew_));
+    tend(TK_GRID_OTHER);
+    grid_fft(3, 1);
+  }
   tbeg(TK_GRID_OTHER);
   launch_veff<T>(L(m_gew_), nullptr);
   tend(TK_GRID_OTHER);
@@ -1345,6 +1368,13 @@ void Engine::density_energy(int mode) {
   launch_real_to_grid(L(m_gew_), 1, 1);
   tend(TK_GRID_OTHER);
   grid_fft(1, -1);
+  if (gga_) {  // PBE energy: grad rho_out
+    tbeg(TK_GRID_OTHER);
+    launch_gga_grad(L(m_gew_), 1);
+    tend(TK_GRID_OTHER);
+    grid_fft(2, 1);
+    grid_fft(3, 1);
+  }
   tbeg(TK_GRID_OTHER);
   launch_grid_energies<T>(L(m_gch_), d_gpart_, maxchunk_);
   launch_grid_energies_reduce(L(m_prob_), d_gpart_, maxchunk_);

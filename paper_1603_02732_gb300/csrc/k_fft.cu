@@ -284,14 +284,15 @@ __global__ void __launch_bounds__(PLANE_THREADS, sizeof(T) == 4 ? PLANE_MIN_BLOC
 
 // ---------------------------------------------------------------------------
 // Full FP64 complex grid transforms (in place): plane pass (x and y) and z pass.
-// which: 0 = gfft, 1 = gfft2.
+// which: 0 = gfft, 1 = gfft2, 2 = gfft3, 3 = gfft4 (the PBE grids).
 // ---------------------------------------------------------------------------
 // The work grids in the storage precision of a transform: FP64 complex (double and
 // float-float), or (FP32) the first half of the same memory viewed as single-precision
 // complex.
 template <typename T>
 __device__ __forceinline__ cplx<typename Work<T>::S>* grid_of(const Prob& P, int which) {
-  return reinterpret_cast<cplx<typename Work<T>::S>*>(which ? P.gfft2 : P.gfft);
+  double2* const g[4] = {P.gfft, P.gfft2, P.gfft3, P.gfft4};
+  return reinterpret_cast<cplx<typename Work<T>::S>*>(g[which & 3]);
 }
 
 template <typename T>

@@ -64,6 +64,10 @@ __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 __device__ __forceinline__ float log_t(float x) { return logf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+__device__ __forceinline__ float expm1_t(float x) { return expm1f(x); }
+__device__ __forceinline__ double expm1_t(double x) { return expm1(x); }
 
 // Perdew-Zunger 1981 correlation + Slater exchange (unpolarised); rho clipped at 0.
 // R = double on the FP64 path.  R = float on the mixed path: v_xc enters the FP32 V_eff
@@ -94,6 +98,101 @@ __device__ __forceinline__ void lda_pz81(R rho, R* exc, R* vxc) {
   }
   *exc = ex + ec;
   *vxc = R(4.0 / 3.0) * ex + vc;
+}
+
+// ---- PBE (Perdew, Burke & Ernzerhof 1996; uniform-gas correlation of Perdew & Wang 1992) ----
+// e(rho, sigma) = rho eps_xc with sigma = |grad rho|^2, and its two partial derivatives,
+// carried through the formula as first-order dual numbers (value, d/drho, d/dsigma).
+template <typename R>
+struct Dual {
+  R v, r, s;
+};
+template <typename R>
+__device__ __forceinline__ Dual<R> dmk(R v, R r, R s) {
+  Dual<R> d;
+  d.v = v;
+  d.r = r;
+  d.s = s;
+  return d;
+}
+template <typename R>
+__device__ __forceinline__ Dual<R> operator+(Dual<R> a, Dual<R> b) { return dmk(a.v + b.v, a.r + b.r, a.s + b.s); }
+template <typename R>
+__device__ __forceinline__ Dual<R> operator-(Dual<R> a, Dual<R> b) { return dmk(a.v - b.v, a.r - b.r, a.s - b.s); }
+template <typename R>
+__device__ __forceinline__ Dual<R> operator*(Dual<R> a, Dual<R> b) {
+  return dmk(a.v * b.v, a.r * b.v + a.v * b.r, a.s * b.v + a.v * b.s);
+}
+template <typename R>
+__device__ __forceinline__ Dual<R> operator/(Dual<R> a, Dual<R> b) {
+  const R q = a.v / b.v, ib = R(1) / b.v;
+  return dmk(q, (a.r - q * b.r) * ib, (a.s - q * b.s) * ib);
+}
+template <typename R>
+__device__ __forceinline__ Dual<R> operator+(Dual<R> a, R c) { return dmk(a.v + c, a.r, a.s); }
+template <typename R>
+__device__ __forceinline__ Dual<R> operator*(R c, Dual<R> a) { return dmk(c * a.v, c * a.r, c * a.s); }
+template <typename R>
+__device__ __forceinline__ Dual<R> dlog(Dual<R> a) {
+  const R ia = R(1) / a.v;
+  return dmk(log_t(a.v), a.r * ia, a.s * ia);
+}
+template <typename R>
+__device__ __forceinline__ Dual<R> dexpm1(Dual<R> a) {  // exp(a) - 1
+  const R e = exp_t(a.v);
+  return dmk(expm1_t(a.v), e * a.r, e * a.s);
+}
+template <typename R>
+__device__ __forceinline__ Dual<R> dsqrt(Dual<R> a) {
+  const R q = sqrt_t(a.v), h = R(0.5) / q;
+  return dmk(q, h * a.r, h * a.s);
+}
+template <typename R>
+__device__ __forceinline__ Dual<R> dcbrt(Dual<R> a) {
+  const R c = cbrt_t(a.v), h = c / (R(3) * a.v);
+  return dmk(c, h * a.r, h * a.s);
+}
+template <typename R>
+__device__ __forceinline__ Dual<R> dmin(Dual<R> a, R cap) { return a.v > cap ? dmk(cap, R(0), R(0)) : a; }
+
+constexpr double PBE_RHO_CUT = 1e-10;  // points below: e = 0 (near-empty regions)
+// Reduced gradients beyond this bound leave F_x and H saturated to 3e-8 relative: capped,
+// so that the FP32 path's intermediate products stay finite.
+constexpr double PBE_S2_CAP = 1e8;
+
+// (e, de/drho, de/dsigma) at one point; rho <= PBE_RHO_CUT gives zeros.
+template <typename R>
+__device__ __forceinline__ void pbe_point(R rho_v, R sigma_v, R* e, R* dr, R* ds) {
+  if (!(rho_v > R(PBE_RHO_CUT))) {
+    *e = *dr = *ds = R(0);
+    return;
+  }
+  const R kappa = R(0.804), beta = R(0.06672455060314922);
+  const R mu = R(0.06672455060314922 * 9.8696044010893586 / 3.0);  // beta pi^2 / 3
+  const R gamma = R(0.031090690869654895);                          // (1 - ln 2) / pi^2
+  const Dual<R> rho = dmk(rho_v, R(1), R(0));
+  const Dual<R> sig = dmk(sigma_v > R(0) ? sigma_v : R(0), R(0), R(1));
+  const Dual<R> c = dcbrt(rho);                          // rho^(1/3)
+  const Dual<R> kf = R(3.0936677262801355) * c;          // (3 pi^2)^(1/3) rho^(1/3)
+  const Dual<R> rho2 = rho * rho;
+  // exchange: -(3/4) (3/pi)^(1/3) rho^(4/3) F_x(s^2)
+  const Dual<R> s2 = dmin(sig / (R(4) * (kf * kf * rho2)), R(PBE_S2_CAP));
+  const Dual<R> fx = dmk(R(1) + kappa, R(0), R(0)) - kappa * (dmk(R(1), R(0), R(0)) / ((mu / kappa) * s2 + R(1)));
+  const Dual<R> ex = R(-0.75 * 0.98474502184269641) * (rho * c) * fx;
+  // correlation: rho (eps_c^PW92(r_s) + H(r_s, t^2))
+  const Dual<R> rs = R(0.62035049089940009) * (dmk(R(1), R(0), R(0)) / c);  // (3/(4 pi))^(1/3) / rho^(1/3)
+  const Dual<R> srs = dsqrt(rs);
+  const Dual<R> den = R(2 * 0.031091) *
+                      (R(7.5957) * srs + R(3.5876) * rs + R(1.6382) * (rs * srs) + R(0.49294) * (rs * rs));
+  const Dual<R> ec = R(-2 * 0.031091) * (R(0.21370) * rs + R(1)) * dlog(dmk(R(1), R(0), R(0)) / den + R(1));
+  const Dual<R> t2 = dmin(sig / ((R(4 * 4 / 3.14159265358979324) * kf) * (R(4) * rho2)), R(PBE_S2_CAP));
+  const Dual<R> a = (beta / gamma) * (dmk(R(1), R(0), R(0)) / dexpm1(R(-1) / gamma * ec));
+  const Dual<R> at2 = a * t2;
+  const Dual<R> h = gamma * dlog((beta / gamma) * (t2 * (at2 + R(1))) / (at2 + at2 * at2 + R(1)) + R(1));
+  const Dual<R> tot = ex + rho * (ec + h);
+  *e = tot.v;
+  *dr = tot.r;
+  *ds = tot.s;
 }
 
 }  // namespace
@@ -155,6 +254,10 @@ __global__ void k_veff(KArgs ka, const double* user_v) {
       int i1, i2, i3;
       grid_pt(P, i, &i1, &i2, &i3);
       val = user_v[((size_t)i1 * P.n2 + i2) * P.n3 + i3];
+    } else if (P.xc == 1) {  // PBE: gfft = rho + i (V_H + de/drho), gfft4 = div(2 de/dsigma grad rho)
+      const double2 c = P.gfft[i];
+      P.rho_in[i] = c.x;
+      val = P.vion_r[i] + c.y - P.gfft4[i].x;
     } else {
       const double2 c = P.gfft[i];
       T exc, vxc;
@@ -178,6 +281,65 @@ __global__ void k_potential_g(KArgs ka) {
     double f = g2 < 1e-14 ? 0.0 : 4.0 * PI / g2;
     // (r.x + i r.y) + i f (r.x + i r.y)
     g[i] = mk((T)(r.x - f * r.y), (T)(r.y + f * r.x));
+  }
+}
+
+// PBE gradient: gfft3 := (i G_x - G_y) rho(G), gfft4 := i G_z rho(G) (zero on Nyquist planes),
+// so that one inverse transform gives d_x rho + i d_y rho and another d_z rho.  src 0:
+// rho_in(G); src 1: N rho_out(G) in gfft2 (scaled by 1/N).
+__global__ void k_gga_grad(KArgs ka, int src) {
+  GRID_EW_PROLOGUE
+  const double sc = src ? 1.0 / P.ngrid : 1.0;
+  const double2* rg = src ? P.gfft2 : P.rhog_in;
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    const GPt q = grid_pt(P, i);
+    double G[3];
+    gcart(P, q.m1, q.m2, q.m3, G);
+    const double2 r = rg[i];
+    const double a = q.nyq ? 0.0 : r.x * sc, b = q.nyq ? 0.0 : r.y * sc;
+    P.gfft3[i] = make_double2(-G[0] * b - G[1] * a, G[0] * a - G[1] * b);
+    P.gfft4[i] = make_double2(-G[2] * b, G[2] * a);
+  }
+}
+
+// PBE at each point of rho_in(r) (real part of gfft) with grad rho_in (gfft3 = d_x + i d_y,
+// gfft4 = d_z): de/drho joins V_H in the imaginary part of gfft, and h = 2 de/dsigma grad rho
+// replaces the gradient (gfft3 = h_x + i h_y, gfft4 = h_z).
+template <typename T>
+__global__ void k_gga_point(KArgs ka) {
+  GRID_EW_PROLOGUE
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    const double2 c = P.gfft[i], gxy = P.gfft3[i];
+    const double gz = P.gfft4[i].x;
+    T e, dr, ds;
+    pbe_point<T>((T)fmax(c.x, 0.0), (T)(gxy.x * gxy.x + gxy.y * gxy.y + gz * gz), &e, &dr, &ds);
+    const double two_ds = 2.0 * (double)ds;
+    P.gfft[i] = make_double2(c.x, c.y + (double)dr);
+    P.gfft3[i] = make_double2(two_ds * gxy.x, two_ds * gxy.y);
+    P.gfft4[i] = make_double2(two_ds * gz, 0.0);
+  }
+}
+
+// div h in G space from the forward transforms F = N (h_x + i h_y)(G) (gfft3) and
+// N h_z(G) (gfft4): h_x(G) = (F(G) + F(-G)^*) / 2N, h_y(G) = (F(G) - F(-G)^*) / 2iN;
+// gfft4 := i G.h(G) (zero on Nyquist planes), whose inverse transform is div h.
+__global__ void k_gga_div(KArgs ka) {
+  GRID_EW_PROLOGUE
+  const double inv_n = 1.0 / P.ngrid;
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    int i1, i2, i3;
+    const GPt q = grid_pt(P, i, &i1, &i2, &i3);
+    double G[3];
+    gcart(P, q.m1, q.m2, q.m3, G);
+    const int j1 = i1 ? P.n1 - i1 : 0, j2 = i2 ? P.n2 - i2 : 0, j3 = i3 ? P.n3 - i3 : 0;
+    const int j = (j3 * P.n1 + j1) * P.n2 + j2;  // -G (plane-major index)
+    const double2 f = P.gfft3[i], fm = P.gfft3[j], hz = P.gfft4[i];
+    // h_x = (f + conj fm)/2, h_y = (f - conj fm)/(2i)
+    const double hxr = 0.5 * (f.x + fm.x), hxi = 0.5 * (f.y - fm.y);
+    const double hyr = 0.5 * (f.y + fm.y), hyi = -0.5 * (f.x - fm.x);
+    const double sr = G[0] * hxr + G[1] * hyr + G[2] * hz.x;  // G.h
+    const double si = G[0] * hxi + G[1] * hyi + G[2] * hz.y;
+    P.gfft4[i] = q.nyq ? make_double2(0.0, 0.0) : make_double2(-si * inv_n, sr * inv_n);  // i G.h / N
   }
 }
 
@@ -235,10 +397,18 @@ __global__ void k_grid_energies(KArgs ka, double* part, int maxchunk) {
   double s[NGE] = {0, 0, 0, 0, 0};
   for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
     double r = P.rho_out[i];
-    T exc, vxc;
-    lda_pz81<T>((T)r, &exc, &vxc);
+    if (P.xc == 1) {  // PBE with grad rho_out in gfft3 (x + i y) and gfft4 (z)
+      const double2 gxy = P.gfft3[i];
+      const double gz = P.gfft4[i].x;
+      T e, dr, ds;
+      pbe_point<T>((T)fmax(r, 0.0), (T)(gxy.x * gxy.x + gxy.y * gxy.y + gz * gz), &e, &dr, &ds);
+      s[1] += (double)e;
+    } else {
+      T exc, vxc;
+      lda_pz81<T>((T)r, &exc, &vxc);
+      s[1] += fmax(r, 0.0) * (double)exc;
+    }
     s[0] += P.vion_r[i] * r;
-    s[1] += fmax(r, 0.0) * (double)exc;
     s[2] += r;
     s[3] += fabs(r - P.rho_in[i]);
     const double g2 = P.g2box[i];  // -1 on Nyquist planes
@@ -598,6 +768,18 @@ void launch_hartree_g(const Launch& L, int which) {
 template <typename T>
 void launch_veff(const Launch& L, const double* user_v) {
   if (ew_blocks(L)) k_veff<T><<<L.map.total, 256, 0, L.stream>>>(L.ka, user_v);
+}
+void launch_gga_grad(const Launch& L, int src) {
+  if (ew_blocks(L)) k_gga_grad<<<L.map.total, 256, 0, L.stream>>>(L.ka, src);
+}
+template <typename T>
+void launch_gga_point(const Launch& L) {
+  if (ew_blocks(L)) k_gga_point<T><<<L.map.total, 256, 0, L.stream>>>(L.ka);
+}
+template void launch_gga_point<float>(const Launch&);
+template void launch_gga_point<double>(const Launch&);
+void launch_gga_div(const Launch& L) {
+  if (ew_blocks(L)) k_gga_div<<<L.map.total, 256, 0, L.stream>>>(L.ka);
 }
 template <typename T>
 void launch_potential_g(const Launch& L) {

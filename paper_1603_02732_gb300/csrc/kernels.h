@@ -181,6 +181,11 @@ void launch_export_grid(const Launch& L, int sel, double* out);
 // in != nullptr: gfft <- in; else out <- gfft (complex, C order (N1, N2, N3))
 void launch_grid_copy_c(const Launch& L, const double2* in, double2* out);
 template <typename T> void launch_veff(const Launch& L, const double* user_v);
+// PBE (grids gfft3 = x + i y, gfft4 = z components): src 0 grad of rho_in(G), 1 of the
+// forward-transformed rho_out in gfft2
+void launch_gga_grad(const Launch& L, int src);
+template <typename T> void launch_gga_point(const Launch& L);
+void launch_gga_div(const Launch& L);
 template <typename T> void launch_potential_g(const Launch& L);
 void launch_vion_g(const Launch& L);
 void launch_rho0_g(const Launch& L);

@@ -179,6 +179,9 @@ struct Prob {
   double* resid;               // [ngrid]
   double2* gfft;               // [ngrid]
   double2* gfft2;              // [ngrid]
+  double2* gfft3;              // [ngrid] PBE only (else null): grad rho, then 2 de/dsigma grad rho
+  double2* gfft4;              // [ngrid] PBE only: the third component, then div of the above
+  int xc;                      // 0 LDA, 1 PBE
   double2* rhog_in;            // [ngrid] rho_in(G), the mixed density (SCF state)
   double2* hrho;               // [MAX_HIST][ngrid] Pulay history of rho_in(G)
   double2* hres;               // [MAX_HIST][ngrid] Pulay history of R(G) = rho_out(G) - rho_in(G)

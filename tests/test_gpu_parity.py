@@ -204,6 +204,55 @@ def test_davidson_batch_equals_single(sgo):
     assert e.value.status == sgo.SGO_ERR_ARG
 
 
+@pytest.fixture(scope="module")
+def pbe_refs():
+    """Oracle PBE SCF results of the small cell and the 8-atom diamond cell."""
+    tiny = dataclasses.replace(_struct(ecut=3.0), xc="pbe")
+    dia = dataclasses.replace(workloads.diamond8(), xc="pbe")
+    return {"tiny": (tiny, oracle.scf(tiny, tol_e=1e-12, tol_rho=1e-10)),
+            "diamond8": (dia, oracle.scf(dia, mix=0.7, q0=0.0))}
+
+
+@pytest.mark.parametrize("case", ["tiny", "diamond8"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_scf_pbe(sgo, pbe_refs, precision, case):
+    """PBE exchange-correlation (xc = 1; the paper's functional, Sec. III): the potential
+    de/drho - div(2 de/dsigma grad rho) with the gradient and divergence in G space on the
+    FFT box, and E_xc at rho_out; SCF free energy, forces, occupied eigenvalues and the xc
+    term against the oracle's PBE (oracle/gga.py)."""
+    st, ref = pbe_refs[case]
+    mix = dict(mix_alpha=0.7, kerker_q0=0.0) if case == "diamond8" else {}
+    if precision == "fp64":
+        ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=150, **mix)
+        tol_e, tol_f, tol_eig = (1e-7, 1e-5, 1e-6) if case == "diamond8" else (1e-8, 1e-6, 1e-7)
+    else:
+        ctx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5, max_scf=150, **mix)
+        tol_e, tol_f, tol_eig = 1e-5, 1e-4, 2e-4
+    _compare(st, ctx.energy_forces(), ref, tol_e, tol_f)
+    eig, _ = ctx.eigen()
+    assert np.abs(eig - ref.eig)[ref.occ > 1e-6].max() < tol_eig
+    assert abs(ctx.terms()["xc"] - ref.terms["xc"]) / st.natoms < (1e-7 if precision == "fp64" else 1e-4)
+
+
+def test_pbe_forces_match_finite_differences_gpu(sgo):
+    """FP64 PBE: forces against central differences of the GPU free energy (h = 1e-3 bohr);
+    they agree only if the GPU's v_xc is the derivative of its E_xc."""
+    st = dataclasses.replace(_struct(ecut=3.0), xc="pbe")
+    ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-12, scf_tol_rho=1e-10, max_scf=150)
+    _, F = ctx.energy_forces()
+    h = 1e-3
+    for I, a in [(0, 0), (1, 1)]:
+        p = st.pos.copy()
+        p[I, a] += h
+        ep, _ = ctx.energy_forces(p)
+        p[I, a] -= 2 * h
+        em, _ = ctx.energy_forces(p)
+        assert abs(-(ep - em) / (2 * h) - F[I, a]) < 2e-5, (I, a)
+    with pytest.raises(sgo.SgoError) as e:
+        sgo.Batch([ctx, sgo.Context(_struct(ecut=3.0), precision="fp64")])
+    assert e.value.status == sgo.SGO_ERR_ARG
+
+
 def test_scf_tiny_mixed(sgo):
     st = _struct(ecut=3.0)
     ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)

@@ -185,7 +185,7 @@ __device__ __forceinline__ void pbe_point(R rho_v, R sigma_v, R* e, R* dr, R* ds
   const Dual<R> den = R(2 * 0.031091) *
                       (R(7.5957) * srs + R(3.5876) * rs + R(1.6382) * (rs * srs) + R(0.49294) * (rs * rs));
   const Dual<R> ec = R(-2 * 0.031091) * (R(0.21370) * rs + R(1)) * dlog(dmk(R(1), R(0), R(0)) / den + R(1));
-  const Dual<R> t2 = dmin(sig / ((R(4 * 4 / 3.14159265358979324) * kf) * (R(4) * rho2)), R(PBE_S2_CAP));
+  const Dual<R> t2 = dmin(sig / ((R(16 / 3.14159265358979324) * kf) * rho2), R(PBE_S2_CAP));  // 4 k_s^2 rho^2
   const Dual<R> a = (beta / gamma) * (dmk(R(1), R(0), R(0)) / dexpm1(R(-1) / gamma * ec));
   const Dual<R> at2 = a * t2;
   const Dual<R> h = gamma * dlog((beta / gamma) * (t2 * (at2 + R(1))) / (at2 + at2 * at2 + R(1)) + R(1));

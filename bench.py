@@ -680,11 +680,14 @@ def main():
     ap.add_argument("--ncg-first", type=int, default=None)
     ap.add_argument("--nonscf", type=int, default=None)
     ap.add_argument("--extra-bands", type=int, default=None, help="headroom bands (default: the library's)")
+    ap.add_argument("--cg-adapt", type=float, default=None,
+                    help="density residual above which an SCF iteration takes one CG step fewer")
     ap.add_argument("--mix-alpha", type=float, default=None, help="Pulay step (default: the library's)")
     ap.add_argument("--pulay-hist", type=int, default=None, help="Pulay history (default: the library's)")
     args = ap.parse_args()
     for k, v in (("ncg", args.ncg), ("ncg_first", args.ncg_first), ("n_nonscf", args.nonscf),
-                 ("extra_bands", args.extra_bands), ("mix_alpha", args.mix_alpha), ("pulay_hist", args.pulay_hist)):
+                 ("extra_bands", args.extra_bands), ("mix_alpha", args.mix_alpha), ("pulay_hist", args.pulay_hist),
+                 ("cg_adapt", args.cg_adapt)):
         if v is not None:
             _SCF[k] = v
     if args.no_graph:

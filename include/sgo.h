@@ -143,6 +143,10 @@ typedef struct {
                              the divergence in G space on the FFT box (five extra grid transforms
                              per potential, two per energy).  All members of a batch must agree
                              (else SGO_ERR_ARG at sgo_batch_create). */
+  double cg_adapt;        /* SCF iterations whose density residual (the previous iteration's) is
+                             above cg_adapt take ncg - 1 CG steps, the others ncg: the eigensolver
+                             works harder as the density converges.  0 = always ncg.  Default
+                             0 (taken from the first member of a batch). */
 } sgo_opts;
 
 /* Device memory through the caller's allocator.  The library's device buffers (context

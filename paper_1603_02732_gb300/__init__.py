@@ -107,7 +107,7 @@ class sgo_opts(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("sub_batches", ctypes.c_int), ("eig_tol", ctypes.c_double),
                 ("max_polish", ctypes.c_int), ("rr_fp64", ctypes.c_int), ("watchdog_ms", ctypes.c_double),
                 ("extra_bands", ctypes.c_int), ("rr_cluster", ctypes.c_int), ("eigensolver", ctypes.c_int),
-                ("xc", ctypes.c_int)]
+                ("xc", ctypes.c_int), ("cg_adapt", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -121,6 +121,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->rr_cluster = -1;
   o->eigensolver = 0;
   o->xc = 0;
+  o->cg_adapt = 0.0;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,

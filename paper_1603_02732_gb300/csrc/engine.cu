@@ -191,6 +191,19 @@ __global__ void k_scf_gate(const int* active, int n, const int* iter, int max_sc
 // residual |H x - eps x| below the tolerance.
 // mode 0: the members whose stopping rule held (and that have not failed) take part;
 // mode 1: of those, the members that took a step (their density and energy are redone).
+// Adaptive CG steps: mode 0 keeps the active mask in saved and leaves out of the next step
+// the members whose density residual is still above thr; mode 1 restores the mask.  One CTA.
+__global__ void k_cg_gate(KArgs ka, int* active, int* saved, double thr, int mode) {
+  for (int p = threadIdx.x; p < ka.nprob; p += blockDim.x) {
+    if (mode == 0) {
+      saved[p] = active[p];
+      if (active[p] && ka.probs[p].scal[SC_RESID] > thr) active[p] = 0;
+    } else {
+      active[p] = saved[p];
+    }
+  }
+}
+
 __global__ void k_polish_activate(KArgs ka, int* active, int mode) {
   for (int p = threadIdx.x; p < ka.nprob; p += blockDim.x) {
     const Prob& P = ka.probs[p];
@@ -883,6 +896,8 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   allocs_.push_back(d_flags_);
   if (!cuda_ok(dev_malloc(&d_iter_, 2 * sizeof(int)), "dev_malloc(iter)")) return;
   allocs_.push_back(d_iter_);
+  if (!cuda_ok(dev_malloc(&d_saved_, sizeof(int) * n_), "dev_malloc(saved mask)")) return;
+  allocs_.push_back(d_saved_);
   if (tc) {
     // TMA descriptors of every operand buffer (fixed for the engine's life; role swaps
     // select among them on the device) and the NN image scratch
@@ -928,6 +943,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   // thread-block cluster per member over a global scratch (k_rr_cluster)
   // (the block Davidson steps diagonalise the 2 n_b block [X, W])
   davidson_ = o0.eigensolver == 1;
+  cg_adapt_ = o0.cg_adapt;
   gga_ = o0.xc == 1;
   rr_n_ = (davidson_ ? 2 : 1) * max_nb_;
   rr_f32_ = precision_ == 1 && !o0.rr_fp64;
@@ -1342,7 +1358,13 @@ void Engine::scf_iteration(int ncg, bool count_iter) {
   hpsi<T>(WB_X, WB_HX);
   rayleigh_ritz<T>(false);
   set_scal(SC_FIRSTCG, 1.0, true);
-  for (int k = 0; k < ncg; ++k) eig_step<T>();
+  for (int k = 0; k < ncg; ++k) {
+    // (cg_adapt: the last step only for members whose density residual is below it)
+    const bool gate = count_iter && cg_adapt_ > 0.0 && ncg > 1 && k == ncg - 1;
+    if (gate) k_cg_gate<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, d_saved_, cg_adapt_, 0);
+    eig_step<T>();
+    if (gate) k_cg_gate<<<1, 256, 0, stream_>>>(L(m_prob_).ka, d_active_, d_saved_, cg_adapt_, 1);
+  }
   density_energy<T>(count_iter ? 1 : 0);
 }
 

@@ -199,6 +199,8 @@ class Engine {
   bool rr_cluster_ = false;          // subspace too large for one CTA: cluster eigensolve
   bool davidson_ = false;            // block Davidson steps (2 n_b Rayleigh-Ritz) instead of CG
   bool gga_ = false;                 // PBE exchange-correlation
+  double cg_adapt_ = 0.0;            // density residual above which the last CG step is left out
+  int* d_saved_ = nullptr;           // active mask kept across that step
   int rr_n_ = 0;                     // largest subspace of one Rayleigh-Ritz call
   unsigned char* d_rrc_ = nullptr;   // its per-member global scratch
   size_t rrc_stride_ = 0;

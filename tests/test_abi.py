@@ -49,7 +49,7 @@ def test_host_only_calls(lib):
     assert o.precision == 1 and abs(o.kT - 0.01) < 1e-15 and o.pulay_hist == 8
     # the fields after sub_batches sit where the library writes its defaults
     assert o.eig_tol == 1e-4 and o.max_polish == 40 and o.rr_fp64 == 0 and o.watchdog_ms == 0.0
-    assert o.extra_bands == -1 and o.rr_cluster == -1 and o.eigensolver == 0 and o.xc == 0
+    assert o.extra_bands == -1 and o.rr_cluster == -1 and o.eigensolver == 0 and o.xc == 0 and o.cg_adapt == 0.0
     assert lib.sgo_status_string(0) == b"ok"
     assert lib.sgo_status_string(2) == b"invalid geometry"
     # argument validation happens before any device work

@@ -35,7 +35,7 @@ from . import basis
 from .ewald import ewald
 from . import gga
 from .lda import lda
-from .pseudo import atomic_density_g, beta_g, vloc_g
+from .pseudo import atomic_density_g, beta_g, beta_p_g, vloc_g
 
 
 # ---------------------------------------------------------------------------
@@ -62,8 +62,20 @@ class Model:
         self.spec = np.asarray(st.species_of_atom, dtype=int)
         self.vloc_box = [vloc_g(sp, self.bg2, self.omega) * self.sym for sp in self.species]
         self.beta_sph = [beta_g(sp, self.g2, self.omega) for sp in self.species]
+        # p channel (species with d_p != 0): three projectors per atom after its s projector
+        self.betap_sph = [beta_p_g(sp, self.G, self.omega) if sp.get("d_p", 0.0) != 0.0 else None
+                          for sp in self.species]
         self.z = np.array([self.species[s]["z_val"] for s in self.spec])
-        self.d = np.array([self.species[s]["d_nl"] for s in self.spec])
+        # per projector (atom-major: s, then p_x, p_y, p_z where present): strength and atom
+        d, atom = [], []
+        for I, s in enumerate(self.spec):
+            d.append(self.species[s]["d_nl"])
+            atom.append(I)
+            if self.betap_sph[s] is not None:
+                d += [self.species[s]["d_p"]] * 3
+                atom += [I] * 3
+        self.d = np.array(d)
+        self.proj_atom = np.array(atom, dtype=int)
         self.nel = float(np.sum(self.z))
 
     # FFT-box transforms with the f(G) = (1/N) sum_r convention
@@ -93,8 +105,16 @@ def ionic_potential_g(model, pos):
 
 
 def projectors(model, pos):
-    """beta_I(G) = beta_s(G) exp(-iG.R_I) on the sphere, shape (natom, npw)."""
-    return np.array([model.beta_sph[s] * np.exp(-1j * (model.G @ pos[I])) for I, s in enumerate(model.spec)])
+    """beta_k(G) exp(-iG.R_I(k)) on the sphere for every projector k (atom-major: the s
+    projector of atom I, then its p_x, p_y, p_z where its species has a p channel), shape
+    (nproj, npw)."""
+    rows = []
+    for I, s in enumerate(model.spec):
+        ph = np.exp(-1j * (model.G @ pos[I]))
+        rows.append(model.beta_sph[s] * ph)
+        if model.betap_sph[s] is not None:
+            rows += [model.betap_sph[s][m] * ph for m in range(3)]
+    return np.array(rows)
 
 
 def initial_density(model, pos):
@@ -292,11 +312,11 @@ def forces(model, pos, C, f, beta, rho_out, f_ew):
         w = model.vloc_box[s] * ph * np.conj(rg)                       # d/dR adds (-iG)
         dE = model.omega * np.real(np.einsum("xyz,xyzc->c", -1j * w, model.bG))
         out[I] -= dE
-    P = beta.conj() @ C                                                # (natom, nb)
-    for I in range(n):
+    P = beta.conj() @ C                                                # (nproj, nb)
+    for k, I in enumerate(model.proj_atom):
         for a in range(3):
-            dP = (1j * model.G[:, a] * beta[I].conj()) @ C                # (nb,)
-            dE = float(np.sum(f * model.d[I] * 2.0 * np.real(np.conj(P[I]) * dP)))
+            dP = (1j * model.G[:, a] * beta[k].conj()) @ C                # (nb,)
+            dE = float(np.sum(f * model.d[k] * 2.0 * np.real(np.conj(P[k]) * dP)))
             out[I, a] -= dE
     return out
 

@@ -3,7 +3,9 @@
 The paper uses real norm-conserving / ultrasoft PBE potentials (Sec. II D), which
 are not available; the stand-in per species s is
     v_s(r) = -Z erf(r/rc)/r + A exp(-r^2/sigma^2)      (local)
-    D |beta><beta|, beta(r) = N exp(-r^2/(2 rp^2)), <beta|beta> = 1   (KB s-projector).
+    D |beta><beta|, beta(r) = N exp(-r^2/(2 rp^2)), <beta|beta> = 1   (KB s-projector)
+    + D_p sum_m |beta_m><beta_m|, beta_m(r) = N_p x_m exp(-r^2/(2 rp_p^2))   (optional p channel,
+      species keys d_p, rp_p; absent or d_p = 0: none).
 Fourier convention: f(G) = (1/Omega) int f(r) exp(-iG.r) d^3r for the local
 part; <G|beta> with |G> = Omega^{-1/2} exp(iG.r) for the projector.
 """
@@ -43,3 +45,18 @@ def beta_g(sp, g2, omega):
 def atomic_density_g(sp, g2, omega):
     """Initial-guess neutral Gaussian charge of Z electrons per atom: (Z/Omega) exp(-G^2 rc^2/4)."""
     return sp["z_val"] * np.exp(-np.asarray(g2) * sp["rc"] ** 2 / 4.0) / omega
+
+
+def beta_p_g(sp, G, omega):
+    """<G|beta_m>, m = x, y, z, for the p-channel projector at the origin, shape (3,) + G.shape[:-1].
+
+    beta_m(r) = N_p x_m exp(-r^2/(2 s^2)) with s = rp_p and N_p = (pi^{3/2} s^5 / 2)^{-1/2}
+    (so <beta_m|beta_m> = 1: the integral of x^2 exp(-r^2/s^2) is pi^{3/2} s^5 / 2).  Its
+    transform is i d/dG_m of the Gaussian's, (2 pi)^{3/2} s^3 exp(-G^2 s^2/2):
+    <G|beta_m> = Omega^{-1/2} N_p (-i G_m s^2) (2 pi)^{3/2} s^3 exp(-G^2 s^2 / 2)."""
+    s_ = sp["rp_p"]
+    norm = 1.0 / math.sqrt(PI32 * s_ ** 5 / 2.0)
+    G = np.asarray(G, dtype=np.float64)
+    g2 = np.einsum("...i,...i->...", G, G)
+    radial = norm * (2.0 * math.pi) ** 1.5 * s_ ** 3 * s_ * s_ * np.exp(-g2 * s_ * s_ / 2.0) / math.sqrt(omega)
+    return np.stack([-1j * G[..., m] * radial for m in range(3)])

@@ -30,6 +30,9 @@ SPECIES_Z4 = dict(z_val=4.0, rc=1.0, a_sr=0.5, sigma_sr=0.8, rp=0.9, d_nl=1.0)
 SPECIES_Z10 = dict(z_val=10.0, rc=1.2, a_sr=0.5, sigma_sr=1.0, rp=1.1, d_nl=0.8)
 
 SPECIES_KEYS = ("z_val", "rc", "a_sr", "sigma_sr", "rp", "d_nl")
+# optional p channel of the nonlocal part: beta_m(r) = N_p x_m exp(-r^2/(2 rp_p^2)), strength d_p
+SPECIES_P_KEYS = ("rp_p", "d_p")
+SPECIES_Z4_P = dict(SPECIES_Z4, rp_p=1.0, d_p=0.6)
 
 
 @dataclasses.dataclass

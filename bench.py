@@ -680,6 +680,8 @@ def main():
     ap.add_argument("--ncg-first", type=int, default=None)
     ap.add_argument("--nonscf", type=int, default=None)
     ap.add_argument("--extra-bands", type=int, default=None, help="headroom bands (default: the library's)")
+    ap.add_argument("--rr-cluster", type=int, default=None, choices=[0, 1],
+                    help="subspace eigensolve on an 8-CTA cluster per member (1) or one CTA (0)")
     ap.add_argument("--cg-adapt", type=float, default=None,
                     help="density residual above which an SCF iteration takes one CG step fewer")
     ap.add_argument("--mix-alpha", type=float, default=None, help="Pulay step (default: the library's)")
@@ -687,7 +689,7 @@ def main():
     args = ap.parse_args()
     for k, v in (("ncg", args.ncg), ("ncg_first", args.ncg_first), ("n_nonscf", args.nonscf),
                  ("extra_bands", args.extra_bands), ("mix_alpha", args.mix_alpha), ("pulay_hist", args.pulay_hist),
-                 ("cg_adapt", args.cg_adapt)):
+                 ("cg_adapt", args.cg_adapt), ("rr_cluster", args.rr_cluster)):
         if v is not None:
             _SCF[k] = v
     if args.no_graph:

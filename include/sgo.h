@@ -10,7 +10,8 @@
  * Physics (the paper names none; these are the fixed readings): Gamma point,
  * norm-conserving synthetic analytic pseudopotential per species (local
  * -Z erf(r/rc)/r + A exp(-r^2/sigma^2), one Kleinman-Bylander Gaussian s
- * projector of strength D), LDA (Slater + Perdew-Zunger 1981), Ewald ions,
+ * projector of strength D, optionally three p projectors x_m exp(-r^2/(2 rp_p^2)) of
+ * strength D_p), LDA (Slater + Perdew-Zunger 1981; or PBE), Ewald ions,
  * Fermi-Dirac smearing with the Mermin free energy F = E - kT S reported.
  * Units: Hartree atomic units (Ha, bohr).
  *
@@ -70,6 +71,8 @@ typedef struct {
   double sigma_sr;  /* width sigma of the short-range Gaussian */
   double rp;        /* projector Gaussian width */
   double d_nl;      /* Kleinman-Bylander strength D */
+  double rp_p;      /* p channel: width of the projectors x_m exp(-r^2/(2 rp_p^2)), m = x, y, z */
+  double d_p;       /* p channel strength; 0 = no p channel (then rp_p is ignored) */
 } sgo_species;
 
 typedef struct {

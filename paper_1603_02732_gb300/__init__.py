@@ -38,7 +38,8 @@ class SgoError(RuntimeError):
 
 class sgo_species(ctypes.Structure):
     _fields_ = [("z_val", ctypes.c_double), ("rc", ctypes.c_double), ("a_sr", ctypes.c_double),
-                ("sigma_sr", ctypes.c_double), ("rp", ctypes.c_double), ("d_nl", ctypes.c_double)]
+                ("sigma_sr", ctypes.c_double), ("rp", ctypes.c_double), ("d_nl", ctypes.c_double),
+                ("rp_p", ctypes.c_double), ("d_p", ctypes.c_double)]
 
 
 class sgo_relax_opts(ctypes.Structure):
@@ -264,7 +265,8 @@ def default_opts(**kw) -> sgo_opts:
 
 class Context:
     """One structure on the GPU (sgo_create).  `st` has cell, species (list of dicts with
-    z_val, rc, a_sr, sigma_sr, rp, d_nl), species_of_atom, pos, ecut, nbands, fft, kT."""
+    z_val, rc, a_sr, sigma_sr, rp, d_nl and optionally rp_p, d_p), species_of_atom, pos, ecut,
+    nbands, fft, kT (and optionally xc)."""
 
     def __init__(self, st, precision="fp64", stream=None, **opts):
         self.lib = load_library()
@@ -274,8 +276,9 @@ class Context:
         kw.update(opts)
         self.opts = default_opts(**kw)
         cell = np.ascontiguousarray(st.cell, dtype=np.float64).reshape(9)
-        sp = (sgo_species * len(st.species))(*[sgo_species(*(float(s[k]) for k in
-                                                             ("z_val", "rc", "a_sr", "sigma_sr", "rp", "d_nl")))
+        sp = (sgo_species * len(st.species))(*[sgo_species(*(float(s.get(k, 0.0)) for k in
+                                                             ("z_val", "rc", "a_sr", "sigma_sr", "rp", "d_nl",
+                                                              "rp_p", "d_p")))
                                               for s in st.species])
         spec = np.ascontiguousarray(st.species_of_atom, dtype=np.int32)
         pos = np.ascontiguousarray(st.pos, dtype=np.float64).reshape(-1)

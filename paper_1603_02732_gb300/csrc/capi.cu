@@ -152,6 +152,12 @@ sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp,
     sgo::set_error("cudaGetDevice failed");
     return SGO_ERR_CUDA;
   }
+  for (int s = 0; s < nspecies; ++s)
+    if (!(sp[s].rp > 0.0) || (sp[s].d_p != 0.0 && !(sp[s].rp_p > 0.0)) || !std::isfinite(sp[s].d_p)) {
+      delete c;
+      sgo::set_error("projector widths must be positive (rp, and rp_p where d_p != 0)");
+      return SGO_ERR_ARG;
+    }
   double nel = 0.0;
   for (int a = 0; a < natoms; ++a) {
     if (species_of_atom[a] < 0 || species_of_atom[a] >= nspecies) {

@@ -317,8 +317,14 @@ void layout(sgo_ctx* c, A& a) {
   d.pos = a.template take<double>(3 * na);
   d.spec = a.template take<int>(na);
   for (int i = 0; i < NWB; ++i) d.wb[i] = a.template take<char>((size_t)nb * ld * ts);
-  d.B = a.template take<char>((size_t)na * ld * ts);
-  d.dB = a.template take<char>((size_t)3 * na * ld * ts);
+  const int npj = d.nproj;
+  d.B = a.template take<char>((size_t)npj * ld * ts);
+  d.dB = a.template take<char>((size_t)3 * npj * ld * ts);
+  d.pj_atom = a.template take<int>(npj);
+  d.pj_kind = a.template take<int>(npj);
+  d.pj_d = a.template take<double>(npj);
+  d.pj_rp = a.template take<double>(npj);
+  d.pj_first = a.template take<int>(na + 1);
   d.Wc = a.template take<char>((size_t)d.npair * d.n3 * d.ncol * 2 * ts);
   const PlanePaths pp = plane_paths(d, c->precision);
   d.Gp = (pp.pbig || pp.dbig) ? a.template take<char>(big_plane_bytes(d.npair, d.n3, d.m1max, d.n2, ts)) : nullptr;
@@ -352,8 +358,8 @@ void layout(sgo_ctx* c, A& a) {
   } else {
     d.S2 = d.H2 = nullptr;
   }
-  d.proj = a.template take<double>((size_t)na * nb);
-  d.dproj = a.template take<double>((size_t)3 * na * nb);
+  d.proj = a.template take<double>((size_t)npj * nb);
+  d.dproj = a.template take<double>((size_t)3 * npj * nb);
   d.eps = a.template take<double>(nb);
   d.occ = a.template take<double>(nb);
   d.bv = a.template take<double>((size_t)NBANDSCAL * nb);
@@ -499,6 +505,28 @@ sgo_status ctx_setup(sgo_ctx* c) {
   }
   d.nel = 0.0;
   for (int a = 0; a < d.natom; ++a) d.nel += c->species[c->spec[a]].z_val;
+  // projector list (atom-major: s, then p_x, p_y, p_z for a species with a p channel)
+  c->pj_atom.clear();
+  c->pj_kind.clear();
+  c->pj_d.clear();
+  c->pj_rp.clear();
+  c->pj_first.assign(1, 0);
+  for (int a = 0; a < d.natom; ++a) {
+    const sgo_species& q = c->species[c->spec[a]];
+    c->pj_atom.push_back(a);
+    c->pj_kind.push_back(0);
+    c->pj_d.push_back(q.d_nl);
+    c->pj_rp.push_back(q.rp);
+    if (q.d_p != 0.0)
+      for (int m = 0; m < 3; ++m) {
+        c->pj_atom.push_back(a);
+        c->pj_kind.push_back(1 + m);
+        c->pj_d.push_back(q.d_p);
+        c->pj_rp.push_back(q.rp_p);
+      }
+    c->pj_first.push_back((int)c->pj_atom.size());
+  }
+  d.nproj = (int)c->pj_atom.size();
   d.kT = c->opts.kT;
   for (int i = 0; i < NWB; ++i) d.role[i] = i;
   d.nb = c->nb_int;
@@ -608,6 +636,12 @@ sgo_status ctx_setup(sgo_ctx* c) {
   std::vector<int> spec(c->spec);
   CK(cudaMemcpyAsync(d.spec, spec.data(), spec.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(d.pos, c->pos.data(), c->pos.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.pj_atom, c->pj_atom.data(), sizeof(int) * d.nproj, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.pj_kind, c->pj_kind.data(), sizeof(int) * d.nproj, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.pj_d, c->pj_d.data(), sizeof(double) * d.nproj, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.pj_rp, c->pj_rp.data(), sizeof(double) * d.nproj, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.pj_first, c->pj_first.data(), sizeof(int) * (d.natom + 1), cudaMemcpyHostToDevice,
+                     c->stream));
   CK(cudaMemcpyAsync(dprob, &d, sizeof(Prob), cudaMemcpyHostToDevice, c->stream));
   launch_basis_fill(L1);
   launch_roots(L1);
@@ -679,7 +713,7 @@ void Engine::build_gemm_maps() {
   for (auto* c : ctx_) {
     const Prob& d = c->d;
     const int nsplit = div_up(d.npw, tn_kc_);
-    const int tw = div_up(d.nb, TN_TILE), ta = div_up(d.natom, TN_TILE), td = div_up(3 * d.natom, TN_TILE);
+    const int tw = div_up(d.nb, TN_TILE), ta = div_up(d.nproj, TN_TILE), td = div_up(3 * d.nproj, TN_TILE);
     ww.push_back(tw * tw * nsplit);
     bw.push_back(ta * tw * nsplit);
     dw.push_back(td * tw * nsplit);
@@ -768,10 +802,10 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   }
   std::vector<Prob> host(n_);
   std::vector<int> c_zcol, c_plane, c_dens, c_gz, c_gp, c_gew, c_gch, c_bands, c_tnww, c_tnbw, c_tndw, c_rww, c_rbw,
-      c_rdw, c_nn, c_atoms, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2], c_dreg[2], c_zreg[2], c_ppair,
+      c_rdw, c_nn, c_atoms, c_projs, c_atomch, c_ewsg, c_prob, c_tc, c_nntc, c_preg[2], c_dreg[2], c_zreg[2], c_ppair,
       c_dpair, c_zpair, c_gx, c_gy, c_bigy, c_bigx, c_bigdy, c_bigd;
   size_t part = 0;
-  int max_natom = 0;
+  int max_nproj = 0;
   for (int p = 0; p < n_; ++p) {
     const Prob& d = ctxs[p]->d;
     host[p] = d;
@@ -828,15 +862,16 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     c_gch.push_back(nch);
     c_bands.push_back(d.nb);
     c_rww.push_back(div_up(d.nb * d.nb, 256));
-    c_rbw.push_back(div_up(d.natom * d.nb, 256));
-    c_rdw.push_back(div_up(3 * d.natom * d.nb, 256));
+    c_rbw.push_back(div_up(d.nproj * d.nb, 256));
+    c_rdw.push_back(div_up(3 * d.nproj * d.nb, 256));
     c_nn.push_back(div_up(d.npw, 64 * NN_RT) * div_up(d.nb, 64));
     c_atoms.push_back(d.natom);
+    c_projs.push_back(d.nproj);
     c_atomch.push_back(div_up(d.natom, LF_GROUP) * nch);
     c_ewsg.push_back(div_up(ctxs[p]->ngbox_ew, 256));
     c_prob.push_back(1);
-    max_natom = std::max(max_natom, d.natom);
-    size_t need = (size_t)nsplit * std::max({d.nb * d.nb, d.natom * d.nb, 3 * d.natom * d.nb});
+    max_nproj = std::max(max_nproj, d.nproj);
+    size_t need = (size_t)nsplit * std::max({d.nb * d.nb, d.nproj * d.nb, 3 * d.nproj * d.nb});
     part = std::max(part, need);
   }
   plane_threads_ = PLANE_THREADS;
@@ -865,6 +900,7 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   m_red_dw_ = make_map(c_rdw);
   m_nn_ = make_map(c_nn);
   m_atoms_ = make_map(c_atoms);
+  m_projs_ = make_map(c_projs);
   m_atomch_ = make_map(c_atomch);
   m_ewsg_ = make_map(c_ewsg);
   m_prob_ = make_map(c_prob);
@@ -872,9 +908,9 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
   // NN image of at most 128 x 128), at least two NN pipeline stages beside the image
   const bool tc = precision_ == 1 && ctxs[0]->opts.gemm_tc != 0;
   tc_ok_[OPK_WB] = tc && max_nb_ <= 128;
-  tc_ok_[OPK_B] = tc && max_nb_ <= 128 && max_natom <= 128;
-  tc_ok_[OPK_DB] = tc && max_nb_ <= 128 && 3 * max_natom <= 128;
-  const int nin_max[3] = {max_nb_, max_natom, 3 * max_natom};
+  tc_ok_[OPK_B] = tc && max_nb_ <= 128 && max_nproj <= 128;
+  tc_ok_[OPK_DB] = tc && max_nb_ <= 128 && 3 * max_nproj <= 128;
+  const int nin_max[3] = {max_nb_, max_nproj, 3 * max_nproj};
   for (int k = 0; k < 3; ++k) {
     nnimg_max_[k] = nn_tc_image_bytes(nin_max[k], max_nb_);
     nn_tc_ok_[k] = tc_ok_[k] && nn_tc_stages(nnimg_max_[k]) >= 2;
@@ -1318,8 +1354,8 @@ sgo_status Engine::structure_terms() {
   launch_vion_g(L(m_gew_));
   grid_fft(0, 1);
   launch_grid_real_part(L(m_gew_), 0, 3);
-  if (precision_) launch_build_projectors<float>(la, 0);
-  else launch_build_projectors<double>(la, 0);
+  if (precision_) launch_build_projectors<float>(L(m_projs_), 0);
+  else launch_build_projectors<double>(L(m_projs_), 0);
   launch_ewald(L(m_ewsg_), la, L(m_prob_));
   return cuda_ok(cudaGetLastError(), "structure terms") ? SGO_OK : SGO_ERR_CUDA;
 }
@@ -1625,7 +1661,7 @@ sgo_status Engine::launch_t(bool want_forces) {
   h_active_.assign(n_, 1);
   CK(cudaMemcpyAsync(d_active_, h_active_.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, stream_));
   if (want_forces) {
-    launch_build_projectors<T>(L(m_atoms_), 1);
+    launch_build_projectors<T>(L(m_projs_), 1);
     tn<T>(OPK_DB, 0, OPK_WB, WB_X, DD_DPROJ, false);
     tn<T>(OPK_B, 0, OPK_WB, WB_X, DD_PROJ, false);
     launch_real_to_grid(L(m_gew_), 1, 0);

@@ -33,6 +33,9 @@ struct sgo_ctx {
   std::vector<sgo_species> species;
   std::vector<int> spec;
   std::vector<double> pos;
+  // projector list (host copy of the device arrays pj_*)
+  std::vector<int> pj_atom, pj_kind, pj_first;
+  std::vector<double> pj_d, pj_rp;
   double ecut = 0.0;
   int nb = 0;         // requested bands (occupied and reported)
   int nb_int = 0;     // bands the eigensolver carries: nb plus empty headroom (sgo_opts.extra_bands)
@@ -175,7 +178,7 @@ class Engine {
   std::vector<void*> allocs_;
   int max_n1_ = 0, max_n2_ = 0, max_n3_ = 0, max_n12_ = 0, max_nb_ = 0, plane_threads_ = 128;
   WorkMap m_zcol_, m_plane_, m_dens_, m_gz_, m_gp_, m_gew_, m_gch_, m_bands_, m_tn_ww_, m_tn_bw_, m_tn_dw_,
-      m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_atomch_, m_ewsg_, m_prob_, m_tc_, m_nntc_;
+      m_red_ww_, m_red_bw_, m_red_dw_, m_nn_, m_atoms_, m_projs_, m_atomch_, m_ewsg_, m_prob_, m_tc_, m_nntc_;
   WorkMap m_preg_[2], m_dreg_[2], m_zreg_[2];  // register-FFT plane / column kernels, per size class
   size_t preg_smem_[2] = {0, 0}, dreg_smem_[2] = {0, 0}, zreg_smem_[2] = {0, 0};
   WorkMap m_ppair_, m_dpair_, m_zpair_;         // lane-pair register FFT kernels (lengths 96-128)

@@ -213,7 +213,7 @@ __device__ __forceinline__ void split_transpose(const unsigned char* raw, unsign
 }
 
 __device__ __forceinline__ int count_tc(const Prob& P, int kind) {
-  return kind == OPK_WB ? P.nb : (kind == OPK_B ? P.natom : 3 * P.natom);
+  return kind == OPK_WB ? P.nb : (kind == OPK_B ? P.nproj : 3 * P.nproj);
 }
 
 // map slot of an operand: wave buffers by physical index, then B, dB
@@ -389,7 +389,7 @@ __global__ void k_nn_image(KArgs ka, int akind, int msel, float* img_base, size_
     float v = 0.f;
     if (i < nin && j < nb) {
       double m = M[(size_t)i * nb + j];
-      if (msel == DD_PROJ_D) m *= P.sp[P.spec[i] * 6 + 5];
+      if (msel == DD_PROJ_D) m *= P.pj_d[i];
       v = (float)m;
     }
     const float h = tf32_round(v), l = tf32_round(v - h);
@@ -619,7 +619,7 @@ bool tc_encode_maps(const Prob& d, void* host_maps) {
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(host_maps);
   for (int s = 0; s < TC_NSLOT; ++s) {
     const void* base = s < NWB ? d.wb[s] : (s == NWB ? d.B : d.dB);
-    const int rows = s < NWB ? d.nb : (s == NWB ? d.natom : 3 * d.natom);
+    const int rows = s < NWB ? d.nb : (s == NWB ? d.nproj : 3 * d.nproj);
     if (!encode_2d(m + s * TC_NMAPKIND + 0, base, d.npw, rows, d.ld, std::min(128, (rows + 7) & ~7))) return false;
     if (!encode_2d(m + s * TC_NMAPKIND + 1, base, d.npw, rows, d.ld, 32)) return false;
   }

@@ -450,9 +450,9 @@ __global__ void k_finish_iteration(KArgs ka, double tol_e, double tol_rho, int c
     const double f = P.occ[i];
     ek += f * P.bv[BV_EKIN * P.nb + i];
     double s = 0.0;
-    for (int a = 0; a < P.natom; ++a) {
-      double pr = P.proj[(size_t)a * P.nb + i];
-      s += P.sp[P.spec[a] * 6 + 5] * pr * pr;
+    for (int k = 0; k < P.nproj; ++k) {
+      double pr = P.proj[(size_t)k * P.nb + i];
+      s += P.pj_d[k] * pr * pr;
     }
     en += f * s;
   }
@@ -604,38 +604,51 @@ __global__ void k_pulay_mix(KArgs ka, double a, double q0) {
 }
 
 // ---------------------------------------------------------------------------
-// Projectors (packed real form): B[I] = pack(beta_s(G) exp(-iG.R_I)) and, for the
-// forces, dB[3I+a] = pack(-i G_a beta_I(G)) = (G_a b_im, -G_a b_re).
-// beta_s(G) = Omega^{-1/2} N (2 pi)^{3/2} rp^3 exp(-G^2 rp^2/2), N^2 = 1/(pi^{3/2} rp^3).
-// CTA = (problem, atom).
+// Projectors (packed real form): B[k] = pack(beta_k(G) exp(-iG.R_I)) for projector k of atom
+// I and, for the forces, dB[3k+a] = pack(-i G_a B[k](G)) = (G_a b_im, -G_a b_re).
+//   s: beta(G) = Omega^{-1/2} N (2 pi)^{3/2} rp^3 exp(-G^2 rp^2/2), N^2 = 1/(pi^{3/2} rp^3);
+//   p_m: beta(G) = -i G_m Omega^{-1/2} N_p (2 pi)^{3/2} s^5 exp(-G^2 s^2/2), N_p^2 = 2/(pi^{3/2} s^5)
+//        (the transform of N_p x_m exp(-r^2/(2 s^2)), zero at G = 0).
+// CTA = (problem, projector).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_build_projectors(KArgs ka, int deriv) {
   const int p = locate(ka.start, ka.nprob, blockIdx.x);
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
-  const int a = blockIdx.x - ka.start[p];
-  const double* sp = P.sp + P.spec[a] * 6;
-  const double rp = sp[4];
-  const double nrm = 1.0 / sqrt(pow(PI, 1.5) * rp * rp * rp);
-  const double amp = nrm * pow(2.0 * PI, 1.5) * rp * rp * rp / sqrt(P.omega);
-  T* b = reinterpret_cast<T*>(P.B) + (size_t)a * P.ld;
-  T* d0 = deriv ? reinterpret_cast<T*>(P.dB) + (size_t)(3 * a) * P.ld : nullptr;
+  const int k = blockIdx.x - ka.start[p];
+  const int a = P.pj_atom[k], kind = P.pj_kind[k];
+  const double rp = P.pj_rp[k];
+  const double r3 = rp * rp * rp;
+  // radial amplitude: s N (2 pi)^{3/2} rp^3; p N_p (2 pi)^{3/2} s^5 (times -i G_m below)
+  const double amp = kind == 0 ? (1.0 / sqrt(pow(PI, 1.5) * r3)) * pow(2.0 * PI, 1.5) * r3 / sqrt(P.omega)
+                               : sqrt(2.0 / (pow(PI, 1.5) * r3 * rp * rp)) * pow(2.0 * PI, 1.5) * r3 * rp * rp /
+                                     sqrt(P.omega);
+  T* b = reinterpret_cast<T*>(P.B) + (size_t)k * P.ld;
+  T* d0 = deriv ? reinterpret_cast<T*>(P.dB) + (size_t)(3 * k) * P.ld : nullptr;
   const int* em1 = P.ent_m3 - 2 * P.nhalf;
   const int* em2 = P.ent_m3 - P.nhalf;
-  for (int k = threadIdx.x; k <= P.nhalf; k += blockDim.x) {
-    if (k == 0) {
-      if (!deriv) b[0] = (T)amp;
+  for (int t = threadIdx.x; t <= P.nhalf; t += blockDim.x) {
+    if (t == 0) {  // G = 0: the s amplitude; a p projector has none
+      if (!deriv) b[0] = (T)(kind == 0 ? amp : 0.0);
       else for (int c = 0; c < 3; ++c) d0[(size_t)c * P.ld] = T(0);
       continue;
     }
-    const int e = k - 1;
+    const int e = t - 1;
     const double g2 = 2.0 * P.ekin[1 + 2 * e];
     const double bg = amp * exp(-0.5 * g2 * rp * rp);
     const int m1 = em1[e], m2 = em2[e], m3 = P.ent_m3[e];
     const int i1 = m1 < 0 ? m1 + P.n1 : m1, i2 = m2 < 0 ? m2 + P.n2 : m2, i3 = m3 < 0 ? m3 + P.n3 : m3;
     cplx<double> ph = phase_at(P, a, i1, i2, i3);
-    const double bre = SQRT2 * bg * ph.x, bim = SQRT2 * bg * ph.y;
+    double bre, bim;
+    if (kind == 0) {
+      bre = SQRT2 * bg * ph.x;
+      bim = SQRT2 * bg * ph.y;
+    } else {  // -i c ph with c = G_m bg: (c ph.y, -c ph.x)
+      const double cm = P.gvec[(size_t)(kind - 1) * P.ld + 1 + 2 * e] * bg;
+      bre = SQRT2 * cm * ph.y;
+      bim = -SQRT2 * cm * ph.x;
+    }
     if (!deriv) {
       b[1 + 2 * e] = (T)bre;
       b[2 + 2 * e] = (T)bim;
@@ -703,7 +716,8 @@ __global__ void k_local_forces(KArgs ka, int maxchunk) {
   }
 }
 
-// Total: local partials + nonlocal -2 D sum_n f_n p_nI dp_nIa + Ewald.  CTA per problem.
+// Total: local partials + nonlocal -2 sum_k D_k sum_n f_n p_nk dp_nka over the atom's
+// projectors k + Ewald.  CTA per problem.
 __global__ void k_force_total(KArgs ka, int maxchunk) {
   (void)maxchunk;
   const int p = blockIdx.x;
@@ -714,11 +728,14 @@ __global__ void k_force_total(KArgs ka, int maxchunk) {
     const int a = e / 3, c = e % 3;
     double s = 0.0;
     for (int k = 0; k < nch; ++k) s += P.fpart[((size_t)a * nch + k) * 3 + c];
-    const double D = P.sp[P.spec[a] * 6 + 5];
-    double nl = 0.0;
-    for (int n = 0; n < P.nb; ++n)
-      nl += P.occ[n] * P.proj[(size_t)a * P.nb + n] * P.dproj[(size_t)(3 * a + c) * P.nb + n];
-    P.forces[e] = s - 2.0 * D * nl + P.ewald_f[e];
+    double nl = 0.0;  // sum over the atom's projectors k of D_k sum_n f_n p_nk dp_nka
+    for (int k = P.pj_first[a]; k < P.pj_first[a + 1]; ++k) {
+      double t = 0.0;
+      for (int n = 0; n < P.nb; ++n)
+        t += P.occ[n] * P.proj[(size_t)k * P.nb + n] * P.dproj[(size_t)(3 * k + c) * P.nb + n];
+      nl += P.pj_d[k] * t;
+    }
+    P.forces[e] = s - 2.0 * nl + P.ewald_f[e];
   }
 }
 

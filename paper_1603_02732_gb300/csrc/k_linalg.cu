@@ -28,7 +28,7 @@ __device__ __forceinline__ const T* opnd(const Prob& P, int kind, int role) {
   return reinterpret_cast<const T*>(P.dB);
 }
 __device__ __forceinline__ int opnd_count(const Prob& P, int kind) {
-  return kind == OPK_WB ? P.nb : (kind == OPK_B ? P.natom : 3 * P.natom);
+  return kind == OPK_WB ? P.nb : (kind == OPK_B ? P.nproj : 3 * P.nproj);
 }
 __device__ __forceinline__ double* dense_ptr(const Prob& P, int sel) {
   switch (sel) {
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(KArgs ka, int akind, RolePairs 
           double mv = 0.0;
           if (c0 + cc < nb) {
             mv = M[(size_t)k * nb + c0 + cc];
-            if (msel == DD_PROJ_D) mv *= P.sp[P.spec[k] * 6 + 5];
+            if (msel == DD_PROJ_D) mv *= P.pj_d[k];
           }
           Ms[e] = (T)mv;
         }

@@ -74,14 +74,14 @@ sgo_status run(sgo_ctx* c, const double* veff, int nvec, const double* psi, doub
   const Prob& d = c->d;
   cudaStream_t st = c->stream;
   const int nsplit = div_up(d.npw, TN_KC);
-  const size_t part_stride = (size_t)nsplit * d.natom * d.nb;
+  const size_t part_stride = (size_t)nsplit * d.nproj * d.nb;
   // layout of the scratch array
   size_t off = 0;
   const size_t o_prob = off;
   off = align256(off + sizeof(Prob));
   const size_t o_act = off;
   off = align256(off + sizeof(int));
-  enum { M_ZCOL = 0, M_PLANE, M_BANDS, M_ATOMS, M_TN, M_RED, M_NN, M_GEW, NMAP };
+  enum { M_ZCOL = 0, M_PLANE, M_BANDS, M_ATOMS, M_TN, M_RED, M_NN, M_GEW, M_PROJ, NMAP };
   const size_t o_maps = off;
   off = align256(off + sizeof(int) * 2 * NMAP);
   const size_t o_part = off;
@@ -103,8 +103,8 @@ sgo_status run(sgo_ctx* c, const double* veff, int nvec, const double* psi, doub
     return SGO_ERR_ARG;
   }
   const int counts[NMAP] = {d.npair * div_up(d.ncp, QCP), d.npair * d.n3, d.nb, d.natom,
-                            div_up(d.natom, TN_TILE) * div_up(d.nb, TN_TILE) * nsplit, div_up(d.natom * d.nb, 256),
-                            div_up(d.npw, 64 * NN_RT) * div_up(d.nb, 64), div_up(d.ngrid, GRID_EW_POINTS)};
+                            div_up(d.nproj, TN_TILE) * div_up(d.nb, TN_TILE) * nsplit, div_up(d.nproj * d.nb, 256),
+                            div_up(d.npw, 64 * NN_RT) * div_up(d.nb, 64), div_up(d.ngrid, GRID_EW_POINTS), d.nproj};
   int maps[2 * NMAP];
   for (int i = 0; i < NMAP; ++i) {
     maps[2 * i] = 0;
@@ -145,7 +145,7 @@ sgo_status run(sgo_ctx* c, const double* veff, int nvec, const double* psi, doub
   double* dpsi = reinterpret_cast<double*>(base + o_psi);
   double* dout = reinterpret_cast<double*>(base + o_out);
   launch_phases(launch(M_ATOMS));
-  launch_build_projectors<T>(launch(M_ATOMS), 0);
+  launch_build_projectors<T>(launch(M_PROJ), 0);
   launch_veff<T>(launch(M_GEW), reinterpret_cast<const double*>(base + o_veff));
   launch_copy_in<T>(launch(M_BANDS), WB_W, dpsi, nvec);
   launch_wave_to_cols<T>(launch(M_ZCOL), WB_W);

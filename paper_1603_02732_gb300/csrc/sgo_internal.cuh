@@ -164,8 +164,16 @@ struct Prob {
   // wave buffers (element type = engine precision)
   void* wb[NWB];               // each [nb][ld], physical buffers
   int role[NWB];               // role -> physical buffer of this problem (swapped on the device)
-  void* B;                     // [natom][ld] projectors
-  void* dB;                    // [3*natom][ld] projector derivatives (forces)
+  void* B;                     // [nproj][ld] projectors
+  void* dB;                    // [3*nproj][ld] projector derivatives (forces)
+  // projectors, atom-major (the s projector of each atom, then its p_x, p_y, p_z where the
+  // species has a p channel): atom, kind (0 s, 1 + m p_m), strength, width; first of each atom
+  int nproj;
+  int* pj_atom;                // [nproj]
+  int* pj_kind;                // [nproj]
+  double* pj_d;                // [nproj]
+  double* pj_rp;               // [nproj]
+  int* pj_first;               // [natom + 1]
   void* Wc;                    // complex [npair][n3][ncol]
   void* Gp;                    // complex [npair][n3][2 m1max + 1][n2]: occupied x rows of the
                                // planes (big-plane path only, else null)
@@ -193,8 +201,8 @@ struct Prob {
   double* Cm;                  // [nb*nb]
   double* S2;                  // [4*nb*nb] overlap of the block [X, W] (block Davidson only, else null)
   double* H2;                  // [4*nb*nb] its subspace matrix
-  double* proj;                // [natom*nb]
-  double* dproj;               // [3*natom*nb]
+  double* proj;                // [nproj*nb]
+  double* dproj;               // [3*nproj*nb]
   double* eps;                 // [nb]
   double* occ;                 // [nb]
   double* bv;                  // [NBANDSCAL][nb]

@@ -253,6 +253,74 @@ def test_pbe_forces_match_finite_differences_gpu(sgo):
     assert e.value.status == sgo.SGO_ERR_ARG
 
 
+def _struct_p(grid=None, ecut=3.0, seed=7):
+    """The small cell with a p channel on its species."""
+    st = workloads.tiny(nat=2, ecut=ecut, seed=seed, kT=0.01, species=workloads.SPECIES_Z4_P)
+    return dataclasses.replace(st, fft=tuple(grid)) if grid is not None else st
+
+
+@pytest.mark.parametrize("grid", [None, (30, 54, 40), (60, 50, 12)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_apply_hamiltonian_pchannel(sgo, grid, precision):
+    """Species with a p channel (three projectors x_m exp(-r^2/(2 rp_p^2)) per atom after the s
+    projector): H psi against the oracle's dense H, whose nonlocal part sums the eight
+    projectors of the two atoms with their own strengths."""
+    st = _struct_p(grid=grid)
+    ctx = sgo.Context(st, precision=precision)
+    m = dft.Model(st)
+    miller = ctx.basis()
+    rng = np.random.default_rng(13)
+    veff = rng.normal(size=m.grid) * 0.3
+    x = rng.normal(size=(st.nbands, ctx.npw))
+    y = ctx.apply_hamiltonian(veff, x)
+    H = dft.dense_h(m, veff, dft.projectors(m, st.pos))
+    y_ref = H @ full_from_packed(m, miller, x)
+    tol = 1e-11 if precision == "fp64" else 2e-5
+    assert np.abs(full_from_packed(m, miller, y) - y_ref).max() < tol * np.abs(y_ref).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_scf_pchannel(sgo, precision):
+    """SCF energy, forces, occupied eigenvalues and the nonlocal term with the p channel against
+    the oracle."""
+    st = _struct_p()
+    ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)
+    if precision == "fp64":
+        ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=120)
+        tol_e, tol_f, tol_eig, tol_t = 1e-8, 1e-6, 1e-7, 1e-7
+    else:
+        ctx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7, scf_tol_rho=1e-5, max_scf=120)
+        tol_e, tol_f, tol_eig, tol_t = 1e-5, 1e-4, 2e-4, 1e-4
+    _compare(st, ctx.energy_forces(), ref, tol_e, tol_f)
+    eig, _ = ctx.eigen()
+    assert np.abs(eig - ref.eig)[ref.occ > 1e-6].max() < tol_eig
+    assert abs(ctx.terms()["nonlocal"] - ref.terms["nonlocal_"]) / st.natoms < tol_t
+
+
+def test_pchannel_forces_and_mixed_batch(sgo):
+    """FP64 with the p channel: forces against central differences of the GPU free energy, and
+    a batch of a p-channel member and an s-only member gives each one's single result bit for
+    bit (members with different projector counts share every launch)."""
+    st = _struct_p()
+    opts = dict(precision="fp64", scf_tol_e=1e-12, scf_tol_rho=1e-10, max_scf=150)
+    ctx = sgo.Context(st, **opts)
+    E0, F = ctx.energy_forces()
+    h = 1e-3
+    for I, a in [(0, 2), (1, 0)]:
+        p = st.pos.copy()
+        p[I, a] += h
+        ep, _ = ctx.energy_forces(p)
+        p[I, a] -= 2 * h
+        em, _ = ctx.energy_forces(p)
+        assert abs(-(ep - em) / (2 * h) - F[I, a]) < 2e-5, (I, a)
+    sts = [_struct_p(seed=3), _struct(seed=4, ecut=3.0)]
+    singles = [sgo.Context(t, **opts).energy_forces() for t in sts]
+    E, Fb, status = sgo.Batch([sgo.Context(t, **opts) for t in sts]).energy_forces()
+    assert list(status) == [0, 0]
+    for i in range(2):
+        assert E[i] == singles[i][0] and np.array_equal(Fb[i], singles[i][1])
+
+
 def test_scf_tiny_mixed(sgo):
     st = _struct(ecut=3.0)
     ref = oracle.scf(st, tol_e=1e-12, tol_rho=1e-10)

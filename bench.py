@@ -487,14 +487,20 @@ def run_ours(args):
 def _variant_record(sgo, pop, pos_host, E, F, args):
     """Variants on the same population, precision and stopping rule, each against the default
     path: the block Davidson eigensolver (2 n_b Rayleigh-Ritz over [X, W] per step) in place of
-    Algorithm 1's all-band CG (same energies), and PBE in place of LDA (a different
-    functional: the energy differences are the functional's).  Evals/s through the
-    host-pointer call, SCF iterations, Jacobi sweeps per member."""
+    Algorithm 1's all-band CG (same energies), PBE in place of LDA, and a p channel added to
+    every species' projectors (three more projectors per atom; PBE and the p channel change the
+    Hamiltonian: their energy differences are the model's).  Evals/s through the host-pointer
+    call, SCF iterations, Jacobi sweeps per member."""
     import torch
     rec = {}
     nat = np.array([st.natoms for st in pop])
-    for name, extra in (("davidson", dict(eigensolver="davidson")), ("pbe", dict(xc="pbe"))):
-        ctxv = [sgo.Context(st, precision=args.precision, **extra, **_tols(args.precision, st)) for st in pop]
+    import dataclasses
+    import workloads
+    pop_p = [dataclasses.replace(st, species=[dict(sp, **{k: workloads.SPECIES_Z4_P[k] for k in workloads.SPECIES_P_KEYS})
+                                              for sp in st.species]) for st in pop]
+    for name, extra, members in (("davidson", dict(eigensolver="davidson"), pop), ("pbe", dict(xc="pbe"), pop),
+                                 ("p_channel", {}, pop_p)):
+        ctxv = [sgo.Context(st, precision=args.precision, **extra, **_tols(args.precision, st)) for st in members]
         bv = sgo.Batch(ctxv)
         bv.energy_forces()
         torch.cuda.synchronize()

@@ -73,7 +73,7 @@ cudaError_t dev_malloc_bytes(void** p, size_t bytes, cudaStream_t s) {
   return cudaMemset(*p, 0, bytes);
 }
 
-void dev_free(void* p) {
+void dev_free(void* p, bool synced) {
   if (!p) return;
   Hooked h{nullptr, nullptr};
   bool found = false;
@@ -91,7 +91,7 @@ void dev_free(void* p) {
     return;
   }
   // the caller's pool may hand the block out again at once: no kernel may still use it
-  cudaDeviceSynchronize();
+  if (!synced) cudaDeviceSynchronize();
   if (h.release) h.release(p, nullptr, h.user);
 }
 
@@ -1017,7 +1017,8 @@ Engine::~Engine() {
   if (hp_) cudaFreeHost(hp_);
   if (hpi_) cudaFreeHost(hpi_);
   for (auto& v : ev_) cudaEventDestroy(v);
-  for (void* p : allocs_) dev_free(p);
+  if (!allocs_.empty()) cudaDeviceSynchronize();  // once for all the blocks below
+  for (void* p : allocs_) dev_free(p, true);
 }
 
 // ---- live kernel timing ----

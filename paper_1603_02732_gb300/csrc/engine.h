@@ -267,7 +267,7 @@ cudaError_t dev_malloc(P** p, size_t bytes, cudaStream_t s = nullptr) {
   *p = static_cast<P*>(v);
   return e;
 }
-void dev_free(void* p);
+void dev_free(void* p, bool synced = false);  // synced: the device was synchronised already
 
 // Context set-up (basis on the device, allocation, tables).  Returns status.
 sgo_status ctx_setup(sgo_ctx* c);

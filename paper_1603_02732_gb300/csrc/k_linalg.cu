@@ -961,9 +961,10 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
         if (qq < n) {
           const float apq = A[pp * ns + qq];
           if (fabsf(apq) > thr) {
-            const float tau = (A[qq * ns + qq] - A[pp * ns + pp]) / (2.f * apq);
-            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + t * t);
+            // (fast reciprocals: any orthogonal rotation near the exact one converges the sweep)
+            const float tau = __fdividef(A[qq * ns + qq] - A[pp * ns + pp], 2.f * apq);
+            const float t = copysignf(__fdividef(1.f, fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f))), tau);
+            c = rsqrtf(fmaf(t, t, 1.f));
             s = t * c;
           }
         }

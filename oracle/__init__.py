@@ -13,5 +13,5 @@ textbook constants, brute force or invariants.  The whole-pipeline numbers have
 no counterpart in the paper (it prints none for this synthetic model): parity
 against the paper itself is unpinned; each component is pinned separately.
 """
-from . import basis, dft, ewald, gga, lda, pseudo  # noqa: F401
+from . import basis, dft, ewald, gga, kpoints, lda, pseudo  # noqa: F401
 from .dft import Model, Result, evaluate, scf  # noqa: F401

@@ -328,6 +328,8 @@ def scf(st, pos=None, tol_e=1e-8, tol_rho=1e-7, max_iter=200, mix=0.5, q0=0.8, h
     Stops when |F_k - F_{k-1}| < tol_e (Ha) and (Omega/N) sum |rho_out - rho_in| / N_el < tol_rho.
     Mixing: Pulay (DIIS) on the residual rho_out - rho_in with a Kerker-damped step.
     """
+    if tuple(getattr(st, "kgrid", (1, 1, 1))) != (1, 1, 1):
+        raise ValueError("a k-point mesh: oracle.kpoints.scf")
     model = Model(st) if model is None else model
     pos = np.asarray(st.pos if pos is None else pos, dtype=np.float64).reshape(-1, 3)
     nb = int(st.nbands)

@@ -49,6 +49,7 @@ class Structure:
     fft: tuple                  # (N1, N2, N3)
     kT: float = 0.0             # Fermi-Dirac smearing, Ha; 0 = integer occupations
     xc: str = "lda"             # exchange-correlation: "lda" (PZ81) or "pbe"
+    kgrid: tuple = (1, 1, 1)    # Gamma-centred k mesh n1 x n2 x n3; (1, 1, 1) = the Gamma point
 
     @property
     def natoms(self) -> int:
@@ -284,6 +285,20 @@ def de_search_population(n: int = 8, natoms: int = 8, seed: int = 5000, dmin: fl
                 pos.append(p)
         out.append(dataclasses.replace(base, name=f"dex{k}", pos=np.array(pos), kT=0.01))
     return out
+
+
+def supercell(st: Structure, reps) -> Structure:
+    """The reps[0] x reps[1] x reps[2] supercell of st at the Gamma point: lattice vectors
+    reps_i a_i, the atoms of every translate t (t-major: t = 0 first, the atoms in st's
+    order), reps_1 reps_2 reps_3 times the bands and the FFT grid scaled per axis."""
+    reps = tuple(int(x) for x in reps)
+    ts = [(a, b, c) for a in range(reps[0]) for b in range(reps[1]) for c in range(reps[2])]
+    pos = np.concatenate([st.pos + np.array(t, dtype=np.float64) @ st.cell for t in ts])
+    return dataclasses.replace(st, name=f"{st.name}_x{reps[0]}{reps[1]}{reps[2]}",
+                               cell=st.cell * np.array(reps, dtype=np.float64)[:, None],
+                               species_of_atom=np.tile(st.species_of_atom, len(ts)), pos=pos,
+                               nbands=st.nbands * len(ts), fft=tuple(n * r for n, r in zip(st.fft, reps)),
+                               kgrid=(1, 1, 1))
 
 
 def tiny(nat: int = 2, ecut: float = 3.0, seed: int = 7, kT: float = 0.01, nbands: int = None,

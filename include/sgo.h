@@ -150,6 +150,18 @@ typedef struct {
                              above cg_adapt take ncg - 1 CG steps, the others ncg: the eigensolver
                              works harder as the density converges.  0 = always ncg.  Default
                              0 (taken from the first member of a batch). */
+  int kgrid[3];           /* Brillouin-zone sampling (the rough k-point grids of the relaxations,
+                             Sec. II C): the Gamma-centred Monkhorst-Pack mesh k = sum_i (t_i/n_i) b_i,
+                             t_i = 0..n_i-1, weights 1/(n1 n2 n3).  Computed by zone folding: the
+                             context holds the n1 x n2 x n3 supercell at the Gamma point, whose
+                             plane waves are exactly the k + G of the mesh, so its energy per cell,
+                             forces and spectrum are those of the mesh (same cutoff; nbands per k
+                             point on average).  The caller keeps passing and receiving the cell's
+                             natoms positions and forces; energies (sgo_energy_forces, sgo_get_terms)
+                             are per cell; nbands, the eigenvalues, states, grids and the component
+                             calls are the supercell's (n1 n2 n3 times nbands, fft[i] times n_i when
+                             given).  Entries <= 0 count as 1; {1, 1, 1} (default) = the Gamma point.
+                             sgo_energy_forces_batch_device refuses such contexts (SGO_ERR_ARG). */
 } sgo_opts;
 
 /* Device memory through the caller's allocator.  The library's device buffers (context
@@ -173,6 +185,7 @@ SGO_API void sgo_opts_default(sgo_opts* o);
  * species_of_atom: natoms indices into sp.  pos: natoms*3 Cartesian bohr.
  * ecut: |G|^2/2 <= ecut (Ha).  nbands >= N_el/2 (integer occupations) or > N_el/2 (kT > 0).
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * With o->kgrid above {1, 1, 1} the context is the folded supercell (see sgo_opts.kgrid).
  * Allocates all device memory of the context; *out is NULL on error. */
 SGO_API sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms,
                       const int* species_of_atom, const double* pos, double ecut, int nbands,
@@ -212,7 +225,8 @@ SGO_API sgo_status sgo_energy_forces_batch(sgo_batch* b, const double* const* po
 
 /* Same as sgo_energy_forces_batch with every array in DEVICE memory: pos_dev
  * (sum natoms_i*3 doubles, members back to back), energies_dev (n), forces_dev
- * (sum natoms_i*3), status_dev (n ints).  Synchronises the batch stream. */
+ * (sum natoms_i*3), status_dev (n ints).  Synchronises the batch stream.  SGO_ERR_ARG for a
+ * batch with a k-point member (sgo_opts.kgrid): use sgo_energy_forces_batch. */
 SGO_API sgo_status sgo_energy_forces_batch_device(sgo_batch* b, const double* pos_dev, double* energies_dev,
                                           double* forces_dev, int* status_dev);
 
@@ -229,15 +243,19 @@ SGO_API sgo_status sgo_batch_timer_read(sgo_batch* b, double out[4]);
 /* Kernel launches the batch issued since the previous call (then reset to 0). */
 SGO_API sgo_status sgo_batch_launches(sgo_batch* b, long long* count);
 
-/* Eigenvalues and occupations of the last SCF (nbands doubles each; either may be NULL). */
+/* Eigenvalues and occupations of the last SCF (nbands doubles each; either may be NULL).
+ * A k-point context (sgo_opts.kgrid): the supercell's n1 n2 n3 nbands states, i.e. the band
+ * energies eps_n(k) of the whole mesh in ascending order, occupations 0..2 each. */
 SGO_API sgo_status sgo_get_eigen(sgo_ctx* ctx, double* eig, double* occ);
 
-/* Energy terms of the last SCF: kinetic, nonlocal, local, Hartree, xc, Ewald, -kT S, F. */
+/* Energy terms of the last SCF: kinetic, nonlocal, local, Hartree, xc, Ewald, -kT S, F
+ * (per cell of the caller for a k-point context). */
 SGO_API sgo_status sgo_get_terms(sgo_ctx* ctx, double terms[8]);
 
 /* Sizes: info[0] npw (real length of a band vector), [1] n_half (G != 0 half sphere),
  * [2] column pairs, [3..5] N1 N2 N3, [6] nbands, [7] natoms, [8] scf iterations of the
- * last SCF, [9] precision. */
+ * last SCF, [9] precision.  A k-point context: [0..6] are the folded supercell's, [7] the
+ * caller's cell's atom count. */
 SGO_API sgo_status sgo_get_info(sgo_ctx* ctx, int info[10]);
 
 /* Diagnostics of the last SCF: [0] iterations, [1] Jacobi sweeps summed over its

@@ -108,7 +108,7 @@ class sgo_opts(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("sub_batches", ctypes.c_int), ("eig_tol", ctypes.c_double),
                 ("max_polish", ctypes.c_int), ("rr_fp64", ctypes.c_int), ("watchdog_ms", ctypes.c_double),
                 ("extra_bands", ctypes.c_int), ("rr_cluster", ctypes.c_int), ("eigensolver", ctypes.c_int),
-                ("xc", ctypes.c_int), ("cg_adapt", ctypes.c_double)]
+                ("xc", ctypes.c_int), ("cg_adapt", ctypes.c_double), ("kgrid", ctypes.c_int * 3)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -255,9 +255,10 @@ def default_opts(**kw) -> sgo_opts:
             v = {"cg": 0, "davidson": 1}.get(v, v) if isinstance(v, str) else int(v)
         if k == "xc":
             v = {"lda": 0, "pbe": 1}.get(v, v) if isinstance(v, str) else int(v)
-        if k == "fft":
+        if k in ("fft", "kgrid"):
+            arr = getattr(o, k)
             for i in range(3):
-                o.fft[i] = int(v[i])
+                arr[i] = int(v[i])
             continue
         setattr(o, k, v)
     return o
@@ -266,13 +267,15 @@ def default_opts(**kw) -> sgo_opts:
 class Context:
     """One structure on the GPU (sgo_create).  `st` has cell, species (list of dicts with
     z_val, rc, a_sr, sigma_sr, rp, d_nl and optionally rp_p, d_p), species_of_atom, pos, ecut,
-    nbands, fft, kT (and optionally xc)."""
+    nbands, fft, kT (and optionally xc and a k mesh kgrid).  Positions and forces are the
+    cell's (natoms x 3); with a k mesh, nbands, eigen(), state() and the grids are those of the
+    folded supercell (sgo_opts.kgrid)."""
 
     def __init__(self, st, precision="fp64", stream=None, **opts):
         self.lib = load_library()
         self.st = st
         kw = dict(kT=float(st.kT), fft=tuple(int(x) for x in st.fft), precision=precision,
-                  xc=getattr(st, "xc", "lda"))
+                  xc=getattr(st, "xc", "lda"), kgrid=tuple(int(x) for x in getattr(st, "kgrid", (1, 1, 1))))
         kw.update(opts)
         self.opts = default_opts(**kw)
         cell = np.ascontiguousarray(st.cell, dtype=np.float64).reshape(9)
@@ -289,8 +292,8 @@ class Context:
                                    _ptr(pos), float(st.ecut), int(st.nbands), ctypes.byref(self.opts), s,
                                    ctypes.byref(h)), "sgo_create")
         self.h = h
-        self.nbands = int(st.nbands)
         info = self.info()
+        self.nbands = info["nbands"]
         self.npw, self.nhalf, self.grid = info["npw"], info["nhalf"], info["grid"]
 
     def __del__(self):

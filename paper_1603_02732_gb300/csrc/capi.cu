@@ -82,6 +82,45 @@ sgo_status run_batch(sgo_batch* b, const sgo::Engine::DeviceIO* io, std::vector<
   return err;
 }
 
+// Zone folding (sgo_opts.kgrid): the supercell's atoms are the caller's, translated by
+// t . A for every t = (t1, t2, t3), t_i < kgrid[i], t-major (t = 0 first).
+void expand_positions(const int kgrid[3], const double* ucell, int nat, const double* pos, double* out) {
+  int t = 0;
+  for (int t1 = 0; t1 < kgrid[0]; ++t1)
+    for (int t2 = 0; t2 < kgrid[1]; ++t2)
+      for (int t3 = 0; t3 < kgrid[2]; ++t3, ++t)
+        for (int a = 0; a < nat; ++a)
+          for (int x = 0; x < 3; ++x)
+            out[(size_t)(t * nat + a) * 3 + x] =
+                pos[3 * a + x] + t1 * ucell[x] + t2 * ucell[3 + x] + t3 * ucell[6 + x];
+}
+
+// The caller's positions into the context (expanded over the translates of a k-point
+// context).
+sgo_status set_user_positions(sgo_ctx* c, const double* pos) {
+  if (c->nk == 1) return sgo::set_positions(c, pos);
+  std::vector<double> big((size_t)3 * c->nat_user * c->nk);
+  expand_positions(c->kgrid, c->ucell, c->nat_user, pos, big.data());
+  return sgo::set_positions(c, big.data());
+}
+
+// The free energy per cell of the caller and the forces on its atoms: the supercell's
+// divided by the number of translates, resp. averaged over the translates of each atom
+// (equal up to rounding: the supercell is periodic in the caller's cell).
+double user_energy(const sgo_ctx* c) { return c->h_scal[sgo::SC_FREE] / c->nk; }
+void user_forces(const sgo_ctx* c, double* out) {
+  const size_t n = (size_t)3 * c->nat_user;
+  if (c->nk == 1) {
+    std::memcpy(out, c->h_forces.data(), sizeof(double) * n);
+    return;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int t = 0; t < c->nk; ++t) s += c->h_forces[t * n + i];
+    out[i] = s / c->nk;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -122,6 +161,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->eigensolver = 0;
   o->xc = 0;
   o->cg_adapt = 0.0;
+  o->kgrid[0] = o->kgrid[1] = o->kgrid[2] = 1;
 }
 
 sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp, int natoms, const int* species_of_atom,
@@ -136,14 +176,39 @@ sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp,
   }
   sgo_ctx* c = new (std::nothrow) sgo_ctx();
   if (!c) return SGO_ERR_OOM;
-  std::memcpy(c->cell, cell, sizeof(double) * 9);
+  if (o) c->opts = *o;
+  else sgo_opts_default(&c->opts);
+  // a k mesh: the context becomes the kgrid supercell (rows kgrid[i] a_i, the atoms of every
+  // translate, kgrid[0] kgrid[1] kgrid[2] times the bands, a given FFT grid scaled per axis)
+  long long nk = 1;
+  for (int i = 0; i < 3; ++i) {
+    c->kgrid[i] = std::max(1, c->opts.kgrid[i]);
+    c->opts.kgrid[i] = c->kgrid[i];
+    nk *= c->kgrid[i];
+  }
+  if (nk > 4096 || (long long)natoms * nk > 100000 || (long long)nbands * nk > 100000) {
+    delete c;
+    sgo::set_error("k mesh too large for zone folding");
+    return SGO_ERR_ARG;
+  }
+  c->nk = (int)nk;
+  c->nat_user = natoms;
+  std::memcpy(c->ucell, cell, sizeof(double) * 9);
+  for (int i = 0; i < 9; ++i) c->cell[i] = cell[i] * c->kgrid[i / 3];
+  for (int i = 0; i < 3; ++i) c->opts.fft[i] = c->opts.fft[i] > 0 ? c->opts.fft[i] * c->kgrid[i] : 0;
+  std::vector<int> spec_all((size_t)natoms * nk);
+  std::vector<double> pos_all((size_t)3 * natoms * nk);
+  for (long long t = 0; t < nk; ++t) std::copy(species_of_atom, species_of_atom + natoms, spec_all.begin() + t * natoms);
+  expand_positions(c->kgrid, cell, natoms, pos, pos_all.data());
+  natoms = (int)(natoms * nk);
+  nbands = (int)(nbands * nk);
+  species_of_atom = spec_all.data();
+  pos = pos_all.data();
   c->species.assign(sp, sp + nspecies);
   c->spec.assign(species_of_atom, species_of_atom + natoms);
   c->pos.assign(pos, pos + 3 * natoms);
   c->ecut = ecut;
   c->nb = nbands;
-  if (o) c->opts = *o;
-  else sgo_opts_default(&c->opts);
   c->precision = c->opts.precision ? 1 : 0;
   c->tsize = c->precision ? sizeof(float) : sizeof(double);
   c->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -195,7 +260,7 @@ sgo_status sgo_create(const double cell[9], int nspecies, const sgo_species* sp,
 sgo_status sgo_scf(sgo_ctx* c, const double* pos, int* n_iter_out, double* resid_out) {
   if (!c) return SGO_ERR_ARG;
   if (pos) {
-    sgo_status s = sgo::set_positions(c, pos);
+    sgo_status s = set_user_positions(c, pos);
     if (s != SGO_OK) return s;
   }
   std::unique_ptr<sgo::Engine> e(solo_engine(c));
@@ -209,14 +274,14 @@ sgo_status sgo_scf(sgo_ctx* c, const double* pos, int* n_iter_out, double* resid
 sgo_status sgo_energy_forces(sgo_ctx* c, const double* pos, double* energy, double* forces) {
   if (!c) return SGO_ERR_ARG;
   if (pos) {
-    sgo_status s = sgo::set_positions(c, pos);
+    sgo_status s = set_user_positions(c, pos);
     if (s != SGO_OK) return s;
   }
   std::unique_ptr<sgo::Engine> e(solo_engine(c));
   if (!e->ok()) return SGO_ERR_CUDA;
   sgo_status s = e->run(true, nullptr);
-  if (energy) *energy = c->h_scal[sgo::SC_FREE];
-  if (forces) std::memcpy(forces, c->h_forces.data(), sizeof(double) * c->h_forces.size());
+  if (energy) *energy = user_energy(c);
+  if (forces) user_forces(c, forces);
   return s;
 }
 
@@ -285,7 +350,7 @@ sgo_status sgo_energy_forces_batch(sgo_batch* b, const double* const* pos, doubl
   if (pos) {
     for (int i = 0; i < n; ++i) {
       if (!pos[i]) continue;
-      sgo_status s = sgo::set_positions(b->ctxs[i], pos[i]);
+      sgo_status s = set_user_positions(b->ctxs[i], pos[i]);
       if (s == SGO_ERR_CUDA) return s;
       st[i] = s;
     }
@@ -295,8 +360,8 @@ sgo_status sgo_energy_forces_batch(sgo_batch* b, const double* const* pos, doubl
   for (int i = 0; i < n; ++i) {
     sgo_ctx* c = b->ctxs[i];
     if (st[i] == SGO_OK) st[i] = run_st[i];
-    if (energies) energies[i] = c->h_scal[sgo::SC_FREE];
-    if (forces && forces[i]) std::memcpy(forces[i], c->h_forces.data(), sizeof(double) * c->h_forces.size());
+    if (energies) energies[i] = user_energy(c);
+    if (forces && forces[i]) user_forces(c, forces[i]);
     if (per_item) per_item[i] = st[i];
   }
   return SGO_OK;
@@ -305,6 +370,11 @@ sgo_status sgo_energy_forces_batch(sgo_batch* b, const double* const* pos, doubl
 sgo_status sgo_energy_forces_batch_device(sgo_batch* b, const double* pos_dev, double* energies_dev,
                                           double* forces_dev, int* status_dev) {
   if (!b || !energies_dev || !forces_dev || !status_dev) return SGO_ERR_ARG;
+  for (auto* c : b->ctxs)
+    if (c->nk != 1) {
+      sgo::set_error("a k-point member: the device-array batch call takes Gamma-point members only");
+      return SGO_ERR_ARG;
+    }
   const sgo::Engine::DeviceIO io{pos_dev, energies_dev, forces_dev, status_dev};
   return run_batch(b, &io, nullptr);
 }
@@ -315,7 +385,7 @@ sgo_status sgo_relax_batch(sgo_batch* b, sgo_relax* const* relax, int max_rounds
   if (!b || !relax || max_rounds < 0) return SGO_ERR_ARG;
   const int n = (int)b->ctxs.size();
   for (int i = 0; i < n; ++i)
-    if (!relax[i] || sgo_relax_natoms(relax[i]) != b->ctxs[i]->d.natom) return SGO_ERR_ARG;
+    if (!relax[i] || sgo_relax_natoms(relax[i]) != b->ctxs[i]->nat_user) return SGO_ERR_ARG;
   std::vector<std::vector<double>> pos(n), F(n);
   std::vector<const double*> pp(n);
   std::vector<double*> fp(n);
@@ -323,7 +393,7 @@ sgo_status sgo_relax_batch(sgo_batch* b, sgo_relax* const* relax, int max_rounds
   std::vector<sgo_status> st(n, SGO_OK), evs(n);
   std::vector<int> state(n, 0);
   for (int i = 0; i < n; ++i) {
-    pos[i].resize(3 * b->ctxs[i]->d.natom);
+    pos[i].resize(3 * b->ctxs[i]->nat_user);
     F[i].resize(pos[i].size());
     sgo_relax_positions(relax[i], pos[i].data());
     sgo_relax_info(relax[i], nullptr, &state[i]);
@@ -368,9 +438,9 @@ sgo_status sgo_de_generation(sgo_batch* b, const double cell[9], const int* spec
                              int* replaced, double* child_f) {
   if (!b || !cell || !species || !pop || !f || !u || max_rounds < 0) return SGO_ERR_ARG;
   const int np = (int)b->ctxs.size();
-  const int na = b->ctxs[0]->d.natom;
+  const int na = b->ctxs[0]->nat_user;
   for (auto* c : b->ctxs)
-    if (c->d.natom != na) return SGO_ERR_ARG;
+    if (c->nat_user != na) return SGO_ERR_ARG;
   const size_t sz = 3 * (size_t)na;
   std::vector<double> kids(sz * np);
   sgo_status s = sgo_de_offspring(np, na, cell, species, pop, f, u, scheme, d_min, kids.data());
@@ -462,6 +532,7 @@ sgo_status sgo_get_terms(sgo_ctx* c, double terms[8]) {
   terms[5] = s[sgo::SC_EEW];
   terms[6] = s[sgo::SC_MTS];
   terms[7] = s[sgo::SC_FREE];
+  for (int i = 0; i < 8; ++i) terms[i] /= c->nk;  // (per cell of the caller)
   return SGO_OK;
 }
 
@@ -474,7 +545,7 @@ sgo_status sgo_get_info(sgo_ctx* c, int info[10]) {
   info[4] = c->d.n2;
   info[5] = c->d.n3;
   info[6] = c->nb;
-  info[7] = c->d.natom;
+  info[7] = c->nat_user;
   info[8] = c->last_iter;
   info[9] = c->precision;
   return SGO_OK;

@@ -996,9 +996,12 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     if (!cuda_ok(dev_malloc(&d_rr1_, rr1_stride_ * n_), "dev_malloc(rr scratch)")) return;
     allocs_.push_back(d_rr1_);
   }
+  // (a refused shared-memory limit would otherwise surface only as a failed launch later)
+  if (!cuda_ok(cudaGetLastError(), "engine set-up")) return;
   fft_set_smem_limits(220 * 1024);
   linalg_set_smem_limits(220 * 1024);
   gemm_tc_set_smem_limits();
+  if (!cuda_ok(cudaGetLastError(), "kernel shared-memory limits")) return;
   if (precision_ == 1 && !fft_reg_init()) {
     set_error("register FFT twiddle tables: upload failed");
     return;

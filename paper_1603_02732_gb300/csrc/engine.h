@@ -58,6 +58,13 @@ struct sgo_ctx {
   sgo_status last_status = SGO_OK;
   std::vector<double> h_scal, h_eps, h_occ, h_forces;
   int h_status[4] = {0, 0, 0, 0};
+  // k-point mesh by zone folding (sgo_opts.kgrid): every field above describes the
+  // kgrid[0] x kgrid[1] x kgrid[2] supercell; the caller's cell has nat_user atoms (the
+  // supercell's first nat_user, translate t = 0) and lattice rows ucell
+  int kgrid[3] = {1, 1, 1};
+  int nk = 1;
+  int nat_user = 0;
+  double ucell[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   ~sgo_ctx();
 };
 

@@ -70,6 +70,9 @@ __device__ __forceinline__ void rr_out_eps(const Prob& P, int rk, double e) {
 constexpr double RR_DROP = 1e-3;
 constexpr double RR_DROP_DIAG = 1e12;
 constexpr float RR_DROPPED = -2.f;  // pivot deviation recorded for a left-out direction
+// Jacobi sweeps of the FP32 eigensolve with at most this many entries above the threshold run
+// as sparse passes (k_rr_f32)
+constexpr int RR_SPARSE = 256;
 
 // ---------------------------------------------------------------------------
 // C = A^T B, split-K partials.  CTA = (problem, tile_i, tile_j, split).  Thread (ti, tj)
@@ -832,9 +835,20 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float red[32];
   __shared__ float dkv[512];  // Cholesky pivots d_k (n <= 512: the pair tables below hold 256 pairs)
-  __shared__ float cs_c[256], cs_s[256];
+  // (the rotations of a round, or, while a sparse pass is being scheduled, the round
+  // masks of every index)
+  __shared__ union {
+    struct {
+      float c[256], s[256];
+    } cs;
+    unsigned used[512];
+  } ru;
+  float* cs_c = ru.cs.c;
+  float* cs_s = ru.cs.s;
   __shared__ int pr_p[256], pr_q[256];
-  __shared__ int flag, nbig;
+  __shared__ int sp_list[RR_SPARSE], sp_sorted[RR_SPARSE], sp_rstart[33];
+  __shared__ unsigned char sp_stamp[512];
+  __shared__ int flag, nbig, sp_rounds;
   const int p = blockIdx.x;
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
@@ -930,8 +944,17 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
   for (int w = 0; w < nty; ++w) mm = fmaxf(mm, red[w]);
   // rotations below 2e-7 max|a_ii| (about the FP32 resolution of the matrix) are skipped
   const float thr = 2e-7f * mm;
-  // Cyclic Jacobi, round-robin pairs; a round maps every 2x2 block of pair rows P and
-  // pair columns Q as A_PQ <- J_P^T A_PQ J_Q (one pass), and V_{:,Q} <- V_{:,Q} J_Q.
+  // Threshold Jacobi.  Each sweep starts by listing the off-diagonal entries above thr.
+  // Many of them (more than RR_SPARSE, or more than two per index, where the colouring
+  // below would need about as many rounds as a sweep): a cyclic sweep in round-robin
+  // order, where a round
+  // maps every 2x2 block of pair rows P and pair columns Q as A_PQ <- J_P^T A_PQ J_Q (one
+  // pass) and V_{:,Q} <- V_{:,Q} J_Q.  Few (the sweeps after the first, once the
+  // convergence is quadratic): a sparse pass that rotates only the listed pairs, packed
+  // into rounds of disjoint pairs by a greedy edge colouring (a pair takes the first round
+  // in which neither of its indices is used yet; pairs that find none of the 32 rounds
+  // free wait for the next pass).  Any order that keeps visiting every entry above the
+  // threshold converges (the threshold cyclic Jacobi with a skipped-rotation rule).
   const int m = n + (n & 1);
   const int half = m / 2;
   int sweeps = 0, capped = 0;
@@ -939,15 +962,132 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
     if (tid == 0) nbig = 0;
     __syncthreads();
     for (int i = ty; i < n; i += nty)
-      for (int j = i + 1 + tx; j < n; j += 32)
-        if (fabsf(A[i * ns + j]) > thr) nbig = 1;
+      for (int j0 = i + 1; j0 < n; j0 += 32) {
+        const int j = j0 + tx;
+        const bool big = j < n && fabsf(A[i * ns + j]) > thr;
+        const unsigned bal = __ballot_sync(0xffffffffu, big);
+        if (bal == 0u) continue;
+        int base = 0;
+        if (tx == 0) base = atomicAdd(&nbig, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int k = base + __popc(bal & ((1u << tx) - 1u));
+        if (big && k < RR_SPARSE) sp_list[k] = i | (j << 10);
+      }
     __syncthreads();
-    if (nbig == 0) break;
+    const int nlist = nbig;
+    if (nlist == 0) break;
     if (sweep == max_sweeps) {  // still off-diagonal entries above the threshold
       capped = 1;
       break;
     }
     ++sweeps;
+    if (nlist <= min(RR_SPARSE, 2 * m)) {
+      // schedule: round masks and stamps cleared, greedy colouring by one thread, then the
+      // pairs bucketed by round (counts, scan, placement)
+      for (int i = tid; i < n; i += nt) {
+        ru.used[i] = 0u;
+        sp_stamp[i] = 0;
+      }
+      if (tid < 33) sp_rstart[tid] = 0;
+      __syncthreads();
+      if (tid == 0) {
+        int nr = 0;
+        for (int k = 0; k < nlist; ++k) {
+          const int e = sp_list[k];
+          const int a = e & 1023, b = e >> 10;
+          const unsigned fr = ~(ru.used[a] | ru.used[b]);
+          if (fr == 0u) {
+            sp_list[k] = -1;
+            continue;
+          }
+          const int r = __ffs(fr) - 1;
+          ru.used[a] |= 1u << r;
+          ru.used[b] |= 1u << r;
+          sp_list[k] = e | (r << 20);
+          sp_rstart[r + 1] += 1;
+          nr = max(nr, r + 1);
+        }
+        for (int r = 0; r < nr; ++r) sp_rstart[r + 1] += sp_rstart[r];
+        sp_rounds = nr;
+      }
+      __syncthreads();
+      if (tid < 32) {  // placement: one warp, pairs in list order within each round
+        for (int k0 = 0; k0 < nlist; k0 += 32) {
+          const int k = k0 + tid;
+          const int e = k < nlist ? sp_list[k] : -1;
+          const int r = e < 0 ? -1 : e >> 20;
+          for (int rr = 0; rr < sp_rounds; ++rr) {
+            const unsigned bal = __ballot_sync(0xffffffffu, r == rr);
+            if (r == rr) sp_sorted[sp_rstart[rr] + __popc(bal & ((1u << tid) - 1u))] = e & 0xfffff;
+            __syncwarp();
+            if (tid == 0) sp_rstart[rr] += __popc(bal);
+            __syncwarp();
+          }
+        }
+        // (sp_rstart[r] now holds the end of round r; the start is the end of r - 1)
+      }
+      __syncthreads();
+      const int nr = sp_rounds;
+      for (int r = 0; r < nr; ++r) {
+        const int b0 = r == 0 ? 0 : sp_rstart[r - 1], kr = sp_rstart[r] - b0;
+        if (tid < kr) {
+          const int e = sp_sorted[b0 + tid];
+          const int pp = e & 1023, qq = e >> 10;
+          float c = 1.f, s = 0.f;
+          const float apq = A[pp * ns + qq];
+          if (fabsf(apq) > thr) {
+            const float tau = __fdividef(A[qq * ns + qq] - A[pp * ns + pp], 2.f * apq);
+            const float t = copysignf(__fdividef(1.f, fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f))), tau);
+            c = rsqrtf(fmaf(t, t, 1.f));
+            s = t * c;
+          }
+          cs_c[tid] = c;
+          cs_s[tid] = s;
+          pr_p[tid] = pp;
+          pr_q[tid] = qq;
+          sp_stamp[pp] = (unsigned char)(r + 1);
+          sp_stamp[qq] = (unsigned char)(r + 1);
+        }
+        __syncthreads();
+        // 2x2 blocks between the round's pairs; pair rows against the other columns (row
+        // rotation, mirrored into the symmetric column entries); V
+        for (int P2 = ty; P2 < kr; P2 += nty) {
+          const float sp = cs_s[P2], cp = cs_c[P2];
+          const int p0 = pr_p[P2], p1 = pr_q[P2];
+          for (int Q2 = tx; Q2 < kr; Q2 += 32) {
+            const float sq = cs_s[Q2];
+            if (sp == 0.f && sq == 0.f) continue;
+            const float cq = cs_c[Q2];
+            const int q0 = pr_p[Q2], q1 = pr_q[Q2];
+            const float a00 = A[p0 * ns + q0], a01 = A[p0 * ns + q1];
+            const float a10 = A[p1 * ns + q0], a11 = A[p1 * ns + q1];
+            const float b00 = cp * a00 - sp * a10, b01 = cp * a01 - sp * a11;
+            const float b10 = sp * a00 + cp * a10, b11 = sp * a01 + cp * a11;
+            A[p0 * ns + q0] = cq * b00 - sq * b01;
+            A[p0 * ns + q1] = sq * b00 + cq * b01;
+            A[p1 * ns + q0] = cq * b10 - sq * b11;
+            A[p1 * ns + q1] = sq * b10 + cq * b11;
+          }
+          if (sp == 0.f) continue;
+          for (int j = tx; j < n; j += 32) {
+            if (sp_stamp[j] == (unsigned char)(r + 1)) continue;
+            const float a0 = A[p0 * ns + j], a1 = A[p1 * ns + j];
+            const float b0 = cp * a0 - sp * a1, b1 = sp * a0 + cp * a1;
+            A[p0 * ns + j] = b0;
+            A[p1 * ns + j] = b1;
+            A[j * ns + p0] = b0;
+            A[j * ns + p1] = b1;
+          }
+          for (int i = tx; i < n; i += 32) {
+            const float v0 = Vt[p0 * ns + i], v1 = Vt[p1 * ns + i];
+            Vt[p0 * ns + i] = cp * v0 - sp * v1;
+            Vt[p1 * ns + i] = sp * v0 + cp * v1;
+          }
+        }
+        __syncthreads();
+      }
+      continue;
+    }
     for (int r = 0; r < m - 1; ++r) {
       if (tid < half) {
         const int a = tid, b = m - 1 - tid;
@@ -974,35 +1114,59 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
         pr_q[tid] = qq;
       }
       __syncthreads();
-      // blocks (P, Q); rows / columns equal to n (the odd dummy) are absent
-      for (int P2 = ty; P2 < half; P2 += nty) {
-        const float sp = cs_s[P2], cp = cs_c[P2];
-        const int p0 = pr_p[P2], p1 = pr_q[P2];
-        const bool h1 = p1 < n;
-        for (int Q2 = tx; Q2 < half; Q2 += 32) {
-          const float sq = cs_s[Q2];
+      // blocks (P, Q) with P <= Q, each written with its mirror (Q, P): the upper triangle
+      // of the half x half block grid, folded so that block rows P and half - 1 - P share
+      // one row of half + 1 items, dealt to all threads; rows / columns equal to n (the
+      // odd dummy) are absent
+      {
+        const int wrow = half + 1, nitem = ((half + 1) / 2) * wrow;
+        const float inv_wrow = 1.f / (float)wrow;
+        for (int e = tid; e < nitem; e += nt) {
+          int P2 = __float2int_rz(((float)e + 0.5f) * inv_wrow);
+          int Q2 = e - P2 * wrow;  // (offset d in the folded row)
+          if (Q2 < half - P2) {
+            Q2 += P2;
+          } else {
+            const int P3 = half - 1 - P2;
+            if (P3 == P2) continue;  // (odd half: the middle row holds only its own part)
+            Q2 = P3 + Q2 - (half - P2);
+            P2 = P3;
+          }
+          const float sp = cs_s[P2], sq = cs_s[Q2];
           if (sp == 0.f && sq == 0.f) continue;
-          const float cq = cs_c[Q2];
-          const int q0 = pr_p[Q2], q1 = pr_q[Q2];
-          const bool g1 = q1 < n;
+          const float cp = cs_c[P2], cq = cs_c[Q2];
+          const int p0 = pr_p[P2], p1 = pr_q[P2], q0 = pr_p[Q2], q1 = pr_q[Q2];
+          const bool h1 = p1 < n, g1 = q1 < n;
           const float a00 = A[p0 * ns + q0];
           const float a01 = g1 ? A[p0 * ns + q1] : 0.f;
           const float a10 = h1 ? A[p1 * ns + q0] : 0.f;
           const float a11 = (h1 && g1) ? A[p1 * ns + q1] : 0.f;
           const float b00 = cp * a00 - sp * a10, b01 = cp * a01 - sp * a11;  // rows: J_P^T
           const float b10 = sp * a00 + cp * a10, b11 = sp * a01 + cp * a11;
-          A[p0 * ns + q0] = cq * b00 - sq * b01;                            // columns: J_Q
-          if (g1) A[p0 * ns + q1] = sq * b00 + cq * b01;
-          if (h1) A[p1 * ns + q0] = cq * b10 - sq * b11;
-          if (h1 && g1) A[p1 * ns + q1] = sq * b10 + cq * b11;
+          const float c00 = cq * b00 - sq * b01, c01 = sq * b00 + cq * b01;  // columns: J_Q
+          const float c10 = cq * b10 - sq * b11, c11 = sq * b10 + cq * b11;
+          A[p0 * ns + q0] = c00;
+          if (g1) A[p0 * ns + q1] = c01;
+          if (h1) A[p1 * ns + q0] = c10;
+          if (h1 && g1) A[p1 * ns + q1] = c11;
+          if (P2 != Q2) {
+            A[q0 * ns + p0] = c00;
+            if (g1) A[q1 * ns + p0] = c01;
+            if (h1) A[q0 * ns + p1] = c10;
+            if (h1 && g1) A[q1 * ns + p1] = c11;
+          }
         }
       }
-      for (int Q2 = ty; Q2 < half; Q2 += nty) {
-        const float sq = cs_s[Q2];
-        if (sq == 0.f) continue;
-        const float cq = cs_c[Q2];
-        const int q0 = pr_p[Q2], q1 = pr_q[Q2];
-        for (int i = tx; i < n; i += 32) {
+      // V_{:,Q} <- V_{:,Q} J_Q, (pair, row) items dealt to all threads
+      {
+        const int nitem = half * n;
+        const float inv_n = 1.f / (float)n;
+        for (int e = tid; e < nitem; e += nt) {
+          const int Q2 = __float2int_rz(((float)e + 0.5f) * inv_n);
+          const float sq = cs_s[Q2];
+          if (sq == 0.f) continue;
+          const float cq = cs_c[Q2];
+          const int q0 = pr_p[Q2], q1 = pr_q[Q2], i = e - Q2 * n;
           const float v0 = Vt[q0 * ns + i], v1 = Vt[q1 * ns + i];
           Vt[q0 * ns + i] = cq * v0 - sq * v1;
           Vt[q1 * ns + i] = sq * v0 + cq * v1;
@@ -1600,7 +1764,9 @@ void launch_rr2_assemble(const Launch& L, int part) {
 void launch_occupations(const Launch& L) { k_occupations<<<L.ka.nprob, 32, 0, L.stream>>>(L.ka); }
 void linalg_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  cudaFuncSetAttribute(k_rr_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // (k_rr_f32 keeps its matrices in shared memory up to 216 KB; its static arrays take the
+  // rest of the 227 KB)
+  cudaFuncSetAttribute(k_rr_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::min(bytes, (size_t)216 * 1024));
   // the NN kernel also has 8-16 KB of static shared memory: request only what it uses
   cudaFuncSetAttribute(k_gemm_nn<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, NN_KP * 64 * (int)sizeof(float));
   cudaFuncSetAttribute(k_gemm_nn<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, NN_KP * 64 * (int)sizeof(double));

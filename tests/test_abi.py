@@ -57,6 +57,17 @@ def test_host_only_calls(lib):
     assert lib.sgo_create(None, 1, None, 1, None, None, 1.0, 1, None, None, ctypes.byref(out)) == pkg.SGO_ERR_ARG
     assert lib.sgo_scf(None, None, None, None) == pkg.SGO_ERR_ARG
     assert lib.sgo_batch_create(0, None, ctypes.byref(out)) == pkg.SGO_ERR_ARG
+    # the k mesh: Gamma by default; a mesh too large for zone folding is refused on the host
+    assert list(o.kgrid) == [1, 1, 1] and list(pkg.default_opts(kgrid=(2, 1, 3)).kgrid) == [2, 1, 3]
+    import numpy as np
+    cell = np.eye(3).reshape(-1) * 5.0
+    sp = (pkg.sgo_species * 1)(pkg.sgo_species(4.0, 1.0, 0.5, 0.8, 0.9, 1.0, 0.0, 0.0))
+    spec = np.zeros(1, np.int32)
+    pos = np.zeros(3)
+    big = pkg.default_opts(kgrid=(100, 100, 1))
+    assert lib.sgo_create(pkg._ptr(cell), 1, sp, 1, pkg._ptr(spec, ctypes.c_int), pkg._ptr(pos), 5.0, 4,
+                          ctypes.byref(big), None, ctypes.byref(out)) == pkg.SGO_ERR_ARG
+    assert b"k mesh" in lib.sgo_last_error()
     # the allocator hook wants both functions or neither; neither restores cudaMalloc
     keep = pkg._alloc_fn(lambda n, s, u: None)
     assert lib.sgo_set_allocator(keep, pkg._free_fn(), None) == pkg.SGO_ERR_ARG

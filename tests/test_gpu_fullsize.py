@@ -107,7 +107,9 @@ def _ledger_configs():
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-rr64", "fp64-davidson", "mixed-davidson"])
 def test_fullsize_error_ledger(sgo, name, precision):
     """Error ledger at full size against stored oracle values (tests/golden/ledger_*.json,
-    written by tests/golden/make_ledger.py from oracle/ alone): every eigenvalue with
+    written by tests/golden/make_ledger.py from oracle/ alone; the diamond cell's 2 x 2 x 2 k
+    mesh against oracle/kpoints.py's Bloch sums, the CUDA path folding the mesh onto the
+    64-atom supercell): every eigenvalue with
     occupation above 1e-6, every energy term, the free energy and every force component.
     Bounds: the accuracy gate (1e-5 Ha/atom, 1e-4 Ha/bohr) for F and forces; per energy
     term 1e-5 Ha/atom (FP64) or 1e-4 Ha/atom (mixed); per eigenvalue with occupation above
@@ -132,6 +134,8 @@ def test_fullsize_error_ledger(sgo, name, precision):
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"ledger_{name}.json")
     ref = json.load(open(path))
     st = workloads.CONFIGS[name]()
+    if st.kgrid != (1, 1, 1) and precision.endswith("davidson"):
+        pytest.skip("the k mesh's folded cell (169 bands) is checked with Algorithm 1's CG steps")
     tol = dict(scf_tol_e=1e-8, scf_tol_rho=1e-7) if precision.startswith("fp64") else dict(
         scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5)
     if precision == "mixed-rr64":
@@ -151,8 +155,13 @@ def test_fullsize_error_ledger(sgo, name, precision):
         ledger[k] = abs(terms[k] - ref["terms"][rk]) / n
     occ_ref = np.array(ref["occ"])
     occd = occ_ref > 1e-6
-    de = np.abs(eig - np.array(ref["eig"]))
-    ledger["max_deig_occupied"] = float(de[occd].max())
+    if occ_ref.ndim == 2:  # a k mesh: the folded cell's spectrum against the mesh's bands, sorted
+        e_ref, e_gpu = np.sort(np.array(ref["eig"])[occd]), np.sort(eig[occ > 1e-6])
+        assert len(e_ref) == len(e_gpu), (len(e_ref), len(e_gpu))
+        ledger["max_deig_occupied"] = float(np.abs(e_gpu - e_ref).max())
+    else:
+        de = np.abs(eig - np.array(ref["eig"]))
+        ledger["max_deig_occupied"] = float(de[occd].max())
     stats = ctx.stats()
     ledger.update(stats)
     print(name, precision, ledger)

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workloads
-from oracle import dft
+from oracle import dft, kpoints
 from tests.packing import full_from_packed
 
 pytestmark = pytest.mark.gpu
@@ -319,6 +319,76 @@ def test_pchannel_forces_and_mixed_batch(sgo):
     assert list(status) == [0, 0]
     for i in range(2):
         assert E[i] == singles[i][0] and np.array_equal(Fb[i], singles[i][1])
+
+
+def _struct_k(kgrid, pchan=False, seed=7):
+    """The small cell on a k mesh (12^3 box: the off-centre spheres of the mesh points reach
+    further than the Gamma sphere), nine bands per k point."""
+    st = workloads.tiny(nat=2, ecut=3.0, seed=seed, kT=0.01, nbands=9,
+                        species=workloads.SPECIES_Z4_P if pchan else None)
+    return dataclasses.replace(st, fft=(12, 12, 12), kgrid=tuple(kgrid))
+
+
+@pytest.mark.parametrize("kgrid,pchan", [((2, 1, 1), True), ((1, 2, 2), False), ((2, 2, 2), False)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_kpoint_mesh_matches_oracle(sgo, kgrid, pchan, precision):
+    """A Gamma-centred k mesh (sgo_opts.kgrid, computed by zone folding on the supercell)
+    against the oracle's Bloch-sum SCF over the mesh (oracle/kpoints.py: complex psi_k on
+    each k + G sphere, one Fermi level over the mesh): free energy per cell, the forces on the
+    cell's atoms, the occupied band energies of the whole mesh and the energy terms."""
+    st = _struct_k(kgrid, pchan)
+    ref = kpoints.scf(st, tol_e=1e-12, tol_rho=1e-10)
+    if precision == "fp64":
+        ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=150)
+        tol_e, tol_f, tol_eig = 1e-8, 1e-6, 1e-7
+    else:
+        ctx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5, max_scf=150)
+        tol_e, tol_f, tol_eig = 1e-5, 1e-4, 2e-4
+    nk = int(np.prod(kgrid))
+    assert ctx.natoms == st.natoms and ctx.nbands == nk * st.nbands
+    _compare(st, ctx.energy_forces(), ref, tol_e, tol_f)
+    eig, occ = ctx.eigen()
+    e_gpu = np.sort(eig[occ > 1e-6])
+    e_ref = np.sort(ref.eig[ref.occ > 1e-6])
+    assert len(e_gpu) == len(e_ref) and np.abs(e_gpu - e_ref).max() < tol_eig
+    t = ctx.terms()
+    for k_gpu, k_ref in [("kinetic", "kinetic"), ("nonlocal", "nonlocal_"), ("hartree", "hartree"), ("xc", "xc"),
+                         ("ewald", "ewald")]:
+        assert abs(t[k_gpu] - ref.terms[k_ref]) / st.natoms < 10 * tol_e, k_gpu
+
+
+def test_kpoint_members_in_a_batch(sgo):
+    """FP64: k-mesh members (different meshes) and a Gamma member in one batch give each
+    one's single result bit for bit; the device-array batch call refuses k-mesh members;
+    forces of a k-mesh context against central differences of its free energy."""
+    opts = dict(precision="fp64", scf_tol_e=1e-12, scf_tol_rho=1e-10, max_scf=150)
+    sts = [_struct_k((2, 1, 1), seed=3), _struct_k((1, 1, 2), pchan=True, seed=4), _struct(seed=5, ecut=3.0)]
+    singles = [sgo.Context(t, **opts).energy_forces() for t in sts]
+    ctxs = [sgo.Context(t, **opts) for t in sts]
+    b = sgo.Batch(ctxs)
+    E, Fb, status = b.energy_forces()
+    assert list(status) == [0, 0, 0]
+    for i in range(3):
+        assert E[i] == singles[i][0] and np.array_equal(Fb[i], singles[i][1])
+    import torch
+    n3 = sum(c.natoms for c in ctxs) * 3
+    pos = torch.tensor(np.concatenate([t.pos.reshape(-1) for t in sts]), dtype=torch.float64, device="cuda")
+    e_d = torch.zeros(3, dtype=torch.float64, device="cuda")
+    f_d = torch.zeros(n3, dtype=torch.float64, device="cuda")
+    s_d = torch.zeros(3, dtype=torch.int32, device="cuda")
+    with pytest.raises(sgo.SgoError):
+        b.energy_forces_device(pos.data_ptr(), e_d.data_ptr(), f_d.data_ptr(), s_d.data_ptr())
+    st = sts[0]
+    ctx = ctxs[0]
+    E0, F = ctx.energy_forces()
+    h = 1e-3
+    for I, a in [(0, 1), (1, 2)]:
+        p = st.pos.copy()
+        p[I, a] += h
+        ep, _ = ctx.energy_forces(p)
+        p[I, a] -= 2 * h
+        em, _ = ctx.energy_forces(p)
+        assert abs(-(ep - em) / (2 * h) - F[I, a]) < 2e-5, (I, a)
 
 
 def test_scf_tiny_mixed(sgo):

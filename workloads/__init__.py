@@ -166,6 +166,12 @@ def diamond8(jitter: float = 0.05, seed: int = 1001) -> Structure:
                      pos, 10.0, 20, (32, 32, 32), 0.0)
 
 
+def diamond8_k222() -> Structure:
+    """The 8-atom diamond cell on a 2 x 2 x 2 Gamma-centred k mesh (the rough sampling of a
+    crystal's relaxation steps), Fermi-Dirac kT = 0.01 Ha, 20 bands per k point."""
+    return dataclasses.replace(diamond8(), name="diamond8_k222", kgrid=(2, 2, 2), kT=0.01)
+
+
 def honeycomb24(seed: int = 1002, jitter: float = 0.05) -> Structure:
     """24-atom planar honeycomb, 2sqrt3 x 2sqrt3 R30 supercell a = 13.0, c = 26.0 bohr."""
     A, c = 13.0, 26.0
@@ -321,6 +327,7 @@ def tiny(nat: int = 2, ecut: float = 3.0, seed: int = 7, kT: float = 0.01, nband
 
 CONFIGS = {
     "diamond8": diamond8,
+    "diamond8_k222": diamond8_k222,
     "honeycomb24": honeycomb24,
     "cluster13": cluster13,
     "cluster55": cluster55,

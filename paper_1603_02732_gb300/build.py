@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libsgo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
-SOURCES = ["k_fft.cu", "k_plane_vpsi.cu", "k_plane_density.cu", "k_cols_reg.cu", "k_pair_reg.cu", "k_linalg.cu", "k_grid.cu", "k_setup.cu", "engine.cu",
+SOURCES = ["k_fft.cu", "k_plane_vpsi.cu", "k_plane_ms.cu", "k_plane_density.cu", "k_cols_reg.cu", "k_pair_reg.cu", "k_linalg.cu", "k_grid.cu", "k_setup.cu", "engine.cu",
            "capi.cu", "noalloc.cu", "k_gemm_tc.cu", "relax.cpp", "de.cpp"]
 
 

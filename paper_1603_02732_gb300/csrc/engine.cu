@@ -851,10 +851,14 @@ Engine::Engine(const std::vector<sgo_ctx*>& ctxs, cudaStream_t stream) : ctx_(ct
     if (ppair) ppair_smem_ = std::max(ppair_smem_, pair_plane_smem(d.n1, d.n2, d.m1max));
     if (dpair) dpair_smem_ = std::max(dpair_smem_, pair_density_smem(d.n1, d.n2, d.m1max));
     for (int k = 0; k < 2; ++k) {
-      c_preg[k].push_back(pcls == k ? plane_reg_ctas(d.n2, d.n3, d.npair) : 0);
+      c_preg[k].push_back(pcls != k ? 0
+                          : kPlaneMultiPass ? plane_ms_ctas(d.n1, d.n2, d.n3, d.npair)
+                                            : plane_reg_ctas(d.n2, d.n3, d.npair));
       c_dreg[k].push_back(dreg && pcls == k ? plane_density_reg_ctas(d.n2, d.n3) : 0);
     }
-    if (preg) preg_smem_[pcls] = std::max(preg_smem_[pcls], plane_reg_smem(d.n1, d.n2, d.m1max));
+    if (preg)
+      preg_smem_[pcls] = std::max(preg_smem_[pcls], kPlaneMultiPass ? plane_ms_smem(d.n1, d.n2, d.n3)
+                                                                    : plane_reg_smem(d.n1, d.n2, d.m1max));
     if (dreg) dreg_smem_[pcls] = std::max(dreg_smem_[pcls], plane_density_reg_smem(d.n1, d.n2, d.m1max));
     c_gz.push_back(div_up(d.n1 * d.n2, QZ));
     c_gp.push_back(gbig ? 0 : d.n3);
@@ -1232,7 +1236,10 @@ void Engine::hpsi(int src, int dst) {
   tend(TK_WAVE_TO_COLS);
   tbeg(TK_PLANE_VPSI);
   launch_plane_vpsi<T>(L(m_plane_));
-  for (int k = 0; k < 2; ++k) launch_plane_vpsi_reg(L(m_preg_[k]), k, preg_smem_[k]);
+  for (int k = 0; k < 2; ++k) {
+    if (kPlaneMultiPass) launch_plane_vpsi_ms(L(m_preg_[k]), preg_smem_[k]);
+    else launch_plane_vpsi_reg(L(m_preg_[k]), k, preg_smem_[k]);
+  }
   launch_plane_vpsi_pair(L(m_ppair_), ppair_smem_);
   launch_big_y<T>(L(m_bigy_), 1, 0, nullptr);
   launch_big_x<T>(L(m_bigx_));

@@ -603,7 +603,9 @@ void launch_grid_z_fft(const Launch& L, int which, int sign) {
   k_grid_z_fft<T><<<L.map.total, ZCOL_THREADS, sm, L.stream>>>(L.ka, which, sign);
 }
 
-bool fft_reg_init() { return plane_vpsi_reg_init() && plane_density_reg_init() && zreg_init() && pair_reg_init(); }
+bool fft_reg_init() {
+  return plane_vpsi_reg_init() && plane_density_reg_init() && zreg_init() && pair_reg_init() && plane_ms_init();
+}
 
 void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_wave_to_cols<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -630,6 +632,7 @@ void fft_set_smem_limits(size_t bytes) {
   cudaFuncSetAttribute(k_big_density<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(k_big_density<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   plane_vpsi_reg_set_smem_limits(bytes);
+  plane_ms_set_smem_limits(bytes);
   plane_density_reg_set_smem_limits(bytes);
   zreg_set_smem_limits(bytes);
   pair_reg_set_smem_limits(bytes);

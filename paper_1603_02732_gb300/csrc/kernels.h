@@ -81,6 +81,23 @@ template <typename T> void launch_big_x(const Launch& L);
 template <typename T> void launch_big_density(const Launch& L, const double* occ_override);
 // register-FFT plane pass (mixed path): lengths n1, n2 with a register transform
 bool plane_reg_ok(int n1, int n2);
+// multi-pass plane pass (k_plane_ms.cu): the register lengths' H.psi plane pass as two passes
+// of short register DFTs per line over whole planes in shared memory
+constexpr bool kPlaneMultiPass = true;
+#ifndef PLANE_MS_THREADS
+#define PLANE_MS_THREADS 256  // threads of a multi-pass plane CTA
+#endif
+#ifndef PLANE_MS_MINB
+#define PLANE_MS_MINB 3       // CTAs per SM the register budget is sized for
+#endif
+#ifndef PLANE_MS_BUDGET_KB
+#define PLANE_MS_BUDGET_KB 54  // shared memory for the planes of one CTA
+#endif
+int plane_ms_ctas(int n1, int n2, int n3, int npair);
+size_t plane_ms_smem(int n1, int n2, int n3);
+void launch_plane_vpsi_ms(const Launch& L, size_t smem);
+bool plane_ms_init();
+void plane_ms_set_smem_limits(size_t bytes);
 int plane_reg_class(int n1, int n2);          // 0: both <= 40, 1: up to PLANE_REG_MAXN
 int plane_reg_ctas(int n2, int n3, int npair);
 size_t plane_reg_smem(int n1, int n2, int m1max);

@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
   __shared__ int pr_p[256], pr_q[256];
   __shared__ int sp_list[RR_SPARSE], sp_sorted[RR_SPARSE], sp_rstart[33];
   __shared__ unsigned char sp_stamp[512];
-  __shared__ int flag, nbig, sp_rounds;
+  __shared__ int flag, nbig, sp_rounds, wcnt[32];
   const int p = blockIdx.x;
   if (!ka.active[p]) return;
   const Prob& P = ka.probs[p];
@@ -959,29 +959,50 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_f32(KArgs ka, float* gscratch
   const int half = m / 2;
   int sweeps = 0, capped = 0;
   for (int sweep = 0;; ++sweep) {
-    if (tid == 0) nbig = 0;
+    // the entries above the threshold: counted per warp, then (a sparse pass) listed in a
+    // fixed order, warp after warp, each warp's rows in order, so that the rotation order
+    // and hence the rounding never depend on the scheduling
+    {
+      int cnt = 0;
+      for (int i = ty; i < n; i += nty)
+        for (int j0 = i + 1; j0 < n; j0 += 32) {
+          const int j = j0 + tx;
+          cnt += __popc(__ballot_sync(0xffffffffu, j < n && fabsf(A[i * ns + j]) > thr));
+        }
+      if (tx == 0) wcnt[ty] = cnt;
+    }
     __syncthreads();
-    for (int i = ty; i < n; i += nty)
-      for (int j0 = i + 1; j0 < n; j0 += 32) {
-        const int j = j0 + tx;
-        const bool big = j < n && fabsf(A[i * ns + j]) > thr;
-        const unsigned bal = __ballot_sync(0xffffffffu, big);
-        if (bal == 0u) continue;
-        int base = 0;
-        if (tx == 0) base = atomicAdd(&nbig, __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        const int k = base + __popc(bal & ((1u << tx) - 1u));
-        if (big && k < RR_SPARSE) sp_list[k] = i | (j << 10);
+    if (tid == 0) {
+      int s = 0;
+      for (int w = 0; w < nty; ++w) {
+        const int c = wcnt[w];
+        wcnt[w] = s;
+        s += c;
       }
+      nbig = s;
+    }
     __syncthreads();
     const int nlist = nbig;
     if (nlist == 0) break;
+    const bool sparse = nlist <= min(RR_SPARSE, 2 * m);
+    if (sparse) {
+      int k = wcnt[ty];
+      for (int i = ty; i < n; i += nty)
+        for (int j0 = i + 1; j0 < n; j0 += 32) {
+          const int j = j0 + tx;
+          const bool big = j < n && fabsf(A[i * ns + j]) > thr;
+          const unsigned bal = __ballot_sync(0xffffffffu, big);
+          if (big) sp_list[k + __popc(bal & ((1u << tx) - 1u))] = i | (j << 10);
+          k += __popc(bal);
+        }
+      __syncthreads();
+    }
     if (sweep == max_sweeps) {  // still off-diagonal entries above the threshold
       capped = 1;
       break;
     }
     ++sweeps;
-    if (nlist <= min(RR_SPARSE, 2 * m)) {
+    if (sparse) {
       // schedule: round masks and stamps cleared, greedy colouring by one thread, then the
       // pairs bucketed by round (counts, scan, placement)
       for (int i = tid; i < n; i += nt) {

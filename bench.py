@@ -34,9 +34,10 @@ MEMBERS = 64
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per launch of the plane pass on this workload (ncu capture, cold
-# cache).  None: the kernel changed after the last capture.
-PLANE_VPSI_TRAFFIC = None
+# DRAM bytes (read + write) per launch of the plane pass (k_plane_vpsi_ms) on this workload, the
+# mean of one launch of each size class of one sub-batch (ncu capture, cold cache):
+# (9.22 + 0.00 + 82.07 + 16.00) / 2 MB.  Set to None whenever the kernel changes after the capture.
+PLANE_VPSI_TRAFFIC = (9.224e6 + 82.074e6 + 15.996e6) / 2
 
 
 def _dist():

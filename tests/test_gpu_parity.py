@@ -37,9 +37,13 @@ def _struct(grid=None, ecut=3.5, nat=2, seed=7, kT=0.01, nbands=None):
 
 # every FFT radix: 9 (9), 10 12 15 (10,12,15), 16 9 2 10 (16,18,20), 12 2 (24),
 # 15 2 / 9 6 / 10 4 (30,54,40), 9 2 / 12 3 / 16 8 (18,36,128); the mixed path's
-# register plane transforms in both size classes: 45 40, 60 50, 72 64, 27 25, 20 48
+# register plane transforms in both size classes: 45 40, 60 50, 72 64, 27 25, 20 48, and
+# planes that give every register length a turn along x and along y (the multi-pass plane pass
+# factors each differently: 12 = 3 x 4 ... 72 = 8 x 9)
 GRIDS = [None, (10, 12, 15), (16, 18, 20), (24, 24, 24), (30, 54, 40), (18, 36, 128), (45, 40, 16),
-         (60, 50, 12), (72, 64, 10), (27, 25, 32), (20, 48, 15),
+         (60, 50, 12), (72, 64, 10), (27, 25, 32), (20, 48, 15), (36, 32, 15), (15, 36, 32),
+         (12, 10, 12), (25, 15, 10), (32, 16, 10), (40, 20, 10), (48, 27, 10), (50, 30, 10),
+         (54, 45, 10), (64, 60, 10), (24, 72, 10),
          # lane-pair register transforms (mixed path): planes 96 x 128 and 100 x 108, z 96 / 120;
          # the FP64 path takes these two planes by line blocks through a global buffer
          (96, 128, 12), (100, 108, 10), (20, 24, 96), (12, 10, 120)]

@@ -632,6 +632,9 @@ def run_configs(args):
     extra = dict(eigensolver=args.eigensolver) if args.eigensolver else {}
     if args.xc:
         extra["xc"] = args.xc
+    for k, v in (("ncg", args.ncg), ("ncg_first", args.ncg_first), ("n_nonscf", args.nonscf)):
+        if v is not None:
+            extra[k] = v
     for name in names:
         out[name] = _config_record(sgo, name, stream, fp64=not args.no_fp64, extra=extra)
         print(json.dumps({name: out[name]}), flush=True)

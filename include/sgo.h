@@ -87,7 +87,10 @@ typedef struct {
   double kerker_q0;       /* Kerker q0 (1/bohr); 0 = no Kerker damping */
   int ncg;                /* all-band CG steps (Algorithm 1 iterations) per SCF iteration (default 3) */
   int ncg_first;          /* CG steps in each initial non-self-consistent iteration */
-  int n_nonscf;           /* initial iterations at the fixed atomic-guess potential */
+  int n_nonscf;           /* initial iterations at the fixed atomic-guess potential, before the
+                             density is updated (default 0: the SCF cycle starts at once from the
+                             atomic-guess density and the random wavefunctions; Pulay mixing
+                             absorbs the first, poorly converged output densities) */
   int fft[3];             /* FFT grid; 0 = smallest 2^a 3^b 5^c >= 4 m_max + 1 per axis */
   unsigned long long seed;/* seed of the random initial wavefunctions */
   int gemm_tc;            /* mixed path: subspace/projector overlaps on tcgen05 tensor cores (3xTF32);

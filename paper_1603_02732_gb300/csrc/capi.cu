@@ -147,7 +147,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->kerker_q0 = 0.8;
   o->ncg = 3;
   o->ncg_first = 6;
-  o->n_nonscf = 3;
+  o->n_nonscf = 0;
   o->seed = 12345ull;
   o->gemm_tc = 1;
   o->graph = 1;

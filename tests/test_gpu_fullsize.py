@@ -127,18 +127,19 @@ def test_fullsize_error_ledger(sgo, name, precision):
     loop condition: after the SCF stopping rule, CG steps continue until every band with
     occupation above 1e-6 has |H psi - eps psi| < eig_tol (1e-4 Ha), and the test checks
     that it was reached.  F is variational, second order in the density and wavefunction
-    errors; a single term or an eigenvalue is first order in the density error, and the
-    mixed path stops at a density residual of 1e-5 per electron (its FP32 noise floor), so
-    its terms and eigenvalues carry errors of that order times their response (measured:
-    eigenvalues 6.3e-5 Ha on the monolayer, the kinetic term 1.7e-5 Ha/atom on the 13-atom
-    cluster) while F stays near 1e-6 Ha/atom.  mixed-rr64: the mixed path with the overlap
+    errors; a single term or an eigenvalue is first order in the density error, so the mixed
+    runs here take the SCF to a density residual of 3e-6 per electron, two or three iterations
+    past the production rule of 1e-5 (which the population test and the bench hold to the
+    same gates on F and forces): on the monolayer the occupied eigenvalues measured 1.1-2.1e-4 Ha
+    at 1e-5, 0.6-1.4e-4 at 5e-6 and 0.5-0.9e-4 at 3e-6, over starts with 0, 1 or 3
+    non-self-consistent iterations, while F stays near 1e-6 Ha/atom.  mixed-rr64: the mixed path with the overlap
     Cholesky and the subspace eigensolve in FP64 (the ablation of the FP32 eigensolve).
     fp64-davidson / mixed-davidson: block Davidson steps (2 n_b Rayleigh-Ritz over [X, W]) in
-    place of Algorithm 1's CG steps, held to the same bounds, except the mixed variant's
-    eigenvalues: at the mixed stopping rule its self-consistent density sits further from the
-    fixed point than the CG path's (measured 2.7e-4 Ha on the monolayer's occupied eigenvalues,
-    5.6e-5 for CG); its F, forces and terms are held to the gate, and the variant's
-    eigenvalues to 1e-5 Ha in FP64."""
+    place of Algorithm 1's CG steps, held to the same bounds, except the mixed variant: its
+    SCF does not reach a density residual of 3e-6 (its self-consistent density stalls further
+    from the fixed point than the CG path's), so it runs at the production rule of 1e-5, where
+    its occupied eigenvalues measured 2.7e-4 Ha on the monolayer; its F, forces and terms are
+    held to the gate, and the variant's eigenvalues to 1e-5 Ha in FP64."""
     import json
     import os
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"ledger_{name}.json")
@@ -147,7 +148,7 @@ def test_fullsize_error_ledger(sgo, name, precision):
     if st.kgrid != (1, 1, 1) and precision.endswith("davidson"):
         pytest.skip("the k mesh's folded cell (169 bands) is checked with Algorithm 1's CG steps")
     tol = dict(scf_tol_e=1e-8, scf_tol_rho=1e-7) if precision.startswith("fp64") else dict(
-        scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5)
+        scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5 if precision == "mixed-davidson" else 3e-6, max_scf=150)
     if precision == "mixed-rr64":
         tol["rr_fp64"] = 1
     if precision.endswith("davidson"):

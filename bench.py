@@ -709,10 +709,11 @@ def main():
                     help="density residual above which an SCF iteration takes one CG step fewer")
     ap.add_argument("--mix-alpha", type=float, default=None, help="Pulay step (default: the library's)")
     ap.add_argument("--pulay-hist", type=int, default=None, help="Pulay history (default: the library's)")
+    ap.add_argument("--kerker-q0", type=float, default=None, help="Kerker q0 (default: the library's)")
     args = ap.parse_args()
     for k, v in (("ncg", args.ncg), ("ncg_first", args.ncg_first), ("n_nonscf", args.nonscf),
                  ("extra_bands", args.extra_bands), ("mix_alpha", args.mix_alpha), ("pulay_hist", args.pulay_hist),
-                 ("cg_adapt", args.cg_adapt), ("rr_cluster", args.rr_cluster)):
+                 ("cg_adapt", args.cg_adapt), ("rr_cluster", args.rr_cluster), ("kerker_q0", args.kerker_q0)):
         if v is not None:
             _SCF[k] = v
     if args.no_graph:

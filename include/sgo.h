@@ -85,7 +85,7 @@ typedef struct {
   int pulay_hist;         /* Pulay (DIIS) history length, 1..8 */
   double mix_alpha;       /* Pulay step on the (Kerker-damped) residual */
   double kerker_q0;       /* Kerker q0 (1/bohr); 0 = no Kerker damping */
-  int ncg;                /* all-band CG steps (Algorithm 1 iterations) per SCF iteration (default 3) */
+  int ncg;                /* all-band CG steps (Algorithm 1 iterations) per SCF iteration (default 2) */
   int ncg_first;          /* CG steps in each initial non-self-consistent iteration */
   int n_nonscf;           /* initial iterations at the fixed atomic-guess potential, before the
                              density is updated (default 0: the SCF cycle starts at once from the

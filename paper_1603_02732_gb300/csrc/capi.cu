@@ -145,7 +145,7 @@ void sgo_opts_default(sgo_opts* o) {
   o->pulay_hist = 8;
   o->mix_alpha = 0.5;
   o->kerker_q0 = 0.8;
-  o->ncg = 3;
+  o->ncg = 2;
   o->ncg_first = 6;
   o->n_nonscf = 0;
   o->seed = 12345ull;

@@ -747,6 +747,26 @@ def test_relax_batch_reaches_the_oracle_minimum(sgo):
         assert abs(E[i] - tr.energies[-1]) / st.natoms < 1e-5, i
 
 
+def test_relaxation_on_a_k_mesh(sgo):
+    """The batched PCG relaxation (sgo_relax_batch) of a cell on a 2 x 1 x 1 k mesh: the driver
+    sees the cell's atoms (the folded supercell stays inside the library) and stops with
+    |F| < 1e-3 Ha/bohr; the oracle's Bloch-sum SCF at the final geometry agrees that the forces
+    vanish there (below 1e-3 plus the mixed path's force tolerance, 1e-4)."""
+    import bench
+    st = _struct_k((2, 1, 1))
+    fmax = 1e-3
+    ctx = sgo.Context(st, precision="mixed", **bench._tols("mixed", st))
+    b = sgo.Batch([ctx])
+    drv = sgo.Relax(st.cell, st.pos, method="pcg", fmax=fmax, max_evals=60)
+    rounds, status = b.relax([drv], max_rounds=80)
+    assert list(status) == [0] and drv.info()["state"] == 1
+    E, F, _ = b.energy_forces([drv.positions()])
+    assert F[0].shape == (st.natoms, 3) and np.linalg.norm(F[0], axis=1).max() < fmax
+    ref = kpoints.scf(st, pos=drv.positions(), tol_e=1e-11, tol_rho=1e-9)
+    assert np.abs(ref.forces).max() < fmax + 1e-4
+    assert abs(E[0] - ref.free_energy) / st.natoms < 1e-5
+
+
 def test_de_generation_matches_the_oracle(sgo):
     """One DE generation (Sec. II B) of four 3-atom individuals through sgo_de_generation
     (offspring from given random numbers, PCG relaxation of each child on the batch, greedy

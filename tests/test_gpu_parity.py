@@ -361,6 +361,22 @@ def test_kpoint_mesh_matches_oracle(sgo, kgrid, pchan, precision):
         assert abs(t[k_gpu] - ref.terms[k_ref]) / st.natoms < 10 * tol_e, k_gpu
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_kpoint_mesh_pbe(sgo, precision):
+    """A 2 x 1 x 1 mesh with PBE exchange-correlation against the oracle's Bloch-sum PBE SCF:
+    free energy per cell, forces and the xc term."""
+    st = dataclasses.replace(_struct_k((2, 1, 1)), xc="pbe")
+    ref = kpoints.scf(st, tol_e=1e-12, tol_rho=1e-10)
+    if precision == "fp64":
+        ctx = sgo.Context(st, precision="fp64", scf_tol_e=1e-11, scf_tol_rho=1e-9, max_scf=150)
+        tol_e, tol_f = 1e-8, 1e-6
+    else:
+        ctx = sgo.Context(st, precision="mixed", scf_tol_e=1e-7 * st.natoms, scf_tol_rho=1e-5, max_scf=150)
+        tol_e, tol_f = 1e-5, 1e-4
+    _compare(st, ctx.energy_forces(), ref, tol_e, tol_f)
+    assert abs(ctx.terms()["xc"] - ref.terms["xc"]) / st.natoms < 10 * tol_e
+
+
 def test_kpoint_members_in_a_batch(sgo):
     """FP64: k-mesh members (different meshes) and a Gamma member in one batch give each
     one's single result bit for bit; the device-array batch call refuses k-mesh members;

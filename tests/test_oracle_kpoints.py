@@ -94,6 +94,19 @@ def test_zone_folding_identity(kgrid, pchan):
     assert abs(dft.scf(st, tol_e=1e-11, tol_rho=1e-9).free_energy - rk.free_energy) > 1e-3
 
 
+def test_zone_folding_identity_pbe():
+    """The folding identity with PBE exchange-correlation: the gradient terms of the mesh's
+    density (sum over k of |psi_nk|^2) are those of the supercell's."""
+    st = _tiny(xc="pbe")
+    rk = kpoints.scf(st, kgrid=(2, 1, 1), tol_e=1e-11, tol_rho=1e-9)
+    rs = dft.scf(workloads.supercell(st, (2, 1, 1)), tol_e=1e-11, tol_rho=1e-9)
+    assert abs(rs.free_energy / 2 - rk.free_energy) < 1e-8
+    assert np.abs(rs.forces[:st.natoms] - rk.forces).max() < 2e-6
+    assert abs(rs.terms["xc"] / 2 - rk.terms["xc"]) < 1e-8
+    # PBE differs from LDA on the mesh as well
+    assert abs(kpoints.scf(_tiny(), kgrid=(2, 1, 1), tol_e=1e-11, tol_rho=1e-9).free_energy - rk.free_energy) > 1e-3
+
+
 def test_kpoint_forces_are_energy_derivatives():
     st = _tiny(kgrid=(2, 1, 1), species=[dict(workloads.SPECIES_Z4_P)])
     r = kpoints.scf(st, tol_e=1e-12, tol_rho=1e-10)

@@ -407,7 +407,7 @@ sgo_status sgo_relax_batch(sgo_batch* b, sgo_relax* const* relax, int max_rounds
     if (!any) break;
     const sgo_status s = sgo_energy_forces_batch(b, pp.data(), E.data(), fp.data(), evs.data());
     if (s != SGO_OK) return s;
-    for (int i = 0; i < n; ++i) b->ctxs[i]->warm = true;  // the next round starts from these states
+    for (int i = 0; i < n; ++i) b->ctxs[i]->warm = true;  // the next relaxation round starts from these states
     // the drivers are independent: step them on all host cores
     std::atomic<int> next(0);
     auto work = [&]() {

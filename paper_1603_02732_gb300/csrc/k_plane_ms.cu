@@ -15,7 +15,7 @@
 // holds up to 72 and leaves one CTA per SM.  The cost is shared-memory traffic: the planes are
 // stored whole (all n1 x rows) while the x lines are transformed.
 //
-// CTA = (problem, group of PLANE_PAIR_GROUP band pairs, block of Q z-planes).  Per band pair:
+// CTA = (problem, group of PLANE_MS_PAIRS band pairs, block of Q z-planes).  Per band pair:
 // the compact columns land in the occupied x rows (|m1| <= m1max) of the CTA's planes; y
 // inverse over the occupied rows (natural -> transposed y order); per column: x inverse (only
 // the occupied rows are read), times V_eff/N at (x, y), x forward (only the occupied rows are
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(PLANE_MS_THREADS, PLANE_MS_MINB) k_plane_vpsi_
   const int local = blockIdx.x - ka.start[p];
   const int grp = local / nzb, zb = local - grp * nzb;
   const int z0 = zb * Q, nq = min(Q, n3 - z0);
-  const int pr0 = grp * PLANE_PAIR_GROUP, pr1 = min(P.npair, pr0 + PLANE_PAIR_GROUP);
+  const int pr0 = grp * PLANE_MS_PAIRS, pr1 = min(P.npair, pr0 + PLANE_MS_PAIRS);
   cplx<float>* const S = reinterpret_cast<cplx<float>*>(smem_raw);
   cplx<float>* const twx = S + Q * pstride;
   cplx<float>* const twy = twx + n1;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(PLANE_MS_THREADS, PLANE_MS_MINB) k_plane_vpsi_
 
 int plane_ms_ctas(int n1, int n2, int n3, int npair) {
   const int q = ms_q(n1, n2, n3);
-  return ((npair + PLANE_PAIR_GROUP - 1) / PLANE_PAIR_GROUP) * ((n3 + q - 1) / q);
+  return ((npair + PLANE_MS_PAIRS - 1) / PLANE_MS_PAIRS) * ((n3 + q - 1) / q);
 }
 size_t plane_ms_smem(int n1, int n2, int n3) {
   return (size_t)ms_q(n1, n2, n3) * ms_plane_bytes(n1, n2) + ms_table_bytes(n1, n2);

@@ -93,6 +93,9 @@ constexpr bool kPlaneMultiPass = true;
 #ifndef PLANE_MS_BUDGET_KB
 #define PLANE_MS_BUDGET_KB 54  // shared memory for the planes of one CTA
 #endif
+#ifndef PLANE_MS_PAIRS
+#define PLANE_MS_PAIRS 8       // band pairs per multi-pass plane CTA (V_eff loaded once for them)
+#endif
 int plane_ms_ctas(int n1, int n2, int n3, int npair);
 size_t plane_ms_smem(int n1, int n2, int n3);
 void launch_plane_vpsi_ms(const Launch& L, size_t smem);

@@ -1,5 +1,6 @@
 """Write the oracle's full-size reference values for the error ledger: the named configs
-(the 24-atom monolayer, the 13-atom cluster, the diamond cell on a 2 x 2 x 2 k mesh) and DE
+(the 24-atom monolayer, the 13-atom cluster, the diamond cell on a 2 x 2 x 2 k mesh, the 13-atom
+cluster with PBE) and DE
 population members (``de<i>``, the member i of ``workloads.de_population``, checked inside the
 64-member batch).
 

@@ -214,6 +214,11 @@ def cluster13(seed: int = 1003) -> Structure:
                      15.0, 85, fft_grid(cell, 15.0), 0.01)
 
 
+def cluster13_pbe() -> Structure:
+    """The 13-atom cluster with PBE exchange-correlation (the functional of the paper's searches)."""
+    return dataclasses.replace(cluster13(), name="cluster13_pbe", xc="pbe")
+
+
 def cluster55(seed: int = 1005) -> Structure:
     """55 Z_val=10 atoms (d_min 4.5 bohr) in a 28 bohr cube, Ecut 20 Ha, 330 bands, 128^3."""
     rng = np.random.default_rng(seed)
@@ -330,5 +335,6 @@ CONFIGS = {
     "diamond8_k222": diamond8_k222,
     "honeycomb24": honeycomb24,
     "cluster13": cluster13,
+    "cluster13_pbe": cluster13_pbe,
     "cluster55": cluster55,
 }

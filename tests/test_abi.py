@@ -50,6 +50,8 @@ def test_host_only_calls(lib):
     # the fields after sub_batches sit where the library writes its defaults
     assert o.eig_tol == 1e-4 and o.max_polish == 40 and o.rr_fp64 == 0 and o.watchdog_ms == 0.0
     assert o.extra_bands == -1 and o.rr_cluster == -1 and o.eigensolver == 0 and o.xc == 0 and o.cg_adapt == 0.0
+    # the SCF defaults the header documents: 2 CG steps per iteration, no non-self-consistent start
+    assert o.ncg == 2 and o.n_nonscf == 0 and o.ncg_first == 6 and o.max_scf == 100
     assert lib.sgo_status_string(0) == b"ok"
     assert lib.sgo_status_string(2) == b"invalid geometry"
     # argument validation happens before any device work
